@@ -1,0 +1,141 @@
+"""Pins of the oracle's tree and geometry (Sec. 2.1 Eq. 1, Tables 1-2; Sec. 2.3).
+
+Each test checks the oracle against something other than itself: values the
+paper prints, closed-form areas and ray intersections, or a published test
+vector.
+"""
+import ctypes as C
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    with open(os.path.join(GOLD, name)) as fh:
+        return [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+
+
+def _basic_tree(n):
+    row = [r for r in _rows("table1_basic.txt") if int(r[-1]) == n][0]
+    r1, r2, a1, a2, p1, p2, s0, w0, q, e, mn = map(float, row[1:12])
+    return O.make_tree(n, 2, s0, w0, (r1, r2), None, q, e, (a1, a2), (p1, p2), 0, 0, mn)
+
+
+@pytest.mark.parametrize("row", _rows("table2_geometry.txt"), ids=lambda r: "n=" + r[0])
+def test_table2_d0_l0_over_height(row):
+    """Table 2: D0/H and L0/H to all printed digits (H = vertical extent of the
+    cylinders, envelope included; n rewritings draw generations 0..n-1)."""
+    n, d0h, l0h = int(row[0]), float(row[1]), float(row[2])
+    t = _basic_tree(n)
+    seg = O.lsystem(t)
+    H = O.tree_height(seg)
+    assert round(t.w0 / H, 3) == pytest.approx(d0h, abs=1e-12)
+    assert round(t.s0 / H, 3) == pytest.approx(l0h, abs=1e-12)
+
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_branch_scaling_laws(n):
+    """Sec. 2.1: L_k = 0.8 L_{k-1} and D_k = 0.5^0.5 D_{k-1}; 2^n - 1 segments."""
+    seg = O.lsystem(_basic_tree(n))
+    assert len(seg) == 2 ** n - 1
+    for g in range(n):
+        rows = seg[seg[:, 7] == g]
+        assert len(rows) == 2 ** g
+        L = np.linalg.norm(rows[:, 3:6] - rows[:, 0:3], axis=1)
+        np.testing.assert_allclose(L, 100.0 * 0.8 ** g, rtol=1e-12)
+        np.testing.assert_allclose(rows[:, 6], 30.0 * 0.5 ** (0.5 * g), rtol=1e-12)
+
+
+def test_children_attach_at_parent_tip_with_branching_angle():
+    """Children start at the end of their parent and make angle |alpha| with it."""
+    seg = O.lsystem(_basic_tree(4))
+    ends = {tuple(np.round(r[3:6], 9)) for r in seg}
+    for r in seg[1:]:
+        assert tuple(np.round(r[0:3], 9)) in ends
+    # the trunk is vertical, its two children tilt by 30 degrees
+    trunk = seg[0]
+    assert np.allclose(trunk[3:6] - trunk[0:3], [0, 0, 100])
+    for r in seg[seg[:, 7] == 1]:
+        d = (r[3:6] - r[0:3]) / np.linalg.norm(r[3:6] - r[0:3])
+        assert math.degrees(math.acos(d[2])) == pytest.approx(30.0, abs=1e-9)
+
+
+def test_seeded_azimuths_spread_children_around_the_parent():
+    """Azimuth form: three children at the same tilt, distinct azimuths drawn
+    from the seed; same seed gives the same tree, another seed another one."""
+    t = O.make_tree(2, 3, 64, 19.2, (0.6,), (0.6,), alpha_deg=(35.0,), azimuth_mode=1, seed=2)
+    a = O.lsystem(t)
+    assert len(a) == 4
+    kids = a[1:]
+    dirs = (kids[:, 3:6] - kids[:, 0:3]) / np.linalg.norm(kids[:, 3:6] - kids[:, 0:3], axis=1)[:, None]
+    np.testing.assert_allclose(np.degrees(np.arccos(dirs[:, 2])), 35.0, atol=1e-9)
+    az = np.degrees(np.arctan2(dirs[:, 1], dirs[:, 0]))
+    assert len(set(np.round(az, 6))) == 3
+    np.testing.assert_array_equal(O.lsystem(t), a)
+    t.seed = 3
+    assert not np.allclose(O.lsystem(t), a)
+
+
+def test_splitmix64_published_vector():
+    L = O.lib()
+    L.orc_splitmix64.restype = C.c_uint64
+    L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+    want = [int(r[0]) for r in _rows("splitmix64_seed1234567.txt")]
+    assert [L.orc_splitmix64(1234567, k) for k in range(5)] == want
+
+
+def test_frontal_area_of_a_cross_flow_cylinder_is_l_times_d():
+    """A vertical cylinder seen along x projects to an L x D rectangle."""
+    seg = np.array([[10.0, 16.0, 4.0, 10.0, 16.0, 16.0, 2.0, 0.0]])
+    assert O.frontal_area(seg, 0.125) == pytest.approx(12.0 * 2.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("theta_deg", [20.0, 45.0, 70.0])
+def test_frontal_area_of_a_tilted_cylinder(theta_deg):
+    """Projection of a flat-capped cylinder whose axis makes angle theta with x:
+    L D sin(theta) + (pi/4) D^2 |cos(theta)| (rectangle plus two half ellipses)."""
+    th = math.radians(theta_deg)
+    L, D = 20.0, 4.0
+    p0 = np.array([30.0, 30.0, 30.0])
+    p1 = p0 + L * np.array([math.cos(th), 0.0, math.sin(th)])
+    seg = np.array([list(p0) + list(p1) + [D, 0.0]])
+    exact = L * D * math.sin(th) + math.pi / 4 * D * D * abs(math.cos(th))
+    assert O.frontal_area(seg, 1.0 / 64) == pytest.approx(exact, rel=3e-3)
+
+
+def test_link_fraction_against_circle_intersection():
+    """q along +x from a fluid point to a vertical cylinder: the chord formula."""
+    c = (20.0, 20.0)
+    r = 3.0
+    pr = O.cylinders_as_prims(np.array([[c[0], c[1], 0.0, c[0], c[1], 40.0, 2 * r, 0]]))
+    for y0 in (18.5, 20.0, 21.7):
+        xs = c[0] - math.sqrt(r * r - (y0 - c[1]) ** 2)
+        x0 = xs - 0.37
+        q = O.prim_ray(pr, [x0, y0, 10.0], [1.0, 0.0, 0.0])
+        assert q == pytest.approx(0.37, abs=1e-12)
+        assert not O.prim_inside(pr, [x0, y0, 10.0])
+        assert O.prim_inside(pr, [x0 + 1.0, y0, 10.0])
+    # a diagonal ray to a half-space: t = (d - n.x) / (n.dir)
+    hs = O.prims([(1, (0.0, 1.0, 0.0, 4.3))])
+    assert O.prim_ray(hs, [1.0, 5.0, 1.0], [1.0, -1.0, 1.0]) == pytest.approx(0.7, abs=1e-12)
+    # entering a cap: axis along z, ray along -z from above the top disc
+    assert O.prim_ray(pr, [20.5, 20.5, 40.25], [0.0, 0.0, -1.0]) == pytest.approx(0.25, abs=1e-12)
+
+
+def test_centre_of_mass_and_placement():
+    """Two equal cylinders mirrored about a point have their COM there; the
+    placed tree has its COM at (Lx/4, Ly/2, Lz/2) and a trunk of the asked length."""
+    seg = np.array([[0, 0, 0, 0, 0, 10, 2, 0], [4, 0, 0, 4, 0, 10, 2, 0]], float)
+    np.testing.assert_allclose(O.tree_com(seg), [2, 0, 5], atol=1e-12)
+    t = O.make_tree(2, 2, 12.0, 2.0, (0.6, 0.6), (0.7, 0.7), alpha_deg=(30.0, 30.0),
+                    azimuth_mode=1, seed=0)
+    s = O.place_tree(t, 12.0, (64, 32, 32))
+    np.testing.assert_allclose(O.tree_com(s), [16, 16, 16], atol=1e-12)
+    assert np.linalg.norm(s[0, 3:6] - s[0, 0:3]) == pytest.approx(12.0)
+    assert s[0, 6] == pytest.approx(2.0)
