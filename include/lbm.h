@@ -1,0 +1,210 @@
+/*
+ * liblbm: D3Q27 cumulant lattice Boltzmann time step on a block-refined mesh
+ * around an L-system tree, with interpolated bounce-back on the branches and
+ * the momentum-exchange drag, for NVIDIA GB300 (sm_103a).
+ *
+ * Paper: Tokiwa, Yin & Onishi, "Drag Crisis in Fractal Trees Revealed by
+ * Simulation and Theory".  Section references below are to that paper.
+ *
+ * Conventions common to every call
+ *  - Every call returns an lbm_status (0 on success, a negative code on
+ *    failure); no call aborts or throws across this boundary.
+ *  - Lattice units throughout: lengths in cells of the level named, the
+ *    inflow speed in cells per time step, density 1 at rest.  "Finest
+ *    cells" are cells of the finest refinement level.
+ *  - Population index i = (cx+1) + 3 (cy+1) + 9 (cz+1) for the D3Q27
+ *    velocity c_i = (cx, cy, cz), cx, cy, cz in {-1, 0, 1}; the opposite
+ *    direction is 26 - i.
+ *  - Host arrays of a level's cells are ordered x fastest, then y, then z,
+ *    over that level's real box (lbm_level_info).
+ *  - The caller owns every host buffer and the device buffer it binds
+ *    (lbm_bind_memory); the domain owns its host-side metadata only.  The
+ *    library never allocates device memory: all device state lives in the
+ *    bound buffer.
+ *  - Calls on one domain are not thread-safe.  Device work is issued
+ *    asynchronously on the stream given to lbm_create_domain; calls that
+ *    return device results to the host synchronise that stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_domain lbm_domain; /* opaque, owned by the library */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,    /* an argument or descriptor field is out of range */
+  LBM_ENOMEM = -2,    /* host allocation failed or the bound buffer is too small */
+  LBM_ECUDA = -3,     /* a CUDA runtime call failed (message: lbm_last_error) */
+  LBM_EUNSTABLE = -4, /* the watchdog found NaN/Inf or a density outside [0.5, 2] */
+  LBM_ESTATE = -5,    /* call out of order (e.g. stepping before binding memory) */
+  LBM_ETIMEOUT = -6   /* reserved: a bounded device wait gave up */
+} lbm_status;
+
+typedef enum {
+  LBM_BC_PERIODIC = 0, /* wrap around */
+  LBM_BC_INOUT = 1,    /* x only: uniform inflow at x = 0, zero-gradient outflow at x = nx (Sec. 2.3) */
+  LBM_BC_SLIP = 2,     /* specular reflection (free slip) */
+  LBM_BC_INFLOW = 3    /* y, z: equilibrium at rho = 1 and the inflow velocity (Sec. 2.3: inflow on all non-outlet faces) */
+} lbm_bc;
+
+typedef enum { LBM_FP32 = 1 } lbm_precision;
+
+/* Problem statement (Sec. 2.2-2.3): domain, inflow, Re_H, refinement.
+   Coarse level = level 0; every finer level halves the cell size and the
+   time step (acoustic scaling, nu_{l+1} = 2 nu_l in lattice units). */
+typedef struct {
+  int nx, ny, nz;          /* level-0 cells; periodic axes must be multiples of block */
+  int levels;              /* 1..6 refinement levels */
+  int block;               /* cells per block edge: 8 or 16 */
+  int bc[3];               /* lbm_bc per axis; x is PERIODIC or INOUT, y/z are PERIODIC, SLIP or INFLOW */
+  double u_in;             /* inflow speed U along +x, lattice units (0 < U < 0.3) */
+  double re_h;             /* Re_H = U H / nu on the finest level, H = tree height in finest cells;
+                              <= 0 selects nu_finest below */
+  double nu_finest;        /* finest-level lattice viscosity when re_h <= 0 */
+  double i_u;              /* inflow turbulence intensity; only 0 (uniform inflow) is supported */
+  unsigned long long seed; /* reserved for seeded inflow turbulence */
+  double refine_margin;    /* finest box = tree bounding box grown by this fraction per side (0.25) */
+  int precision;           /* lbm_precision */
+  int galilean;            /* 1: Galilean correction of the diagonal second-order cumulants */
+  double omega2;           /* bulk relaxation rate (1) */
+  int boxes[6][6];         /* optional refinement boxes R_l (l >= 1) in level-l cells,
+                              lo xyz then hi xyz (exclusive); all zero: derived from the tree */
+} lbm_domain_desc;
+
+/* Parametric L-system of Eq. (1), Sec. 2.1.  n rewritings of rule p1 draw
+   branch generations 0..n-1.  Child k of a branch gets length s * r[k],
+   diameter w * dfac[k] (the paper: q^e and (1-q)^e), and a frame rotated
+   by "+"(alpha[k]) about U and "/"(phi[k]) about H.  azimuth_mode 0 applies
+   + then / with the fixed phi[k]; azimuth_mode 1 applies / then + with phi
+   drawn uniformly in [0, 360) degrees from SplitMix64(seed) at counter
+   (index of the parent branch in drawing order) * children + k.  The trunk
+   points along +z.  The tree is scaled so the trunk is trunk_cells finest
+   cells long and its volume centroid is placed at (Lx/4, Ly/2, Lz/2) of the
+   domain (Sec. 2.3). */
+typedef struct {
+  int n;
+  int children;            /* 1..4 */
+  double s0, w0;           /* axiom A(s0, w0) */
+  double min_len;          /* rule p1 applies while s >= min */
+  double r[4], dfac[4], alpha_deg[4], phi_deg[4];
+  int azimuth_mode;
+  unsigned long long seed;
+  double trunk_cells;
+} lbm_tree_desc;
+
+/* Create a domain (host metadata only; no device work).  cuda_stream is a
+   cudaStream_t (NULL = legacy default stream).  *out receives the handle. */
+int lbm_create_domain(const lbm_domain_desc* desc, void* cuda_stream, lbm_domain** out);
+
+/* Build the tree of Eq. (1), place it, derive the refinement boxes (unless
+   given), classify the cells of every level and build the cut-link lists
+   with their wall fractions q (Sec. 2.2, interpolated bounce-back).  Must
+   precede lbm_memory_requirements.  Host only. */
+int lbm_set_geometry(lbm_domain* d, const lbm_tree_desc* tree);
+
+/* As lbm_set_geometry, from ready segments: n rows of 8 doubles
+   x0 y0 z0 x1 y1 z1 diameter generation, in finest cells, already placed. */
+int lbm_set_geometry_segments(lbm_domain* d, const double* seg, int n);
+
+/* General solid primitives in finest cells: kind[k] 0 = flat-capped
+   cylinder (params x0 y0 z0 x1 y1 z1 D -), 1 = half-space n.x <= d
+   (nx ny nz d), 2 = axis-aligned box (lo xyz, hi xyz); params n x 8.
+   A cell is solid when its centre lies in any primitive.  n = 0: no solid. */
+int lbm_set_geometry_prims(lbm_domain* d, const int* kind, const double* params, int n);
+
+/* Bytes of device memory the domain needs (populations, tables, scratch). */
+int lbm_memory_requirements(const lbm_domain* d, size_t* bytes);
+
+/* Bind a caller-owned device buffer of at least the required size (256-byte
+   aligned), upload the tables and set every population to the inflow
+   equilibrium.  The buffer must stay valid until lbm_destroy. */
+int lbm_bind_memory(lbm_domain* d, void* device_ptr, size_t bytes);
+
+/* Equilibrium state rho, u on every level (resets the force history). */
+int lbm_init_uniform(lbm_domain* d, double rho, const double u[3]);
+
+/* Equilibrium state from host fields over one level's real box:
+   rho[n], u[3n] (x fastest); n must equal the box's cell count. */
+int lbm_init_field(lbm_domain* d, int level, const double* rho, const double* u, size_t n);
+
+/* Advance n coarse steps (2^l steps of level l each), asynchronously.
+   Returns the status of the last watchdog check (lbm_set_watchdog). */
+int lbm_step(lbm_domain* d, int n_coarse);
+
+/* Momentum-exchange force on the tree (Sec. 2.2, Wen et al. 2014) in
+   finest-level lattice units: force_last of the last finest step and
+   force_mean averaged over the finest steps since the last init or
+   lbm_reset_force; c_d = force_last[0] / (1/2 U^2 A_x) (Eq. 7, rho = 1,
+   A_x in finest cells^2).  Any pointer may be NULL.  Synchronises. */
+int lbm_drag(lbm_domain* d, double force_last[3], double force_mean[3], double* c_d);
+int lbm_reset_force(lbm_domain* d);
+
+/* Populations f_i(x) of one level's real box (27 per cell, NaN for cells
+   that are not fluid), at the current coarse-step boundary.  Synchronises. */
+int lbm_get_populations(lbm_domain* d, int level, double* f, size_t n_cells);
+
+/* Density and velocity per cell of one level's real box (NaN: not fluid). */
+int lbm_get_velocity(lbm_domain* d, int level, double* rho, double* u, size_t n_cells);
+
+/* Volume-weighted total mass and momentum of all levels, FP64 on device
+   (level-l cells weigh 8^-l).  Synchronises. */
+int lbm_mass(lbm_domain* d, double* mass, double mom[3]);
+
+/* Real box [lo, hi) of a level in level-l cells, and cell counts. */
+int lbm_level_info(const lbm_domain* d, int level, int lo[3], int hi[3], long long* n_fluid,
+                   long long* n_links, long long* n_active_blocks);
+
+/* Tree height H and frontal area A_x (finest cells), finest viscosity. */
+int lbm_geometry_info(const lbm_domain* d, double* height, double* frontal_area, int* n_segments,
+                      double* nu_finest);
+
+/* Cell type per cell of a level's real box: 0 fluid, 1 solid, 2 covered by
+   the next finer level. */
+int lbm_get_cell_types(const lbm_domain* d, int level, unsigned char* out, size_t n_cells);
+
+/* Cut links of a level: cell (linear index over the real box), direction
+   and wall fraction q; n is the capacity, *count the number of links. */
+int lbm_get_links(const lbm_domain* d, int level, long long* cell, int* dir, double* q, size_t n,
+                  long long* count);
+
+/* Placed segments (rows of 8 doubles) of the tree; n capacity. */
+int lbm_get_segments(const lbm_domain* d, double* seg, int n, int* count);
+
+/* Every `every` coarse steps lbm_step checks for NaN/Inf and densities
+   outside [0.5, 2] (synchronising); 0 disables (default). */
+int lbm_set_watchdog(lbm_domain* d, int every);
+
+/* 1: replay one captured CUDA graph per coarse step (default); 0: launch
+   the kernels directly. */
+int lbm_use_graphs(lbm_domain* d, int on);
+
+/* Kernel timing with CUDA events on the domain's stream (adds no
+   synchronisation inside lbm_step; graphs are bypassed while on).
+   lbm_get_timing returns, per kernel class k (0 collide-stream, 1 faces,
+   2 bounce-back + force, 3 interface), the summed milliseconds, the number
+   of launches and the cell updates / links processed.  Synchronises. */
+int lbm_set_timing(lbm_domain* d, int on);
+int lbm_get_timing(lbm_domain* d, double ms[4], long long launches[4], long long units[4]);
+
+/* Cell updates per coarse step (sum over levels of fluid cells * 2^l) and
+   the number of kernels launched per coarse step. */
+int lbm_work_per_step(const lbm_domain* d, long long* cell_updates, int* kernels);
+
+/* Write / read the full state (populations, parities, step and force
+   history) to / from a file; the domain must be built identically. */
+int lbm_save(lbm_domain* d, const char* path);
+int lbm_load(lbm_domain* d, const char* path);
+
+void lbm_destroy(lbm_domain* d);
+const char* lbm_status_string(int status);
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -174,27 +174,22 @@ def refine_boxes(seg, levels, n0, block, margin=0.25):
     """Refinement boxes R_l (l >= 1) in level-l cells, [lo, hi).
 
     Finest level: the tree's bounding box grown by ``margin`` of its extent on
-    every side, then rounded outward to whole blocks of the next coarser level.
-    Each intermediate level: its finer box's footprint grown by one block of
-    its own parent level on every side."""
+    every side, rounded outward to whole blocks of finest cells.  Each coarser
+    level: the footprint of the next finer box on it, rounded outward to whole
+    blocks of its own cells and grown by one block on every side."""
     boxes = [None] * levels
     if levels == 1:
         return boxes
     lo, hi = tree_bbox(seg)
     ext = hi - lo
-    lo_f = lo - margin * ext
-    hi_f = hi + margin * ext
-    # finest level L-1; its parent is level L-2
-    lo_c = np.floor(lo_f / 2.0)
-    hi_c = np.ceil(hi_f / 2.0)
-    lo_c = np.floor(lo_c / block) * block
-    hi_c = np.ceil(hi_c / block) * block
-    boxes[levels - 1] = (2 * lo_c).astype(int).tolist() + (2 * hi_c).astype(int).tolist()
+    lo_f = np.floor((lo - margin * ext) / block) * block
+    hi_f = np.ceil((hi + margin * ext) / block) * block
+    boxes[levels - 1] = lo_f.astype(int).tolist() + hi_f.astype(int).tolist()
     for l in range(levels - 2, 0, -1):
-        f = boxes[l + 1]
-        lo_p = np.floor(np.array(f[:3]) / 4.0 / block) * block - block
-        hi_p = np.ceil(np.array(f[3:]) / 4.0 / block) * block + block
-        boxes[l] = (2 * lo_p).astype(int).tolist() + (2 * hi_p).astype(int).tolist()
+        f = np.array(boxes[l + 1], dtype=float)
+        lo_l = np.floor(f[:3] / 2.0 / block) * block - block
+        hi_l = np.ceil(f[3:] / 2.0 / block) * block + block
+        boxes[l] = lo_l.astype(int).tolist() + hi_l.astype(int).tolist()
     return boxes
 
 

@@ -1,0 +1,799 @@
+// C-ABI of liblbm (include/lbm.h): domain set-up, device memory binding,
+// the recursively sub-cycled step driver, drag and diagnostics.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace lbm;
+
+namespace {
+thread_local std::string g_error;
+
+int fail(int code, const std::string& msg) {
+  g_error = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  g_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return LBM_ECUDA;
+}
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+double rest_weight(int i) {
+  auto w1 = [](int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; };
+  return w1(cx(i)) * w1(cy(i)) * w1(cz(i));
+}
+
+// equilibrium: rho times the product of 1-D three-point distributions with
+// mean u_a and variance 1/3
+double equilibrium(int i, double rho, const double u[3]) {
+  auto phi = [](int c, double v) { return c == 0 ? 2.0 / 3.0 - v * v : 0.5 * (1.0 / 3.0 + v * v + c * v); };
+  return rho * phi(cx(i), u[0]) * phi(cy(i), u[1]) * phi(cz(i), u[2]);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+enum { KC_COLLIDE = 0, KC_FACES = 1, KC_WALLS = 2, KC_IFACE = 3 };
+}  // namespace
+
+struct lbm_domain {
+  lbm_domain_desc d{};
+  cudaStream_t stream = nullptr;
+  Tree tree;
+  bool have_tree = false;
+  std::vector<Prim> prims;
+  Mesh mesh;
+  bool built = false;
+  double H = 0, A_x = 0, nu_f = 0;
+  // device
+  char* base = nullptr;
+  size_t need = 0;
+  size_t off_partials = 0, off_accum = 0, off_mpart = 0;
+  int max_wall_parts = 0;
+  float feq_in[27];
+  int parity0 = 0;
+  long long steps = 0;
+  bool use_graphs = true;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int watchdog = 0;
+  int last_status = LBM_OK;
+  // timing
+  bool timing = false;
+  struct Rec {
+    cudaEvent_t a, b;
+    int cls;
+    long long units;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  double ms[4] = {0, 0, 0, 0};
+  long long launches[4] = {0, 0, 0, 0}, units[4] = {0, 0, 0, 0};
+
+  template <class T>
+  T* dev(size_t off) const { return reinterpret_cast<T*>(base + off); }
+};
+
+namespace {
+
+void free_graphs(lbm_domain* d) {
+  for (auto& g : d->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+cudaEvent_t take_event(lbm_domain* d) {
+  if (d->pool_used == d->pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    d->pool.push_back(e);
+  }
+  return d->pool[d->pool_used++];
+}
+
+struct Timed {
+  lbm_domain* d;
+  int cls;
+  long long units;
+  cudaEvent_t a = nullptr;
+  Timed(lbm_domain* dd, int c, long long u) : d(dd), cls(c), units(u) {
+    if (d->timing) {
+      a = take_event(d);
+      cudaEventRecord(a, d->stream);
+    }
+  }
+  ~Timed() {
+    if (d->timing) {
+      cudaEvent_t b = take_event(d);
+      cudaEventRecord(b, d->stream);
+      d->recs.push_back({a, b, cls, units});
+    }
+  }
+};
+
+int advance(lbm_domain* dm, int l, int parity) {
+  Mesh& m = dm->mesh;
+  Level& v = m.lv[l];
+  float* f = dm->dev<float>(v.off_f);
+  int rc;
+  {
+    Timed t(dm, KC_COLLIDE, v.n_fluid);
+    CollideArgs a{f, dm->dev<int>(v.off_nbr), dm->dev<int>(v.off_maskoff), dm->dev<uint8_t>(v.off_masks),
+                  v.n_active, (float)v.omega1, (float)dm->d.omega2, dm->d.galilean};
+    if ((rc = launch_collide(a, v.B, parity, dm->stream))) return rc;
+  }
+  if (l == 0 && !v.face[parity].empty()) {
+    Timed t(dm, KC_FACES, (long long)v.face[parity].size());
+    if ((rc = launch_faces(f, dm->dev<FaceEntry>(v.off_face[parity]), (int)v.face[parity].size(), nullptr,
+                           dm->feq_in, dm->stream)))
+      return rc;
+  }
+  if (!v.wall[parity].empty()) {
+    Timed t(dm, KC_WALLS, (long long)v.wall[parity].size());
+    int n = (int)v.wall[parity].size();
+    if ((rc = launch_walls(f, dm->dev<WallEntry>(v.off_wall[parity]), n, dm->dev<double>(dm->off_partials),
+                           dm->stream)))
+      return rc;
+    if (l == m.L - 1 &&
+        (rc = launch_force_reduce(dm->dev<double>(dm->off_partials), walls_partial_count(n),
+                                  dm->dev<double>(dm->off_accum), dm->stream)))
+      return rc;
+  }
+  if (l + 1 < m.L) {
+    Level& F = m.lv[l + 1];
+    float* ff = dm->dev<float>(F.off_f);
+    float* saved = dm->dev<float>(v.off_saved);
+    if ((rc = advance(dm, l + 1, 0))) return rc;
+    {
+      Timed t(dm, KC_IFACE, (long long)v.expl.size());
+      if ((rc = launch_explode(ff, f, dm->dev<ExplodeEntry>(v.off_expl), (int)v.expl.size(),
+                               dm->dev<SaveEntry>(v.off_save), (int)v.save.size(), saved, parity, dm->stream)))
+        return rc;
+    }
+    if ((rc = advance(dm, l + 1, 1))) return rc;
+    {
+      Timed t(dm, KC_IFACE, (long long)v.infl.size() + (long long)v.coal.size());
+      if ((rc = launch_inflow(ff, f, dm->dev<InflowEntry>(v.off_infl), (int)v.infl.size(), saved, parity,
+                              dm->stream)))
+        return rc;
+      if ((rc = launch_coalesce(f, ff, dm->dev<CoalesceEntry>(v.off_coal), (int)v.coal.size(), saved, parity,
+                                dm->stream)))
+        return rc;
+    }
+  }
+  return LBM_OK;
+}
+
+int kernels_per_step(const Mesh& m, int l) {
+  const Level& v = m.lv[l];
+  int k = 1;
+  if (l == 0 && !v.face[0].empty()) k += 1;
+  if (!v.wall[0].empty()) k += (l == m.L - 1) ? 2 : 1;
+  if (l + 1 < m.L) k += 2 * kernels_per_step(m, l + 1) + (v.expl.size() || v.save.size() ? 1 : 0) +
+                        (v.infl.empty() ? 0 : 1) + (v.coal.empty() ? 0 : 1);
+  return k;
+}
+
+int build(lbm_domain* d) {
+  // viscosity from Re_H = U H / nu on the finest level (Sec. 2.3)
+  if (d->d.re_h > 0) {
+    if (!(d->H > 0)) return fail(LBM_EINVAL, "Re_H needs a tree with a height");
+    d->nu_f = d->d.u_in * d->H / d->d.re_h;
+  } else {
+    d->nu_f = d->d.nu_finest;
+  }
+  if (!(d->nu_f > 0)) return fail(LBM_EINVAL, "viscosity must be positive");
+  int boxes[6][6];
+  std::memcpy(boxes, d->d.boxes, sizeof boxes);
+  bool given = false;
+  for (int l = 1; l < d->d.levels; ++l)
+    for (int q = 0; q < 6; ++q) given |= boxes[l][q] != 0;
+  if (d->d.levels > 1 && !given) {
+    if (!d->have_tree || d->tree.count() == 0) return fail(LBM_EINVAL, "refinement needs boxes or a tree");
+    refinement_boxes(d->tree, d->d.levels, d->d.block, d->d.refine_margin, boxes);
+  }
+  d->mesh = Mesh();
+  int rc = build_mesh(d->d, boxes, d->prims, &d->mesh);
+  if (rc) return fail(rc, d->mesh.error);
+  const int L = d->d.levels;
+  for (int l = 0; l < L; ++l) {
+    Level& v = d->mesh.lv[l];
+    v.nu = d->nu_f * std::ldexp(1.0, -(L - 1 - l));
+    v.omega1 = 1.0 / (3.0 * v.nu + 0.5);
+  }
+  // device layout
+  size_t off = 0;
+  auto put = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  d->max_wall_parts = 1;
+  size_t max_blocks = 1;
+  for (int l = 0; l < L; ++l) {
+    Level& v = d->mesh.lv[l];
+    v.off_f = put(v.f_elems() * sizeof(float));
+    v.off_nbr = put(v.nbr.size() * sizeof(int));
+    v.off_maskoff = put(v.maskoff.size() * sizeof(int));
+    v.off_masks = put(v.masks.size());
+    for (int p = 0; p < 2; ++p) {
+      v.off_wall[p] = put(v.wall[p].size() * sizeof(WallEntry));
+      v.off_face[p] = put(v.face[p].size() * sizeof(FaceEntry));
+    }
+    v.off_expl = put(v.expl.size() * sizeof(ExplodeEntry));
+    v.off_save = put(v.save.size() * sizeof(SaveEntry));
+    v.off_infl = put(v.infl.size() * sizeof(InflowEntry));
+    v.off_coal = put(v.coal.size() * sizeof(CoalesceEntry));
+    v.off_saved = put(v.save.size() * sizeof(float));
+    d->max_wall_parts = std::max(d->max_wall_parts, walls_partial_count((int)v.wall[0].size()));
+    max_blocks = std::max(max_blocks, (size_t)v.n_active);
+  }
+  d->off_partials = put((size_t)d->max_wall_parts * 3 * sizeof(double));
+  d->off_accum = put(8 * sizeof(double));
+  d->off_mpart = put(max_blocks * 5 * sizeof(double));
+  d->need = off;
+  double u[3] = {d->d.u_in, 0, 0};
+  for (int i = 0; i < 27; ++i) d->feq_in[i] = (float)(equilibrium(i, 1.0, u) - rest_weight(i));
+  d->built = true;
+  return LBM_OK;
+}
+
+int upload(lbm_domain* d) {
+  auto cp = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+    if (!bytes) return cudaSuccess;
+    return cudaMemcpyAsync(d->base + off, src, bytes, cudaMemcpyHostToDevice, d->stream);
+  };
+  for (Level& v : d->mesh.lv) {
+    CK(cp(v.off_nbr, v.nbr.data(), v.nbr.size() * sizeof(int)));
+    CK(cp(v.off_maskoff, v.maskoff.data(), v.maskoff.size() * sizeof(int)));
+    CK(cp(v.off_masks, v.masks.data(), v.masks.size()));
+    for (int p = 0; p < 2; ++p) {
+      CK(cp(v.off_wall[p], v.wall[p].data(), v.wall[p].size() * sizeof(WallEntry)));
+      CK(cp(v.off_face[p], v.face[p].data(), v.face[p].size() * sizeof(FaceEntry)));
+    }
+    CK(cp(v.off_expl, v.expl.data(), v.expl.size() * sizeof(ExplodeEntry)));
+    CK(cp(v.off_save, v.save.data(), v.save.size() * sizeof(SaveEntry)));
+    CK(cp(v.off_infl, v.infl.data(), v.infl.size() * sizeof(InflowEntry)));
+    CK(cp(v.off_coal, v.coal.data(), v.coal.size() * sizeof(CoalesceEntry)));
+  }
+  return LBM_OK;
+}
+
+int reset_force(lbm_domain* d) {
+  CK(cudaMemsetAsync(d->base + d->off_accum, 0, 8 * sizeof(double), d->stream));
+  return LBM_OK;
+}
+
+int fill_uniform(lbm_domain* d, double rho, const double u[3]) {
+  float dev[27];
+  for (int i = 0; i < 27; ++i) dev[i] = (float)(equilibrium(i, rho, u) - rest_weight(i));
+  for (Level& v : d->mesh.lv) {
+    int rc = launch_fill(d->dev<float>(v.off_f), v.n_storage, v.B, dev, d->stream);
+    if (rc) return fail(rc, cuda_error_string());
+  }
+  d->parity0 = 0;
+  return reset_force(d);
+}
+
+int level_parity(const lbm_domain* d, int l) { return l == 0 ? d->parity0 : 0; }
+
+// slot holding the incoming f_i of a cell at the current coarse-step boundary
+long long incoming_slot(const Level& v, int parity, int x, int y, int z, int i) {
+  if (!parity) return v.addr(x, y, z, i);
+  return v.addr(x - cx(i), y - cy(i), z - cz(i), opposite(i));
+}
+
+int capture_graphs(lbm_domain* d) {
+  if (!d->use_graphs || d->stream == nullptr || d->timing) return LBM_OK;
+  for (int p = 0; p < 2; ++p) {
+    if (d->graph[p]) continue;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = advance(d, 0, p);
+    cudaError_t e = cudaStreamEndCapture(d->stream, &g);
+    if (rc) return fail(rc, cuda_error_string());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&d->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  return LBM_OK;
+}
+
+int mass_device(lbm_domain* d, double* mass, double mom[3], double* bad) {
+  double m = 0, p[3] = {0, 0, 0}, b = 0;
+  std::vector<double> part;
+  for (int l = 0; l < d->mesh.L; ++l) {
+    Level& v = d->mesh.lv[l];
+    if (!v.n_active) continue;
+    int rc = launch_mass(d->dev<float>(v.off_f), d->dev<int>(v.off_nbr), d->dev<int>(v.off_maskoff),
+                         d->dev<uint8_t>(v.off_masks), v.n_active, v.B, level_parity(d, l),
+                         d->dev<double>(d->off_mpart), d->stream);
+    if (rc) return fail(rc, cuda_error_string());
+    part.resize((size_t)v.n_active * 5);
+    CK(cudaMemcpyAsync(part.data(), d->base + d->off_mpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    double w = std::ldexp(1.0, -3 * l), ml = 0, pl[3] = {0, 0, 0}, bl = 0;
+    for (int s = 0; s < v.n_active; ++s) {
+      // subtract the cells that are not fluid: k_mass skips them already
+      ml += part[5 * s];
+      pl[0] += part[5 * s + 1];
+      pl[1] += part[5 * s + 2];
+      pl[2] += part[5 * s + 3];
+      bl += part[5 * s + 4];
+    }
+    m += w * ml;
+    for (int a = 0; a < 3; ++a) p[a] += w * pl[a];
+    b += bl;
+  }
+  if (mass) *mass = m;
+  if (mom)
+    for (int a = 0; a < 3; ++a) mom[a] = p[a];
+  if (bad) *bad = b;
+  return LBM_OK;
+}
+
+bool valid_level(const lbm_domain* d, int level) { return d && d->built && level >= 0 && level < d->mesh.L; }
+
+long long box_cells(const Level& v) {
+  return (long long)(v.rhi[0] - v.rlo[0]) * (v.rhi[1] - v.rlo[1]) * (v.rhi[2] - v.rlo[2]);
+}
+
+int download_level(lbm_domain* d, const Level& v, std::vector<float>& host) {
+  host.resize(v.f_elems());
+  CK(cudaMemcpyAsync(host.data(), d->base + v.off_f, host.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                     d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_error.c_str(); }
+
+const char* lbm_status_string(int s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_EUNSTABLE: return "unstable: non-finite or out-of-range density";
+    case LBM_ESTATE: return "call out of order";
+    case LBM_ETIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+int lbm_create_domain(const lbm_domain_desc* desc, void* cuda_stream, lbm_domain** out) {
+  if (!desc || !out) return fail(LBM_EINVAL, "null argument");
+  *out = nullptr;
+  const lbm_domain_desc& s = *desc;
+  if (s.nx < 1 || s.ny < 1 || s.nz < 1 || s.levels < 1 || s.levels > 6 || (s.block != 8 && s.block != 16))
+    return fail(LBM_EINVAL, "domain size, levels (1..6) or block (8|16) out of range");
+  if ((long long)s.nx * s.ny * s.nz > (1LL << 34)) return fail(LBM_EINVAL, "domain too large");
+  if (s.bc[0] != LBM_BC_PERIODIC && s.bc[0] != LBM_BC_INOUT) return fail(LBM_EINVAL, "x faces: periodic or in/out");
+  for (int a = 1; a < 3; ++a)
+    if (s.bc[a] != LBM_BC_PERIODIC && s.bc[a] != LBM_BC_SLIP && s.bc[a] != LBM_BC_INFLOW)
+      return fail(LBM_EINVAL, "y/z faces: periodic, slip or inflow");
+  if (!(std::fabs(s.u_in) < 0.3)) return fail(LBM_EINVAL, "inflow speed must be below 0.3");
+  if (s.i_u != 0.0) return fail(LBM_EINVAL, "only uniform inflow (i_u = 0) is supported");
+  if (s.precision != LBM_FP32) return fail(LBM_EINVAL, "only FP32 populations are supported");
+  if (!(s.omega2 > 0 && s.omega2 < 2)) return fail(LBM_EINVAL, "omega2 must lie in (0, 2)");
+  auto* d = new (std::nothrow) lbm_domain();
+  if (!d) return fail(LBM_ENOMEM, "host allocation");
+  d->d = s;
+  d->stream = (cudaStream_t)cuda_stream;
+  *out = d;
+  return LBM_OK;
+}
+
+int lbm_set_geometry_prims(lbm_domain* d, const int* kind, const double* params, int n) {
+  if (!d || n < 0 || (n > 0 && (!kind || !params))) return fail(LBM_EINVAL, "bad primitives");
+  if (d->base) return fail(LBM_ESTATE, "geometry is fixed once memory is bound");
+  d->prims.clear();
+  for (int k = 0; k < n; ++k) {
+    if (kind[k] < 0 || kind[k] > 2) return fail(LBM_EINVAL, "primitive kind must be 0, 1 or 2");
+    Prim p{kind[k], {}};
+    std::memcpy(p.p, params + 8 * k, 8 * sizeof(double));
+    d->prims.push_back(p);
+  }
+  if (!d->have_tree) d->H = 0;
+  return build(d);
+}
+
+int lbm_set_geometry_segments(lbm_domain* d, const double* seg, int n) {
+  if (!d || n < 0 || (n > 0 && !seg)) return fail(LBM_EINVAL, "bad segments");
+  if (d->base) return fail(LBM_ESTATE, "geometry is fixed once memory is bound");
+  d->tree.seg.assign(seg, seg + 8 * (size_t)n);
+  d->have_tree = true;
+  d->prims.clear();
+  for (int k = 0; k < n; ++k) {
+    if (!(seg[8 * k + 6] > 0)) return fail(LBM_EINVAL, "segment diameter must be positive");
+    Prim p{0, {}};
+    std::memcpy(p.p, seg + 8 * k, 8 * sizeof(double));
+    d->prims.push_back(p);
+  }
+  d->H = n ? tree_height(d->tree) : 0.0;
+  d->A_x = n ? frontal_area(d->tree, 0.125) : 0.0;
+  return build(d);
+}
+
+int lbm_set_geometry(lbm_domain* d, const lbm_tree_desc* t) {
+  if (!d || !t) return fail(LBM_EINVAL, "null argument");
+  if (!(t->trunk_cells > 0)) return fail(LBM_EINVAL, "trunk_cells must be positive");
+  Tree tr;
+  int rc = build_lsystem(*t, &tr);
+  if (rc) return fail(rc, "bad L-system parameters");
+  if (tr.count() > 0) {
+    const int fin = 1 << (d->d.levels - 1);
+    double shift0[3] = {0, 0, 0};
+    tree_affine(&tr, t->trunk_cells / t->s0, shift0);
+    double c[3];
+    tree_centroid(tr, c);
+    double target[3] = {d->d.nx * fin / 4.0, d->d.ny * fin / 2.0, d->d.nz * fin / 2.0};
+    double sh[3] = {target[0] - c[0], target[1] - c[1], target[2] - c[2]};
+    tree_affine(&tr, 1.0, sh);
+  }
+  return lbm_set_geometry_segments(d, tr.seg.data(), tr.count());
+}
+
+int lbm_memory_requirements(const lbm_domain* d, size_t* bytes) {
+  if (!d || !bytes) return fail(LBM_EINVAL, "null argument");
+  if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
+  *bytes = d->need;
+  return LBM_OK;
+}
+
+int lbm_bind_memory(lbm_domain* d, void* ptr, size_t bytes) {
+  if (!d || !ptr) return fail(LBM_EINVAL, "null argument");
+  if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
+  if (bytes < d->need) return fail(LBM_ENOMEM, "bound buffer smaller than lbm_memory_requirements");
+  if ((uintptr_t)ptr & 255) return fail(LBM_EINVAL, "bound buffer must be 256-byte aligned");
+  free_graphs(d);
+  d->base = (char*)ptr;
+  int rc = upload(d);
+  if (rc) return rc;
+  double u[3] = {d->d.u_in, 0, 0};
+  if ((rc = fill_uniform(d, 1.0, u))) return rc;
+  d->steps = 0;
+  CK(cudaStreamSynchronize(d->stream));
+  return LBM_OK;
+}
+
+int lbm_init_uniform(lbm_domain* d, double rho, const double u[3]) {
+  if (!d || !u) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  int rc = fill_uniform(d, rho, u);
+  if (rc) return rc;
+  d->steps = 0;
+  CK(cudaStreamSynchronize(d->stream));
+  return LBM_OK;
+}
+
+int lbm_init_field(lbm_domain* d, int level, const double* rho, const double* u, size_t n) {
+  if (!d || !rho || !u) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
+  Level& v = d->mesh.lv[level];
+  if ((long long)n != box_cells(v)) return fail(LBM_EINVAL, "cell count does not match the level's box");
+  std::vector<float> host;
+  int rc = download_level(d, v, host);
+  if (rc) return rc;
+  const int par = level_parity(d, level);
+  size_t k = 0;
+  for (int z = v.rlo[2]; z < v.rhi[2]; ++z)
+    for (int y = v.rlo[1]; y < v.rhi[1]; ++y)
+      for (int x = v.rlo[0]; x < v.rhi[0]; ++x, ++k) {
+        if (v.cell_type(x, y, z) != FLUID) continue;
+        for (int i = 0; i < kQ; ++i) {
+          long long s = incoming_slot(v, par, x, y, z, i);
+          host[s] = (float)(equilibrium(i, rho[k], u + 3 * k) - rest_weight(i));
+        }
+      }
+  CK(cudaMemcpyAsync(d->base + v.off_f, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice,
+                     d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return LBM_OK;
+}
+
+int lbm_step(lbm_domain* d, int n) {
+  if (!d || n < 0) return fail(LBM_EINVAL, "bad argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  int rc = capture_graphs(d);
+  if (rc) return rc;
+  for (int k = 0; k < n; ++k) {
+    if (d->graph[d->parity0] && !d->timing) {
+      CK(cudaGraphLaunch(d->graph[d->parity0], d->stream));
+    } else {
+      if ((rc = advance(d, 0, d->parity0))) return fail(rc, cuda_error_string());
+    }
+    d->parity0 ^= 1;
+    d->steps++;
+    if (d->watchdog > 0 && d->steps % d->watchdog == 0) {
+      double bad = 0;
+      if ((rc = mass_device(d, nullptr, nullptr, &bad))) return rc;
+      d->last_status = bad > 0 ? LBM_EUNSTABLE : LBM_OK;
+      if (bad > 0) return fail(LBM_EUNSTABLE, "watchdog: non-finite or out-of-range density");
+    }
+  }
+  return d->last_status;
+}
+
+int lbm_drag(lbm_domain* d, double last[3], double mean[3], double* c_d) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  double acc[8];
+  CK(cudaMemcpyAsync(acc, d->base + d->off_accum, sizeof acc, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  if (last)
+    for (int a = 0; a < 3; ++a) last[a] = acc[a];
+  if (mean)
+    for (int a = 0; a < 3; ++a) mean[a] = acc[6] > 0 ? acc[3 + a] / acc[6] : 0.0;
+  if (c_d) {
+    double u = d->d.u_in;
+    *c_d = (d->A_x > 0 && u != 0) ? acc[0] / (0.5 * u * u * d->A_x) : std::numeric_limits<double>::quiet_NaN();
+  }
+  return LBM_OK;
+}
+
+int lbm_reset_force(lbm_domain* d) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  return reset_force(d);
+}
+
+int lbm_get_populations(lbm_domain* d, int level, double* f, size_t n) {
+  if (!d || !f) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
+  Level& v = d->mesh.lv[level];
+  if ((long long)n != box_cells(v)) return fail(LBM_EINVAL, "cell count does not match the level's box");
+  std::vector<float> host;
+  int rc = download_level(d, v, host);
+  if (rc) return rc;
+  const int par = level_parity(d, level);
+  size_t k = 0;
+  for (int z = v.rlo[2]; z < v.rhi[2]; ++z)
+    for (int y = v.rlo[1]; y < v.rhi[1]; ++y)
+      for (int x = v.rlo[0]; x < v.rhi[0]; ++x, ++k) {
+        bool fl = v.cell_type(x, y, z) == FLUID;
+        for (int i = 0; i < kQ; ++i)
+          f[27 * k + i] = fl ? rest_weight(i) + (double)host[incoming_slot(v, par, x, y, z, i)]
+                             : std::numeric_limits<double>::quiet_NaN();
+      }
+  return LBM_OK;
+}
+
+int lbm_get_velocity(lbm_domain* d, int level, double* rho, double* u, size_t n) {
+  if (!d || !rho || !u) return fail(LBM_EINVAL, "null argument");
+  if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
+  std::vector<double> f(n * 27);
+  int rc = lbm_get_populations(d, level, f.data(), n);
+  if (rc) return rc;
+  for (size_t k = 0; k < n; ++k) {
+    double r = 0, j[3] = {0, 0, 0};
+    for (int i = 0; i < kQ; ++i) {
+      double v = f[27 * k + i];
+      r += v;
+      j[0] += cx(i) * v;
+      j[1] += cy(i) * v;
+      j[2] += cz(i) * v;
+    }
+    rho[k] = r;
+    for (int a = 0; a < 3; ++a) u[3 * k + a] = j[a] / r;
+  }
+  return LBM_OK;
+}
+
+int lbm_mass(lbm_domain* d, double* mass, double mom[3]) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  return mass_device(d, mass, mom, nullptr);
+}
+
+int lbm_level_info(const lbm_domain* d, int level, int lo[3], int hi[3], long long* n_fluid, long long* n_links,
+                   long long* n_active_blocks) {
+  if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level or geometry not set");
+  const Level& v = d->mesh.lv[level];
+  for (int a = 0; a < 3; ++a) {
+    if (lo) lo[a] = v.rlo[a];
+    if (hi) hi[a] = v.rhi[a];
+  }
+  if (n_fluid) *n_fluid = v.n_fluid;
+  if (n_links) *n_links = (long long)v.links.size();
+  if (n_active_blocks) *n_active_blocks = v.n_active;
+  return LBM_OK;
+}
+
+int lbm_geometry_info(const lbm_domain* d, double* height, double* area, int* nseg, double* nu_f) {
+  if (!d || !d->built) return fail(LBM_ESTATE, "geometry not set");
+  if (height) *height = d->H;
+  if (area) *area = d->A_x;
+  if (nseg) *nseg = d->have_tree ? d->tree.count() : 0;
+  if (nu_f) *nu_f = d->nu_f;
+  return LBM_OK;
+}
+
+int lbm_get_cell_types(const lbm_domain* d, int level, unsigned char* out, size_t n) {
+  if (!out || !valid_level(d, level)) return fail(LBM_EINVAL, "bad argument");
+  const Level& v = d->mesh.lv[level];
+  if ((long long)n != box_cells(v)) return fail(LBM_EINVAL, "cell count does not match the level's box");
+  size_t k = 0;
+  for (int z = v.rlo[2]; z < v.rhi[2]; ++z)
+    for (int y = v.rlo[1]; y < v.rhi[1]; ++y)
+      for (int x = v.rlo[0]; x < v.rhi[0]; ++x, ++k) out[k] = (unsigned char)v.cell_type(x, y, z);
+  return LBM_OK;
+}
+
+int lbm_get_links(const lbm_domain* d, int level, long long* cell, int* dir, double* q, size_t n,
+                  long long* count) {
+  if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level or geometry not set");
+  const Level& v = d->mesh.lv[level];
+  if (count) *count = (long long)v.links.size();
+  if (!cell || !dir || !q) return LBM_OK;
+  const long long nx = v.rhi[0] - v.rlo[0], ny = v.rhi[1] - v.rlo[1];
+  for (size_t k = 0; k < v.links.size() && k < n; ++k) {
+    const Link& L = v.links[k];
+    cell[k] = (L.x - v.rlo[0]) + nx * ((L.y - v.rlo[1]) + ny * (L.z - v.rlo[2]));
+    dir[k] = L.dir;
+    q[k] = L.q;
+  }
+  return LBM_OK;
+}
+
+int lbm_get_segments(const lbm_domain* d, double* seg, int n, int* count) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  int c = d->have_tree ? d->tree.count() : 0;
+  if (count) *count = c;
+  if (seg)
+    for (int k = 0; k < c && k < n; ++k) std::memcpy(seg + 8 * k, &d->tree.seg[8 * k], 8 * sizeof(double));
+  return LBM_OK;
+}
+
+int lbm_set_watchdog(lbm_domain* d, int every) {
+  if (!d || every < 0) return fail(LBM_EINVAL, "bad argument");
+  d->watchdog = every;
+  return LBM_OK;
+}
+
+int lbm_use_graphs(lbm_domain* d, int on) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  d->use_graphs = on != 0;
+  if (!on) free_graphs(d);
+  return LBM_OK;
+}
+
+int lbm_set_timing(lbm_domain* d, int on) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  d->timing = on != 0;
+  return LBM_OK;
+}
+
+int lbm_get_timing(lbm_domain* d, double ms[4], long long launches[4], long long units[4]) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (d->base) CK(cudaStreamSynchronize(d->stream));
+  for (auto& r : d->recs) {
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    d->ms[r.cls] += t;
+    d->launches[r.cls] += 1;
+    d->units[r.cls] += r.units;
+  }
+  d->recs.clear();
+  d->pool_used = 0;
+  for (int k = 0; k < 4; ++k) {
+    if (ms) ms[k] = d->ms[k];
+    if (launches) launches[k] = d->launches[k];
+    if (units) units[k] = d->units[k];
+    d->ms[k] = 0;
+    d->launches[k] = 0;
+    d->units[k] = 0;
+  }
+  return LBM_OK;
+}
+
+int lbm_work_per_step(const lbm_domain* d, long long* cell_updates, int* kernels) {
+  if (!d || !d->built) return fail(LBM_ESTATE, "geometry not set");
+  long long cu = 0;
+  for (int l = 0; l < d->mesh.L; ++l) cu += d->mesh.lv[l].n_fluid << l;
+  if (cell_updates) *cell_updates = cu;
+  if (kernels) *kernels = kernels_per_step(d->mesh, 0);
+  return LBM_OK;
+}
+
+int lbm_save(lbm_domain* d, const char* path) {
+  if (!d || !path) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(LBM_EINVAL, "cannot open file");
+  const char magic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
+  long long hdr[4] = {(long long)d->need, d->parity0, d->steps, d->mesh.L};
+  std::fwrite(magic, 1, 8, fp);
+  std::fwrite(hdr, sizeof hdr, 1, fp);
+  std::vector<float> host;
+  for (const Level& v : d->mesh.lv) {
+    int rc = download_level(d, v, host);
+    if (rc) {
+      std::fclose(fp);
+      return rc;
+    }
+    std::fwrite(host.data(), sizeof(float), host.size(), fp);
+  }
+  double acc[8];
+  cudaError_t e = cudaMemcpyAsync(acc, d->base + d->off_accum, sizeof acc, cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+  if (e != cudaSuccess) {
+    std::fclose(fp);
+    return cuda_fail(e, "cudaMemcpyAsync");
+  }
+  std::fwrite(acc, sizeof acc, 1, fp);
+  bool ok = std::fclose(fp) == 0;
+  return ok ? LBM_OK : fail(LBM_EINVAL, "write failed");
+}
+
+int lbm_load(lbm_domain* d, const char* path) {
+  if (!d || !path) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(LBM_EINVAL, "cannot open file");
+  char magic[8];
+  long long hdr[4];
+  bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "LBMSTAT1", 8) == 0 &&
+            std::fread(hdr, sizeof hdr, 1, fp) == 1 && hdr[0] == (long long)d->need && hdr[3] == d->mesh.L;
+  if (!ok) {
+    std::fclose(fp);
+    return fail(LBM_EINVAL, "state file does not match this domain");
+  }
+  std::vector<float> host;
+  for (const Level& v : d->mesh.lv) {
+    host.resize(v.f_elems());
+    if (std::fread(host.data(), sizeof(float), host.size(), fp) != host.size()) {
+      std::fclose(fp);
+      return fail(LBM_EINVAL, "truncated state file");
+    }
+    cudaError_t e = cudaMemcpyAsync(d->base + v.off_f, host.data(), host.size() * sizeof(float),
+                                    cudaMemcpyHostToDevice, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if (e != cudaSuccess) {
+      std::fclose(fp);
+      return cuda_fail(e, "cudaMemcpyAsync");
+    }
+  }
+  double acc[8];
+  if (std::fread(acc, sizeof acc, 1, fp) != 1) {
+    std::fclose(fp);
+    return fail(LBM_EINVAL, "truncated state file");
+  }
+  std::fclose(fp);
+  CK(cudaMemcpyAsync(d->base + d->off_accum, acc, sizeof acc, cudaMemcpyHostToDevice, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  free_graphs(d);
+  d->parity0 = (int)hdr[1];
+  d->steps = hdr[2];
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_domain* d) {
+  if (!d) return;
+  free_graphs(d);
+  for (auto e : d->pool) cudaEventDestroy(e);
+  delete d;
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Internal declarations of liblbm (host side and kernel launch wrappers).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr int kQ = 27;
+inline int cx(int i) { return i % 3 - 1; }
+inline int cy(int i) { return (i / 3) % 3 - 1; }
+inline int cz(int i) { return i / 9 - 1; }
+inline int opposite(int i) { return 26 - i; }
+inline int dir_index(int x, int y, int z) { return (x + 1) + 3 * (y + 1) + 9 * (z + 1); }
+
+// ---------------------------------------------------------------- geometry
+struct Prim {
+  int kind;  // 0 cylinder, 1 half-space, 2 box
+  double p[8];
+};
+
+struct Tree {
+  std::vector<double> seg;  // rows of 8: x0 y0 z0 x1 y1 z1 D gen
+  int count() const { return (int)(seg.size() / 8); }
+};
+
+// Eq. (1): rewrite the axiom n times, then interpret the string with a turtle.
+int build_lsystem(const lbm_tree_desc& t, Tree* out);
+void tree_bounds(const Tree& t, double lo[3], double hi[3]);
+double tree_height(const Tree& t);
+void tree_centroid(const Tree& t, double c[3]);
+void tree_affine(Tree* t, double scale, const double shift[3]);
+double frontal_area(const Tree& t, double pitch);
+
+bool prim_contains(const Prim& p, const double x[3]);
+double prim_entry(const Prim& p, const double x[3], const double d[3]);  // t >= 0 or +inf
+void prim_bounds(const Prim& p, double lo[3], double hi[3]);
+
+// ---------------------------------------------------------------- device tables
+// Offsets are element offsets (floats) into a level's population array.
+struct FaceEntry {   // domain faces of level 0 (Sec. 2.3)
+  long long dst;
+  long long src;     // -1: inflow equilibrium of direction dir
+  int dir;
+  int pad;
+};
+struct WallEntry {   // one cut link (Bouzidi linear bounce-back + momentum exchange)
+  long long dst, a, b, c;  // a: f*_i(x_f); b: f*_i(x_f - c_i) or -1; c: f*_ibar(x_f)
+  float q;
+  int dir;
+};
+struct ExplodeEntry {    // fine inflow before the second fine step
+  long long dst;         // fine ghost slot
+  long long src[2];      // coarse post-collision slot per coarse parity
+};
+struct SaveEntry {       // fine post-collision value of the first fine step kept for later
+  long long src;
+};
+struct InflowEntry {     // fine inflow for the next first fine step
+  long long dst;         // fine own slot
+  long long csrc[2];     // coarse post-collision slot per coarse parity (used when r < 0)
+  int r;                 // index into the saved values, or -1
+  int pad;
+};
+struct CoalesceEntry {   // coarse cell next to the fine region, one direction
+  long long dst[2];      // coarse slot per coarse parity (also its coarse source)
+  long long fsrc[8];     // >= 0 fine slot; < 0: saved value -(v+1)
+  int nfine;
+  int ncoarse;
+};
+
+// ---------------------------------------------------------------- mesh
+enum CellType : uint8_t { FLUID = 0, SOLID = 1, COVERED = 2, OUTSIDE = 3 };
+enum BlockState : int8_t { ABSENT = 0, ACTIVE = 1, GHOST = 2 };
+
+struct Link {
+  int x, y, z, dir;
+  double q;
+};
+
+struct Level {
+  int l = 0, B = 16;
+  int rlo[3] = {0, 0, 0}, rhi[3] = {0, 0, 0};  // real region, level-l cells
+  int org[3] = {0, 0, 0}, nb[3] = {0, 0, 0};    // block grid origin (cells) and extent (blocks)
+  bool wrap[3] = {false, false, false};          // periodic axes (level 0)
+  int dom[3] = {0, 0, 0};                        // level extent along periodic axes
+  std::vector<int> slot;                         // block grid -> storage index, -1 absent
+  std::vector<int> grid_of;                      // storage index -> block grid index
+  int n_active = 0, n_storage = 0;
+  std::vector<uint8_t> type;                     // n_storage * B^3
+  std::vector<int> nbr;                          // n_active * 27
+  std::vector<int> maskoff;                      // n_active: -1 all fluid, else mask block index
+  std::vector<uint8_t> masks;                    // collide flags, B^3 per masked block
+  long long n_fluid = 0;
+  double nu = 0, omega1 = 1;
+  std::vector<Link> links;
+  std::vector<WallEntry> wall[2];
+  std::vector<FaceEntry> face[2];
+  // interface with the next finer level (this level = coarse)
+  std::vector<ExplodeEntry> expl;
+  std::vector<SaveEntry> save;
+  std::vector<InflowEntry> infl;
+  std::vector<CoalesceEntry> coal;
+  // device offsets (bytes from the bound base)
+  size_t off_f = 0, off_nbr = 0, off_maskoff = 0, off_masks = 0;
+  size_t off_wall[2] = {0, 0}, off_face[2] = {0, 0};
+  size_t off_expl = 0, off_save = 0, off_infl = 0, off_coal = 0, off_saved = 0;
+
+  long long cells_per_block() const { return (long long)B * B * B; }
+  size_t f_elems() const { return (size_t)n_storage * kQ * cells_per_block(); }
+  bool in_real(int x, int y, int z) const {
+    return x >= rlo[0] && x < rhi[0] && y >= rlo[1] && y < rhi[1] && z >= rlo[2] && z < rhi[2];
+  }
+  // storage index and local cell of a level-l cell (periodic wrap applied); -1 if no storage
+  int locate(int x, int y, int z, int* local) const;
+  CellType cell_type(int x, int y, int z) const;
+  long long addr(int x, int y, int z, int dir) const;  // element offset or -1
+};
+
+struct Mesh {
+  int L = 1, B = 16;
+  int n0[3] = {0, 0, 0};
+  int bc[3] = {0, 0, 0};
+  std::vector<Level> lv;
+  int boxes[6][6] = {};
+  std::string error;
+};
+
+// Build block structure, cell types (solid from primitives), links and all tables.
+int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vector<Prim>& prims, Mesh* m);
+// Refinement boxes from the tree (finest: bounding box grown by margin; coarser: footprint + 1 block).
+void refinement_boxes(const Tree& t, int levels, int block, double margin, int boxes[6][6]);
+
+// ---------------------------------------------------------------- kernels (kernels.cu)
+struct CollideArgs {
+  float* f;
+  const int* nbr;
+  const int* maskoff;
+  const uint8_t* masks;
+  int n_active;
+  float omega1, omega2;
+  int galilean;
+};
+int launch_collide(const CollideArgs& a, int B, int odd, void* stream);
+int launch_faces(float* f, const FaceEntry* e, int n, const float* feq_in_dev_unused, const float feq[27],
+                 void* stream);
+int launch_walls(float* f, const WallEntry* e, int n, double* partials, void* stream);
+int walls_partial_count(int n);
+int launch_force_reduce(const double* partials, int nparts, double* accum, void* stream);
+int launch_explode(float* fine, const float* coarse, const ExplodeEntry* e, int ne, const SaveEntry* s,
+                   int ns, float* saved, int parity, void* stream);
+int launch_inflow(float* fine, const float* coarse, const InflowEntry* e, int n, const float* saved,
+                  int parity, void* stream);
+int launch_coalesce(float* coarse, const float* fine, const CoalesceEntry* e, int n, const float* saved,
+                    int parity, void* stream);
+int launch_fill(float* f, long long n_blocks, int B, const float dev[27], void* stream);
+int launch_mass(const float* f, const int* nbr, const int* maskoff, const uint8_t* masks, int n_active,
+                int B, int parity, double* partials, void* stream);
+int mass_partial_count(int n_active);
+const char* cuda_error_string();
+
+}  // namespace lbm

@@ -1,0 +1,388 @@
+// GB300 (sm_103a) kernels of the cumulant LBM step.
+//
+//  k_collide   fused collision + streaming, in-place AA pattern, one CTA per
+//              active block, one thread per (x, y) column walking z.
+//  k_faces     domain faces of level 0 (inflow, zero-gradient outflow, slip).
+//  k_walls     Bouzidi linear bounce-back on cut links fused with the
+//              momentum-exchange force; FP64 warp-shuffle + CTA reduction
+//              into per-CTA partials.
+//  k_force     fixed-order FP64 sum of the partials (deterministic).
+//  k_explode / k_inflow / k_coalesce   refinement-interface transfer.
+//  k_fill      equilibrium initialisation; k_mass FP64 mass / momentum.
+//
+// The step is a bandwidth-bound stencil: every population is read once and
+// written once per cell update (2 x 27 x 4 bytes in FP32); no tensor cores.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "cumulant.cuh"
+#include "internal.h"
+
+namespace lbm {
+namespace {
+
+__device__ __forceinline__ constexpr int dcx(int i) { return i % 3 - 1; }
+__device__ __forceinline__ constexpr int dcy(int i) { return (i / 3) % 3 - 1; }
+__device__ __forceinline__ constexpr int dcz(int i) { return i / 9 - 1; }
+
+// neighbour-block digit (0, 1, 2) of a local coordinate shifted by s in [-1, 1]
+template <int B>
+__device__ __forceinline__ int block_digit(int c) {
+  return c < 0 ? 0 : (c >= B ? 2 : 1);
+}
+
+template <int B, bool ODD>
+__global__ void __launch_bounds__(B * B) k_collide(CollideArgs a) {
+  constexpr int C3 = B * B * B;
+  __shared__ long long s_base[27];
+  const int blk = blockIdx.x;
+  if (threadIdx.x < 27) s_base[threadIdx.x] = (long long)a.nbr[(size_t)blk * 27 + threadIdx.x] * (27LL * C3);
+  __syncthreads();
+  const int lx = threadIdx.x % B, ly = threadIdx.x / B;
+  const int mo = a.maskoff[blk];
+  const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
+  const Rates rates{a.omega1, a.omega2, a.galilean};
+  float* __restrict__ f = a.f;
+  for (int lz = 0; lz < B; ++lz) {
+    const int cell = (lz * B + ly) * B + lx;
+    if (mask && !mask[cell]) continue;
+    float d[27];
+    if (!ODD) {
+      const float* p = f + s_base[13] + cell;
+#pragma unroll
+      for (int i = 0; i < 27; ++i) d[i] = p[i * C3];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 27; ++i) {
+        // pull f_i from (x - c_i, ibar)
+        const int nx = lx - dcx(i), ny = ly - dcy(i), nz = lz - dcz(i);
+        const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
+        const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
+        d[i] = f[s_base[bd] + (26 - i) * C3 + nc];
+      }
+    }
+    cumulant_collide(d, rates);
+    if (!ODD) {
+      float* p = f + s_base[13] + cell;
+#pragma unroll
+      for (int i = 0; i < 27; ++i) p[(26 - i) * C3] = d[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 27; ++i) {
+        // push f*_i to (x + c_i, i)
+        const int nx = lx + dcx(i), ny = ly + dcy(i), nz = lz + dcz(i);
+        const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
+        const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
+        f[s_base[bd] + i * C3 + nc] = d[i];
+      }
+    }
+  }
+}
+
+struct Feq27 {
+  float v[27];
+};
+
+__global__ void k_faces(float* __restrict__ f, const FaceEntry* __restrict__ e, int n, Feq27 feq) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const FaceEntry x = e[t];
+  f[x.dst] = x.src < 0 ? feq.v[x.dir] : f[x.src];
+}
+
+constexpr int kWallThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide FP64 sum of three values in a fixed order; result valid in thread 0
+template <int NT>
+__device__ void block_sum3(double& a, double& b, double& c) {
+  __shared__ double s[3][NT / 32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s[0][w] = a;
+    s[1][w] = b;
+    s[2][w] = c;
+  }
+  __syncthreads();
+  if (w == 0) {
+    a = lane < NT / 32 ? s[0][lane] : 0.0;
+    b = lane < NT / 32 ? s[1][lane] : 0.0;
+    c = lane < NT / 32 ? s[2][lane] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+  }
+}
+
+__global__ void __launch_bounds__(kWallThreads) k_walls(float* __restrict__ f, const WallEntry* __restrict__ e,
+                                                        int n, double* __restrict__ partials) {
+  const int t = blockIdx.x * kWallThreads + threadIdx.x;
+  double Fx = 0.0, Fy = 0.0, Fz = 0.0;
+  if (t < n) {
+    const WallEntry w = e[t];
+    const float fa = f[w.a];  // f*_i(x_f), toward the wall (deviation)
+    const float q = w.q;
+    float out;
+    if (w.b < 0) {
+      out = fa;  // second fluid node missing: simple bounce-back
+    } else if (q < 0.5f) {
+      out = 2.0f * q * fa + (1.0f - 2.0f * q) * f[w.b];
+    } else {
+      const float fc = f[w.c];
+      out = fa / (2.0f * q) + (2.0f * q - 1.0f) / (2.0f * q) * fc;
+    }
+    f[w.dst] = out;
+    // momentum exchange, resting wall: c_i (f*_i + f_ibar), full populations
+    const int i = w.dir;
+    const double wi = (dcx(i) ? 1.0 / 6.0 : 2.0 / 3.0) * (dcy(i) ? 1.0 / 6.0 : 2.0 / 3.0) *
+                      (dcz(i) ? 1.0 / 6.0 : 2.0 / 3.0);
+    const double s = 2.0 * wi + (double)fa + (double)out;
+    Fx = dcx(i) * s;
+    Fy = dcy(i) * s;
+    Fz = dcz(i) * s;
+  }
+  block_sum3<kWallThreads>(Fx, Fy, Fz);
+  if (threadIdx.x == 0) {
+    partials[3 * blockIdx.x + 0] = Fx;
+    partials[3 * blockIdx.x + 1] = Fy;
+    partials[3 * blockIdx.x + 2] = Fz;
+  }
+}
+
+// accum: [0..2] force of the last finest step, [3..5] running sum, [6] count
+__global__ void __launch_bounds__(256) k_force(const double* __restrict__ partials, int nparts,
+                                               double* __restrict__ accum) {
+  double a = 0, b = 0, c = 0;
+  for (int k = threadIdx.x; k < nparts; k += 256) {
+    a += partials[3 * k];
+    b += partials[3 * k + 1];
+    c += partials[3 * k + 2];
+  }
+  block_sum3<256>(a, b, c);
+  if (threadIdx.x == 0) {
+    accum[0] = a;
+    accum[1] = b;
+    accum[2] = c;
+    accum[3] += a;
+    accum[4] += b;
+    accum[5] += c;
+    accum[6] += 1.0;
+  }
+}
+
+__global__ void k_explode(float* __restrict__ fine, const float* __restrict__ coarse,
+                          const ExplodeEntry* __restrict__ e, int ne, const SaveEntry* __restrict__ s, int ns,
+                          float* __restrict__ saved, int parity) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ne) {
+    const ExplodeEntry x = e[t];
+    fine[x.dst] = coarse[parity ? x.src[1] : x.src[0]];
+  }
+  if (t < ns) saved[t] = fine[s[t].src];
+}
+
+__global__ void k_inflow(float* __restrict__ fine, const float* __restrict__ coarse,
+                         const InflowEntry* __restrict__ e, int n, const float* __restrict__ saved, int parity) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const InflowEntry x = e[t];
+  fine[x.dst] = x.r >= 0 ? saved[x.r] : coarse[parity ? x.csrc[1] : x.csrc[0]];
+}
+
+__global__ void k_coalesce(float* __restrict__ coarse, const float* __restrict__ fine,
+                           const CoalesceEntry* __restrict__ e, int n, const float* __restrict__ saved, int parity) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CoalesceEntry& x = e[t];
+  const long long dst = parity ? x.dst[1] : x.dst[0];
+  float v = x.ncoarse ? (float)x.ncoarse * coarse[dst] : 0.0f;
+  for (int k = 0; k < x.nfine; ++k) {
+    const long long s = x.fsrc[k];
+    v += s >= 0 ? fine[s] : saved[-s - 1];
+  }
+  coarse[dst] = v * 0.125f;
+}
+
+__global__ void k_fill(float* __restrict__ f, long long n, int c3, Feq27 dev) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = (int)((t / c3) % 27);
+  f[t] = dev.v[i];
+}
+
+// FP64 mass and momentum of the incoming populations of one level; per CTA
+// partials [mass, jx, jy, jz, bad cells]
+template <int B>
+__global__ void __launch_bounds__(B * B) k_mass(const float* __restrict__ f, const int* __restrict__ nbr,
+                                                const int* __restrict__ maskoff, const uint8_t* __restrict__ masks,
+                                                int parity, double* __restrict__ partials) {
+  constexpr int C3 = B * B * B;
+  __shared__ long long s_base[27];
+  __shared__ double s_bad[B * B / 32];
+  const int blk = blockIdx.x;
+  if (threadIdx.x < 27) s_base[threadIdx.x] = (long long)nbr[(size_t)blk * 27 + threadIdx.x] * (27LL * C3);
+  __syncthreads();
+  const int lx = threadIdx.x % B, ly = threadIdx.x / B;
+  const int mo = maskoff[blk];
+  const uint8_t* mask = mo >= 0 ? masks + (size_t)mo * C3 : nullptr;
+  double m = 0, jx = 0, jy = 0, jz = 0, bad = 0;
+  for (int lz = 0; lz < B; ++lz) {
+    const int cell = (lz * B + ly) * B + lx;
+    if (mask && !mask[cell]) continue;
+    double rho = 0, ax = 0, ay = 0, az = 0;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+      float v;
+      if (!parity) {
+        v = f[s_base[13] + i * C3 + cell];
+      } else {
+        const int nx = lx - dcx(i), ny = ly - dcy(i), nz = lz - dcz(i);
+        const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
+        const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
+        v = f[s_base[bd] + (26 - i) * C3 + nc];
+      }
+      const double w = (dcx(i) ? 1.0 / 6.0 : 2.0 / 3.0) * (dcy(i) ? 1.0 / 6.0 : 2.0 / 3.0) *
+                       (dcz(i) ? 1.0 / 6.0 : 2.0 / 3.0);
+      rho += w + (double)v;
+      ax += dcx(i) * (double)v;
+      ay += dcy(i) * (double)v;
+      az += dcz(i) * (double)v;
+    }
+    if (!(rho >= 0.5 && rho <= 2.0)) bad += 1.0;  // also catches NaN
+    m += rho;
+    jx += ax;
+    jy += ay;
+    jz += az;
+  }
+  block_sum3<B * B>(m, jx, jy);
+  double z = warp_sum(jz), b = warp_sum(bad);
+  __shared__ double s_z[B * B / 32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_z[w] = z;
+    s_bad[w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double zz = 0, bb = 0;
+    for (int k = 0; k < B * B / 32; ++k) {
+      zz += s_z[k];
+      bb += s_bad[k];
+    }
+    double* p = partials + 5 * (size_t)blk;
+    p[0] = m;
+    p[1] = jx;
+    p[2] = jy;
+    p[3] = zz;
+    p[4] = bb;
+  }
+}
+
+thread_local char g_err[256] = "";
+
+int check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(g_err, sizeof g_err, "%s: %s", what, cudaGetErrorString(e));
+    return LBM_ECUDA;
+  }
+  return LBM_OK;
+}
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+const char* cuda_error_string() { return g_err; }
+
+int launch_collide(const CollideArgs& a, int B, int odd, void* stream) {
+  if (a.n_active == 0) return LBM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (B == 16) {
+    if (odd) k_collide<16, true><<<a.n_active, 256, 0, s>>>(a);
+    else k_collide<16, false><<<a.n_active, 256, 0, s>>>(a);
+  } else if (B == 8) {
+    if (odd) k_collide<8, true><<<a.n_active, 64, 0, s>>>(a);
+    else k_collide<8, false><<<a.n_active, 64, 0, s>>>(a);
+  } else {
+    return LBM_EINVAL;
+  }
+  return check_launch("collide");
+}
+
+int launch_faces(float* f, const FaceEntry* e, int n, const float*, const float feq[27], void* stream) {
+  if (n == 0) return LBM_OK;
+  Feq27 v;
+  for (int i = 0; i < 27; ++i) v.v[i] = feq[i];
+  k_faces<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(f, e, n, v);
+  return check_launch("faces");
+}
+
+int walls_partial_count(int n) { return (int)blocks_for(n, kWallThreads); }
+
+int launch_walls(float* f, const WallEntry* e, int n, double* partials, void* stream) {
+  if (n == 0) return LBM_OK;
+  k_walls<<<blocks_for(n, kWallThreads), kWallThreads, 0, (cudaStream_t)stream>>>(f, e, n, partials);
+  return check_launch("walls");
+}
+
+int launch_force_reduce(const double* partials, int nparts, double* accum, void* stream) {
+  k_force<<<1, 256, 0, (cudaStream_t)stream>>>(partials, nparts, accum);
+  return check_launch("force");
+}
+
+int launch_explode(float* fine, const float* coarse, const ExplodeEntry* e, int ne, const SaveEntry* s, int ns,
+                   float* saved, int parity, void* stream) {
+  long long n = ne > ns ? ne : ns;
+  if (n == 0) return LBM_OK;
+  k_explode<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(fine, coarse, e, ne, s, ns, saved, parity);
+  return check_launch("explode");
+}
+
+int launch_inflow(float* fine, const float* coarse, const InflowEntry* e, int n, const float* saved, int parity,
+                  void* stream) {
+  if (n == 0) return LBM_OK;
+  k_inflow<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(fine, coarse, e, n, saved, parity);
+  return check_launch("inflow");
+}
+
+int launch_coalesce(float* coarse, const float* fine, const CoalesceEntry* e, int n, const float* saved, int parity,
+                    void* stream) {
+  if (n == 0) return LBM_OK;
+  k_coalesce<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(coarse, fine, e, n, saved, parity);
+  return check_launch("coalesce");
+}
+
+int launch_fill(float* f, long long n_blocks, int B, const float dev[27], void* stream) {
+  Feq27 v;
+  for (int i = 0; i < 27; ++i) v.v[i] = dev[i];
+  const int c3 = B * B * B;
+  long long n = n_blocks * 27LL * c3;
+  if (n == 0) return LBM_OK;
+  k_fill<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(f, n, c3, v);
+  return check_launch("fill");
+}
+
+int mass_partial_count(int n_active) { return n_active; }
+
+int launch_mass(const float* f, const int* nbr, const int* maskoff, const uint8_t* masks, int n_active, int B,
+                int parity, double* partials, void* stream) {
+  if (n_active == 0) return LBM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (B == 16) k_mass<16><<<n_active, 256, 0, s>>>(f, nbr, maskoff, masks, parity, partials);
+  else if (B == 8) k_mass<8><<<n_active, 64, 0, s>>>(f, nbr, maskoff, masks, parity, partials);
+  else return LBM_EINVAL;
+  return check_launch("mass");
+}
+
+}  // namespace lbm

@@ -1,0 +1,630 @@
+// Block-structured refinement mesh (Sec. 2.2: octree leaves holding cubic
+// blocks of cells) and the slot tables of the in-place (AA) update.
+//
+// Storage: every level keeps its blocks in one array f[block][27][B^3]
+// (floats, x fastest inside a block).  Active blocks (those with cells this
+// level updates) come first in Morton order, then ghost blocks, which only
+// give storage to the populations that cross the level's edge: the domain
+// faces, the cut links into solid cells, and the interface with the next
+// finer or coarser level.
+//
+// AA pattern: an even step reads f_i(x) from slot (x, i) and writes the
+// post-collision f*_i(x) to (x, ibar); an odd step reads f_i(x) from
+// (x - c_i, ibar) and writes f*_i(x) to (x + c_i, i).  Consequently, after
+// an even step f*_i(x) sits in (x, ibar) and the next step expects the
+// incoming f_i(x) in (x - c_i, ibar); after an odd step f*_i(x) sits in
+// (x + c_i, i) and the next step expects f_i(x) in (x, i).  Every table
+// below is a list of (destination slot, source slots) pairs per parity.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace lbm {
+namespace {
+
+int floordiv(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+int wrapmod(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffff;
+  x = (x | x << 32) & 0x1f00000000ffffULL;
+  x = (x | x << 16) & 0x1f0000ff0000ffULL;
+  x = (x | x << 8) & 0x100f00f00f00f00fULL;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+  x = (x | x << 2) & 0x1249249249249249ULL;
+  return x;
+}
+uint64_t morton(int x, int y, int z) { return spread3(x) | spread3(y) << 1 | spread3(z) << 2; }
+
+bool in_box(const int lo[3], const int hi[3], int x, int y, int z) {
+  return x >= lo[0] && x < hi[0] && y >= lo[1] && y < hi[1] && z >= lo[2] && z < hi[2];
+}
+
+}  // namespace
+
+int Level::locate(int x, int y, int z, int* local) const {
+  int c[3] = {x, y, z};
+  int b[3], r[3];
+  for (int a = 0; a < 3; ++a) {
+    if (wrap[a]) c[a] = wrapmod(c[a], dom[a]);
+    int rel = c[a] - org[a];
+    if (rel < 0) return -1;
+    b[a] = rel / B;
+    if (b[a] >= nb[a]) return -1;
+    r[a] = rel - b[a] * B;
+  }
+  int s = slot[((size_t)b[2] * nb[1] + b[1]) * nb[0] + b[0]];
+  if (s < 0) return -1;
+  *local = (r[2] * B + r[1]) * B + r[0];
+  return s;
+}
+
+CellType Level::cell_type(int x, int y, int z) const {
+  int loc;
+  int s = locate(x, y, z, &loc);
+  if (s < 0) return OUTSIDE;
+  return (CellType)type[(size_t)s * cells_per_block() + loc];
+}
+
+long long Level::addr(int x, int y, int z, int dir) const {
+  int loc;
+  int s = locate(x, y, z, &loc);
+  if (s < 0) return -1;
+  return ((long long)s * kQ + dir) * cells_per_block() + loc;
+}
+
+void refinement_boxes(const Tree& t, int levels, int block, double margin, int boxes[6][6]) {
+  for (int l = 0; l < 6; ++l)
+    for (int q = 0; q < 6; ++q) boxes[l][q] = 0;
+  if (levels < 2) return;
+  double lo[3], hi[3];
+  tree_bounds(t, lo, hi);
+  const int B = block;
+  for (int a = 0; a < 3; ++a) {
+    double ext = hi[a] - lo[a];
+    double glo = lo[a] - margin * ext, ghi = hi[a] + margin * ext;
+    // finest cells, rounded outward to whole finest blocks
+    boxes[levels - 1][a] = (int)std::floor(glo / B) * B;
+    boxes[levels - 1][3 + a] = (int)std::ceil(ghi / B) * B;
+  }
+  // each coarser box: the finer box's footprint rounded outward to whole
+  // blocks of its own level, plus one block on every side
+  for (int l = levels - 2; l >= 1; --l)
+    for (int a = 0; a < 3; ++a) {
+      boxes[l][a] = floordiv(boxes[l + 1][a], 2 * B) * B - B;
+      boxes[l][3 + a] = -floordiv(-boxes[l + 1][3 + a], 2 * B) * B + B;
+    }
+}
+
+namespace {
+
+// cell of level l is updated by level l (inside its real region, not covered by l+1)
+bool live(const Mesh& m, int l, int x, int y, int z) {
+  const Level& v = m.lv[l];
+  int c[3] = {x, y, z};
+  for (int a = 0; a < 3; ++a)
+    if (v.wrap[a]) c[a] = wrapmod(c[a], v.dom[a]);
+  if (!v.in_real(c[0], c[1], c[2])) return false;
+  if (l + 1 < m.L) {
+    const Level& f = m.lv[l + 1];
+    if (f.in_real(2 * c[0], 2 * c[1], 2 * c[2])) return false;
+  }
+  return true;
+}
+
+CellType base_type(const Mesh& m, int l, int x, int y, int z) {
+  const Level& v = m.lv[l];
+  if (!v.in_real(x, y, z)) return OUTSIDE;
+  if (l + 1 < m.L && m.lv[l + 1].in_real(2 * x, 2 * y, 2 * z)) return COVERED;
+  return FLUID;
+}
+
+void block_origin(const Level& v, int gi, int o[3]) {
+  int bx = gi % v.nb[0], by = (gi / v.nb[0]) % v.nb[1], bz = gi / (v.nb[0] * v.nb[1]);
+  o[0] = v.org[0] + bx * v.B;
+  o[1] = v.org[1] + by * v.B;
+  o[2] = v.org[2] + bz * v.B;
+}
+
+int layout_level(Mesh& m, int l) {
+  Level& v = m.lv[l];
+  const int B = v.B;
+  size_t ng = (size_t)v.nb[0] * v.nb[1] * v.nb[2];
+  std::vector<int8_t> state(ng, ABSENT);
+  for (int bz = 0; bz < v.nb[2]; ++bz)
+    for (int by = 0; by < v.nb[1]; ++by)
+      for (int bx = 0; bx < v.nb[0]; ++bx) {
+        size_t gi = ((size_t)bz * v.nb[1] + by) * v.nb[0] + bx;
+        int o[3] = {v.org[0] + bx * B, v.org[1] + by * B, v.org[2] + bz * B};
+        bool any = false;
+        for (int z = 0; z < B && !any; ++z)
+          for (int y = 0; y < B && !any; ++y)
+            for (int x = 0; x < B && !any; ++x)
+              if (live(m, l, o[0] + x, o[1] + y, o[2] + z)) any = true;
+        if (any) state[gi] = ACTIVE;
+      }
+  for (int bz = 0; bz < v.nb[2]; ++bz)
+    for (int by = 0; by < v.nb[1]; ++by)
+      for (int bx = 0; bx < v.nb[0]; ++bx) {
+        size_t gi = ((size_t)bz * v.nb[1] + by) * v.nb[0] + bx;
+        if (state[gi] != ABSENT) continue;
+        bool near = false;
+        for (int dz = -1; dz <= 1 && !near; ++dz)
+          for (int dy = -1; dy <= 1 && !near; ++dy)
+            for (int dx = -1; dx <= 1 && !near; ++dx) {
+              int n[3] = {bx + dx, by + dy, bz + dz};
+              bool ok = true;
+              for (int a = 0; a < 3; ++a) {
+                if (v.wrap[a]) n[a] = wrapmod(n[a], v.nb[a]);
+                if (n[a] < 0 || n[a] >= v.nb[a]) ok = false;
+              }
+              if (ok && state[((size_t)n[2] * v.nb[1] + n[1]) * v.nb[0] + n[0]] == ACTIVE) near = true;
+            }
+        if (near) state[gi] = GHOST;
+      }
+  std::vector<std::pair<uint64_t, int>> act, gho;
+  for (size_t gi = 0; gi < ng; ++gi) {
+    int bx = (int)(gi % v.nb[0]), by = (int)((gi / v.nb[0]) % v.nb[1]), bz = (int)(gi / ((size_t)v.nb[0] * v.nb[1]));
+    if (state[gi] == ACTIVE) act.push_back({morton(bx, by, bz), (int)gi});
+    if (state[gi] == GHOST) gho.push_back({morton(bx, by, bz), (int)gi});
+  }
+  std::sort(act.begin(), act.end());
+  std::sort(gho.begin(), gho.end());
+  v.slot.assign(ng, -1);
+  v.grid_of.clear();
+  for (auto& p : act) { v.slot[p.second] = (int)v.grid_of.size(); v.grid_of.push_back(p.second); }
+  for (auto& p : gho) { v.slot[p.second] = (int)v.grid_of.size(); v.grid_of.push_back(p.second); }
+  v.n_active = (int)act.size();
+  v.n_storage = (int)v.grid_of.size();
+  const long long cpb = v.cells_per_block();
+  v.type.assign((size_t)v.n_storage * cpb, OUTSIDE);
+  for (int s = 0; s < v.n_storage; ++s) {
+    int o[3];
+    block_origin(v, v.grid_of[s], o);
+    for (int z = 0; z < B; ++z)
+      for (int y = 0; y < B; ++y)
+        for (int x = 0; x < B; ++x) {
+          int gx = o[0] + x, gy = o[1] + y, gz = o[2] + z;
+          v.type[(size_t)s * cpb + (z * B + y) * B + x] = base_type(m, l, gx, gy, gz);
+        }
+  }
+  // neighbour table of active blocks
+  v.nbr.assign((size_t)v.n_active * kQ, -1);
+  for (int s = 0; s < v.n_active; ++s) {
+    int gi = v.grid_of[s];
+    int b[3] = {gi % v.nb[0], (gi / v.nb[0]) % v.nb[1], gi / (v.nb[0] * v.nb[1])};
+    for (int d = 0; d < kQ; ++d) {
+      int n[3] = {b[0] + cx(d), b[1] + cy(d), b[2] + cz(d)};
+      for (int a = 0; a < 3; ++a) {
+        if (v.wrap[a]) n[a] = wrapmod(n[a], v.nb[a]);
+        if (n[a] < 0 || n[a] >= v.nb[a]) {
+          m.error = "active block without neighbour storage";
+          return LBM_EINVAL;
+        }
+      }
+      int t = v.slot[((size_t)n[2] * v.nb[1] + n[1]) * v.nb[0] + n[0]];
+      if (t < 0) {
+        m.error = "active block without neighbour storage";
+        return LBM_EINVAL;
+      }
+      v.nbr[(size_t)s * kQ + d] = t;
+    }
+  }
+  return LBM_OK;
+}
+
+int classify_solids(Mesh& m, int l, const std::vector<Prim>& prims) {
+  Level& v = m.lv[l];
+  const int B = v.B;
+  const long long cpb = v.cells_per_block();
+  const double h = std::ldexp(1.0, m.L - 1 - l);
+  std::vector<double> plo(prims.size() * 3), phi(prims.size() * 3);
+  for (size_t k = 0; k < prims.size(); ++k) prim_bounds(prims[k], &plo[3 * k], &phi[3 * k]);
+  std::vector<int> cand;
+  for (int s = 0; s < v.n_active; ++s) {
+    int o[3];
+    block_origin(v, v.grid_of[s], o);
+    cand.clear();
+    for (size_t k = 0; k < prims.size(); ++k) {
+      bool hit = true;
+      for (int a = 0; a < 3; ++a) {
+        double lo = o[a] * h - h, hi = (o[a] + B) * h + h;
+        if (phi[3 * k + a] < lo || plo[3 * k + a] > hi) hit = false;
+      }
+      if (hit) cand.push_back((int)k);
+    }
+    if (cand.empty()) continue;
+    for (int z = 0; z < B; ++z)
+      for (int y = 0; y < B; ++y)
+        for (int x = 0; x < B; ++x) {
+          uint8_t& t = v.type[(size_t)s * cpb + (z * B + y) * B + x];
+          if (t != FLUID) continue;
+          double c[3] = {(o[0] + x + 0.5) * h, (o[1] + y + 0.5) * h, (o[2] + z + 0.5) * h};
+          for (int k : cand)
+            if (prim_contains(prims[k], c)) {
+              t = SOLID;
+              break;
+            }
+        }
+  }
+  return LBM_OK;
+}
+
+int build_links(Mesh& m, int l, const std::vector<Prim>& prims) {
+  Level& v = m.lv[l];
+  const int B = v.B;
+  const long long cpb = v.cells_per_block();
+  const double h = std::ldexp(1.0, m.L - 1 - l);
+  v.links.clear();
+  for (int s = 0; s < v.n_active; ++s) {
+    int o[3];
+    block_origin(v, v.grid_of[s], o);
+    for (int z = 0; z < B; ++z)
+      for (int y = 0; y < B; ++y)
+        for (int x = 0; x < B; ++x) {
+          if (v.type[(size_t)s * cpb + (z * B + y) * B + x] != SOLID) continue;
+          int sx = o[0] + x, sy = o[1] + y, sz = o[2] + z;
+          for (int i = 0; i < kQ; ++i) {
+            if (i == 13) continue;
+            int fx = sx - cx(i), fy = sy - cy(i), fz = sz - cz(i);
+            if (v.cell_type(fx, fy, fz) != FLUID) continue;
+            double p0[3] = {(fx + 0.5) * h, (fy + 0.5) * h, (fz + 0.5) * h};
+            double dd[3] = {cx(i) * h, cy(i) * h, cz(i) * h};
+            double q = std::numeric_limits<double>::infinity();
+            for (const Prim& p : prims) q = std::min(q, prim_entry(p, p0, dd));
+            if (!(q <= 1.0)) q = 1.0;
+            if (q < 1e-6) q = 1e-6;
+            int c[3] = {fx, fy, fz};
+            for (int a = 0; a < 3; ++a)
+              if (v.wrap[a]) c[a] = wrapmod(c[a], v.dom[a]);
+            v.links.push_back({c[0], c[1], c[2], i, q});
+          }
+        }
+  }
+  std::sort(v.links.begin(), v.links.end(), [&](const Link& a, const Link& b) {
+    long long ka = v.addr(a.x, a.y, a.z, 0), kb = v.addr(b.x, b.y, b.z, 0);
+    return ka != kb ? ka < kb : a.dir < b.dir;
+  });
+  for (int p = 0; p < 2; ++p) v.wall[p].clear();
+  for (const Link& k : v.links) {
+    int i = k.dir, ib = opposite(i);
+    int x = k.x, y = k.y, z = k.z;
+    // the link cell must not touch another level (its value would be overwritten)
+    for (int d = 0; d < kQ; ++d) {
+      CellType t = v.cell_type(x + cx(d), y + cy(d), z + cz(d));
+      if (t == COVERED || (t == OUTSIDE && l > 0)) {
+        m.error = "the geometry touches a refinement interface";
+        return LBM_EINVAL;
+      }
+    }
+    bool back = v.cell_type(x - cx(i), y - cy(i), z - cz(i)) == FLUID;
+    WallEntry e0, e1;
+    e0.dst = v.addr(x + cx(i), y + cy(i), z + cz(i), i);
+    e0.a = v.addr(x, y, z, ib);
+    e0.b = back ? v.addr(x - cx(i), y - cy(i), z - cz(i), ib) : -1;
+    e0.c = v.addr(x, y, z, i);
+    e1.dst = v.addr(x, y, z, ib);
+    e1.a = v.addr(x + cx(i), y + cy(i), z + cz(i), i);
+    e1.b = back ? v.addr(x, y, z, i) : -1;
+    e1.c = v.addr(x - cx(i), y - cy(i), z - cz(i), ib);
+    e0.q = e1.q = (float)k.q;
+    e0.dir = e1.dir = i;
+    if (e0.dst < 0 || e0.a < 0 || e0.c < 0 || e1.a < 0 || e1.c < 0) {
+      m.error = "cut link without storage";
+      return LBM_EINVAL;
+    }
+    v.wall[0].push_back(e0);
+    v.wall[1].push_back(e1);
+  }
+  return LBM_OK;
+}
+
+// Sec. 2.3 faces of level 0: the source a boundary cell pulls from outside.
+// Returns false for the inflow equilibrium, else the cell and direction.
+bool face_source(const Mesh& m, int gx, int gy, int gz, int i, int* sx, int* sy, int* sz, int* sj) {
+  const int* n = m.n0;
+  int g[3] = {gx, gy, gz};
+  int c[3] = {cx(i), cy(i), cz(i)};
+  for (int a = 0; a < 3; ++a)
+    if (m.bc[a] == LBM_BC_PERIODIC) g[a] = wrapmod(g[a], n[a]);
+  if (g[0] < 0) return false;
+  for (int a = 1; a < 3; ++a) {
+    if (g[a] >= 0 && g[a] < n[a]) continue;
+    if (m.bc[a] == LBM_BC_INFLOW) return false;
+    g[a] = g[a] < 0 ? -1 - g[a] : 2 * n[a] - 1 - g[a];
+    c[a] = -c[a];
+  }
+  if (g[0] >= n[0]) g[0] = n[0] - 1;
+  *sx = g[0];
+  *sy = g[1];
+  *sz = g[2];
+  *sj = dir_index(c[0], c[1], c[2]);
+  return true;
+}
+
+int build_faces(Mesh& m) {
+  Level& v = m.lv[0];
+  const int B = v.B;
+  const long long cpb = v.cells_per_block();
+  for (int p = 0; p < 2; ++p) v.face[p].clear();
+  for (int s = 0; s < v.n_active; ++s) {
+    int o[3];
+    block_origin(v, v.grid_of[s], o);
+    for (int z = 0; z < B; ++z)
+      for (int y = 0; y < B; ++y)
+        for (int x = 0; x < B; ++x) {
+          if (v.type[(size_t)s * cpb + (z * B + y) * B + x] != FLUID) continue;
+          int X = o[0] + x, Y = o[1] + y, Z = o[2] + z;
+          bool edge = false;
+          for (int a = 0; a < 3; ++a) {
+            int c = a == 0 ? X : (a == 1 ? Y : Z);
+            if (m.bc[a] != LBM_BC_PERIODIC && (c == 0 || c == m.n0[a] - 1)) edge = true;
+          }
+          if (!edge) continue;
+          for (int i = 0; i < kQ; ++i) {
+            int gx = X - cx(i), gy = Y - cy(i), gz = Z - cz(i);
+            bool out = false;
+            int g[3] = {gx, gy, gz};
+            for (int a = 0; a < 3; ++a)
+              if (m.bc[a] != LBM_BC_PERIODIC && (g[a] < 0 || g[a] >= m.n0[a])) out = true;
+            if (!out) continue;
+            int sx, sy, sz, sj;
+            bool cell = face_source(m, gx, gy, gz, i, &sx, &sy, &sz, &sj);
+            FaceEntry e0{}, e1{};
+            e0.dir = e1.dir = i;
+            e0.dst = v.addr(gx, gy, gz, opposite(i));
+            e1.dst = v.addr(X, Y, Z, i);
+            if (cell) {
+              e0.src = v.addr(sx, sy, sz, opposite(sj));
+              e1.src = v.addr(sx + cx(sj), sy + cy(sj), sz + cz(sj), sj);
+            } else {
+              e0.src = e1.src = -1;
+            }
+            if (e0.dst < 0 || e1.dst < 0 || (cell && (e0.src < 0 || e1.src < 0))) {
+              m.error = "face slot without storage";
+              return LBM_EINVAL;
+            }
+            v.face[0].push_back(e0);
+            v.face[1].push_back(e1);
+          }
+        }
+  }
+  return LBM_OK;
+}
+
+// Interface between level l (coarse) and l+1 (fine).  The exchange is the
+// exact advection, at fine resolution, of the coarse post-collision field
+// held constant over the coarse step by virtual fine cells outside the fine
+// region (see the oracle's description of the same scheme); it reduces to:
+//  * before the second fine step, a fine cell x whose neighbour x - c_i lies
+//    outside receives the coarse post-collision f*_i of parent(x - c_i);
+//  * before the next first fine step it receives f*_i of x - 2c_i: the fine
+//    post-collision value of the first fine step when x - 2c_i is inside,
+//    else the coarse value of parent(x - 2c_i);
+//  * a coarse cell W next to the fine region receives, per direction, the
+//    mean over its 8 children p of: fine f*_i(p - c_i) of the second fine
+//    step, or fine f*_i(p - 2c_i) of the first, or coarse f*_i(W - c_i).
+int build_interface(Mesh& m, int l) {
+  Level& C = m.lv[l];
+  Level& F = m.lv[l + 1];
+  C.expl.clear();
+  C.save.clear();
+  C.infl.clear();
+  C.coal.clear();
+  std::unordered_map<long long, int> saved;
+  auto save_index = [&](int x, int y, int z, int i) -> int {
+    long long key = F.addr(x, y, z, opposite(i));
+    auto it = saved.find(key);
+    if (it != saved.end()) return it->second;
+    int k = (int)C.save.size();
+    C.save.push_back({key});
+    saved.emplace(key, k);
+    return k;
+  };
+  auto coarse_post = [&](int X, int Y, int Z, int i, int parity) -> long long {
+    if (parity == 0) return C.addr(X, Y, Z, opposite(i));
+    return C.addr(X + cx(i), Y + cy(i), Z + cz(i), i);
+  };
+  const int* lo = F.rlo;
+  const int* hi = F.rhi;
+  for (int z = lo[2]; z < hi[2]; ++z)
+    for (int y = lo[1]; y < hi[1]; ++y)
+      for (int x = lo[0]; x < hi[0]; ++x) {
+        bool shell = x == lo[0] || x == hi[0] - 1 || y == lo[1] || y == hi[1] - 1 || z == lo[2] || z == hi[2] - 1;
+        if (!shell) continue;
+        for (int i = 0; i < kQ; ++i) {
+          int ax = x - cx(i), ay = y - cy(i), az = z - cz(i);
+          if (in_box(lo, hi, ax, ay, az)) continue;
+          if (F.cell_type(x, y, z) != FLUID) {
+            m.error = "refinement interface crosses a solid";
+            return LBM_EINVAL;
+          }
+          int px = floordiv(ax, 2), py = floordiv(ay, 2), pz = floordiv(az, 2);
+          if (C.cell_type(px, py, pz) != FLUID) {
+            m.error = "refinement box too close to the coarser level's edge";
+            return LBM_EINVAL;
+          }
+          ExplodeEntry e{};
+          e.dst = F.addr(ax, ay, az, opposite(i));
+          e.src[0] = coarse_post(px, py, pz, i, 0);
+          e.src[1] = coarse_post(px, py, pz, i, 1);
+          InflowEntry f{};
+          f.dst = F.addr(x, y, z, i);
+          int bx = x - 2 * cx(i), by = y - 2 * cy(i), bz = z - 2 * cz(i);
+          if (in_box(lo, hi, bx, by, bz)) {
+            if (F.cell_type(bx, by, bz) != FLUID) {
+              m.error = "refinement interface crosses a solid";
+              return LBM_EINVAL;
+            }
+            f.r = save_index(bx, by, bz, i);
+            f.csrc[0] = f.csrc[1] = -1;
+          } else {
+            int qx = floordiv(bx, 2), qy = floordiv(by, 2), qz = floordiv(bz, 2);
+            if (C.cell_type(qx, qy, qz) != FLUID) {
+              m.error = "refinement box too close to the coarser level's edge";
+              return LBM_EINVAL;
+            }
+            f.r = -1;
+            f.csrc[0] = coarse_post(qx, qy, qz, i, 0);
+            f.csrc[1] = coarse_post(qx, qy, qz, i, 1);
+          }
+          if (e.dst < 0 || e.src[0] < 0 || e.src[1] < 0 || f.dst < 0 ||
+              (f.r < 0 && (f.csrc[0] < 0 || f.csrc[1] < 0))) {
+            m.error = "interface slot without storage";
+            return LBM_EINVAL;
+          }
+          C.expl.push_back(e);
+          C.infl.push_back(f);
+        }
+      }
+  // coarse cells around the footprint [lo/2, hi/2)
+  int clo[3], chi[3];
+  for (int a = 0; a < 3; ++a) {
+    clo[a] = lo[a] / 2;
+    chi[a] = hi[a] / 2;
+  }
+  for (int Z = clo[2] - 1; Z <= chi[2]; ++Z)
+    for (int Y = clo[1] - 1; Y <= chi[1]; ++Y)
+      for (int X = clo[0] - 1; X <= chi[0]; ++X) {
+        if (in_box(clo, chi, X, Y, Z)) continue;
+        if (C.cell_type(X, Y, Z) != FLUID) {
+          m.error = "refinement box too close to a solid or an edge";
+          return LBM_EINVAL;
+        }
+        for (int i = 0; i < kQ; ++i) {
+          CoalesceEntry e{};
+          for (int s = 0; s < 8; ++s) {
+            int px = 2 * X + (s & 1), py = 2 * Y + ((s >> 1) & 1), pz = 2 * Z + (s >> 2);
+            int ax = px - cx(i), ay = py - cy(i), az = pz - cz(i);
+            int bx = px - 2 * cx(i), by = py - 2 * cy(i), bz = pz - 2 * cz(i);
+            if (in_box(lo, hi, ax, ay, az)) {
+              long long a = F.addr(px, py, pz, i);
+              if (a < 0) {
+                m.error = "interface slot without storage";
+                return LBM_EINVAL;
+              }
+              e.fsrc[e.nfine++] = a;
+            } else if (in_box(lo, hi, bx, by, bz)) {
+              e.fsrc[e.nfine++] = -(long long)save_index(bx, by, bz, i) - 1;
+            } else {
+              e.ncoarse++;
+            }
+          }
+          if (e.nfine == 0) continue;
+          e.dst[0] = C.addr(X - cx(i), Y - cy(i), Z - cz(i), opposite(i));
+          e.dst[1] = C.addr(X, Y, Z, i);
+          if (e.dst[0] < 0 || e.dst[1] < 0) {
+            m.error = "interface slot without storage";
+            return LBM_EINVAL;
+          }
+          C.coal.push_back(e);
+        }
+      }
+  return LBM_OK;
+}
+
+}  // namespace
+
+int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vector<Prim>& prims, Mesh* out) {
+  Mesh& m = *out;
+  m.L = d.levels;
+  m.B = d.block;
+  m.n0[0] = d.nx;
+  m.n0[1] = d.ny;
+  m.n0[2] = d.nz;
+  for (int a = 0; a < 3; ++a) m.bc[a] = d.bc[a];
+  std::memcpy(m.boxes, boxes, sizeof(m.boxes));
+  m.lv.assign(m.L, Level());
+  const int B = m.B;
+  for (int l = 0; l < m.L; ++l) {
+    Level& v = m.lv[l];
+    v.l = l;
+    v.B = B;
+    if (l == 0) {
+      for (int a = 0; a < 3; ++a) {
+        v.rlo[a] = 0;
+        v.rhi[a] = m.n0[a];
+        if (m.bc[a] == LBM_BC_PERIODIC) {
+          if (m.n0[a] % B) {
+            m.error = "periodic axes must be multiples of the block size";
+            return LBM_EINVAL;
+          }
+          v.wrap[a] = true;
+          v.dom[a] = m.n0[a];
+          v.org[a] = 0;
+          v.nb[a] = m.n0[a] / B;
+        } else {
+          v.org[a] = -B;
+          v.nb[a] = (m.n0[a] + B - 1) / B + 2;
+        }
+      }
+    } else {
+      const Level& p = m.lv[l - 1];
+      for (int a = 0; a < 3; ++a) {
+        v.rlo[a] = boxes[l][a];
+        v.rhi[a] = boxes[l][3 + a];
+        if (v.rlo[a] % B || v.rhi[a] % B || v.rhi[a] <= v.rlo[a]) {
+          m.error = "refinement boxes must be aligned to whole blocks of their level";
+          return LBM_EINVAL;
+        }
+        // footprint inside the parent's real region, two parent cells to spare
+        if (v.rlo[a] / 2 < p.rlo[a] + 2 || v.rhi[a] / 2 > p.rhi[a] - 2) {
+          m.error = "refinement box leaves less than two cells of margin inside its parent level";
+          return LBM_EINVAL;
+        }
+        v.org[a] = v.rlo[a] - B;
+        v.nb[a] = (v.rhi[a] - v.rlo[a]) / B + 2;
+      }
+    }
+  }
+  for (int l = 0; l < m.L; ++l) {
+    int rc = layout_level(m, l);
+    if (rc) return rc;
+  }
+  for (int l = 0; l < m.L; ++l) {
+    classify_solids(m, l, prims);
+    Level& v = m.lv[l];
+    // collide masks and counts
+    const long long cpb = v.cells_per_block();
+    v.maskoff.assign(v.n_active, -1);
+    v.masks.clear();
+    v.n_fluid = 0;
+    for (int s = 0; s < v.n_active; ++s) {
+      const uint8_t* t = &v.type[(size_t)s * cpb];
+      long long nf = 0;
+      for (long long c = 0; c < cpb; ++c) nf += t[c] == FLUID;
+      v.n_fluid += nf;
+      if (nf != cpb) {
+        v.maskoff[s] = (int)(v.masks.size() / cpb);
+        for (long long c = 0; c < cpb; ++c) v.masks.push_back(t[c] == FLUID ? 1 : 0);
+      }
+    }
+    if (l + 1 < m.L) {
+      for (long long c = 0; c < (long long)v.n_active * cpb; ++c)
+        if (v.type[c] == SOLID) {
+          m.error = "the tree must lie inside the finest level's box";
+          return LBM_EINVAL;
+        }
+    }
+  }
+  for (int l = 0; l < m.L; ++l) {
+    int rc = build_links(m, l, prims);
+    if (rc) return rc;
+  }
+  int rc = build_faces(m);
+  if (rc) return rc;
+  for (int l = 0; l + 1 < m.L; ++l) {
+    rc = build_interface(m, l);
+    if (rc) return rc;
+  }
+  return LBM_OK;
+}
+
+}  // namespace lbm

@@ -1,0 +1,349 @@
+"""Python binding of liblbm (include/lbm.h): ctypes argument marshalling only.
+
+Every function named ``lbm_*`` here calls the C function of the same name;
+all computation runs in the library's CUDA kernels.  Device memory and the
+stream come from PyTorch (``Domain`` allocates the bound buffer with
+``torch.empty`` on the current device).  Importing this module fails loudly
+when the compiled library is missing: there is no other code path.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+BC = {"periodic": 0, "inout": 1, "slip": 2, "inflow": 3}
+LBM_FP32 = 1
+
+
+class DomainDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("levels", C.c_int), ("block", C.c_int),
+                ("bc", C.c_int * 3), ("u_in", C.c_double), ("re_h", C.c_double), ("nu_finest", C.c_double),
+                ("i_u", C.c_double), ("seed", C.c_ulonglong), ("refine_margin", C.c_double),
+                ("precision", C.c_int), ("galilean", C.c_int), ("omega2", C.c_double),
+                ("boxes", (C.c_int * 6) * 6)]
+
+
+class TreeDesc(C.Structure):
+    _fields_ = [("n", C.c_int), ("children", C.c_int), ("s0", C.c_double), ("w0", C.c_double),
+                ("min_len", C.c_double), ("r", C.c_double * 4), ("dfac", C.c_double * 4),
+                ("alpha_deg", C.c_double * 4), ("phi_deg", C.c_double * 4), ("azimuth_mode", C.c_int),
+                ("seed", C.c_ulonglong), ("trunk_cells", C.c_double)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = "%s failed: %s (%d): %s" % (where, _lib.lbm_status_string(code).decode(), code,
+                                          _lib.lbm_last_error().decode())
+        super().__init__(msg)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblbm.so is not built (run __graft_entry__.build()); there is no fallback path")
+    L = C.CDLL(LIB_PATH)
+    vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    dp, ip, llp, ubp = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_ubyte)
+    sig = {
+        "lbm_create_domain": ([C.POINTER(DomainDesc), vp, C.POINTER(vp)], i),
+        "lbm_set_geometry": ([vp, C.POINTER(TreeDesc)], i),
+        "lbm_set_geometry_segments": ([vp, dp, i], i),
+        "lbm_set_geometry_prims": ([vp, ip, dp, i], i),
+        "lbm_memory_requirements": ([vp, C.POINTER(sz)], i),
+        "lbm_bind_memory": ([vp, vp, sz], i),
+        "lbm_init_uniform": ([vp, d, dp], i),
+        "lbm_init_field": ([vp, i, dp, dp, sz], i),
+        "lbm_step": ([vp, i], i),
+        "lbm_drag": ([vp, dp, dp, dp], i),
+        "lbm_reset_force": ([vp], i),
+        "lbm_get_populations": ([vp, i, dp, sz], i),
+        "lbm_get_velocity": ([vp, i, dp, dp, sz], i),
+        "lbm_mass": ([vp, dp, dp], i),
+        "lbm_level_info": ([vp, i, ip, ip, llp, llp, llp], i),
+        "lbm_geometry_info": ([vp, dp, dp, ip, dp], i),
+        "lbm_get_cell_types": ([vp, i, ubp, sz], i),
+        "lbm_get_links": ([vp, i, llp, ip, dp, sz, llp], i),
+        "lbm_get_segments": ([vp, dp, i, ip], i),
+        "lbm_set_watchdog": ([vp, i], i),
+        "lbm_use_graphs": ([vp, i], i),
+        "lbm_set_timing": ([vp, i], i),
+        "lbm_get_timing": ([vp, dp, llp, llp], i),
+        "lbm_work_per_step": ([vp, llp, ip], i),
+        "lbm_save": ([vp, C.c_char_p], i),
+        "lbm_load": ([vp, C.c_char_p], i),
+        "lbm_destroy": ([vp], None),
+        "lbm_status_string": ([i], C.c_char_p),
+        "lbm_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+_lib = _load()
+
+
+def _ck(rc, where):
+    if rc != LBM_OK:
+        raise LbmError(rc, where)
+    return rc
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# ---------------------------------------------------------------- thin wrappers, C names
+
+def lbm_create_domain(desc, stream_ptr=0):
+    h = C.c_void_p()
+    _ck(_lib.lbm_create_domain(C.byref(desc), C.c_void_p(stream_ptr), C.byref(h)), "lbm_create_domain")
+    return h
+
+
+def lbm_set_geometry(h, tree):
+    return _ck(_lib.lbm_set_geometry(h, C.byref(tree)), "lbm_set_geometry")
+
+
+def lbm_set_geometry_segments(h, seg):
+    seg = np.ascontiguousarray(seg, dtype=np.float64).reshape(-1, 8)
+    return _ck(_lib.lbm_set_geometry_segments(h, _dp(seg), len(seg)), "lbm_set_geometry_segments")
+
+
+def lbm_set_geometry_prims(h, kinds, params):
+    kinds = np.ascontiguousarray(kinds, dtype=np.int32)
+    params = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 8)
+    return _ck(_lib.lbm_set_geometry_prims(h, kinds.ctypes.data_as(C.POINTER(C.c_int)), _dp(params),
+                                           len(kinds)), "lbm_set_geometry_prims")
+
+
+def lbm_memory_requirements(h):
+    n = C.c_size_t()
+    _ck(_lib.lbm_memory_requirements(h, C.byref(n)), "lbm_memory_requirements")
+    return n.value
+
+
+def lbm_bind_memory(h, ptr, nbytes):
+    return _ck(_lib.lbm_bind_memory(h, C.c_void_p(ptr), nbytes), "lbm_bind_memory")
+
+
+def lbm_init_uniform(h, rho, u):
+    u = np.asarray(u, dtype=np.float64)
+    return _ck(_lib.lbm_init_uniform(h, float(rho), _dp(u)), "lbm_init_uniform")
+
+
+def lbm_init_field(h, level, rho, u):
+    rho = np.ascontiguousarray(rho, dtype=np.float64).ravel()
+    u = np.ascontiguousarray(u, dtype=np.float64).ravel()
+    return _ck(_lib.lbm_init_field(h, level, _dp(rho), _dp(u), len(rho)), "lbm_init_field")
+
+
+def lbm_step(h, n):
+    return _ck(_lib.lbm_step(h, int(n)), "lbm_step")
+
+
+def lbm_drag(h):
+    last, mean, cd = np.zeros(3), np.zeros(3), C.c_double()
+    _ck(_lib.lbm_drag(h, _dp(last), _dp(mean), C.byref(cd)), "lbm_drag")
+    return last, mean, cd.value
+
+
+def lbm_reset_force(h):
+    return _ck(_lib.lbm_reset_force(h), "lbm_reset_force")
+
+
+def lbm_level_info(h, level):
+    lo, hi = (C.c_int * 3)(), (C.c_int * 3)()
+    nf, nl, nb = C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _ck(_lib.lbm_level_info(h, level, lo, hi, C.byref(nf), C.byref(nl), C.byref(nb)), "lbm_level_info")
+    return {"lo": tuple(lo), "hi": tuple(hi), "n_fluid": nf.value, "n_links": nl.value, "n_active_blocks": nb.value}
+
+
+def _box_shape(h, level):
+    info = lbm_level_info(h, level)
+    return tuple(info["hi"][a] - info["lo"][a] for a in range(3))
+
+
+def lbm_get_populations(h, level):
+    nx, ny, nz = _box_shape(h, level)
+    out = np.zeros(nx * ny * nz * 27)
+    _ck(_lib.lbm_get_populations(h, level, _dp(out), nx * ny * nz), "lbm_get_populations")
+    return out.reshape(nz, ny, nx, 27)
+
+
+def lbm_get_velocity(h, level):
+    nx, ny, nz = _box_shape(h, level)
+    rho, u = np.zeros(nx * ny * nz), np.zeros(nx * ny * nz * 3)
+    _ck(_lib.lbm_get_velocity(h, level, _dp(rho), _dp(u), nx * ny * nz), "lbm_get_velocity")
+    return rho.reshape(nz, ny, nx), u.reshape(nz, ny, nx, 3)
+
+
+def lbm_mass(h):
+    m, p = C.c_double(), np.zeros(3)
+    _ck(_lib.lbm_mass(h, C.byref(m), _dp(p)), "lbm_mass")
+    return m.value, p
+
+
+def lbm_geometry_info(h):
+    H, A, nu = C.c_double(), C.c_double(), C.c_double()
+    ns = C.c_int()
+    _ck(_lib.lbm_geometry_info(h, C.byref(H), C.byref(A), C.byref(ns), C.byref(nu)), "lbm_geometry_info")
+    return {"H": H.value, "A_x": A.value, "n_segments": ns.value, "nu_finest": nu.value}
+
+
+def lbm_get_cell_types(h, level):
+    nx, ny, nz = _box_shape(h, level)
+    out = np.zeros(nx * ny * nz, np.uint8)
+    _ck(_lib.lbm_get_cell_types(h, level, out.ctypes.data_as(C.POINTER(C.c_ubyte)), nx * ny * nz),
+        "lbm_get_cell_types")
+    return out.reshape(nz, ny, nx)
+
+
+def lbm_get_links(h, level):
+    n = C.c_longlong()
+    _ck(_lib.lbm_get_links(h, level, None, None, None, 0, C.byref(n)), "lbm_get_links")
+    cell = np.zeros(n.value, np.int64)
+    d = np.zeros(n.value, np.int32)
+    q = np.zeros(n.value)
+    _ck(_lib.lbm_get_links(h, level, cell.ctypes.data_as(C.POINTER(C.c_longlong)),
+                           d.ctypes.data_as(C.POINTER(C.c_int)), _dp(q), n.value, C.byref(n)), "lbm_get_links")
+    return cell, d, q
+
+
+def lbm_get_segments(h):
+    n = C.c_int()
+    _ck(_lib.lbm_get_segments(h, None, 0, C.byref(n)), "lbm_get_segments")
+    seg = np.zeros((n.value, 8))
+    _ck(_lib.lbm_get_segments(h, _dp(seg), n.value, C.byref(n)), "lbm_get_segments")
+    return seg
+
+
+def lbm_set_watchdog(h, every):
+    return _ck(_lib.lbm_set_watchdog(h, int(every)), "lbm_set_watchdog")
+
+
+def lbm_use_graphs(h, on):
+    return _ck(_lib.lbm_use_graphs(h, int(bool(on))), "lbm_use_graphs")
+
+
+def lbm_set_timing(h, on):
+    return _ck(_lib.lbm_set_timing(h, int(bool(on))), "lbm_set_timing")
+
+
+def lbm_get_timing(h):
+    ms = np.zeros(4)
+    la = np.zeros(4, np.int64)
+    un = np.zeros(4, np.int64)
+    _ck(_lib.lbm_get_timing(h, _dp(ms), la.ctypes.data_as(C.POINTER(C.c_longlong)),
+                            un.ctypes.data_as(C.POINTER(C.c_longlong))), "lbm_get_timing")
+    return ms, la, un
+
+
+def lbm_work_per_step(h):
+    cu, k = C.c_longlong(), C.c_int()
+    _ck(_lib.lbm_work_per_step(h, C.byref(cu), C.byref(k)), "lbm_work_per_step")
+    return cu.value, k.value
+
+
+def lbm_save(h, path):
+    return _ck(_lib.lbm_save(h, path.encode()), "lbm_save")
+
+
+def lbm_load(h, path):
+    return _ck(_lib.lbm_load(h, path.encode()), "lbm_load")
+
+
+def lbm_destroy(h):
+    _lib.lbm_destroy(h)
+
+
+def lbm_status_string(code):
+    return _lib.lbm_status_string(code).decode()
+
+
+# ---------------------------------------------------------------- descriptors
+
+def domain_desc(nx, ny, nz, levels=1, block=16, bc=("inout", "slip", "slip"), u_in=0.05, re_h=0.0,
+                nu_finest=0.0, refine_margin=0.25, galilean=True, omega2=1.0, boxes=None):
+    d = DomainDesc()
+    d.nx, d.ny, d.nz, d.levels, d.block = nx, ny, nz, levels, block
+    for a in range(3):
+        d.bc[a] = BC[bc[a]] if isinstance(bc[a], str) else int(bc[a])
+    d.u_in, d.re_h, d.nu_finest, d.i_u, d.seed = u_in, re_h, nu_finest, 0.0, 0
+    d.refine_margin, d.precision, d.galilean, d.omega2 = refine_margin, LBM_FP32, int(galilean), omega2
+    if boxes:
+        for l, b in enumerate(boxes):
+            if b is not None:
+                for q in range(6):
+                    d.boxes[l][q] = int(b[q])
+    return d
+
+
+def tree_desc(n, children=2, s0=100.0, w0=30.0, r=(0.8,), dfac=(0.5 ** 0.5,), alpha_deg=(30.0, -30.0),
+              phi_deg=(137.0,), azimuth_mode=0, seed=0, min_len=0.02, trunk_cells=None):
+    t = TreeDesc()
+    t.n, t.children, t.s0, t.w0, t.min_len = n, children, s0, w0, min_len
+    for k in range(children):
+        t.r[k] = r[k % len(r)]
+        t.dfac[k] = dfac[k % len(dfac)]
+        t.alpha_deg[k] = alpha_deg[k % len(alpha_deg)]
+        t.phi_deg[k] = phi_deg[k % len(phi_deg)]
+    t.azimuth_mode, t.seed = azimuth_mode, seed
+    t.trunk_cells = s0 if trunk_cells is None else trunk_cells
+    return t
+
+
+class Domain:
+    """Convenience owner of a domain handle and its torch-allocated buffer."""
+
+    def __init__(self, desc, tree=None, segments=None, prims=None, device="cuda", stream=None, bind=True):
+        self._torch = None
+        self.stream = stream
+        sp = 0
+        if stream is not None:
+            sp = stream.cuda_stream
+        self.h = lbm_create_domain(desc, sp)
+        self.desc = desc
+        if tree is not None:
+            lbm_set_geometry(self.h, tree)
+        elif segments is not None:
+            lbm_set_geometry_segments(self.h, segments)
+        else:
+            kinds, params = prims if prims is not None else ([], np.zeros((0, 8)))
+            lbm_set_geometry_prims(self.h, kinds, params)
+        self.nbytes = lbm_memory_requirements(self.h)
+        self.buffer = None
+        if bind:
+            self.bind(device)
+
+    def bind(self, device="cuda"):
+        import torch
+        self._torch = torch
+        self.buffer = torch.empty(max(self.nbytes, 256), dtype=torch.uint8, device=device)
+        lbm_bind_memory(self.h, self.buffer.data_ptr(), self.buffer.numel())
+
+    def __getattr__(self, name):
+        fn = globals().get("lbm_" + name)
+        if fn is None:
+            raise AttributeError(name)
+        return lambda *a, **k: fn(self.h, *a, **k)
+
+    def close(self):
+        if getattr(self, "h", None):
+            if self.buffer is not None:
+                self._torch.cuda.synchronize(self.buffer.device)
+            lbm_destroy(self.h)
+            self.h = None
+            self.buffer = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

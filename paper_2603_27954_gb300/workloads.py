@@ -1,0 +1,46 @@
+"""Seeded synthetic workloads shaped like the paper's tree-drag runs.
+
+Plain parameter records (no method arithmetic); the test-suite hands the same
+records to the CUDA library and to the oracle.  The paper's own runs (Sec.
+2.3: a 32H x 16H x 16H box, Re_H from 2.5e3 to 1.2e5, finest cells of H/1024
+to H/2048) are far larger; these stand in for them with trees from the
+parametric L-system of Eq. (1), seeded branch azimuths and lattice inflow
+speed 0.05.
+"""
+
+# tree of Eq. (1) in the "azimuth" form: each child tilted by alpha from its
+# parent and turned about the parent's axis by a seeded azimuth
+TINY_TREE = dict(n=2, children=2, s0=12.0, w0=2.0, r=(0.6,), dfac=(0.7,), alpha_deg=(30.0,),
+                 azimuth_mode=1, seed=0, trunk_cells=12.0)
+
+CASES = {
+    # single-level 64x32x32, trunk 12 cells / diameter 2, two children, Re_H = 100
+    "tiny": dict(n0=(64, 32, 32), levels=1, block=16, bc=("inout", "slip", "slip"), u_in=0.05, re_h=100.0,
+                 steps=1000, tree=TINY_TREE),
+    # two levels, coarse 256x128x128 in 16^3 blocks, 3 generations of 3 children,
+    # trunk 64 finest cells (diameter 0.3 of its length, as w0/s0 of Table 1), Re_H = 2.5e3
+    "amr2": dict(n0=(256, 128, 128), levels=2, block=16, bc=("inout", "inflow", "inflow"), u_in=0.05,
+                 re_h=2500.0, steps=10000,
+                 tree=dict(n=4, children=3, s0=64.0, w0=19.2, r=(0.6,), dfac=(0.6,), alpha_deg=(35.0,),
+                           azimuth_mode=1, seed=1, trunk_cells=64.0)),
+    # the two-level case scaled down by 4 (8^3 blocks), sized for the oracle
+    "amr2_small": dict(n0=(64, 48, 48), levels=2, block=8, bc=("inout", "inflow", "inflow"), u_in=0.05,
+                       re_h=400.0, steps=100,
+                       tree=dict(n=3, children=3, s0=16.0, w0=4.8, r=(0.6,), dfac=(0.6,), alpha_deg=(35.0,),
+                                 azimuth_mode=1, seed=1, trunk_cells=16.0)),
+}
+
+
+def tgv_fields(lo, hi, scale, n, amplitude, mean=(0.0, 0.0, 0.0)):
+    """Taylor-Green initial field (rho, u) on cells [lo, hi) of a level whose
+    cells are 1/scale of a level-0 cell, wavelength n level-0 cells."""
+    import numpy as np
+    k = 2 * np.pi / n
+    z, y, x = np.meshgrid(*(np.arange(lo[a], hi[a]) + 0.5 for a in (2, 1, 0)), indexing="ij")
+    x = x / scale - 0.5
+    y = y / scale - 0.5
+    ux = mean[0] + amplitude * np.sin(k * x) * np.cos(k * y)
+    uy = mean[1] - amplitude * np.cos(k * x) * np.sin(k * y)
+    uz = mean[2] + 0 * x
+    rho = 1 - 0.75 * amplitude ** 2 * (np.cos(2 * k * x) + np.cos(2 * k * y))
+    return rho, np.stack([ux, uy, uz], -1)

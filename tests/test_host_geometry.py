@@ -1,0 +1,142 @@
+"""The library's host side (no GPU needed) against the oracle: the L-system,
+placement, tree height, frontal area, refinement boxes, cell classification
+per level and the cut links with their wall fractions.  Cell types and link
+sets are integer data and must agree exactly."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_27954_gb300 import lbm as L
+from paper_2603_27954_gb300 import workloads as W
+
+
+def oracle_tree(t):
+    return O.make_tree(t["n"], t["children"], t["s0"], t["w0"], t["r"], t["dfac"], alpha_deg=t["alpha_deg"],
+                       phi_deg=t.get("phi_deg", (0.0,)), azimuth_mode=t["azimuth_mode"], seed=t["seed"])
+
+
+def lib_domain(case):
+    c = W.CASES[case]
+    d = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"], re_h=c["re_h"])
+    h = L.lbm_create_domain(d)
+    L.lbm_set_geometry(h, L.tree_desc(**c["tree"]))
+    return h
+
+
+def oracle_case(case):
+    c = W.CASES[case]
+    return O.tree_case(*c["n0"], oracle_tree(c["tree"]), c["tree"]["trunk_cells"], c["re_h"], u_in=c["u_in"],
+                       levels=c["levels"], block=c["block"], bc=c["bc"])
+
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_lsystem_matches_oracle_paper_form(n):
+    """Table 1 trees (fixed phi = 137 deg): identical segments."""
+    h = L.lbm_create_domain(L.domain_desc(64, 64, 64, bc=("periodic",) * 3, nu_finest=0.01))
+    t = L.tree_desc(n, trunk_cells=100.0)
+    L.lbm_set_geometry(h, t)
+    seg = L.lbm_get_segments(h)
+    ref = O.place_tree(O.make_tree(n), 100.0, (64, 64, 64))
+    np.testing.assert_allclose(seg, ref, rtol=0, atol=1e-9)
+    L.lbm_destroy(h)
+
+
+@pytest.mark.parametrize("case", ["tiny", "amr2_small", "amr2"])
+def test_geometry_scalars_match_oracle(case):
+    h = lib_domain(case)
+    g = L.lbm_geometry_info(h)
+    _, info = oracle_case(case) if case != "amr2" else (None, None)
+    if info is None:
+        c = W.CASES[case]
+        fin = 2 ** (c["levels"] - 1)
+        seg = O.place_tree(oracle_tree(c["tree"]), c["tree"]["trunk_cells"], tuple(n * fin for n in c["n0"]))
+        info = {"segments": seg, "H": O.tree_height(seg), "A_x": O.frontal_area(seg),
+                "boxes": O.refine_boxes(seg, c["levels"], c["n0"], c["block"])}
+    np.testing.assert_allclose(L.lbm_get_segments(h), info["segments"], atol=1e-9)
+    assert g["H"] == pytest.approx(info["H"], rel=1e-12)
+    assert g["A_x"] == pytest.approx(info["A_x"], rel=1e-12)
+    for l in range(1, len(info["boxes"])):
+        li = L.lbm_level_info(h, l)
+        assert list(li["lo"]) + list(li["hi"]) == list(info["boxes"][l])
+    L.lbm_destroy(h)
+
+
+@pytest.mark.parametrize("case", ["tiny", "amr2_small"])
+def test_cell_types_and_links_match_oracle(case):
+    h = lib_domain(case)
+    sim, info = oracle_case(case)
+    levels = W.CASES[case]["levels"]
+    total_links = 0
+    for l in range(levels):
+        lt = L.lbm_get_cell_types(h, l)
+        ot = sim.cell_type(l)
+        np.testing.assert_array_equal(lt, ot)
+        c1, d1, q1 = L.lbm_get_links(h, l)
+        c2, d2, q2 = sim.links(l)
+        k1 = np.lexsort((d1, c1))
+        k2 = np.lexsort((d2, c2))
+        np.testing.assert_array_equal(c1[k1], c2[k2])
+        np.testing.assert_array_equal(d1[k1], d2[k2])
+        np.testing.assert_allclose(q1[k1], q2[k2], rtol=0, atol=1e-12)
+        total_links += len(q1)
+        if len(q1):
+            assert (q1 > 0).all() and (q1 <= 1).all()
+    assert total_links > 0
+    L.lbm_destroy(h)
+
+
+def test_planar_walls_links_match_oracle():
+    """General primitives (two half-spaces) classify and link identically."""
+    kinds = [1, 1]
+    params = np.zeros((2, 8))
+    params[0, :4] = (0, 1, 0, 2.3)
+    params[1, :4] = (0, -1, 0, -17.8)
+    h = L.lbm_create_domain(L.domain_desc(16, 20, 16, bc=("periodic", "periodic", "periodic"), nu_finest=0.1))
+    with pytest.raises(L.LbmError):
+        L.lbm_set_geometry_prims(h, kinds, params)  # y = 20 is not a multiple of the block
+    L.lbm_destroy(h)
+    h = L.lbm_create_domain(L.domain_desc(16, 32, 16, block=16, bc=("periodic",) * 3, nu_finest=0.1))
+    params[1, :4] = (0, -1, 0, -29.6)
+    L.lbm_set_geometry_prims(h, kinds, params)
+    s = O.Sim(16, 32, 16, bc=("periodic",) * 3, nu0=0.1, u_in=0.0)
+    s.set_prims(O.prims([(1, params[0, :4]), (1, params[1, :4])]))
+    np.testing.assert_array_equal(L.lbm_get_cell_types(h, 0), s.cell_type(0))
+    c1, d1, q1 = L.lbm_get_links(h, 0)
+    c2, d2, q2 = s.links(0)
+    k1, k2 = np.lexsort((d1, c1)), np.lexsort((d2, c2))
+    np.testing.assert_array_equal(c1[k1], c2[k2])
+    np.testing.assert_allclose(q1[k1], q2[k2], atol=1e-12)
+    L.lbm_destroy(h)
+
+
+def test_invalid_descriptors_are_rejected():
+    bad = [
+        dict(levels=0), dict(levels=7), dict(block=12), dict(u_in=0.5),
+    ]
+    for kw in bad:
+        args = dict(nx=32, ny=32, nz=32, bc=("inout", "slip", "slip"), nu_finest=0.01)
+        args.update(kw)
+        nx, ny, nz = args.pop("nx"), args.pop("ny"), args.pop("nz")
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_create_domain(L.domain_desc(nx, ny, nz, **args))
+        assert e.value.code == L.LBM_EINVAL
+    h = L.lbm_create_domain(L.domain_desc(32, 32, 32, bc=("inout", "slip", "slip"), nu_finest=0.01))
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_memory_requirements(h)
+    assert e.value.code == L.LBM_ESTATE
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_step(h, 1)
+    assert e.value.code == L.LBM_ESTATE
+    L.lbm_destroy(h)
+
+
+def test_ragged_domain_keeps_every_cell():
+    """A domain that is not a multiple of the block size: partial blocks hold
+    the extra cells, the rest of those blocks is outside."""
+    h = L.lbm_create_domain(L.domain_desc(40, 20, 24, bc=("inout", "slip", "slip"), nu_finest=0.02))
+    L.lbm_set_geometry_prims(h, [], np.zeros((0, 8)))
+    info = L.lbm_level_info(h, 0)
+    assert info["n_fluid"] == 40 * 20 * 24
+    assert info["n_active_blocks"] == 3 * 2 * 2
+    assert (L.lbm_get_cell_types(h, 0) == 0).all()
+    L.lbm_destroy(h)
