@@ -2,13 +2,6 @@
 L-system tree, with interpolated bounce-back and momentum-exchange drag.
 
 The compute path is liblbm.so (CUDA for sm_103a) behind the C-ABI in
-include/lbm.h; ``lbm`` is its ctypes binding.
+include/lbm.h; ``paper_2603_27954_gb300.lbm`` is its ctypes binding and
+``paper_2603_27954_gb300.build`` compiles it.
 """
-import os
-
-HERE = os.path.dirname(os.path.abspath(__file__))
-
-
-def build(force=False):
-    from . import build as _b
-    return _b.build(force=force)
