@@ -1,0 +1,326 @@
+"""Throughput of the cumulant-LBM tree-drag step on GB300.
+
+One step = one coarse step of the whole path: collide-stream of every level
+(2^l sub-steps of level l), faces, bounce-back with the FP64 drag reduction,
+and the refinement-interface transfer, replayed as one CUDA graph.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is whole-job MLUPS (cell updates summed over
+levels, level l counted 2^l times per coarse step, over all ranks) with the
+state resident in HBM; ``e2e`` is the same metric through the C-ABI including
+binding (table upload and initialisation) and a host read of the drag after
+every step.  With N > 1 every rank runs an independent replica (the problem
+does not shard on one GPU per rank here) and the time is the maximum over
+ranks.  ``--impl reference`` times the FP64 CPU oracle on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CASE = "amr2"
+SMALL = "amr2_small"
+BYTES_PER_UPDATE = 2 * 27 * 4  # read and write 27 FP32 populations
+KERNEL_SOURCES = ["paper_2603_27954_gb300/csrc/kernels.cu", "paper_2603_27954_gb300/csrc/cumulant.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per collide launch from the committed ncu summary, if it was
+    taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "collide_amr2_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d
+
+
+def workload_desc(L, W, case):
+    c = W.CASES[case]
+    desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
+                         re_h=c["re_h"])
+    return desc, L.tree_desc(**c["tree"]), c
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rate(case, steps):
+    """Oracle MLUPS on `steps` coarse steps of a workload; also its drag."""
+    import oracle as O
+    from paper_2603_27954_gb300 import workloads as W
+    c = W.CASES[case]
+    t = c["tree"]
+    tree = O.make_tree(t["n"], t["children"], t["s0"], t["w0"], t["r"], t["dfac"], alpha_deg=t["alpha_deg"],
+                       azimuth_mode=t["azimuth_mode"], seed=t["seed"])
+    sim, info = O.tree_case(*c["n0"], tree, t["trunk_cells"], c["re_h"], u_in=c["u_in"], levels=c["levels"],
+                            block=c["block"], bc=c["bc"])
+    updates = 0
+    for l in range(c["levels"]):
+        updates += int((sim.cell_type(l) == 0).sum()) << l
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    last, _, _ = sim.force()
+    cd = O.drag_coefficient(last[0], c["u_in"], info["A_x"])
+    return updates * steps / dt / 1e6, dt, cd, updates
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # each step: one coarse step of the workload scaled down by 4 per axis
+    # (the oracle would need minutes per coarse step of the full size)
+    import oracle as O
+    from paper_2603_27954_gb300 import workloads as W
+    c = W.CASES[SMALL]
+    t = c["tree"]
+    tree = O.make_tree(t["n"], t["children"], t["s0"], t["w0"], t["r"], t["dfac"], alpha_deg=t["alpha_deg"],
+                       azimuth_mode=t["azimuth_mode"], seed=t["seed"])
+    sim, info = O.tree_case(*c["n0"], tree, t["trunk_cells"], c["re_h"], u_in=c["u_in"], levels=c["levels"],
+                            block=c["block"], bc=c["bc"])
+    updates = sum(int((sim.cell_type(l) == 0).sum()) << l for l in range(c["levels"]))
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = updates * args.steps / dt / 1e6
+    cores = os.cpu_count()
+    sample = "%d coarse steps of the two-level tree case scaled down 4x per axis (coarse %dx%dx%d, %d cell updates per step)" % (
+        args.steps, *c["n0"], updates)
+    line = {
+        "impl": "reference", "metric": "D3Q27 cumulant LBM MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "FP64 CPU oracle, " + sample},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--timing-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_27954_gb300 import lbm as L
+    from paper_2603_27954_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    desc, tree, c = workload_desc(L, W, CASE)
+    stream = torch.cuda.Stream()
+    dom = L.Domain(desc, tree=tree, stream=stream)
+    updates, kernels = dom.work_per_step()
+    dom.step(args.warmup)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dom.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = updates * world * args.steps / (ms_max / 1e3) / 1e6
+
+    # per-kernel timing with CUDA events on the domain's stream (direct launches)
+    dom.set_timing(True)
+    dom.step(args.timing_steps)
+    kms, klaunch, kunits = dom.get_timing()
+    dom.set_timing(False)
+    peak, peak_kind = measured_peaks()
+    coll_gbs = kunits[0] * BYTES_PER_UPDATE / (kms[0] / 1e3) / 1e9
+    total_ms = float(kms.sum())
+    tr = profiled_traffic()
+    roofline = {"bound": "hbm", "kernel": "k_collide (fused collide-stream)",
+                "achieved": coll_gbs, "peak": peak, "peak_kind": peak_kind + " copy bandwidth", "unit": "GB/s",
+                "frac": coll_gbs / peak,
+                "traffic": tr["bytes_per_launch"] if tr else None,
+                "traffic_note": tr["note"] if tr else "no ncu capture of the current kernel sources",
+                "algorithmic_bytes_per_launch": kunits[0] * BYTES_PER_UPDATE / max(1, klaunch[0]),
+                "share_of_step_time": float(kms[0] / total_ms) if total_ms else None,
+                "path_frac": updates * BYTES_PER_UPDATE * args.steps / (ms_max / 1e3) / 1e9 / peak}
+
+    # end to end through the C-ABI: re-bind (upload tables, initialise), then
+    # every step followed by a host read of the drag
+    torch.cuda.synchronize()
+    barrier()
+    h0 = time.perf_counter()
+    L.lbm_bind_memory(dom.h, dom.buffer.data_ptr(), dom.buffer.numel())
+    for _ in range(args.e2e_steps):
+        dom.step(1)
+        _, _, cd = dom.drag()
+    torch.cuda.synchronize()
+    h1 = time.perf_counter()
+    tt = torch.tensor([h1 - h0], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_value = updates * world * args.e2e_steps / float(tt.item()) / 1e6
+    info0 = L.lbm_level_info(dom.h, 0)
+    geo = dom.geometry_info()
+
+    cpu = None
+    cd_err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # about 10-20 s of oracle work: time a few steps, then size the sample
+        r0, dt0, _, _ = oracle_rate(SMALL, 2)
+        small_steps = max(4, min(400, int(12.0 / max(dt0 / 2, 1e-3))))
+        o_mlups, o_dt, o_cd, o_upd = oracle_rate(SMALL, small_steps)
+        d2, t2, c2 = workload_desc(L, W, SMALL)
+        sdom = L.Domain(d2, tree=t2, stream=stream)
+        sdom.step(small_steps)
+        _, _, g_cd = sdom.drag()
+        sdom.close()
+        cpu = {"value": o_mlups, "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d coarse steps (%.1f s) of the two-level tree case scaled down 4x per axis, "
+                         "%d cell updates per step" % (small_steps, o_dt, o_upd)}
+        cd_err = {"case": "two-level tree case scaled down 4x, after %d coarse steps" % small_steps,
+                  "cd_gpu": g_cd, "cd_oracle": o_cd, "rel_err": abs(g_cd - o_cd) / abs(o_cd)}
+
+    line = {
+        "metric": "D3Q27 cumulant LBM MLUPS & % HBM roofline; C_D rel. error vs FP64 oracle",
+        "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "two-level tree drag: coarse %dx%dx%d in %d^3 blocks, finest box %s, L-system n=%d x %d "
+                               "children, trunk %g finest cells, Re_H=%g, U=%g" % (
+                                   *c["n0"], c["block"], str(L.lbm_level_info(dom.h, 1)["lo"]) + "-" +
+                                   str(L.lbm_level_info(dom.h, 1)["hi"]), c["tree"]["n"], c["tree"]["children"],
+                                   c["tree"]["trunk_cells"], c["re_h"], c["u_in"]),
+                   "cell_updates_per_step": updates, "l2": "inputs larger than L2 (%.2f GB of populations and tables)"
+                   % (dom.nbytes / 1e9), "replicas": world},
+        "roofline": roofline,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": dom.nbytes / args.e2e_steps,
+                "d2h_bytes_per_step": 64,
+                "note": "includes binding (table upload and equilibrium initialisation of %.2f GB) once and a "
+                        "synchronous drag read after each of %d steps" % (dom.nbytes / 1e9, args.e2e_steps)},
+        "gpu_launches": kernels * args.steps,
+        "kernels_per_step": kernels,
+        "cd": cd,
+        "cd_rel_err_vs_oracle": cd_err,
+        "cpu_baseline": cpu,
+        "geometry": {"H_finest_cells": geo["H"], "A_x": geo["A_x"], "segments": geo["n_segments"],
+                     "nu_finest": geo["nu_finest"], "fluid_cells_level0": info0["n_fluid"]},
+    }
+    dom.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
