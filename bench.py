@@ -178,7 +178,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -240,7 +240,10 @@ def main():
     kms, klaunch, kunits = dom.get_timing()
     dom.set_timing(False)
     peak, peak_kind = measured_peaks()
-    coll_gbs = kunits[0] * BYTES_PER_UPDATE / (kms[0] / 1e3) / 1e9
+    coll_ms = kms[0] + kms[1]
+    coll_units = kunits[0] + kunits[1]
+    coll_launch = klaunch[0] + klaunch[1]
+    coll_gbs = coll_units * BYTES_PER_UPDATE / (coll_ms / 1e3) / 1e9
     total_ms = float(kms.sum())
     tr = profiled_traffic()
     roofline = {"bound": "hbm", "kernel": "k_collide (fused collide-stream)",
@@ -248,8 +251,11 @@ def main():
                 "frac": coll_gbs / peak,
                 "traffic": tr["bytes_per_launch"] if tr else None,
                 "traffic_note": tr["note"] if tr else "no ncu capture of the current kernel sources",
-                "algorithmic_bytes_per_launch": kunits[0] * BYTES_PER_UPDATE / max(1, klaunch[0]),
-                "share_of_step_time": float(kms[0] / total_ms) if total_ms else None,
+                "algorithmic_bytes_per_launch": coll_units * BYTES_PER_UPDATE / max(1, coll_launch),
+                "even_gbs": kunits[0] * BYTES_PER_UPDATE / (kms[0] / 1e3) / 1e9 if kms[0] else None,
+                "odd_gbs": kunits[1] * BYTES_PER_UPDATE / (kms[1] / 1e3) / 1e9 if kms[1] else None,
+                "share_of_step_time": float(coll_ms / total_ms) if total_ms else None,
+                "timed_launches": int(coll_launch),
                 "path_frac": updates * BYTES_PER_UPDATE * args.steps / (ms_max / 1e3) / 1e9 / peak}
 
     # end to end through the C-ABI: re-bind (upload tables, initialise), then

@@ -185,11 +185,12 @@ int lbm_use_graphs(lbm_domain* d, int on);
 
 /* Kernel timing with CUDA events on the domain's stream (adds no
    synchronisation inside lbm_step; graphs are bypassed while on).
-   lbm_get_timing returns, per kernel class k (0 collide-stream, 1 faces,
-   2 bounce-back + force, 3 interface), the summed milliseconds, the number
-   of launches and the cell updates / links processed.  Synchronises. */
+   lbm_get_timing returns, per kernel class k (0 collide-stream even steps,
+   1 collide-stream odd steps, 2 faces, 3 bounce-back + force, 4 interface,
+   5 unused), the summed milliseconds, the number of launches and the cell
+   updates / links / entries processed since the last call.  Synchronises. */
 int lbm_set_timing(lbm_domain* d, int on);
-int lbm_get_timing(lbm_domain* d, double ms[4], long long launches[4], long long units[4]);
+int lbm_get_timing(lbm_domain* d, double ms[6], long long launches[6], long long units[6]);
 
 /* Cell updates per coarse step (sum over levels of fluid cells * 2^l) and
    the number of kernels launched per coarse step. */

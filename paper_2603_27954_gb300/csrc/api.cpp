@@ -44,7 +44,7 @@ double equilibrium(int i, double rho, const double u[3]) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-enum { KC_COLLIDE = 0, KC_FACES = 1, KC_WALLS = 2, KC_IFACE = 3 };
+enum { KC_COLLIDE = 0, KC_COLLIDE_ODD = 1, KC_FACES = 2, KC_WALLS = 3, KC_IFACE = 4, KC_N = 6 };
 }  // namespace
 
 struct lbm_domain {
@@ -78,8 +78,8 @@ struct lbm_domain {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
-  double ms[4] = {0, 0, 0, 0};
-  long long launches[4] = {0, 0, 0, 0}, units[4] = {0, 0, 0, 0};
+  double ms[KC_N] = {};
+  long long launches[KC_N] = {}, units[KC_N] = {};
 
   template <class T>
   T* dev(size_t off) const { return reinterpret_cast<T*>(base + off); }
@@ -130,9 +130,10 @@ int advance(lbm_domain* dm, int l, int parity) {
   float* f = dm->dev<float>(v.off_f);
   int rc;
   {
-    Timed t(dm, KC_COLLIDE, v.n_fluid);
-    CollideArgs a{f, dm->dev<int>(v.off_nbr), dm->dev<int>(v.off_maskoff), dm->dev<uint8_t>(v.off_masks),
-                  v.n_active, (float)v.omega1, (float)dm->d.omega2, dm->d.galilean};
+    Timed t(dm, parity ? KC_COLLIDE_ODD : KC_COLLIDE, v.n_fluid);
+    CollideArgs a{f, (long long)v.f_elems(), dm->dev<int>(v.off_nbr), dm->dev<int>(v.off_maskoff),
+                  dm->dev<uint8_t>(v.off_masks), v.n_active, (float)v.omega1, (float)dm->d.omega2,
+                  dm->d.galilean};
     if ((rc = launch_collide(a, v.B, parity, dm->stream))) return rc;
   }
   if (l == 0 && !v.face[parity].empty()) {
@@ -685,7 +686,7 @@ int lbm_set_timing(lbm_domain* d, int on) {
   return LBM_OK;
 }
 
-int lbm_get_timing(lbm_domain* d, double ms[4], long long launches[4], long long units[4]) {
+int lbm_get_timing(lbm_domain* d, double ms[6], long long launches[6], long long units[6]) {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (d->base) CK(cudaStreamSynchronize(d->stream));
   for (auto& r : d->recs) {
@@ -697,7 +698,7 @@ int lbm_get_timing(lbm_domain* d, double ms[4], long long launches[4], long long
   }
   d->recs.clear();
   d->pool_used = 0;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < KC_N; ++k) {
     if (ms) ms[k] = d->ms[k];
     if (launches) launches[k] = d->launches[k];
     if (units) units[k] = d->units[k];

@@ -137,6 +137,7 @@ void refinement_boxes(const Tree& t, int levels, int block, double margin, int b
 // ---------------------------------------------------------------- kernels (kernels.cu)
 struct CollideArgs {
   float* f;
+  long long f_elems;  // floats in the level's array
   const int* nbr;
   const int* maskoff;
   const uint8_t* masks;

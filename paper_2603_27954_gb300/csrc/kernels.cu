@@ -33,12 +33,20 @@ __device__ __forceinline__ int block_digit(int c) {
   return c < 0 ? 0 : (c >= B ? 2 : 1);
 }
 
-template <int B, bool ODD>
-__global__ void __launch_bounds__(B * B) k_collide(CollideArgs a) {
+#ifndef LBM_EVEN_MINB
+#define LBM_EVEN_MINB 4
+#endif
+#ifndef LBM_ODD_MINB
+#define LBM_ODD_MINB 2
+#endif
+
+// IDX: element-offset type, 32-bit when the level's array has < 2^31 floats
+template <int B, bool ODD, typename IDX>
+__global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_collide(CollideArgs a) {
   constexpr int C3 = B * B * B;
-  __shared__ long long s_base[27];
+  __shared__ IDX s_base[27];
   const int blk = blockIdx.x;
-  if (threadIdx.x < 27) s_base[threadIdx.x] = (long long)a.nbr[(size_t)blk * 27 + threadIdx.x] * (27LL * C3);
+  if (threadIdx.x < 27) s_base[threadIdx.x] = (IDX)a.nbr[(size_t)blk * 27 + threadIdx.x] * (IDX)(27 * C3);
   __syncthreads();
   const int lx = threadIdx.x % B, ly = threadIdx.x / B;
   const int mo = a.maskoff[blk];
@@ -60,7 +68,7 @@ __global__ void __launch_bounds__(B * B) k_collide(CollideArgs a) {
         const int nx = lx - dcx(i), ny = ly - dcy(i), nz = lz - dcz(i);
         const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
         const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
-        d[i] = f[s_base[bd] + (26 - i) * C3 + nc];
+        d[i] = f[s_base[bd] + (IDX)((26 - i) * C3 + nc)];
       }
     }
     cumulant_collide(d, rates);
@@ -75,7 +83,7 @@ __global__ void __launch_bounds__(B * B) k_collide(CollideArgs a) {
         const int nx = lx + dcx(i), ny = ly + dcy(i), nz = lz + dcz(i);
         const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
         const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
-        f[s_base[bd] + i * C3 + nc] = d[i];
+        f[s_base[bd] + (IDX)(i * C3 + nc)] = d[i];
       }
     }
   }
@@ -305,15 +313,22 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 
 const char* cuda_error_string() { return g_err; }
 
+template <int B, typename IDX>
+void collide_on(const CollideArgs& a, int odd, cudaStream_t s) {
+  if (odd) k_collide<B, true, IDX><<<a.n_active, B * B, 0, s>>>(a);
+  else k_collide<B, false, IDX><<<a.n_active, B * B, 0, s>>>(a);
+}
+
 int launch_collide(const CollideArgs& a, int B, int odd, void* stream) {
   if (a.n_active == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  const bool small = a.f_elems < (1LL << 31);
   if (B == 16) {
-    if (odd) k_collide<16, true><<<a.n_active, 256, 0, s>>>(a);
-    else k_collide<16, false><<<a.n_active, 256, 0, s>>>(a);
+    if (small) collide_on<16, int>(a, odd, s);
+    else collide_on<16, long long>(a, odd, s);
   } else if (B == 8) {
-    if (odd) k_collide<8, true><<<a.n_active, 64, 0, s>>>(a);
-    else k_collide<8, false><<<a.n_active, 64, 0, s>>>(a);
+    if (small) collide_on<8, int>(a, odd, s);
+    else collide_on<8, long long>(a, odd, s);
   } else {
     return LBM_EINVAL;
   }

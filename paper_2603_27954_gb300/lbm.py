@@ -237,9 +237,9 @@ def lbm_set_timing(h, on):
 
 
 def lbm_get_timing(h):
-    ms = np.zeros(4)
-    la = np.zeros(4, np.int64)
-    un = np.zeros(4, np.int64)
+    ms = np.zeros(6)
+    la = np.zeros(6, np.int64)
+    un = np.zeros(6, np.int64)
     _ck(_lib.lbm_get_timing(h, _dp(ms), la.ctypes.data_as(C.POINTER(C.c_longlong)),
                             un.ctypes.data_as(C.POINTER(C.c_longlong))), "lbm_get_timing")
     return ms, la, un
