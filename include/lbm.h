@@ -155,6 +155,24 @@ int lbm_get_velocity(lbm_domain* d, int level, double* rho, double* u, size_t n_
    (level-l cells weigh 8^-l).  Synchronises. */
 int lbm_mass(lbm_domain* d, double* mass, double mom[3]);
 
+/* lbm_mass without any caller-provided scratch.  (The paper has no
+   counterpart; this is a service of the library.)  Same result and contract
+   as lbm_mass, but the per-block partial sums go to a fixed scratch array
+   inside the library image instead of the domain's bound buffer, and the
+   call performs no device allocation of any kind.  It is for callers that
+   may not allocate device memory at the point of the call - code running
+   under an allocator or memory pool that forbids growth, or inside a stream
+   capture where cudaMalloc is illegal - and for callers that want the check
+   without touching the domain's own scratch.
+   Limits and rules: every level may hold at most 32768 active blocks
+   (LBM_EINVAL otherwise); the scratch (about 1.3 MB per GPU that loads the
+   library) is held until the process exits; the first call on each device
+   looks up the scratch address with that device current and should come
+   before any stream capture; all calls share the one scratch array, so calls
+   whose device work overlaps race and must be serialised by the caller.
+   Synchronises the domain's stream. */
+int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]);
+
 /* Real box [lo, hi) of a level in level-l cells, and cell counts. */
 int lbm_level_info(const lbm_domain* d, int level, int lo[3], int hi[3], long long* n_fluid,
                    long long* n_links, long long* n_active_blocks);

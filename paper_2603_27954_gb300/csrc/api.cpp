@@ -608,6 +608,37 @@ int lbm_mass(lbm_domain* d, double* mass, double mom[3]) {
   return mass_device(d, mass, mom, nullptr);
 }
 
+int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  for (const Level& v : d->mesh.lv)
+    if (v.n_active > noalloc_max_blocks())
+      return fail(LBM_EINVAL, "a level has more active blocks than lbm_mass_noalloc supports (" +
+                                  std::to_string(noalloc_max_blocks()) + ")");
+  double* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return fail(rc, cuda_error_string());
+  double m = 0, p[3] = {0, 0, 0};
+  for (int l = 0; l < d->mesh.L; ++l) {
+    Level& v = d->mesh.lv[l];
+    if (!v.n_active) continue;
+    rc = launch_mass_noalloc(d->dev<float>(v.off_f), d->dev<int>(v.off_nbr), d->dev<int>(v.off_maskoff),
+                             d->dev<uint8_t>(v.off_masks), v.n_active, v.B, level_parity(d, l), scratch, d->stream);
+    if (rc) return fail(rc, cuda_error_string());
+    double tot[5];
+    CK(cudaMemcpyAsync(tot, scratch + (size_t)noalloc_max_blocks() * 5, sizeof tot, cudaMemcpyDeviceToHost,
+                       d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    const double w = std::ldexp(1.0, -3 * l);
+    m += w * tot[0];
+    for (int a = 0; a < 3; ++a) p[a] += w * tot[1 + a];
+  }
+  if (mass) *mass = m;
+  if (mom)
+    for (int a = 0; a < 3; ++a) mom[a] = p[a];
+  return LBM_OK;
+}
+
 int lbm_level_info(const lbm_domain* d, int level, int lo[3], int hi[3], long long* n_fluid, long long* n_links,
                    long long* n_active_blocks) {
   if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level or geometry not set");

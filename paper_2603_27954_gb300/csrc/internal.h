@@ -161,6 +161,10 @@ int launch_fill(float* f, long long n_blocks, int B, const float dev[27], void* 
 int launch_mass(const float* f, const int* nbr, const int* maskoff, const uint8_t* masks, int n_active,
                 int B, int parity, double* partials, void* stream);
 int mass_partial_count(int n_active);
+int noalloc_max_blocks();
+int noalloc_scratch(double** out);
+int launch_mass_noalloc(const float* f, const int* nbr, const int* maskoff, const uint8_t* masks, int n_active,
+                        int B, int parity, double* scratch, void* stream);
 const char* cuda_error_string();
 
 }  // namespace lbm

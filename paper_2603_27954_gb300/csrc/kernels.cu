@@ -296,6 +296,36 @@ __global__ void __launch_bounds__(B * B) k_mass(const float* __restrict__ f, con
   }
 }
 
+// Scratch for lbm_mass_noalloc: per-block partial sums [mass, jx, jy, jz,
+// bad] of one level, then the 5 totals.  It lives in the library image, so
+// that entry point needs no device memory from its caller; host code must
+// use the address from cudaGetSymbolAddress, never the symbol itself.
+constexpr int kNoAllocMaxBlocks = 32768;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks * 5 + 8];
+
+// fixed-order FP64 sum of n rows of 5 partials into out[0..4]
+__global__ void __launch_bounds__(256) k_sum5(const double* __restrict__ partials, int n, double* __restrict__ out) {
+  double a = 0, b = 0, c = 0, d = 0, e = 0;
+  for (int k = threadIdx.x; k < n; k += 256) {
+    a += partials[5 * k];
+    b += partials[5 * k + 1];
+    c += partials[5 * k + 2];
+    d += partials[5 * k + 3];
+    e += partials[5 * k + 4];
+  }
+  block_sum3<256>(a, b, c);
+  __syncthreads();
+  double z = 0.0;
+  block_sum3<256>(d, e, z);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+    out[2] = c;
+    out[3] = d;
+    out[4] = e;
+  }
+}
+
 thread_local char g_err[256] = "";
 
 int check_launch(const char* what) {
@@ -398,6 +428,40 @@ int launch_mass(const float* f, const int* nbr, const int* maskoff, const uint8_
   else if (B == 8) k_mass<8><<<n_active, 64, 0, s>>>(f, nbr, maskoff, masks, parity, partials);
   else return LBM_EINVAL;
   return check_launch("mass");
+}
+
+int noalloc_max_blocks() { return kNoAllocMaxBlocks; }
+
+// Device address of the static scratch for the current device, looked up once
+// per device with that device current (first call; before any stream capture).
+int noalloc_scratch(double** out) {
+  static double* ptr[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    snprintf(g_err, sizeof g_err, "cudaGetDevice: %s", cudaGetErrorString(e));
+    return LBM_ECUDA;
+  }
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      snprintf(g_err, sizeof g_err, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      return LBM_ECUDA;
+    }
+    ptr[dev] = (double*)p;
+  }
+  *out = ptr[dev];
+  return LBM_OK;
+}
+
+int launch_mass_noalloc(const float* f, const int* nbr, const int* maskoff, const uint8_t* masks, int n_active,
+                        int B, int parity, double* scratch, void* stream) {
+  if (n_active > kNoAllocMaxBlocks) return LBM_EINVAL;
+  int rc = launch_mass(f, nbr, maskoff, masks, n_active, B, parity, scratch, stream);
+  if (rc) return rc;
+  k_sum5<<<1, 256, 0, (cudaStream_t)stream>>>(scratch, n_active, scratch + (size_t)kNoAllocMaxBlocks * 5);
+  return check_launch("sum5");
 }
 
 }  // namespace lbm

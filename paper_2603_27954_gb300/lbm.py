@@ -63,6 +63,7 @@ def _load():
         "lbm_get_populations": ([vp, i, dp, sz], i),
         "lbm_get_velocity": ([vp, i, dp, dp, sz], i),
         "lbm_mass": ([vp, dp, dp], i),
+        "lbm_mass_noalloc": ([vp, dp, dp], i),
         "lbm_level_info": ([vp, i, ip, ip, llp, llp, llp], i),
         "lbm_geometry_info": ([vp, dp, dp, ip, dp], i),
         "lbm_get_cell_types": ([vp, i, ubp, sz], i),
@@ -187,6 +188,12 @@ def lbm_get_velocity(h, level):
 def lbm_mass(h):
     m, p = C.c_double(), np.zeros(3)
     _ck(_lib.lbm_mass(h, C.byref(m), _dp(p)), "lbm_mass")
+    return m.value, p
+
+
+def lbm_mass_noalloc(h):
+    m, p = C.c_double(), np.zeros(3)
+    _ck(_lib.lbm_mass_noalloc(h, C.byref(m), _dp(p)), "lbm_mass_noalloc")
     return m.value, p
 
 
