@@ -63,6 +63,13 @@ def profiled_traffic():
     return d
 
 
+def job_rate(units_per_rank, steps, ms_local, world, reduce_max):
+    """Whole-job rate over all ranks: every rank's units over the slowest
+    rank's time (max over ranks), in millions per second; also that time."""
+    ms_max = reduce_max(ms_local)
+    return units_per_rank * world * steps / (ms_max / 1e3) / 1e6, ms_max
+
+
 def workload_desc(L, W, case):
     c = W.CASES[case]
     desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
@@ -228,11 +235,14 @@ def main():
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = updates * world * args.steps / (ms_max / 1e3) / 1e6
+
+    def reduce_max(x):
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    value, ms_max = job_rate(updates, args.steps, ms, world, reduce_max)
 
     # per-kernel timing with CUDA events on the domain's stream (direct launches)
     dom.set_timing(True)
@@ -269,10 +279,7 @@ def main():
         _, _, cd = dom.drag()
     torch.cuda.synchronize()
     h1 = time.perf_counter()
-    tt = torch.tensor([h1 - h0], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_value = updates * world * args.e2e_steps / float(tt.item()) / 1e6
+    e2e_value, _ = job_rate(updates, args.e2e_steps, (h1 - h0) * 1e3, world, reduce_max)
     info0 = L.lbm_level_info(dom.h, 0)
     geo = dom.geometry_info()
 
