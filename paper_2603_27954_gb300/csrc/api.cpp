@@ -133,7 +133,7 @@ int advance(lbm_domain* dm, int l, int parity) {
     Timed t(dm, parity ? KC_COLLIDE_ODD : KC_COLLIDE, v.n_fluid);
     CollideArgs a{f, (long long)v.f_elems(), dm->dev<int>(v.off_nbr), dm->dev<int>(v.off_maskoff),
                   dm->dev<uint8_t>(v.off_masks), v.n_active, (float)v.omega1, (float)dm->d.omega2,
-                  dm->d.galilean};
+                  dm->d.galilean, dm->dev<double>(dm->off_accum) + 7};
     if ((rc = launch_collide(a, v.B, parity, dm->stream))) return rc;
   }
   if (l == 0 && !v.face[parity].empty()) {
@@ -468,7 +468,9 @@ int lbm_bind_memory(lbm_domain* d, void* ptr, size_t bytes) {
   if ((uintptr_t)ptr & 255) return fail(LBM_EINVAL, "bound buffer must be 256-byte aligned");
   free_graphs(d);
   d->base = (char*)ptr;
-  int rc = upload(d);
+  int rc = prepare_kernels();
+  if (rc) return fail(rc, cuda_error_string());
+  rc = upload(d);
   if (rc) return rc;
   double u[3] = {d->d.u_in, 0, 0};
   if ((rc = fill_uniform(d, 1.0, u))) return rc;
@@ -542,6 +544,7 @@ int lbm_drag(lbm_domain* d, double last[3], double mean[3], double* c_d) {
   double acc[8];
   CK(cudaMemcpyAsync(acc, d->base + d->off_accum, sizeof acc, cudaMemcpyDeviceToHost, d->stream));
   CK(cudaStreamSynchronize(d->stream));
+  if (acc[7] != 0.0) return fail(LBM_ETIMEOUT, "a bounded device wait gave up (collide staging)");
   if (last)
     for (int a = 0; a < 3; ++a) last[a] = acc[a];
   if (mean)

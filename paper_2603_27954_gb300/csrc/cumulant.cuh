@@ -20,6 +20,8 @@
 // m* - m_w is formed from small quantities, so nothing cancels.
 #pragma once
 
+#include <math.h>
+
 #ifndef LBM_HD
 #define LBM_HD __host__ __device__ __forceinline__
 #endif
@@ -31,12 +33,22 @@ struct Rates {
   int galilean;
 };
 
-// 1-D map from central moments about u to the three populations.
-LBM_HD void central_to_pop(float m0, float m1, float m2, float u, float& fm, float& f0, float& fp) {
-  float u2 = u * u;
-  f0 = m0 * (1.0f - u2) - 2.0f * u * m1 - m2;
-  fp = 0.5f * ((u2 + u) * m0 + (2.0f * u + 1.0f) * m1 + m2);
-  fm = 0.5f * ((u2 - u) * m0 + (2.0f * u - 1.0f) * m1 + m2);
+// 1-D map from central moments (M0, M1, M2) about u to the three
+// populations f(-1), f(0), f(+1): from the raw moments R1 = M1 + u M0 and
+// R2 = M2 + 2u M1 + u^2 M0, f(+-1) = (R2 +- R1) / 2 and f(0) = M0 - R2.
+// The coefficients depend on u only and are formed once per axis.
+struct AxisMap {
+  float a0, a1, ap, am, bp, bm;
+};
+LBM_HD AxisMap axis_map(float u) {
+  const float u2 = u * u;
+  return AxisMap{1.0f - u2, -2.0f * u, 0.5f * (u2 + u), 0.5f * (u2 - u), u + 0.5f, u - 0.5f};
+}
+LBM_HD void central_to_pop(float m0, float m1, float m2, const AxisMap& A, float& fm, float& f0, float& fp) {
+  const float h = 0.5f * m2;
+  f0 = fmaf(A.a0, m0, fmaf(A.a1, m1, -m2));
+  fp = fmaf(A.ap, m0, fmaf(A.bp, m1, h));
+  fm = fmaf(A.am, m0, fmaf(A.bm, m1, h));
 }
 
 LBM_HD void cumulant_collide(float* d, const Rates& r) {
@@ -134,31 +146,33 @@ LBM_HD void cumulant_collide(float* d, const Rates& r) {
           2.0f * (sxx2 * qyz * qyz + syy2 * qxz * qxz + szz2 * qxy * qxy) + 8.0f * qxy * qxz * qyz;  // 222
 
   // ---- back to populations: z pass, y pass, x pass
+  const AxisMap Mx = axis_map(ux), My = axis_map(uy), Mz = axis_map(uz);
   float t[27];
 #pragma unroll
   for (int ab = 0; ab < 9; ++ab)  // moment index a + 3b, population cz
-    central_to_pop(m[ab], m[ab + 9], m[ab + 18], uz, t[ab], t[ab + 9], t[ab + 18]);
+    central_to_pop(m[ab], m[ab + 9], m[ab + 18], Mz, t[ab], t[ab + 9], t[ab + 18]);
 #pragma unroll
   for (int zc = 0; zc < 3; ++zc)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int o = 9 * zc + a;  // moment a, moment b (stride 3), population cz
       float p0, p1, p2;
-      central_to_pop(t[o], t[o + 3], t[o + 6], uy, p0, p1, p2);
+      central_to_pop(t[o], t[o + 3], t[o + 6], My, p0, p1, p2);
       t[o] = p0;
       t[o + 3] = p1;
       t[o + 6] = p2;
     }
-  const float w_edge[3] = {1.0f / 6.0f, 2.0f / 3.0f, 1.0f / 6.0f};
+  // (rho - 1) w_i for the four distinct rest weights (number of zero components)
+  const float dw[4] = {drho * (1.0f / 216.0f), drho * (1.0f / 54.0f), drho * (2.0f / 27.0f), drho * (8.0f / 27.0f)};
 #pragma unroll
   for (int yz = 0; yz < 9; ++yz) {
     const int o = 3 * yz;  // moment a, population cy, cz
     float p0, p1, p2;
-    central_to_pop(t[o], t[o + 1], t[o + 2], ux, p0, p1, p2);
-    const float wyz = w_edge[yz % 3] * w_edge[yz / 3];
-    d[o] = rho * p0 + drho * (wyz * w_edge[0]);
-    d[o + 1] = rho * p1 + drho * (wyz * w_edge[1]);
-    d[o + 2] = rho * p2 + drho * (wyz * w_edge[2]);
+    central_to_pop(t[o], t[o + 1], t[o + 2], Mx, p0, p1, p2);
+    const int zeros = (yz % 3 == 1) + (yz / 3 == 1);
+    d[o] = fmaf(rho, p0, dw[zeros]);
+    d[o + 1] = fmaf(rho, p1, dw[zeros + 1]);
+    d[o + 2] = fmaf(rho, p2, dw[zeros]);
   }
 }
 

@@ -144,7 +144,9 @@ struct CollideArgs {
   int n_active;
   float omega1, omega2;
   int galilean;
+  double* err;  // set to 1 when a bounded device wait gives up
 };
+int prepare_kernels();
 int launch_collide(const CollideArgs& a, int B, int odd, void* stream);
 int launch_faces(float* f, const FaceEntry* e, int n, const float* feq_in_dev_unused, const float feq[27],
                  void* stream);
