@@ -70,11 +70,40 @@ def job_rate(units_per_rank, steps, ms_local, world, reduce_max):
     return units_per_rank * world * steps / (ms_max / 1e3) / 1e6, ms_max
 
 
-def workload_desc(L, W, case):
+def workload_desc(L, W, case, precision=None):
     c = W.CASES[case]
     desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
-                         re_h=c["re_h"])
+                         re_h=c["re_h"], precision=precision or L.LBM_FP32)
     return desc, L.tree_desc(**c["tree"]), c
+
+
+def fp16_form(L, W, torch, stream, steps, warmup, fp32_value, peak):
+    """The FP16-deviation storage form on the same workload: MLUPS, its
+    collide roofline at 108 B per update, and the speed-up over FP32."""
+    desc, tree, _ = workload_desc(L, W, CASE, L.LBM_FP16_DEV)
+    dom = L.Domain(desc, tree=tree, stream=stream)
+    updates, _ = dom.work_per_step()
+    dom.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dom.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    value = updates * steps / (ms / 1e3) / 1e6
+    dom.set_timing(True)
+    dom.step(20)
+    kms, _, kunits = dom.get_timing()
+    dom.set_timing(False)
+    gbs = (kunits[0] + kunits[1]) * 108 / ((kms[0] + kms[1]) / 1e3) / 1e9
+    _, _, cd = dom.drag()
+    dom.close()
+    return {"value": value, "unit": "MLUPS", "speedup_vs_fp32": value / fp32_value, "ms_per_step": ms / steps,
+            "dtype": "f16 storage of (f - w) * 2^13, f32 collision, f64 reductions",
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "bytes_per_update": 108}, "cd": cd}
 
 
 class Clocks:
@@ -189,6 +218,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--timing-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=50)
     args = ap.parse_args()
@@ -283,6 +313,10 @@ def main():
     info0 = L.lbm_level_info(dom.h, 0)
     geo = dom.geometry_info()
 
+    fp16 = None
+    if not args.no_fp16:
+        fp16 = fp16_form(L, W, torch, stream, args.steps, args.warmup, value, peak)
+
     cpu = None
     cd_err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -295,11 +329,17 @@ def main():
         sdom.step(small_steps)
         _, _, g_cd = sdom.drag()
         sdom.close()
+        d16, _, _ = workload_desc(L, W, SMALL, L.LBM_FP16_DEV)
+        hdom = L.Domain(d16, tree=t2, stream=stream)
+        hdom.step(small_steps)
+        _, _, h_cd = hdom.drag()
+        hdom.close()
         cpu = {"value": o_mlups, "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
                "sample": "%d coarse steps (%.1f s) of the two-level tree case scaled down 4x per axis, "
                          "%d cell updates per step" % (small_steps, o_dt, o_upd)}
         cd_err = {"case": "two-level tree case scaled down 4x, after %d coarse steps" % small_steps,
-                  "cd_gpu": g_cd, "cd_oracle": o_cd, "rel_err": abs(g_cd - o_cd) / abs(o_cd)}
+                  "cd_gpu": g_cd, "cd_oracle": o_cd, "rel_err": abs(g_cd - o_cd) / abs(o_cd),
+                  "fp16_cd_gpu": h_cd, "fp16_rel_err": abs(h_cd - o_cd) / abs(o_cd)}
 
     line = {
         "metric": "D3Q27 cumulant LBM MLUPS & % HBM roofline; C_D rel. error vs FP64 oracle",
@@ -323,6 +363,7 @@ def main():
         "kernels_per_step": kernels,
         "cd": cd,
         "cd_rel_err_vs_oracle": cd_err,
+        "fp16_form": fp16,
         "cpu_baseline": cpu,
         "geometry": {"H_finest_cells": geo["H"], "A_x": geo["A_x"], "segments": geo["n_segments"],
                      "nu_finest": geo["nu_finest"], "fluid_cells_level0": info0["n_fluid"]},

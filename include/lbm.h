@@ -52,7 +52,10 @@ typedef enum {
   LBM_BC_INFLOW = 3    /* y, z: equilibrium at rho = 1 and the inflow velocity (Sec. 2.3: inflow on all non-outlet faces) */
 } lbm_bc;
 
-typedef enum { LBM_FP32 = 1 } lbm_precision;
+/* Population storage.  LBM_FP32: f_i - w_i in FP32.  LBM_FP16_DEV:
+   (f_i - w_i) * 2^13 in IEEE binary16 (the power-of-two scale is per level).
+   Collision arithmetic is FP32 in both; the drag and mass reductions FP64. */
+typedef enum { LBM_FP32 = 1, LBM_FP16_DEV = 2 } lbm_precision;
 
 /* Problem statement (Sec. 2.2-2.3): domain, inflow, Re_H, refinement.
    Coarse level = level 0; every finer level halves the cell size and the

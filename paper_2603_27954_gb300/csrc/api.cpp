@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "half_host.h"
 #include "internal.h"
 
 using namespace lbm;
@@ -127,26 +128,29 @@ struct Timed {
 int advance(lbm_domain* dm, int l, int parity) {
   Mesh& m = dm->mesh;
   Level& v = m.lv[l];
-  float* f = dm->dev<float>(v.off_f);
+  void* f = dm->base + v.off_f;
+  const int half = v.esize == 2;
   int rc;
   {
     Timed t(dm, parity ? KC_COLLIDE_ODD : KC_COLLIDE, v.n_fluid);
     CollideArgs a{f, (long long)v.f_elems(), dm->dev<int>(v.off_nbr), dm->dev<int>(v.off_maskoff),
                   dm->dev<uint8_t>(v.off_masks), v.n_active, (float)v.omega1, (float)dm->d.omega2,
-                  dm->d.galilean, dm->dev<double>(dm->off_accum) + 7};
+                  dm->d.galilean, dm->dev<double>(dm->off_accum) + 7, v.esize == 2, v.scale, 1.0f / v.scale};
     if ((rc = launch_collide(a, v.B, parity, dm->stream))) return rc;
   }
   if (l == 0 && !v.face[parity].empty()) {
     Timed t(dm, KC_FACES, (long long)v.face[parity].size());
-    if ((rc = launch_faces(f, dm->dev<FaceEntry>(v.off_face[parity]), (int)v.face[parity].size(), nullptr,
-                           dm->feq_in, dm->stream)))
+    float feq[27];
+    for (int i = 0; i < 27; ++i) feq[i] = dm->feq_in[i] * v.scale;
+    if ((rc = launch_faces(f, half, dm->dev<FaceEntry>(v.off_face[parity]), (int)v.face[parity].size(), feq,
+                           dm->stream)))
       return rc;
   }
   if (!v.wall[parity].empty()) {
     Timed t(dm, KC_WALLS, (long long)v.wall[parity].size());
     int n = (int)v.wall[parity].size();
-    if ((rc = launch_walls(f, dm->dev<WallEntry>(v.off_wall[parity]), n, dm->dev<double>(dm->off_partials),
-                           dm->stream)))
+    if ((rc = launch_walls(f, half, 1.0f / v.scale, dm->dev<WallEntry>(v.off_wall[parity]), n,
+                           dm->dev<double>(dm->off_partials), dm->stream)))
       return rc;
     if (l == m.L - 1 &&
         (rc = launch_force_reduce(dm->dev<double>(dm->off_partials), walls_partial_count(n),
@@ -155,23 +159,24 @@ int advance(lbm_domain* dm, int l, int parity) {
   }
   if (l + 1 < m.L) {
     Level& F = m.lv[l + 1];
-    float* ff = dm->dev<float>(F.off_f);
+    void* ff = dm->base + F.off_f;
     float* saved = dm->dev<float>(v.off_saved);
+    const float ratio = F.scale / v.scale;
     if ((rc = advance(dm, l + 1, 0))) return rc;
     {
       Timed t(dm, KC_IFACE, (long long)v.expl.size());
-      if ((rc = launch_explode(ff, f, dm->dev<ExplodeEntry>(v.off_expl), (int)v.expl.size(),
+      if ((rc = launch_explode(ff, f, half, ratio, dm->dev<ExplodeEntry>(v.off_expl), (int)v.expl.size(),
                                dm->dev<SaveEntry>(v.off_save), (int)v.save.size(), saved, parity, dm->stream)))
         return rc;
     }
     if ((rc = advance(dm, l + 1, 1))) return rc;
     {
       Timed t(dm, KC_IFACE, (long long)v.infl.size() + (long long)v.coal.size());
-      if ((rc = launch_inflow(ff, f, dm->dev<InflowEntry>(v.off_infl), (int)v.infl.size(), saved, parity,
-                              dm->stream)))
+      if ((rc = launch_inflow(ff, f, half, ratio, dm->dev<InflowEntry>(v.off_infl), (int)v.infl.size(), saved,
+                              parity, dm->stream)))
         return rc;
-      if ((rc = launch_coalesce(f, ff, dm->dev<CoalesceEntry>(v.off_coal), (int)v.coal.size(), saved, parity,
-                                dm->stream)))
+      if ((rc = launch_coalesce(f, ff, half, ratio, dm->dev<CoalesceEntry>(v.off_coal), (int)v.coal.size(), saved,
+                                parity, dm->stream)))
         return rc;
     }
   }
@@ -214,6 +219,10 @@ int build(lbm_domain* d) {
     Level& v = d->mesh.lv[l];
     v.nu = d->nu_f * std::ldexp(1.0, -(L - 1 - l));
     v.omega1 = 1.0 / (3.0 * v.nu + 0.5);
+    // FP16: deviations are at most ~0.1, so 2^13 keeps them far from both the
+    // FP16 overflow (65504) and its subnormal range (below 6.1e-5 / 2^13)
+    v.esize = d->d.precision == LBM_FP16_DEV ? 2 : 4;
+    v.scale = d->d.precision == LBM_FP16_DEV ? 8192.0f : 1.0f;
   }
   // device layout
   size_t off = 0;
@@ -226,7 +235,7 @@ int build(lbm_domain* d) {
   size_t max_blocks = 1;
   for (int l = 0; l < L; ++l) {
     Level& v = d->mesh.lv[l];
-    v.off_f = put(v.f_elems() * sizeof(float));
+    v.off_f = put(v.f_elems() * (size_t)v.esize);
     v.off_nbr = put(v.nbr.size() * sizeof(int));
     v.off_maskoff = put(v.maskoff.size() * sizeof(int));
     v.off_masks = put(v.masks.size());
@@ -279,10 +288,10 @@ int reset_force(lbm_domain* d) {
 }
 
 int fill_uniform(lbm_domain* d, double rho, const double u[3]) {
-  float dev[27];
-  for (int i = 0; i < 27; ++i) dev[i] = (float)(equilibrium(i, rho, u) - rest_weight(i));
   for (Level& v : d->mesh.lv) {
-    int rc = launch_fill(d->dev<float>(v.off_f), v.n_storage, v.B, dev, d->stream);
+    float dev[27];
+    for (int i = 0; i < 27; ++i) dev[i] = (float)((equilibrium(i, rho, u) - rest_weight(i)) * v.scale);
+    int rc = launch_fill(d->base + v.off_f, v.esize == 2, v.n_storage, v.B, dev, d->stream);
     if (rc) return fail(rc, cuda_error_string());
   }
   d->parity0 = 0;
@@ -320,9 +329,9 @@ int mass_device(lbm_domain* d, double* mass, double mom[3], double* bad) {
   for (int l = 0; l < d->mesh.L; ++l) {
     Level& v = d->mesh.lv[l];
     if (!v.n_active) continue;
-    int rc = launch_mass(d->dev<float>(v.off_f), d->dev<int>(v.off_nbr), d->dev<int>(v.off_maskoff),
-                         d->dev<uint8_t>(v.off_masks), v.n_active, v.B, level_parity(d, l),
-                         d->dev<double>(d->off_mpart), d->stream);
+    int rc = launch_mass(d->base + v.off_f, v.esize == 2, 1.0f / v.scale, d->dev<int>(v.off_nbr),
+                         d->dev<int>(v.off_maskoff), d->dev<uint8_t>(v.off_masks), v.n_active, v.B,
+                         level_parity(d, l), d->dev<double>(d->off_mpart), d->stream);
     if (rc) return fail(rc, cuda_error_string());
     part.resize((size_t)v.n_active * 5);
     CK(cudaMemcpyAsync(part.data(), d->base + d->off_mpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
@@ -354,12 +363,33 @@ long long box_cells(const Level& v) {
   return (long long)(v.rhi[0] - v.rlo[0]) * (v.rhi[1] - v.rlo[1]) * (v.rhi[2] - v.rlo[2]);
 }
 
-int download_level(lbm_domain* d, const Level& v, std::vector<float>& host) {
-  host.resize(v.f_elems());
-  CK(cudaMemcpyAsync(host.data(), d->base + v.off_f, host.size() * sizeof(float), cudaMemcpyDeviceToHost,
-                     d->stream));
+int download_level(lbm_domain* d, const Level& v, std::vector<uint8_t>& host) {
+  host.resize(v.f_elems() * (size_t)v.esize);
+  CK(cudaMemcpyAsync(host.data(), d->base + v.off_f, host.size(), cudaMemcpyDeviceToHost, d->stream));
   CK(cudaStreamSynchronize(d->stream));
   return LBM_OK;
+}
+
+// deviation f - w of the stored element k (decoded and unscaled)
+double stored_dev(const Level& v, const std::vector<uint8_t>& host, long long k) {
+  if (v.esize == 2) {
+    uint16_t h;
+    std::memcpy(&h, host.data() + 2 * k, 2);
+    return (double)half_bits_to_float(h) / v.scale;
+  }
+  float x;
+  std::memcpy(&x, host.data() + 4 * k, 4);
+  return x;
+}
+
+void store_dev(const Level& v, std::vector<uint8_t>& host, long long k, double dev) {
+  if (v.esize == 2) {
+    const uint16_t h = float_to_half_bits((float)(dev * v.scale));
+    std::memcpy(host.data() + 2 * k, &h, 2);
+  } else {
+    const float x = (float)dev;
+    std::memcpy(host.data() + 4 * k, &x, 4);
+  }
 }
 
 }  // namespace
@@ -394,7 +424,8 @@ int lbm_create_domain(const lbm_domain_desc* desc, void* cuda_stream, lbm_domain
       return fail(LBM_EINVAL, "y/z faces: periodic, slip or inflow");
   if (!(std::fabs(s.u_in) < 0.3)) return fail(LBM_EINVAL, "inflow speed must be below 0.3");
   if (s.i_u != 0.0) return fail(LBM_EINVAL, "only uniform inflow (i_u = 0) is supported");
-  if (s.precision != LBM_FP32) return fail(LBM_EINVAL, "only FP32 populations are supported");
+  if (s.precision != LBM_FP32 && s.precision != LBM_FP16_DEV)
+    return fail(LBM_EINVAL, "precision must be LBM_FP32 or LBM_FP16_DEV");
   if (!(s.omega2 > 0 && s.omega2 < 2)) return fail(LBM_EINVAL, "omega2 must lie in (0, 2)");
   auto* d = new (std::nothrow) lbm_domain();
   if (!d) return fail(LBM_ENOMEM, "host allocation");
@@ -495,7 +526,7 @@ int lbm_init_field(lbm_domain* d, int level, const double* rho, const double* u,
   if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
   Level& v = d->mesh.lv[level];
   if ((long long)n != box_cells(v)) return fail(LBM_EINVAL, "cell count does not match the level's box");
-  std::vector<float> host;
+  std::vector<uint8_t> host;
   int rc = download_level(d, v, host);
   if (rc) return rc;
   const int par = level_parity(d, level);
@@ -504,13 +535,10 @@ int lbm_init_field(lbm_domain* d, int level, const double* rho, const double* u,
     for (int y = v.rlo[1]; y < v.rhi[1]; ++y)
       for (int x = v.rlo[0]; x < v.rhi[0]; ++x, ++k) {
         if (v.cell_type(x, y, z) != FLUID) continue;
-        for (int i = 0; i < kQ; ++i) {
-          long long s = incoming_slot(v, par, x, y, z, i);
-          host[s] = (float)(equilibrium(i, rho[k], u + 3 * k) - rest_weight(i));
-        }
+        for (int i = 0; i < kQ; ++i)
+          store_dev(v, host, incoming_slot(v, par, x, y, z, i), equilibrium(i, rho[k], u + 3 * k) - rest_weight(i));
       }
-  CK(cudaMemcpyAsync(d->base + v.off_f, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice,
-                     d->stream));
+  CK(cudaMemcpyAsync(d->base + v.off_f, host.data(), host.size(), cudaMemcpyHostToDevice, d->stream));
   CK(cudaStreamSynchronize(d->stream));
   return LBM_OK;
 }
@@ -568,7 +596,7 @@ int lbm_get_populations(lbm_domain* d, int level, double* f, size_t n) {
   if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
   Level& v = d->mesh.lv[level];
   if ((long long)n != box_cells(v)) return fail(LBM_EINVAL, "cell count does not match the level's box");
-  std::vector<float> host;
+  std::vector<uint8_t> host;
   int rc = download_level(d, v, host);
   if (rc) return rc;
   const int par = level_parity(d, level);
@@ -578,7 +606,7 @@ int lbm_get_populations(lbm_domain* d, int level, double* f, size_t n) {
       for (int x = v.rlo[0]; x < v.rhi[0]; ++x, ++k) {
         bool fl = v.cell_type(x, y, z) == FLUID;
         for (int i = 0; i < kQ; ++i)
-          f[27 * k + i] = fl ? rest_weight(i) + (double)host[incoming_slot(v, par, x, y, z, i)]
+          f[27 * k + i] = fl ? rest_weight(i) + stored_dev(v, host, incoming_slot(v, par, x, y, z, i))
                              : std::numeric_limits<double>::quiet_NaN();
       }
   return LBM_OK;
@@ -625,8 +653,9 @@ int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]) {
   for (int l = 0; l < d->mesh.L; ++l) {
     Level& v = d->mesh.lv[l];
     if (!v.n_active) continue;
-    rc = launch_mass_noalloc(d->dev<float>(v.off_f), d->dev<int>(v.off_nbr), d->dev<int>(v.off_maskoff),
-                             d->dev<uint8_t>(v.off_masks), v.n_active, v.B, level_parity(d, l), scratch, d->stream);
+    rc = launch_mass_noalloc(d->base + v.off_f, v.esize == 2, 1.0f / v.scale, d->dev<int>(v.off_nbr),
+                             d->dev<int>(v.off_maskoff), d->dev<uint8_t>(v.off_masks), v.n_active, v.B,
+                             level_parity(d, l), scratch, d->stream);
     if (rc) return fail(rc, cuda_error_string());
     double tot[5];
     CK(cudaMemcpyAsync(tot, scratch + (size_t)noalloc_max_blocks() * 5, sizeof tot, cudaMemcpyDeviceToHost,
@@ -761,14 +790,14 @@ int lbm_save(lbm_domain* d, const char* path) {
   long long hdr[4] = {(long long)d->need, d->parity0, d->steps, d->mesh.L};
   std::fwrite(magic, 1, 8, fp);
   std::fwrite(hdr, sizeof hdr, 1, fp);
-  std::vector<float> host;
+  std::vector<uint8_t> host;
   for (const Level& v : d->mesh.lv) {
     int rc = download_level(d, v, host);
     if (rc) {
       std::fclose(fp);
       return rc;
     }
-    std::fwrite(host.data(), sizeof(float), host.size(), fp);
+    std::fwrite(host.data(), 1, host.size(), fp);
   }
   double acc[8];
   cudaError_t e = cudaMemcpyAsync(acc, d->base + d->off_accum, sizeof acc, cudaMemcpyDeviceToHost, d->stream);
@@ -795,15 +824,14 @@ int lbm_load(lbm_domain* d, const char* path) {
     std::fclose(fp);
     return fail(LBM_EINVAL, "state file does not match this domain");
   }
-  std::vector<float> host;
+  std::vector<uint8_t> host;
   for (const Level& v : d->mesh.lv) {
-    host.resize(v.f_elems());
-    if (std::fread(host.data(), sizeof(float), host.size(), fp) != host.size()) {
+    host.resize(v.f_elems() * (size_t)v.esize);
+    if (std::fread(host.data(), 1, host.size(), fp) != host.size()) {
       std::fclose(fp);
       return fail(LBM_EINVAL, "truncated state file");
     }
-    cudaError_t e = cudaMemcpyAsync(d->base + v.off_f, host.data(), host.size() * sizeof(float),
-                                    cudaMemcpyHostToDevice, d->stream);
+    cudaError_t e = cudaMemcpyAsync(d->base + v.off_f, host.data(), host.size(), cudaMemcpyHostToDevice, d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) {
       std::fclose(fp);

@@ -51,7 +51,12 @@ LBM_HD void central_to_pop(float m0, float m1, float m2, const AxisMap& A, float
   fm = fmaf(A.am, m0, fmaf(A.bm, m1, h));
 }
 
-LBM_HD void cumulant_collide(float* d, const Rates& r) {
+// d holds the 27 deviations multiplied by a storage scale s_in on entry and
+// receives the post-collision deviations multiplied by s_out (both 1 for FP32
+// storage; the FP16 form folds its power-of-two scale into the moment sums
+// and the final multiply-add instead of scaling every population).
+template <bool SCALED>
+LBM_HD void cumulant_collide_s(float* d, const Rates& r, float inv_s_in, float s_out) {
   // ---- raw moments of the deviations: three passes (x, then y, then z)
   float x0[9], x1[9], x2[9];
 #pragma unroll
@@ -72,16 +77,17 @@ LBM_HD void cumulant_collide(float* d, const Rates& r) {
     y11[z] = x1[o + 2] - x1[o];
     y20[z] = x2[o] + x2[o + 1] + x2[o + 2];
   }
-  const float drho = y00[0] + y00[1] + y00[2];
-  const float jz = y00[2] - y00[0];
-  const float szz = y00[2] + y00[0];
-  const float jy = y01[0] + y01[1] + y01[2];
-  const float syz = y01[2] - y01[0];
-  const float syy = y02[0] + y02[1] + y02[2];
-  const float jx = y10[0] + y10[1] + y10[2];
-  const float sxz = y10[2] - y10[0];
-  const float sxy = y11[0] + y11[1] + y11[2];
-  const float sxx = y20[0] + y20[1] + y20[2];
+  const float sc = SCALED ? inv_s_in : 1.0f;
+  const float drho = (y00[0] + y00[1] + y00[2]) * sc;
+  const float jz = (y00[2] - y00[0]) * sc;
+  const float szz = (y00[2] + y00[0]) * sc;
+  const float jy = (y01[0] + y01[1] + y01[2]) * sc;
+  const float syz = (y01[2] - y01[0]) * sc;
+  const float syy = (y02[0] + y02[1] + y02[2]) * sc;
+  const float jx = (y10[0] + y10[1] + y10[2]) * sc;
+  const float sxz = (y10[2] - y10[0]) * sc;
+  const float sxy = (y11[0] + y11[1] + y11[2]) * sc;
+  const float sxx = (y20[0] + y20[1] + y20[2]) * sc;
 
   const float rho = 1.0f + drho;
   const float ir = 1.0f / rho;
@@ -163,17 +169,21 @@ LBM_HD void cumulant_collide(float* d, const Rates& r) {
       t[o + 6] = p2;
     }
   // (rho - 1) w_i for the four distinct rest weights (number of zero components)
-  const float dw[4] = {drho * (1.0f / 216.0f), drho * (1.0f / 54.0f), drho * (2.0f / 27.0f), drho * (8.0f / 27.0f)};
+  const float so = SCALED ? s_out : 1.0f;
+  const float rs = rho * so, ds = drho * so;
+  const float dw[4] = {ds * (1.0f / 216.0f), ds * (1.0f / 54.0f), ds * (2.0f / 27.0f), ds * (8.0f / 27.0f)};
 #pragma unroll
   for (int yz = 0; yz < 9; ++yz) {
     const int o = 3 * yz;  // moment a, population cy, cz
     float p0, p1, p2;
     central_to_pop(t[o], t[o + 1], t[o + 2], Mx, p0, p1, p2);
     const int zeros = (yz % 3 == 1) + (yz / 3 == 1);
-    d[o] = fmaf(rho, p0, dw[zeros]);
-    d[o + 1] = fmaf(rho, p1, dw[zeros + 1]);
-    d[o + 2] = fmaf(rho, p2, dw[zeros]);
+    d[o] = fmaf(rs, p0, dw[zeros]);
+    d[o + 1] = fmaf(rs, p1, dw[zeros + 1]);
+    d[o + 2] = fmaf(rs, p2, dw[zeros]);
   }
 }
+
+LBM_HD void cumulant_collide(float* d, const Rates& r) { cumulant_collide_s<false>(d, r, 1.0f, 1.0f); }
 
 }  // namespace lbm

@@ -96,6 +96,8 @@ struct Level {
   std::vector<uint8_t> masks;                    // collide flags, B^3 per masked block
   long long n_fluid = 0;
   double nu = 0, omega1 = 1;
+  int esize = 4;        // bytes per stored population: 4 (FP32) or 2 (FP16)
+  float scale = 1.0f;   // stored value = (f - w) * scale
   std::vector<Link> links;
   std::vector<WallEntry> wall[2];
   std::vector<FaceEntry> face[2];
@@ -136,37 +138,38 @@ void refinement_boxes(const Tree& t, int levels, int block, double margin, int b
 
 // ---------------------------------------------------------------- kernels (kernels.cu)
 struct CollideArgs {
-  float* f;
-  long long f_elems;  // floats in the level's array
+  void* f;            // level populations: float, or __half when half != 0
+  long long f_elems;  // elements in the level's array
   const int* nbr;
   const int* maskoff;
   const uint8_t* masks;
   int n_active;
   float omega1, omega2;
   int galilean;
-  double* err;  // set to 1 when a bounded device wait gives up
+  double* err;        // set to 1 when a bounded device wait gives up
+  int half;           // FP16 storage of scaled deviations
+  float scale, inv_scale;
 };
 int prepare_kernels();
 int launch_collide(const CollideArgs& a, int B, int odd, void* stream);
-int launch_faces(float* f, const FaceEntry* e, int n, const float* feq_in_dev_unused, const float feq[27],
-                 void* stream);
-int launch_walls(float* f, const WallEntry* e, int n, double* partials, void* stream);
+int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], void* stream);
+int launch_walls(void* f, int half, float inv_scale, const WallEntry* e, int n, double* partials, void* stream);
 int walls_partial_count(int n);
 int launch_force_reduce(const double* partials, int nparts, double* accum, void* stream);
-int launch_explode(float* fine, const float* coarse, const ExplodeEntry* e, int ne, const SaveEntry* s,
-                   int ns, float* saved, int parity, void* stream);
-int launch_inflow(float* fine, const float* coarse, const InflowEntry* e, int n, const float* saved,
-                  int parity, void* stream);
-int launch_coalesce(float* coarse, const float* fine, const CoalesceEntry* e, int n, const float* saved,
-                    int parity, void* stream);
-int launch_fill(float* f, long long n_blocks, int B, const float dev[27], void* stream);
-int launch_mass(const float* f, const int* nbr, const int* maskoff, const uint8_t* masks, int n_active,
-                int B, int parity, double* partials, void* stream);
+int launch_explode(void* fine, const void* coarse, int half, float ratio, const ExplodeEntry* e, int ne,
+                   const SaveEntry* s, int ns, float* saved, int parity, void* stream);
+int launch_inflow(void* fine, const void* coarse, int half, float ratio, const InflowEntry* e, int n,
+                  const float* saved, int parity, void* stream);
+int launch_coalesce(void* coarse, const void* fine, int half, float ratio, const CoalesceEntry* e, int n,
+                    const float* saved, int parity, void* stream);
+int launch_fill(void* f, int half, long long n_blocks, int B, const float dev[27], void* stream);
+int launch_mass(const void* f, int half, float inv_scale, const int* nbr, const int* maskoff, const uint8_t* masks,
+                int n_active, int B, int parity, double* partials, void* stream);
 int mass_partial_count(int n_active);
 int noalloc_max_blocks();
 int noalloc_scratch(double** out);
-int launch_mass_noalloc(const float* f, const int* nbr, const int* maskoff, const uint8_t* masks, int n_active,
-                        int B, int parity, double* scratch, void* stream);
+int launch_mass_noalloc(const void* f, int half, float inv_scale, const int* nbr, const int* maskoff,
+                        const uint8_t* masks, int n_active, int B, int parity, double* scratch, void* stream);
 const char* cuda_error_string();
 
 }  // namespace lbm

@@ -12,11 +12,13 @@
 //
 // The step is a bandwidth-bound stencil: every population is read once and
 // written once per cell update (2 x 27 x 4 bytes in FP32); no tensor cores.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
 #include <cstdint>
 #include <cstdio>
+#include <type_traits>
 
 #include "cumulant.cuh"
 #include "internal.h"
@@ -34,6 +36,23 @@ __device__ __forceinline__ int block_digit(int c) {
   return c < 0 ? 0 : (c >= B ? 2 : 1);
 }
 
+// Population storage: FP32 deviations f - w, or FP16 deviations times a
+// per-level power-of-two scale.  ld/st move the stored (scaled) value.
+template <typename S>
+struct Store;
+template <>
+struct Store<float> {
+  static constexpr bool scaled = false;
+  static __device__ __forceinline__ float ld(const float* p, long long i) { return p[i]; }
+  static __device__ __forceinline__ void st(float* p, long long i, float v) { p[i] = v; }
+};
+template <>
+struct Store<__half> {
+  static constexpr bool scaled = true;
+  static __device__ __forceinline__ float ld(const __half* p, long long i) { return __half2float(p[i]); }
+  static __device__ __forceinline__ void st(__half* p, long long i, float v) { p[i] = __float2half_rn(v); }
+};
+
 #ifndef LBM_EVEN_MINB
 #define LBM_EVEN_MINB 4
 #endif
@@ -41,8 +60,8 @@ __device__ __forceinline__ int block_digit(int c) {
 #define LBM_ODD_MINB 2
 #endif
 
-// IDX: element-offset type, 32-bit when the level's array has < 2^31 floats
-template <int B, bool ODD, typename IDX>
+// IDX: element-offset type, 32-bit when the level's array has < 2^31 elements
+template <int B, bool ODD, typename IDX, typename S>
 __global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_collide(CollideArgs a) {
   constexpr int C3 = B * B * B;
   __shared__ IDX s_base[27];
@@ -53,15 +72,15 @@ __global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_c
   const int mo = a.maskoff[blk];
   const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
   const Rates rates{a.omega1, a.omega2, a.galilean};
-  float* __restrict__ f = a.f;
+  S* __restrict__ f = reinterpret_cast<S*>(a.f);
   for (int lz = 0; lz < B; ++lz) {
     const int cell = (lz * B + ly) * B + lx;
     if (mask && !mask[cell]) continue;
     float d[27];
     if (!ODD) {
-      const float* p = f + s_base[13] + cell;
+      const S* p = f + s_base[13] + cell;
 #pragma unroll
-      for (int i = 0; i < 27; ++i) d[i] = p[i * C3];
+      for (int i = 0; i < 27; ++i) d[i] = Store<S>::ld(p, i * C3);
     } else {
 #pragma unroll
       for (int i = 0; i < 27; ++i) {
@@ -69,14 +88,14 @@ __global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_c
         const int nx = lx - dcx(i), ny = ly - dcy(i), nz = lz - dcz(i);
         const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
         const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
-        d[i] = f[s_base[bd] + (IDX)((26 - i) * C3 + nc)];
+        d[i] = Store<S>::ld(f, s_base[bd] + (IDX)((26 - i) * C3 + nc));
       }
     }
-    cumulant_collide(d, rates);
+    cumulant_collide_s<Store<S>::scaled>(d, rates, a.inv_scale, a.scale);
     if (!ODD) {
-      float* p = f + s_base[13] + cell;
+      S* p = f + s_base[13] + cell;
 #pragma unroll
-      for (int i = 0; i < 27; ++i) p[(26 - i) * C3] = d[i];
+      for (int i = 0; i < 27; ++i) Store<S>::st(p, (26 - i) * C3, d[i]);
     } else {
 #pragma unroll
       for (int i = 0; i < 27; ++i) {
@@ -84,7 +103,7 @@ __global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_c
         const int nx = lx + dcx(i), ny = ly + dcy(i), nz = lz + dcz(i);
         const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
         const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
-        f[s_base[bd] + (IDX)(i * C3 + nc)] = d[i];
+        Store<S>::st(f, s_base[bd] + (IDX)(i * C3 + nc), d[i]);
       }
     }
   }
@@ -236,7 +255,7 @@ __global__ void __launch_bounds__(256, LBM_STAGED_MINB) k_collide_odd_staged(Col
   const int mo = a.maskoff[blk];
   const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
   const Rates rates{a.omega1, a.omega2, a.galilean};
-  float* __restrict__ f = a.f;
+  float* __restrict__ f = reinterpret_cast<float*>(a.f);
   // this thread's halo copies (threads 32..255 share 300 items)
   HaloItem items[2];
   int nitems = 0;
@@ -331,7 +350,7 @@ __global__ void __launch_bounds__(256, 2) k_collide_even_tma(CollideArgs a) {
   const int blk = blockIdx.x;
   const int t = threadIdx.x;
   const IDX own = (IDX)a.nbr[(size_t)blk * 27 + 13] * (IDX)(27 * C3);
-  float* __restrict__ fb = a.f + own;
+  float* __restrict__ fb = reinterpret_cast<float*>(a.f) + own;
   if (t == 0) {
     for (int k = 0; k < NS; ++k) mbar_init(&bar[k], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -401,7 +420,7 @@ __global__ void __launch_bounds__(256, 2) k_collide_even_tma(CollideArgs a) {
 // memory instruction with a constant offset (plane and dz).  The two z-face
 // slabs, where 9 directions reach into the z neighbours, take the general
 // address path (the branch is uniform across the CTA).
-template <int B, typename IDX>
+template <int B, typename IDX, typename S>
 __global__ void __launch_bounds__(B * B, LBM_ODD_MINB) k_collide_odd_cols(CollideArgs a) {
   constexpr int C3 = B * B * B, S2 = B * B;
   __shared__ IDX s_base[27];
@@ -410,8 +429,8 @@ __global__ void __launch_bounds__(B * B, LBM_ODD_MINB) k_collide_odd_cols(Collid
   if (t < 27) s_base[t] = (IDX)a.nbr[(size_t)blk * 27 + t] * (IDX)(27 * C3);
   __syncthreads();
   const int lx = t % B, ly = t / B;
-  float* __restrict__ f = a.f;
-  float* col[9];
+  S* __restrict__ f = reinterpret_cast<S*>(a.f);
+  S* col[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int nx = lx + (k % 3 - 1), ny = ly + (k / 3 - 1);
@@ -429,28 +448,28 @@ __global__ void __launch_bounds__(B * B, LBM_ODD_MINB) k_collide_odd_cols(Collid
       if (!face) {
 #pragma unroll
         for (int i = 0; i < 27; ++i)  // pull f_i from (x - c_i, ibar)
-          d[i] = col[(1 - dcx(i)) + 3 * (1 - dcy(i))][(26 - i) * C3 - dcz(i) * S2];
+          d[i] = Store<S>::ld(col[(1 - dcx(i)) + 3 * (1 - dcy(i))], (26 - i) * C3 - dcz(i) * S2);
       } else {
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
           const int nx = lx - dcx(i), ny = ly - dcy(i), nz = lz - dcz(i);
           const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
           const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
-          d[i] = f[s_base[bd] + (IDX)((26 - i) * C3 + nc)];
+          d[i] = Store<S>::ld(f, s_base[bd] + (IDX)((26 - i) * C3 + nc));
         }
       }
-      cumulant_collide(d, rates);
+      cumulant_collide_s<Store<S>::scaled>(d, rates, a.inv_scale, a.scale);
       if (!face) {
 #pragma unroll
         for (int i = 0; i < 27; ++i)  // push f*_i to (x + c_i, i)
-          col[(1 + dcx(i)) + 3 * (1 + dcy(i))][i * C3 + dcz(i) * S2] = d[i];
+          Store<S>::st(col[(1 + dcx(i)) + 3 * (1 + dcy(i))], i * C3 + dcz(i) * S2, d[i]);
       } else {
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
           const int nx = lx + dcx(i), ny = ly + dcy(i), nz = lz + dcz(i);
           const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
           const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
-          f[s_base[bd] + (IDX)(i * C3 + nc)] = d[i];
+          Store<S>::st(f, s_base[bd] + (IDX)(i * C3 + nc), d[i]);
         }
       }
     }
@@ -463,11 +482,13 @@ struct Feq27 {
   float v[27];
 };
 
-__global__ void k_faces(float* __restrict__ f, const FaceEntry* __restrict__ e, int n, Feq27 feq) {
+template <typename S>
+__global__ void k_faces(S* __restrict__ f, const FaceEntry* __restrict__ e, int n, Feq27 feq) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const FaceEntry x = e[t];
-  f[x.dst] = x.src < 0 ? feq.v[x.dir] : f[x.src];
+  if (x.src < 0) Store<S>::st(f, x.dst, feq.v[x.dir]);
+  else f[x.dst] = f[x.src];
 }
 
 constexpr int kWallThreads = 256;
@@ -502,29 +523,32 @@ __device__ void block_sum3(double& a, double& b, double& c) {
   }
 }
 
-__global__ void __launch_bounds__(kWallThreads) k_walls(float* __restrict__ f, const WallEntry* __restrict__ e,
-                                                        int n, double* __restrict__ partials) {
+template <typename S>
+__global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const WallEntry* __restrict__ e, int n,
+                                                        float inv_scale, double* __restrict__ partials) {
   const int t = blockIdx.x * kWallThreads + threadIdx.x;
   double Fx = 0.0, Fy = 0.0, Fz = 0.0;
   if (t < n) {
     const WallEntry w = e[t];
-    const float fa = f[w.a];  // f*_i(x_f), toward the wall (deviation)
+    const float fa = Store<S>::ld(f, w.a);  // f*_i(x_f), toward the wall (stored deviation)
     const float q = w.q;
     float out;
     if (w.b < 0) {
       out = fa;  // second fluid node missing: simple bounce-back
     } else if (q < 0.5f) {
-      out = 2.0f * q * fa + (1.0f - 2.0f * q) * f[w.b];
+      out = 2.0f * q * fa + (1.0f - 2.0f * q) * Store<S>::ld(f, w.b);
     } else {
-      const float fc = f[w.c];
+      const float fc = Store<S>::ld(f, w.c);
       out = fa / (2.0f * q) + (2.0f * q - 1.0f) / (2.0f * q) * fc;
     }
-    f[w.dst] = out;
+    Store<S>::st(f, w.dst, out);
     // momentum exchange, resting wall: c_i (f*_i + f_ibar), full populations
     const int i = w.dir;
     const double wi = (dcx(i) ? 1.0 / 6.0 : 2.0 / 3.0) * (dcy(i) ? 1.0 / 6.0 : 2.0 / 3.0) *
                       (dcz(i) ? 1.0 / 6.0 : 2.0 / 3.0);
-    const double s = 2.0 * wi + (double)fa + (double)out;
+    double sum = (double)fa + (double)out;
+    if (Store<S>::scaled) sum *= (double)inv_scale;
+    const double s = 2.0 * wi + sum;
     Fx = dcx(i) * s;
     Fy = dcy(i) * s;
     Fz = dcz(i) * s;
@@ -558,52 +582,60 @@ __global__ void __launch_bounds__(256) k_force(const double* __restrict__ partia
   }
 }
 
-__global__ void k_explode(float* __restrict__ fine, const float* __restrict__ coarse,
-                          const ExplodeEntry* __restrict__ e, int ne, const SaveEntry* __restrict__ s, int ns,
-                          float* __restrict__ saved, int parity) {
+// Interface kernels.  ratio = s_fine / s_coarse maps stored coarse values to
+// the fine scale (1 for FP32); saved values are fine-scaled floats.
+template <typename S>
+__global__ void k_explode(S* __restrict__ fine, const S* __restrict__ coarse, const ExplodeEntry* __restrict__ e,
+                          int ne, const SaveEntry* __restrict__ s, int ns, float* __restrict__ saved, int parity,
+                          float ratio) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < ne) {
     const ExplodeEntry x = e[t];
-    fine[x.dst] = coarse[parity ? x.src[1] : x.src[0]];
+    Store<S>::st(fine, x.dst, Store<S>::ld(coarse, parity ? x.src[1] : x.src[0]) * ratio);
   }
-  if (t < ns) saved[t] = fine[s[t].src];
+  if (t < ns) saved[t] = Store<S>::ld(fine, s[t].src);
 }
 
-__global__ void k_inflow(float* __restrict__ fine, const float* __restrict__ coarse,
-                         const InflowEntry* __restrict__ e, int n, const float* __restrict__ saved, int parity) {
+template <typename S>
+__global__ void k_inflow(S* __restrict__ fine, const S* __restrict__ coarse, const InflowEntry* __restrict__ e, int n,
+                         const float* __restrict__ saved, int parity, float ratio) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const InflowEntry x = e[t];
-  fine[x.dst] = x.r >= 0 ? saved[x.r] : coarse[parity ? x.csrc[1] : x.csrc[0]];
+  Store<S>::st(fine, x.dst, x.r >= 0 ? saved[x.r] : Store<S>::ld(coarse, parity ? x.csrc[1] : x.csrc[0]) * ratio);
 }
 
-__global__ void k_coalesce(float* __restrict__ coarse, const float* __restrict__ fine,
-                           const CoalesceEntry* __restrict__ e, int n, const float* __restrict__ saved, int parity) {
+template <typename S>
+__global__ void k_coalesce(S* __restrict__ coarse, const S* __restrict__ fine, const CoalesceEntry* __restrict__ e,
+                           int n, const float* __restrict__ saved, int parity, float ratio) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const CoalesceEntry& x = e[t];
   const long long dst = parity ? x.dst[1] : x.dst[0];
-  float v = x.ncoarse ? (float)x.ncoarse * coarse[dst] : 0.0f;
+  float vf = 0.0f;
   for (int k = 0; k < x.nfine; ++k) {
     const long long s = x.fsrc[k];
-    v += s >= 0 ? fine[s] : saved[-s - 1];
+    vf += s >= 0 ? Store<S>::ld(fine, s) : saved[-s - 1];
   }
-  coarse[dst] = v * 0.125f;
+  float v = vf / ratio;
+  if (x.ncoarse) v += (float)x.ncoarse * Store<S>::ld(coarse, dst);
+  Store<S>::st(coarse, dst, v * 0.125f);
 }
 
-__global__ void k_fill(float* __restrict__ f, long long n, int c3, Feq27 dev) {
+template <typename S>
+__global__ void k_fill(S* __restrict__ f, long long n, int c3, Feq27 dev) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int i = (int)((t / c3) % 27);
-  f[t] = dev.v[i];
+  Store<S>::st(f, t, dev.v[i]);
 }
 
 // FP64 mass and momentum of the incoming populations of one level; per CTA
 // partials [mass, jx, jy, jz, bad cells]
-template <int B>
-__global__ void __launch_bounds__(B * B) k_mass(const float* __restrict__ f, const int* __restrict__ nbr,
+template <int B, typename S>
+__global__ void __launch_bounds__(B * B) k_mass(const S* __restrict__ f, const int* __restrict__ nbr,
                                                 const int* __restrict__ maskoff, const uint8_t* __restrict__ masks,
-                                                int parity, double* __restrict__ partials) {
+                                                int parity, float inv_scale, double* __restrict__ partials) {
   constexpr int C3 = B * B * B;
   __shared__ long long s_base[27];
   __shared__ double s_bad[B * B / 32];
@@ -622,13 +654,14 @@ __global__ void __launch_bounds__(B * B) k_mass(const float* __restrict__ f, con
     for (int i = 0; i < 27; ++i) {
       float v;
       if (!parity) {
-        v = f[s_base[13] + i * C3 + cell];
+        v = Store<S>::ld(f, s_base[13] + i * C3 + cell);
       } else {
         const int nx = lx - dcx(i), ny = ly - dcy(i), nz = lz - dcz(i);
         const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
         const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
-        v = f[s_base[bd] + (26 - i) * C3 + nc];
+        v = Store<S>::ld(f, s_base[bd] + (26 - i) * C3 + nc);
       }
+      if (Store<S>::scaled) v *= inv_scale;
       const double w = (dcx(i) ? 1.0 / 6.0 : 2.0 / 3.0) * (dcy(i) ? 1.0 / 6.0 : 2.0 / 3.0) *
                        (dcz(i) ? 1.0 / 6.0 : 2.0 / 3.0);
       rho += w + (double)v;
@@ -720,15 +753,28 @@ const char* cuda_error_string() { return g_err; }
 #define LBM_EVEN_VARIANT 0  // 0 direct, 1 bulk copies through shared memory
 #endif
 
-template <int B, typename IDX>
+template <int B, typename IDX, typename S>
 void collide_on(const CollideArgs& a, int odd, cudaStream_t s) {
+  constexpr bool f32 = std::is_same<S, float>::value;
   if (odd) {
-    if (LBM_ODD_VARIANT == 1 && B == 16) k_collide_odd_staged<IDX><<<a.n_active, 256, kStageBytes, s>>>(a);
-    else if (LBM_ODD_VARIANT == 2) k_collide<B, true, IDX><<<a.n_active, B * B, 0, s>>>(a);
-    else k_collide_odd_cols<B, IDX><<<a.n_active, B * B, 0, s>>>(a);
+    if (f32 && LBM_ODD_VARIANT == 1 && B == 16) k_collide_odd_staged<IDX><<<a.n_active, 256, kStageBytes, s>>>(a);
+    else if (LBM_ODD_VARIANT == 2) k_collide<B, true, IDX, S><<<a.n_active, B * B, 0, s>>>(a);
+    else k_collide_odd_cols<B, IDX, S><<<a.n_active, B * B, 0, s>>>(a);
   } else {
-    if (LBM_EVEN_VARIANT == 1 && B == 16) k_collide_even_tma<IDX><<<a.n_active, 256, kEvenBytes, s>>>(a);
-    else k_collide<B, false, IDX><<<a.n_active, B * B, 0, s>>>(a);
+    if (f32 && LBM_EVEN_VARIANT == 1 && B == 16) k_collide_even_tma<IDX><<<a.n_active, 256, kEvenBytes, s>>>(a);
+    else k_collide<B, false, IDX, S><<<a.n_active, B * B, 0, s>>>(a);
+  }
+}
+
+template <typename S>
+void collide_typed(const CollideArgs& a, int B, int odd, cudaStream_t s) {
+  const bool small = a.f_elems < (1LL << 31);
+  if (B == 16) {
+    if (small) collide_on<16, int, S>(a, odd, s);
+    else collide_on<16, long long, S>(a, odd, s);
+  } else {
+    if (small) collide_on<8, int, S>(a, odd, s);
+    else collide_on<8, long long, S>(a, odd, s);
   }
 }
 
@@ -752,33 +798,29 @@ int prepare_kernels() {
 
 int launch_collide(const CollideArgs& a, int B, int odd, void* stream) {
   if (a.n_active == 0) return LBM_OK;
+  if (B != 16 && B != 8) return LBM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  const bool small = a.f_elems < (1LL << 31);
-  if (B == 16) {
-    if (small) collide_on<16, int>(a, odd, s);
-    else collide_on<16, long long>(a, odd, s);
-  } else if (B == 8) {
-    if (small) collide_on<8, int>(a, odd, s);
-    else collide_on<8, long long>(a, odd, s);
-  } else {
-    return LBM_EINVAL;
-  }
+  if (a.half) collide_typed<__half>(a, B, odd, s);
+  else collide_typed<float>(a, B, odd, s);
   return check_launch("collide");
 }
 
-int launch_faces(float* f, const FaceEntry* e, int n, const float*, const float feq[27], void* stream) {
+int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], void* stream) {
   if (n == 0) return LBM_OK;
   Feq27 v;
   for (int i = 0; i < 27; ++i) v.v[i] = feq[i];
-  k_faces<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(f, e, n, v);
+  if (half) k_faces<__half><<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>((__half*)f, e, n, v);
+  else k_faces<float><<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>((float*)f, e, n, v);
   return check_launch("faces");
 }
 
 int walls_partial_count(int n) { return (int)blocks_for(n, kWallThreads); }
 
-int launch_walls(float* f, const WallEntry* e, int n, double* partials, void* stream) {
+int launch_walls(void* f, int half, float inv_scale, const WallEntry* e, int n, double* partials, void* stream) {
   if (n == 0) return LBM_OK;
-  k_walls<<<blocks_for(n, kWallThreads), kWallThreads, 0, (cudaStream_t)stream>>>(f, e, n, partials);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (half) k_walls<__half><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((__half*)f, e, n, inv_scale, partials);
+  else k_walls<float><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((float*)f, e, n, inv_scale, partials);
   return check_launch("walls");
 }
 
@@ -787,47 +829,70 @@ int launch_force_reduce(const double* partials, int nparts, double* accum, void*
   return check_launch("force");
 }
 
-int launch_explode(float* fine, const float* coarse, const ExplodeEntry* e, int ne, const SaveEntry* s, int ns,
-                   float* saved, int parity, void* stream) {
+int launch_explode(void* fine, const void* coarse, int half, float ratio, const ExplodeEntry* e, int ne,
+                   const SaveEntry* sv, int ns, float* saved, int parity, void* stream) {
   long long n = ne > ns ? ne : ns;
   if (n == 0) return LBM_OK;
-  k_explode<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(fine, coarse, e, ne, s, ns, saved, parity);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (half)
+    k_explode<__half><<<blocks_for(n, 256), 256, 0, s>>>((__half*)fine, (const __half*)coarse, e, ne, sv, ns, saved,
+                                                          parity, ratio);
+  else
+    k_explode<float><<<blocks_for(n, 256), 256, 0, s>>>((float*)fine, (const float*)coarse, e, ne, sv, ns, saved,
+                                                         parity, ratio);
   return check_launch("explode");
 }
 
-int launch_inflow(float* fine, const float* coarse, const InflowEntry* e, int n, const float* saved, int parity,
-                  void* stream) {
+int launch_inflow(void* fine, const void* coarse, int half, float ratio, const InflowEntry* e, int n,
+                  const float* saved, int parity, void* stream) {
   if (n == 0) return LBM_OK;
-  k_inflow<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(fine, coarse, e, n, saved, parity);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (half)
+    k_inflow<__half><<<blocks_for(n, 256), 256, 0, s>>>((__half*)fine, (const __half*)coarse, e, n, saved, parity,
+                                                         ratio);
+  else
+    k_inflow<float><<<blocks_for(n, 256), 256, 0, s>>>((float*)fine, (const float*)coarse, e, n, saved, parity, ratio);
   return check_launch("inflow");
 }
 
-int launch_coalesce(float* coarse, const float* fine, const CoalesceEntry* e, int n, const float* saved, int parity,
-                    void* stream) {
+int launch_coalesce(void* coarse, const void* fine, int half, float ratio, const CoalesceEntry* e, int n,
+                    const float* saved, int parity, void* stream) {
   if (n == 0) return LBM_OK;
-  k_coalesce<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(coarse, fine, e, n, saved, parity);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (half)
+    k_coalesce<__half><<<blocks_for(n, 256), 256, 0, s>>>((__half*)coarse, (const __half*)fine, e, n, saved, parity,
+                                                           ratio);
+  else
+    k_coalesce<float><<<blocks_for(n, 256), 256, 0, s>>>((float*)coarse, (const float*)fine, e, n, saved, parity,
+                                                          ratio);
   return check_launch("coalesce");
 }
 
-int launch_fill(float* f, long long n_blocks, int B, const float dev[27], void* stream) {
+int launch_fill(void* f, int half, long long n_blocks, int B, const float dev[27], void* stream) {
   Feq27 v;
   for (int i = 0; i < 27; ++i) v.v[i] = dev[i];
   const int c3 = B * B * B;
   long long n = n_blocks * 27LL * c3;
   if (n == 0) return LBM_OK;
-  k_fill<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(f, n, c3, v);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (half) k_fill<__half><<<blocks_for(n, 256), 256, 0, s>>>((__half*)f, n, c3, v);
+  else k_fill<float><<<blocks_for(n, 256), 256, 0, s>>>((float*)f, n, c3, v);
   return check_launch("fill");
 }
 
 int mass_partial_count(int n_active) { return n_active; }
 
-int launch_mass(const float* f, const int* nbr, const int* maskoff, const uint8_t* masks, int n_active, int B,
-                int parity, double* partials, void* stream) {
+int launch_mass(const void* f, int half, float inv_scale, const int* nbr, const int* maskoff, const uint8_t* masks,
+                int n_active, int B, int parity, double* partials, void* stream) {
   if (n_active == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (B == 16) k_mass<16><<<n_active, 256, 0, s>>>(f, nbr, maskoff, masks, parity, partials);
-  else if (B == 8) k_mass<8><<<n_active, 64, 0, s>>>(f, nbr, maskoff, masks, parity, partials);
-  else return LBM_EINVAL;
+  if (half) {
+    if (B == 16) k_mass<16, __half><<<n_active, 256, 0, s>>>((const __half*)f, nbr, maskoff, masks, parity, inv_scale, partials);
+    else k_mass<8, __half><<<n_active, 64, 0, s>>>((const __half*)f, nbr, maskoff, masks, parity, inv_scale, partials);
+  } else {
+    if (B == 16) k_mass<16, float><<<n_active, 256, 0, s>>>((const float*)f, nbr, maskoff, masks, parity, 1.0f, partials);
+    else k_mass<8, float><<<n_active, 64, 0, s>>>((const float*)f, nbr, maskoff, masks, parity, 1.0f, partials);
+  }
   return check_launch("mass");
 }
 
@@ -856,10 +921,10 @@ int noalloc_scratch(double** out) {
   return LBM_OK;
 }
 
-int launch_mass_noalloc(const float* f, const int* nbr, const int* maskoff, const uint8_t* masks, int n_active,
-                        int B, int parity, double* scratch, void* stream) {
+int launch_mass_noalloc(const void* f, int half, float inv_scale, const int* nbr, const int* maskoff,
+                        const uint8_t* masks, int n_active, int B, int parity, double* scratch, void* stream) {
   if (n_active > kNoAllocMaxBlocks) return LBM_EINVAL;
-  int rc = launch_mass(f, nbr, maskoff, masks, n_active, B, parity, scratch, stream);
+  int rc = launch_mass(f, half, inv_scale, nbr, maskoff, masks, n_active, B, parity, scratch, stream);
   if (rc) return rc;
   k_sum5<<<1, 256, 0, (cudaStream_t)stream>>>(scratch, n_active, scratch + (size_t)kNoAllocMaxBlocks * 5);
   return check_launch("sum5");

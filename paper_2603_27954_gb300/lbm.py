@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 BC = {"periodic": 0, "inout": 1, "slip": 2, "inflow": 3}
 LBM_FP32 = 1
+LBM_FP16_DEV = 2
 
 
 class DomainDesc(C.Structure):
@@ -277,13 +278,13 @@ def lbm_status_string(code):
 # ---------------------------------------------------------------- descriptors
 
 def domain_desc(nx, ny, nz, levels=1, block=16, bc=("inout", "slip", "slip"), u_in=0.05, re_h=0.0,
-                nu_finest=0.0, refine_margin=0.25, galilean=True, omega2=1.0, boxes=None):
+                nu_finest=0.0, refine_margin=0.25, galilean=True, omega2=1.0, boxes=None, precision=LBM_FP32):
     d = DomainDesc()
     d.nx, d.ny, d.nz, d.levels, d.block = nx, ny, nz, levels, block
     for a in range(3):
         d.bc[a] = BC[bc[a]] if isinstance(bc[a], str) else int(bc[a])
     d.u_in, d.re_h, d.nu_finest, d.i_u, d.seed = u_in, re_h, nu_finest, 0.0, 0
-    d.refine_margin, d.precision, d.galilean, d.omega2 = refine_margin, LBM_FP32, int(galilean), omega2
+    d.refine_margin, d.precision, d.galilean, d.omega2 = refine_margin, precision, int(galilean), omega2
     if boxes:
         for l, b in enumerate(boxes):
             if b is not None:

@@ -171,6 +171,30 @@ def test_refined_periodic_box_matches_oracle_and_conserves_mass(L, stream):
     dom.close()
 
 
+def test_refined_periodic_box_block16_matches_oracle(L, stream):
+    """Two levels with 16^3 blocks (the bench's block size): every population
+    after 1, 2 and 5 coarse steps, mass conserved."""
+    boxes = [None, [32, 32, 32, 96, 96, 96]]
+    dom = refined_periodic(L, stream, boxes=(boxes[1],), N=64, block=16)
+    sim = O.Sim(64, 64, 64, levels=2, boxes=boxes, bc=("periodic",) * 3, nu0=0.02, u_in=0.0)
+    for lv in range(2):
+        info = L.lbm_level_info(dom.h, lv)
+        rho, u = W.tgv_fields(info["lo"], info["hi"], 2 ** lv, 64, 0.03, (0.04, -0.01, 0.02))
+        dom.init_field(lv, rho, u)
+        sim.init_field(lv, rho, u)
+    m0, _ = dom.mass()
+    done = 0
+    for s in (1, 2, 5):
+        dom.step(s - done)
+        sim.step(s - done)
+        done = s
+        for lv in range(2):
+            compare_pops(dom.get_populations(lv), sim.f(lv), 2e-6)
+    m1, _ = dom.mass()
+    assert abs(m1 - m0) / m0 < 2e-7
+    dom.close()
+
+
 def test_uniform_flow_crosses_refinement_on_gpu(L, stream):
     dom = refined_periodic(L, stream)
     u = np.array([0.05, 0.02, -0.01])
