@@ -196,6 +196,75 @@ int lbm_get_links(const lbm_domain* d, int level, long long* cell, int* dir, dou
 /* Placed segments (rows of 8 doubles) of the tree; n capacity. */
 int lbm_get_segments(const lbm_domain* d, double* seg, int n, int* count);
 
+/* Per-branch momentum-exchange forces (Sec. 2.4's branch-wise view of the
+   tree, measured by the LBM).  Every cut link belongs to the cylinder (or
+   primitive) its ray enters first; with branch forces on, every finest step
+   adds each branch's force to a running FP64 sum (deterministic order).
+   lbm_get_branch_forces returns, for the n >= number of branches, the mean
+   force per branch since the last lbm_reset_force / init (finest-level
+   lattice units, rows x y z) and the number of steps averaged.  The sum over
+   branches equals the total of lbm_drag.  Toggling recaptures the graphs. */
+int lbm_set_branch_forces(lbm_domain* d, int on);
+int lbm_get_branch_forces(lbm_domain* d, double* mean_xyz, int n, long long* steps);
+
+/* Branch-wise description of the tree for the analytical model (Sec. 2.4,
+   Eq. 3: F_d = C_d (1/2 rho U^2) L D sin^3(alpha)) and its learned sectional
+   drag: one row of 9 doubles per branch, in lbm_get_segments order:
+   log10 Re_d (U D / nu, finest level), generation, D/H, cos(alpha) (alpha =
+   angle between the axis and the flow), inflow turbulence intensity,
+   shielding depth (mean number of other branches met upstream by the
+   x-parallel lines through 16 points of the axis), L, D (finest cells),
+   sin^3(alpha).  n is the capacity in rows, *count the number of branches. */
+int lbm_branch_table(const lbm_domain* d, double* rows, int n, int* count);
+
+/* Branch-wise drag estimate (Sec. 2.4, Eq. 3 summed as in Eq. 5): with
+   c_k = F_d,k / (rho U^2 L_k D_k / 2) the sectional drag coefficient of
+   branch k, C_D-est = sum_k c_k L_k D_k / A_x.  rows: n rows of
+   lbm_branch_table (host, 9 doubles each); c_sect: host array of n c_k, or
+   NULL for the cylinder law c_k = C_d(Re_d,k) sin^3(alpha_k) with
+   C_d(Re) = 1 + 10 Re^(-2/3) (White's cross-flow cylinder correlation,
+   standing in for the paper's fit to measurements); area: A_x in the same
+   length unit as L and D.  Writes *cd_est and, if c_out is not NULL, the n
+   coefficients used.  Host arithmetic, no device work; LBM_EINVAL for null
+   pointers, n < 0 or area <= 0. */
+int lbm_branch_drag_estimate(const double* rows, int n, const double* c_sect, double area, double* cd_est,
+                             double* c_out);
+
+/* ---- Sectional-drag surrogate (a learned C_d for Eq. 3, Sec. 2.4) ----
+   A fully connected network: n_in inputs, `hidden` layers of `width` GELU
+   units, one output; BF16 weights with FP32 accumulation in its forward and
+   backward kernels, FP32 master weights and Adam (beta 0.9 / 0.999, eps 1e-8)
+   moments, deterministic reductions.  The paper fits its cylinder drag law
+   to measured data instead; this learned law is trained on per-branch forces
+   that the LBM measures (lbm_get_branch_forces, lbm_branch_table).
+   Parameters are one flat FP32 vector: per layer W (out x in, row-major) then
+   the bias.  Inputs are standardised with (x - mu_x) / sd_x and the target
+   with (y - mu_y) / sd_y (lbm_mlp_set_normalization); the loss is the mean
+   squared error of the standardised output.  x is batch x n_in FP32, y and
+   the optional idx (rows of x and y to use, int32) have batch entries; all
+   are device pointers.  The caller binds one device buffer of
+   lbm_mlp_memory_requirements bytes for a maximum batch. */
+typedef struct lbm_mlp lbm_mlp;
+int lbm_mlp_create(int n_in, int width, int hidden, void* cuda_stream, lbm_mlp** out);
+int lbm_mlp_memory_requirements(const lbm_mlp* m, int max_batch, size_t* bytes);
+int lbm_mlp_bind_memory(lbm_mlp* m, void* device_ptr, size_t bytes, int max_batch);
+int lbm_mlp_param_count(const lbm_mlp* m, long long* n);
+/* set / read the FP32 master parameters (host arrays); set resets Adam */
+int lbm_mlp_set_params(lbm_mlp* m, const float* host, long long n);
+int lbm_mlp_get_params(lbm_mlp* m, float* host, long long n);
+int lbm_mlp_set_normalization(lbm_mlp* m, const float* mu_x, const float* sd_x, float mu_y, float sd_y);
+/* y[b] = prediction (de-standardised) for x[b]; asynchronous */
+int lbm_mlp_forward(lbm_mlp* m, const float* x, int batch, float* y);
+/* loss and the gradient of the loss with respect to the parameters (host
+   array of lbm_mlp_param_count floats, may be NULL); synchronises */
+int lbm_mlp_gradients(lbm_mlp* m, const float* x, const float* y, const int* idx, int batch, float* grad_host,
+                      double* loss);
+/* one Adam step at learning rate lr; loss may be NULL (no synchronisation) */
+int lbm_mlp_train_step(lbm_mlp* m, const float* x, const float* y, const int* idx, int batch, float lr,
+                       double* loss);
+const char* lbm_mlp_last_error(void);
+void lbm_mlp_destroy(lbm_mlp* m);
+
 /* Every `every` coarse steps lbm_step checks for NaN/Inf and densities
    outside [0.5, 2] (synchronising); 0 disables (default). */
 int lbm_set_watchdog(lbm_domain* d, int every);

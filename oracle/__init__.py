@@ -99,6 +99,8 @@ def _declare(L):
     L.orc_mass.argtypes = [C.c_void_p, C.POINTER(C.c_double), _dp]
     L.orc_cell_type.argtypes = [C.c_void_p, C.c_int, _bp]
     L.orc_cell_type.restype = C.c_int
+    L.orc_branch_forces.argtypes = [C.c_void_p, _dp, C.c_int]
+    L.orc_branch_forces.restype = C.c_int
 
 
 # ---------------------------------------------------------------- tree (Sec. 2.1)
@@ -343,6 +345,11 @@ class Sim:
         p = np.zeros(3)
         lib().orc_mass(self._h, C.byref(m), p)
         return m.value, p
+
+    def branch_forces(self, n):
+        out = np.zeros((max(1, n), 3))
+        lib().orc_branch_forces(self._h, out, max(1, n))
+        return out[:n]
 
     def cell_type(self, level):
         nx, ny, nz = self.shape(level)

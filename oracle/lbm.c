@@ -54,6 +54,7 @@ typedef struct {
   int* ldir;
   double* lq;
   long* lback; /* index of x_f - c_i if it is a fluid cell, else -1 */
+  int* lseg;   /* primitive whose surface the link enters first */
   orc_rates rates;
   double F[3];
 } lev;
@@ -65,6 +66,8 @@ struct orc_sim {
   double feq_in[27];
   double Fsum[3];
   long nF;
+  int nprim;
+  double* Fseg; /* per-primitive running sum of the finest level's force */
 };
 
 static long lidx(const lev* v, int x, int y, int z) {
@@ -174,8 +177,9 @@ void orc_destroy(orc_sim* s) {
   for (int l = 0; l < 6; ++l) {
     lev* v = &s->lv[l];
     free(v->A); free(v->B); free(v->type); free(v->ring);
-    free(v->lcell); free(v->ldir); free(v->lq); free(v->lback);
+    free(v->lcell); free(v->ldir); free(v->lq); free(v->lback); free(v->lseg);
   }
+  free(s->Fseg);
   free(s);
 }
 
@@ -189,6 +193,7 @@ void orc_init_uniform(orc_sim* s, double rho, const double u[3]) {
   }
   s->Fsum[0] = s->Fsum[1] = s->Fsum[2] = 0;
   s->nF = 0;
+  if (s->Fseg) memset(s->Fseg, 0, 3 * sizeof(double) * (size_t)s->nprim);
 }
 
 int orc_init_field(orc_sim* s, int level, const double* rho, const double* u) {
@@ -228,12 +233,13 @@ int orc_set_prims(orc_sim* s, const orc_prim* pr, int np) {
       double c[3] = {(x + 0.5) * h, (y + 0.5) * h, (z + 0.5) * h};
       if (orc_prim_inside(pr, np, c)) v->type[id] = T_SOLID;
     }
-    free(v->lcell); free(v->ldir); free(v->lq); free(v->lback);
+    free(v->lcell); free(v->ldir); free(v->lq); free(v->lback); free(v->lseg);
     long cap = 1024, nl = 0;
     v->lcell = malloc(cap * sizeof(long));
     v->ldir = malloc(cap * sizeof(int));
     v->lq = malloc(cap * sizeof(double));
     v->lback = malloc(cap * sizeof(long));
+    v->lseg = malloc(cap * sizeof(int));
     for (long id = 0; id < v->ncell; ++id) {
       if (v->type[id] != T_FLUID) continue;
       int x, y, z;
@@ -245,7 +251,23 @@ int orc_set_prims(orc_sim* s, const orc_prim* pr, int np) {
         if (nb < 0 || v->type[nb] != T_SOLID) continue;
         double p0[3] = {(x + 0.5) * h, (y + 0.5) * h, (z + 0.5) * h};
         double dd[3] = {cx(i) * h, cy(i) * h, cz(i) * h};
-        double q = orc_prim_ray(pr, np, p0, dd);
+        /* the link's branch: the primitive its ray enters first (ties: lowest index),
+           or, if no ray entry is found, the first primitive holding the solid centre */
+        double q = INFINITY;
+        int seg = -1;
+        for (int k = 0; k < np; ++k) {
+          double tk = orc_prim_ray(pr + k, 1, p0, dd);
+          if (tk < q) { q = tk; seg = k; }
+        }
+        if (seg < 0) {
+          long sid = l == 0 ? level0_cell(s, x + cx(i), y + cy(i), z + cz(i)) : lidx(v, x + cx(i), y + cy(i), z + cz(i));
+          int sx, sy, sz;
+          lcoord(v, sid, &sx, &sy, &sz);
+          double sc[3] = {(sx + 0.5) * h, (sy + 0.5) * h, (sz + 0.5) * h};
+          for (int k = 0; k < np && seg < 0; ++k)
+            if (orc_prim_inside(pr + k, 1, sc)) seg = k;
+          if (seg < 0) seg = 0;
+        }
         if (!(q <= 1.0)) q = 1.0;
         if (q < 1e-6) q = 1e-6;
         long bk = l == 0 ? level0_cell(s, x - cx(i), y - cy(i), z - cz(i))
@@ -263,13 +285,17 @@ int orc_set_prims(orc_sim* s, const orc_prim* pr, int np) {
           v->ldir = realloc(v->ldir, cap * sizeof(int));
           v->lq = realloc(v->lq, cap * sizeof(double));
           v->lback = realloc(v->lback, cap * sizeof(long));
+          v->lseg = realloc(v->lseg, cap * sizeof(int));
         }
-        v->lcell[nl] = id; v->ldir[nl] = i; v->lq[nl] = q; v->lback[nl] = bk;
+        v->lcell[nl] = id; v->ldir[nl] = i; v->lq[nl] = q; v->lback[nl] = bk; v->lseg[nl] = seg;
         ++nl;
       }
     }
     v->nlink = nl;
   }
+  free(s->Fseg);
+  s->nprim = np;
+  s->Fseg = calloc(3 * (size_t)(np > 0 ? np : 1), sizeof(double));
   return 0;
 }
 
@@ -342,6 +368,12 @@ static void stream_level(orc_sim* s, int l) {
     F[0] += cx(i) * (fa + out);
     F[1] += cy(i) * (fa + out);
     F[2] += cz(i) * (fa + out);
+    if (l == s->L - 1 && s->Fseg) {
+      double* g = s->Fseg + 3 * v->lseg[k];
+      g[0] += cx(i) * (fa + out);
+      g[1] += cy(i) * (fa + out);
+      g[2] += cz(i) * (fa + out);
+    }
   }
   v->F[0] = F[0]; v->F[1] = F[1]; v->F[2] = F[2];
   if (l == s->L - 1) {
@@ -482,4 +514,12 @@ int orc_cell_type(const orc_sim* s, int level, unsigned char* out) {
     for (int y = v->rlo[1]; y < v->rhi[1]; ++y)
       for (int x = v->rlo[0]; x < v->rhi[0]; ++x, ++k) out[k] = v->type[lidx(v, x, y, z)];
   return (int)k;
+}
+
+/* per-branch mean force of the finest level since the last initialisation */
+int orc_branch_forces(const orc_sim* s, double* mean, int n) {
+  if (n < s->nprim) return -1;
+  for (int k = 0; k < s->nprim; ++k)
+    for (int a = 0; a < 3; ++a) mean[3 * k + a] = s->nF > 0 ? s->Fseg[3 * k + a] / (double)s->nF : 0.0;
+  return s->nprim;
 }

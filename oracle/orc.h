@@ -100,5 +100,6 @@ int orc_level_links(const orc_sim* s, int level, long* cell, int* dir, double* q
 void orc_force(const orc_sim* s, double last[3], double sum[3], long* nsum);
 void orc_mass(const orc_sim* s, double* mass, double mom[3]);
 int orc_cell_type(const orc_sim* s, int level, unsigned char* out);
+int orc_branch_forces(const orc_sim* s, double* mean, int n);
 
 #endif

@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "liblbm.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SRC = ["geometry.cpp", "mesh.cpp", "api.cpp"]
-CUDA_SRC = ["kernels.cu"]
+CUDA_SRC = ["kernels.cu", "mlp.cu"]
 
 
 def _cuda_home():

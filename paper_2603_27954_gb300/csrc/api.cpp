@@ -61,6 +61,9 @@ struct lbm_domain {
   char* base = nullptr;
   size_t need = 0;
   size_t off_partials = 0, off_accum = 0, off_mpart = 0;
+  size_t off_linkf = 0, off_segb = 0, off_segacc = 0;  // per-branch forces (finest level)
+  int n_seg = 0;
+  bool branch_forces = false;
   int max_wall_parts = 0;
   float feq_in[27];
   int parity0 = 0;
@@ -149,8 +152,13 @@ int advance(lbm_domain* dm, int l, int parity) {
   if (!v.wall[parity].empty()) {
     Timed t(dm, KC_WALLS, (long long)v.wall[parity].size());
     int n = (int)v.wall[parity].size();
+    const bool per_branch = dm->branch_forces && l == m.L - 1;
     if ((rc = launch_walls(f, half, 1.0f / v.scale, dm->dev<WallEntry>(v.off_wall[parity]), n,
-                           dm->dev<double>(dm->off_partials), dm->stream)))
+                           dm->dev<double>(dm->off_partials), per_branch ? dm->dev<double>(dm->off_linkf) : nullptr,
+                           dm->stream)))
+      return rc;
+    if (per_branch && (rc = launch_segments(dm->dev<double>(dm->off_linkf), dm->dev<int>(dm->off_segb), dm->n_seg,
+                                            dm->dev<double>(dm->off_segacc), dm->stream)))
       return rc;
     if (l == m.L - 1 &&
         (rc = launch_force_reduce(dm->dev<double>(dm->off_partials), walls_partial_count(n),
@@ -251,6 +259,13 @@ int build(lbm_domain* d) {
     d->max_wall_parts = std::max(d->max_wall_parts, walls_partial_count((int)v.wall[0].size()));
     max_blocks = std::max(max_blocks, (size_t)v.n_active);
   }
+  {
+    const Level& fl = d->mesh.lv[L - 1];
+    d->n_seg = (int)d->prims.size();
+    d->off_linkf = put(fl.links.size() * 3 * sizeof(double));
+    d->off_segb = put((size_t)(d->n_seg + 1) * sizeof(int));
+    d->off_segacc = put((size_t)d->n_seg * 4 * sizeof(double));
+  }
   d->off_partials = put((size_t)d->max_wall_parts * 3 * sizeof(double));
   d->off_accum = put(8 * sizeof(double));
   d->off_mpart = put(max_blocks * 5 * sizeof(double));
@@ -279,11 +294,14 @@ int upload(lbm_domain* d) {
     CK(cp(v.off_infl, v.infl.data(), v.infl.size() * sizeof(InflowEntry)));
     CK(cp(v.off_coal, v.coal.data(), v.coal.size() * sizeof(CoalesceEntry)));
   }
+  const Level& fl = d->mesh.lv.back();
+  if (d->n_seg) CK(cp(d->off_segb, fl.seg_begin.data(), fl.seg_begin.size() * sizeof(int)));
   return LBM_OK;
 }
 
 int reset_force(lbm_domain* d) {
   CK(cudaMemsetAsync(d->base + d->off_accum, 0, 8 * sizeof(double), d->stream));
+  if (d->n_seg) CK(cudaMemsetAsync(d->base + d->off_segacc, 0, (size_t)d->n_seg * 4 * sizeof(double), d->stream));
   return LBM_OK;
 }
 
@@ -727,6 +745,58 @@ int lbm_get_segments(const lbm_domain* d, double* seg, int n, int* count) {
   if (count) *count = c;
   if (seg)
     for (int k = 0; k < c && k < n; ++k) std::memcpy(seg + 8 * k, &d->tree.seg[8 * k], 8 * sizeof(double));
+  return LBM_OK;
+}
+
+int lbm_set_branch_forces(lbm_domain* d, int on) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (d->branch_forces != (on != 0)) free_graphs(d);
+  d->branch_forces = on != 0;
+  return LBM_OK;
+}
+
+int lbm_get_branch_forces(lbm_domain* d, double* mean, int n, long long* steps) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  if (n < d->n_seg) return fail(LBM_EINVAL, "capacity below the number of branches");
+  std::vector<double> acc((size_t)d->n_seg * 4);
+  if (d->n_seg) {
+    CK(cudaMemcpyAsync(acc.data(), d->base + d->off_segacc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+  }
+  long long cnt = d->n_seg ? (long long)acc[3] : 0;
+  for (int k = 0; k < d->n_seg; ++k)
+    for (int a = 0; a < 3; ++a) mean[3 * k + a] = acc[4 * k + 3] > 0 ? acc[4 * k + a] / acc[4 * k + 3] : 0.0;
+  if (steps) *steps = cnt;
+  return LBM_OK;
+}
+
+int lbm_branch_table(const lbm_domain* d, double* rows, int n, int* count) {
+  if (!d || !d->built) return fail(LBM_ESTATE, "geometry not set");
+  if (!d->have_tree) return fail(LBM_ESTATE, "no tree: set the geometry from a tree or segments");
+  std::vector<double> tab;
+  branch_table(d->tree, d->d.u_in, d->nu_f, d->H, d->d.i_u, &tab);
+  const int c = d->tree.count();
+  if (count) *count = c;
+  if (rows) {
+    if (n < c) return fail(LBM_EINVAL, "capacity below the number of branches");
+    std::memcpy(rows, tab.data(), tab.size() * sizeof(double));
+  }
+  return LBM_OK;
+}
+
+int lbm_branch_drag_estimate(const double* rows, int n, const double* c_sect, double area, double* cd_est,
+                             double* c_out) {
+  if (!rows || !cd_est || n < 0 || !(area > 0)) return fail(LBM_EINVAL, "bad argument");
+  double sum = 0;
+  for (int k = 0; k < n; ++k) {
+    const double* r = rows + 9 * (size_t)k;
+    const double c = c_sect ? c_sect[k] : (1.0 + 10.0 * std::pow(10.0, -2.0 / 3.0 * r[0])) * r[8];
+    if (c_out) c_out[k] = c;
+    sum += c * r[6] * r[7];
+  }
+  *cd_est = sum / area;
   return LBM_OK;
 }
 

@@ -339,4 +339,44 @@ void prim_bounds(const Prim& p, double lo[3], double hi[3]) {
   }
 }
 
+// Branch-wise description of the tree (Sec. 2.4): per cylinder its length L,
+// diameter D, the angle alpha between its axis and the flow (x), and the
+// inputs of the sectional-drag surrogate.  Shielding depth: the mean, over 16
+// points along the axis, of the number of other cylinders that the
+// x-parallel line through the point meets upstream of it.
+void branch_table(const Tree& t, double u, double nu, double height, double i_u, std::vector<double>* out) {
+  const int n = t.count();
+  out->assign((size_t)n * 9, 0.0);
+  const double dir[3] = {1, 0, 0};
+  for (int k = 0; k < n; ++k) {
+    const double* r = &t.seg[8 * k];
+    double a[3];
+    const double len = seg_unit_axis(r, a);
+    const double D = r[6];
+    const double cosa = std::fabs(a[0]);
+    const double sina = std::sqrt(std::max(0.0, 1.0 - cosa * cosa));
+    double shield = 0;
+    for (int j = 0; j < 16; ++j) {
+      const double s = (j + 0.5) / 16.0;
+      const double p[3] = {r[0] + s * (r[3] - r[0]), r[1] + s * (r[4] - r[1]), r[2] + s * (r[5] - r[2])};
+      const double x0[3] = {0.0, p[1], p[2]};
+      for (int m = 0; m < n; ++m) {
+        if (m == k) continue;
+        double t0, t1;
+        if (cylinder_span(&t.seg[8 * m], x0, dir, &t0, &t1) && t0 < p[0]) shield += 1.0;
+      }
+    }
+    double* row = &(*out)[(size_t)9 * k];
+    row[0] = std::log10(u * D / nu);  // local Reynolds number of the branch
+    row[1] = r[7];                    // generation
+    row[2] = D / height;
+    row[3] = cosa;                    // cosine of the angle to the flow
+    row[4] = i_u;
+    row[5] = shield / 16.0;
+    row[6] = len;
+    row[7] = D;
+    row[8] = sina * sina * sina;
+  }
+}
+
 }  // namespace lbm

@@ -34,6 +34,8 @@ double tree_height(const Tree& t);
 void tree_centroid(const Tree& t, double c[3]);
 void tree_affine(Tree* t, double scale, const double shift[3]);
 double frontal_area(const Tree& t, double pitch);
+// rows of 9: log10 Re_d, generation, D/H, cos(alpha), I_u, shielding depth, L, D, sin^3(alpha)
+void branch_table(const Tree& t, double u, double nu, double height, double i_u, std::vector<double>* out);
 
 bool prim_contains(const Prim& p, const double x[3]);
 double prim_entry(const Prim& p, const double x[3], const double d[3]);  // t >= 0 or +inf
@@ -51,6 +53,8 @@ struct WallEntry {   // one cut link (Bouzidi linear bounce-back + momentum exch
   long long dst, a, b, c;  // a: f*_i(x_f); b: f*_i(x_f - c_i) or -1; c: f*_ibar(x_f)
   float q;
   int dir;
+  int seg;                 // branch of the link (links are ordered by branch)
+  int pad;
 };
 struct ExplodeEntry {    // fine inflow before the second fine step
   long long dst;         // fine ghost slot
@@ -79,6 +83,7 @@ enum BlockState : int8_t { ABSENT = 0, ACTIVE = 1, GHOST = 2 };
 struct Link {
   int x, y, z, dir;
   double q;
+  int seg;  // primitive (branch) whose surface the link crosses first
 };
 
 struct Level {
@@ -100,6 +105,7 @@ struct Level {
   float scale = 1.0f;   // stored value = (f - w) * scale
   std::vector<Link> links;
   std::vector<WallEntry> wall[2];
+  std::vector<int> seg_begin;                    // n_seg + 1 offsets into the ordered links
   std::vector<FaceEntry> face[2];
   // interface with the next finer level (this level = coarse)
   std::vector<ExplodeEntry> expl;
@@ -153,7 +159,9 @@ struct CollideArgs {
 int prepare_kernels();
 int launch_collide(const CollideArgs& a, int B, int odd, void* stream);
 int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], void* stream);
-int launch_walls(void* f, int half, float inv_scale, const WallEntry* e, int n, double* partials, void* stream);
+int launch_walls(void* f, int half, float inv_scale, const WallEntry* e, int n, double* partials,
+                 double* link_force, void* stream);
+int launch_segments(const double* link_force, const int* seg_begin, int n_seg, double* seg_accum, void* stream);
 int walls_partial_count(int n);
 int launch_force_reduce(const double* partials, int nparts, double* accum, void* stream);
 int launch_explode(void* fine, const void* coarse, int half, float ratio, const ExplodeEntry* e, int ne,
@@ -171,5 +179,8 @@ int noalloc_scratch(double** out);
 int launch_mass_noalloc(const void* f, int half, float inv_scale, const int* nbr, const int* maskoff,
                         const uint8_t* masks, int n_active, int B, int parity, double* scratch, void* stream);
 const char* cuda_error_string();
+
+// surrogate network kernels (mlp.cu); W / B operands of the GEMMs are BF16 or FP32
+const char* mlp_error_string();
 
 }  // namespace lbm

@@ -525,7 +525,8 @@ __device__ void block_sum3(double& a, double& b, double& c) {
 
 template <typename S>
 __global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const WallEntry* __restrict__ e, int n,
-                                                        float inv_scale, double* __restrict__ partials) {
+                                                        float inv_scale, double* __restrict__ partials,
+                                                        double* __restrict__ link_force) {
   const int t = blockIdx.x * kWallThreads + threadIdx.x;
   double Fx = 0.0, Fy = 0.0, Fz = 0.0;
   if (t < n) {
@@ -552,12 +553,38 @@ __global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const
     Fx = dcx(i) * s;
     Fy = dcy(i) * s;
     Fz = dcz(i) * s;
+    if (link_force) {
+      link_force[3 * (size_t)t] = Fx;
+      link_force[3 * (size_t)t + 1] = Fy;
+      link_force[3 * (size_t)t + 2] = Fz;
+    }
   }
   block_sum3<kWallThreads>(Fx, Fy, Fz);
   if (threadIdx.x == 0) {
     partials[3 * blockIdx.x + 0] = Fx;
     partials[3 * blockIdx.x + 1] = Fy;
     partials[3 * blockIdx.x + 2] = Fz;
+  }
+}
+
+// per-branch force of one finest step: one CTA per branch sums its links
+// (contiguous, fixed order) and adds them to the branch's running sums
+// seg_accum[4 k .. 4 k + 2]; seg_accum[4 k + 3] counts the steps
+__global__ void __launch_bounds__(256) k_segments(const double* __restrict__ link_force,
+                                                  const int* __restrict__ seg_begin, double* __restrict__ seg_accum) {
+  const int k = blockIdx.x;
+  double a = 0, b = 0, c = 0;
+  for (int j = seg_begin[k] + threadIdx.x; j < seg_begin[k + 1]; j += 256) {
+    a += link_force[3 * (size_t)j];
+    b += link_force[3 * (size_t)j + 1];
+    c += link_force[3 * (size_t)j + 2];
+  }
+  block_sum3<256>(a, b, c);
+  if (threadIdx.x == 0) {
+    seg_accum[4 * k] += a;
+    seg_accum[4 * k + 1] += b;
+    seg_accum[4 * k + 2] += c;
+    seg_accum[4 * k + 3] += 1.0;
   }
 }
 
@@ -816,12 +843,23 @@ int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[2
 
 int walls_partial_count(int n) { return (int)blocks_for(n, kWallThreads); }
 
-int launch_walls(void* f, int half, float inv_scale, const WallEntry* e, int n, double* partials, void* stream) {
+int launch_walls(void* f, int half, float inv_scale, const WallEntry* e, int n, double* partials,
+                 double* link_force, void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (half) k_walls<__half><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((__half*)f, e, n, inv_scale, partials);
-  else k_walls<float><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((float*)f, e, n, inv_scale, partials);
+  if (half)
+    k_walls<__half><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((__half*)f, e, n, inv_scale, partials,
+                                                                          link_force);
+  else
+    k_walls<float><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((float*)f, e, n, inv_scale, partials,
+                                                                         link_force);
   return check_launch("walls");
+}
+
+int launch_segments(const double* link_force, const int* seg_begin, int n_seg, double* seg_accum, void* stream) {
+  if (n_seg == 0) return LBM_OK;
+  k_segments<<<n_seg, 256, 0, (cudaStream_t)stream>>>(link_force, seg_begin, seg_accum);
+  return check_launch("segments");
 }
 
 int launch_force_reduce(const double* partials, int nparts, double* accum, void* stream) {

@@ -278,20 +278,36 @@ int build_links(Mesh& m, int l, const std::vector<Prim>& prims) {
             double p0[3] = {(fx + 0.5) * h, (fy + 0.5) * h, (fz + 0.5) * h};
             double dd[3] = {cx(i) * h, cy(i) * h, cz(i) * h};
             double q = std::numeric_limits<double>::infinity();
-            for (const Prim& p : prims) q = std::min(q, prim_entry(p, p0, dd));
+            int seg = -1;
+            for (size_t k = 0; k < prims.size(); ++k) {
+              const double t = prim_entry(prims[k], p0, dd);
+              if (t < q) {
+                q = t;
+                seg = (int)k;
+              }
+            }
+            if (seg < 0) {  // the solid cell's centre lies inside: first primitive containing it
+              double sc[3] = {(sx + 0.5) * h, (sy + 0.5) * h, (sz + 0.5) * h};
+              for (size_t k = 0; k < prims.size() && seg < 0; ++k)
+                if (prim_contains(prims[k], sc)) seg = (int)k;
+            }
             if (!(q <= 1.0)) q = 1.0;
             if (q < 1e-6) q = 1e-6;
             int c[3] = {fx, fy, fz};
             for (int a = 0; a < 3; ++a)
               if (v.wrap[a]) c[a] = wrapmod(c[a], v.dom[a]);
-            v.links.push_back({c[0], c[1], c[2], i, q});
+            v.links.push_back({c[0], c[1], c[2], i, q, seg < 0 ? 0 : seg});
           }
         }
   }
   std::sort(v.links.begin(), v.links.end(), [&](const Link& a, const Link& b) {
+    if (a.seg != b.seg) return a.seg < b.seg;
     long long ka = v.addr(a.x, a.y, a.z, 0), kb = v.addr(b.x, b.y, b.z, 0);
     return ka != kb ? ka < kb : a.dir < b.dir;
   });
+  v.seg_begin.assign(prims.size() + 1, 0);
+  for (const Link& k : v.links) v.seg_begin[k.seg + 1]++;
+  for (size_t k = 0; k < prims.size(); ++k) v.seg_begin[k + 1] += v.seg_begin[k];
   for (int p = 0; p < 2; ++p) v.wall[p].clear();
   for (const Link& k : v.links) {
     int i = k.dir, ib = opposite(i);
@@ -316,6 +332,8 @@ int build_links(Mesh& m, int l, const std::vector<Prim>& prims) {
     e1.c = v.addr(x - cx(i), y - cy(i), z - cz(i), ib);
     e0.q = e1.q = (float)k.q;
     e0.dir = e1.dir = i;
+    e0.seg = e1.seg = k.seg;
+    e0.pad = e1.pad = 0;
     if (e0.dst < 0 || e0.a < 0 || e0.c < 0 || e1.a < 0 || e1.c < 0) {
       m.error = "cut link without storage";
       return LBM_EINVAL;

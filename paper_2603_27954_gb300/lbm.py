@@ -71,6 +71,10 @@ def _load():
         "lbm_get_links": ([vp, i, llp, ip, dp, sz, llp], i),
         "lbm_get_segments": ([vp, dp, i, ip], i),
         "lbm_set_watchdog": ([vp, i], i),
+        "lbm_branch_table": ([vp, dp, i, ip], i),
+        "lbm_branch_drag_estimate": ([dp, i, dp, C.c_double, dp, dp], i),
+        "lbm_set_branch_forces": ([vp, i], i),
+        "lbm_get_branch_forces": ([vp, dp, i, llp], i),
         "lbm_use_graphs": ([vp, i], i),
         "lbm_set_timing": ([vp, i], i),
         "lbm_get_timing": ([vp, dp, llp, llp], i),
@@ -79,6 +83,18 @@ def _load():
         "lbm_load": ([vp, C.c_char_p], i),
         "lbm_destroy": ([vp], None),
         "lbm_status_string": ([i], C.c_char_p),
+        "lbm_mlp_create": ([i, i, i, vp, C.POINTER(vp)], i),
+        "lbm_mlp_memory_requirements": ([vp, i, C.POINTER(sz)], i),
+        "lbm_mlp_bind_memory": ([vp, vp, sz, i], i),
+        "lbm_mlp_param_count": ([vp, llp], i),
+        "lbm_mlp_set_params": ([vp, C.POINTER(C.c_float), C.c_longlong], i),
+        "lbm_mlp_get_params": ([vp, C.POINTER(C.c_float), C.c_longlong], i),
+        "lbm_mlp_set_normalization": ([vp, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float, C.c_float], i),
+        "lbm_mlp_forward": ([vp, vp, i, vp], i),
+        "lbm_mlp_gradients": ([vp, vp, vp, vp, i, C.POINTER(C.c_float), dp], i),
+        "lbm_mlp_train_step": ([vp, vp, vp, vp, i, C.c_float, dp], i),
+        "lbm_mlp_last_error": ([], C.c_char_p),
+        "lbm_mlp_destroy": ([vp], None),
         "lbm_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -232,6 +248,37 @@ def lbm_get_segments(h):
     return seg
 
 
+def lbm_set_branch_forces(h, on):
+    return _ck(_lib.lbm_set_branch_forces(h, int(bool(on))), "lbm_set_branch_forces")
+
+
+def lbm_get_branch_forces(h, n_branches):
+    out = np.zeros((max(1, n_branches), 3))
+    steps = C.c_longlong()
+    _ck(_lib.lbm_get_branch_forces(h, _dp(out), max(1, n_branches), C.byref(steps)), "lbm_get_branch_forces")
+    return out[:n_branches], steps.value
+
+
+def lbm_branch_drag_estimate(rows, area, c_sect=None):
+    """Eq. 5 over the branches of a branch table; returns (C_D-est, c_k)."""
+    rows = np.ascontiguousarray(rows, dtype=np.float64)
+    n = rows.shape[0]
+    c_out = np.zeros(max(1, n))
+    cs = None if c_sect is None else np.ascontiguousarray(c_sect, dtype=np.float64)
+    cd = C.c_double()
+    _ck(_lib.lbm_branch_drag_estimate(_dp(rows) if n else _dp(np.zeros(9)), n, _dp(cs) if cs is not None else None,
+                                      float(area), C.byref(cd), _dp(c_out)), "lbm_branch_drag_estimate")
+    return cd.value, c_out[:n]
+
+
+def lbm_branch_table(h):
+    n = C.c_int()
+    _ck(_lib.lbm_branch_table(h, None, 0, C.byref(n)), "lbm_branch_table")
+    out = np.zeros((max(1, n.value), 9))
+    _ck(_lib.lbm_branch_table(h, _dp(out), max(1, n.value), C.byref(n)), "lbm_branch_table")
+    return out[:n.value]
+
+
 def lbm_set_watchdog(h, every):
     return _ck(_lib.lbm_set_watchdog(h, int(every)), "lbm_set_watchdog")
 
@@ -347,6 +394,96 @@ class Domain:
             if self.buffer is not None:
                 self._torch.cuda.synchronize(self.buffer.device)
             lbm_destroy(self.h)
+            self.h = None
+            self.buffer = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- surrogate network
+
+class MlpError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed (%d): %s" % (where, code, _lib.lbm_mlp_last_error().decode()))
+
+
+def _mck(rc, where):
+    if rc != LBM_OK:
+        raise MlpError(rc, where)
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class Mlp:
+    """Owner of an lbm_mlp handle and its torch-allocated buffer.  Device
+    arrays are torch tensors; this class only passes their pointers."""
+
+    def __init__(self, n_in=6, width=128, hidden=3, max_batch=4096, stream=None, device="cuda"):
+        import torch
+        self._torch = torch
+        self.stream = stream
+        h = C.c_void_p()
+        _mck(_lib.lbm_mlp_create(n_in, width, hidden, C.c_void_p(stream.cuda_stream if stream else 0),
+                                 C.byref(h)), "lbm_mlp_create")
+        self.h = h
+        n = C.c_size_t()
+        _mck(_lib.lbm_mlp_memory_requirements(h, max_batch, C.byref(n)), "lbm_mlp_memory_requirements")
+        self.buffer = torch.empty(n.value, dtype=torch.uint8, device=device)
+        _mck(_lib.lbm_mlp_bind_memory(h, self.buffer.data_ptr(), n.value, max_batch), "lbm_mlp_bind_memory")
+        p = C.c_longlong()
+        _mck(_lib.lbm_mlp_param_count(h, C.byref(p)), "lbm_mlp_param_count")
+        self.n_params, self.max_batch, self.n_in = p.value, max_batch, n_in
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _mck(_lib.lbm_mlp_set_params(self.h, _fp(w), len(w)), "lbm_mlp_set_params")
+
+    def get_params(self):
+        w = np.zeros(self.n_params, np.float32)
+        _mck(_lib.lbm_mlp_get_params(self.h, _fp(w), len(w)), "lbm_mlp_get_params")
+        return w
+
+    def set_normalization(self, mu_x, sd_x, mu_y, sd_y):
+        mu = np.ascontiguousarray(mu_x, dtype=np.float32)
+        sd = np.ascontiguousarray(sd_x, dtype=np.float32)
+        _mck(_lib.lbm_mlp_set_normalization(self.h, _fp(mu), _fp(sd), float(mu_y), float(sd_y)),
+             "lbm_mlp_set_normalization")
+
+    def forward(self, x):
+        """x: device float32 tensor (batch, n_in) -> device tensor (batch,)."""
+        y = self._torch.empty(x.shape[0], dtype=self._torch.float32, device=x.device)
+        _mck(_lib.lbm_mlp_forward(self.h, C.c_void_p(x.data_ptr()), x.shape[0], C.c_void_p(y.data_ptr())),
+             "lbm_mlp_forward")
+        return y
+
+    def gradients(self, x, y, idx=None):
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_double()
+        n = idx.shape[0] if idx is not None else x.shape[0]
+        _mck(_lib.lbm_mlp_gradients(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                    C.c_void_p(idx.data_ptr() if idx is not None else 0), n, _fp(g),
+                                    C.byref(loss)), "lbm_mlp_gradients")
+        return g, loss.value
+
+    def train_step(self, x, y, idx=None, lr=1e-3, want_loss=False):
+        loss = C.c_double()
+        n = idx.shape[0] if idx is not None else x.shape[0]
+        _mck(_lib.lbm_mlp_train_step(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                     C.c_void_p(idx.data_ptr() if idx is not None else 0), n, float(lr),
+                                     C.byref(loss) if want_loss else None), "lbm_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._torch.cuda.synchronize()
+            _lib.lbm_mlp_destroy(self.h)
             self.h = None
             self.buffer = None
 

@@ -44,3 +44,27 @@ def tgv_fields(lo, hi, scale, n, amplitude, mean=(0.0, 0.0, 0.0)):
     uz = mean[2] + 0 * x
     rho = 1 - 0.75 * amplitude ** 2 * (np.cos(2 * k * x) + np.cos(2 * k * y))
     return rho, np.stack([ux, uy, uz], -1)
+
+
+# ---------------------------------------------------------------- surrogate training cases
+# Single-level 128x64x64 channels (slip side walls) with seeded random trees:
+# trunk 16 cells long, diameter 0.3 of its length, 2-3 generations of 2-3
+# children, branch angle 20-50 deg, length ratio 0.55-0.7, diameter ratio
+# 0.6-0.75, Re_H 80-600 (uniform in log).  Each case runs `steps` updates;
+# forces are averaged over the last `average` of them.
+SURROGATE_DOMAIN = dict(n0=(128, 64, 64), levels=1, block=16, bc=("inout", "slip", "slip"), u_in=0.05)
+SURROGATE_STEPS = dict(steps=4000, average=2000)
+
+
+def surrogate_cases(count, seed):
+    """`count` seeded (tree, Re_H) records for the surrogate's data set."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        tree = dict(n=int(rng.integers(2, 4)), children=int(rng.integers(2, 4)), s0=16.0, w0=4.8,
+                    r=(float(rng.uniform(0.55, 0.7)),), dfac=(float(rng.uniform(0.6, 0.75)),),
+                    alpha_deg=(float(rng.uniform(20.0, 50.0)),), azimuth_mode=1,
+                    seed=int(rng.integers(0, 1 << 30)), trunk_cells=16.0)
+        out.append(dict(tree=tree, re_h=float(np.exp(rng.uniform(np.log(80.0), np.log(600.0))))))
+    return out

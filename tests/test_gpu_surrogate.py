@@ -1,0 +1,192 @@
+"""GPU parity for the branch-wise model's inputs and the surrogate network.
+
+Per-branch forces: the library's per-link momentum-exchange forces reduced
+per branch (FP64, fixed order) against the oracle's, at the bound the total
+force is held to (1e-4 relative).
+
+Network: forward, gradients and Adam of the CUDA kernels (bfloat16 weights,
+FP32 accumulation) against the FP64 oracle with the same rounded weights.
+FP32 accumulation over K <= 128 terms of O(1) products bounds the forward
+error by ~K * 2^-24 relative, about 1e-5; the gradients, two more FP32
+contractions deep, are held to 2e-4 relative (L2 norm over all parameters).
+Adam moves each weight by lr * m / (sqrt(v) + eps), which at the first step
+is lr * sign(g): weights whose gradient is well above the gradient error
+must move identically up to FP32 rounding.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import surrogate as S
+from paper_2603_27954_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_27954_gb300 import lbm
+    return lbm
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+    return torch.cuda.Stream()
+
+
+def oracle_tree(t):
+    return O.make_tree(t["n"], t["children"], t["s0"], t["w0"], t["r"], t["dfac"], alpha_deg=t["alpha_deg"],
+                       azimuth_mode=t["azimuth_mode"], seed=t["seed"])
+
+
+@pytest.mark.parametrize("case,steps", [("tiny", 40), ("amr2_small", 4)])
+def test_branch_forces_match_oracle(L, stream, case, steps):
+    c = W.CASES[case]
+    desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
+                         re_h=c["re_h"])
+    dom = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=stream)
+    dom.set_branch_forces(True)
+    sim, info = O.tree_case(*c["n0"], oracle_tree(c["tree"]), c["tree"]["trunk_cells"], c["re_h"],
+                            u_in=c["u_in"], levels=c["levels"], block=c["block"], bc=c["bc"])
+    dom.step(steps)
+    sim.step(steps)
+    nb = len(info["segments"])
+    fb, cnt = dom.get_branch_forces(nb)
+    ref = sim.branch_forces(nb)
+    _, tot, n = sim.force()
+    assert cnt == n
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(fb, ref, rtol=1e-4, atol=1e-4 * scale)
+    _, mean, _ = dom.drag()
+    np.testing.assert_allclose(fb.sum(axis=0), mean, rtol=0, atol=1e-9 * scale)
+    dom.close()
+
+
+def test_branch_forces_off_by_default_and_reset(L, stream):
+    c = W.CASES["tiny"]
+    desc = L.domain_desc(*c["n0"], levels=1, block=c["block"], bc=c["bc"], u_in=c["u_in"], re_h=c["re_h"])
+    dom = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=stream)
+    dom.step(3)
+    fb, cnt = dom.get_branch_forces(3)
+    assert cnt == 0 and not fb.any()
+    dom.set_branch_forces(True)
+    dom.step(3)
+    dom.reset_force()
+    dom.step(2)
+    assert dom.get_branch_forces(3)[1] == 2
+    dom.close()
+
+
+def make_net(L, n_in, width, hidden, batch, seed, max_batch=None):
+    import torch
+    shapes = S.layer_shapes(n_in, width, hidden)
+    p = S.init_params(shapes, seed)
+    rng = np.random.default_rng(seed + 7)
+    x = (rng.standard_normal((batch, n_in)) * rng.uniform(0.1, 5, n_in) + rng.uniform(-3, 3, n_in))
+    y = np.tanh(x[:, 0] / 3) + 0.1 * x[:, -1] + 0.05 * rng.standard_normal(batch)
+    x, y = x.astype(np.float32), y.astype(np.float32)
+    norm = S.Norm.fit(x, y)
+    net = L.Mlp(n_in, width, hidden, max_batch=max_batch or batch)
+    net.set_params(p)
+    net.set_normalization(norm.mu_x, norm.sd_x, norm.mu_y, norm.sd_y)
+    # the oracle sees exactly the float32 values the GPU holds
+    norm = S.Norm(norm.mu_x.astype(np.float32), norm.sd_x.astype(np.float32), np.float32(norm.mu_y),
+                  np.float32(norm.sd_y))
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.from_numpy(y).cuda()
+    return net, shapes, p.astype(np.float64), x, y, xd, yd, norm
+
+
+@pytest.mark.parametrize("n_in,width,hidden,batch", [(6, 128, 3, 1000), (5, 37, 2, 77), (6, 128, 1, 1)])
+def test_mlp_forward_matches_oracle(L, n_in, width, hidden, batch):
+    net, shapes, p, x, y, xd, yd, norm = make_net(L, n_in, width, hidden, batch, seed=11)
+    out = net.forward(xd).cpu().numpy().astype(np.float64)
+    ref, _ = S.forward(p, shapes, x, norm)
+    np.testing.assert_allclose(out, ref, rtol=2e-5, atol=2e-5 * np.abs(ref).max())
+    net.close()
+
+
+@pytest.mark.parametrize("n_in,width,hidden,batch", [(6, 128, 3, 1000), (5, 37, 2, 77)])
+def test_mlp_gradients_match_oracle(L, n_in, width, hidden, batch):
+    net, shapes, p, x, y, xd, yd, norm = make_net(L, n_in, width, hidden, batch, seed=12)
+    g, loss = net.gradients(xd, yd)
+    lref, gref = S.loss_and_grad(p, shapes, x, y, norm)
+    assert loss == pytest.approx(lref, rel=1e-5)
+    rel = np.linalg.norm(g - gref) / np.linalg.norm(gref)
+    assert rel < 2e-4, rel
+    net.close()
+
+
+def test_mlp_gradients_with_index_gather(L):
+    """A mini-batch given by row indices equals the same rows passed densely."""
+    import torch
+    net, shapes, p, x, y, xd, yd, norm = make_net(L, 6, 64, 2, 300, seed=13)
+    idx = np.random.default_rng(5).permutation(300)[:129].astype(np.int32)
+    g, loss = net.gradients(xd, yd, torch.from_numpy(idx).cuda())
+    lref, gref = S.loss_and_grad(p, shapes, x[idx], y[idx], norm)
+    assert loss == pytest.approx(lref, rel=1e-5)
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) < 2e-4
+    net.close()
+
+
+def test_mlp_adam_steps_match_oracle(L):
+    lr = 1e-3
+    net, shapes, p, x, y, xd, yd, norm = make_net(L, 6, 128, 3, 512, seed=14)
+    _, g0 = S.loss_and_grad(p, shapes, x, y, norm)
+    net.train_step(xd, yd, lr=lr)
+    w1 = net.get_params().astype(np.float64)
+    opt = S.Adam(len(p), lr)
+    r1 = opt.step(p, g0)
+    clear = np.abs(g0) > 1e-2 * np.sqrt(np.mean(g0 * g0))
+    assert clear.mean() > 0.9
+    np.testing.assert_allclose(w1[clear], r1[clear], rtol=0, atol=1e-3 * lr + 1e-7)
+    assert np.abs(w1 - r1).max() <= 2 * lr + 1e-7
+    # a few more steps: the losses follow the oracle's trajectory
+    losses, refs = [], []
+    pr = r1
+    for _ in range(10):
+        losses.append(net.train_step(xd, yd, lr=lr, want_loss=True))
+        lr_, g = S.loss_and_grad(pr, shapes, x, y, norm)
+        refs.append(lr_)
+        pr = opt.step(pr, g)
+    np.testing.assert_allclose(losses, refs, rtol=1e-3)
+    assert losses[-1] < losses[0]
+    net.close()
+
+
+def test_mlp_rejects_bad_arguments(L):
+    import torch
+    net = L.Mlp(6, 32, 1, max_batch=8)
+    x = torch.zeros(9, 6, device="cuda")
+    with pytest.raises(L.MlpError):
+        net.forward(x)  # batch above the bound capacity
+    with pytest.raises(L.MlpError):
+        net.set_params(np.zeros(3, np.float32))
+    with pytest.raises(L.MlpError):
+        net.set_normalization(np.zeros(6), np.zeros(6), 0.0, 1.0)  # zero spread
+    net.close()
+
+
+def test_learned_law_beats_cylinder_law_on_held_out_trees(L, stream):
+    """Train the network on LBM per-branch data of 40 seeded trees, then
+    estimate C_D (Eq. 5) of 10 held-out trees: the learned law is within 3 %
+    of the LBM's C_D on average and closer than the cylinder law."""
+    from paper_2603_27954_gb300 import surrogate as SG
+    cases = W.surrogate_cases(50, seed=2026)
+    samples = [SG.simulate(c, stream=stream) for c in cases]
+    train, held = samples[:40], samples[40:]
+    x, y = SG.dataset(train)
+    net = SG.train(x, y, seed=1)
+    err_nn, err_law = [], []
+    for s in held:
+        c = SG.predict(net, s.rows)
+        err_nn.append(abs(SG.estimate(s.rows, s.area, c) - s.cd) / s.cd)
+        err_law.append(abs(SG.estimate(s.rows, s.area) - s.cd) / s.cd)
+    net.close()
+    print("held-out C_D error: learned %.4f  cylinder law %.4f" % (np.mean(err_nn), np.mean(err_law)))
+    assert np.mean(err_nn) < 0.03
+    assert np.mean(err_nn) < np.mean(err_law)
