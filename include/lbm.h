@@ -202,25 +202,39 @@ int lbm_get_segments(const lbm_domain* d, double* seg, int n, int* count);
    adds each branch's force to a running FP64 sum (deterministic order).
    lbm_get_branch_forces returns, for the n >= number of branches, the mean
    force per branch since the last lbm_reset_force / init (finest-level
-   lattice units, rows x y z) and the number of steps averaged.  The sum over
-   branches equals the total of lbm_drag.  Toggling recaptures the graphs. */
+   lattice units, rows x y z) and the number of steps averaged.  Per link the
+   rest state (rho = 1, u = 0) is subtracted, c_i (f*_i + f_ibar - 2 w_i):
+   one branch's links do not close a surface, so the uniform reference
+   pressure would otherwise enter its force.  Over all cut links of a finite
+   solid sum c_i w_i = 0, so the sum over branches still equals the total of
+   lbm_drag (up to rounding).  Toggling recaptures the graphs. */
 int lbm_set_branch_forces(lbm_domain* d, int on);
 int lbm_get_branch_forces(lbm_domain* d, double* mean_xyz, int n, long long* steps);
 
 /* Branch-wise description of the tree for the analytical model (Sec. 2.4,
    Eq. 3: F_d = C_d (1/2 rho U^2) L D sin^3(alpha)) and its learned sectional
-   drag: one row of 9 doubles per branch, in lbm_get_segments order:
-   log10 Re_d (U D / nu, finest level), generation, D/H, cos(alpha) (alpha =
-   angle between the axis and the flow), inflow turbulence intensity,
-   shielding depth (mean number of other branches met upstream by the
-   x-parallel lines through 16 points of the axis), L, D (finest cells),
-   sin^3(alpha).  n is the capacity in rows, *count the number of branches. */
+   drag: one row of LBM_BRANCH_COLS doubles per branch, in lbm_get_segments
+   order:
+     0 log10 Re_d (U D / nu, finest level)   1 generation   2 D/H
+     3 cos(alpha), alpha in [0, pi] the angle between the flow and the axis
+       drawn from the branch's base to its tip
+     4 inflow turbulence intensity
+     5 shielding depth: mean number of other branches that the stream-wise
+       lines through 16 points of the axis enter upstream of the point
+     6 L   7 D (finest cells)   8 sin^3(alpha)
+     9 shadowed fraction: of 16 axial x 5 lateral points spread over the
+       branch's projected width (offsets -0.4 D .. 0.4 D normal to the axis
+       and the flow), those whose stream-wise line enters another branch
+       more than D/2 upstream
+    10 leaf: 1 if no other branch starts at this branch's tip, else 0
+   n is the capacity in rows, *count the number of branches. */
+#define LBM_BRANCH_COLS 11
 int lbm_branch_table(const lbm_domain* d, double* rows, int n, int* count);
 
 /* Branch-wise drag estimate (Sec. 2.4, Eq. 3 summed as in Eq. 5): with
    c_k = F_d,k / (rho U^2 L_k D_k / 2) the sectional drag coefficient of
    branch k, C_D-est = sum_k c_k L_k D_k / A_x.  rows: n rows of
-   lbm_branch_table (host, 9 doubles each); c_sect: host array of n c_k, or
+   lbm_branch_table (host, LBM_BRANCH_COLS doubles each); c_sect: host array of n c_k, or
    NULL for the cylinder law c_k = C_d(Re_d,k) sin^3(alpha_k) with
    C_d(Re) = 1 + 10 Re^(-2/3) (White's cross-flow cylinder correlation,
    standing in for the paper's fit to measurements); area: A_x in the same

@@ -354,6 +354,12 @@ static void stream_level(orc_sim* s, int l) {
   }
   /* interpolated bounce-back and momentum exchange */
   double F[3] = {0, 0, 0};
+  /* per-branch forces take the gauge form: the rest state (rho = 1, u = 0,
+     f = w) is subtracted from every link, since one branch's links do not
+     close a surface and the uniform reference pressure would not cancel */
+  double wrest[27];
+  const double zero[3] = {0, 0, 0};
+  orc_equilibrium(1.0, zero, wrest);
   for (long k = 0; k < v->nlink; ++k) {
     long id = v->lcell[k];
     int i = v->ldir[k], ib = opp(i);
@@ -370,9 +376,10 @@ static void stream_level(orc_sim* s, int l) {
     F[2] += cz(i) * (fa + out);
     if (l == s->L - 1 && s->Fseg) {
       double* g = s->Fseg + 3 * v->lseg[k];
-      g[0] += cx(i) * (fa + out);
-      g[1] += cy(i) * (fa + out);
-      g[2] += cz(i) * (fa + out);
+      const double gs = fa + out - 2.0 * wrest[i];
+      g[0] += cx(i) * gs;
+      g[1] += cy(i) * gs;
+      g[2] += cz(i) * gs;
     }
   }
   v->F[0] = F[0]; v->F[1] = F[1]; v->F[2] = F[2];

@@ -18,9 +18,10 @@ layers, one linear output, mean-squared-error loss on the standardised
 target, Adam (Kingma & Ba 2015).  The forward pass uses the weights rounded
 to bfloat16 (round to nearest even), as the GPU does; everything else is
 float64 here.  The branch feature table is restated from its definition:
-log10 Re_d, generation, D/H, |cos alpha|, I_u, shielding depth (the mean
-number of other branches met upstream along stream-wise lines through 16
-axis points), L, D, sin^3 alpha.
+log10 Re_d, generation, D/H, cos alpha (signed), I_u, shielding depth (the
+mean number of other branches met upstream along stream-wise lines through
+16 axis points), L, D, sin^3 alpha, the shadowed fraction of the branch's
+silhouette and a leaf flag.
 """
 import math
 
@@ -39,11 +40,12 @@ def cylinder_cd_white(re):
 
 def branch_geometry(seg):
     """L, D and cos(alpha) per branch (segments: x0 y0 z0 x1 y1 z1 D gen),
-    alpha measured from the stream-wise x axis."""
+    alpha in [0, pi] measured from the stream-wise x axis to the axis drawn
+    from the branch's base to its tip."""
     seg = np.asarray(seg, dtype=np.float64)
     d = seg[:, 3:6] - seg[:, 0:3]
     L = np.linalg.norm(d, axis=1)
-    cosa = np.abs(d[:, 0]) / L
+    cosa = d[:, 0] / L
     return L, seg[:, 6], cosa
 
 
@@ -79,20 +81,55 @@ def shielding_depth(seg, k, samples=16):
     return hits / samples
 
 
+def shadowed_fraction(seg, k, axial=16, lateral=(-0.4, -0.2, 0.0, 0.2, 0.4)):
+    """Fraction of points spread over branch k's projected silhouette
+    (`axial` stations along the axis, `lateral` offsets in diameters along
+    the direction normal to the axis and the stream) whose stream-wise line
+    enters another branch more than D/2 upstream of the point."""
+    seg = np.asarray(seg, dtype=np.float64)
+    pr = [cylinders_as_prims(seg[m:m + 1]) for m in range(len(seg))]
+    a, b = seg[k, 0:3], seg[k, 3:6]
+    ax = (b - a) / np.linalg.norm(b - a)
+    w = np.cross(ax, [1.0, 0.0, 0.0])
+    w = w / np.linalg.norm(w) if np.linalg.norm(w) > 1e-9 else np.array([0.0, 1.0, 0.0])
+    D = seg[k, 6]
+    hit = 0
+    for j in range(axial):
+        for s in lateral:
+            p = a + (j + 0.5) / axial * (b - a) + s * D * w
+            start = np.array([0.0, p[1], p[2]])
+            if any(np.isfinite(t) and t < p[0] - 0.5 * D
+                   for t in (prim_ray(pr[m], start, (1.0, 0.0, 0.0)) for m in range(len(seg)) if m != k)):
+                hit += 1
+    return hit / (axial * len(lateral))
+
+
+def is_leaf(seg, k):
+    """No other branch starts at branch k's tip."""
+    seg = np.asarray(seg, dtype=np.float64)
+    tip = seg[k, 3:6]
+    others = np.delete(seg[:, 0:3], k, axis=0)
+    return not np.any(np.abs(others - tip).sum(axis=1) < 1e-9 * (1.0 + np.linalg.norm(seg[k, 3:6] - seg[k, 0:3])))
+
+
 def branch_features(seg, u, nu, height, i_u=0.0):
-    """Rows of 9 per branch in the order stated in the module header."""
+    """Rows of 11 per branch: log10 Re_d, generation, D/H, cos alpha, I_u,
+    shielding depth, L, D, sin^3 alpha, shadowed fraction, leaf flag."""
     L, D, cosa = branch_geometry(seg)
     sin3 = np.sqrt(np.maximum(0.0, 1.0 - cosa * cosa)) ** 3
-    rows = np.zeros((len(L), 9))
+    n = len(L)
+    rows = np.zeros((n, 11))
     rows[:, 0] = np.log10(u * D / nu)
     rows[:, 1] = np.asarray(seg)[:, 7]
     rows[:, 2] = D / height
     rows[:, 3] = cosa
     rows[:, 4] = i_u
-    rows[:, 5] = [shielding_depth(seg, k) for k in range(len(L))]
+    rows[:, 5] = [shielding_depth(seg, k) for k in range(n)]
     rows[:, 6] = L
     rows[:, 7] = D
     rows[:, 8] = sin3
+    rows[:, 9] = [shadowed_fraction(seg, k) for k in range(n)]
+    rows[:, 10] = [1.0 if is_leaf(seg, k) else 0.0 for k in range(n)]
     return rows
 
 

@@ -791,7 +791,7 @@ int lbm_branch_drag_estimate(const double* rows, int n, const double* c_sect, do
   if (!rows || !cd_est || n < 0 || !(area > 0)) return fail(LBM_EINVAL, "bad argument");
   double sum = 0;
   for (int k = 0; k < n; ++k) {
-    const double* r = rows + 9 * (size_t)k;
+    const double* r = rows + LBM_BRANCH_COLS * (size_t)k;
     const double c = c_sect ? c_sect[k] : (1.0 + 10.0 * std::pow(10.0, -2.0 / 3.0 * r[0])) * r[8];
     if (c_out) c_out[k] = c;
     sum += c * r[6] * r[7];

@@ -346,36 +346,77 @@ void prim_bounds(const Prim& p, double lo[3], double hi[3]) {
 // x-parallel line through the point meets upstream of it.
 void branch_table(const Tree& t, double u, double nu, double height, double i_u, std::vector<double>* out) {
   const int n = t.count();
-  out->assign((size_t)n * 9, 0.0);
+  out->assign((size_t)n * LBM_BRANCH_COLS, 0.0);
   const double dir[3] = {1, 0, 0};
+  // does the stream-wise line through p meet another branch m != k that it
+  // enters at x < xmax?  (the line starts on the x = 0 plane)
+  auto upstream = [&](int k, const double p[3], double xmax, int* count) {
+    const double x0[3] = {0.0, p[1], p[2]};
+    int c = 0;
+    for (int m = 0; m < n; ++m) {
+      if (m == k) continue;
+      double t0, t1;
+      if (cylinder_span(&t.seg[8 * m], x0, dir, &t0, &t1) && t0 < xmax) ++c;
+    }
+    if (count) *count = c;
+    return c > 0;
+  };
   for (int k = 0; k < n; ++k) {
     const double* r = &t.seg[8 * k];
     double a[3];
     const double len = seg_unit_axis(r, a);
     const double D = r[6];
-    const double cosa = std::fabs(a[0]);
+    const double cosa = a[0];  // signed: the axis points from the branch's base to its tip
     const double sina = std::sqrt(std::max(0.0, 1.0 - cosa * cosa));
+    // shielding depth: other branches entered upstream along 16 axis points
     double shield = 0;
     for (int j = 0; j < 16; ++j) {
       const double s = (j + 0.5) / 16.0;
       const double p[3] = {r[0] + s * (r[3] - r[0]), r[1] + s * (r[4] - r[1]), r[2] + s * (r[5] - r[2])};
-      const double x0[3] = {0.0, p[1], p[2]};
-      for (int m = 0; m < n; ++m) {
-        if (m == k) continue;
-        double t0, t1;
-        if (cylinder_span(&t.seg[8 * m], x0, dir, &t0, &t1) && t0 < p[0]) shield += 1.0;
+      int c = 0;
+      upstream(k, p, p[0], &c);
+      shield += c;
+    }
+    // shadowed fraction of the silhouette: 16 axial x 5 lateral points across
+    // the projected width (lateral direction normal to the axis and the flow)
+    double w[3] = {0.0, a[2], -a[1]};  // a x e_x
+    const double wn = std::sqrt(w[1] * w[1] + w[2] * w[2]);
+    if (wn > 1e-9) {
+      w[1] /= wn;
+      w[2] /= wn;
+    } else {
+      w[1] = 1.0;
+      w[2] = 0.0;
+    }
+    int shadowed = 0;
+    for (int j = 0; j < 16; ++j) {
+      const double s = (j + 0.5) / 16.0;
+      for (int l = -2; l <= 2; ++l) {
+        const double o = 0.2 * l * D;
+        const double p[3] = {r[0] + s * (r[3] - r[0]) + o * w[0], r[1] + s * (r[4] - r[1]) + o * w[1],
+                             r[2] + s * (r[5] - r[2]) + o * w[2]};
+        if (upstream(k, p, p[0] - 0.5 * D, nullptr)) ++shadowed;
       }
     }
-    double* row = &(*out)[(size_t)9 * k];
+    // leaf: no other branch starts at this branch's tip
+    bool leaf = true;
+    for (int m = 0; m < n && leaf; ++m) {
+      if (m == k) continue;
+      const double* q = &t.seg[8 * m];
+      if (std::fabs(q[0] - r[3]) + std::fabs(q[1] - r[4]) + std::fabs(q[2] - r[5]) < 1e-9 * (1.0 + len)) leaf = false;
+    }
+    double* row = &(*out)[(size_t)LBM_BRANCH_COLS * k];
     row[0] = std::log10(u * D / nu);  // local Reynolds number of the branch
     row[1] = r[7];                    // generation
     row[2] = D / height;
-    row[3] = cosa;                    // cosine of the angle to the flow
+    row[3] = cosa;  // cosine of the angle to the flow
     row[4] = i_u;
     row[5] = shield / 16.0;
     row[6] = len;
     row[7] = D;
     row[8] = sina * sina * sina;
+    row[9] = shadowed / 80.0;
+    row[10] = leaf ? 1.0 : 0.0;
   }
 }
 

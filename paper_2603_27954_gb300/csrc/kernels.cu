@@ -553,10 +553,12 @@ __global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const
     Fx = dcx(i) * s;
     Fy = dcy(i) * s;
     Fz = dcz(i) * s;
+    // per-link force in gauge form (rest state f = w subtracted): a branch's
+    // links do not close a surface, so the reference pressure must not enter
     if (link_force) {
-      link_force[3 * (size_t)t] = Fx;
-      link_force[3 * (size_t)t + 1] = Fy;
-      link_force[3 * (size_t)t + 2] = Fz;
+      link_force[3 * (size_t)t] = dcx(i) * sum;
+      link_force[3 * (size_t)t + 1] = dcy(i) * sum;
+      link_force[3 * (size_t)t + 2] = dcz(i) * sum;
     }
   }
   block_sum3<kWallThreads>(Fx, Fy, Fz);

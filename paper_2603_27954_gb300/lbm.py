@@ -18,6 +18,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_ETIMEO
 BC = {"periodic": 0, "inout": 1, "slip": 2, "inflow": 3}
 LBM_FP32 = 1
 LBM_FP16_DEV = 2
+BRANCH_COLS = 11  # columns of lbm_branch_table
 
 
 class DomainDesc(C.Structure):
@@ -266,7 +267,7 @@ def lbm_branch_drag_estimate(rows, area, c_sect=None):
     c_out = np.zeros(max(1, n))
     cs = None if c_sect is None else np.ascontiguousarray(c_sect, dtype=np.float64)
     cd = C.c_double()
-    _ck(_lib.lbm_branch_drag_estimate(_dp(rows) if n else _dp(np.zeros(9)), n, _dp(cs) if cs is not None else None,
+    _ck(_lib.lbm_branch_drag_estimate(_dp(rows) if n else _dp(np.zeros(BRANCH_COLS)), n, _dp(cs) if cs is not None else None,
                                       float(area), C.byref(cd), _dp(c_out)), "lbm_branch_drag_estimate")
     return cd.value, c_out[:n]
 
@@ -274,7 +275,7 @@ def lbm_branch_drag_estimate(rows, area, c_sect=None):
 def lbm_branch_table(h):
     n = C.c_int()
     _ck(_lib.lbm_branch_table(h, None, 0, C.byref(n)), "lbm_branch_table")
-    out = np.zeros((max(1, n.value), 9))
+    out = np.zeros((max(1, n.value), BRANCH_COLS))
     _ck(_lib.lbm_branch_table(h, _dp(out), max(1, n.value), C.byref(n)), "lbm_branch_table")
     return out[:n.value]
 

@@ -5,9 +5,9 @@ cylinder law C_d(Re) fitted to measurements (Eq. 5).  Here the per-branch
 law is learned from the LBM itself: every simulated tree yields, per branch,
 the features of lbm_branch_table and the measured sectional coefficient
 c_k = F_x,k / (rho U^2 L_k D_k / 2) (per-branch momentum-exchange forces,
-lbm_get_branch_forces).  A 6-input network (log10 Re_d, generation, D/H,
-|cos alpha|, I_u, shielding depth) trained by the library's kernels
-predicts c_k, and Eq. 5 turns the predictions into C_D-est.
+lbm_get_branch_forces).  A 6-input network (log10 Re_d, D/H, cos alpha,
+shielding depth, shadowed fraction, leaf flag) trained by the library's
+kernels predicts c_k, and Eq. 5 turns the predictions into C_D-est.
 
 Everything numeric runs in liblbm (simulation, feature table, network
 kernels, Eq. 5); this module only sequences the calls.
@@ -17,7 +17,9 @@ import numpy as np
 from . import lbm as L
 from . import workloads as W
 
-N_FEATURES = 6  # leading columns of the branch table used as inputs
+# branch-table columns used as network inputs: log10 Re_d, D/H, cos alpha,
+# shielding depth, shadowed fraction, leaf flag
+FEATURES = (0, 2, 3, 5, 9, 10)
 
 
 class Sample:
@@ -57,7 +59,7 @@ def simulate(case, stream=None, domain=None, steps=None, average=None):
 def dataset(samples):
     """Stack the branch rows of several samples: inputs (float32, n x 6) and
     targets (float32, n)."""
-    x = np.concatenate([s.rows[:, :N_FEATURES] for s in samples]).astype(np.float32)
+    x = np.concatenate([s.rows[:, FEATURES] for s in samples]).astype(np.float32)
     y = np.concatenate([s.c for s in samples]).astype(np.float32)
     return x, y
 
@@ -69,7 +71,7 @@ def standardisation(x, y):
     return x.mean(axis=0), sd, float(y.mean()), float(y.std()) or 1.0
 
 
-def train(x, y, width=128, hidden=3, steps=3000, batch=256, lr=1e-3, seed=0, stream=None):
+def train(x, y, width=128, hidden=3, steps=2000, batch=256, lr=3e-4, seed=0, stream=None):
     """Fit the network to (x, y) with mini-batch Adam; returns the Mlp."""
     import torch
     n = len(y)
@@ -100,7 +102,7 @@ def train(x, y, width=128, hidden=3, steps=3000, batch=256, lr=1e-3, seed=0, str
 def predict(net, rows):
     """Sectional coefficients predicted for the branches of a branch table."""
     import torch
-    x = torch.from_numpy(np.ascontiguousarray(rows[:, :N_FEATURES], dtype=np.float32)).cuda()
+    x = torch.from_numpy(np.ascontiguousarray(rows[:, FEATURES], dtype=np.float32)).cuda()
     return net.forward(x).cpu().numpy().astype(np.float64)
 
 

@@ -41,6 +41,25 @@ def test_inclination_factor(alpha_deg, factor):
     assert F[0] == pytest.approx(factor * 0.5 * 0.01 * 10.0 * 2.0, abs=1e-15)
 
 
+def test_shadowed_fraction_and_leaf_flag():
+    D = 4.0
+    # tandem: the downstream branch lies fully in the upstream one's shadow
+    tandem = np.array([[10, 10, 0, 10, 10, 20, D, 0], [30, 10, 0, 30, 10, 20, D, 0]], float)
+    assert S.shadowed_fraction(tandem, 1) == 1.0 and S.shadowed_fraction(tandem, 0) == 0.0
+    # offset sideways by 0.625 D: the lateral points at -0.4 D and -0.2 D of
+    # the downstream branch (2 of 5, y = 10.9 and 11.7) lie behind the
+    # upstream cylinder (|y - 10| < 2)
+    half = np.array([[10, 10, 0, 10, 10, 20, D, 0], [30, 12.5, 0, 30, 12.5, 20, D, 0]], float)
+    assert S.shadowed_fraction(half, 1) == pytest.approx(0.4)
+    # an overlapping body whose front face is not ahead of the branch's own
+    # front face (x - D/2) casts no shadow on it
+    touch = np.array([[10, 10, 0, 10, 10, 20, D, 0], [9.9, 10, 0, 9.9, 10, 20, D, 0]], float)
+    assert S.shadowed_fraction(touch, 1) == 0.0
+    # a two-generation fork: the trunk carries children, the children are leaves
+    fork = np.array([[0, 0, 0, 0, 0, 10, 2, 0], [0, 0, 10, 3, 0, 15, 1, 1], [0, 0, 10, -3, 0, 15, 1, 1]], float)
+    assert [S.is_leaf(fork, k) for k in range(3)] == [False, True, True]
+
+
 def test_shielding_depth_tandem_and_side_by_side():
     D = 4.0
     tandem = np.array([[10, 10, 0, 10, 10, 20, D, 0], [30, 10, 0, 30, 10, 20, D, 0]], float)
@@ -65,8 +84,10 @@ def test_library_branch_table_matches_oracle(case):
     tab = L.lbm_branch_table(h)
     ref = S.branch_features(seg, c["u_in"], g["nu_finest"], g["H"])
     L.lbm_destroy(h)
-    assert tab.shape == ref.shape == (len(seg), 9)
-    np.testing.assert_array_equal(tab[:, 5], ref[:, 5])  # shielding: integer counts / 16
+    assert tab.shape == ref.shape == (len(seg), L.BRANCH_COLS)
+    # counts of ray hits and the leaf flag are integer data
+    for col in (5, 9, 10):
+        np.testing.assert_array_equal(tab[:, col], ref[:, col])
     np.testing.assert_allclose(tab, ref, rtol=1e-12, atol=1e-13)
 
 
@@ -194,3 +215,21 @@ def test_library_branch_estimate_matches_oracle(case):
     assert cd2 == pytest.approx(np.sum(given * Lk * Dk) / g["A_x"], rel=1e-12)
     with pytest.raises(L.LbmError):
         L.lbm_branch_drag_estimate(rows, 0.0)
+
+
+def test_oracle_branch_forces_vanish_at_rest():
+    """Fluid at rest at the reference density: every population stays w_i,
+    so each branch's gauge-form force is zero (a plain momentum exchange
+    would leave each open branch surface with a net reference-pressure force)."""
+    c = W.CASES["tiny"]
+    t = c["tree"]
+    tree = O.make_tree(t["n"], t["children"], t["s0"], t["w0"], t["r"], t["dfac"], alpha_deg=t["alpha_deg"],
+                       azimuth_mode=t["azimuth_mode"], seed=t["seed"])
+    sim, info = O.tree_case(*c["n0"], tree, t["trunk_cells"], c["re_h"], u_in=0.0, levels=1,
+                            block=c["block"], bc=("periodic",) * 3)
+    sim.init_uniform(1.0, np.zeros(3))
+    sim.step(3)
+    fb = sim.branch_forces(len(info["segments"]))
+    assert np.abs(fb).max() < 1e-15
+    _, tot, _ = sim.force()
+    assert np.abs(tot).max() < 1e-13
