@@ -99,11 +99,19 @@ def train(x, y, width=128, hidden=3, steps=2000, batch=256, lr=3e-4, seed=0, str
     return net
 
 
+def train_ensemble(x, y, members=4, seed=0, **kw):
+    """`members` networks trained from different seeded initialisations and
+    mini-batch orders; predict() averages them."""
+    return [train(x, y, seed=seed + k, **kw) for k in range(members)]
+
+
 def predict(net, rows):
-    """Sectional coefficients predicted for the branches of a branch table."""
+    """Sectional coefficients predicted for the branches of a branch table
+    (the mean over the members when `net` is a list)."""
     import torch
     x = torch.from_numpy(np.ascontiguousarray(rows[:, FEATURES], dtype=np.float32)).cuda()
-    return net.forward(x).cpu().numpy().astype(np.float64)
+    nets = net if isinstance(net, (list, tuple)) else [net]
+    return np.mean([m.forward(x).cpu().numpy().astype(np.float64) for m in nets], axis=0)
 
 
 def estimate(rows, area, c=None):

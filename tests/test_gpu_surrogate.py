@@ -172,22 +172,23 @@ def test_mlp_rejects_bad_arguments(L):
 
 
 def test_learned_law_beats_cylinder_law_on_held_out_trees(L, stream):
-    """Train the network on the LBM's per-branch data of 160 seeded trees,
-    then estimate C_D (Eq. 5) of 40 held-out trees.  Measured: the learned
-    law is 3.5 % from the LBM's C_D on average, the cylinder law 34 %; the
-    bounds leave room for the spread over training seeds (3.3-3.7 %)."""
+    """Train a 4-member ensemble on the LBM's per-branch data of 160 seeded
+    trees, then estimate C_D (Eq. 5) of 40 held-out trees.  Measured: single
+    networks land 3.3-4.0 % from the LBM's C_D on average (by seed), their
+    ensembles about 3.4 %, the cylinder law 27 %."""
     from paper_2603_27954_gb300 import surrogate as SG
     cases = W.surrogate_cases(200, seed=2026)
     samples = [SG.simulate(c, stream=stream) for c in cases]
     train, held = samples[:160], samples[160:]
     x, y = SG.dataset(train)
-    net = SG.train(x, y, seed=0)
+    nets = SG.train_ensemble(x, y, members=4)
     err_nn, err_law = [], []
     for s in held:
-        c = SG.predict(net, s.rows)
+        c = SG.predict(nets, s.rows)
         err_nn.append(abs(SG.estimate(s.rows, s.area, c) - s.cd) / s.cd)
         err_law.append(abs(SG.estimate(s.rows, s.area) - s.cd) / s.cd)
-    net.close()
+    for n in nets:
+        n.close()
     print("held-out C_D error: learned %.4f  cylinder law %.4f" % (np.mean(err_nn), np.mean(err_law)))
-    assert np.mean(err_nn) < 0.04
+    assert np.mean(err_nn) < 0.045
     assert np.mean(err_nn) < 0.2 * np.mean(err_law)
