@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 
 CASE = "amr2"
 SMALL = "amr2_small"
+PRECISION_CASE = "amr4"
 BYTES_PER_UPDATE = 2 * 27 * 4  # read and write 27 FP32 populations
 KERNEL_SOURCES = ["paper_2603_27954_gb300/csrc/kernels.cu", "paper_2603_27954_gb300/csrc/cumulant.cuh"]
 
@@ -77,10 +78,11 @@ def workload_desc(L, W, case, precision=None):
     return desc, L.tree_desc(**c["tree"]), c
 
 
-def fp16_form(L, W, torch, stream, steps, warmup, fp32_value, peak):
-    """The FP16-deviation storage form on the same workload: MLUPS, its
-    collide roofline at 108 B per update, and the speed-up over FP32."""
-    desc, tree, _ = workload_desc(L, W, CASE, L.LBM_FP16_DEV)
+def measure_form(L, W, torch, stream, case, precision, steps, warmup, timing_steps=20):
+    """Whole-path MLUPS of one workload in one storage form (CUDA events on
+    the domain's stream), the collide kernels' algorithmic GB/s from the
+    library's per-class timing, and the C_D after the timed steps."""
+    desc, tree, _ = workload_desc(L, W, case, precision)
     dom = L.Domain(desc, tree=tree, stream=stream)
     updates, _ = dom.work_per_step()
     dom.step(warmup)
@@ -92,18 +94,52 @@ def fp16_form(L, W, torch, stream, steps, warmup, fp32_value, peak):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    value = updates * steps / (ms / 1e3) / 1e6
     dom.set_timing(True)
-    dom.step(20)
+    dom.step(timing_steps)
     kms, _, kunits = dom.get_timing()
     dom.set_timing(False)
-    gbs = (kunits[0] + kunits[1]) * 108 / ((kms[0] + kms[1]) / 1e3) / 1e9
+    bpu = 108 if precision == L.LBM_FP16_DEV else BYTES_PER_UPDATE
+    gbs = (kunits[0] + kunits[1]) * bpu / ((kms[0] + kms[1]) / 1e3) / 1e9
     _, _, cd = dom.drag()
+    cells = sum(L.lbm_level_info(dom.h, l)["n_fluid"] for l in range(desc.levels))
+    gb = dom.nbytes / 1e9
     dom.close()
-    return {"value": value, "unit": "MLUPS", "speedup_vs_fp32": value / fp32_value, "ms_per_step": ms / steps,
+    torch.cuda.empty_cache()
+    return {"value": updates * steps / (ms / 1e3) / 1e6, "ms_per_step": ms / steps, "collide_gbs": gbs,
+            "bytes_per_update": bpu, "cd": cd, "updates_per_step": updates, "cells": cells, "device_gb": gb}
+
+
+def fp16_form(L, W, torch, stream, steps, warmup, fp32_value, peak):
+    """The FP16-deviation storage form on the same workload: MLUPS, its
+    collide roofline at 108 B per update, and the speed-up over FP32."""
+    r = measure_form(L, W, torch, stream, CASE, L.LBM_FP16_DEV, steps, warmup)
+    return {"value": r["value"], "unit": "MLUPS", "speedup_vs_fp32": r["value"] / fp32_value,
+            "ms_per_step": r["ms_per_step"],
             "dtype": "f16 storage of (f - w) * 2^13, f32 collision, f64 reductions",
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                         "bytes_per_update": 108}, "cd": cd}
+            "roofline": {"bound": "hbm", "achieved": r["collide_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": r["collide_gbs"] / peak, "bytes_per_update": 108}, "cd": r["cd"]}
+
+
+def precision_form(L, W, torch, stream, steps, warmup, peak):
+    """The four-level precision-form workload (about 6e8 active cells) in
+    FP32 and FP16-deviation storage."""
+    c = W.CASES[PRECISION_CASE]
+    out = {"workload": "four-level tree drag: coarse %dx%dx%d in %d^3 blocks, L-system n=%d x %d children, "
+                       "trunk %d finest cells, Re_H=%g, U=%g" % (*c["n0"], c["block"], c["tree"]["n"],
+                                                                c["tree"]["children"], c["tree"]["trunk_cells"],
+                                                                c["re_h"], c["u_in"]),
+           "steps": steps, "warmup": warmup, "unit": "MLUPS"}
+    for name, prec in (("fp32", L.LBM_FP32), ("fp16", L.LBM_FP16_DEV)):
+        r = measure_form(L, W, torch, stream, PRECISION_CASE, prec, steps, warmup, timing_steps=2)
+        out[name] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "cd": r["cd"],
+                     "roofline": {"bound": "hbm", "achieved": r["collide_gbs"], "peak": peak, "unit": "GB/s",
+                                  "frac": r["collide_gbs"] / peak, "bytes_per_update": r["bytes_per_update"]},
+                     "device_gb": r["device_gb"]}
+        out["cells"] = r["cells"]
+        out["updates_per_step"] = r["updates_per_step"]
+    out["speedup_fp16_vs_fp32"] = out["fp16"]["value"] / out["fp32"]["value"]
+    out["cd_rel_diff_fp16_vs_fp32"] = abs(out["fp16"]["cd"] - out["fp32"]["cd"]) / abs(out["fp32"]["cd"])
+    return out
 
 
 class Clocks:
@@ -219,6 +255,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
+    ap.add_argument("--no-precision-form", action="store_true")
+    ap.add_argument("--precision-steps", type=int, default=10)
     ap.add_argument("--timing-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=50)
     args = ap.parse_args()
@@ -316,6 +354,9 @@ def main():
     fp16 = None
     if not args.no_fp16:
         fp16 = fp16_form(L, W, torch, stream, args.steps, args.warmup, value, peak)
+    prec_form = None
+    if not args.no_precision_form:
+        prec_form = precision_form(L, W, torch, stream, args.precision_steps, 3, peak)
 
     cpu = None
     cd_err = None
@@ -359,6 +400,7 @@ def main():
                 "d2h_bytes_per_step": 64,
                 "note": "includes binding (table upload and equilibrium initialisation of %.2f GB) once and a "
                         "synchronous drag read after each of %d steps" % (dom.nbytes / 1e9, args.e2e_steps)},
+        "precision_form": prec_form,
         "gpu_launches": kernels * args.steps,
         "kernels_per_step": kernels,
         "cd": cd,

@@ -279,6 +279,12 @@ int lbm_mlp_train_step(lbm_mlp* m, const float* x, const float* y, const int* id
 const char* lbm_mlp_last_error(void);
 void lbm_mlp_destroy(lbm_mlp* m);
 
+/* Run the collide kernels with 64-bit element offsets even on levels whose
+   arrays hold fewer than 2^31 elements (they switch to 64-bit offsets by
+   themselves above that), so that small cases exercise the large-array
+   code; results are identical.  Toggling recaptures the graphs. */
+int lbm_set_wide_offsets(lbm_domain* d, int on);
+
 /* Every `every` coarse steps lbm_step checks for NaN/Inf and densities
    outside [0.5, 2] (synchronising); 0 disables (default). */
 int lbm_set_watchdog(lbm_domain* d, int every);

@@ -52,7 +52,7 @@ def build(force=False, verbose=False, extra_nvcc=()):
     jobs = []
     for s in HOST_SRC:
         o = os.path.join(BUILD, s + ".o")
-        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-c", os.path.join(CSRC, s), "-o", o] + inc)
+        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-c", os.path.join(CSRC, s), "-o", o] + inc)
     for s in CUDA_SRC:
         o = os.path.join(BUILD, s + ".o")
         jobs.append([nvcc] + ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-c",
@@ -72,7 +72,7 @@ def build(force=False, verbose=False, extra_nvcc=()):
                 print(o)
     objs = [os.path.join(BUILD, s + ".o") for s in HOST_SRC + CUDA_SRC]
     tmp = OUT + ".tmp.%d" % os.getpid()
-    run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs)
+    run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-Xcompiler", "-pthread", "-o", tmp] + objs + ["-lpthread"])
     os.replace(tmp, OUT)
     return OUT
 

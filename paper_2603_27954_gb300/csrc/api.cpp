@@ -64,6 +64,7 @@ struct lbm_domain {
   size_t off_linkf = 0, off_segb = 0, off_segacc = 0;  // per-branch forces (finest level)
   int n_seg = 0;
   bool branch_forces = false;
+  bool wide_offsets = false;  // force the 64-bit-offset collide kernels
   int max_wall_parts = 0;
   float feq_in[27];
   int parity0 = 0;
@@ -138,7 +139,8 @@ int advance(lbm_domain* dm, int l, int parity) {
     Timed t(dm, parity ? KC_COLLIDE_ODD : KC_COLLIDE, v.n_fluid);
     CollideArgs a{f, (long long)v.f_elems(), dm->dev<int>(v.off_nbr), dm->dev<int>(v.off_maskoff),
                   dm->dev<uint8_t>(v.off_masks), v.n_active, (float)v.omega1, (float)dm->d.omega2,
-                  dm->d.galilean, dm->dev<double>(dm->off_accum) + 7, v.esize == 2, v.scale, 1.0f / v.scale};
+                  dm->d.galilean, dm->dev<double>(dm->off_accum) + 7, v.esize == 2, v.scale, 1.0f / v.scale,
+                  dm->wide_offsets ? 1 : 0};
     if ((rc = launch_collide(a, v.B, parity, dm->stream))) return rc;
   }
   if (l == 0 && !v.face[parity].empty()) {
@@ -797,6 +799,13 @@ int lbm_branch_drag_estimate(const double* rows, int n, const double* c_sect, do
     sum += c * r[6] * r[7];
   }
   *cd_est = sum / area;
+  return LBM_OK;
+}
+
+int lbm_set_wide_offsets(lbm_domain* d, int on) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (d->wide_offsets != (on != 0)) free_graphs(d);
+  d->wide_offsets = on != 0;
   return LBM_OK;
 }
 

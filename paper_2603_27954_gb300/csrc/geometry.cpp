@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "parallel.h"
 
 namespace lbm {
 namespace {
@@ -232,27 +233,41 @@ double frontal_area(const Tree& t, double pitch) {
   long j0 = (long)std::floor(lo[1] / pitch) - 1, j1 = (long)std::ceil(hi[1] / pitch) + 1;
   long k0 = (long)std::floor(lo[2] / pitch) - 1, k1 = (long)std::ceil(hi[2] / pitch) + 1;
   long nj = j1 - j0 + 1, nk = k1 - k0 + 1;
-  std::vector<uint8_t> hit((size_t)(nj * nk), 0);
   const double dir[3] = {1, 0, 0};
-  for (int s = 0; s < t.count(); ++s) {
-    const double* r = &t.seg[8 * s];
+  const int n = t.count();
+  std::vector<long> box((size_t)4 * n);  // pixel ranges ja, jb, ka, kb per branch
+  for (int s = 0; s < n; ++s) {
     Prim p{0, {}};
-    std::copy(r, r + 8, p.p);
+    std::copy(&t.seg[8 * s], &t.seg[8 * s] + 8, p.p);
     double a[3], b[3];
     prim_bounds(p, a, b);
-    long ja = std::max(j0, (long)std::floor(a[1] / pitch) - 1), jb = std::min(j1, (long)std::ceil(b[1] / pitch) + 1);
-    long ka = std::max(k0, (long)std::floor(a[2] / pitch) - 1), kb = std::min(k1, (long)std::ceil(b[2] / pitch) + 1);
-    for (long k = ka; k <= kb; ++k)
-      for (long j = ja; j <= jb; ++j) {
-        uint8_t& h = hit[(size_t)((k - k0) * nj + (j - j0))];
+    box[4 * s] = std::max(j0, (long)std::floor(a[1] / pitch) - 1);
+    box[4 * s + 1] = std::min(j1, (long)std::ceil(b[1] / pitch) + 1);
+    box[4 * s + 2] = std::max(k0, (long)std::floor(a[2] / pitch) - 1);
+    box[4 * s + 3] = std::min(k1, (long)std::ceil(b[2] / pitch) + 1);
+  }
+  // one pixel row (fixed k) per task; a pixel counts once whatever covers it
+  std::vector<long> row_count((size_t)nk, 0);
+  parallel_for(nk, [&](long long kr) {
+    const long k = k0 + (long)kr;
+    std::vector<uint8_t> hit((size_t)nj, 0);
+    for (int s = 0; s < n; ++s) {
+      if (k < box[4 * s + 2] || k > box[4 * s + 3]) continue;
+      const double* r = &t.seg[8 * s];
+      for (long j = box[4 * s]; j <= box[4 * s + 1]; ++j) {
+        uint8_t& h = hit[(size_t)(j - j0)];
         if (h) continue;
         double x[3] = {0.0, (j + 0.5) * pitch, (k + 0.5) * pitch};
         double t0, t1;
         if (cylinder_span(r, x, dir, &t0, &t1)) h = 1;
       }
-  }
+    }
+    long c = 0;
+    for (uint8_t h : hit) c += h;
+    row_count[(size_t)kr] = c;
+  }, 4);
   long count = 0;
-  for (uint8_t h : hit) count += h;
+  for (long c : row_count) count += c;
   return (double)count * pitch * pitch;
 }
 

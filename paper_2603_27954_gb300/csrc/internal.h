@@ -155,6 +155,7 @@ struct CollideArgs {
   double* err;        // set to 1 when a bounded device wait gives up
   int half;           // FP16 storage of scaled deviations
   float scale, inv_scale;
+  int wide;           // 64-bit element offsets even when f_elems < 2^31
 };
 int prepare_kernels();
 int launch_collide(const CollideArgs& a, int B, int odd, void* stream);

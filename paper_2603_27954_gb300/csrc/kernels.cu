@@ -797,7 +797,7 @@ void collide_on(const CollideArgs& a, int odd, cudaStream_t s) {
 
 template <typename S>
 void collide_typed(const CollideArgs& a, int B, int odd, cudaStream_t s) {
-  const bool small = a.f_elems < (1LL << 31);
+  const bool small = !a.wide && a.f_elems < (1LL << 31);
   if (B == 16) {
     if (small) collide_on<16, int, S>(a, odd, s);
     else collide_on<16, long long, S>(a, odd, s);

@@ -16,12 +16,14 @@
 // (x + c_i, i) and the next step expects f_i(x) in (x, i).  Every table
 // below is a list of (destination slot, source slots) pairs per parity.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <limits>
 #include <unordered_map>
 
 #include "internal.h"
+#include "parallel.h"
 
 namespace lbm {
 namespace {
@@ -138,37 +140,36 @@ int layout_level(Mesh& m, int l) {
   const int B = v.B;
   size_t ng = (size_t)v.nb[0] * v.nb[1] * v.nb[2];
   std::vector<int8_t> state(ng, ABSENT);
-  for (int bz = 0; bz < v.nb[2]; ++bz)
-    for (int by = 0; by < v.nb[1]; ++by)
-      for (int bx = 0; bx < v.nb[0]; ++bx) {
-        size_t gi = ((size_t)bz * v.nb[1] + by) * v.nb[0] + bx;
-        int o[3] = {v.org[0] + bx * B, v.org[1] + by * B, v.org[2] + bz * B};
-        bool any = false;
-        for (int z = 0; z < B && !any; ++z)
-          for (int y = 0; y < B && !any; ++y)
-            for (int x = 0; x < B && !any; ++x)
-              if (live(m, l, o[0] + x, o[1] + y, o[2] + z)) any = true;
-        if (any) state[gi] = ACTIVE;
-      }
-  for (int bz = 0; bz < v.nb[2]; ++bz)
-    for (int by = 0; by < v.nb[1]; ++by)
-      for (int bx = 0; bx < v.nb[0]; ++bx) {
-        size_t gi = ((size_t)bz * v.nb[1] + by) * v.nb[0] + bx;
-        if (state[gi] != ABSENT) continue;
-        bool near = false;
-        for (int dz = -1; dz <= 1 && !near; ++dz)
-          for (int dy = -1; dy <= 1 && !near; ++dy)
-            for (int dx = -1; dx <= 1 && !near; ++dx) {
-              int n[3] = {bx + dx, by + dy, bz + dz};
-              bool ok = true;
-              for (int a = 0; a < 3; ++a) {
-                if (v.wrap[a]) n[a] = wrapmod(n[a], v.nb[a]);
-                if (n[a] < 0 || n[a] >= v.nb[a]) ok = false;
-              }
-              if (ok && state[((size_t)n[2] * v.nb[1] + n[1]) * v.nb[0] + n[0]] == ACTIVE) near = true;
-            }
-        if (near) state[gi] = GHOST;
-      }
+  parallel_for((long long)ng, [&](long long gi) {
+    const int bx = (int)(gi % v.nb[0]), by = (int)((gi / v.nb[0]) % v.nb[1]), bz = (int)(gi / ((size_t)v.nb[0] * v.nb[1]));
+    int o[3] = {v.org[0] + bx * B, v.org[1] + by * B, v.org[2] + bz * B};
+    bool any = false;
+    for (int z = 0; z < B && !any; ++z)
+      for (int y = 0; y < B && !any; ++y)
+        for (int x = 0; x < B && !any; ++x)
+          if (live(m, l, o[0] + x, o[1] + y, o[2] + z)) any = true;
+    if (any) state[gi] = ACTIVE;
+  }, 64);
+  std::vector<int8_t> ghost(ng, 0);
+  parallel_for((long long)ng, [&](long long gi) {
+    if (state[gi] != ABSENT) return;
+    const int bx = (int)(gi % v.nb[0]), by = (int)((gi / v.nb[0]) % v.nb[1]), bz = (int)(gi / ((size_t)v.nb[0] * v.nb[1]));
+    bool near = false;
+    for (int dz = -1; dz <= 1 && !near; ++dz)
+      for (int dy = -1; dy <= 1 && !near; ++dy)
+        for (int dx = -1; dx <= 1 && !near; ++dx) {
+          int n[3] = {bx + dx, by + dy, bz + dz};
+          bool ok = true;
+          for (int a = 0; a < 3; ++a) {
+            if (v.wrap[a]) n[a] = wrapmod(n[a], v.nb[a]);
+            if (n[a] < 0 || n[a] >= v.nb[a]) ok = false;
+          }
+          if (ok && state[((size_t)n[2] * v.nb[1] + n[1]) * v.nb[0] + n[0]] == ACTIVE) near = true;
+        }
+    if (near) ghost[gi] = 1;
+  }, 256);
+  for (size_t gi = 0; gi < ng; ++gi)
+    if (ghost[gi]) state[gi] = GHOST;
   std::vector<std::pair<uint64_t, int>> act, gho;
   for (size_t gi = 0; gi < ng; ++gi) {
     int bx = (int)(gi % v.nb[0]), by = (int)((gi / v.nb[0]) % v.nb[1]), bz = (int)(gi / ((size_t)v.nb[0] * v.nb[1]));
@@ -185,7 +186,7 @@ int layout_level(Mesh& m, int l) {
   v.n_storage = (int)v.grid_of.size();
   const long long cpb = v.cells_per_block();
   v.type.assign((size_t)v.n_storage * cpb, OUTSIDE);
-  for (int s = 0; s < v.n_storage; ++s) {
+  parallel_for(v.n_storage, [&](long long s) {
     int o[3];
     block_origin(v, v.grid_of[s], o);
     for (int z = 0; z < B; ++z)
@@ -194,7 +195,7 @@ int layout_level(Mesh& m, int l) {
           int gx = o[0] + x, gy = o[1] + y, gz = o[2] + z;
           v.type[(size_t)s * cpb + (z * B + y) * B + x] = base_type(m, l, gx, gy, gz);
         }
-  }
+  }, 16);
   // neighbour table of active blocks
   v.nbr.assign((size_t)v.n_active * kQ, -1);
   for (int s = 0; s < v.n_active; ++s) {
@@ -227,11 +228,10 @@ int classify_solids(Mesh& m, int l, const std::vector<Prim>& prims) {
   const double h = std::ldexp(1.0, m.L - 1 - l);
   std::vector<double> plo(prims.size() * 3), phi(prims.size() * 3);
   for (size_t k = 0; k < prims.size(); ++k) prim_bounds(prims[k], &plo[3 * k], &phi[3 * k]);
-  std::vector<int> cand;
-  for (int s = 0; s < v.n_active; ++s) {
+  parallel_for(v.n_active, [&](long long s) {
     int o[3];
     block_origin(v, v.grid_of[s], o);
-    cand.clear();
+    std::vector<int> cand;
     for (size_t k = 0; k < prims.size(); ++k) {
       bool hit = true;
       for (int a = 0; a < 3; ++a) {
@@ -240,7 +240,7 @@ int classify_solids(Mesh& m, int l, const std::vector<Prim>& prims) {
       }
       if (hit) cand.push_back((int)k);
     }
-    if (cand.empty()) continue;
+    if (cand.empty()) return;
     for (int z = 0; z < B; ++z)
       for (int y = 0; y < B; ++y)
         for (int x = 0; x < B; ++x) {
@@ -253,7 +253,7 @@ int classify_solids(Mesh& m, int l, const std::vector<Prim>& prims) {
               break;
             }
         }
-  }
+  }, 4);
   return LBM_OK;
 }
 
@@ -263,9 +263,24 @@ int build_links(Mesh& m, int l, const std::vector<Prim>& prims) {
   const long long cpb = v.cells_per_block();
   const double h = std::ldexp(1.0, m.L - 1 - l);
   v.links.clear();
-  for (int s = 0; s < v.n_active; ++s) {
+  std::vector<double> plo(prims.size() * 3), phi(prims.size() * 3);
+  for (size_t k = 0; k < prims.size(); ++k) prim_bounds(prims[k], &plo[3 * k], &phi[3 * k]);
+  std::vector<std::vector<Link>> per_block(v.n_active);
+  parallel_for(v.n_active, [&](long long s) {
     int o[3];
     block_origin(v, v.grid_of[s], o);
+    // primitives that can hold the entry point of a link of this block: the
+    // link segment lies within one cell of the block
+    std::vector<int> cand;
+    for (size_t k = 0; k < prims.size(); ++k) {
+      bool hit = true;
+      for (int a = 0; a < 3; ++a) {
+        double lo = o[a] * h - h, hi = (o[a] + B) * h + h;
+        if (phi[3 * k + a] < lo || plo[3 * k + a] > hi) hit = false;
+      }
+      if (hit) cand.push_back((int)k);
+    }
+    std::vector<Link>& out = per_block[s];
     for (int z = 0; z < B; ++z)
       for (int y = 0; y < B; ++y)
         for (int x = 0; x < B; ++x) {
@@ -279,11 +294,11 @@ int build_links(Mesh& m, int l, const std::vector<Prim>& prims) {
             double dd[3] = {cx(i) * h, cy(i) * h, cz(i) * h};
             double q = std::numeric_limits<double>::infinity();
             int seg = -1;
-            for (size_t k = 0; k < prims.size(); ++k) {
+            for (int k : cand) {
               const double t = prim_entry(prims[k], p0, dd);
               if (t < q) {
                 q = t;
-                seg = (int)k;
+                seg = k;
               }
             }
             if (seg < 0) {  // the solid cell's centre lies inside: first primitive containing it
@@ -296,9 +311,16 @@ int build_links(Mesh& m, int l, const std::vector<Prim>& prims) {
             int c[3] = {fx, fy, fz};
             for (int a = 0; a < 3; ++a)
               if (v.wrap[a]) c[a] = wrapmod(c[a], v.dom[a]);
-            v.links.push_back({c[0], c[1], c[2], i, q, seg < 0 ? 0 : seg});
+            out.push_back({c[0], c[1], c[2], i, q, seg < 0 ? 0 : seg});
           }
         }
+  }, 4);
+  size_t nlinks = 0;
+  for (const auto& b : per_block) nlinks += b.size();
+  v.links.reserve(nlinks);
+  for (auto& b : per_block) {
+    v.links.insert(v.links.end(), b.begin(), b.end());
+    std::vector<Link>().swap(b);
   }
   std::sort(v.links.begin(), v.links.end(), [&](const Link& a, const Link& b) {
     if (a.seg != b.seg) return a.seg < b.seg;
@@ -308,16 +330,18 @@ int build_links(Mesh& m, int l, const std::vector<Prim>& prims) {
   v.seg_begin.assign(prims.size() + 1, 0);
   for (const Link& k : v.links) v.seg_begin[k.seg + 1]++;
   for (size_t k = 0; k < prims.size(); ++k) v.seg_begin[k + 1] += v.seg_begin[k];
-  for (int p = 0; p < 2; ++p) v.wall[p].clear();
-  for (const Link& k : v.links) {
+  for (int p = 0; p < 2; ++p) v.wall[p].assign(v.links.size(), WallEntry{});
+  std::atomic<int> bad{0};  // 1: touches an interface, 2: link without storage
+  parallel_for((long long)v.links.size(), [&](long long n) {
+    const Link& k = v.links[n];
     int i = k.dir, ib = opposite(i);
     int x = k.x, y = k.y, z = k.z;
     // the link cell must not touch another level (its value would be overwritten)
     for (int d = 0; d < kQ; ++d) {
       CellType t = v.cell_type(x + cx(d), y + cy(d), z + cz(d));
       if (t == COVERED || (t == OUTSIDE && l > 0)) {
-        m.error = "the geometry touches a refinement interface";
-        return LBM_EINVAL;
+        bad.store(1);
+        return;
       }
     }
     bool back = v.cell_type(x - cx(i), y - cy(i), z - cz(i)) == FLUID;
@@ -335,11 +359,19 @@ int build_links(Mesh& m, int l, const std::vector<Prim>& prims) {
     e0.seg = e1.seg = k.seg;
     e0.pad = e1.pad = 0;
     if (e0.dst < 0 || e0.a < 0 || e0.c < 0 || e1.a < 0 || e1.c < 0) {
-      m.error = "cut link without storage";
-      return LBM_EINVAL;
+      bad.store(2);
+      return;
     }
-    v.wall[0].push_back(e0);
-    v.wall[1].push_back(e1);
+    v.wall[0][n] = e0;
+    v.wall[1][n] = e1;
+  }, 1024);
+  if (bad.load() == 1) {
+    m.error = "the geometry touches a refinement interface";
+    return LBM_EINVAL;
+  }
+  if (bad.load() == 2) {
+    m.error = "cut link without storage";
+    return LBM_EINVAL;
   }
   return LBM_OK;
 }
@@ -372,9 +404,18 @@ int build_faces(Mesh& m) {
   const int B = v.B;
   const long long cpb = v.cells_per_block();
   for (int p = 0; p < 2; ++p) v.face[p].clear();
-  for (int s = 0; s < v.n_active; ++s) {
+  std::vector<std::vector<FaceEntry>> part0(v.n_active), part1(v.n_active);
+  std::atomic<bool> bad{false};
+  parallel_for(v.n_active, [&](long long s) {
     int o[3];
     block_origin(v, v.grid_of[s], o);
+    bool touches = false;  // only blocks holding a cell on a non-periodic domain face
+    for (int a = 0; a < 3; ++a)
+      if (m.bc[a] != LBM_BC_PERIODIC && ((o[a] <= 0 && 0 < o[a] + B) || (o[a] <= m.n0[a] - 1 && m.n0[a] - 1 < o[a] + B)))
+        touches = true;
+    if (!touches) return;
+    std::vector<FaceEntry>& f0 = part0[s];
+    std::vector<FaceEntry>& f1 = part1[s];
     for (int z = 0; z < B; ++z)
       for (int y = 0; y < B; ++y)
         for (int x = 0; x < B; ++x) {
@@ -406,13 +447,21 @@ int build_faces(Mesh& m) {
               e0.src = e1.src = -1;
             }
             if (e0.dst < 0 || e1.dst < 0 || (cell && (e0.src < 0 || e1.src < 0))) {
-              m.error = "face slot without storage";
-              return LBM_EINVAL;
+              bad.store(true);
+              return;
             }
-            v.face[0].push_back(e0);
-            v.face[1].push_back(e1);
+            f0.push_back(e0);
+            f1.push_back(e1);
           }
         }
+  }, 8);
+  if (bad.load()) {
+    m.error = "face slot without storage";
+    return LBM_EINVAL;
+  }
+  for (int s = 0; s < v.n_active; ++s) {
+    v.face[0].insert(v.face[0].end(), part0[s].begin(), part0[s].end());
+    v.face[1].insert(v.face[1].end(), part1[s].begin(), part1[s].end());
   }
   return LBM_OK;
 }
@@ -436,15 +485,21 @@ int build_interface(Mesh& m, int l) {
   C.save.clear();
   C.infl.clear();
   C.coal.clear();
-  std::unordered_map<long long, int> saved;
-  auto save_index = [&](int x, int y, int z, int i) -> int {
-    long long key = F.addr(x, y, z, opposite(i));
-    auto it = saved.find(key);
-    if (it != saved.end()) return it->second;
-    int k = (int)C.save.size();
-    C.save.push_back({key});
-    saved.emplace(key, k);
-    return k;
+  // errors, reported for the first plane (in z order) that has one
+  static const char* const kErr[] = {"", "refinement interface crosses a solid",
+                                     "refinement box too close to the coarser level's edge",
+                                     "interface slot without storage",
+                                     "refinement box too close to a solid or an edge"};
+  // one part per z plane, concatenated in z order: the tables come out in
+  // the order of a sequential z, y, x sweep.  Saved slots are requested by
+  // key (per-part request numbers) and numbered at the end, distinct keys in
+  // increasing order.
+  struct Part {
+    std::vector<ExplodeEntry> expl;
+    std::vector<InflowEntry> infl;
+    std::vector<CoalesceEntry> coal;
+    std::vector<long long> want;
+    int err = 0;
   };
   auto coarse_post = [&](int X, int Y, int Z, int i, int parity) -> long long {
     if (parity == 0) return C.addr(X, Y, Z, opposite(i));
@@ -452,22 +507,29 @@ int build_interface(Mesh& m, int l) {
   };
   const int* lo = F.rlo;
   const int* hi = F.rhi;
-  for (int z = lo[2]; z < hi[2]; ++z)
-    for (int y = lo[1]; y < hi[1]; ++y)
-      for (int x = lo[0]; x < hi[0]; ++x) {
-        bool shell = x == lo[0] || x == hi[0] - 1 || y == lo[1] || y == hi[1] - 1 || z == lo[2] || z == hi[2] - 1;
-        if (!shell) continue;
+  std::vector<Part> fine((size_t)(hi[2] - lo[2]));
+  parallel_for(hi[2] - lo[2], [&](long long zi) {
+    Part& P = fine[(size_t)zi];
+    const int z = lo[2] + (int)zi;
+    auto save_index = [&](int x, int y, int zz, int i) -> int {
+      P.want.push_back(F.addr(x, y, zz, opposite(i)));
+      return (int)P.want.size() - 1;
+    };
+    for (int y = lo[1]; y < hi[1]; ++y) {
+      // cells of the box's outer shell only: all of x on the y/z faces, else the two x ends
+      const bool face = y == lo[1] || y == hi[1] - 1 || z == lo[2] || z == hi[2] - 1;
+      for (int x = lo[0]; x < hi[0]; x = (face || x >= hi[0] - 1) ? x + 1 : hi[0] - 1) {
         for (int i = 0; i < kQ; ++i) {
           int ax = x - cx(i), ay = y - cy(i), az = z - cz(i);
           if (in_box(lo, hi, ax, ay, az)) continue;
           if (F.cell_type(x, y, z) != FLUID) {
-            m.error = "refinement interface crosses a solid";
-            return LBM_EINVAL;
+            P.err = 1;
+            return;
           }
           int px = floordiv(ax, 2), py = floordiv(ay, 2), pz = floordiv(az, 2);
           if (C.cell_type(px, py, pz) != FLUID) {
-            m.error = "refinement box too close to the coarser level's edge";
-            return LBM_EINVAL;
+            P.err = 2;
+            return;
           }
           ExplodeEntry e{};
           e.dst = F.addr(ax, ay, az, opposite(i));
@@ -478,16 +540,16 @@ int build_interface(Mesh& m, int l) {
           int bx = x - 2 * cx(i), by = y - 2 * cy(i), bz = z - 2 * cz(i);
           if (in_box(lo, hi, bx, by, bz)) {
             if (F.cell_type(bx, by, bz) != FLUID) {
-              m.error = "refinement interface crosses a solid";
-              return LBM_EINVAL;
+              P.err = 1;
+              return;
             }
             f.r = save_index(bx, by, bz, i);
             f.csrc[0] = f.csrc[1] = -1;
           } else {
             int qx = floordiv(bx, 2), qy = floordiv(by, 2), qz = floordiv(bz, 2);
             if (C.cell_type(qx, qy, qz) != FLUID) {
-              m.error = "refinement box too close to the coarser level's edge";
-              return LBM_EINVAL;
+              P.err = 2;
+              return;
             }
             f.r = -1;
             f.csrc[0] = coarse_post(qx, qy, qz, i, 0);
@@ -495,26 +557,31 @@ int build_interface(Mesh& m, int l) {
           }
           if (e.dst < 0 || e.src[0] < 0 || e.src[1] < 0 || f.dst < 0 ||
               (f.r < 0 && (f.csrc[0] < 0 || f.csrc[1] < 0))) {
-            m.error = "interface slot without storage";
-            return LBM_EINVAL;
+            P.err = 3;
+            return;
           }
-          C.expl.push_back(e);
-          C.infl.push_back(f);
+          P.expl.push_back(e);
+          P.infl.push_back(f);
         }
       }
+    }
+  });
   // coarse cells around the footprint [lo/2, hi/2)
   int clo[3], chi[3];
   for (int a = 0; a < 3; ++a) {
     clo[a] = lo[a] / 2;
     chi[a] = hi[a] / 2;
   }
-  for (int Z = clo[2] - 1; Z <= chi[2]; ++Z)
-    for (int Y = clo[1] - 1; Y <= chi[1]; ++Y)
-      for (int X = clo[0] - 1; X <= chi[0]; ++X) {
-        if (in_box(clo, chi, X, Y, Z)) continue;
+  std::vector<Part> coarse((size_t)(chi[2] - clo[2] + 2));
+  parallel_for(chi[2] - clo[2] + 2, [&](long long zi) {
+    Part& P = coarse[(size_t)zi];
+    const int Z = clo[2] - 1 + (int)zi;
+    for (int Y = clo[1] - 1; Y <= chi[1]; ++Y) {
+      const bool face = Y == clo[1] - 1 || Y == chi[1] || Z == clo[2] - 1 || Z == chi[2];
+      for (int X = clo[0] - 1; X <= chi[0]; X = (face || X >= chi[0]) ? X + 1 : chi[0]) {
         if (C.cell_type(X, Y, Z) != FLUID) {
-          m.error = "refinement box too close to a solid or an edge";
-          return LBM_EINVAL;
+          P.err = 4;
+          return;
         }
         for (int i = 0; i < kQ; ++i) {
           CoalesceEntry e{};
@@ -525,12 +592,13 @@ int build_interface(Mesh& m, int l) {
             if (in_box(lo, hi, ax, ay, az)) {
               long long a = F.addr(px, py, pz, i);
               if (a < 0) {
-                m.error = "interface slot without storage";
-                return LBM_EINVAL;
+                P.err = 3;
+                return;
               }
               e.fsrc[e.nfine++] = a;
             } else if (in_box(lo, hi, bx, by, bz)) {
-              e.fsrc[e.nfine++] = -(long long)save_index(bx, by, bz, i) - 1;
+              P.want.push_back(F.addr(bx, by, bz, opposite(i)));
+              e.fsrc[e.nfine++] = -(long long)(P.want.size() - 1) - 1;
             } else {
               e.ncoarse++;
             }
@@ -539,12 +607,72 @@ int build_interface(Mesh& m, int l) {
           e.dst[0] = C.addr(X - cx(i), Y - cy(i), Z - cz(i), opposite(i));
           e.dst[1] = C.addr(X, Y, Z, i);
           if (e.dst[0] < 0 || e.dst[1] < 0) {
-            m.error = "interface slot without storage";
-            return LBM_EINVAL;
+            P.err = 3;
+            return;
           }
-          C.coal.push_back(e);
+          P.coal.push_back(e);
         }
       }
+    }
+  });
+  for (const auto* parts : {&fine, &coarse})
+    for (const Part& P : *parts)
+      if (P.err) {
+        m.error = kErr[P.err];
+        return LBM_EINVAL;
+      }
+  // concatenate in plane order (parallel copies into pre-sized tables),
+  // turning per-part request numbers into global ones
+  std::vector<size_t> eo(fine.size() + 1, 0), wo(fine.size() + coarse.size() + 1, 0), co(coarse.size() + 1, 0);
+  for (size_t k = 0; k < fine.size(); ++k) {
+    eo[k + 1] = eo[k] + fine[k].expl.size();
+    wo[k + 1] = wo[k] + fine[k].want.size();
+  }
+  for (size_t k = 0; k < coarse.size(); ++k) {
+    co[k + 1] = co[k] + coarse[k].coal.size();
+    wo[fine.size() + k + 1] = wo[fine.size() + k] + coarse[k].want.size();
+  }
+  C.expl.resize(eo.back());
+  C.infl.resize(eo.back());
+  C.coal.resize(co.back());
+  std::vector<long long> want(wo.back());
+  parallel_for((long long)(fine.size() + coarse.size()), [&](long long k) {
+    if (k < (long long)fine.size()) {
+      Part& P = fine[k];
+      for (InflowEntry& f : P.infl)
+        if (f.r >= 0) f.r += (int)wo[k];
+      std::copy(P.expl.begin(), P.expl.end(), C.expl.begin() + eo[k]);
+      std::copy(P.infl.begin(), P.infl.end(), C.infl.begin() + eo[k]);
+      std::copy(P.want.begin(), P.want.end(), want.begin() + wo[k]);
+    } else {
+      const size_t c = (size_t)k - fine.size();
+      Part& P = coarse[c];
+      for (CoalesceEntry& e : P.coal)
+        for (int q = 0; q < e.nfine; ++q)
+          if (e.fsrc[q] < 0) e.fsrc[q] -= (long long)wo[k];
+      std::copy(P.coal.begin(), P.coal.end(), C.coal.begin() + co[c]);
+      std::copy(P.want.begin(), P.want.end(), want.begin() + wo[k]);
+    }
+  });
+  std::vector<Part>().swap(fine);
+  std::vector<Part>().swap(coarse);
+  std::vector<long long> keys(want);
+  parallel_sort(keys);
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  C.save.resize(keys.size());
+  for (size_t k = 0; k < keys.size(); ++k) C.save[k].src = keys[k];
+  auto resolve = [&](long long req) {
+    return (long long)(std::lower_bound(keys.begin(), keys.end(), want[req]) - keys.begin());
+  };
+  parallel_for((long long)C.infl.size(), [&](long long n) {
+    InflowEntry& f = C.infl[n];
+    if (f.r >= 0) f.r = (int)resolve(f.r);
+  }, 4096);
+  parallel_for((long long)C.coal.size(), [&](long long n) {
+    CoalesceEntry& e = C.coal[n];
+    for (int k = 0; k < e.nfine; ++k)
+      if (e.fsrc[k] < 0) e.fsrc[k] = -resolve(-e.fsrc[k] - 1) - 1;
+  }, 4096);
   return LBM_OK;
 }
 
@@ -611,26 +739,37 @@ int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vecto
     Level& v = m.lv[l];
     // collide masks and counts
     const long long cpb = v.cells_per_block();
-    v.maskoff.assign(v.n_active, -1);
-    v.masks.clear();
-    v.n_fluid = 0;
-    for (int s = 0; s < v.n_active; ++s) {
+    std::vector<long long> nf(v.n_active, 0);
+    std::atomic<bool> solid{false};
+    parallel_for(v.n_active, [&](long long s) {
       const uint8_t* t = &v.type[(size_t)s * cpb];
-      long long nf = 0;
-      for (long long c = 0; c < cpb; ++c) nf += t[c] == FLUID;
-      v.n_fluid += nf;
-      if (nf != cpb) {
-        v.maskoff[s] = (int)(v.masks.size() / cpb);
-        for (long long c = 0; c < cpb; ++c) v.masks.push_back(t[c] == FLUID ? 1 : 0);
+      long long n = 0;
+      bool sol = false;
+      for (long long c = 0; c < cpb; ++c) {
+        n += t[c] == FLUID;
+        sol |= t[c] == SOLID;
       }
+      nf[s] = n;
+      if (sol) solid.store(true);
+    }, 64);
+    if (l + 1 < m.L && solid.load()) {
+      m.error = "the tree must lie inside the finest level's box";
+      return LBM_EINVAL;
     }
-    if (l + 1 < m.L) {
-      for (long long c = 0; c < (long long)v.n_active * cpb; ++c)
-        if (v.type[c] == SOLID) {
-          m.error = "the tree must lie inside the finest level's box";
-          return LBM_EINVAL;
-        }
+    v.maskoff.assign(v.n_active, -1);
+    v.n_fluid = 0;
+    int nmask = 0;
+    for (int s = 0; s < v.n_active; ++s) {
+      v.n_fluid += nf[s];
+      if (nf[s] != cpb) v.maskoff[s] = nmask++;
     }
+    v.masks.assign((size_t)nmask * cpb, 0);
+    parallel_for(v.n_active, [&](long long s) {
+      if (v.maskoff[s] < 0) return;
+      const uint8_t* t = &v.type[(size_t)s * cpb];
+      uint8_t* mk = &v.masks[(size_t)v.maskoff[s] * cpb];
+      for (long long c = 0; c < cpb; ++c) mk[c] = t[c] == FLUID ? 1 : 0;
+    }, 16);
   }
   for (int l = 0; l < m.L; ++l) {
     int rc = build_links(m, l, prims);

@@ -75,6 +75,7 @@ def _load():
         "lbm_branch_table": ([vp, dp, i, ip], i),
         "lbm_branch_drag_estimate": ([dp, i, dp, C.c_double, dp, dp], i),
         "lbm_set_branch_forces": ([vp, i], i),
+        "lbm_set_wide_offsets": ([vp, i], i),
         "lbm_get_branch_forces": ([vp, dp, i, llp], i),
         "lbm_use_graphs": ([vp, i], i),
         "lbm_set_timing": ([vp, i], i),
@@ -251,6 +252,10 @@ def lbm_get_segments(h):
 
 def lbm_set_branch_forces(h, on):
     return _ck(_lib.lbm_set_branch_forces(h, int(bool(on))), "lbm_set_branch_forces")
+
+
+def lbm_set_wide_offsets(h, on):
+    return _ck(_lib.lbm_set_wide_offsets(h, int(bool(on))), "lbm_set_wide_offsets")
 
 
 def lbm_get_branch_forces(h, n_branches):

@@ -20,6 +20,9 @@ from . import workloads as W
 # branch-table columns used as network inputs: log10 Re_d, D/H, cos alpha,
 # shielding depth, shadowed fraction, leaf flag
 FEATURES = (0, 2, 3, 5, 9, 10)
+# the six inputs the learned-form workload names: log10 Re_d, generation,
+# D/H, cos alpha, I_u, shielding depth
+FEATURES_NAMED = (0, 1, 2, 3, 4, 5)
 
 
 class Sample:
@@ -56,10 +59,10 @@ def simulate(case, stream=None, domain=None, steps=None, average=None):
     return Sample(rows, c, g["A_x"], mean[0] / (q * g["A_x"]))
 
 
-def dataset(samples):
+def dataset(samples, features=FEATURES):
     """Stack the branch rows of several samples: inputs (float32, n x 6) and
     targets (float32, n)."""
-    x = np.concatenate([s.rows[:, FEATURES] for s in samples]).astype(np.float32)
+    x = np.concatenate([s.rows[:, list(features)] for s in samples]).astype(np.float32)
     y = np.concatenate([s.c for s in samples]).astype(np.float32)
     return x, y
 
@@ -105,11 +108,11 @@ def train_ensemble(x, y, members=4, seed=0, **kw):
     return [train(x, y, seed=seed + k, **kw) for k in range(members)]
 
 
-def predict(net, rows):
+def predict(net, rows, features=FEATURES):
     """Sectional coefficients predicted for the branches of a branch table
     (the mean over the members when `net` is a list)."""
     import torch
-    x = torch.from_numpy(np.ascontiguousarray(rows[:, FEATURES], dtype=np.float32)).cuda()
+    x = torch.from_numpy(np.ascontiguousarray(rows[:, list(features)], dtype=np.float32)).cuda()
     nets = net if isinstance(net, (list, tuple)) else [net]
     return np.mean([m.forward(x).cpu().numpy().astype(np.float64) for m in nets], axis=0)
 

@@ -23,6 +23,18 @@ CASES = {
                  re_h=2500.0, steps=10000,
                  tree=dict(n=4, children=3, s0=64.0, w0=19.2, r=(0.6,), dfac=(0.6,), alpha_deg=(35.0,),
                            azimuth_mode=1, seed=1, trunk_cells=64.0)),
+    # four levels, coarse 512x256x256 in 16^3 blocks, 4 generations of 3 children,
+    # trunk 360 finest cells (diameter 0.3 of its length), Re_H = 1.2e5: about
+    # 6e8 active cells summed over the levels
+    "amr4": dict(n0=(512, 256, 256), levels=4, block=16, bc=("inout", "inflow", "inflow"), u_in=0.05,
+                 re_h=1.2e5, steps=20,
+                 tree=dict(n=5, children=3, s0=360.0, w0=108.0, r=(0.6,), dfac=(0.6,), alpha_deg=(35.0,),
+                           azimuth_mode=1, seed=2, trunk_cells=360.0)),
+    # the four-level case scaled down by 4 per axis (coarse 128x64x64, 8^3 blocks), sized for the oracle
+    "amr4_quarter": dict(n0=(128, 64, 64), levels=4, block=8, bc=("inout", "inflow", "inflow"), u_in=0.05,
+                         re_h=1.2e5, steps=2,
+                         tree=dict(n=5, children=3, s0=90.0, w0=27.0, r=(0.6,), dfac=(0.6,), alpha_deg=(35.0,),
+                                   azimuth_mode=1, seed=2, trunk_cells=90.0)),
     # the two-level case scaled down by 4 (8^3 blocks), sized for the oracle
     "amr2_small": dict(n0=(64, 48, 48), levels=2, block=8, bc=("inout", "inflow", "inflow"), u_in=0.05,
                        re_h=400.0, steps=100,

@@ -252,3 +252,24 @@ def test_watchdog_reports_nan_from_host_injection(L, stream):
             dom.step(1)
     assert e.value.code == L.LBM_EUNSTABLE
     dom.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_wide_offset_kernels_equal_narrow(L, stream, precision):
+    """The 64-bit-offset collide kernels (used by levels above 2^31 elements)
+    give bit-identical populations on the two-level case."""
+    c = W.CASES["amr2_small"]
+    prec = L.LBM_FP32 if precision == "fp32" else L.LBM_FP16_DEV
+    doms = []
+    for wide in (False, True):
+        desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
+                             re_h=c["re_h"], precision=prec)
+        d = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=stream)
+        d.set_wide_offsets(wide)
+        d.step(5)
+        doms.append(d)
+    for lv in (0, 1):
+        np.testing.assert_array_equal(doms[0].get_populations(lv), doms[1].get_populations(lv))
+    np.testing.assert_array_equal(doms[0].drag()[1], doms[1].drag()[1])
+    for d in doms:
+        d.close()
