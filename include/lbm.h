@@ -69,7 +69,8 @@ typedef struct {
   double re_h;             /* Re_H = U H / nu on the finest level, H = tree height in finest cells;
                               <= 0 selects nu_finest below */
   double nu_finest;        /* finest-level lattice viscosity when re_h <= 0 */
-  double i_u;              /* inflow turbulence intensity; only 0 (uniform inflow) is supported */
+  double i_u;              /* inflow turbulence intensity u'_rms / U in [0, 0.5]; 0: uniform inflow,
+                              > 0: random-Fourier-mode inflow (lbm_set_inflow_turbulence) */
   unsigned long long seed; /* reserved for seeded inflow turbulence */
   double refine_margin;    /* finest box = tree bounding box grown by this fraction per side (0.25) */
   int precision;           /* lbm_precision */
@@ -278,6 +279,24 @@ int lbm_mlp_train_step(lbm_mlp* m, const float* x, const float* y, const int* id
                        double* loss);
 const char* lbm_mlp_last_error(void);
 void lbm_mlp_destroy(lbm_mlp* m);
+
+/* Turbulent inflow (domains with i_u > 0; Sec. 4.3 defines I_u = u'_rms / U).
+   Every inflow-equilibrium value pulled from outside level 0 is the
+   equilibrium at rho = 1 and u = U e_x + u'(p - U t e_x) at the centre p of
+   the cell it is pulled from, t the coarse steps done: a frozen synthetic
+   field carried through the inflow at U (Taylor's hypothesis).
+     u'(x) = sum_n a_n cos(k_n . x + psi_n),   a_n . k_n = 0,
+   n_modes modes (default 256) with a von Karman spectrum whose integral
+   length is `integral_length` level-0 cells (0: the tree height), scaled so
+   that the expected stream-wise variance is (I_u U)^2; directions, phases
+   and polarisations come from SplitMix64 draws of the domain's seed
+   (counter 2^40 + 4 n + j).  Lengths and wavenumbers in level-0 cells;
+   wavenumbers log-spaced over [k_e / 4, min(16 k_e, pi / 4)], k_e =
+   0.747 / integral_length.  n_modes at most 1024.  LBM_ESTATE when i_u = 0. */
+int lbm_set_inflow_turbulence(lbm_domain* d, int n_modes, double integral_length);
+/* The mode table, 7 doubles per mode: k (3), a (3), psi; n is the capacity
+   in modes, *count the number of modes (0 for uniform inflow). */
+int lbm_inflow_modes(const lbm_domain* d, double* modes, int n, int* count);
 
 /* Run the collide kernels with 64-bit element offsets even on levels whose
    arrays hold fewer than 2^31 elements (they switch to 64-bit offsets by

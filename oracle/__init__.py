@@ -101,6 +101,10 @@ def _declare(L):
     L.orc_cell_type.restype = C.c_int
     L.orc_branch_forces.argtypes = [C.c_void_p, _dp, C.c_int]
     L.orc_branch_forces.restype = C.c_int
+    L.orc_set_turbulence.argtypes = [C.c_void_p, _dp, C.c_int, C.c_double]
+    L.orc_set_turbulence.restype = C.c_int
+    L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+    L.orc_splitmix64.restype = C.c_uint64
 
 
 # ---------------------------------------------------------------- tree (Sec. 2.1)
@@ -345,6 +349,11 @@ class Sim:
         p = np.zeros(3)
         lib().orc_mass(self._h, C.byref(m), p)
         return m.value, p
+
+    def set_turbulence(self, modes, u_in):
+        """Turbulent inflow from a mode table (n x 7: k, a, psi)."""
+        m = np.ascontiguousarray(modes, dtype=np.float64).reshape(-1, 7)
+        lib().orc_set_turbulence(self._h, m.ravel() if len(m) else np.zeros(7), len(m), float(u_in))
 
     def branch_forces(self, n):
         out = np.zeros((max(1, n), 3))

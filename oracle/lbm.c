@@ -68,6 +68,10 @@ struct orc_sim {
   long nF;
   int nprim;
   double* Fseg; /* per-primitive running sum of the finest level's force */
+  long t;       /* coarse steps done */
+  int nturb;    /* random Fourier modes of a turbulent inflow (0: uniform) */
+  double* turb; /* per mode: k (3), a (3), psi */
+  double u_in;
 };
 
 static long lidx(const lev* v, int x, int y, int z) {
@@ -180,11 +184,13 @@ void orc_destroy(orc_sim* s) {
     free(v->lcell); free(v->ldir); free(v->lq); free(v->lback); free(v->lseg);
   }
   free(s->Fseg);
+  free(s->turb);
   free(s);
 }
 
 void orc_init_uniform(orc_sim* s, double rho, const double u[3]) {
   double feq[27];
+  s->t = 0;
   orc_equilibrium(rho, u, feq);
   for (int l = 0; l < s->L; ++l) {
     lev* v = &s->lv[l];
@@ -300,16 +306,33 @@ int orc_set_prims(orc_sim* s, const orc_prim* pr, int np) {
 }
 
 /* value of f*_i pulled from level-0 position g (possibly outside the domain) */
+/* inflow equilibrium pulled from level-0 cell g (periodic axes wrapped):
+   uniform, or at u = U e_x + sum_n a_n cos(k_n . (p - U t e_x) + psi_n), p the
+   cell centre, t the coarse steps done (frozen synthetic turbulence) */
+static double inflow_value(const orc_sim* s, const int g[3], int i) {
+  if (s->nturb == 0) return s->feq_in[i];
+  double p[3] = {g[0] + 0.5 - s->u_in * (double)s->t, g[1] + 0.5, g[2] + 0.5};
+  double u[3] = {s->u_in, 0, 0};
+  for (int n = 0; n < s->nturb; ++n) {
+    const double* m = s->turb + 7 * n;
+    double c = cos(m[0] * p[0] + m[1] * p[1] + m[2] * p[2] + m[6]);
+    for (int a = 0; a < 3; ++a) u[a] += m[3 + a] * c;
+  }
+  double feq[27];
+  orc_equilibrium(1.0, u, feq);
+  return feq[i];
+}
+
 static double pull0(const orc_sim* s, const double* A, int gx, int gy, int gz, int i) {
   const lev* v = &s->lv[0];
   int g[3] = {gx, gy, gz};
   for (int a = 0; a < 3; ++a)
     if (s->d.bc[a] == ORC_BC_PERIODIC) g[a] = wrapi(g[a], v->n[a]);
-  if (g[0] < 0) return s->feq_in[i]; /* inflow face */
+  if (g[0] < 0) return inflow_value(s, g, i); /* inflow face */
   int c[3] = {cx(i), cy(i), cz(i)};
   for (int a = 1; a < 3; ++a) {
     if (g[a] < 0 || g[a] >= v->n[a]) {
-      if (s->d.bc[a] == ORC_BC_INFLOW) return s->feq_in[i];
+      if (s->d.bc[a] == ORC_BC_INFLOW) return inflow_value(s, g, i);
       /* specular slip: mirror the cell across the face, flip that component */
       g[a] = g[a] < 0 ? -1 - g[a] : 2 * v->n[a] - 1 - g[a];
       c[a] = -c[a];
@@ -430,7 +453,25 @@ static void step_level(orc_sim* s, int l) {
 }
 
 void orc_step(orc_sim* s, int ncoarse) {
-  for (int n = 0; n < ncoarse; ++n) step_level(s, 0);
+  for (int n = 0; n < ncoarse; ++n) {
+    step_level(s, 0);
+    s->t++;
+  }
+}
+
+int orc_set_turbulence(orc_sim* s, const double* modes, int n, double u_in) {
+  if (n < 0) return -1;
+  free(s->turb);
+  s->turb = NULL;
+  s->nturb = 0;
+  if (n > 0) {
+    s->turb = malloc(7 * sizeof(double) * (size_t)n);
+    if (!s->turb) return -1;
+    memcpy(s->turb, modes, 7 * sizeof(double) * (size_t)n);
+  }
+  s->nturb = n;
+  s->u_in = u_in;
+  return 0;
 }
 
 void orc_level_box(const orc_sim* s, int level, int lo[3], int hi[3]) {

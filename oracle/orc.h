@@ -92,6 +92,8 @@ void orc_init_uniform(orc_sim* s, double rho, const double u[3]);
 /* per-cell equilibrium initialisation of one level from rho[n], u[3n] over its real box */
 int orc_init_field(orc_sim* s, int level, const double* rho, const double* u);
 void orc_step(orc_sim* s, int ncoarse);
+/* turbulent inflow: n modes of 7 doubles (k, a, psi), mean speed u_in */
+int orc_set_turbulence(orc_sim* s, const double* modes, int n, double u_in);
 /* real box of a level and its populations f_i(x) (NaN for non-fluid cells), x fastest */
 void orc_level_box(const orc_sim* s, int level, int lo[3], int hi[3]);
 void orc_get_f(const orc_sim* s, int level, double* out);

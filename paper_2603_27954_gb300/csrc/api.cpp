@@ -65,6 +65,10 @@ struct lbm_domain {
   int n_seg = 0;
   bool branch_forces = false;
   bool wide_offsets = false;  // force the 64-bit-offset collide kernels
+  // turbulent inflow (random Fourier modes), on when d.i_u > 0
+  int n_modes = 256;
+  double l_int = 0;  // integral length in level-0 cells; 0: the tree height
+  size_t off_modes = 0, off_facepos = 0, off_tick = 0;
   int max_wall_parts = 0;
   float feq_in[27];
   int parity0 = 0;
@@ -147,7 +151,14 @@ int advance(lbm_domain* dm, int l, int parity) {
     Timed t(dm, KC_FACES, (long long)v.face[parity].size());
     float feq[27];
     for (int i = 0; i < 27; ++i) feq[i] = dm->feq_in[i] * v.scale;
-    if ((rc = launch_faces(f, half, dm->dev<FaceEntry>(v.off_face[parity]), (int)v.face[parity].size(), feq,
+    TurbArgs tb{nullptr, nullptr, 0, (float)dm->d.u_in, v.scale, nullptr};
+    if (dm->d.i_u > 0) {
+      tb.pos = dm->dev<int>(dm->off_facepos);
+      tb.modes = dm->dev<float>(dm->off_modes);
+      tb.n_modes = dm->n_modes;
+      tb.tick = dm->dev<long long>(dm->off_tick);
+    }
+    if ((rc = launch_faces(f, half, dm->dev<FaceEntry>(v.off_face[parity]), (int)v.face[parity].size(), feq, tb,
                            dm->stream)))
       return rc;
   }
@@ -190,6 +201,7 @@ int advance(lbm_domain* dm, int l, int parity) {
         return rc;
     }
   }
+  if (l == 0 && dm->d.i_u > 0 && (rc = launch_tick(dm->dev<long long>(dm->off_tick), dm->stream))) return rc;
   return LBM_OK;
 }
 
@@ -197,6 +209,7 @@ int kernels_per_step(const Mesh& m, int l) {
   const Level& v = m.lv[l];
   int k = 1;
   if (l == 0 && !v.face[0].empty()) k += 1;
+  if (l == 0 && m.turbulent) k += 1;
   if (!v.wall[0].empty()) k += (l == m.L - 1) ? 2 : 1;
   if (l + 1 < m.L) k += 2 * kernels_per_step(m, l + 1) + (v.expl.size() || v.save.size() ? 1 : 0) +
                         (v.infl.empty() ? 0 : 1) + (v.coal.empty() ? 0 : 1);
@@ -270,11 +283,43 @@ int build(lbm_domain* d) {
   }
   d->off_partials = put((size_t)d->max_wall_parts * 3 * sizeof(double));
   d->off_accum = put(8 * sizeof(double));
+  d->off_tick = put(sizeof(long long));
+  d->mesh.turbulent = d->d.i_u > 0;
+  if (d->d.i_u > 0) {
+    d->off_modes = put((size_t)kMaxModes * kModeCols * sizeof(float));
+    d->off_facepos = put(d->mesh.lv[0].face_pos.size() * sizeof(int));
+  }
   d->off_mpart = put(max_blocks * 5 * sizeof(double));
   d->need = off;
   double u[3] = {d->d.u_in, 0, 0};
   for (int i = 0; i < 27; ++i) d->feq_in[i] = (float)(equilibrium(i, 1.0, u) - rest_weight(i));
   d->built = true;
+  return LBM_OK;
+}
+
+double integral_length(const lbm_domain* d) {
+  return d->l_int > 0 ? d->l_int : d->H * std::ldexp(1.0, -(d->d.levels - 1));
+}
+
+void make_modes(const lbm_domain* d, std::vector<double>* modes) {
+  rfm_modes(d->d.seed, d->n_modes, d->d.i_u, d->d.u_in, integral_length(d), modes);
+}
+
+int upload_modes(lbm_domain* d) {
+  std::vector<double> m;
+  make_modes(d, &m);
+  std::vector<float> mf(m.begin(), m.end());
+  if (!mf.empty())
+    CK(cudaMemcpyAsync(d->base + d->off_modes, mf.data(), mf.size() * sizeof(float), cudaMemcpyHostToDevice,
+                       d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return LBM_OK;
+}
+
+// the device copy of the coarse-step count (turbulent inflow time)
+int set_tick(lbm_domain* d) {
+  CK(cudaMemcpyAsync(d->base + d->off_tick, &d->steps, sizeof(long long), cudaMemcpyHostToDevice, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
   return LBM_OK;
 }
 
@@ -298,6 +343,12 @@ int upload(lbm_domain* d) {
   }
   const Level& fl = d->mesh.lv.back();
   if (d->n_seg) CK(cp(d->off_segb, fl.seg_begin.data(), fl.seg_begin.size() * sizeof(int)));
+  if (d->d.i_u > 0) {
+    const Level& l0 = d->mesh.lv[0];
+    CK(cp(d->off_facepos, l0.face_pos.data(), l0.face_pos.size() * sizeof(int)));
+    int rc = upload_modes(d);
+    if (rc) return rc;
+  }
   return LBM_OK;
 }
 
@@ -443,7 +494,8 @@ int lbm_create_domain(const lbm_domain_desc* desc, void* cuda_stream, lbm_domain
     if (s.bc[a] != LBM_BC_PERIODIC && s.bc[a] != LBM_BC_SLIP && s.bc[a] != LBM_BC_INFLOW)
       return fail(LBM_EINVAL, "y/z faces: periodic, slip or inflow");
   if (!(std::fabs(s.u_in) < 0.3)) return fail(LBM_EINVAL, "inflow speed must be below 0.3");
-  if (s.i_u != 0.0) return fail(LBM_EINVAL, "only uniform inflow (i_u = 0) is supported");
+  if (!(s.i_u >= 0.0 && s.i_u <= 0.5)) return fail(LBM_EINVAL, "inflow turbulence intensity must lie in [0, 0.5]");
+  if (s.i_u > 0 && s.bc[0] != LBM_BC_INOUT) return fail(LBM_EINVAL, "turbulent inflow needs the in/out x faces");
   if (s.precision != LBM_FP32 && s.precision != LBM_FP16_DEV)
     return fail(LBM_EINVAL, "precision must be LBM_FP32 or LBM_FP16_DEV");
   if (!(s.omega2 > 0 && s.omega2 < 2)) return fail(LBM_EINVAL, "omega2 must lie in (0, 2)");
@@ -526,8 +578,7 @@ int lbm_bind_memory(lbm_domain* d, void* ptr, size_t bytes) {
   double u[3] = {d->d.u_in, 0, 0};
   if ((rc = fill_uniform(d, 1.0, u))) return rc;
   d->steps = 0;
-  CK(cudaStreamSynchronize(d->stream));
-  return LBM_OK;
+  return set_tick(d);
 }
 
 int lbm_init_uniform(lbm_domain* d, double rho, const double u[3]) {
@@ -536,8 +587,7 @@ int lbm_init_uniform(lbm_domain* d, double rho, const double u[3]) {
   int rc = fill_uniform(d, rho, u);
   if (rc) return rc;
   d->steps = 0;
-  CK(cudaStreamSynchronize(d->stream));
-  return LBM_OK;
+  return set_tick(d);
 }
 
 int lbm_init_field(lbm_domain* d, int level, const double* rho, const double* u, size_t n) {
@@ -802,6 +852,33 @@ int lbm_branch_drag_estimate(const double* rows, int n, const double* c_sect, do
   return LBM_OK;
 }
 
+int lbm_set_inflow_turbulence(lbm_domain* d, int n_modes, double integral_length) {
+  if (!d || n_modes < 1 || n_modes > kMaxModes || integral_length < 0) return fail(LBM_EINVAL, "bad argument");
+  if (!(d->d.i_u > 0)) return fail(LBM_ESTATE, "the domain has uniform inflow (i_u = 0)");
+  d->n_modes = n_modes;
+  d->l_int = integral_length;
+  if (d->base) {
+    free_graphs(d);
+    return upload_modes(d);
+  }
+  return LBM_OK;
+}
+
+int lbm_inflow_modes(const lbm_domain* d, double* modes, int n, int* count) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
+  const int c = d->d.i_u > 0 ? d->n_modes : 0;
+  if (count) *count = c;
+  if (modes && c) {
+    if (n < c) return fail(LBM_EINVAL, "capacity below the number of modes");
+    std::vector<double> m;
+    make_modes(d, &m);
+    for (int k = 0; k < c; ++k)
+      for (int j = 0; j < 7; ++j) modes[7 * k + j] = m[(size_t)k * kModeCols + j];
+  }
+  return LBM_OK;
+}
+
 int lbm_set_wide_offsets(lbm_domain* d, int on) {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (d->wide_offsets != (on != 0)) free_graphs(d);
@@ -928,7 +1005,7 @@ int lbm_load(lbm_domain* d, const char* path) {
   free_graphs(d);
   d->parity0 = (int)hdr[1];
   d->steps = hdr[2];
-  return LBM_OK;
+  return set_tick(d);
 }
 
 void lbm_destroy(lbm_domain* d) {

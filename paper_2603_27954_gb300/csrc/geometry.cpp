@@ -10,9 +10,6 @@
 #include "parallel.h"
 
 namespace lbm {
-namespace {
-
-constexpr double kPi = 3.14159265358979323846;
 
 // SplitMix64 (Steele, Lea & Flood 2014), counter form: output number k of
 // a generator seeded with `seed`.
@@ -24,6 +21,10 @@ uint64_t splitmix(uint64_t seed, uint64_t k) {
   z *= 0x94D049BB133111EBULL;
   return z ^ (z >> 31);
 }
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
 
 struct Module {
   char sym;     // 'A' apex, '!' width, 'F' segment, '[' ']', '+' about U, '/' about H

@@ -43,6 +43,12 @@ void prim_bounds(const Prim& p, double lo[3], double hi[3]);
 
 // ---------------------------------------------------------------- device tables
 // Offsets are element offsets (floats) into a level's population array.
+// random-Fourier-mode inflow: per mode k (3), a (3), psi, pad
+constexpr int kModeCols = 8;
+constexpr int kMaxModes = 1024;
+uint64_t splitmix(uint64_t seed, uint64_t k);
+void rfm_modes(uint64_t seed, int n, double i_u, double u, double l_int, std::vector<double>* out);
+
 struct FaceEntry {   // domain faces of level 0 (Sec. 2.3)
   long long dst;
   long long src;     // -1: inflow equilibrium of direction dir
@@ -107,6 +113,7 @@ struct Level {
   std::vector<WallEntry> wall[2];
   std::vector<int> seg_begin;                    // n_seg + 1 offsets into the ordered links
   std::vector<FaceEntry> face[2];
+  std::vector<int> face_pos;  // per face entry: pulled-from cell (x, y, z, 0), periodic axes wrapped
   // interface with the next finer level (this level = coarse)
   std::vector<ExplodeEntry> expl;
   std::vector<SaveEntry> save;
@@ -129,6 +136,7 @@ struct Level {
 };
 
 struct Mesh {
+  bool turbulent = false;  // level-0 inflow from random Fourier modes (one tick launch per coarse step)
   int L = 1, B = 16;
   int n0[3] = {0, 0, 0};
   int bc[3] = {0, 0, 0};
@@ -159,7 +167,17 @@ struct CollideArgs {
 };
 int prepare_kernels();
 int launch_collide(const CollideArgs& a, int B, int odd, void* stream);
-int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], void* stream);
+struct TurbArgs {      // turbulent inflow; n_modes == 0: uniform inflow equilibrium
+  const int* pos;       // per face entry: level-0 cell (x, y, z, 0) the value is pulled from
+  const float* modes;   // n_modes x kModeCols
+  int n_modes;
+  float u;              // mean inflow speed along x
+  float scale;          // storage scale of the level
+  const long long* tick;  // coarse steps done
+};
+int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], const TurbArgs& turb,
+                 void* stream);
+int launch_tick(long long* tick, void* stream);
 int launch_walls(void* f, int half, float inv_scale, const WallEntry* e, int n, double* partials,
                  double* link_force, void* stream);
 int launch_segments(const double* link_force, const int* seg_begin, int n_seg, double* seg_accum, void* stream);

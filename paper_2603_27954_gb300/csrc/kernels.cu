@@ -491,6 +491,48 @@ __global__ void k_faces(S* __restrict__ f, const FaceEntry* __restrict__ e, int 
   else f[x.dst] = f[x.src];
 }
 
+// deviation f_i^eq(rho = 1, u) - w_i of the product-form equilibrium: per
+// axis 2/3 - u^2 for c = 0 and (1/3 + u^2 + c u) / 2 for c = +-1
+__device__ __forceinline__ float eq_axis(int c, float u) {
+  return c == 0 ? 2.0f / 3.0f - u * u : 0.5f * (1.0f / 3.0f + u * u + c * u);
+}
+__device__ __forceinline__ float eq_dev(int i, float ux, float uy, float uz) {
+  const int a = dcx(i), b = dcy(i), c = dcz(i);
+  const float w = (a ? 1.0f / 6.0f : 2.0f / 3.0f) * (b ? 1.0f / 6.0f : 2.0f / 3.0f) * (c ? 1.0f / 6.0f : 2.0f / 3.0f);
+  return eq_axis(a, ux) * eq_axis(b, uy) * eq_axis(c, uz) - w;
+}
+
+// faces with a turbulent inflow: entries that pull the inflow equilibrium get
+// it at the velocity U e_x + sum_n a_n cos(k_n . (p - U t e_x) + psi_n) of their
+// pulled-from cell centre p, t = coarse steps done (frozen field carried at U)
+template <typename S>
+__global__ void __launch_bounds__(128) k_faces_turb(S* __restrict__ f, const FaceEntry* __restrict__ e, int n,
+                                                     TurbArgs tb) {
+  extern __shared__ float sm[];  // the mode table
+  for (int k = threadIdx.x; k < tb.n_modes * kModeCols; k += blockDim.x) sm[k] = tb.modes[k];
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const FaceEntry x = e[t];
+  if (x.src >= 0) {
+    f[x.dst] = f[x.src];
+    return;
+  }
+  const float px = tb.pos[4 * t] + 0.5f - tb.u * (float)(*tb.tick);
+  const float py = tb.pos[4 * t + 1] + 0.5f, pz = tb.pos[4 * t + 2] + 0.5f;
+  float ux = tb.u, uy = 0.0f, uz = 0.0f;
+  for (int m = 0; m < tb.n_modes; ++m) {
+    const float* r = sm + m * kModeCols;
+    const float c = cosf(fmaf(r[0], px, fmaf(r[1], py, fmaf(r[2], pz, r[6]))));
+    ux = fmaf(r[3], c, ux);
+    uy = fmaf(r[4], c, uy);
+    uz = fmaf(r[5], c, uz);
+  }
+  Store<S>::st(f, x.dst, eq_dev(x.dir, ux, uy, uz) * tb.scale);
+}
+
+__global__ void k_tick(long long* tick) { *tick += 1; }
+
 constexpr int kWallThreads = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -834,13 +876,26 @@ int launch_collide(const CollideArgs& a, int B, int odd, void* stream) {
   return check_launch("collide");
 }
 
-int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], void* stream) {
+int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], const TurbArgs& turb,
+                 void* stream) {
   if (n == 0) return LBM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (turb.n_modes > 0) {
+    const size_t smem = (size_t)turb.n_modes * kModeCols * sizeof(float);
+    if (half) k_faces_turb<__half><<<blocks_for(n, 128), 128, smem, s>>>((__half*)f, e, n, turb);
+    else k_faces_turb<float><<<blocks_for(n, 128), 128, smem, s>>>((float*)f, e, n, turb);
+    return check_launch("faces_turb");
+  }
   Feq27 v;
   for (int i = 0; i < 27; ++i) v.v[i] = feq[i];
-  if (half) k_faces<__half><<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>((__half*)f, e, n, v);
-  else k_faces<float><<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>((float*)f, e, n, v);
+  if (half) k_faces<__half><<<blocks_for(n, 256), 256, 0, s>>>((__half*)f, e, n, v);
+  else k_faces<float><<<blocks_for(n, 256), 256, 0, s>>>((float*)f, e, n, v);
   return check_launch("faces");
+}
+
+int launch_tick(long long* tick, void* stream) {
+  k_tick<<<1, 1, 0, (cudaStream_t)stream>>>(tick);
+  return check_launch("tick");
 }
 
 int walls_partial_count(int n) { return (int)blocks_for(n, kWallThreads); }

@@ -405,6 +405,7 @@ int build_faces(Mesh& m) {
   const long long cpb = v.cells_per_block();
   for (int p = 0; p < 2; ++p) v.face[p].clear();
   std::vector<std::vector<FaceEntry>> part0(v.n_active), part1(v.n_active);
+  std::vector<std::vector<int>> partp(v.n_active);
   std::atomic<bool> bad{false};
   parallel_for(v.n_active, [&](long long s) {
     int o[3];
@@ -416,6 +417,7 @@ int build_faces(Mesh& m) {
     if (!touches) return;
     std::vector<FaceEntry>& f0 = part0[s];
     std::vector<FaceEntry>& f1 = part1[s];
+    std::vector<int>& fp = partp[s];
     for (int z = 0; z < B; ++z)
       for (int y = 0; y < B; ++y)
         for (int x = 0; x < B; ++x) {
@@ -452,6 +454,10 @@ int build_faces(Mesh& m) {
             }
             f0.push_back(e0);
             f1.push_back(e1);
+            int w[3] = {gx, gy, gz};
+            for (int a = 0; a < 3; ++a)
+              if (m.bc[a] == LBM_BC_PERIODIC) w[a] = wrapmod(w[a], m.n0[a]);
+            fp.insert(fp.end(), {w[0], w[1], w[2], 0});
           }
         }
   }, 8);
@@ -459,9 +465,11 @@ int build_faces(Mesh& m) {
     m.error = "face slot without storage";
     return LBM_EINVAL;
   }
+  v.face_pos.clear();
   for (int s = 0; s < v.n_active; ++s) {
     v.face[0].insert(v.face[0].end(), part0[s].begin(), part0[s].end());
     v.face[1].insert(v.face[1].end(), part1[s].begin(), part1[s].end());
+    v.face_pos.insert(v.face_pos.end(), partp[s].begin(), partp[s].end());
   }
   return LBM_OK;
 }

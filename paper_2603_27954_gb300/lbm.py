@@ -76,6 +76,8 @@ def _load():
         "lbm_branch_drag_estimate": ([dp, i, dp, C.c_double, dp, dp], i),
         "lbm_set_branch_forces": ([vp, i], i),
         "lbm_set_wide_offsets": ([vp, i], i),
+        "lbm_set_inflow_turbulence": ([vp, i, C.c_double], i),
+        "lbm_inflow_modes": ([vp, dp, i, ip], i),
         "lbm_get_branch_forces": ([vp, dp, i, llp], i),
         "lbm_use_graphs": ([vp, i], i),
         "lbm_set_timing": ([vp, i], i),
@@ -254,6 +256,19 @@ def lbm_set_branch_forces(h, on):
     return _ck(_lib.lbm_set_branch_forces(h, int(bool(on))), "lbm_set_branch_forces")
 
 
+def lbm_set_inflow_turbulence(h, n_modes=256, integral_length=0.0):
+    return _ck(_lib.lbm_set_inflow_turbulence(h, int(n_modes), float(integral_length)), "lbm_set_inflow_turbulence")
+
+
+def lbm_inflow_modes(h):
+    """Mode table (n x 7: k, a, psi) of a turbulent-inflow domain."""
+    n = C.c_int()
+    _ck(_lib.lbm_inflow_modes(h, None, 0, C.byref(n)), "lbm_inflow_modes")
+    out = np.zeros((max(1, n.value), 7))
+    _ck(_lib.lbm_inflow_modes(h, _dp(out), max(1, n.value), C.byref(n)), "lbm_inflow_modes")
+    return out[:n.value]
+
+
 def lbm_set_wide_offsets(h, on):
     return _ck(_lib.lbm_set_wide_offsets(h, int(bool(on))), "lbm_set_wide_offsets")
 
@@ -331,12 +346,13 @@ def lbm_status_string(code):
 # ---------------------------------------------------------------- descriptors
 
 def domain_desc(nx, ny, nz, levels=1, block=16, bc=("inout", "slip", "slip"), u_in=0.05, re_h=0.0,
-                nu_finest=0.0, refine_margin=0.25, galilean=True, omega2=1.0, boxes=None, precision=LBM_FP32):
+                nu_finest=0.0, refine_margin=0.25, galilean=True, omega2=1.0, boxes=None, precision=LBM_FP32,
+                i_u=0.0, seed=0):
     d = DomainDesc()
     d.nx, d.ny, d.nz, d.levels, d.block = nx, ny, nz, levels, block
     for a in range(3):
         d.bc[a] = BC[bc[a]] if isinstance(bc[a], str) else int(bc[a])
-    d.u_in, d.re_h, d.nu_finest, d.i_u, d.seed = u_in, re_h, nu_finest, 0.0, 0
+    d.u_in, d.re_h, d.nu_finest, d.i_u, d.seed = u_in, re_h, nu_finest, i_u, seed
     d.refine_margin, d.precision, d.galilean, d.omega2 = refine_margin, precision, int(galilean), omega2
     if boxes:
         for l, b in enumerate(boxes):
