@@ -142,6 +142,57 @@ def precision_form(L, W, torch, stream, steps, warmup, peak):
     return out
 
 
+def batched_form(L, W, torch, stream, steps, peak):
+    """The 16-case batched form: the cases stepped one after another (each by
+    its own CUDA graph) against the batch (one persistent collide launch per
+    level depth and sub-step, one graph per coarse step), schedule from the
+    autotuner."""
+    doms, updates = [], 0
+    for c in W.batch_cases():
+        desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
+                             re_h=c["re_h"], i_u=c["i_u"], seed=c["seed"])
+        d = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=stream)
+        updates += d.work_per_step()[0]
+        doms.append(d)
+    blocks = [sum(L.lbm_level_info(d.h, l)["n_active_blocks"] for l in range(d.desc.levels)) for d in doms]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def sequential(n):
+        for _ in range(n):
+            for d in doms:
+                d.step(1)
+
+    sequential(3)
+    ms_seq = timed(lambda: sequential(steps))
+    batch = L.Batch(doms, stream=stream)
+    best, tune_ms = batch.autotune(steps=3)
+    batch.step(3)
+    ms_batch = timed(lambda: batch.step(steps))
+    batch.close()
+    gb = sum(d.nbytes for d in doms) / 1e9
+    for d in doms:
+        d.close()
+    torch.cuda.empty_cache()
+    seq = updates * steps / (ms_seq / 1e3) / 1e6
+    bat = updates * steps / (ms_batch / 1e3) / 1e6
+    return {"workload": "16 cases: trees of 1-4 child generations x Re_H {2.5e3, 1e4, 4e4, 1.2e5}, 2-3 levels, "
+                        "16^3 blocks (%d-%d blocks per case), I_u = 8 %% random-Fourier-mode inflow in half "
+                        "of them" % (min(blocks), max(blocks)),
+            "unit": "MLUPS", "steps": steps, "updates_per_step": updates, "device_gb": gb,
+            "value": bat, "sequential_value": seq, "speedup_vs_sequential": bat / seq,
+            "ms_per_step": ms_batch / steps, "sequential_ms_per_step": ms_seq / steps,
+            "schedule": best.as_dict(), "autotune_ms_per_step": tune_ms,
+            "path_frac": updates * BYTES_PER_UPDATE * steps / (ms_batch / 1e3) / 1e9 / peak}
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons while running."""
 
@@ -256,6 +307,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--no-precision-form", action="store_true")
+    ap.add_argument("--no-batched-form", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--precision-steps", type=int, default=10)
     ap.add_argument("--timing-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=50)
@@ -357,6 +410,9 @@ def main():
     prec_form = None
     if not args.no_precision_form:
         prec_form = precision_form(L, W, torch, stream, args.precision_steps, 3, peak)
+    batched = None
+    if not args.no_batched_form:
+        batched = batched_form(L, W, torch, stream, args.batched_steps, peak)
 
     cpu = None
     cd_err = None
@@ -401,6 +457,7 @@ def main():
                 "note": "includes binding (table upload and equilibrium initialisation of %.2f GB) once and a "
                         "synchronous drag read after each of %d steps" % (dom.nbytes / 1e9, args.e2e_steps)},
         "precision_form": prec_form,
+        "batched_form": batched,
         "gpu_launches": kernels * args.steps,
         "kernels_per_step": kernels,
         "cd": cd,

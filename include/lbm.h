@@ -57,6 +57,14 @@ typedef enum {
    Collision arithmetic is FP32 in both; the drag and mass reductions FP64. */
 typedef enum { LBM_FP32 = 1, LBM_FP16_DEV = 2 } lbm_precision;
 
+/* Collide-kernel variants (all compute the same result).  Odd AA step:
+   per-thread column pointers (default), TMA/cp.async staging through shared
+   memory (FP32 and 16^3 blocks only; others fall back to the default), or
+   direct neighbour addressing.  Even step: direct loads and stores (default)
+   or a 4-stage TMA bulk pipeline (FP32 and 16^3 blocks only). */
+typedef enum { LBM_ODD_COLUMNS = 0, LBM_ODD_STAGED = 1, LBM_ODD_DIRECT = 2 } lbm_odd_variant;
+typedef enum { LBM_EVEN_DIRECT = 0, LBM_EVEN_TMA = 1 } lbm_even_variant;
+
 /* Problem statement (Sec. 2.2-2.3): domain, inflow, Re_H, refinement.
    Coarse level = level 0; every finer level halves the cell size and the
    time step (acoustic scaling, nu_{l+1} = 2 nu_l in lattice units). */
@@ -297,6 +305,43 @@ int lbm_set_inflow_turbulence(lbm_domain* d, int n_modes, double integral_length
 /* The mode table, 7 doubles per mode: k (3), a (3), psi; n is the capacity
    in modes, *count the number of modes (0 for uniform inflow). */
 int lbm_inflow_modes(const lbm_domain* d, double* modes, int n, int* count);
+
+/* ---- Schedules, autotuning and batches ----
+   A schedule picks the collide-kernel variants and, for batches, the size of
+   the persistent grid (ctas_per_sm CTAs per SM, 0: one CTA per block).
+   lbm_autotune and lbm_batch_autotune time every available candidate for
+   `steps` coarse steps (after one untimed step each) with CUDA events and
+   keep the fastest; they advance the simulation by the steps they time, so
+   re-initialise (lbm_init_uniform) before a production run. */
+typedef struct {
+  int ctas_per_sm;   /* batches only; ignored by single domains */
+  int odd_variant;   /* lbm_odd_variant */
+  int even_variant;  /* lbm_even_variant */
+} lbm_schedule;
+int lbm_set_schedule(lbm_domain* d, const lbm_schedule* s);
+int lbm_get_schedule(const lbm_domain* d, lbm_schedule* s);
+int lbm_autotune(lbm_domain* d, int steps, lbm_schedule* best, double* ms_per_step);
+
+/* A batch steps several independent domains (bound, same block size and
+   precision, same step parity) in lockstep: per level depth and sub-step
+   ONE persistent collide launch walks a work list of (level, block) pairs of
+   every domain that has that level, the per-domain boundary, force and
+   interface kernels follow on the batch's stream, and each coarse step of
+   the whole batch is one CUDA graph launch.  Results are identical to
+   stepping each domain alone.  The batch binds its own small device buffer
+   (descriptors and work lists).  Batches take the column-pointer or direct
+   odd step and the direct even step.  The domains must outlive the batch
+   and must not be stepped on their own while they are in it. */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_create(lbm_domain* const* domains, int n, void* cuda_stream, lbm_batch** out);
+int lbm_batch_memory_requirements(const lbm_batch* b, size_t* bytes);
+int lbm_batch_bind_memory(lbm_batch* b, void* device_ptr, size_t bytes);
+int lbm_batch_set_schedule(lbm_batch* b, const lbm_schedule* s);
+int lbm_batch_get_schedule(const lbm_batch* b, lbm_schedule* s);
+int lbm_batch_step(lbm_batch* b, int n_coarse_steps);
+int lbm_batch_use_graphs(lbm_batch* b, int on);
+int lbm_batch_autotune(lbm_batch* b, int steps, lbm_schedule* best, double* ms_per_step);
+void lbm_batch_destroy(lbm_batch* b);
 
 /* Run the collide kernels with 64-bit element offsets even on levels whose
    arrays hold fewer than 2^31 elements (they switch to 64-bit offsets by

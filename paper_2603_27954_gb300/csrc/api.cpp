@@ -65,6 +65,7 @@ struct lbm_domain {
   int n_seg = 0;
   bool branch_forces = false;
   bool wide_offsets = false;  // force the 64-bit-offset collide kernels
+  int odd_variant = LBM_ODD_COLUMNS, even_variant = LBM_EVEN_DIRECT;
   // turbulent inflow (random Fourier modes), on when d.i_u > 0
   int n_modes = 256;
   double l_int = 0;  // integral length in level-0 cells; 0: the tree height
@@ -133,20 +134,22 @@ struct Timed {
   }
 };
 
-int advance(lbm_domain* dm, int l, int parity) {
+CollideArgs collide_args(lbm_domain* dm, int l) {
+  Level& v = dm->mesh.lv[l];
+  return CollideArgs{dm->base + v.off_f, (long long)v.f_elems(), dm->dev<int>(v.off_nbr),
+                     dm->dev<int>(v.off_maskoff), dm->dev<uint8_t>(v.off_masks), v.n_active, (float)v.omega1,
+                     (float)dm->d.omega2, dm->d.galilean, dm->dev<double>(dm->off_accum) + 7, v.esize == 2, v.scale,
+                     1.0f / v.scale, dm->wide_offsets ? 1 : 0, dm->odd_variant, dm->even_variant};
+}
+
+// level l after its collide-stream sweep: faces (level 0), bounce-back and
+// momentum exchange, per-branch and total force reductions (finest level)
+int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s) {
   Mesh& m = dm->mesh;
   Level& v = m.lv[l];
   void* f = dm->base + v.off_f;
   const int half = v.esize == 2;
   int rc;
-  {
-    Timed t(dm, parity ? KC_COLLIDE_ODD : KC_COLLIDE, v.n_fluid);
-    CollideArgs a{f, (long long)v.f_elems(), dm->dev<int>(v.off_nbr), dm->dev<int>(v.off_maskoff),
-                  dm->dev<uint8_t>(v.off_masks), v.n_active, (float)v.omega1, (float)dm->d.omega2,
-                  dm->d.galilean, dm->dev<double>(dm->off_accum) + 7, v.esize == 2, v.scale, 1.0f / v.scale,
-                  dm->wide_offsets ? 1 : 0};
-    if ((rc = launch_collide(a, v.B, parity, dm->stream))) return rc;
-  }
   if (l == 0 && !v.face[parity].empty()) {
     Timed t(dm, KC_FACES, (long long)v.face[parity].size());
     float feq[27];
@@ -159,7 +162,7 @@ int advance(lbm_domain* dm, int l, int parity) {
       tb.tick = dm->dev<long long>(dm->off_tick);
     }
     if ((rc = launch_faces(f, half, dm->dev<FaceEntry>(v.off_face[parity]), (int)v.face[parity].size(), feq, tb,
-                           dm->stream)))
+                           s)))
       return rc;
   }
   if (!v.wall[parity].empty()) {
@@ -168,40 +171,66 @@ int advance(lbm_domain* dm, int l, int parity) {
     const bool per_branch = dm->branch_forces && l == m.L - 1;
     if ((rc = launch_walls(f, half, 1.0f / v.scale, dm->dev<WallEntry>(v.off_wall[parity]), n,
                            dm->dev<double>(dm->off_partials), per_branch ? dm->dev<double>(dm->off_linkf) : nullptr,
-                           dm->stream)))
+                           s)))
       return rc;
     if (per_branch && (rc = launch_segments(dm->dev<double>(dm->off_linkf), dm->dev<int>(dm->off_segb), dm->n_seg,
-                                            dm->dev<double>(dm->off_segacc), dm->stream)))
+                                            dm->dev<double>(dm->off_segacc), s)))
       return rc;
-    if (l == m.L - 1 &&
-        (rc = launch_force_reduce(dm->dev<double>(dm->off_partials), walls_partial_count(n),
-                                  dm->dev<double>(dm->off_accum), dm->stream)))
+    if (l == m.L - 1 && (rc = launch_force_reduce(dm->dev<double>(dm->off_partials), walls_partial_count(n),
+                                                  dm->dev<double>(dm->off_accum), s)))
       return rc;
   }
+  return LBM_OK;
+}
+
+// coarse post-collision values into the fine ghosts before the second fine step
+int iface_explode(lbm_domain* dm, int l, int parity, cudaStream_t s) {
+  Level& v = dm->mesh.lv[l];
+  Level& F = dm->mesh.lv[l + 1];
+  Timed t(dm, KC_IFACE, (long long)v.expl.size());
+  return launch_explode(dm->base + F.off_f, dm->base + v.off_f, v.esize == 2, F.scale / v.scale,
+                        dm->dev<ExplodeEntry>(v.off_expl), (int)v.expl.size(), dm->dev<SaveEntry>(v.off_save),
+                        (int)v.save.size(), dm->dev<float>(v.off_saved), parity, s);
+}
+
+// fine inflow for the next first fine step, and coarse cells from their children
+int iface_inflow(lbm_domain* dm, int l, int parity, cudaStream_t s) {
+  Level& v = dm->mesh.lv[l];
+  Level& F = dm->mesh.lv[l + 1];
+  Timed t(dm, KC_IFACE, (long long)v.infl.size() + (long long)v.coal.size());
+  void* ff = dm->base + F.off_f;
+  void* f = dm->base + v.off_f;
+  const float ratio = F.scale / v.scale;
+  float* saved = dm->dev<float>(v.off_saved);
+  int rc = launch_inflow(ff, f, v.esize == 2, ratio, dm->dev<InflowEntry>(v.off_infl), (int)v.infl.size(), saved,
+                         parity, s);
+  if (rc) return rc;
+  return launch_coalesce(f, ff, v.esize == 2, ratio, dm->dev<CoalesceEntry>(v.off_coal), (int)v.coal.size(), saved,
+                         parity, s);
+}
+
+int end_coarse_step(lbm_domain* dm, cudaStream_t s) {
+  if (dm->d.i_u > 0) return launch_tick(dm->dev<long long>(dm->off_tick), s);
+  return LBM_OK;
+}
+
+// one step of level l (recursively the two steps of every finer level)
+int advance(lbm_domain* dm, int l, int parity) {
+  Mesh& m = dm->mesh;
+  Level& v = m.lv[l];
+  int rc;
+  {
+    Timed t(dm, parity ? KC_COLLIDE_ODD : KC_COLLIDE, v.n_fluid);
+    if ((rc = launch_collide(collide_args(dm, l), v.B, parity, dm->stream))) return rc;
+  }
+  if ((rc = post_collide(dm, l, parity, dm->stream))) return rc;
   if (l + 1 < m.L) {
-    Level& F = m.lv[l + 1];
-    void* ff = dm->base + F.off_f;
-    float* saved = dm->dev<float>(v.off_saved);
-    const float ratio = F.scale / v.scale;
     if ((rc = advance(dm, l + 1, 0))) return rc;
-    {
-      Timed t(dm, KC_IFACE, (long long)v.expl.size());
-      if ((rc = launch_explode(ff, f, half, ratio, dm->dev<ExplodeEntry>(v.off_expl), (int)v.expl.size(),
-                               dm->dev<SaveEntry>(v.off_save), (int)v.save.size(), saved, parity, dm->stream)))
-        return rc;
-    }
+    if ((rc = iface_explode(dm, l, parity, dm->stream))) return rc;
     if ((rc = advance(dm, l + 1, 1))) return rc;
-    {
-      Timed t(dm, KC_IFACE, (long long)v.infl.size() + (long long)v.coal.size());
-      if ((rc = launch_inflow(ff, f, half, ratio, dm->dev<InflowEntry>(v.off_infl), (int)v.infl.size(), saved,
-                              parity, dm->stream)))
-        return rc;
-      if ((rc = launch_coalesce(f, ff, half, ratio, dm->dev<CoalesceEntry>(v.off_coal), (int)v.coal.size(), saved,
-                                parity, dm->stream)))
-        return rc;
-    }
+    if ((rc = iface_inflow(dm, l, parity, dm->stream))) return rc;
   }
-  if (l == 0 && dm->d.i_u > 0 && (rc = launch_tick(dm->dev<long long>(dm->off_tick), dm->stream))) return rc;
+  if (l == 0) return end_coarse_step(dm, dm->stream);
   return LBM_OK;
 }
 
@@ -1013,6 +1042,325 @@ void lbm_destroy(lbm_domain* d) {
   free_graphs(d);
   for (auto e : d->pool) cudaEventDestroy(e);
   delete d;
+}
+
+
+// ---------------------------------------------------------------- schedules and autotuning
+
+namespace {
+
+bool variant_ok(const lbm_domain* d, int odd, int even) {
+  if (odd < LBM_ODD_COLUMNS || odd > LBM_ODD_DIRECT || even < LBM_EVEN_DIRECT || even > LBM_EVEN_TMA) return false;
+  const bool staged_ok = d->d.precision == LBM_FP32 && d->d.block == 16;
+  if (odd == LBM_ODD_STAGED && !staged_ok) return false;
+  if (even == LBM_EVEN_TMA && !staged_ok) return false;
+  return true;
+}
+
+// CUDA-event time of `steps` coarse steps after one untimed step
+int time_steps(lbm_domain* d, int steps, double* ms) {
+  int rc = lbm_step(d, 1);
+  if (rc) return rc;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, d->stream));
+  rc = lbm_step(d, steps);
+  CK(cudaEventRecord(b, d->stream));
+  CK(cudaEventSynchronize(b));
+  float t = 0;
+  cudaEventElapsedTime(&t, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = t / std::max(1, steps);
+  return rc;
+}
+
+}  // namespace
+
+int lbm_set_schedule(lbm_domain* d, const lbm_schedule* s) {
+  if (!d || !s) return fail(LBM_EINVAL, "null argument");
+  if (!variant_ok(d, s->odd_variant, s->even_variant)) return fail(LBM_EINVAL, "variant not available here");
+  if (d->odd_variant != s->odd_variant || d->even_variant != s->even_variant) free_graphs(d);
+  d->odd_variant = s->odd_variant;
+  d->even_variant = s->even_variant;
+  return LBM_OK;
+}
+
+int lbm_get_schedule(const lbm_domain* d, lbm_schedule* s) {
+  if (!d || !s) return fail(LBM_EINVAL, "null argument");
+  s->ctas_per_sm = 0;
+  s->odd_variant = d->odd_variant;
+  s->even_variant = d->even_variant;
+  return LBM_OK;
+}
+
+int lbm_autotune(lbm_domain* d, int steps, lbm_schedule* best, double* ms_per_step) {
+  if (!d || steps < 1) return fail(LBM_EINVAL, "bad argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  lbm_schedule b{0, d->odd_variant, d->even_variant};
+  double bms = std::numeric_limits<double>::infinity();
+  for (int odd = LBM_ODD_COLUMNS; odd <= LBM_ODD_DIRECT; ++odd)
+    for (int even = LBM_EVEN_DIRECT; even <= LBM_EVEN_TMA; ++even) {
+      if (!variant_ok(d, odd, even)) continue;
+      lbm_schedule c{0, odd, even};
+      int rc = lbm_set_schedule(d, &c);
+      if (rc) return rc;
+      double ms;
+      if ((rc = time_steps(d, steps, &ms))) return rc;
+      if (ms < bms) {
+        bms = ms;
+        b = c;
+      }
+    }
+  int rc = lbm_set_schedule(d, &b);
+  if (rc) return rc;
+  if (best) *best = b;
+  if (ms_per_step) *ms_per_step = bms;
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+
+struct lbm_batch {
+  std::vector<lbm_domain*> doms;
+  cudaStream_t stream = nullptr;
+  int B = 16, half = 0, wide = 0, L = 1, sms = 1;
+  std::vector<CollideArgs> descs;          // per (domain, level)
+  std::vector<std::vector<int2>> items;    // per depth: (descriptor, block) of every domain with that level
+  char* base = nullptr;
+  size_t need = 0, off_descs = 0;
+  std::vector<size_t> off_items;
+  lbm_schedule sched{0, LBM_ODD_COLUMNS, LBM_EVEN_DIRECT};
+  bool use_graphs = true;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+void free_batch_graphs(lbm_batch* b) {
+  for (auto& g : b->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// device descriptors follow the domains' schedules and offsets
+void build_descs(lbm_batch* b) {
+  b->descs.clear();
+  for (lbm_domain* d : b->doms) {
+    d->odd_variant = b->sched.odd_variant;
+    for (int l = 0; l < d->mesh.L; ++l) b->descs.push_back(collide_args(d, l));
+  }
+}
+
+int batch_advance(lbm_batch* b, int l, int parity) {
+  const int grid = b->sched.ctas_per_sm > 0 ? b->sched.ctas_per_sm * b->sms : 0;
+  int rc = launch_collide_batch(reinterpret_cast<const CollideArgs*>(b->base + b->off_descs),
+                                reinterpret_cast<const int2*>(b->base + b->off_items[l]), (int)b->items[l].size(), b->B,
+                                parity, b->sched.odd_variant, b->half, b->wide, grid, b->stream);
+  if (rc) return fail(rc, cuda_error_string());
+  for (lbm_domain* d : b->doms)
+    if (l < d->mesh.L && (rc = post_collide(d, l, parity, b->stream))) return fail(rc, cuda_error_string());
+  if (l + 1 < b->L) {
+    if ((rc = batch_advance(b, l + 1, 0))) return rc;
+    for (lbm_domain* d : b->doms)
+      if (l + 1 < d->mesh.L && (rc = iface_explode(d, l, parity, b->stream))) return fail(rc, cuda_error_string());
+    if ((rc = batch_advance(b, l + 1, 1))) return rc;
+    for (lbm_domain* d : b->doms)
+      if (l + 1 < d->mesh.L && (rc = iface_inflow(d, l, parity, b->stream))) return fail(rc, cuda_error_string());
+  }
+  if (l == 0)
+    for (lbm_domain* d : b->doms)
+      if ((rc = end_coarse_step(d, b->stream))) return fail(rc, cuda_error_string());
+  return LBM_OK;
+}
+
+int upload_descs(lbm_batch* b) {
+  build_descs(b);
+  CK(cudaMemcpyAsync(b->base + b->off_descs, b->descs.data(), b->descs.size() * sizeof(CollideArgs),
+                     cudaMemcpyHostToDevice, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  return LBM_OK;
+}
+
+int capture_batch(lbm_batch* b) {
+  if (!b->use_graphs || b->stream == nullptr) return LBM_OK;
+  for (int p = 0; p < 2; ++p) {
+    if (b->graph[p]) continue;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = batch_advance(b, 0, p);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(lbm_domain* const* domains, int n, void* cuda_stream, lbm_batch** out) {
+  if (!domains || n < 1 || !out) return fail(LBM_EINVAL, "bad argument");
+  *out = nullptr;
+  auto* b = new (std::nothrow) lbm_batch();
+  if (!b) return fail(LBM_ENOMEM, "host allocation");
+  b->stream = (cudaStream_t)cuda_stream;
+  for (int k = 0; k < n; ++k) {
+    lbm_domain* d = domains[k];
+    std::string why;
+    if (!d || !d->base) why = "every domain must have bound memory";
+    else if (d->d.block != domains[0]->d.block) why = "all domains must share the block size";
+    else if (d->d.precision != domains[0]->d.precision) why = "all domains must share the storage precision";
+    else if (d->parity0 != domains[0]->parity0) why = "all domains must be at the same step parity";
+    else if (d->timing) why = "per-class timing must be off";
+    for (int j = 0; j < k && why.empty(); ++j)
+      if (domains[j] == d) why = "a domain appears twice";
+    if (!why.empty()) {
+      delete b;
+      return fail(LBM_EINVAL, why);
+    }
+    b->doms.push_back(d);
+    b->L = std::max(b->L, d->mesh.L);
+    for (const Level& v : d->mesh.lv)
+      if (v.f_elems() >= (1LL << 31) || d->wide_offsets) b->wide = 1;
+  }
+  b->B = domains[0]->d.block;
+  b->half = domains[0]->d.precision == LBM_FP16_DEV;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) b->sms = 1;
+  b->items.assign(b->L, {});
+  int desc = 0;
+  for (lbm_domain* d : b->doms)
+    for (int l = 0; l < d->mesh.L; ++l, ++desc)
+      for (int s2 = 0; s2 < d->mesh.lv[l].n_active; ++s2) b->items[l].push_back(int2{desc, s2});
+  size_t off = 0;
+  auto put = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  b->off_descs = put((size_t)desc * sizeof(CollideArgs));
+  for (int l = 0; l < b->L; ++l) b->off_items.push_back(put(b->items[l].size() * sizeof(int2)));
+  b->need = off;
+  *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_memory_requirements(const lbm_batch* b, size_t* bytes) {
+  if (!b || !bytes) return fail(LBM_EINVAL, "null argument");
+  *bytes = b->need;
+  return LBM_OK;
+}
+
+int lbm_batch_bind_memory(lbm_batch* b, void* ptr, size_t bytes) {
+  if (!b || !ptr) return fail(LBM_EINVAL, "null argument");
+  if (bytes < b->need) return fail(LBM_ENOMEM, "bound buffer smaller than lbm_batch_memory_requirements");
+  if ((uintptr_t)ptr & 255) return fail(LBM_EINVAL, "bound buffer must be 256-byte aligned");
+  free_batch_graphs(b);
+  b->base = (char*)ptr;
+  for (int l = 0; l < b->L; ++l)
+    if (!b->items[l].empty())
+      CK(cudaMemcpyAsync(b->base + b->off_items[l], b->items[l].data(), b->items[l].size() * sizeof(int2),
+                         cudaMemcpyHostToDevice, b->stream));
+  return upload_descs(b);
+}
+
+int lbm_batch_set_schedule(lbm_batch* b, const lbm_schedule* s) {
+  if (!b || !s) return fail(LBM_EINVAL, "null argument");
+  if (s->ctas_per_sm < 0 || s->ctas_per_sm > 64 || (s->odd_variant != LBM_ODD_COLUMNS && s->odd_variant != LBM_ODD_DIRECT))
+    return fail(LBM_EINVAL, "batches take column-pointer or direct odd steps and 0..64 CTAs per SM");
+  b->sched = *s;
+  b->sched.even_variant = LBM_EVEN_DIRECT;
+  free_batch_graphs(b);
+  for (lbm_domain* d : b->doms) free_graphs(d);
+  if (b->base) return upload_descs(b);
+  return LBM_OK;
+}
+
+int lbm_batch_get_schedule(const lbm_batch* b, lbm_schedule* s) {
+  if (!b || !s) return fail(LBM_EINVAL, "null argument");
+  *s = b->sched;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int n) {
+  if (!b || n < 0) return fail(LBM_EINVAL, "bad argument");
+  if (!b->base) return fail(LBM_ESTATE, "bind memory first");
+  const int p0 = b->doms[0]->parity0;
+  for (lbm_domain* d : b->doms)
+    if (d->parity0 != p0 || !d->base) return fail(LBM_ESTATE, "domains left lockstep or lost their memory");
+  int rc = capture_batch(b);
+  if (rc) return rc;
+  for (int k = 0; k < n; ++k) {
+    const int p = b->doms[0]->parity0;
+    if (b->graph[p]) {
+      CK(cudaGraphLaunch(b->graph[p], b->stream));
+    } else if ((rc = batch_advance(b, 0, p))) {
+      return rc;
+    }
+    for (lbm_domain* d : b->doms) {
+      d->parity0 ^= 1;
+      d->steps++;
+    }
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_use_graphs(lbm_batch* b, int on) {
+  if (!b) return fail(LBM_EINVAL, "null argument");
+  b->use_graphs = on != 0;
+  if (!on) free_batch_graphs(b);
+  return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch* b, int steps, lbm_schedule* best, double* ms_per_step) {
+  if (!b || steps < 1) return fail(LBM_EINVAL, "bad argument");
+  if (!b->base) return fail(LBM_ESTATE, "bind memory first");
+  static const int kCtas[] = {0, 1, 2, 3, 4, 6, 8};
+  lbm_schedule bs = b->sched;
+  double bms = std::numeric_limits<double>::infinity();
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = LBM_OK;
+  for (int odd : {(int)LBM_ODD_COLUMNS, (int)LBM_ODD_DIRECT})
+    for (int c : kCtas) {
+      lbm_schedule s{c, odd, LBM_EVEN_DIRECT};
+      if ((rc = lbm_batch_set_schedule(b, &s)) || (rc = lbm_batch_step(b, 1))) break;
+      cudaEventRecord(e0, b->stream);
+      if ((rc = lbm_batch_step(b, steps))) break;
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float t = 0;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (t / steps < bms) {
+        bms = t / steps;
+        bs = s;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if ((rc = lbm_batch_set_schedule(b, &bs))) return rc;
+  if (best) *best = bs;
+  if (ms_per_step) *ms_per_step = bms;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  free_batch_graphs(b);
+  delete b;
 }
 
 }  // extern "C"

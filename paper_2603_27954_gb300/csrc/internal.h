@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <vector_types.h>  // int2
+
 #include "../../include/lbm.h"
 
 namespace lbm {
@@ -164,6 +166,8 @@ struct CollideArgs {
   int half;           // FP16 storage of scaled deviations
   float scale, inv_scale;
   int wide;           // 64-bit element offsets even when f_elems < 2^31
+  int odd_variant;    // LBM_ODD_COLUMNS | LBM_ODD_STAGED | LBM_ODD_DIRECT
+  int even_variant;   // LBM_EVEN_DIRECT | LBM_EVEN_TMA
 };
 int prepare_kernels();
 int launch_collide(const CollideArgs& a, int B, int odd, void* stream);
@@ -177,6 +181,9 @@ struct TurbArgs {      // turbulent inflow; n_modes == 0: uniform inflow equilib
 };
 int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], const TurbArgs& turb,
                  void* stream);
+// one launch over a work list of (index into lv, block) pairs; grid <= 0: one CTA per item
+int launch_collide_batch(const CollideArgs* lv, const int2* items, int n_items, int B, int odd, int odd_variant,
+                         int half, int wide, int grid, void* stream);
 int launch_tick(long long* tick, void* stream);
 int launch_walls(void* f, int half, float inv_scale, const WallEntry* e, int n, double* partials,
                  double* link_force, void* stream);

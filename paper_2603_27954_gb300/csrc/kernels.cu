@@ -15,6 +15,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <cstdio>
@@ -61,11 +62,12 @@ struct Store<__half> {
 #endif
 
 // IDX: element-offset type, 32-bit when the level's array has < 2^31 elements
+// One active block `blk` of a level: even step (own slots) or odd step with
+// direct neighbour addressing.  s_base: 27 shared slots for the neighbour
+// blocks' element offsets.
 template <int B, bool ODD, typename IDX, typename S>
-__global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_collide(CollideArgs a) {
+__device__ __forceinline__ void collide_block(const CollideArgs& a, const int blk, IDX* s_base) {
   constexpr int C3 = B * B * B;
-  __shared__ IDX s_base[27];
-  const int blk = blockIdx.x;
   if (threadIdx.x < 27) s_base[threadIdx.x] = (IDX)a.nbr[(size_t)blk * 27 + threadIdx.x] * (IDX)(27 * C3);
   __syncthreads();
   const int lx = threadIdx.x % B, ly = threadIdx.x / B;
@@ -107,6 +109,12 @@ __global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_c
       }
     }
   }
+}
+
+template <int B, bool ODD, typename IDX, typename S>
+__global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_collide(CollideArgs a) {
+  __shared__ IDX s_base[27];
+  collide_block<B, ODD, IDX, S>(a, blockIdx.x, s_base);
 }
 
 // ---------------------------------------------------------------------------
@@ -421,10 +429,8 @@ __global__ void __launch_bounds__(256, 2) k_collide_even_tma(CollideArgs a) {
 // slabs, where 9 directions reach into the z neighbours, take the general
 // address path (the branch is uniform across the CTA).
 template <int B, typename IDX, typename S>
-__global__ void __launch_bounds__(B * B, LBM_ODD_MINB) k_collide_odd_cols(CollideArgs a) {
+__device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int blk, IDX* s_base) {
   constexpr int C3 = B * B * B, S2 = B * B;
-  __shared__ IDX s_base[27];
-  const int blk = blockIdx.x;
   const int t = threadIdx.x;
   if (t < 27) s_base[t] = (IDX)a.nbr[(size_t)blk * 27 + t] * (IDX)(27 * C3);
   __syncthreads();
@@ -475,6 +481,28 @@ __global__ void __launch_bounds__(B * B, LBM_ODD_MINB) k_collide_odd_cols(Collid
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) col[k] += S2;
+  }
+}
+
+template <int B, typename IDX, typename S>
+__global__ void __launch_bounds__(B * B, LBM_ODD_MINB) k_collide_odd_cols(CollideArgs a) {
+  __shared__ IDX s_base[27];
+  odd_cols_block<B, IDX, S>(a, blockIdx.x, s_base);
+}
+
+// Batched, persistent form: the CTAs walk a work list of (level descriptor,
+// block) pairs that spans several domains and levels, `gridDim.x` apart.
+// KIND 0: even step; 1: odd step, direct addressing; 2: odd step, column pointers.
+template <int B, int KIND, typename IDX, typename S>
+__global__ void __launch_bounds__(B * B, KIND ? LBM_ODD_MINB : LBM_EVEN_MINB)
+    k_collide_batch(const CollideArgs* __restrict__ lv, const int2* __restrict__ items, int n) {
+  __shared__ IDX s_base[27];
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int2 w = items[it];
+    const CollideArgs a = lv[w.x];
+    __syncthreads();  // the previous item's readers of s_base are done
+    if (KIND == 2) odd_cols_block<B, IDX, S>(a, w.y, s_base);
+    else collide_block<B, KIND == 1, IDX, S>(a, w.y, s_base);
   }
 }
 
@@ -817,22 +845,17 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 
 const char* cuda_error_string() { return g_err; }
 
-#ifndef LBM_ODD_VARIANT
-#define LBM_ODD_VARIANT 0  // 0 column pointers, 1 shared-memory staging, 2 direct
-#endif
-#ifndef LBM_EVEN_VARIANT
-#define LBM_EVEN_VARIANT 0  // 0 direct, 1 bulk copies through shared memory
-#endif
-
 template <int B, typename IDX, typename S>
 void collide_on(const CollideArgs& a, int odd, cudaStream_t s) {
   constexpr bool f32 = std::is_same<S, float>::value;
   if (odd) {
-    if (f32 && LBM_ODD_VARIANT == 1 && B == 16) k_collide_odd_staged<IDX><<<a.n_active, 256, kStageBytes, s>>>(a);
-    else if (LBM_ODD_VARIANT == 2) k_collide<B, true, IDX, S><<<a.n_active, B * B, 0, s>>>(a);
+    if (f32 && a.odd_variant == LBM_ODD_STAGED && B == 16)
+      k_collide_odd_staged<IDX><<<a.n_active, 256, kStageBytes, s>>>(a);
+    else if (a.odd_variant == LBM_ODD_DIRECT) k_collide<B, true, IDX, S><<<a.n_active, B * B, 0, s>>>(a);
     else k_collide_odd_cols<B, IDX, S><<<a.n_active, B * B, 0, s>>>(a);
   } else {
-    if (f32 && LBM_EVEN_VARIANT == 1 && B == 16) k_collide_even_tma<IDX><<<a.n_active, 256, kEvenBytes, s>>>(a);
+    if (f32 && a.even_variant == LBM_EVEN_TMA && B == 16)
+      k_collide_even_tma<IDX><<<a.n_active, 256, kEvenBytes, s>>>(a);
     else k_collide<B, false, IDX, S><<<a.n_active, B * B, 0, s>>>(a);
   }
 }
@@ -846,6 +869,25 @@ void collide_typed(const CollideArgs& a, int B, int odd, cudaStream_t s) {
   } else {
     if (small) collide_on<8, int, S>(a, odd, s);
     else collide_on<8, long long, S>(a, odd, s);
+  }
+}
+
+template <int B, typename IDX, typename S>
+void batch_on(const CollideArgs* lv, const int2* items, int n, int kind, int grid, cudaStream_t s) {
+  if (kind == 0) k_collide_batch<B, 0, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n);
+  else if (kind == 1) k_collide_batch<B, 1, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n);
+  else k_collide_batch<B, 2, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n);
+}
+
+template <typename S>
+void batch_typed(const CollideArgs* lv, const int2* items, int n, int B, int wide, int kind, int grid,
+                 cudaStream_t s) {
+  if (B == 16) {
+    if (!wide) batch_on<16, int, S>(lv, items, n, kind, grid, s);
+    else batch_on<16, long long, S>(lv, items, n, kind, grid, s);
+  } else {
+    if (!wide) batch_on<8, int, S>(lv, items, n, kind, grid, s);
+    else batch_on<8, long long, S>(lv, items, n, kind, grid, s);
   }
 }
 
@@ -874,6 +916,18 @@ int launch_collide(const CollideArgs& a, int B, int odd, void* stream) {
   if (a.half) collide_typed<__half>(a, B, odd, s);
   else collide_typed<float>(a, B, odd, s);
   return check_launch("collide");
+}
+
+int launch_collide_batch(const CollideArgs* lv, const int2* items, int n_items, int B, int odd, int odd_variant,
+                         int half, int wide, int grid, void* stream) {
+  if (n_items == 0) return LBM_OK;
+  if (B != 16 && B != 8) return LBM_EINVAL;
+  const int kind = !odd ? 0 : (odd_variant == LBM_ODD_DIRECT ? 1 : 2);
+  const int g = grid > 0 ? std::min(grid, n_items) : n_items;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (half) batch_typed<__half>(lv, items, n_items, B, wide, kind, g, s);
+  else batch_typed<float>(lv, items, n_items, B, wide, kind, g, s);
+  return check_launch("collide_batch");
 }
 
 int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], const TurbArgs& turb,

@@ -36,6 +36,18 @@ class TreeDesc(C.Structure):
                 ("seed", C.c_ulonglong), ("trunk_cells", C.c_double)]
 
 
+class Schedule(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int), ("odd_variant", C.c_int), ("even_variant", C.c_int)]
+
+    def as_dict(self):
+        return {"ctas_per_sm": self.ctas_per_sm, "odd_variant": ODD_VARIANTS[self.odd_variant],
+                "even_variant": EVEN_VARIANTS[self.even_variant]}
+
+
+ODD_VARIANTS = {0: "columns", 1: "staged", 2: "direct"}
+EVEN_VARIANTS = {0: "direct", 1: "tma"}
+
+
 class LbmError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -77,6 +89,18 @@ def _load():
         "lbm_set_branch_forces": ([vp, i], i),
         "lbm_set_wide_offsets": ([vp, i], i),
         "lbm_set_inflow_turbulence": ([vp, i, C.c_double], i),
+        "lbm_set_schedule": ([vp, C.POINTER(Schedule)], i),
+        "lbm_get_schedule": ([vp, C.POINTER(Schedule)], i),
+        "lbm_autotune": ([vp, i, C.POINTER(Schedule), dp], i),
+        "lbm_batch_create": ([C.POINTER(vp), i, vp, C.POINTER(vp)], i),
+        "lbm_batch_memory_requirements": ([vp, C.POINTER(sz)], i),
+        "lbm_batch_bind_memory": ([vp, vp, sz], i),
+        "lbm_batch_set_schedule": ([vp, C.POINTER(Schedule)], i),
+        "lbm_batch_get_schedule": ([vp, C.POINTER(Schedule)], i),
+        "lbm_batch_step": ([vp, i], i),
+        "lbm_batch_use_graphs": ([vp, i], i),
+        "lbm_batch_autotune": ([vp, i, C.POINTER(Schedule), dp], i),
+        "lbm_batch_destroy": ([vp], None),
         "lbm_inflow_modes": ([vp, dp, i, ip], i),
         "lbm_get_branch_forces": ([vp, dp, i, llp], i),
         "lbm_use_graphs": ([vp, i], i),
@@ -267,6 +291,23 @@ def lbm_inflow_modes(h):
     out = np.zeros((max(1, n.value), 7))
     _ck(_lib.lbm_inflow_modes(h, _dp(out), max(1, n.value), C.byref(n)), "lbm_inflow_modes")
     return out[:n.value]
+
+
+def lbm_set_schedule(h, ctas_per_sm=0, odd_variant=0, even_variant=0):
+    return _ck(_lib.lbm_set_schedule(h, C.byref(Schedule(ctas_per_sm, odd_variant, even_variant))), "lbm_set_schedule")
+
+
+def lbm_get_schedule(h):
+    s = Schedule()
+    _ck(_lib.lbm_get_schedule(h, C.byref(s)), "lbm_get_schedule")
+    return s
+
+
+def lbm_autotune(h, steps=3):
+    """Time every collide-variant pair, keep the fastest: (Schedule, ms per coarse step)."""
+    s, ms = Schedule(), C.c_double()
+    _ck(_lib.lbm_autotune(h, steps, C.byref(s), C.byref(ms)), "lbm_autotune")
+    return s, ms.value
 
 
 def lbm_set_wide_offsets(h, on):
@@ -506,6 +547,57 @@ class Mlp:
         if getattr(self, "h", None):
             self._torch.cuda.synchronize()
             _lib.lbm_mlp_destroy(self.h)
+            self.h = None
+            self.buffer = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owner of an lbm_batch over several bound Domain objects (kept alive here)."""
+
+    def __init__(self, domains, stream=None, device="cuda"):
+        import torch
+        self._torch = torch
+        self.domains = list(domains)
+        arr = (C.c_void_p * len(self.domains))(*[d.h for d in self.domains])
+        h = C.c_void_p()
+        _ck(_lib.lbm_batch_create(arr, len(self.domains), C.c_void_p(stream.cuda_stream if stream else 0),
+                                  C.byref(h)), "lbm_batch_create")
+        self.h = h
+        n = C.c_size_t()
+        _ck(_lib.lbm_batch_memory_requirements(h, C.byref(n)), "lbm_batch_memory_requirements")
+        self.buffer = torch.empty(max(n.value, 256), dtype=torch.uint8, device=device)
+        _ck(_lib.lbm_batch_bind_memory(h, self.buffer.data_ptr(), self.buffer.numel()), "lbm_batch_bind_memory")
+
+    def step(self, n=1):
+        return _ck(_lib.lbm_batch_step(self.h, int(n)), "lbm_batch_step")
+
+    def set_schedule(self, ctas_per_sm=0, odd_variant=0):
+        return _ck(_lib.lbm_batch_set_schedule(self.h, C.byref(Schedule(ctas_per_sm, odd_variant, 0))),
+                   "lbm_batch_set_schedule")
+
+    def get_schedule(self):
+        s = Schedule()
+        _ck(_lib.lbm_batch_get_schedule(self.h, C.byref(s)), "lbm_batch_get_schedule")
+        return s
+
+    def use_graphs(self, on):
+        return _ck(_lib.lbm_batch_use_graphs(self.h, int(bool(on))), "lbm_batch_use_graphs")
+
+    def autotune(self, steps=2):
+        s, ms = Schedule(), C.c_double()
+        _ck(_lib.lbm_batch_autotune(self.h, int(steps), C.byref(s), C.byref(ms)), "lbm_batch_autotune")
+        return s, ms.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._torch.cuda.synchronize()
+            _lib.lbm_batch_destroy(self.h)
             self.h = None
             self.buffer = None
 

@@ -35,6 +35,12 @@ CASES = {
                          re_h=1.2e5, steps=2,
                          tree=dict(n=5, children=3, s0=90.0, w0=27.0, r=(0.6,), dfac=(0.6,), alpha_deg=(35.0,),
                                    azimuth_mode=1, seed=2, trunk_cells=90.0)),
+    # three levels, coarse 48x32x32 in 8^3 blocks, 2 generations of 3 children,
+    # trunk 16 finest cells: the smallest case with two nested interfaces
+    "amr3_small": dict(n0=(48, 32, 32), levels=3, block=8, bc=("inout", "inflow", "inflow"), u_in=0.05,
+                       re_h=800.0, steps=20,
+                       tree=dict(n=3, children=3, s0=16.0, w0=4.8, r=(0.6,), dfac=(0.6,), alpha_deg=(35.0,),
+                                 azimuth_mode=1, seed=4, trunk_cells=16.0)),
     # the two-level case scaled down by 4 (8^3 blocks), sized for the oracle
     "amr2_small": dict(n0=(64, 48, 48), levels=2, block=8, bc=("inout", "inflow", "inflow"), u_in=0.05,
                        re_h=400.0, steps=100,
@@ -79,4 +85,32 @@ def surrogate_cases(count, seed):
                     alpha_deg=(float(rng.uniform(20.0, 50.0)),), azimuth_mode=1,
                     seed=int(rng.integers(0, 1 << 30)), trunk_cells=16.0)
         out.append(dict(tree=tree, re_h=float(np.exp(rng.uniform(np.log(80.0), np.log(600.0))))))
+    return out
+
+
+# ---------------------------------------------------------------- batched form
+# 16 independent cases: trees of 1-4 child generations (3 children, ratios
+# 0.6 / 0.6, 35 deg, seeded azimuths) x Re_H in {2.5e3, 1e4, 4e4, 1.2e5}; the
+# tree size sets the domain (64 to 4096 coarse blocks of 16^3) and the levels
+# (2 or 3); the cases with Re_H = 1e4 and 1.2e5 have turbulent inflow with
+# I_u = 8 % (256 random Fourier modes, integral length = the tree height).
+BATCH_DOMAINS = {
+    1: dict(n0=(64, 64, 64), levels=2, trunk=16.0),
+    2: dict(n0=(192, 96, 96), levels=2, trunk=48.0),
+    3: dict(n0=(256, 128, 128), levels=3, trunk=64.0),
+    4: dict(n0=(512, 256, 128), levels=3, trunk=96.0),
+}
+BATCH_RE = (2.5e3, 1e4, 4e4, 1.2e5)
+
+
+def batch_cases():
+    """The 16 case records of the batched form, in (generations, Re_H) order."""
+    out = []
+    for g, dom in BATCH_DOMAINS.items():
+        for k, re in enumerate(BATCH_RE):
+            t = dom["trunk"]
+            out.append(dict(n0=dom["n0"], levels=dom["levels"], block=16, bc=("inout", "inflow", "inflow"),
+                            u_in=0.05, re_h=re, i_u=0.08 if k % 2 else 0.0, seed=100 + 4 * g + k,
+                            tree=dict(n=g + 1, children=3, s0=t, w0=0.3 * t, r=(0.6,), dfac=(0.6,),
+                                      alpha_deg=(35.0,), azimuth_mode=1, seed=4 + g, trunk_cells=t)))
     return out

@@ -1,0 +1,148 @@
+"""Batched form: several domains of different sizes, level counts and inflow
+kinds stepped in lockstep by one persistent collide launch per level depth
+and sub-step and one CUDA graph per coarse step.  The batch must give the
+populations and forces of stepping each domain alone, bit for bit, under
+every schedule (persistent grid size, odd-step variant)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_27954_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_27954_gb300 import lbm
+    return lbm
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+    return torch.cuda.Stream()
+
+
+def records():
+    """Four 8^3-block cases: one, two and three levels, uniform and turbulent inflow."""
+    tiny8 = dict(W.CASES["tiny"], block=8)
+    turb = dict(W.CASES["amr2_small"], i_u=0.08, seed=5)
+    return [tiny8, W.CASES["amr2_small"], turb, W.CASES["amr3_small"]]
+
+
+def make(L, stream, c):
+    desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
+                         re_h=c["re_h"], i_u=c.get("i_u", 0.0), seed=c.get("seed", 0))
+    dom = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=stream)
+    dom.set_branch_forces(True)
+    return dom
+
+
+def state(dom, levels):
+    return [dom.get_populations(l) for l in range(levels)], dom.drag()[1], dom.get_branch_forces(
+        dom.geometry_info()["n_segments"])[0]
+
+
+@pytest.mark.parametrize("ctas,odd", [(0, 0), (2, 0), (3, 2), (1, 2)])
+def test_batch_equals_domains_stepped_alone(L, stream, ctas, odd):
+    recs = records()
+    alone = [make(L, stream, c) for c in recs]
+    for d in alone:
+        d.step(5)
+    doms = [make(L, stream, c) for c in recs]
+    batch = L.Batch(doms, stream=stream)
+    batch.set_schedule(ctas, odd)
+    batch.step(5)
+    for a, b, c in zip(alone, doms, recs):
+        sa, sb = state(a, c["levels"]), state(b, c["levels"])
+        for pa, pb in zip(sa[0], sb[0]):
+            np.testing.assert_array_equal(pa, pb)
+        np.testing.assert_array_equal(sa[1], sb[1])
+        np.testing.assert_array_equal(sa[2], sb[2])
+    batch.close()
+    for d in alone + doms:
+        d.close()
+
+
+def test_batch_autotune_picks_a_candidate_and_graphs_match_direct(L, stream):
+    recs = records()
+    d1 = [make(L, stream, c) for c in recs]
+    d2 = [make(L, stream, c) for c in recs]
+    b1, b2 = L.Batch(d1, stream=stream), L.Batch(d2, stream=stream)
+    best, ms = b1.autotune(steps=2)
+    assert best.ctas_per_sm in (0, 1, 2, 3, 4, 6, 8) and best.odd_variant in (0, 2) and ms > 0
+    # both batches continue from the same state: re-initialise, then step with and without graphs
+    for d in d1 + d2:
+        d.init_uniform(1.0, np.array([0.05, 0.0, 0.0]))
+    b2.set_schedule(best.ctas_per_sm, best.odd_variant)
+    b2.use_graphs(False)
+    b1.step(4)
+    b2.step(4)
+    for a, b, c in zip(d1, d2, recs):
+        for l in range(c["levels"]):
+            np.testing.assert_array_equal(a.get_populations(l), b.get_populations(l))
+    for x in (b1, b2):
+        x.close()
+    for d in d1 + d2:
+        d.close()
+
+
+def test_batch_rejects_mixed_domains(L, stream):
+    a = make(L, stream, records()[0])
+    b = make(L, stream, W.CASES["tiny"])  # 16^3 blocks
+    with pytest.raises(L.LbmError):
+        L.Batch([a, b], stream=stream)
+    with pytest.raises(L.LbmError):
+        L.Batch([a, a], stream=stream)
+    a.step(1)
+    c = make(L, stream, records()[1])
+    with pytest.raises(L.LbmError):
+        L.Batch([a, c], stream=stream)  # different step parity
+    for d in (a, b, c):
+        d.close()
+
+
+def test_domain_autotune_keeps_results(L, stream):
+    """Every collide variant of a single domain gives the same populations."""
+    c = W.CASES["amr2_small"]
+    ref = make(L, stream, c)
+    ref.step(3)
+    want = [ref.get_populations(l) for l in range(2)]
+    ref.close()
+    tuned = make(L, stream, c)
+    best, ms = tuned.autotune(2)
+    assert ms > 0
+    for odd in (0, 2):
+        d = make(L, stream, c)
+        d.set_schedule(0, odd, 0)
+        d.step(3)
+        for l in range(2):
+            np.testing.assert_array_equal(d.get_populations(l), want[l])
+        d.close()
+    tuned.close()
+
+
+def test_three_level_small_case_matches_oracle(L, stream):
+    c = W.CASES["amr3_small"]
+    t = c["tree"]
+    dom = make(L, stream, c)
+    tree = O.make_tree(t["n"], t["children"], t["s0"], t["w0"], t["r"], t["dfac"], alpha_deg=t["alpha_deg"],
+                       azimuth_mode=t["azimuth_mode"], seed=t["seed"])
+    sim, _ = O.tree_case(*c["n0"], tree, t["trunk_cells"], c["re_h"], u_in=c["u_in"], levels=c["levels"],
+                         block=c["block"], bc=c["bc"])
+    done = 0
+    for s in (1, 3):
+        dom.step(s - done)
+        sim.step(s - done)
+        done = s
+        for l in range(3):
+            f, ref = dom.get_populations(l), sim.f(l)
+            ok = ~np.isnan(ref)
+            assert np.array_equal(ok, ~np.isnan(f))
+            assert np.abs(f[ok] - ref[ok]).max() < 2e-6
+        np.testing.assert_allclose(dom.drag()[0], sim.force()[0], rtol=1e-4, atol=1e-7)
+    dom.close()
