@@ -1136,9 +1136,29 @@ struct lbm_batch {
   lbm_schedule sched{0, LBM_ODD_COLUMNS, LBM_EVEN_DIRECT};
   bool use_graphs = true;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // per-domain work of a phase runs on one side stream per domain, joined
+  // before the next collide launch (parallel branches in the captured graph)
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
+
+// run fn(d, stream) for every domain that qualifies, each on its own side
+// stream forked from and joined back into the batch stream
+template <class F>
+int fan_out(lbm_batch* b, F&& fn) {
+  CK(cudaEventRecord(b->fork, b->stream));
+  for (size_t k = 0; k < b->doms.size(); ++k) {
+    CK(cudaStreamWaitEvent(b->side[k], b->fork, 0));
+    int rc = fn(b->doms[k], b->side[k]);
+    if (rc) return fail(rc, cuda_error_string());
+    CK(cudaEventRecord(b->done[k], b->side[k]));
+  }
+  for (size_t k = 0; k < b->doms.size(); ++k) CK(cudaStreamWaitEvent(b->stream, b->done[k], 0));
+  return LBM_OK;
+}
 
 void free_batch_graphs(lbm_batch* b) {
   for (auto& g : b->graph)
@@ -1163,19 +1183,26 @@ int batch_advance(lbm_batch* b, int l, int parity) {
                                 reinterpret_cast<const int2*>(b->base + b->off_items[l]), (int)b->items[l].size(), b->B,
                                 parity, b->sched.odd_variant, b->half, b->wide, grid, b->stream);
   if (rc) return fail(rc, cuda_error_string());
-  for (lbm_domain* d : b->doms)
-    if (l < d->mesh.L && (rc = post_collide(d, l, parity, b->stream))) return fail(rc, cuda_error_string());
+  if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) {
+         return l < d->mesh.L ? post_collide(d, l, parity, s) : LBM_OK;
+       })))
+    return rc;
   if (l + 1 < b->L) {
     if ((rc = batch_advance(b, l + 1, 0))) return rc;
-    for (lbm_domain* d : b->doms)
-      if (l + 1 < d->mesh.L && (rc = iface_explode(d, l, parity, b->stream))) return fail(rc, cuda_error_string());
+    if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) {
+           return l + 1 < d->mesh.L ? iface_explode(d, l, parity, s) : LBM_OK;
+         })))
+      return rc;
     if ((rc = batch_advance(b, l + 1, 1))) return rc;
-    for (lbm_domain* d : b->doms)
-      if (l + 1 < d->mesh.L && (rc = iface_inflow(d, l, parity, b->stream))) return fail(rc, cuda_error_string());
+    if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) {
+           int r = l + 1 < d->mesh.L ? iface_inflow(d, l, parity, s) : LBM_OK;
+           if (!r && l == 0) r = end_coarse_step(d, s);
+           return r;
+         })))
+      return rc;
+  } else if (l == 0) {
+    if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) { return end_coarse_step(d, s); }))) return rc;
   }
-  if (l == 0)
-    for (lbm_domain* d : b->doms)
-      if ((rc = end_coarse_step(d, b->stream))) return fail(rc, cuda_error_string());
   return LBM_OK;
 }
 
@@ -1235,6 +1262,19 @@ int lbm_batch_create(lbm_domain* const* domains, int n, void* cuda_stream, lbm_b
   }
   b->B = domains[0]->d.block;
   b->half = domains[0]->d.precision == LBM_FP16_DEV;
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < n && ok; ++k) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) b->side.push_back(st);
+    ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) b->done.push_back(ev);
+  }
+  if (!ok) {
+    lbm_batch_destroy(b);
+    return fail(LBM_ECUDA, "stream or event creation failed");
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) b->sms = 1;
@@ -1360,6 +1400,13 @@ int lbm_batch_autotune(lbm_batch* b, int steps, lbm_schedule* best, double* ms_p
 void lbm_batch_destroy(lbm_batch* b) {
   if (!b) return;
   free_batch_graphs(b);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (cudaStream_t st : b->side) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (cudaEvent_t ev : b->done) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
   delete b;
 }
 
