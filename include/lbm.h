@@ -253,6 +253,33 @@ int lbm_branch_table(const lbm_domain* d, double* rows, int n, int* count);
 int lbm_branch_drag_estimate(const double* rows, int n, const double* c_sect, double area, double* cd_est,
                              double* c_out);
 
+/* ---- Friction and pressure drag (Sec. 3: C_F from the wall shear stress
+   integrated over the tree surface, C_P = C_D - C_F) ----
+   The surface of every primitive is covered by quadrature points (spacing
+   1/2 finest cell; cylinders: lateral lines and end-cap rings; half-spaces:
+   a grid over the finest level; points inside another primitive dropped).
+   A cell's viscous stress is sigma' = -(1 - omega1/2) dev(sum_i c_i c_i
+   (f_i - f_i^eq)) from its pre-collision populations at the step boundary;
+   at a point it is extrapolated linearly to the wall from two fluid cells
+   along the normal (A: the finest-level cell containing x + delta n for the
+   first delta in {1, 1.5, 2} that is fluid; B: the cell containing
+   x + (delta + 1) n if fluid and at least 1/4 cell farther out, else A
+   alone).  The tangential traction (sigma' n minus its normal part) times
+   the point's area is its friction force; sums are FP64, fixed order.
+   lbm_friction: the friction force of the current state (finest-level
+   lattice units), per branch if per_branch (n rows of 3) is given, and
+   C_F = F_x / (1/2 U^2 A_x).  Synchronises.
+   lbm_set_friction_mean: also accumulate it after every coarse step;
+   lbm_get_friction_mean returns the mean since the last lbm_reset_force and
+   the number of coarse steps averaged.  Toggling recaptures the graphs.
+   lbm_friction_samples: 13 doubles per point - cell A (x y z), cell B
+   (x y z, -1e9 when absent), n (3), area, the two normal distances (0 for
+   absent B), branch; n is the capacity in points. */
+int lbm_friction(lbm_domain* d, double force[3], double* per_branch, int n, double* c_f);
+int lbm_set_friction_mean(lbm_domain* d, int on);
+int lbm_get_friction_mean(lbm_domain* d, double mean[3], double* per_branch, int n, long long* steps);
+int lbm_friction_samples(const lbm_domain* d, double* rows, int n, int* count);
+
 /* ---- Sectional-drag surrogate (a learned C_d for Eq. 3, Sec. 2.4) ----
    A fully connected network: n_in inputs, `hidden` layers of `width` GELU
    units, one output; BF16 weights with FP32 accumulation in its forward and

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "liblbm.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-HOST_SRC = ["geometry.cpp", "mesh.cpp", "turbulence.cpp", "api.cpp"]
+HOST_SRC = ["geometry.cpp", "mesh.cpp", "turbulence.cpp", "friction.cpp", "api.cpp"]
 CUDA_SRC = ["kernels.cu", "mlp.cu"]
 
 

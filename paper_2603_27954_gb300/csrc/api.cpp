@@ -66,6 +66,11 @@ struct lbm_domain {
   bool branch_forces = false;
   bool wide_offsets = false;  // force the 64-bit-offset collide kernels
   int odd_variant = LBM_ODD_COLUMNS, even_variant = LBM_EVEN_DIRECT;
+  // wall-shear quadrature (friction force, C_F)
+  std::vector<FrictionSample> fsamp;
+  std::vector<int> fseg_begin;
+  size_t off_fsamp = 0, off_fforce = 0, off_fsegb = 0, off_facc = 0, off_fmean = 0;
+  bool friction_mean = false;
   // turbulent inflow (random Fourier modes), on when d.i_u > 0
   int n_modes = 256;
   double l_int = 0;  // integral length in level-0 cells; 0: the tree height
@@ -209,8 +214,26 @@ int iface_inflow(lbm_domain* dm, int l, int parity, cudaStream_t s) {
                          parity, s);
 }
 
-int end_coarse_step(lbm_domain* dm, cudaStream_t s) {
-  if (dm->d.i_u > 0) return launch_tick(dm->dev<long long>(dm->off_tick), s);
+// friction of the finest level at the current step boundary, added to acc
+int friction_into(lbm_domain* dm, int odd, double* acc, cudaStream_t s) {
+  const Level& v = dm->mesh.lv.back();
+  if (dm->fsamp.empty()) return LBM_OK;
+  int rc = launch_friction(dm->base + v.off_f, v.esize == 2, 1.0f / v.scale, v.B, dm->dev<int>(v.off_nbr), odd,
+                           (float)v.omega1, dm->dev<FrictionSample>(dm->off_fsamp), (int)dm->fsamp.size(),
+                           dm->dev<double>(dm->off_fforce), s);
+  if (rc) return rc;
+  return launch_segments(dm->dev<double>(dm->off_fforce), dm->dev<int>(dm->off_fsegb), (int)dm->prims.size(), acc, s);
+}
+
+// after the last kernel of a coarse step of parity p
+int end_coarse_step(lbm_domain* dm, int parity, cudaStream_t s) {
+  int rc;
+  if (dm->d.i_u > 0 && (rc = launch_tick(dm->dev<long long>(dm->off_tick), s))) return rc;
+  if (dm->friction_mean) {
+    // the finest level's incoming values: parity 0 on refined domains, else the next level-0 parity
+    const int odd = dm->mesh.L == 1 ? (parity ^ 1) : 0;
+    if ((rc = friction_into(dm, odd, dm->dev<double>(dm->off_fmean), s))) return rc;
+  }
   return LBM_OK;
 }
 
@@ -230,7 +253,7 @@ int advance(lbm_domain* dm, int l, int parity) {
     if ((rc = advance(dm, l + 1, 1))) return rc;
     if ((rc = iface_inflow(dm, l, parity, dm->stream))) return rc;
   }
-  if (l == 0) return end_coarse_step(dm, dm->stream);
+  if (l == 0) return end_coarse_step(dm, parity, dm->stream);
   return LBM_OK;
 }
 
@@ -239,6 +262,7 @@ int kernels_per_step(const Mesh& m, int l) {
   int k = 1;
   if (l == 0 && !v.face[0].empty()) k += 1;
   if (l == 0 && m.turbulent) k += 1;
+  if (l == 0 && m.friction) k += 2;
   if (!v.wall[0].empty()) k += (l == m.L - 1) ? 2 : 1;
   if (l + 1 < m.L) k += 2 * kernels_per_step(m, l + 1) + (v.expl.size() || v.save.size() ? 1 : 0) +
                         (v.infl.empty() ? 0 : 1) + (v.coal.empty() ? 0 : 1);
@@ -313,7 +337,14 @@ int build(lbm_domain* d) {
   d->off_partials = put((size_t)d->max_wall_parts * 3 * sizeof(double));
   d->off_accum = put(8 * sizeof(double));
   d->off_tick = put(sizeof(long long));
+  build_friction_samples(d->mesh, d->prims, &d->fsamp, &d->fseg_begin);
+  d->off_fsamp = put(d->fsamp.size() * sizeof(FrictionSample));
+  d->off_fforce = put(d->fsamp.size() * 3 * sizeof(double));
+  d->off_fsegb = put(d->fseg_begin.size() * sizeof(int));
+  d->off_facc = put(std::max<size_t>(1, d->prims.size()) * 4 * sizeof(double));
+  d->off_fmean = put(std::max<size_t>(1, d->prims.size()) * 4 * sizeof(double));
   d->mesh.turbulent = d->d.i_u > 0;
+  d->mesh.friction = d->friction_mean;
   if (d->d.i_u > 0) {
     d->off_modes = put((size_t)kMaxModes * kModeCols * sizeof(float));
     d->off_facepos = put(d->mesh.lv[0].face_pos.size() * sizeof(int));
@@ -372,6 +403,8 @@ int upload(lbm_domain* d) {
   }
   const Level& fl = d->mesh.lv.back();
   if (d->n_seg) CK(cp(d->off_segb, fl.seg_begin.data(), fl.seg_begin.size() * sizeof(int)));
+  CK(cp(d->off_fsamp, d->fsamp.data(), d->fsamp.size() * sizeof(FrictionSample)));
+  CK(cp(d->off_fsegb, d->fseg_begin.data(), d->fseg_begin.size() * sizeof(int)));
   if (d->d.i_u > 0) {
     const Level& l0 = d->mesh.lv[0];
     CK(cp(d->off_facepos, l0.face_pos.data(), l0.face_pos.size() * sizeof(int)));
@@ -383,6 +416,7 @@ int upload(lbm_domain* d) {
 
 int reset_force(lbm_domain* d) {
   CK(cudaMemsetAsync(d->base + d->off_accum, 0, 8 * sizeof(double), d->stream));
+  CK(cudaMemsetAsync(d->base + d->off_fmean, 0, std::max<size_t>(1, d->prims.size()) * 4 * sizeof(double), d->stream));
   if (d->n_seg) CK(cudaMemsetAsync(d->base + d->off_segacc, 0, (size_t)d->n_seg * 4 * sizeof(double), d->stream));
   return LBM_OK;
 }
@@ -908,6 +942,92 @@ int lbm_inflow_modes(const lbm_domain* d, double* modes, int n, int* count) {
   return LBM_OK;
 }
 
+// sums the per-branch accumulators into total and (optionally) per-branch rows
+void friction_rows(const lbm_domain* d, const std::vector<double>& acc, double total[3], double* rows, bool mean,
+                   long long* steps) {
+  for (int a = 0; a < 3; ++a) total[a] = 0;
+  long long cnt = 0;
+  for (size_t k = 0; k < d->prims.size(); ++k) {
+    const double w = mean ? (acc[4 * k + 3] > 0 ? 1.0 / acc[4 * k + 3] : 0.0) : 1.0;
+    cnt = std::max(cnt, (long long)acc[4 * k + 3]);
+    for (int a = 0; a < 3; ++a) {
+      const double v = acc[4 * k + a] * w;
+      total[a] += v;
+      if (rows) rows[3 * k + a] = v;
+    }
+  }
+  if (steps) *steps = cnt;
+}
+
+int lbm_friction(lbm_domain* d, double force[3], double* per_branch, int n, double* c_f) {
+  if (!d || !force) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  if (per_branch && n < (int)d->prims.size()) return fail(LBM_EINVAL, "capacity below the number of branches");
+  const size_t nb = std::max<size_t>(1, d->prims.size()) * 4;
+  CK(cudaMemsetAsync(d->base + d->off_facc, 0, nb * sizeof(double), d->stream));
+  int rc = friction_into(d, level_parity(d, d->mesh.L - 1), d->dev<double>(d->off_facc), d->stream);
+  if (rc) return fail(rc, cuda_error_string());
+  std::vector<double> acc(nb);
+  CK(cudaMemcpyAsync(acc.data(), d->base + d->off_facc, nb * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  friction_rows(d, acc, force, per_branch, false, nullptr);
+  if (c_f) {
+    const double u = d->d.u_in;
+    *c_f = (d->A_x > 0 && u != 0) ? force[0] / (0.5 * u * u * d->A_x) : std::numeric_limits<double>::quiet_NaN();
+  }
+  return LBM_OK;
+}
+
+int lbm_set_friction_mean(lbm_domain* d, int on) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (d->friction_mean != (on != 0)) free_graphs(d);
+  d->friction_mean = on != 0;
+  d->mesh.friction = d->friction_mean;
+  return LBM_OK;
+}
+
+int lbm_get_friction_mean(lbm_domain* d, double mean[3], double* per_branch, int n, long long* steps) {
+  if (!d || !mean) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  if (per_branch && n < (int)d->prims.size()) return fail(LBM_EINVAL, "capacity below the number of branches");
+  const size_t nb = std::max<size_t>(1, d->prims.size()) * 4;
+  std::vector<double> acc(nb);
+  CK(cudaMemcpyAsync(acc.data(), d->base + d->off_fmean, nb * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  friction_rows(d, acc, mean, per_branch, true, steps);
+  return LBM_OK;
+}
+
+int lbm_friction_samples(const lbm_domain* d, double* rows, int n, int* count) {
+  if (!d || !d->built) return fail(LBM_ESTATE, "set the geometry first");
+  const int c = (int)d->fsamp.size();
+  if (count) *count = c;
+  if (rows) {
+    if (n < c) return fail(LBM_EINVAL, "capacity below the number of samples");
+    const Level& v = d->mesh.lv.back();
+    const int B = v.B;
+    auto cell_xyz = [&](int slot, int cell, double* r) {
+      const int gi = v.grid_of[slot];
+      r[0] = v.org[0] + (gi % v.nb[0]) * B + cell % B;
+      r[1] = v.org[1] + ((gi / v.nb[0]) % v.nb[1]) * B + (cell / B) % B;
+      r[2] = v.org[2] + (gi / (v.nb[0] * v.nb[1])) * B + cell / (B * B);
+    };
+    for (int k = 0; k < c; ++k) {
+      const FrictionSample& q = d->fsamp[k];
+      double* r = rows + 13 * (size_t)k;
+      cell_xyz(q.slot[0], q.cell[0], r);
+      if (q.slot[1] >= 0) cell_xyz(q.slot[1], q.cell[1], r + 3);
+      else r[3] = r[4] = r[5] = -1e9;
+      for (int a = 0; a < 3; ++a) r[6 + a] = q.n[a];
+      r[9] = q.area;
+      r[10] = q.dist[0];
+      r[11] = q.slot[1] >= 0 ? q.dist[1] : 0.0;
+      r[12] = q.seg;
+    }
+  }
+  return LBM_OK;
+}
+
 int lbm_set_wide_offsets(lbm_domain* d, int on) {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (d->wide_offsets != (on != 0)) free_graphs(d);
@@ -1196,12 +1316,12 @@ int batch_advance(lbm_batch* b, int l, int parity) {
     if ((rc = batch_advance(b, l + 1, 1))) return rc;
     if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) {
            int r = l + 1 < d->mesh.L ? iface_inflow(d, l, parity, s) : LBM_OK;
-           if (!r && l == 0) r = end_coarse_step(d, s);
+           if (!r && l == 0) r = end_coarse_step(d, parity, s);
            return r;
          })))
       return rc;
   } else if (l == 0) {
-    if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) { return end_coarse_step(d, s); }))) return rc;
+    if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) { return end_coarse_step(d, parity, s); }))) return rc;
   }
   return LBM_OK;
 }

@@ -51,6 +51,16 @@ constexpr int kMaxModes = 1024;
 uint64_t splitmix(uint64_t seed, uint64_t k);
 void rfm_modes(uint64_t seed, int n, double i_u, double u, double l_int, std::vector<double>* out);
 
+struct FrictionSample {  // wall-shear quadrature point of the finest level
+  int slot[2];           // storage blocks of the two sampled fluid cells (slot[1] < 0: one cell)
+  int cell[2];           // their indices inside the blocks
+  float n[3];            // outward wall normal
+  float area;            // quadrature weight (finest cells^2)
+  float dist[2];         // normal distances of the cell centres from the wall point
+  int seg;               // primitive (branch) the point lies on
+  int pad;
+};
+
 struct FaceEntry {   // domain faces of level 0 (Sec. 2.3)
   long long dst;
   long long src;     // -1: inflow equilibrium of direction dir
@@ -139,6 +149,7 @@ struct Level {
 
 struct Mesh {
   bool turbulent = false;  // level-0 inflow from random Fourier modes (one tick launch per coarse step)
+  bool friction = false;   // wall-shear sums at the end of every coarse step (two launches)
   int L = 1, B = 16;
   int n0[3] = {0, 0, 0};
   int bc[3] = {0, 0, 0};
@@ -147,6 +158,9 @@ struct Mesh {
   std::string error;
 };
 
+// Wall-shear quadrature points of the finest level, grouped by primitive.
+int build_friction_samples(const Mesh& m, const std::vector<Prim>& prims, std::vector<FrictionSample>* out,
+                           std::vector<int>* seg_begin);
 // Build block structure, cell types (solid from primitives), links and all tables.
 int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vector<Prim>& prims, Mesh* m);
 // Refinement boxes from the tree (finest: bounding box grown by margin; coarser: footprint + 1 block).
@@ -185,6 +199,9 @@ int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[2
 int launch_collide_batch(const CollideArgs* lv, const int2* items, int n_items, int B, int odd, int odd_variant,
                          int half, int wide, int grid, void* stream);
 int launch_tick(long long* tick, void* stream);
+// per-sample viscous traction times area, tangential part: out[3 k .. 3 k + 2]
+int launch_friction(const void* f, int half, float inv_scale, int B, const int* nbr, int odd, float omega1,
+                    const FrictionSample* e, int n, double* out, void* stream);
 int launch_walls(void* f, int half, float inv_scale, const WallEntry* e, int n, double* partials,
                  double* link_force, void* stream);
 int launch_segments(const double* link_force, const int* seg_begin, int n_seg, double* seg_accum, void* stream);

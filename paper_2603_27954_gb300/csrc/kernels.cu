@@ -561,6 +561,83 @@ __global__ void __launch_bounds__(128) k_faces_turb(S* __restrict__ f, const Fac
 
 __global__ void k_tick(long long* tick) { *tick += 1; }
 
+// Viscous stress of one cell from its pre-collision populations (incoming
+// values at the step boundary: own slots on even parity, (x - c_i, ibar) on
+// odd parity):
+//   Pi^neq = sum_i c c (f_i - f_i^eq) = sum_i c c d_i - (sum_i d_i) I / 3 - j j / rho,
+//   sigma' = -(1 - omega1 / 2) dev(Pi^neq)
+template <int B, typename S>
+__device__ void cell_stress(const S* __restrict__ f, const int* __restrict__ nbr, int slot, int cell, int odd,
+                            float om1, float inv_scale, double sg[3][3]) {
+  constexpr int C3 = B * B * B;
+  const int lx = cell % B, ly = (cell / B) % B, lz = cell / (B * B);
+  double sum = 0, j[3] = {0, 0, 0}, P[6] = {0, 0, 0, 0, 0, 0};  // xx yy zz xy xz yz
+  for (int i = 0; i < 27; ++i) {
+    long long a;
+    if (!odd) {
+      a = ((long long)slot * 27 + i) * C3 + cell;
+    } else {
+      const int nx = lx - dcx(i), ny = ly - dcy(i), nz = lz - dcz(i);
+      const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
+      const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
+      a = ((long long)nbr[(size_t)slot * 27 + bd] * 27 + (26 - i)) * C3 + nc;
+    }
+    const double d = (double)Store<S>::ld(f, a) * inv_scale;
+    const int cx_ = dcx(i), cy_ = dcy(i), cz_ = dcz(i);
+    sum += d;
+    j[0] += cx_ * d;
+    j[1] += cy_ * d;
+    j[2] += cz_ * d;
+    P[0] += cx_ * cx_ * d;
+    P[1] += cy_ * cy_ * d;
+    P[2] += cz_ * cz_ * d;
+    P[3] += cx_ * cy_ * d;
+    P[4] += cx_ * cz_ * d;
+    P[5] += cy_ * cz_ * d;
+  }
+  const double rho = 1.0 + sum;
+  double Q[3][3];
+  Q[0][0] = P[0] - sum / 3.0 - j[0] * j[0] / rho;
+  Q[1][1] = P[1] - sum / 3.0 - j[1] * j[1] / rho;
+  Q[2][2] = P[2] - sum / 3.0 - j[2] * j[2] / rho;
+  Q[0][1] = Q[1][0] = P[3] - j[0] * j[1] / rho;
+  Q[0][2] = Q[2][0] = P[4] - j[0] * j[2] / rho;
+  Q[1][2] = Q[2][1] = P[5] - j[1] * j[2] / rho;
+  const double tr = (Q[0][0] + Q[1][1] + Q[2][2]) / 3.0;
+  const double c = -(1.0 - 0.5 * (double)om1);
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) sg[r][q] = c * (Q[r][q] - (r == q ? tr : 0.0));
+}
+
+// Friction force of one quadrature point: the stress extrapolated linearly to
+// the wall from its two cells (or that of its one cell), tangential traction
+// (sigma' n minus its normal part) times the area.  out[3 k .. 3 k + 2].
+template <int B, typename S>
+__global__ void __launch_bounds__(128) k_friction(const S* __restrict__ f, const FrictionSample* __restrict__ e, int n,
+                                                   const int* __restrict__ nbr, int odd, float om1, float inv_scale,
+                                                   double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const FrictionSample sm = e[t];
+  double sa[3][3], sw[3][3];
+  cell_stress<B, S>(f, nbr, sm.slot[0], sm.cell[0], odd, om1, inv_scale, sa);
+  if (sm.slot[1] >= 0) {
+    double sb[3][3];
+    cell_stress<B, S>(f, nbr, sm.slot[1], sm.cell[1], odd, om1, inv_scale, sb);
+    const double w = (double)sm.dist[0] / ((double)sm.dist[1] - (double)sm.dist[0]);
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) sw[r][q] = sa[r][q] + (sa[r][q] - sb[r][q]) * w;
+  } else {
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) sw[r][q] = sa[r][q];
+  }
+  const double nv[3] = {sm.n[0], sm.n[1], sm.n[2]};
+  double tv[3];
+  for (int k = 0; k < 3; ++k) tv[k] = sw[k][0] * nv[0] + sw[k][1] * nv[1] + sw[k][2] * nv[2];
+  const double tn = tv[0] * nv[0] + tv[1] * nv[1] + tv[2] * nv[2];
+  for (int k = 0; k < 3; ++k) out[3 * (size_t)t + k] = (tv[k] - tn * nv[k]) * (double)sm.area;
+}
+
 constexpr int kWallThreads = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -945,6 +1022,21 @@ int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[2
   if (half) k_faces<__half><<<blocks_for(n, 256), 256, 0, s>>>((__half*)f, e, n, v);
   else k_faces<float><<<blocks_for(n, 256), 256, 0, s>>>((float*)f, e, n, v);
   return check_launch("faces");
+}
+
+int launch_friction(const void* f, int half, float inv_scale, int B, const int* nbr, int odd, float omega1,
+                    const FrictionSample* e, int n, double* out, void* stream) {
+  if (n == 0) return LBM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned g = blocks_for(n, 128);
+  if (B == 16) {
+    if (half) k_friction<16, __half><<<g, 128, 0, s>>>((const __half*)f, e, n, nbr, odd, omega1, inv_scale, out);
+    else k_friction<16, float><<<g, 128, 0, s>>>((const float*)f, e, n, nbr, odd, omega1, inv_scale, out);
+  } else {
+    if (half) k_friction<8, __half><<<g, 128, 0, s>>>((const __half*)f, e, n, nbr, odd, omega1, inv_scale, out);
+    else k_friction<8, float><<<g, 128, 0, s>>>((const float*)f, e, n, nbr, odd, omega1, inv_scale, out);
+  }
+  return check_launch("friction");
 }
 
 int launch_tick(long long* tick, void* stream) {

@@ -89,6 +89,10 @@ def _load():
         "lbm_set_branch_forces": ([vp, i], i),
         "lbm_set_wide_offsets": ([vp, i], i),
         "lbm_set_inflow_turbulence": ([vp, i, C.c_double], i),
+        "lbm_friction": ([vp, dp, dp, i, dp], i),
+        "lbm_set_friction_mean": ([vp, i], i),
+        "lbm_get_friction_mean": ([vp, dp, dp, i, llp], i),
+        "lbm_friction_samples": ([vp, dp, i, ip], i),
         "lbm_set_schedule": ([vp, C.POINTER(Schedule)], i),
         "lbm_get_schedule": ([vp, C.POINTER(Schedule)], i),
         "lbm_autotune": ([vp, i, C.POINTER(Schedule), dp], i),
@@ -291,6 +295,43 @@ def lbm_inflow_modes(h):
     out = np.zeros((max(1, n.value), 7))
     _ck(_lib.lbm_inflow_modes(h, _dp(out), max(1, n.value), C.byref(n)), "lbm_inflow_modes")
     return out[:n.value]
+
+
+def _n_prims(h):
+    n = C.c_int()
+    _ck(_lib.lbm_friction_samples(h, None, 0, C.byref(n)), "lbm_friction_samples")
+    return n.value
+
+
+def lbm_friction(h, n_branches=0):
+    """Friction force of the current state, per-branch rows (n_branches x 3) and C_F."""
+    f = np.zeros(3)
+    rows = np.zeros((max(1, n_branches), 3))
+    cf = C.c_double()
+    _ck(_lib.lbm_friction(h, _dp(f), _dp(rows) if n_branches else None, n_branches, C.byref(cf)), "lbm_friction")
+    return f, rows[:n_branches], cf.value
+
+
+def lbm_set_friction_mean(h, on):
+    return _ck(_lib.lbm_set_friction_mean(h, int(bool(on))), "lbm_set_friction_mean")
+
+
+def lbm_get_friction_mean(h, n_branches=0):
+    f = np.zeros(3)
+    rows = np.zeros((max(1, n_branches), 3))
+    steps = C.c_longlong()
+    _ck(_lib.lbm_get_friction_mean(h, _dp(f), _dp(rows) if n_branches else None, n_branches, C.byref(steps)),
+        "lbm_get_friction_mean")
+    return f, rows[:n_branches], steps.value
+
+
+def lbm_friction_samples(h):
+    """Quadrature points, n x 13: cell A (3), cell B (3), normal (3), area, distances (2), branch."""
+    n = _n_prims(h)
+    out = np.zeros((max(1, n), 13))
+    c = C.c_int()
+    _ck(_lib.lbm_friction_samples(h, _dp(out), max(1, n), C.byref(c)), "lbm_friction_samples")
+    return out[:c.value]
 
 
 def lbm_set_schedule(h, ctas_per_sm=0, odd_variant=0, even_variant=0):
