@@ -392,6 +392,10 @@ def main():
     # end to end through the C-ABI: re-bind (upload tables, initialise), then
     # every step followed by a host read of the drag
     torch.cuda.synchronize()
+    # drag decomposition of the state the timed run reached (Sec. 3: C_D, C_F, C_P = C_D - C_F)
+    _, _, cd_run = dom.drag()
+    _, _, cf_run = dom.friction()
+    steps_run = args.warmup + args.steps + args.timing_steps
     barrier()
     h0 = time.perf_counter()
     L.lbm_bind_memory(dom.h, dom.buffer.data_ptr(), dom.buffer.numel())
@@ -460,7 +464,8 @@ def main():
         "batched_form": batched,
         "gpu_launches": kernels * args.steps,
         "kernels_per_step": kernels,
-        "cd": cd,
+        "cd": cd_run,
+        "drag_decomposition": {"cd": cd_run, "cf": cf_run, "cp": cd_run - cf_run, "coarse_steps": steps_run},
         "cd_rel_err_vs_oracle": cd_err,
         "fp16_form": fp16,
         "cpu_baseline": cpu,

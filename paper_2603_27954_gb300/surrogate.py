@@ -7,7 +7,10 @@ the features of lbm_branch_table and the measured sectional coefficient
 c_k = F_x,k / (rho U^2 L_k D_k / 2) (per-branch momentum-exchange forces,
 lbm_get_branch_forces).  A 6-input network (log10 Re_d, D/H, cos alpha,
 shielding depth, shadowed fraction, leaf flag) trained by the library's
-kernels predicts c_k, and Eq. 5 turns the predictions into C_D-est.
+kernels predicts c_k, and Eq. 5 turns the predictions into C_D-est.  The same
+pipeline learns the sectional friction coefficient from the per-branch wall
+shear (lbm_get_friction_mean) for Eq. 4 and C_F-est; C_P-est = C_D-est -
+C_F-est (Eq. 6).
 
 Everything numeric runs in liblbm (simulation, feature table, network
 kernels, Eq. 5); this module only sequences the calls.
@@ -26,11 +29,12 @@ FEATURES_NAMED = (0, 1, 2, 3, 4, 5)
 
 
 class Sample:
-    """One simulated tree: its branch table, measured sectional
-    coefficients, frontal area and measured C_D."""
+    """One simulated tree: its branch table, measured sectional drag and
+    friction coefficients, frontal area, measured C_D and C_F."""
 
-    def __init__(self, rows, c, area, cd):
+    def __init__(self, rows, c, area, cd, cf=None, c_f=None):
         self.rows, self.c, self.area, self.cd = rows, c, area, cd
+        self.cf, self.c_f = cf, c_f
 
 
 def simulate(case, stream=None, domain=None, steps=None, average=None):
@@ -44,6 +48,7 @@ def simulate(case, stream=None, domain=None, steps=None, average=None):
     dom = L.Domain(desc, tree=L.tree_desc(**case["tree"]), stream=stream)
     try:
         dom.set_branch_forces(True)
+        dom.set_friction_mean(True)
         dom.step(steps - average)
         dom.reset_force()
         dom.step(average)
@@ -51,19 +56,20 @@ def simulate(case, stream=None, domain=None, steps=None, average=None):
         rows = L.lbm_branch_table(dom.h)
         fb, _ = dom.get_branch_forces(len(rows))
         _, mean, _ = dom.drag()
+        fmean, frows, _ = dom.get_friction_mean(len(rows))
     finally:
         dom.close()
     u = dom_kw["u_in"]
     q = 0.5 * u * u
-    c = fb[:, 0] / (q * rows[:, 6] * rows[:, 7])
-    return Sample(rows, c, g["A_x"], mean[0] / (q * g["A_x"]))
+    ld = q * rows[:, 6] * rows[:, 7]
+    return Sample(rows, fb[:, 0] / ld, g["A_x"], mean[0] / (q * g["A_x"]), fmean[0] / (q * g["A_x"]), frows[:, 0] / ld)
 
 
-def dataset(samples, features=FEATURES):
+def dataset(samples, features=FEATURES, target="c"):
     """Stack the branch rows of several samples: inputs (float32, n x 6) and
-    targets (float32, n)."""
+    targets (float32, n): sectional drag "c" or sectional friction "c_f"."""
     x = np.concatenate([s.rows[:, list(features)] for s in samples]).astype(np.float32)
-    y = np.concatenate([s.c for s in samples]).astype(np.float32)
+    y = np.concatenate([getattr(s, target) for s in samples]).astype(np.float32)
     return x, y
 
 

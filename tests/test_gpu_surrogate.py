@@ -196,3 +196,13 @@ def test_learned_law_beats_cylinder_law_on_held_out_trees(L, stream):
     assert err["chosen"] < 0.2 * err["law"]
     assert err["named"] < 0.5 * err["law"]
     assert err["chosen"] < err["named"]
+    # friction (Eq. 4 with a learned sectional friction coefficient): C_F-est
+    # against the LBM's wall-shear C_F, and C_P-est = C_D-est - C_F-est
+    x, y = SG.dataset(train, SG.FEATURES, target="c_f")
+    nets = SG.train_ensemble(x, y, members=2)
+    ef = [abs(SG.estimate(s.rows, s.area, SG.predict(nets, s.rows)) - s.cf) / s.cf for s in held]
+    for n in nets:
+        n.close()
+    print("held-out C_F error: learned %.4f; C_F / C_D of the held-out trees %.3f-%.3f"
+          % (np.mean(ef), min(s.cf / s.cd for s in held), max(s.cf / s.cd for s in held)))
+    assert np.mean(ef) < 0.1
