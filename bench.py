@@ -31,7 +31,7 @@ CASE = "amr2"
 SMALL = "amr2_small"
 PRECISION_CASE = "amr4"
 BYTES_PER_UPDATE = 2 * 27 * 4  # read and write 27 FP32 populations
-KERNEL_SOURCES = ["paper_2603_27954_gb300/csrc/kernels.cu", "paper_2603_27954_gb300/csrc/cumulant.cuh"]
+KERNEL_SOURCES = ["paper_2603_27954_gb300/csrc/collide.cuh", "paper_2603_27954_gb300/csrc/cumulant.cuh"]
 
 
 def kernel_hash():
