@@ -47,7 +47,7 @@ struct Store<__half> {
 #define LBM_EVEN_MINB 4
 #endif
 #ifndef LBM_ODD_MINB
-#define LBM_ODD_MINB 2
+#define LBM_ODD_MINB 4
 #endif
 
 // IDX: element-offset type, 32-bit when the level's array has < 2^31 elements
@@ -425,13 +425,17 @@ __device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int b
   __syncthreads();
   const int lx = t % B, ly = t / B;
   S* __restrict__ f = reinterpret_cast<S*>(a.f);
-  S* col[9];
+  // the 9 column pointers of the (x, y) neighbourhood at slab lz, rebuilt
+  // from shared memory before the pull and again after the collision so
+  // that none of them is live across it (saves ~20 registers per thread)
+  auto cols = [&](S** col, int lz) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const int nx = lx + (k % 3 - 1), ny = ly + (k / 3 - 1);
-    const int xyd = block_digit<B>(nx) + 3 * block_digit<B>(ny);
-    col[k] = f + s_base[xyd + 9] + (IDX)((ny & (B - 1)) * B + (nx & (B - 1)));
-  }
+    for (int k = 0; k < 9; ++k) {
+      const int nx = lx + (k % 3 - 1), ny = ly + (k / 3 - 1);
+      const int xyd = block_digit<B>(nx) + 3 * block_digit<B>(ny);
+      col[k] = f + s_base[xyd + 9] + (IDX)((lz * B + (ny & (B - 1))) * B + (nx & (B - 1)));
+    }
+  };
   const int mo = a.maskoff[blk];
   const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
   const Rates rates{a.omega1, a.omega2, a.galilean};
@@ -441,6 +445,8 @@ __device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int b
     if (!mask || mask[cell]) {
       float d[27];
       if (!face) {
+        S* col[9];
+        cols(col, lz);
 #pragma unroll
         for (int i = 0; i < 27; ++i)  // pull f_i from (x - c_i, ibar)
           d[i] = Store<S>::ld(col[(1 - dcx(i)) + 3 * (1 - dcy(i))], (26 - i) * C3 - dcz(i) * S2);
@@ -454,7 +460,10 @@ __device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int b
         }
       }
       cumulant_collide_s<Store<S>::scaled>(d, rates, a.inv_scale, a.scale);
+      asm volatile("" ::: "memory");  // keep the pointer rebuild after the collision
       if (!face) {
+        S* col[9];
+        cols(col, lz);
 #pragma unroll
         for (int i = 0; i < 27; ++i)  // push f*_i to (x + c_i, i)
           Store<S>::st(col[(1 + dcx(i)) + 3 * (1 + dcy(i))], i * C3 + dcz(i) * S2, d[i]);
@@ -468,8 +477,6 @@ __device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int b
         }
       }
     }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) col[k] += S2;
   }
 }
 
