@@ -566,6 +566,7 @@ int lbm_create_domain(const lbm_domain_desc* desc, void* cuda_stream, lbm_domain
   if (!d) return fail(LBM_ENOMEM, "host allocation");
   d->d = s;
   d->stream = (cudaStream_t)cuda_stream;
+  if (s.precision == LBM_FP16_DEV) d->even_variant = LBM_EVEN_PAIRS;
   *out = d;
   return LBM_OK;
 }
@@ -1170,10 +1171,11 @@ void lbm_destroy(lbm_domain* d) {
 namespace {
 
 bool variant_ok(const lbm_domain* d, int odd, int even) {
-  if (odd < LBM_ODD_COLUMNS || odd > LBM_ODD_DIRECT || even < LBM_EVEN_DIRECT || even > LBM_EVEN_TMA) return false;
+  if (odd < LBM_ODD_COLUMNS || odd > LBM_ODD_DIRECT || even < LBM_EVEN_DIRECT || even > LBM_EVEN_PAIRS) return false;
   const bool staged_ok = d->d.precision == LBM_FP32 && d->d.block == 16;
   if (odd == LBM_ODD_STAGED && !staged_ok) return false;
   if (even == LBM_EVEN_TMA && !staged_ok) return false;
+  if (even == LBM_EVEN_PAIRS && d->d.precision != LBM_FP16_DEV) return false;
   return true;
 }
 
@@ -1221,7 +1223,7 @@ int lbm_autotune(lbm_domain* d, int steps, lbm_schedule* best, double* ms_per_st
   lbm_schedule b{0, d->odd_variant, d->even_variant};
   double bms = std::numeric_limits<double>::infinity();
   for (int odd = LBM_ODD_COLUMNS; odd <= LBM_ODD_DIRECT; ++odd)
-    for (int even = LBM_EVEN_DIRECT; even <= LBM_EVEN_TMA; ++even) {
+    for (int even = LBM_EVEN_DIRECT; even <= LBM_EVEN_PAIRS; ++even) {
       if (!variant_ok(d, odd, even)) continue;
       lbm_schedule c{0, odd, even};
       int rc = lbm_set_schedule(d, &c);

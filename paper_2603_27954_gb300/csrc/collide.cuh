@@ -100,6 +100,56 @@ __device__ __forceinline__ void collide_block(const CollideArgs& a, const int bl
   }
 }
 
+// Even step of the FP16 form with two x-neighbouring cells per thread: one
+// 4-byte load or store moves a population of both cells, halving the
+// load/store instructions of the one-cell-per-thread kernel (whose FP16 form
+// is bound by instruction issue, not bytes).  The two collisions run one
+// after the other; a pair with one non-fluid cell writes only the other.
+#ifndef LBM_PAIR_MINB
+#define LBM_PAIR_MINB 6
+#endif
+template <int B, typename IDX>
+__global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_h2(CollideArgs a) {
+  constexpr int C3 = B * B * B;
+  const int blk = blockIdx.x;
+  const IDX own = (IDX)a.nbr[(size_t)blk * 27 + 13] * (IDX)(27 * C3);
+  const int lx = 2 * (threadIdx.x % (B / 2)), ly = threadIdx.x / (B / 2);
+  const int mo = a.maskoff[blk];
+  const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
+  const Rates rates{a.omega1, a.omega2, a.galilean};
+  __half* __restrict__ f = reinterpret_cast<__half*>(a.f);
+  for (int lz = 0; lz < B; ++lz) {
+    const int cell = (lz * B + ly) * B + lx;
+    const bool m0 = !mask || mask[cell], m1 = !mask || mask[cell + 1];
+    if (!m0 && !m1) continue;
+    const __half2* p = reinterpret_cast<const __half2*>(f + own + cell);
+    __half2 h[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) h[i] = p[i * (C3 / 2)];
+    float d[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) d[i] = __low2float(h[i]);
+    cumulant_collide_s<true>(d, rates, a.inv_scale, a.scale);
+    __half o[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) o[i] = __float2half_rn(d[i]);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) d[i] = __high2float(h[i]);
+    cumulant_collide_s<true>(d, rates, a.inv_scale, a.scale);
+    if (m0 && m1) {
+      __half2* q = reinterpret_cast<__half2*>(f + own + cell);
+#pragma unroll
+      for (int i = 0; i < 27; ++i) q[(26 - i) * (C3 / 2)] = __halves2half2(o[i], __float2half_rn(d[i]));
+    } else if (m0) {
+#pragma unroll
+      for (int i = 0; i < 27; ++i) f[own + (IDX)((26 - i) * C3 + cell)] = o[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 27; ++i) f[own + (IDX)((26 - i) * C3 + cell + 1)] = __float2half_rn(d[i]);
+    }
+  }
+}
+
 template <int B, bool ODD, typename IDX, typename S>
 __global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_collide(CollideArgs a) {
   __shared__ IDX s_base[27];

@@ -455,6 +455,8 @@ void collide_on(const CollideArgs& a, int odd, cudaStream_t s) {
   } else {
     if (f32 && a.even_variant == LBM_EVEN_TMA && B == 16)
       k_collide_even_tma<IDX><<<a.n_active, 256, kEvenBytes, s>>>(a);
+    else if (!f32 && a.even_variant == LBM_EVEN_PAIRS)
+      k_collide_even_h2<B, IDX><<<a.n_active, B * B / 2, 0, s>>>(a);
     else k_collide<B, false, IDX, S><<<a.n_active, B * B, 0, s>>>(a);
   }
 }

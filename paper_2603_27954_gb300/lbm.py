@@ -45,7 +45,7 @@ class Schedule(C.Structure):
 
 
 ODD_VARIANTS = {0: "columns", 1: "staged", 2: "direct"}
-EVEN_VARIANTS = {0: "direct", 1: "tma"}
+EVEN_VARIANTS = {0: "direct", 1: "tma", 2: "pairs"}
 
 
 class LbmError(RuntimeError):

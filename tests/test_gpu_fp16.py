@@ -105,3 +105,22 @@ def test_fp16_refined_periodic_mass(L, stream):
     m1, _ = dom.mass()
     assert abs(m1 - m0) / m0 < 1e-4  # FP16 rounding of each stored deviation is not conservative
     dom.close()
+
+
+@pytest.mark.parametrize("case", ["tiny", "amr2_small"])
+def test_fp16_paired_even_step_equals_direct(L, stream, case):
+    """Two cells per thread with 4-byte pair loads and stores (16^3 and 8^3
+    blocks, pairs with one solid cell) give the one-cell-per-thread result
+    bit for bit over both parities."""
+    c = W.CASES[case]
+    out = []
+    for even in (0, 2):
+        desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
+                             re_h=c["re_h"], precision=L.LBM_FP16_DEV)
+        d = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=stream)
+        d.set_schedule(0, 0, even)
+        d.step(5)
+        out.append([d.get_populations(l) for l in range(c["levels"])])
+        d.close()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
