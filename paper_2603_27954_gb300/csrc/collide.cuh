@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "cumulant.cuh"
 #include "internal.h"
@@ -49,6 +50,11 @@ struct Store<__half> {
 #ifndef LBM_ODD_MINB
 #define LBM_ODD_MINB 4
 #endif
+#ifndef LBM_ODD_MINB_HALF
+#define LBM_ODD_MINB_HALF 5  // the FP16 odd step fits 48 registers without spills
+#endif
+template <typename S>
+constexpr int odd_minb() { return std::is_same<S, __half>::value ? LBM_ODD_MINB_HALF : LBM_ODD_MINB; }
 
 // IDX: element-offset type, 32-bit when the level's array has < 2^31 elements
 // One active block `blk` of a level: even step (own slots) or odd step with
@@ -468,22 +474,39 @@ __global__ void __launch_bounds__(256, 2) k_collide_even_tma(CollideArgs a) {
 // slabs, where 9 directions reach into the z neighbours, take the general
 // address path (the branch is uniform across the CTA).
 template <int B, typename IDX, typename S>
-__device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int blk, IDX* s_base) {
+__device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int blk, IDX* s_base, IDX* s_col) {
   constexpr int C3 = B * B * B, S2 = B * B;
   const int t = threadIdx.x;
   if (t < 27) s_base[t] = (IDX)a.nbr[(size_t)blk * 27 + t] * (IDX)(27 * C3);
   __syncthreads();
   const int lx = t % B, ly = t / B;
   S* __restrict__ f = reinterpret_cast<S*>(a.f);
+  // FP16: element offsets of the thread's 9 neighbour columns at slab 0 kept
+  // in shared memory (s_col[k * B * B + t], read only by this thread), which
+  // makes each rebuild one load and one add per column; FP32 recomputes them
+  // (measured: the 9 KB per CTA cost the FP32 step more L1 than it saved)
+  constexpr bool kSmemCols = std::is_same<S, __half>::value;
+  if (kSmemCols) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int nx = lx + (k % 3 - 1), ny = ly + (k / 3 - 1);
+      const int xyd = block_digit<B>(nx) + 3 * block_digit<B>(ny);
+      s_col[k * S2 + t] = s_base[xyd + 9] + (IDX)((ny & (B - 1)) * B + (nx & (B - 1)));
+    }
+  }
   // the 9 column pointers of the (x, y) neighbourhood at slab lz, rebuilt
   // from shared memory before the pull and again after the collision so
   // that none of them is live across it (saves ~20 registers per thread)
   auto cols = [&](S** col, int lz) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      const int nx = lx + (k % 3 - 1), ny = ly + (k / 3 - 1);
-      const int xyd = block_digit<B>(nx) + 3 * block_digit<B>(ny);
-      col[k] = f + s_base[xyd + 9] + (IDX)((lz * B + (ny & (B - 1))) * B + (nx & (B - 1)));
+      if (kSmemCols) {
+        col[k] = f + (s_col[k * S2 + t] + (IDX)(lz * S2));
+      } else {
+        const int nx = lx + (k % 3 - 1), ny = ly + (k / 3 - 1);
+        const int xyd = block_digit<B>(nx) + 3 * block_digit<B>(ny);
+        col[k] = f + s_base[xyd + 9] + (IDX)((lz * B + (ny & (B - 1))) * B + (nx & (B - 1)));
+      }
     }
   };
   const int mo = a.maskoff[blk];
@@ -531,9 +554,10 @@ __device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int b
 }
 
 template <int B, typename IDX, typename S>
-__global__ void __launch_bounds__(B * B, LBM_ODD_MINB) k_collide_odd_cols(CollideArgs a) {
+__global__ void __launch_bounds__(B * B, odd_minb<S>()) k_collide_odd_cols(CollideArgs a) {
   __shared__ IDX s_base[27];
-  odd_cols_block<B, IDX, S>(a, blockIdx.x, s_base);
+  __shared__ IDX s_col[std::is_same<S, __half>::value ? 9 * B * B : 1];
+  odd_cols_block<B, IDX, S>(a, blockIdx.x, s_base, s_col);
 }
 
 // Batched, persistent form: the CTAs walk a work list of (level descriptor,
@@ -543,11 +567,12 @@ template <int B, int KIND, typename IDX, typename S>
 __global__ void __launch_bounds__(B * B, KIND ? LBM_ODD_MINB : LBM_EVEN_MINB)
     k_collide_batch(const CollideArgs* __restrict__ lv, const int2* __restrict__ items, int n) {
   __shared__ IDX s_base[27];
+  __shared__ IDX s_col[KIND == 2 && std::is_same<S, __half>::value ? 9 * B * B : 1];
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const int2 w = items[it];
     const CollideArgs a = lv[w.x];
     __syncthreads();  // the previous item's readers of s_base are done
-    if (KIND == 2) odd_cols_block<B, IDX, S>(a, w.y, s_base);
+    if (KIND == 2) odd_cols_block<B, IDX, S>(a, w.y, s_base, s_col);
     else collide_block<B, KIND == 1, IDX, S>(a, w.y, s_base);
   }
 }
