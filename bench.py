@@ -399,6 +399,7 @@ def main():
     barrier()
     h0 = time.perf_counter()
     L.lbm_bind_memory(dom.h, dom.buffer.data_ptr(), dom.buffer.numel())
+    hb = time.perf_counter()
     for _ in range(args.e2e_steps):
         dom.step(1)
         _, _, cd = dom.drag()
@@ -457,7 +458,7 @@ def main():
         "roofline": roofline,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": dom.nbytes / args.e2e_steps,
-                "d2h_bytes_per_step": 64,
+                "d2h_bytes_per_step": 64, "bind_ms": (hb - h0) * 1e3, "steps_ms": (h1 - hb) * 1e3,
                 "note": "includes binding (table upload and equilibrium initialisation of %.2f GB) once and a "
                         "synchronous drag read after each of %d steps" % (dom.nbytes / 1e9, args.e2e_steps)},
         "precision_form": prec_form,
