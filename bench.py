@@ -263,12 +263,24 @@ def oracle_rate(case, steps):
     return updates * steps / dt / 1e6, dt, cd, updates
 
 
+METRIC = "D3Q27 cumulant LBM MLUPS & % HBM roofline; C_D rel. error vs FP64 oracle"
+
+
+def workload_config(W):
+    """The benchmark workload, identical in both arms."""
+    c = W.CASES[CASE]
+    return {"workload": "two-level tree drag: coarse %dx%dx%d in %d^3 blocks, L-system n=%d x %d children, trunk %g "
+                        "finest cells, Re_H=%g, U=%g" % (*c["n0"], c["block"], c["tree"]["n"], c["tree"]["children"],
+                                                         c["tree"]["trunk_cells"], c["re_h"], c["u_in"])}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    # each step: one coarse step of the workload scaled down by 4 per axis
-    # (the oracle would need minutes per coarse step of the full size)
+    # each step: a bounded sample of the workload - one coarse step of the same
+    # tree case scaled down by 4 per axis (the oracle needs about two seconds
+    # per coarse step of the full size, far too long for a run of K steps)
     import oracle as O
     from paper_2603_27954_gb300 import workloads as W
     c = W.CASES[SMALL]
@@ -287,10 +299,10 @@ def run_reference(args):
     sample = "%d coarse steps of the two-level tree case scaled down 4x per axis (coarse %dx%dx%d, %d cell updates per step)" % (
         args.steps, *c["n0"], updates)
     line = {
-        "impl": "reference", "metric": "D3Q27 cumulant LBM MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "FP64 CPU oracle, " + sample},
+        "config": workload_config(W),
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -444,17 +456,15 @@ def main():
                   "fp16_cd_gpu": h_cd, "fp16_rel_err": abs(h_cd - o_cd) / abs(o_cd)}
 
     line = {
-        "metric": "D3Q27 cumulant LBM MLUPS & % HBM roofline; C_D rel. error vs FP64 oracle",
+        "metric": METRIC,
         "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "two-level tree drag: coarse %dx%dx%d in %d^3 blocks, finest box %s, L-system n=%d x %d "
-                               "children, trunk %g finest cells, Re_H=%g, U=%g" % (
-                                   *c["n0"], c["block"], str(L.lbm_level_info(dom.h, 1)["lo"]) + "-" +
-                                   str(L.lbm_level_info(dom.h, 1)["hi"]), c["tree"]["n"], c["tree"]["children"],
-                                   c["tree"]["trunk_cells"], c["re_h"], c["u_in"]),
-                   "cell_updates_per_step": updates, "l2": "inputs larger than L2 (%.2f GB of populations and tables)"
-                   % (dom.nbytes / 1e9), "replicas": world},
+        "config": workload_config(W),
+        "workload_detail": {"finest_box": [list(L.lbm_level_info(dom.h, 1)["lo"]), list(L.lbm_level_info(dom.h, 1)["hi"])],
+                            "cell_updates_per_step": updates,
+                            "l2": "inputs larger than L2 (%.2f GB of populations and tables)" % (dom.nbytes / 1e9),
+                            "replicas": world},
         "roofline": roofline,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": dom.nbytes / args.e2e_steps,
