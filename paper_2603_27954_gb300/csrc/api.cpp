@@ -71,6 +71,8 @@ struct lbm_domain {
   std::vector<int> fseg_begin;
   size_t off_fsamp = 0, off_fforce = 0, off_fsegb = 0, off_facc = 0, off_fmean = 0;
   bool friction_mean = false;
+  // host tables page-locked in place at the first binding (faster, steadier uploads)
+  std::vector<void*> pinned;
   // turbulent inflow (random Fourier modes), on when d.i_u > 0
   int n_modes = 256;
   double l_int = 0;  // integral length in level-0 cells; 0: the tree height
@@ -101,6 +103,36 @@ struct lbm_domain {
 };
 
 namespace {
+
+void unpin_tables(lbm_domain* d) {
+  for (void* p : d->pinned) cudaHostUnregister(p);
+  d->pinned.clear();
+}
+
+// page-lock the larger host tables so that lbm_bind_memory uploads them by
+// DMA from pinned memory; a table that cannot be registered stays pageable
+void pin_tables(lbm_domain* d) {
+  if (!d->pinned.empty()) return;
+  auto pin = [&](void* p, size_t bytes) {
+    if (bytes < (1u << 16)) return;
+    if (cudaHostRegister(p, bytes, cudaHostRegisterDefault) == cudaSuccess) d->pinned.push_back(p);
+    else cudaGetLastError();
+  };
+  for (Level& v : d->mesh.lv) {
+    pin(v.nbr.data(), v.nbr.size() * sizeof(int));
+    pin(v.maskoff.data(), v.maskoff.size() * sizeof(int));
+    pin(v.masks.data(), v.masks.size());
+    for (int p = 0; p < 2; ++p) {
+      pin(v.wall[p].data(), v.wall[p].size() * sizeof(WallEntry));
+      pin(v.face[p].data(), v.face[p].size() * sizeof(FaceEntry));
+    }
+    pin(v.expl.data(), v.expl.size() * sizeof(ExplodeEntry));
+    pin(v.save.data(), v.save.size() * sizeof(SaveEntry));
+    pin(v.infl.data(), v.infl.size() * sizeof(InflowEntry));
+    pin(v.coal.data(), v.coal.size() * sizeof(CoalesceEntry));
+  }
+  pin(d->fsamp.data(), d->fsamp.size() * sizeof(FrictionSample));
+}
 
 void free_graphs(lbm_domain* d) {
   for (auto& g : d->graph)
@@ -287,6 +319,7 @@ int build(lbm_domain* d) {
     if (!d->have_tree || d->tree.count() == 0) return fail(LBM_EINVAL, "refinement needs boxes or a tree");
     refinement_boxes(d->tree, d->d.levels, d->d.block, d->d.refine_margin, boxes);
   }
+  unpin_tables(d);
   d->mesh = Mesh();
   int rc = build_mesh(d->d, boxes, d->prims, &d->mesh);
   if (rc) return fail(rc, d->mesh.error);
@@ -635,6 +668,7 @@ int lbm_bind_memory(lbm_domain* d, void* ptr, size_t bytes) {
   if ((uintptr_t)ptr & 255) return fail(LBM_EINVAL, "bound buffer must be 256-byte aligned");
   free_graphs(d);
   d->base = (char*)ptr;
+  pin_tables(d);
   int rc = prepare_kernels();
   if (rc) return fail(rc, cuda_error_string());
   rc = upload(d);
@@ -1161,6 +1195,7 @@ int lbm_load(lbm_domain* d, const char* path) {
 void lbm_destroy(lbm_domain* d) {
   if (!d) return;
   free_graphs(d);
+  unpin_tables(d);
   for (auto e : d->pool) cudaEventDestroy(e);
   delete d;
 }
