@@ -1,0 +1,41 @@
+"""Schedule validation on the host (no GPU): every collide-variant pair a
+domain accepts, and the ones it must refuse (staged and TMA kernels only
+for FP32 in 16^3 blocks, paired even steps only for FP16 storage)."""
+import numpy as np
+import pytest
+
+from paper_2603_27954_gb300 import lbm as L
+
+
+def domain(precision, block=16):
+    h = L.lbm_create_domain(L.domain_desc(32, 32, 32, block=block, bc=("periodic",) * 3, nu_finest=0.02,
+                                          precision=precision))
+    L.lbm_set_geometry_prims(h, [], np.zeros((0, 8)))
+    return h
+
+
+@pytest.mark.parametrize("precision,block,odd,even,ok", [
+    (L.LBM_FP32, 16, 0, 0, True), (L.LBM_FP32, 16, 1, 1, True), (L.LBM_FP32, 16, 2, 0, True),
+    (L.LBM_FP32, 16, 0, 2, False), (L.LBM_FP32, 8, 1, 0, False), (L.LBM_FP32, 8, 0, 1, False),
+    (L.LBM_FP16_DEV, 16, 0, 2, True), (L.LBM_FP16_DEV, 8, 2, 2, True), (L.LBM_FP16_DEV, 16, 1, 0, False),
+    (L.LBM_FP16_DEV, 16, 0, 1, False), (L.LBM_FP32, 16, 3, 0, False), (L.LBM_FP32, 16, 0, 3, False),
+])
+def test_schedule_validation(precision, block, odd, even, ok):
+    h = domain(precision, block)
+    if ok:
+        L.lbm_set_schedule(h, 0, odd, even)
+        s = L.lbm_get_schedule(h)
+        assert (s.odd_variant, s.even_variant) == (odd, even)
+    else:
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_set_schedule(h, 0, odd, even)
+        assert e.value.code == L.LBM_EINVAL
+    L.lbm_destroy(h)
+
+
+def test_default_schedules():
+    for precision, even in ((L.LBM_FP32, 0), (L.LBM_FP16_DEV, 2)):
+        h = domain(precision)
+        s = L.lbm_get_schedule(h)
+        assert (s.odd_variant, s.even_variant) == (0, even)
+        L.lbm_destroy(h)
