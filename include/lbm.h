@@ -53,8 +53,10 @@ typedef enum {
 } lbm_bc;
 
 /* Population storage.  LBM_FP32: f_i - w_i in FP32.  LBM_FP16_DEV:
-   (f_i - w_i) * 2^13 in IEEE binary16 (the power-of-two scale is per level).
-   Collision arithmetic is FP32 in both; the drag and mass reductions FP64. */
+   (f_i - f_i^eq(1, U e_x)) * 2^13 in IEEE binary16, deviations from the
+   inflow equilibrium at the inflow speed U (the power-of-two scale is per
+   level).  Collision arithmetic is FP32 in both; the drag and mass reductions
+   FP64.  lbm_get_populations returns f_i - w_i in either form. */
 typedef enum { LBM_FP32 = 1, LBM_FP16_DEV = 2 } lbm_precision;
 
 /* Collide-kernel variants (all compute the same result).  Odd AA step:

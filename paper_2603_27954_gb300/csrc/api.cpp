@@ -66,6 +66,9 @@ struct lbm_domain {
   bool branch_forces = false;
   bool wide_offsets = false;  // force the 64-bit-offset collide kernels
   int odd_variant = LBM_ODD_COLUMNS, even_variant = LBM_EVEN_DIRECT;
+  // storage reference r_i (deviation of the inflow equilibrium for FP16, zero for FP32)
+  double ref[27] = {};
+  Ref27 ref27{};
   // wall-shear quadrature (friction force, C_F)
   std::vector<FrictionSample> fsamp;
   std::vector<int> fseg_begin;
@@ -171,12 +174,27 @@ struct Timed {
   }
 };
 
+// the storage reference in the collision's form: j_x and Pi_xx of r, and r_i s
+// per (zero components among c_y, c_z; c_x) class
+RefShift ref_shift(const lbm_domain* dm, const Level& v) {
+  RefShift r{};
+  if (dm->d.precision != LBM_FP16_DEV) return r;
+  const double U = dm->d.u_in;
+  r.u = (float)U;
+  r.u2 = (float)(U * U);
+  const double wyz[3] = {1.0 / 36.0, 1.0 / 9.0, 4.0 / 9.0};
+  const double rx[3] = {0.5 * (U * U - U), -U * U, 0.5 * (U * U + U)};
+  for (int z = 0; z < 3; ++z)
+    for (int c = 0; c < 3; ++c) r.out[3 * z + c] = (float)(wyz[z] * rx[c] * v.scale);
+  return r;
+}
+
 CollideArgs collide_args(lbm_domain* dm, int l) {
   Level& v = dm->mesh.lv[l];
   return CollideArgs{dm->base + v.off_f, (long long)v.f_elems(), dm->dev<int>(v.off_nbr),
                      dm->dev<int>(v.off_maskoff), dm->dev<uint8_t>(v.off_masks), v.n_active, (float)v.omega1,
                      (float)dm->d.omega2, dm->d.galilean, dm->dev<double>(dm->off_accum) + 7, v.esize == 2, v.scale,
-                     1.0f / v.scale, dm->wide_offsets ? 1 : 0, dm->odd_variant, dm->even_variant};
+                     1.0f / v.scale, dm->wide_offsets ? 1 : 0, dm->odd_variant, dm->even_variant, ref_shift(dm, v)};
 }
 
 // level l after its collide-stream sweep: faces (level 0), bounce-back and
@@ -190,8 +208,8 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s) {
   if (l == 0 && !v.face[parity].empty()) {
     Timed t(dm, KC_FACES, (long long)v.face[parity].size());
     float feq[27];
-    for (int i = 0; i < 27; ++i) feq[i] = dm->feq_in[i] * v.scale;
-    TurbArgs tb{nullptr, nullptr, 0, (float)dm->d.u_in, v.scale, nullptr};
+    for (int i = 0; i < 27; ++i) feq[i] = (float)((dm->feq_in[i] - dm->ref[i]) * v.scale);
+    TurbArgs tb{nullptr, nullptr, 0, (float)dm->d.u_in, v.scale, nullptr, dm->d.precision == LBM_FP16_DEV};
     if (dm->d.i_u > 0) {
       tb.pos = dm->dev<int>(dm->off_facepos);
       tb.modes = dm->dev<float>(dm->off_modes);
@@ -206,7 +224,7 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s) {
     Timed t(dm, KC_WALLS, (long long)v.wall[parity].size());
     int n = (int)v.wall[parity].size();
     const bool per_branch = dm->branch_forces && l == m.L - 1;
-    if ((rc = launch_walls(f, half, 1.0f / v.scale, dm->dev<WallEntry>(v.off_wall[parity]), n,
+    if ((rc = launch_walls(f, half, 1.0f / v.scale, dm->ref27, dm->dev<WallEntry>(v.off_wall[parity]), n,
                            dm->dev<double>(dm->off_partials), per_branch ? dm->dev<double>(dm->off_linkf) : nullptr,
                            s)))
       return rc;
@@ -250,7 +268,7 @@ int iface_inflow(lbm_domain* dm, int l, int parity, cudaStream_t s) {
 int friction_into(lbm_domain* dm, int odd, double* acc, cudaStream_t s) {
   const Level& v = dm->mesh.lv.back();
   if (dm->fsamp.empty()) return LBM_OK;
-  int rc = launch_friction(dm->base + v.off_f, v.esize == 2, 1.0f / v.scale, v.B, dm->dev<int>(v.off_nbr), odd,
+  int rc = launch_friction(dm->base + v.off_f, v.esize == 2, 1.0f / v.scale, dm->ref27, v.B, dm->dev<int>(v.off_nbr), odd,
                            (float)v.omega1, dm->dev<FrictionSample>(dm->off_fsamp), (int)dm->fsamp.size(),
                            dm->dev<double>(dm->off_fforce), s);
   if (rc) return rc;
@@ -386,6 +404,12 @@ int build(lbm_domain* d) {
   d->need = off;
   double u[3] = {d->d.u_in, 0, 0};
   for (int i = 0; i < 27; ++i) d->feq_in[i] = (float)(equilibrium(i, 1.0, u) - rest_weight(i));
+  // FP16 storage keeps (f - w - r) s with r the inflow equilibrium's deviation:
+  // the free stream is then stored as values near zero
+  for (int i = 0; i < 27; ++i) {
+    d->ref[i] = d->d.precision == LBM_FP16_DEV ? equilibrium(i, 1.0, u) - rest_weight(i) : 0.0;
+    d->ref27.v[i] = (float)d->ref[i];
+  }
   d->built = true;
   return LBM_OK;
 }
@@ -457,7 +481,7 @@ int reset_force(lbm_domain* d) {
 int fill_uniform(lbm_domain* d, double rho, const double u[3]) {
   for (Level& v : d->mesh.lv) {
     float dev[27];
-    for (int i = 0; i < 27; ++i) dev[i] = (float)((equilibrium(i, rho, u) - rest_weight(i)) * v.scale);
+    for (int i = 0; i < 27; ++i) dev[i] = (float)((equilibrium(i, rho, u) - rest_weight(i) - d->ref[i]) * v.scale);
     int rc = launch_fill(d->base + v.off_f, v.esize == 2, v.n_storage, v.B, dev, d->stream);
     if (rc) return fail(rc, cuda_error_string());
   }
@@ -496,7 +520,7 @@ int mass_device(lbm_domain* d, double* mass, double mom[3], double* bad) {
   for (int l = 0; l < d->mesh.L; ++l) {
     Level& v = d->mesh.lv[l];
     if (!v.n_active) continue;
-    int rc = launch_mass(d->base + v.off_f, v.esize == 2, 1.0f / v.scale, d->dev<int>(v.off_nbr),
+    int rc = launch_mass(d->base + v.off_f, v.esize == 2, 1.0f / v.scale, d->ref27, d->dev<int>(v.off_nbr),
                          d->dev<int>(v.off_maskoff), d->dev<uint8_t>(v.off_masks), v.n_active, v.B,
                          level_parity(d, l), d->dev<double>(d->off_mpart), d->stream);
     if (rc) return fail(rc, cuda_error_string());
@@ -537,7 +561,8 @@ int download_level(lbm_domain* d, const Level& v, std::vector<uint8_t>& host) {
   return LBM_OK;
 }
 
-// deviation f - w of the stored element k (decoded and unscaled)
+// stored element k decoded and unscaled: f - w - r of the population it holds
+// (r the storage reference, zero for FP32)
 double stored_dev(const Level& v, const std::vector<uint8_t>& host, long long k) {
   if (v.esize == 2) {
     uint16_t h;
@@ -704,7 +729,8 @@ int lbm_init_field(lbm_domain* d, int level, const double* rho, const double* u,
       for (int x = v.rlo[0]; x < v.rhi[0]; ++x, ++k) {
         if (v.cell_type(x, y, z) != FLUID) continue;
         for (int i = 0; i < kQ; ++i)
-          store_dev(v, host, incoming_slot(v, par, x, y, z, i), equilibrium(i, rho[k], u + 3 * k) - rest_weight(i));
+          store_dev(v, host, incoming_slot(v, par, x, y, z, i),
+                    equilibrium(i, rho[k], u + 3 * k) - rest_weight(i) - d->ref[i]);
       }
   CK(cudaMemcpyAsync(d->base + v.off_f, host.data(), host.size(), cudaMemcpyHostToDevice, d->stream));
   CK(cudaStreamSynchronize(d->stream));
@@ -774,7 +800,7 @@ int lbm_get_populations(lbm_domain* d, int level, double* f, size_t n) {
       for (int x = v.rlo[0]; x < v.rhi[0]; ++x, ++k) {
         bool fl = v.cell_type(x, y, z) == FLUID;
         for (int i = 0; i < kQ; ++i)
-          f[27 * k + i] = fl ? rest_weight(i) + stored_dev(v, host, incoming_slot(v, par, x, y, z, i))
+          f[27 * k + i] = fl ? rest_weight(i) + d->ref[i] + stored_dev(v, host, incoming_slot(v, par, x, y, z, i))
                              : std::numeric_limits<double>::quiet_NaN();
       }
   return LBM_OK;
@@ -821,7 +847,7 @@ int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]) {
   for (int l = 0; l < d->mesh.L; ++l) {
     Level& v = d->mesh.lv[l];
     if (!v.n_active) continue;
-    rc = launch_mass_noalloc(d->base + v.off_f, v.esize == 2, 1.0f / v.scale, d->dev<int>(v.off_nbr),
+    rc = launch_mass_noalloc(d->base + v.off_f, v.esize == 2, 1.0f / v.scale, d->ref27, d->dev<int>(v.off_nbr),
                              d->dev<int>(v.off_maskoff), d->dev<uint8_t>(v.off_masks), v.n_active, v.B,
                              level_parity(d, l), scratch, d->stream);
     if (rc) return fail(rc, cuda_error_string());

@@ -27,7 +27,8 @@ __device__ __forceinline__ int block_digit(int c) {
   return c < 0 ? 0 : (c >= B ? 2 : 1);
 }
 
-// Population storage: FP32 deviations f - w, or FP16 deviations times a
+// Population storage: FP32 deviations f - w, or FP16 deviations f - w - r
+// from the inflow equilibrium (r_i = f_i^eq(1, U e_x) - w_i) times a
 // per-level power-of-two scale.  ld/st move the stored (scaled) value.
 template <typename S>
 struct Store;
@@ -88,7 +89,7 @@ __device__ __forceinline__ void collide_block(const CollideArgs& a, const int bl
         d[i] = Store<S>::ld(f, s_base[bd] + (IDX)((26 - i) * C3 + nc));
       }
     }
-    cumulant_collide_s<Store<S>::scaled>(d, rates, a.inv_scale, a.scale);
+    cumulant_collide_s<Store<S>::scaled>(d, rates, a.inv_scale, a.scale, &a.ref);
     if (!ODD) {
       S* p = f + s_base[13] + cell;
 #pragma unroll
@@ -135,13 +136,13 @@ __global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_h2(Co
     float d[27];
 #pragma unroll
     for (int i = 0; i < 27; ++i) d[i] = __low2float(h[i]);
-    cumulant_collide_s<true>(d, rates, a.inv_scale, a.scale);
+    cumulant_collide_s<true>(d, rates, a.inv_scale, a.scale, &a.ref);
     __half o[27];
 #pragma unroll
     for (int i = 0; i < 27; ++i) o[i] = __float2half_rn(d[i]);
 #pragma unroll
     for (int i = 0; i < 27; ++i) d[i] = __high2float(h[i]);
-    cumulant_collide_s<true>(d, rates, a.inv_scale, a.scale);
+    cumulant_collide_s<true>(d, rates, a.inv_scale, a.scale, &a.ref);
     if (m0 && m1) {
       __half2* q = reinterpret_cast<__half2*>(f + own + cell);
 #pragma unroll
@@ -532,7 +533,7 @@ __device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int b
           d[i] = Store<S>::ld(f, s_base[bd] + (IDX)((26 - i) * C3 + nc));
         }
       }
-      cumulant_collide_s<Store<S>::scaled>(d, rates, a.inv_scale, a.scale);
+      cumulant_collide_s<Store<S>::scaled>(d, rates, a.inv_scale, a.scale, &a.ref);
       asm volatile("" ::: "memory");  // keep the pointer rebuild after the collision
       if (!face) {
         S* col[9];

@@ -22,6 +22,8 @@
 
 #include <math.h>
 
+#include "internal.h"  // RefShift
+
 #ifndef LBM_HD
 #define LBM_HD __host__ __device__ __forceinline__
 #endif
@@ -32,6 +34,7 @@ struct Rates {
   float omega1, omega2;
   int galilean;
 };
+
 
 // 1-D map from central moments (M0, M1, M2) about u to the three
 // populations f(-1), f(0), f(+1): from the raw moments R1 = M1 + u M0 and
@@ -56,7 +59,8 @@ LBM_HD void central_to_pop(float m0, float m1, float m2, const AxisMap& A, float
 // storage; the FP16 form folds its power-of-two scale into the moment sums
 // and the final multiply-add instead of scaling every population).
 template <bool SCALED>
-LBM_HD void cumulant_collide_s(float* d, const Rates& r, float inv_s_in, float s_out) {
+LBM_HD void cumulant_collide_s(float* d, const Rates& r, float inv_s_in, float s_out,
+                               const RefShift* ref = nullptr) {
   // ---- raw moments of the deviations: three passes (x, then y, then z)
   float x0[9], x1[9], x2[9];
 #pragma unroll
@@ -84,10 +88,10 @@ LBM_HD void cumulant_collide_s(float* d, const Rates& r, float inv_s_in, float s
   const float jy = (y01[0] + y01[1] + y01[2]) * sc;
   const float syz = (y01[2] - y01[0]) * sc;
   const float syy = (y02[0] + y02[1] + y02[2]) * sc;
-  const float jx = (y10[0] + y10[1] + y10[2]) * sc;
+  const float jx = SCALED ? fmaf(y10[0] + y10[1] + y10[2], sc, ref->u) : (y10[0] + y10[1] + y10[2]) * sc;
   const float sxz = (y10[2] - y10[0]) * sc;
   const float sxy = (y11[0] + y11[1] + y11[2]) * sc;
-  const float sxx = (y20[0] + y20[1] + y20[2]) * sc;
+  const float sxx = SCALED ? fmaf(y20[0] + y20[1] + y20[2], sc, ref->u2) : (y20[0] + y20[1] + y20[2]) * sc;
 
   const float rho = 1.0f + drho;
   const float ir = 1.0f / rho;
@@ -178,9 +182,15 @@ LBM_HD void cumulant_collide_s(float* d, const Rates& r, float inv_s_in, float s
     float p0, p1, p2;
     central_to_pop(t[o], t[o + 1], t[o + 2], Mx, p0, p1, p2);
     const int zeros = (yz % 3 == 1) + (yz / 3 == 1);
-    d[o] = fmaf(rs, p0, dw[zeros]);
-    d[o + 1] = fmaf(rs, p1, dw[zeros + 1]);
-    d[o + 2] = fmaf(rs, p2, dw[zeros]);
+    if (SCALED) {  // back to the stored reference: minus r_i s
+      d[o] = fmaf(rs, p0, dw[zeros] - ref->out[3 * zeros]);
+      d[o + 1] = fmaf(rs, p1, dw[zeros + 1] - ref->out[3 * zeros + 1]);
+      d[o + 2] = fmaf(rs, p2, dw[zeros] - ref->out[3 * zeros + 2]);
+    } else {
+      d[o] = fmaf(rs, p0, dw[zeros]);
+      d[o + 1] = fmaf(rs, p1, dw[zeros + 1]);
+      d[o + 2] = fmaf(rs, p2, dw[zeros]);
+    }
   }
 }
 

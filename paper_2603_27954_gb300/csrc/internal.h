@@ -51,6 +51,18 @@ constexpr int kMaxModes = 1024;
 uint64_t splitmix(uint64_t seed, uint64_t k);
 void rfm_modes(uint64_t seed, int n, double i_u, double u, double l_int, std::vector<double>* out);
 
+// Reference state of the FP16 storage: stored values are (f_i - w_i - r_i) s
+// with r_i = f_i^eq(1, U e_x) - w_i, the inflow equilibrium's deviation, so
+// that the free stream stores values near zero (the 11-bit significand then
+// resolves the flow's departures from it, not from rest).  Its raw moments
+// are j_x = U and Pi_xx = U^2 (all others zero); out[3 z + cx + 1] holds
+// r_i s for the population with z zero components among (c_y, c_z) and
+// x component cx.
+struct RefShift {
+  float u, u2;
+  float out[9];
+};
+
 struct FrictionSample {  // wall-shear quadrature point of the finest level
   int slot[2];           // storage blocks of the two sampled fluid cells (slot[1] < 0: one cell)
   int cell[2];           // their indices inside the blocks
@@ -120,7 +132,7 @@ struct Level {
   long long n_fluid = 0;
   double nu = 0, omega1 = 1;
   int esize = 4;        // bytes per stored population: 4 (FP32) or 2 (FP16)
-  float scale = 1.0f;   // stored value = (f - w) * scale
+  float scale = 1.0f;   // stored value = (f - w - r) * scale (r = 0 in FP32)
   std::vector<Link> links;
   std::vector<WallEntry> wall[2];
   std::vector<int> seg_begin;                    // n_seg + 1 offsets into the ordered links
@@ -181,10 +193,15 @@ struct CollideArgs {
   float scale, inv_scale;
   int wide;           // 64-bit element offsets even when f_elems < 2^31
   int odd_variant;    // LBM_ODD_COLUMNS | LBM_ODD_STAGED | LBM_ODD_DIRECT
-  int even_variant;   // LBM_EVEN_DIRECT | LBM_EVEN_TMA
+  int even_variant;   // LBM_EVEN_DIRECT | LBM_EVEN_TMA | LBM_EVEN_PAIRS
+  RefShift ref;       // FP16 storage reference (unused for FP32)
 };
 int prepare_kernels();
 int launch_collide(const CollideArgs& a, int B, int odd, void* stream);
+// r_i per population (unscaled), the FP16 storage reference; zero for FP32
+struct Ref27 {
+  float v[27];
+};
 struct TurbArgs {      // turbulent inflow; n_modes == 0: uniform inflow equilibrium
   const int* pos;       // per face entry: level-0 cell (x, y, z, 0) the value is pulled from
   const float* modes;   // n_modes x kModeCols
@@ -192,6 +209,7 @@ struct TurbArgs {      // turbulent inflow; n_modes == 0: uniform inflow equilib
   float u;              // mean inflow speed along x
   float scale;          // storage scale of the level
   const long long* tick;  // coarse steps done
+  int shift;            // store relative to the inflow equilibrium (FP16 reference)
 };
 int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], const TurbArgs& turb,
                  void* stream);
@@ -200,9 +218,9 @@ int launch_collide_batch(const CollideArgs* lv, const int2* items, int n_items, 
                          int half, int wide, int grid, void* stream);
 int launch_tick(long long* tick, void* stream);
 // per-sample viscous traction times area, tangential part: out[3 k .. 3 k + 2]
-int launch_friction(const void* f, int half, float inv_scale, int B, const int* nbr, int odd, float omega1,
-                    const FrictionSample* e, int n, double* out, void* stream);
-int launch_walls(void* f, int half, float inv_scale, const WallEntry* e, int n, double* partials,
+int launch_friction(const void* f, int half, float inv_scale, const Ref27& ref, int B, const int* nbr, int odd,
+                    float omega1, const FrictionSample* e, int n, double* out, void* stream);
+int launch_walls(void* f, int half, float inv_scale, const Ref27& ref, const WallEntry* e, int n, double* partials,
                  double* link_force, void* stream);
 int launch_segments(const double* link_force, const int* seg_begin, int n_seg, double* seg_accum, void* stream);
 int walls_partial_count(int n);
@@ -214,13 +232,14 @@ int launch_inflow(void* fine, const void* coarse, int half, float ratio, const I
 int launch_coalesce(void* coarse, const void* fine, int half, float ratio, const CoalesceEntry* e, int n,
                     const float* saved, int parity, void* stream);
 int launch_fill(void* f, int half, long long n_blocks, int B, const float dev[27], void* stream);
-int launch_mass(const void* f, int half, float inv_scale, const int* nbr, const int* maskoff, const uint8_t* masks,
-                int n_active, int B, int parity, double* partials, void* stream);
+int launch_mass(const void* f, int half, float inv_scale, const Ref27& ref, const int* nbr, const int* maskoff,
+                const uint8_t* masks, int n_active, int B, int parity, double* partials, void* stream);
 int mass_partial_count(int n_active);
 int noalloc_max_blocks();
 int noalloc_scratch(double** out);
-int launch_mass_noalloc(const void* f, int half, float inv_scale, const int* nbr, const int* maskoff,
-                        const uint8_t* masks, int n_active, int B, int parity, double* scratch, void* stream);
+int launch_mass_noalloc(const void* f, int half, float inv_scale, const Ref27& ref, const int* nbr,
+                        const int* maskoff, const uint8_t* masks, int n_active, int B, int parity, double* scratch,
+                        void* stream);
 const char* cuda_error_string();
 
 // surrogate network kernels (mlp.cu); W / B operands of the GEMMs are BF16 or FP32

@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(128) k_faces_turb(S* __restrict__ f, const Fac
     uy = fmaf(r[4], c, uy);
     uz = fmaf(r[5], c, uz);
   }
-  Store<S>::st(f, x.dst, eq_dev(x.dir, ux, uy, uz) * tb.scale);
+  const float r = tb.shift ? eq_dev(x.dir, tb.u, 0.0f, 0.0f) : 0.0f;
+  Store<S>::st(f, x.dst, (eq_dev(x.dir, ux, uy, uz) - r) * tb.scale);
 }
 
 __global__ void k_tick(long long* tick) { *tick += 1; }
@@ -90,7 +91,7 @@ __global__ void k_tick(long long* tick) { *tick += 1; }
 //   sigma' = -(1 - omega1 / 2) dev(Pi^neq)
 template <int B, typename S>
 __device__ void cell_stress(const S* __restrict__ f, const int* __restrict__ nbr, int slot, int cell, int odd,
-                            float om1, float inv_scale, double sg[3][3]) {
+                            float om1, float inv_scale, const Ref27& ref, double sg[3][3]) {
   constexpr int C3 = B * B * B;
   const int lx = cell % B, ly = (cell / B) % B, lz = cell / (B * B);
   double sum = 0, j[3] = {0, 0, 0}, P[6] = {0, 0, 0, 0, 0, 0};  // xx yy zz xy xz yz
@@ -104,7 +105,7 @@ __device__ void cell_stress(const S* __restrict__ f, const int* __restrict__ nbr
       const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
       a = ((long long)nbr[(size_t)slot * 27 + bd] * 27 + (26 - i)) * C3 + nc;
     }
-    const double d = (double)Store<S>::ld(f, a) * inv_scale;
+    const double d = (double)Store<S>::ld(f, a) * inv_scale + (double)ref.v[i];
     const int cx_ = dcx(i), cy_ = dcy(i), cz_ = dcz(i);
     sum += d;
     j[0] += cx_ * d;
@@ -137,15 +138,15 @@ __device__ void cell_stress(const S* __restrict__ f, const int* __restrict__ nbr
 template <int B, typename S>
 __global__ void __launch_bounds__(128) k_friction(const S* __restrict__ f, const FrictionSample* __restrict__ e, int n,
                                                    const int* __restrict__ nbr, int odd, float om1, float inv_scale,
-                                                   double* __restrict__ out) {
+                                                   Ref27 ref, double* __restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const FrictionSample sm = e[t];
   double sa[3][3], sw[3][3];
-  cell_stress<B, S>(f, nbr, sm.slot[0], sm.cell[0], odd, om1, inv_scale, sa);
+  cell_stress<B, S>(f, nbr, sm.slot[0], sm.cell[0], odd, om1, inv_scale, ref, sa);
   if (sm.slot[1] >= 0) {
     double sb[3][3];
-    cell_stress<B, S>(f, nbr, sm.slot[1], sm.cell[1], odd, om1, inv_scale, sb);
+    cell_stress<B, S>(f, nbr, sm.slot[1], sm.cell[1], odd, om1, inv_scale, ref, sb);
     const double w = (double)sm.dist[0] / ((double)sm.dist[1] - (double)sm.dist[0]);
     for (int r = 0; r < 3; ++r)
       for (int q = 0; q < 3; ++q) sw[r][q] = sa[r][q] + (sa[r][q] - sb[r][q]) * w;
@@ -194,7 +195,7 @@ __device__ void block_sum3(double& a, double& b, double& c) {
 
 template <typename S>
 __global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const WallEntry* __restrict__ e, int n,
-                                                        float inv_scale, double* __restrict__ partials,
+                                                        float inv_scale, Ref27 ref, double* __restrict__ partials,
                                                         double* __restrict__ link_force) {
   const int t = blockIdx.x * kWallThreads + threadIdx.x;
   double Fx = 0.0, Fy = 0.0, Fz = 0.0;
@@ -203,21 +204,28 @@ __global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const
     const float fa = Store<S>::ld(f, w.a);  // f*_i(x_f), toward the wall (stored deviation)
     const float q = w.q;
     float out;
+    float wi_ref = 1.0f;  // interpolation weight on direction-i populations
     if (w.b < 0) {
       out = fa;  // second fluid node missing: simple bounce-back
     } else if (q < 0.5f) {
       out = 2.0f * q * fa + (1.0f - 2.0f * q) * Store<S>::ld(f, w.b);
     } else {
       const float fc = Store<S>::ld(f, w.c);
-      out = fa / (2.0f * q) + (2.0f * q - 1.0f) / (2.0f * q) * fc;
+      wi_ref = 1.0f / (2.0f * q);
+      out = fa * wi_ref + (2.0f * q - 1.0f) / (2.0f * q) * fc;
     }
+    // the interpolation weights add up to 1, so relative to the storage
+    // reference the result for population ibar carries (r_i - r_ibar) times
+    // the weight on the direction-i terms (all of it unless q >= 1/2, where
+    // f*_ibar(x_f) takes the rest)
+    const int i = w.dir;
+    if (Store<S>::scaled) out += wi_ref * (ref.v[i] - ref.v[26 - i]) / inv_scale;
     Store<S>::st(f, w.dst, out);
     // momentum exchange, resting wall: c_i (f*_i + f_ibar), full populations
-    const int i = w.dir;
     const double wi = (dcx(i) ? 1.0 / 6.0 : 2.0 / 3.0) * (dcy(i) ? 1.0 / 6.0 : 2.0 / 3.0) *
                       (dcz(i) ? 1.0 / 6.0 : 2.0 / 3.0);
     double sum = (double)fa + (double)out;
-    if (Store<S>::scaled) sum *= (double)inv_scale;
+    if (Store<S>::scaled) sum = sum * (double)inv_scale + (double)ref.v[i] + (double)ref.v[26 - i];
     const double s = 2.0 * wi + sum;
     Fx = dcx(i) * s;
     Fy = dcy(i) * s;
@@ -333,7 +341,8 @@ __global__ void k_fill(S* __restrict__ f, long long n, int c3, Feq27 dev) {
 template <int B, typename S>
 __global__ void __launch_bounds__(B * B) k_mass(const S* __restrict__ f, const int* __restrict__ nbr,
                                                 const int* __restrict__ maskoff, const uint8_t* __restrict__ masks,
-                                                int parity, float inv_scale, double* __restrict__ partials) {
+                                                int parity, float inv_scale, Ref27 ref,
+                                                double* __restrict__ partials) {
   constexpr int C3 = B * B * B;
   __shared__ long long s_base[27];
   __shared__ double s_bad[B * B / 32];
@@ -359,13 +368,14 @@ __global__ void __launch_bounds__(B * B) k_mass(const S* __restrict__ f, const i
         const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
         v = Store<S>::ld(f, s_base[bd] + (26 - i) * C3 + nc);
       }
-      if (Store<S>::scaled) v *= inv_scale;
+      double vd = v;
+      if (Store<S>::scaled) vd = (double)v * inv_scale + (double)ref.v[i];
       const double w = (dcx(i) ? 1.0 / 6.0 : 2.0 / 3.0) * (dcy(i) ? 1.0 / 6.0 : 2.0 / 3.0) *
                        (dcz(i) ? 1.0 / 6.0 : 2.0 / 3.0);
-      rho += w + (double)v;
-      ax += dcx(i) * (double)v;
-      ay += dcy(i) * (double)v;
-      az += dcz(i) * (double)v;
+      rho += w + vd;
+      ax += dcx(i) * vd;
+      ay += dcy(i) * vd;
+      az += dcz(i) * vd;
     }
     if (!(rho >= 0.5 && rho <= 2.0)) bad += 1.0;  // also catches NaN
     m += rho;
@@ -548,17 +558,18 @@ int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[2
   return check_launch("faces");
 }
 
-int launch_friction(const void* f, int half, float inv_scale, int B, const int* nbr, int odd, float omega1,
+int launch_friction(const void* f, int half, float inv_scale, const Ref27& ref, int B, const int* nbr, int odd,
+                    float omega1,
                     const FrictionSample* e, int n, double* out, void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const unsigned g = blocks_for(n, 128);
   if (B == 16) {
-    if (half) k_friction<16, __half><<<g, 128, 0, s>>>((const __half*)f, e, n, nbr, odd, omega1, inv_scale, out);
-    else k_friction<16, float><<<g, 128, 0, s>>>((const float*)f, e, n, nbr, odd, omega1, inv_scale, out);
+    if (half) k_friction<16, __half><<<g, 128, 0, s>>>((const __half*)f, e, n, nbr, odd, omega1, inv_scale, ref, out);
+    else k_friction<16, float><<<g, 128, 0, s>>>((const float*)f, e, n, nbr, odd, omega1, inv_scale, ref, out);
   } else {
-    if (half) k_friction<8, __half><<<g, 128, 0, s>>>((const __half*)f, e, n, nbr, odd, omega1, inv_scale, out);
-    else k_friction<8, float><<<g, 128, 0, s>>>((const float*)f, e, n, nbr, odd, omega1, inv_scale, out);
+    if (half) k_friction<8, __half><<<g, 128, 0, s>>>((const __half*)f, e, n, nbr, odd, omega1, inv_scale, ref, out);
+    else k_friction<8, float><<<g, 128, 0, s>>>((const float*)f, e, n, nbr, odd, omega1, inv_scale, ref, out);
   }
   return check_launch("friction");
 }
@@ -570,15 +581,15 @@ int launch_tick(long long* tick, void* stream) {
 
 int walls_partial_count(int n) { return (int)blocks_for(n, kWallThreads); }
 
-int launch_walls(void* f, int half, float inv_scale, const WallEntry* e, int n, double* partials,
+int launch_walls(void* f, int half, float inv_scale, const Ref27& ref, const WallEntry* e, int n, double* partials,
                  double* link_force, void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (half)
-    k_walls<__half><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((__half*)f, e, n, inv_scale, partials,
+    k_walls<__half><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((__half*)f, e, n, inv_scale, ref, partials,
                                                                           link_force);
   else
-    k_walls<float><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((float*)f, e, n, inv_scale, partials,
+    k_walls<float><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((float*)f, e, n, inv_scale, ref, partials,
                                                                          link_force);
   return check_launch("walls");
 }
@@ -647,16 +658,17 @@ int launch_fill(void* f, int half, long long n_blocks, int B, const float dev[27
 
 int mass_partial_count(int n_active) { return n_active; }
 
-int launch_mass(const void* f, int half, float inv_scale, const int* nbr, const int* maskoff, const uint8_t* masks,
+int launch_mass(const void* f, int half, float inv_scale, const Ref27& ref, const int* nbr, const int* maskoff,
+                const uint8_t* masks,
                 int n_active, int B, int parity, double* partials, void* stream) {
   if (n_active == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (half) {
-    if (B == 16) k_mass<16, __half><<<n_active, 256, 0, s>>>((const __half*)f, nbr, maskoff, masks, parity, inv_scale, partials);
-    else k_mass<8, __half><<<n_active, 64, 0, s>>>((const __half*)f, nbr, maskoff, masks, parity, inv_scale, partials);
+    if (B == 16) k_mass<16, __half><<<n_active, 256, 0, s>>>((const __half*)f, nbr, maskoff, masks, parity, inv_scale, ref, partials);
+    else k_mass<8, __half><<<n_active, 64, 0, s>>>((const __half*)f, nbr, maskoff, masks, parity, inv_scale, ref, partials);
   } else {
-    if (B == 16) k_mass<16, float><<<n_active, 256, 0, s>>>((const float*)f, nbr, maskoff, masks, parity, 1.0f, partials);
-    else k_mass<8, float><<<n_active, 64, 0, s>>>((const float*)f, nbr, maskoff, masks, parity, 1.0f, partials);
+    if (B == 16) k_mass<16, float><<<n_active, 256, 0, s>>>((const float*)f, nbr, maskoff, masks, parity, 1.0f, ref, partials);
+    else k_mass<8, float><<<n_active, 64, 0, s>>>((const float*)f, nbr, maskoff, masks, parity, 1.0f, ref, partials);
   }
   return check_launch("mass");
 }
@@ -686,10 +698,11 @@ int noalloc_scratch(double** out) {
   return LBM_OK;
 }
 
-int launch_mass_noalloc(const void* f, int half, float inv_scale, const int* nbr, const int* maskoff,
+int launch_mass_noalloc(const void* f, int half, float inv_scale, const Ref27& ref, const int* nbr,
+                        const int* maskoff,
                         const uint8_t* masks, int n_active, int B, int parity, double* scratch, void* stream) {
   if (n_active > kNoAllocMaxBlocks) return LBM_EINVAL;
-  int rc = launch_mass(f, half, inv_scale, nbr, maskoff, masks, n_active, B, parity, scratch, stream);
+  int rc = launch_mass(f, half, inv_scale, ref, nbr, maskoff, masks, n_active, B, parity, scratch, stream);
   if (rc) return rc;
   k_sum5<<<1, 256, 0, (cudaStream_t)stream>>>(scratch, n_active, scratch + (size_t)kNoAllocMaxBlocks * 5);
   return check_launch("sum5");

@@ -1,10 +1,9 @@
-"""FP16-deviation storage: populations stored as (f_i - w_i) * 2^13 in IEEE
-binary16, collision in FP32, drag and mass reductions in FP64, against the
-FP64 oracle.
+"""FP16-deviation storage: populations stored as (f_i - f_i^eq(1, U e_x)) * 2^13
+in IEEE binary16 (deviations from the inflow equilibrium), collision in FP32,
+drag and mass reductions in FP64, against the FP64 oracle.
 
-Bounds for the reduced-precision form: the target is C_D within 2e-3 relative
-of the oracle; the measured errors (see the test) are above it and the
-bounds hold the measured level.  A stored deviation of
+Bounds for the reduced-precision form: C_D within 2e-3 relative of the
+oracle, instantaneous and run-averaged.  A stored deviation of
 size ~1e-2 carries a rounding of ~5e-6 (2^-11 relative), so populations stay
 within 1e-4 absolute over the short horizons below and the velocity within
 5e-3 relative L2 over the 1000-step run.
@@ -67,10 +66,10 @@ def test_fp16_tiny_case_drag_within_2e3(L, stream):
     mean_ref = ref_sum / n
     print("fp16 C_D %.6f oracle %.6f rel %.2e; mean F_x rel %.2e" % (
         cd, cd_ref, abs(cd - cd_ref) / abs(cd_ref), abs(mean[0] - mean_ref[0]) / abs(mean_ref[0])))
-    # measured on GB300: instantaneous C_D 3.7e-3 and run-averaged drag 2.6e-3 relative to the
-    # FP64 oracle, so the 2e-3 target for this form is not met; the bounds hold the measured level
-    assert abs(cd - cd_ref) <= 5e-3 * abs(cd_ref), (cd, cd_ref)
-    assert abs(mean[0] - mean_ref[0]) <= 3.5e-3 * abs(mean_ref[0]), (mean, mean_ref)
+    # the 2e-3 target of the FP16 form, on the instantaneous C_D and on the run-averaged drag
+    # (measured on GB300 with deviations stored from the inflow equilibrium: 1.6e-3 and 6.0e-4)
+    assert abs(cd - cd_ref) <= 2e-3 * abs(cd_ref), (cd, cd_ref)
+    assert abs(mean[0] - mean_ref[0]) <= 2e-3 * abs(mean_ref[0]), (mean, mean_ref)
     _, u = dom.get_velocity(0)
     _, ur = sim.macro(0)
     ok = ~np.isnan(ur[..., 0])
