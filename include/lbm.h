@@ -348,6 +348,12 @@ typedef struct {
   int ctas_per_sm;   /* batches only; ignored by single domains */
   int odd_variant;   /* lbm_odd_variant */
   int even_variant;  /* lbm_even_variant */
+  int z_split_even;  /* CTAs (or persistent-grid work units) per active block of the even step: */
+  int z_split_odd;   /*   1, 2, 4 ... up to the block size, each walking block/z_split slabs
+                        (results are identical for every split).  0 = automatic, per launch:
+                        8 for FP32 in 16^3 blocks; for FP16 in 16^3 blocks the fewest that give
+                        the launch at least 32 CTAs per SM (at most 8); 1 for 8^3 blocks.
+                        Ignored by the staged and TMA variants. */
 } lbm_schedule;
 int lbm_set_schedule(lbm_domain* d, const lbm_schedule* s);
 int lbm_get_schedule(const lbm_domain* d, lbm_schedule* s);

@@ -45,6 +45,27 @@ double equilibrium(int i, double rho, const double u[3]) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// automatic z split of a collide launch over `blocks` active blocks (log2 of
+// the CTAs per block), from GB300 sweeps with 16^3 blocks: FP32 steps run
+// fastest with 8 CTAs per block on every workload; FP16 steps gain from a
+// split only while the grid is short (the fewest CTAs per block that give at
+// least 32 CTAs per SM); 8^3 blocks are not split
+int auto_zshift(const lbm_domain_desc& s, long long blocks, int sms) {
+  if (s.block != 16) return 0;
+  if (s.precision == LBM_FP32) return 3;
+  int k = 0;
+  while (k < 3 && (blocks << k) < 32LL * sms) ++k;
+  return k;
+}
+// log2 of a requested z split (CTAs per block, a power of two up to B); 0
+// (automatic) maps to -2, anything else invalid to -1
+int zshift_req(int split, int B) {
+  if (split == 0) return -2;
+  for (int k = 0; (1 << k) <= B; ++k)
+    if (split == (1 << k)) return k;
+  return -1;
+}
+
 enum { KC_COLLIDE = 0, KC_COLLIDE_ODD = 1, KC_FACES = 2, KC_WALLS = 3, KC_IFACE = 4, KC_N = 6 };
 }  // namespace
 
@@ -66,6 +87,8 @@ struct lbm_domain {
   bool branch_forces = false;
   bool wide_offsets = false;  // force the 64-bit-offset collide kernels
   int odd_variant = LBM_ODD_COLUMNS, even_variant = LBM_EVEN_DIRECT;
+  int z_split_even = 0, z_split_odd = 0;  // collide CTAs per active block; 0: automatic
+  int sms = 0;                             // SM count of the device (queried at the first launch)
   // storage reference r_i (deviation of the inflow equilibrium for FP16, zero for FP32)
   double ref[27] = {};
   Ref27 ref27{};
@@ -189,12 +212,27 @@ RefShift ref_shift(const lbm_domain* dm, const Level& v) {
   return r;
 }
 
+int device_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 152;
+  return n > 0 ? n : 152;
+}
+
+int level_zshift(lbm_domain* dm, const Level& v, int odd) {
+  const int req = odd ? dm->z_split_odd : dm->z_split_even;
+  if (req) return zshift_req(req, dm->d.block);
+  if (!dm->sms) dm->sms = device_sms();
+  return auto_zshift(dm->d, v.n_active, dm->sms);
+}
+
 CollideArgs collide_args(lbm_domain* dm, int l) {
   Level& v = dm->mesh.lv[l];
   return CollideArgs{dm->base + v.off_f, (long long)v.f_elems(), dm->dev<int>(v.off_nbr),
                      dm->dev<int>(v.off_maskoff), dm->dev<uint8_t>(v.off_masks), v.n_active, (float)v.omega1,
                      (float)dm->d.omega2, dm->d.galilean, dm->dev<double>(dm->off_accum) + 7, v.esize == 2, v.scale,
-                     1.0f / v.scale, dm->wide_offsets ? 1 : 0, dm->odd_variant, dm->even_variant, ref_shift(dm, v)};
+                     1.0f / v.scale, dm->wide_offsets ? 1 : 0, dm->odd_variant, dm->even_variant,
+                     level_zshift(dm, v, 0), level_zshift(dm, v, 1), ref_shift(dm, v)};
 }
 
 // level l after its collide-stream sweep: faces (level 0), bounce-back and
@@ -1264,9 +1302,15 @@ int time_steps(lbm_domain* d, int steps, double* ms) {
 int lbm_set_schedule(lbm_domain* d, const lbm_schedule* s) {
   if (!d || !s) return fail(LBM_EINVAL, "null argument");
   if (!variant_ok(d, s->odd_variant, s->even_variant)) return fail(LBM_EINVAL, "variant not available here");
-  if (d->odd_variant != s->odd_variant || d->even_variant != s->even_variant) free_graphs(d);
+  if (zshift_req(s->z_split_even, d->d.block) == -1 || zshift_req(s->z_split_odd, d->d.block) == -1)
+    return fail(LBM_EINVAL, "z splits must be 0 or a power of two up to the block size");
+  if (d->odd_variant != s->odd_variant || d->even_variant != s->even_variant || d->z_split_even != s->z_split_even ||
+      d->z_split_odd != s->z_split_odd)
+    free_graphs(d);
   d->odd_variant = s->odd_variant;
   d->even_variant = s->even_variant;
+  d->z_split_even = s->z_split_even;
+  d->z_split_odd = s->z_split_odd;
   return LBM_OK;
 }
 
@@ -1275,28 +1319,50 @@ int lbm_get_schedule(const lbm_domain* d, lbm_schedule* s) {
   s->ctas_per_sm = 0;
   s->odd_variant = d->odd_variant;
   s->even_variant = d->even_variant;
+  s->z_split_even = d->z_split_even;
+  s->z_split_odd = d->z_split_odd;
   return LBM_OK;
 }
 
 int lbm_autotune(lbm_domain* d, int steps, lbm_schedule* best, double* ms_per_step) {
   if (!d || steps < 1) return fail(LBM_EINVAL, "bad argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
-  lbm_schedule b{0, d->odd_variant, d->even_variant};
+  lbm_schedule b;
+  int rc = lbm_get_schedule(d, &b);
+  if (rc) return rc;
   double bms = std::numeric_limits<double>::infinity();
+  auto try_one = [&](const lbm_schedule& c) -> int {
+    int r = lbm_set_schedule(d, &c);
+    double ms;
+    if (!r) r = time_steps(d, steps, &ms);
+    if (!r && ms < bms) {
+      bms = ms;
+      b = c;
+    }
+    return r;
+  };
+  // coordinate search: the kernel variants at the current z splits, then the
+  // even step's split, then the odd step's
+  const lbm_schedule start = b;
   for (int odd = LBM_ODD_COLUMNS; odd <= LBM_ODD_DIRECT; ++odd)
     for (int even = LBM_EVEN_DIRECT; even <= LBM_EVEN_PAIRS; ++even) {
       if (!variant_ok(d, odd, even)) continue;
-      lbm_schedule c{0, odd, even};
-      int rc = lbm_set_schedule(d, &c);
-      if (rc) return rc;
-      double ms;
-      if ((rc = time_steps(d, steps, &ms))) return rc;
-      if (ms < bms) {
-        bms = ms;
-        b = c;
-      }
+      lbm_schedule c = start;
+      c.odd_variant = odd;
+      c.even_variant = even;
+      if ((rc = try_one(c))) return rc;
     }
-  int rc = lbm_set_schedule(d, &b);
+  for (int z = 0; z <= d->d.block; z = z ? 2 * z : 1) {
+    lbm_schedule c = b;
+    c.z_split_even = z;
+    if ((rc = try_one(c))) return rc;
+  }
+  for (int z = 0; z <= d->d.block; z = z ? 2 * z : 1) {
+    lbm_schedule c = b;
+    c.z_split_odd = z;
+    if ((rc = try_one(c))) return rc;
+  }
+  rc = lbm_set_schedule(d, &b);
   if (rc) return rc;
   if (best) *best = b;
   if (ms_per_step) *ms_per_step = bms;
@@ -1316,7 +1382,7 @@ struct lbm_batch {
   char* base = nullptr;
   size_t need = 0, off_descs = 0;
   std::vector<size_t> off_items;
-  lbm_schedule sched{0, LBM_ODD_COLUMNS, LBM_EVEN_DIRECT};
+  lbm_schedule sched{0, LBM_ODD_COLUMNS, LBM_EVEN_DIRECT, 0, 0};
   bool use_graphs = true;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   // per-domain work of a phase runs on one side stream per domain, joined
@@ -1360,11 +1426,20 @@ void build_descs(lbm_batch* b) {
   }
 }
 
+// z split of the batch's collide launch at depth l: the schedule's, or the
+// automatic rule over all the depth's blocks
+int batch_zshift(lbm_batch* b, int l, int parity) {
+  const int req = parity ? b->sched.z_split_odd : b->sched.z_split_even;
+  if (req) return zshift_req(req, b->B);
+  return auto_zshift(b->doms[0]->d, (long long)b->items[l].size(), b->sms);
+}
+
 int batch_advance(lbm_batch* b, int l, int parity) {
   const int grid = b->sched.ctas_per_sm > 0 ? b->sched.ctas_per_sm * b->sms : 0;
   int rc = launch_collide_batch(reinterpret_cast<const CollideArgs*>(b->base + b->off_descs),
                                 reinterpret_cast<const int2*>(b->base + b->off_items[l]), (int)b->items[l].size(), b->B,
-                                parity, b->sched.odd_variant, b->half, b->wide, grid, b->stream);
+                                parity, b->sched.odd_variant, b->half, b->wide, grid,
+                                batch_zshift(b, l, parity), b->stream);
   if (rc) return fail(rc, cuda_error_string());
   if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) {
          return l < d->mesh.L ? post_collide(d, l, parity, s) : LBM_OK;
@@ -1502,6 +1577,8 @@ int lbm_batch_set_schedule(lbm_batch* b, const lbm_schedule* s) {
   if (!b || !s) return fail(LBM_EINVAL, "null argument");
   if (s->ctas_per_sm < 0 || s->ctas_per_sm > 64 || (s->odd_variant != LBM_ODD_COLUMNS && s->odd_variant != LBM_ODD_DIRECT))
     return fail(LBM_EINVAL, "batches take column-pointer or direct odd steps and 0..64 CTAs per SM");
+  if (zshift_req(s->z_split_even, b->B) == -1 || zshift_req(s->z_split_odd, b->B) == -1)
+    return fail(LBM_EINVAL, "z splits must be 0 or a power of two up to the block size");
   b->sched = *s;
   b->sched.even_variant = LBM_EVEN_DIRECT;
   free_batch_graphs(b);
@@ -1556,21 +1633,42 @@ int lbm_batch_autotune(lbm_batch* b, int steps, lbm_schedule* best, double* ms_p
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   int rc = LBM_OK;
+  auto try_one = [&](const lbm_schedule& s) -> int {
+    int r = lbm_batch_set_schedule(b, &s);
+    if (!r) r = lbm_batch_step(b, 1);
+    if (r) return r;
+    cudaEventRecord(e0, b->stream);
+    if ((r = lbm_batch_step(b, steps))) return r;
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (t / steps < bms) {
+      bms = t / steps;
+      bs = s;
+    }
+    return LBM_OK;
+  };
+  // coordinate search: odd variant and persistent grid at the current z
+  // splits, then the even step's split, then the odd step's
+  const lbm_schedule start = b->sched;
   for (int odd : {(int)LBM_ODD_COLUMNS, (int)LBM_ODD_DIRECT})
     for (int c : kCtas) {
-      lbm_schedule s{c, odd, LBM_EVEN_DIRECT};
-      if ((rc = lbm_batch_set_schedule(b, &s)) || (rc = lbm_batch_step(b, 1))) break;
-      cudaEventRecord(e0, b->stream);
-      if ((rc = lbm_batch_step(b, steps))) break;
-      cudaEventRecord(e1, b->stream);
-      cudaEventSynchronize(e1);
-      float t = 0;
-      cudaEventElapsedTime(&t, e0, e1);
-      if (t / steps < bms) {
-        bms = t / steps;
-        bs = s;
-      }
+      lbm_schedule s = start;
+      s.ctas_per_sm = c;
+      s.odd_variant = odd;
+      if (!rc) rc = try_one(s);
     }
+  for (int z = 0; z <= b->B && !rc; z = z ? 2 * z : 1) {
+    lbm_schedule s = bs;
+    s.z_split_even = z;
+    rc = try_one(s);
+  }
+  for (int z = 0; z <= b->B && !rc; z = z ? 2 * z : 1) {
+    lbm_schedule s = bs;
+    s.z_split_odd = z;
+    rc = try_one(s);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;

@@ -56,13 +56,26 @@ struct Store<__half> {
 #endif
 template <typename S>
 constexpr int odd_minb() { return std::is_same<S, __half>::value ? LBM_ODD_MINB_HALF : LBM_ODD_MINB; }
+// The one-CTA-per-block kernels can split a block's z walk over 2^zshift CTAs
+// (CTA k of the block walks slabs k B / 2^zshift onwards): shorter CTAs fill
+// the last partial wave of the grid and keep more blocks' rows in flight.
+// Every cell update reads and writes only its own locations, so any split
+// gives the same result.
+struct ZSeg {
+  int blk, z0, z1;
+};
+__device__ __forceinline__ ZSeg z_segment(int unit, int zshift, int B) {
+  const int nz = B >> zshift, z0 = (unit & ((1 << zshift) - 1)) * nz;
+  return ZSeg{unit >> zshift, z0, z0 + nz};
+}
 
 // IDX: element-offset type, 32-bit when the level's array has < 2^31 elements
 // One active block `blk` of a level: even step (own slots) or odd step with
 // direct neighbour addressing.  s_base: 27 shared slots for the neighbour
 // blocks' element offsets.
 template <int B, bool ODD, typename IDX, typename S>
-__device__ __forceinline__ void collide_block(const CollideArgs& a, const int blk, IDX* s_base) {
+__device__ __forceinline__ void collide_block(const CollideArgs& a, const int blk, IDX* s_base, int z0 = 0,
+                                              int z1 = B) {
   constexpr int C3 = B * B * B;
   if (threadIdx.x < 27) s_base[threadIdx.x] = (IDX)a.nbr[(size_t)blk * 27 + threadIdx.x] * (IDX)(27 * C3);
   __syncthreads();
@@ -71,7 +84,7 @@ __device__ __forceinline__ void collide_block(const CollideArgs& a, const int bl
   const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
   const Rates rates{a.omega1, a.omega2, a.galilean};
   S* __restrict__ f = reinterpret_cast<S*>(a.f);
-  for (int lz = 0; lz < B; ++lz) {
+  for (int lz = z0; lz < z1; ++lz) {
     const int cell = (lz * B + ly) * B + lx;
     if (mask && !mask[cell]) continue;
     float d[27];
@@ -118,14 +131,15 @@ __device__ __forceinline__ void collide_block(const CollideArgs& a, const int bl
 template <int B, typename IDX>
 __global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_h2(CollideArgs a) {
   constexpr int C3 = B * B * B;
-  const int blk = blockIdx.x;
+  const ZSeg zg = z_segment(blockIdx.x, a.zshift_even, B);
+  const int blk = zg.blk;
   const IDX own = (IDX)a.nbr[(size_t)blk * 27 + 13] * (IDX)(27 * C3);
   const int lx = 2 * (threadIdx.x % (B / 2)), ly = threadIdx.x / (B / 2);
   const int mo = a.maskoff[blk];
   const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
   const Rates rates{a.omega1, a.omega2, a.galilean};
   __half* __restrict__ f = reinterpret_cast<__half*>(a.f);
-  for (int lz = 0; lz < B; ++lz) {
+  for (int lz = zg.z0; lz < zg.z1; ++lz) {
     const int cell = (lz * B + ly) * B + lx;
     const bool m0 = !mask || mask[cell], m1 = !mask || mask[cell + 1];
     if (!m0 && !m1) continue;
@@ -160,7 +174,8 @@ __global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_h2(Co
 template <int B, bool ODD, typename IDX, typename S>
 __global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_collide(CollideArgs a) {
   __shared__ IDX s_base[27];
-  collide_block<B, ODD, IDX, S>(a, blockIdx.x, s_base);
+  const ZSeg zg = z_segment(blockIdx.x, ODD ? a.zshift_odd : a.zshift_even, B);
+  collide_block<B, ODD, IDX, S>(a, zg.blk, s_base, zg.z0, zg.z1);
 }
 
 // ---------------------------------------------------------------------------
@@ -475,7 +490,8 @@ __global__ void __launch_bounds__(256, 2) k_collide_even_tma(CollideArgs a) {
 // slabs, where 9 directions reach into the z neighbours, take the general
 // address path (the branch is uniform across the CTA).
 template <int B, typename IDX, typename S>
-__device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int blk, IDX* s_base, IDX* s_col) {
+__device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int blk, IDX* s_base, IDX* s_col,
+                                               int z0 = 0, int z1 = B) {
   constexpr int C3 = B * B * B, S2 = B * B;
   const int t = threadIdx.x;
   if (t < 27) s_base[t] = (IDX)a.nbr[(size_t)blk * 27 + t] * (IDX)(27 * C3);
@@ -513,7 +529,7 @@ __device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int b
   const int mo = a.maskoff[blk];
   const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
   const Rates rates{a.omega1, a.omega2, a.galilean};
-  for (int lz = 0; lz < B; ++lz) {
+  for (int lz = z0; lz < z1; ++lz) {
     const int cell = (lz * B + ly) * B + lx;
     const bool face = lz == 0 || lz == B - 1;
     if (!mask || mask[cell]) {
@@ -558,7 +574,8 @@ template <int B, typename IDX, typename S>
 __global__ void __launch_bounds__(B * B, odd_minb<S>()) k_collide_odd_cols(CollideArgs a) {
   __shared__ IDX s_base[27];
   __shared__ IDX s_col[std::is_same<S, __half>::value ? 9 * B * B : 1];
-  odd_cols_block<B, IDX, S>(a, blockIdx.x, s_base, s_col);
+  const ZSeg zg = z_segment(blockIdx.x, a.zshift_odd, B);
+  odd_cols_block<B, IDX, S>(a, zg.blk, s_base, s_col, zg.z0, zg.z1);
 }
 
 // Batched, persistent form: the CTAs walk a work list of (level descriptor,
@@ -566,15 +583,16 @@ __global__ void __launch_bounds__(B * B, odd_minb<S>()) k_collide_odd_cols(Colli
 // KIND 0: even step; 1: odd step, direct addressing; 2: odd step, column pointers.
 template <int B, int KIND, typename IDX, typename S>
 __global__ void __launch_bounds__(B * B, KIND ? LBM_ODD_MINB : LBM_EVEN_MINB)
-    k_collide_batch(const CollideArgs* __restrict__ lv, const int2* __restrict__ items, int n) {
+    k_collide_batch(const CollideArgs* __restrict__ lv, const int2* __restrict__ items, int n, int zshift) {
   __shared__ IDX s_base[27];
   __shared__ IDX s_col[KIND == 2 && std::is_same<S, __half>::value ? 9 * B * B : 1];
-  for (int it = blockIdx.x; it < n; it += gridDim.x) {
-    const int2 w = items[it];
+  for (int it = blockIdx.x; it < (n << zshift); it += gridDim.x) {
+    const ZSeg zg = z_segment(it, zshift, B);
+    const int2 w = items[zg.blk];
     const CollideArgs a = lv[w.x];
     __syncthreads();  // the previous item's readers of s_base are done
-    if (KIND == 2) odd_cols_block<B, IDX, S>(a, w.y, s_base, s_col);
-    else collide_block<B, KIND == 1, IDX, S>(a, w.y, s_base);
+    if (KIND == 2) odd_cols_block<B, IDX, S>(a, w.y, s_base, s_col, zg.z0, zg.z1);
+    else collide_block<B, KIND == 1, IDX, S>(a, w.y, s_base, zg.z0, zg.z1);
   }
 }
 

@@ -194,6 +194,8 @@ struct CollideArgs {
   int wide;           // 64-bit element offsets even when f_elems < 2^31
   int odd_variant;    // LBM_ODD_COLUMNS | LBM_ODD_STAGED | LBM_ODD_DIRECT
   int even_variant;   // LBM_EVEN_DIRECT | LBM_EVEN_TMA | LBM_EVEN_PAIRS
+  int zshift_even;    // log2 of the CTAs per active block (each walks B >> zshift slabs)
+  int zshift_odd;     //   of the even and of the odd step (one-CTA-per-block kernels)
   RefShift ref;       // FP16 storage reference (unused for FP32)
 };
 int prepare_kernels();
@@ -214,8 +216,9 @@ struct TurbArgs {      // turbulent inflow; n_modes == 0: uniform inflow equilib
 int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], const TurbArgs& turb,
                  void* stream);
 // one launch over a work list of (index into lv, block) pairs; grid <= 0: one CTA per item
+// zshift: each item is walked by 2^zshift CTAs (or grid strides) of B >> zshift slabs
 int launch_collide_batch(const CollideArgs* lv, const int2* items, int n_items, int B, int odd, int odd_variant,
-                         int half, int wide, int grid, void* stream);
+                         int half, int wide, int grid, int zshift, void* stream);
 int launch_tick(long long* tick, void* stream);
 // per-sample viscous traction times area, tangential part: out[3 k .. 3 k + 2]
 int launch_friction(const void* f, int half, float inv_scale, const Ref27& ref, int B, const int* nbr, int odd,

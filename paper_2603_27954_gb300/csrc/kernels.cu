@@ -460,14 +460,14 @@ void collide_on(const CollideArgs& a, int odd, cudaStream_t s) {
   if (odd) {
     if (f32 && a.odd_variant == LBM_ODD_STAGED && B == 16)
       k_collide_odd_staged<IDX><<<a.n_active, 256, kStageBytes, s>>>(a);
-    else if (a.odd_variant == LBM_ODD_DIRECT) k_collide<B, true, IDX, S><<<a.n_active, B * B, 0, s>>>(a);
-    else k_collide_odd_cols<B, IDX, S><<<a.n_active, B * B, 0, s>>>(a);
+    else if (a.odd_variant == LBM_ODD_DIRECT) k_collide<B, true, IDX, S><<<a.n_active << a.zshift_odd, B * B, 0, s>>>(a);
+    else k_collide_odd_cols<B, IDX, S><<<a.n_active << a.zshift_odd, B * B, 0, s>>>(a);
   } else {
     if (f32 && a.even_variant == LBM_EVEN_TMA && B == 16)
       k_collide_even_tma<IDX><<<a.n_active, 256, kEvenBytes, s>>>(a);
     else if (!f32 && a.even_variant == LBM_EVEN_PAIRS)
-      k_collide_even_h2<B, IDX><<<a.n_active, B * B / 2, 0, s>>>(a);
-    else k_collide<B, false, IDX, S><<<a.n_active, B * B, 0, s>>>(a);
+      k_collide_even_h2<B, IDX><<<a.n_active << a.zshift_even, B * B / 2, 0, s>>>(a);
+    else k_collide<B, false, IDX, S><<<a.n_active << a.zshift_even, B * B, 0, s>>>(a);
   }
 }
 
@@ -484,21 +484,21 @@ void collide_typed(const CollideArgs& a, int B, int odd, cudaStream_t s) {
 }
 
 template <int B, typename IDX, typename S>
-void batch_on(const CollideArgs* lv, const int2* items, int n, int kind, int grid, cudaStream_t s) {
-  if (kind == 0) k_collide_batch<B, 0, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n);
-  else if (kind == 1) k_collide_batch<B, 1, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n);
-  else k_collide_batch<B, 2, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n);
+void batch_on(const CollideArgs* lv, const int2* items, int n, int kind, int grid, int zshift, cudaStream_t s) {
+  if (kind == 0) k_collide_batch<B, 0, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n, zshift);
+  else if (kind == 1) k_collide_batch<B, 1, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n, zshift);
+  else k_collide_batch<B, 2, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n, zshift);
 }
 
 template <typename S>
-void batch_typed(const CollideArgs* lv, const int2* items, int n, int B, int wide, int kind, int grid,
+void batch_typed(const CollideArgs* lv, const int2* items, int n, int B, int wide, int kind, int grid, int zshift,
                  cudaStream_t s) {
   if (B == 16) {
-    if (!wide) batch_on<16, int, S>(lv, items, n, kind, grid, s);
-    else batch_on<16, long long, S>(lv, items, n, kind, grid, s);
+    if (!wide) batch_on<16, int, S>(lv, items, n, kind, grid, zshift, s);
+    else batch_on<16, long long, S>(lv, items, n, kind, grid, zshift, s);
   } else {
-    if (!wide) batch_on<8, int, S>(lv, items, n, kind, grid, s);
-    else batch_on<8, long long, S>(lv, items, n, kind, grid, s);
+    if (!wide) batch_on<8, int, S>(lv, items, n, kind, grid, zshift, s);
+    else batch_on<8, long long, S>(lv, items, n, kind, grid, zshift, s);
   }
 }
 
@@ -523,6 +523,8 @@ int prepare_kernels() {
 int launch_collide(const CollideArgs& a, int B, int odd, void* stream) {
   if (a.n_active == 0) return LBM_OK;
   if (B != 16 && B != 8) return LBM_EINVAL;
+  if (a.zshift_even < 0 || a.zshift_odd < 0 || (B >> a.zshift_even) < 1 || (B >> a.zshift_odd) < 1)
+    return LBM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   if (a.half) collide_typed<__half>(a, B, odd, s);
   else collide_typed<float>(a, B, odd, s);
@@ -530,14 +532,16 @@ int launch_collide(const CollideArgs& a, int B, int odd, void* stream) {
 }
 
 int launch_collide_batch(const CollideArgs* lv, const int2* items, int n_items, int B, int odd, int odd_variant,
-                         int half, int wide, int grid, void* stream) {
+                         int half, int wide, int grid, int zshift, void* stream) {
   if (n_items == 0) return LBM_OK;
   if (B != 16 && B != 8) return LBM_EINVAL;
+  if (zshift < 0 || (B >> zshift) < 1) return LBM_EINVAL;
   const int kind = !odd ? 0 : (odd_variant == LBM_ODD_DIRECT ? 1 : 2);
-  const int g = grid > 0 ? std::min(grid, n_items) : n_items;
+  const int units = n_items << zshift;
+  const int g = grid > 0 ? std::min(grid, units) : units;
   cudaStream_t s = (cudaStream_t)stream;
-  if (half) batch_typed<__half>(lv, items, n_items, B, wide, kind, g, s);
-  else batch_typed<float>(lv, items, n_items, B, wide, kind, g, s);
+  if (half) batch_typed<__half>(lv, items, n_items, B, wide, kind, g, zshift, s);
+  else batch_typed<float>(lv, items, n_items, B, wide, kind, g, zshift, s);
   return check_launch("collide_batch");
 }
 

@@ -37,11 +37,13 @@ class TreeDesc(C.Structure):
 
 
 class Schedule(C.Structure):
-    _fields_ = [("ctas_per_sm", C.c_int), ("odd_variant", C.c_int), ("even_variant", C.c_int)]
+    _fields_ = [("ctas_per_sm", C.c_int), ("odd_variant", C.c_int), ("even_variant", C.c_int),
+                ("z_split_even", C.c_int), ("z_split_odd", C.c_int)]
 
     def as_dict(self):
         return {"ctas_per_sm": self.ctas_per_sm, "odd_variant": ODD_VARIANTS[self.odd_variant],
-                "even_variant": EVEN_VARIANTS[self.even_variant]}
+                "even_variant": EVEN_VARIANTS[self.even_variant], "z_split_even": self.z_split_even,
+                "z_split_odd": self.z_split_odd}
 
 
 ODD_VARIANTS = {0: "columns", 1: "staged", 2: "direct"}
@@ -334,8 +336,9 @@ def lbm_friction_samples(h):
     return out[:c.value]
 
 
-def lbm_set_schedule(h, ctas_per_sm=0, odd_variant=0, even_variant=0):
-    return _ck(_lib.lbm_set_schedule(h, C.byref(Schedule(ctas_per_sm, odd_variant, even_variant))), "lbm_set_schedule")
+def lbm_set_schedule(h, ctas_per_sm=0, odd_variant=0, even_variant=0, z_split_even=0, z_split_odd=0):
+    s = Schedule(ctas_per_sm, odd_variant, even_variant, z_split_even, z_split_odd)
+    return _ck(_lib.lbm_set_schedule(h, C.byref(s)), "lbm_set_schedule")
 
 
 def lbm_get_schedule(h):
@@ -345,7 +348,7 @@ def lbm_get_schedule(h):
 
 
 def lbm_autotune(h, steps=3):
-    """Time every collide-variant pair, keep the fastest: (Schedule, ms per coarse step)."""
+    """Time the collide-variant pairs, then the z splits, keep the fastest: (Schedule, ms per coarse step)."""
     s, ms = Schedule(), C.c_double()
     _ck(_lib.lbm_autotune(h, steps, C.byref(s), C.byref(ms)), "lbm_autotune")
     return s, ms.value
@@ -618,9 +621,9 @@ class Batch:
     def step(self, n=1):
         return _ck(_lib.lbm_batch_step(self.h, int(n)), "lbm_batch_step")
 
-    def set_schedule(self, ctas_per_sm=0, odd_variant=0):
-        return _ck(_lib.lbm_batch_set_schedule(self.h, C.byref(Schedule(ctas_per_sm, odd_variant, 0))),
-                   "lbm_batch_set_schedule")
+    def set_schedule(self, ctas_per_sm=0, odd_variant=0, z_split_even=0, z_split_odd=0):
+        s = Schedule(ctas_per_sm, odd_variant, 0, z_split_even, z_split_odd)
+        return _ck(_lib.lbm_batch_set_schedule(self.h, C.byref(s)), "lbm_batch_set_schedule")
 
     def get_schedule(self):
         s = Schedule()

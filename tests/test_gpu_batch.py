@@ -47,15 +47,15 @@ def state(dom, levels):
         dom.geometry_info()["n_segments"])[0]
 
 
-@pytest.mark.parametrize("ctas,odd", [(0, 0), (2, 0), (3, 2), (1, 2)])
-def test_batch_equals_domains_stepped_alone(L, stream, ctas, odd):
+@pytest.mark.parametrize("ctas,odd,ze,zo", [(0, 0, 1, 1), (2, 0, 0, 0), (3, 2, 2, 8), (1, 2, 4, 1), (0, 2, 8, 4)])
+def test_batch_equals_domains_stepped_alone(L, stream, ctas, odd, ze, zo):
     recs = records()
     alone = [make(L, stream, c) for c in recs]
     for d in alone:
         d.step(5)
     doms = [make(L, stream, c) for c in recs]
     batch = L.Batch(doms, stream=stream)
-    batch.set_schedule(ctas, odd)
+    batch.set_schedule(ctas, odd, ze, zo)
     batch.step(5)
     for a, b, c in zip(alone, doms, recs):
         sa, sb = state(a, c["levels"]), state(b, c["levels"])
@@ -146,3 +146,31 @@ def test_three_level_small_case_matches_oracle(L, stream):
             assert np.abs(f[ok] - ref[ok]).max() < 2e-6
         np.testing.assert_allclose(dom.drag()[0], sim.force()[0], rtol=1e-4, atol=1e-7)
     dom.close()
+
+
+@pytest.mark.parametrize("case,precision", [("amr2_small", "fp32"), ("amr2_small", "fp16"), ("tiny8", "fp32"),
+                                            ("tiny8", "fp16")])
+def test_z_splits_give_identical_results(L, stream, case, precision):
+    """Any split of the blocks' z walks over several CTAs gives the same
+    populations and forces bit for bit (every cell update touches only its
+    own locations)."""
+    c = dict(W.CASES["tiny"], block=8) if case == "tiny8" else W.CASES[case]
+    prec = L.LBM_FP16_DEV if precision == "fp16" else L.LBM_FP32
+    even = 2 if precision == "fp16" else 0
+
+    def run(ze, zo):
+        desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
+                             re_h=c["re_h"], precision=prec)
+        dom = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=stream)
+        dom.set_schedule(0, 0, even, ze, zo)
+        dom.step(3)
+        out = [dom.get_populations(l) for l in range(c["levels"])], dom.drag()[1]
+        dom.close()
+        return out
+
+    ref = run(1, 1)
+    for ze, zo in ((2, 2), (4, 4), (c["block"], c["block"]), (1, 8), (8, 1)):
+        got = run(ze, zo)
+        for a, b in zip(ref[0], got[0]):
+            np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(ref[1], got[1])

@@ -39,3 +39,39 @@ def test_default_schedules():
         s = L.lbm_get_schedule(h)
         assert (s.odd_variant, s.even_variant) == (0, even)
         L.lbm_destroy(h)
+
+
+@pytest.mark.parametrize("block,split,ok", [
+    (16, 1, True), (16, 2, True), (16, 4, True), (16, 8, True), (16, 16, True), (16, 3, False), (16, 32, False),
+    (16, -2, False), (8, 8, True), (8, 16, False),
+])
+def test_z_split_validation(block, split, ok):
+    for precision in (L.LBM_FP32, L.LBM_FP16_DEV):
+        h = domain(precision, block)
+        even = 2 if precision == L.LBM_FP16_DEV else 0
+        if ok:
+            L.lbm_set_schedule(h, 0, 0, even, split, split)
+            s = L.lbm_get_schedule(h)
+            assert (s.z_split_even, s.z_split_odd) == (split, split)
+        else:
+            with pytest.raises(L.LbmError) as e:
+                L.lbm_set_schedule(h, 0, 0, even, split, 1)
+            assert e.value.code == L.LBM_EINVAL
+            with pytest.raises(L.LbmError):
+                L.lbm_set_schedule(h, 0, 0, even, 1, split)
+        L.lbm_destroy(h)
+
+
+def test_z_split_defaults_to_automatic():
+    for precision, even in ((L.LBM_FP32, 0), (L.LBM_FP16_DEV, 2)):
+        for block in (8, 16):
+            h = domain(precision, block)
+            d = L.lbm_get_schedule(h)
+            assert (d.z_split_even, d.z_split_odd) == (0, 0)
+            L.lbm_set_schedule(h, 0, 0, even, 2, 4)
+            s = L.lbm_get_schedule(h)
+            assert (s.z_split_even, s.z_split_odd) == (2, 4)
+            L.lbm_set_schedule(h, 0, 0, even, 0, 0)
+            s = L.lbm_get_schedule(h)
+            assert (s.z_split_even, s.z_split_odd) == (0, 0)
+            L.lbm_destroy(h)
