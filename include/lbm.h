@@ -63,8 +63,10 @@ typedef enum { LBM_FP32 = 1, LBM_FP16_DEV = 2 } lbm_precision;
    per-thread column pointers (default), TMA/cp.async staging through shared
    memory (FP32 and 16^3 blocks only; others fall back to the default), or
    direct neighbour addressing.  Even step: direct loads and stores, a
-   4-stage TMA bulk pipeline (FP32 and 16^3 blocks only), or two cells per
-   thread moved with 4-byte pairs (FP16 storage only).  Defaults: column
+   4-stage TMA bulk pipeline (FP32 and 16^3 blocks only), or two
+   x-neighbouring cells per thread moved with 4-byte pairs and collided as one
+   in packed FP32 (FP16 storage only; the FP16 direct even step runs the same
+   packed code in both lanes and equals it bit for bit).  Defaults: column
    pointers; direct even step for FP32, pairs for FP16. */
 typedef enum { LBM_ODD_COLUMNS = 0, LBM_ODD_STAGED = 1, LBM_ODD_DIRECT = 2 } lbm_odd_variant;
 typedef enum { LBM_EVEN_DIRECT = 0, LBM_EVEN_TMA = 1, LBM_EVEN_PAIRS = 2 } lbm_even_variant;

@@ -102,7 +102,10 @@ __device__ __forceinline__ void collide_block(const CollideArgs& a, const int bl
         d[i] = Store<S>::ld(f, s_base[bd] + (IDX)((26 - i) * C3 + nc));
       }
     }
-    cumulant_collide_s<Store<S>::scaled>(d, rates, a.inv_scale, a.scale, &a.ref);
+    // the FP16 even step runs the packed code in both lanes, so that it
+    // equals the paired even step bit for bit
+    if (Store<S>::scaled && !ODD) cumulant_collide_h_as_pair(d, rates, a.inv_scale, a.scale, &a.ref);
+    else cumulant_collide_s<Store<S>::scaled>(d, rates, a.inv_scale, a.scale, &a.ref);
     if (!ODD) {
       S* p = f + s_base[13] + cell;
 #pragma unroll
@@ -123,8 +126,9 @@ __device__ __forceinline__ void collide_block(const CollideArgs& a, const int bl
 // Even step of the FP16 form with two x-neighbouring cells per thread: one
 // 4-byte load or store moves a population of both cells, halving the
 // load/store instructions of the one-cell-per-thread kernel (whose FP16 form
-// is bound by instruction issue, not bytes).  The two collisions run one
-// after the other; a pair with one non-fluid cell writes only the other.
+// is bound by instruction issue, not bytes), and the two collisions run as
+// one in packed FP32 (two lanes per instruction); a pair with one non-fluid
+// cell writes only the other.
 #ifndef LBM_PAIR_MINB
 #define LBM_PAIR_MINB 6
 #endif
@@ -144,29 +148,23 @@ __global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_h2(Co
     const bool m0 = !mask || mask[cell], m1 = !mask || mask[cell + 1];
     if (!m0 && !m1) continue;
     const __half2* p = reinterpret_cast<const __half2*>(f + own + cell);
-    __half2 h[27];
+    F2 d[27];
 #pragma unroll
-    for (int i = 0; i < 27; ++i) h[i] = p[i * (C3 / 2)];
-    float d[27];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) d[i] = __low2float(h[i]);
-    cumulant_collide_s<true>(d, rates, a.inv_scale, a.scale, &a.ref);
-    __half o[27];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) o[i] = __float2half_rn(d[i]);
-#pragma unroll
-    for (int i = 0; i < 27; ++i) d[i] = __high2float(h[i]);
-    cumulant_collide_s<true>(d, rates, a.inv_scale, a.scale, &a.ref);
+    for (int i = 0; i < 27; ++i) {
+      const __half2 h = p[i * (C3 / 2)];
+      d[i] = F2::pack(__low2float(h), __high2float(h));
+    }
+    cumulant_collide_h2(d, rates, a.inv_scale, a.scale, &a.ref);
     if (m0 && m1) {
       __half2* q = reinterpret_cast<__half2*>(f + own + cell);
 #pragma unroll
-      for (int i = 0; i < 27; ++i) q[(26 - i) * (C3 / 2)] = __halves2half2(o[i], __float2half_rn(d[i]));
+      for (int i = 0; i < 27; ++i) q[(26 - i) * (C3 / 2)] = __floats2half2_rn(d[i].lo(), d[i].hi());
     } else if (m0) {
 #pragma unroll
-      for (int i = 0; i < 27; ++i) f[own + (IDX)((26 - i) * C3 + cell)] = o[i];
+      for (int i = 0; i < 27; ++i) f[own + (IDX)((26 - i) * C3 + cell)] = __float2half_rn(d[i].lo());
     } else {
 #pragma unroll
-      for (int i = 0; i < 27; ++i) f[own + (IDX)((26 - i) * C3 + cell + 1)] = __float2half_rn(d[i]);
+      for (int i = 0; i < 27; ++i) f[own + (IDX)((26 - i) * C3 + cell + 1)] = __float2half_rn(d[i].hi());
     }
   }
 }
