@@ -148,6 +148,17 @@ void pin_tables(lbm_domain* d) {
     pin(v.nbr.data(), v.nbr.size() * sizeof(int));
     pin(v.maskoff.data(), v.maskoff.size() * sizeof(int));
     pin(v.masks.data(), v.masks.size());
+    if (v.narrow_ok && !d->wide_offsets) {
+      for (int p = 0; p < 2; ++p) {
+        pin(v.wall_n[p].data(), v.wall_n[p].size() * sizeof(WallEntryN));
+        pin(v.face_n[p].data(), v.face_n[p].size() * sizeof(FaceEntryN));
+      }
+      pin(v.expl_n.data(), v.expl_n.size() * sizeof(ExplodeEntryN));
+      pin(v.save_n.data(), v.save_n.size() * sizeof(SaveEntryN));
+      pin(v.infl_n.data(), v.infl_n.size() * sizeof(InflowEntryN));
+      pin(v.coal_n.data(), v.coal_n.size() * sizeof(CoalesceEntryN));
+      continue;
+    }
     for (int p = 0; p < 2; ++p) {
       pin(v.wall[p].data(), v.wall[p].size() * sizeof(WallEntry));
       pin(v.face[p].data(), v.face[p].size() * sizeof(FaceEntry));
@@ -254,7 +265,7 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s) {
       tb.n_modes = dm->n_modes;
       tb.tick = dm->dev<long long>(dm->off_tick);
     }
-    if ((rc = launch_faces(f, half, dm->dev<FaceEntry>(v.off_face[parity]), (int)v.face[parity].size(), feq, tb,
+    if ((rc = launch_faces(f, half, dm->base + v.off_face[parity], v.narrow, (int)v.face[parity].size(), feq, tb,
                            s)))
       return rc;
   }
@@ -262,7 +273,7 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s) {
     Timed t(dm, KC_WALLS, (long long)v.wall[parity].size());
     int n = (int)v.wall[parity].size();
     const bool per_branch = dm->branch_forces && l == m.L - 1;
-    if ((rc = launch_walls(f, half, 1.0f / v.scale, dm->ref27, dm->dev<WallEntry>(v.off_wall[parity]), n,
+    if ((rc = launch_walls(f, half, 1.0f / v.scale, dm->ref27, dm->base + v.off_wall[parity], v.narrow, n,
                            dm->dev<double>(dm->off_partials), per_branch ? dm->dev<double>(dm->off_linkf) : nullptr,
                            s)))
       return rc;
@@ -282,7 +293,7 @@ int iface_explode(lbm_domain* dm, int l, int parity, cudaStream_t s) {
   Level& F = dm->mesh.lv[l + 1];
   Timed t(dm, KC_IFACE, (long long)v.expl.size());
   return launch_explode(dm->base + F.off_f, dm->base + v.off_f, v.esize == 2, F.scale / v.scale,
-                        dm->dev<ExplodeEntry>(v.off_expl), (int)v.expl.size(), dm->dev<SaveEntry>(v.off_save),
+                        dm->base + v.off_expl, v.narrow, (int)v.expl.size(), dm->base + v.off_save,
                         (int)v.save.size(), dm->dev<float>(v.off_saved), parity, s);
 }
 
@@ -295,10 +306,10 @@ int iface_inflow(lbm_domain* dm, int l, int parity, cudaStream_t s) {
   void* f = dm->base + v.off_f;
   const float ratio = F.scale / v.scale;
   float* saved = dm->dev<float>(v.off_saved);
-  int rc = launch_inflow(ff, f, v.esize == 2, ratio, dm->dev<InflowEntry>(v.off_infl), (int)v.infl.size(), saved,
+  int rc = launch_inflow(ff, f, v.esize == 2, ratio, dm->base + v.off_infl, v.narrow, (int)v.infl.size(), saved,
                          parity, s);
   if (rc) return rc;
-  return launch_coalesce(f, ff, v.esize == 2, ratio, dm->dev<CoalesceEntry>(v.off_coal), (int)v.coal.size(), saved,
+  return launch_coalesce(f, ff, v.esize == 2, ratio, dm->base + v.off_coal, v.narrow, (int)v.coal.size(), saved,
                          parity, s);
 }
 
@@ -389,7 +400,8 @@ int build(lbm_domain* d) {
     v.esize = d->d.precision == LBM_FP16_DEV ? 2 : 4;
     v.scale = d->d.precision == LBM_FP16_DEV ? 8192.0f : 1.0f;
   }
-  // device layout
+  narrow_tables(&d->mesh);
+  // device layout (table space for the 64-bit form, which the 32-bit one fits)
   size_t off = 0;
   auto put = [&](size_t bytes) {
     size_t o = off;
@@ -478,15 +490,26 @@ int set_tick(lbm_domain* d) {
   return LBM_OK;
 }
 
-int upload(lbm_domain* d) {
+// boundary and interface tables of every level, 32-bit where the level allows
+// it and 64-bit offsets are not forced (the device space fits the 64-bit form)
+int upload_tables(lbm_domain* d) {
   auto cp = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
     if (!bytes) return cudaSuccess;
     return cudaMemcpyAsync(d->base + off, src, bytes, cudaMemcpyHostToDevice, d->stream);
   };
   for (Level& v : d->mesh.lv) {
-    CK(cp(v.off_nbr, v.nbr.data(), v.nbr.size() * sizeof(int)));
-    CK(cp(v.off_maskoff, v.maskoff.data(), v.maskoff.size() * sizeof(int)));
-    CK(cp(v.off_masks, v.masks.data(), v.masks.size()));
+    v.narrow = v.narrow_ok && !d->wide_offsets;
+    if (v.narrow) {
+      for (int p = 0; p < 2; ++p) {
+        CK(cp(v.off_wall[p], v.wall_n[p].data(), v.wall_n[p].size() * sizeof(WallEntryN)));
+        CK(cp(v.off_face[p], v.face_n[p].data(), v.face_n[p].size() * sizeof(FaceEntryN)));
+      }
+      CK(cp(v.off_expl, v.expl_n.data(), v.expl_n.size() * sizeof(ExplodeEntryN)));
+      CK(cp(v.off_save, v.save_n.data(), v.save_n.size() * sizeof(SaveEntryN)));
+      CK(cp(v.off_infl, v.infl_n.data(), v.infl_n.size() * sizeof(InflowEntryN)));
+      CK(cp(v.off_coal, v.coal_n.data(), v.coal_n.size() * sizeof(CoalesceEntryN)));
+      continue;
+    }
     for (int p = 0; p < 2; ++p) {
       CK(cp(v.off_wall[p], v.wall[p].data(), v.wall[p].size() * sizeof(WallEntry)));
       CK(cp(v.off_face[p], v.face[p].data(), v.face[p].size() * sizeof(FaceEntry)));
@@ -496,6 +519,21 @@ int upload(lbm_domain* d) {
     CK(cp(v.off_infl, v.infl.data(), v.infl.size() * sizeof(InflowEntry)));
     CK(cp(v.off_coal, v.coal.data(), v.coal.size() * sizeof(CoalesceEntry)));
   }
+  return LBM_OK;
+}
+
+int upload(lbm_domain* d) {
+  auto cp = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+    if (!bytes) return cudaSuccess;
+    return cudaMemcpyAsync(d->base + off, src, bytes, cudaMemcpyHostToDevice, d->stream);
+  };
+  for (Level& v : d->mesh.lv) {
+    CK(cp(v.off_nbr, v.nbr.data(), v.nbr.size() * sizeof(int)));
+    CK(cp(v.off_maskoff, v.maskoff.data(), v.maskoff.size() * sizeof(int)));
+    CK(cp(v.off_masks, v.masks.data(), v.masks.size()));
+  }
+  int rc = upload_tables(d);
+  if (rc) return rc;
   const Level& fl = d->mesh.lv.back();
   if (d->n_seg) CK(cp(d->off_segb, fl.seg_begin.data(), fl.seg_begin.size() * sizeof(int)));
   CK(cp(d->off_fsamp, d->fsamp.data(), d->fsamp.size() * sizeof(FrictionSample)));
@@ -1129,8 +1167,11 @@ int lbm_friction_samples(const lbm_domain* d, double* rows, int n, int* count) {
 
 int lbm_set_wide_offsets(lbm_domain* d, int on) {
   if (!d) return fail(LBM_EINVAL, "null argument");
-  if (d->wide_offsets != (on != 0)) free_graphs(d);
+  const bool change = d->wide_offsets != (on != 0);
+  if (change) free_graphs(d);
   d->wide_offsets = on != 0;
+  // the tables follow (their device space holds the 64-bit form either way)
+  if (change && d->base) return upload_tables(d);
   return LBM_OK;
 }
 

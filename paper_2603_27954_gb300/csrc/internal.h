@@ -106,6 +106,35 @@ struct CoalesceEntry {   // coarse cell next to the fine region, one direction
   int ncoarse;
 };
 
+// The same tables with 32-bit element offsets, uploaded instead of the
+// 64-bit ones when every array they address holds fewer than 2^31 elements
+// (40-55 % fewer table bytes per step for the boundary and interface kernels).
+struct FaceEntryN {
+  int dst, src, dir;
+};
+struct WallEntryN {
+  int dst, a, b, c;
+  float q;
+  int dir;
+};
+struct ExplodeEntryN {
+  int dst;
+  int src[2];
+};
+struct SaveEntryN {
+  int src;
+};
+struct InflowEntryN {
+  int dst;
+  int csrc[2];
+  int r;
+};
+struct CoalesceEntryN {
+  int dst[2];
+  int fsrc[8];
+  short nfine, ncoarse;
+};
+
 // ---------------------------------------------------------------- mesh
 enum CellType : uint8_t { FLUID = 0, SOLID = 1, COVERED = 2, OUTSIDE = 3 };
 enum BlockState : int8_t { ABSENT = 0, ACTIVE = 1, GHOST = 2 };
@@ -143,6 +172,14 @@ struct Level {
   std::vector<SaveEntry> save;
   std::vector<InflowEntry> infl;
   std::vector<CoalesceEntry> coal;
+  // 32-bit forms (filled when narrow_ok) and the form on the device
+  bool narrow_ok = false, narrow = false;
+  std::vector<WallEntryN> wall_n[2];
+  std::vector<FaceEntryN> face_n[2];
+  std::vector<ExplodeEntryN> expl_n;
+  std::vector<SaveEntryN> save_n;
+  std::vector<InflowEntryN> infl_n;
+  std::vector<CoalesceEntryN> coal_n;
   // device offsets (bytes from the bound base)
   size_t off_f = 0, off_nbr = 0, off_maskoff = 0, off_masks = 0;
   size_t off_wall[2] = {0, 0}, off_face[2] = {0, 0};
@@ -213,7 +250,9 @@ struct TurbArgs {      // turbulent inflow; n_modes == 0: uniform inflow equilib
   const long long* tick;  // coarse steps done
   int shift;            // store relative to the inflow equilibrium (FP16 reference)
 };
-int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], const TurbArgs& turb,
+// Table arguments `e` point to the 64-bit entries, or to the 32-bit ones (the
+// ...N types) when `narrow` is set.
+int launch_faces(void* f, int half, const void* e, int narrow, int n, const float feq[27], const TurbArgs& turb,
                  void* stream);
 // one launch over a work list of (index into lv, block) pairs; grid <= 0: one CTA per item
 // zshift: each item is walked by 2^zshift CTAs (or grid strides) of B >> zshift slabs
@@ -223,17 +262,19 @@ int launch_tick(long long* tick, void* stream);
 // per-sample viscous traction times area, tangential part: out[3 k .. 3 k + 2]
 int launch_friction(const void* f, int half, float inv_scale, const Ref27& ref, int B, const int* nbr, int odd,
                     float omega1, const FrictionSample* e, int n, double* out, void* stream);
-int launch_walls(void* f, int half, float inv_scale, const Ref27& ref, const WallEntry* e, int n, double* partials,
-                 double* link_force, void* stream);
+int launch_walls(void* f, int half, float inv_scale, const Ref27& ref, const void* e, int narrow, int n,
+                 double* partials, double* link_force, void* stream);
 int launch_segments(const double* link_force, const int* seg_begin, int n_seg, double* seg_accum, void* stream);
 int walls_partial_count(int n);
 int launch_force_reduce(const double* partials, int nparts, double* accum, void* stream);
-int launch_explode(void* fine, const void* coarse, int half, float ratio, const ExplodeEntry* e, int ne,
-                   const SaveEntry* s, int ns, float* saved, int parity, void* stream);
-int launch_inflow(void* fine, const void* coarse, int half, float ratio, const InflowEntry* e, int n,
+int launch_explode(void* fine, const void* coarse, int half, float ratio, const void* e, int narrow, int ne,
+                   const void* s, int ns, float* saved, int parity, void* stream);
+int launch_inflow(void* fine, const void* coarse, int half, float ratio, const void* e, int narrow, int n,
                   const float* saved, int parity, void* stream);
-int launch_coalesce(void* coarse, const void* fine, int half, float ratio, const CoalesceEntry* e, int n,
+int launch_coalesce(void* coarse, const void* fine, int half, float ratio, const void* e, int narrow, int n,
                     const float* saved, int parity, void* stream);
+// fill the 32-bit tables of every level whose addressed arrays allow them
+void narrow_tables(Mesh* m);
 int launch_fill(void* f, int half, long long n_blocks, int B, const float dev[27], void* stream);
 int launch_mass(const void* f, int half, float inv_scale, const Ref27& ref, const int* nbr, const int* maskoff,
                 const uint8_t* masks, int n_active, int B, int parity, double* partials, void* stream);

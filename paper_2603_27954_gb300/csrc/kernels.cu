@@ -32,11 +32,11 @@ struct Feq27 {
   float v[27];
 };
 
-template <typename S>
-__global__ void k_faces(S* __restrict__ f, const FaceEntry* __restrict__ e, int n, Feq27 feq) {
+template <typename S, typename E>
+__global__ void k_faces(S* __restrict__ f, const E* __restrict__ e, int n, Feq27 feq) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const FaceEntry x = e[t];
+  const E x = e[t];
   if (x.src < 0) Store<S>::st(f, x.dst, feq.v[x.dir]);
   else f[x.dst] = f[x.src];
 }
@@ -55,15 +55,15 @@ __device__ __forceinline__ float eq_dev(int i, float ux, float uy, float uz) {
 // faces with a turbulent inflow: entries that pull the inflow equilibrium get
 // it at the velocity U e_x + sum_n a_n cos(k_n . (p - U t e_x) + psi_n) of their
 // pulled-from cell centre p, t = coarse steps done (frozen field carried at U)
-template <typename S>
-__global__ void __launch_bounds__(128) k_faces_turb(S* __restrict__ f, const FaceEntry* __restrict__ e, int n,
+template <typename S, typename E>
+__global__ void __launch_bounds__(128) k_faces_turb(S* __restrict__ f, const E* __restrict__ e, int n,
                                                      TurbArgs tb) {
   extern __shared__ float sm[];  // the mode table
   for (int k = threadIdx.x; k < tb.n_modes * kModeCols; k += blockDim.x) sm[k] = tb.modes[k];
   __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const FaceEntry x = e[t];
+  const E x = e[t];
   if (x.src >= 0) {
     f[x.dst] = f[x.src];
     return;
@@ -193,14 +193,14 @@ __device__ void block_sum3(double& a, double& b, double& c) {
   }
 }
 
-template <typename S>
-__global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const WallEntry* __restrict__ e, int n,
+template <typename S, typename E>
+__global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const E* __restrict__ e, int n,
                                                         float inv_scale, Ref27 ref, double* __restrict__ partials,
                                                         double* __restrict__ link_force) {
   const int t = blockIdx.x * kWallThreads + threadIdx.x;
   double Fx = 0.0, Fy = 0.0, Fz = 0.0;
   if (t < n) {
-    const WallEntry w = e[t];
+    const E w = e[t];
     const float fa = Store<S>::ld(f, w.a);  // f*_i(x_f), toward the wall (stored deviation)
     const float q = w.q;
     float out;
@@ -290,33 +290,32 @@ __global__ void __launch_bounds__(256) k_force(const double* __restrict__ partia
 
 // Interface kernels.  ratio = s_fine / s_coarse maps stored coarse values to
 // the fine scale (1 for FP32); saved values are fine-scaled floats.
-template <typename S>
-__global__ void k_explode(S* __restrict__ fine, const S* __restrict__ coarse, const ExplodeEntry* __restrict__ e,
-                          int ne, const SaveEntry* __restrict__ s, int ns, float* __restrict__ saved, int parity,
-                          float ratio) {
+template <typename S, typename E, typename SE>
+__global__ void k_explode(S* __restrict__ fine, const S* __restrict__ coarse, const E* __restrict__ e, int ne,
+                          const SE* __restrict__ s, int ns, float* __restrict__ saved, int parity, float ratio) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < ne) {
-    const ExplodeEntry x = e[t];
+    const E x = e[t];
     Store<S>::st(fine, x.dst, Store<S>::ld(coarse, parity ? x.src[1] : x.src[0]) * ratio);
   }
   if (t < ns) saved[t] = Store<S>::ld(fine, s[t].src);
 }
 
-template <typename S>
-__global__ void k_inflow(S* __restrict__ fine, const S* __restrict__ coarse, const InflowEntry* __restrict__ e, int n,
+template <typename S, typename E>
+__global__ void k_inflow(S* __restrict__ fine, const S* __restrict__ coarse, const E* __restrict__ e, int n,
                          const float* __restrict__ saved, int parity, float ratio) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const InflowEntry x = e[t];
+  const E x = e[t];
   Store<S>::st(fine, x.dst, x.r >= 0 ? saved[x.r] : Store<S>::ld(coarse, parity ? x.csrc[1] : x.csrc[0]) * ratio);
 }
 
-template <typename S>
-__global__ void k_coalesce(S* __restrict__ coarse, const S* __restrict__ fine, const CoalesceEntry* __restrict__ e,
-                           int n, const float* __restrict__ saved, int parity, float ratio) {
+template <typename S, typename E>
+__global__ void k_coalesce(S* __restrict__ coarse, const S* __restrict__ fine, const E* __restrict__ e, int n,
+                           const float* __restrict__ saved, int parity, float ratio) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const CoalesceEntry& x = e[t];
+  const E& x = e[t];
   const long long dst = parity ? x.dst[1] : x.dst[0];
   float vf = 0.0f;
   for (int k = 0; k < x.nfine; ++k) {
@@ -545,20 +544,26 @@ int launch_collide_batch(const CollideArgs* lv, const int2* items, int n_items, 
   return check_launch("collide_batch");
 }
 
-int launch_faces(void* f, int half, const FaceEntry* e, int n, const float feq[27], const TurbArgs& turb,
-                 void* stream) {
-  if (n == 0) return LBM_OK;
-  cudaStream_t s = (cudaStream_t)stream;
+template <typename E>
+void faces_typed(void* f, int half, const E* e, int n, const float feq[27], const TurbArgs& turb, cudaStream_t s) {
   if (turb.n_modes > 0) {
     const size_t smem = (size_t)turb.n_modes * kModeCols * sizeof(float);
-    if (half) k_faces_turb<__half><<<blocks_for(n, 128), 128, smem, s>>>((__half*)f, e, n, turb);
-    else k_faces_turb<float><<<blocks_for(n, 128), 128, smem, s>>>((float*)f, e, n, turb);
-    return check_launch("faces_turb");
+    if (half) k_faces_turb<__half, E><<<blocks_for(n, 128), 128, smem, s>>>((__half*)f, e, n, turb);
+    else k_faces_turb<float, E><<<blocks_for(n, 128), 128, smem, s>>>((float*)f, e, n, turb);
+    return;
   }
   Feq27 v;
   for (int i = 0; i < 27; ++i) v.v[i] = feq[i];
-  if (half) k_faces<__half><<<blocks_for(n, 256), 256, 0, s>>>((__half*)f, e, n, v);
-  else k_faces<float><<<blocks_for(n, 256), 256, 0, s>>>((float*)f, e, n, v);
+  if (half) k_faces<__half, E><<<blocks_for(n, 256), 256, 0, s>>>((__half*)f, e, n, v);
+  else k_faces<float, E><<<blocks_for(n, 256), 256, 0, s>>>((float*)f, e, n, v);
+}
+
+int launch_faces(void* f, int half, const void* e, int narrow, int n, const float feq[27], const TurbArgs& turb,
+                 void* stream) {
+  if (n == 0) return LBM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (narrow) faces_typed(f, half, (const FaceEntryN*)e, n, feq, turb, s);
+  else faces_typed(f, half, (const FaceEntry*)e, n, feq, turb, s);
   return check_launch("faces");
 }
 
@@ -585,16 +590,20 @@ int launch_tick(long long* tick, void* stream) {
 
 int walls_partial_count(int n) { return (int)blocks_for(n, kWallThreads); }
 
-int launch_walls(void* f, int half, float inv_scale, const Ref27& ref, const WallEntry* e, int n, double* partials,
-                 double* link_force, void* stream) {
+template <typename E>
+void walls_typed(void* f, int half, float inv_scale, const Ref27& ref, const E* e, int n, double* partials,
+                 double* link_force, cudaStream_t s) {
+  const unsigned g = blocks_for(n, kWallThreads);
+  if (half) k_walls<__half, E><<<g, kWallThreads, 0, s>>>((__half*)f, e, n, inv_scale, ref, partials, link_force);
+  else k_walls<float, E><<<g, kWallThreads, 0, s>>>((float*)f, e, n, inv_scale, ref, partials, link_force);
+}
+
+int launch_walls(void* f, int half, float inv_scale, const Ref27& ref, const void* e, int narrow, int n,
+                 double* partials, double* link_force, void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (half)
-    k_walls<__half><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((__half*)f, e, n, inv_scale, ref, partials,
-                                                                          link_force);
-  else
-    k_walls<float><<<blocks_for(n, kWallThreads), kWallThreads, 0, s>>>((float*)f, e, n, inv_scale, ref, partials,
-                                                                         link_force);
+  if (narrow) walls_typed(f, half, inv_scale, ref, (const WallEntryN*)e, n, partials, link_force, s);
+  else walls_typed(f, half, inv_scale, ref, (const WallEntry*)e, n, partials, link_force, s);
   return check_launch("walls");
 }
 
@@ -609,42 +618,65 @@ int launch_force_reduce(const double* partials, int nparts, double* accum, void*
   return check_launch("force");
 }
 
-int launch_explode(void* fine, const void* coarse, int half, float ratio, const ExplodeEntry* e, int ne,
-                   const SaveEntry* sv, int ns, float* saved, int parity, void* stream) {
-  long long n = ne > ns ? ne : ns;
-  if (n == 0) return LBM_OK;
-  cudaStream_t s = (cudaStream_t)stream;
+template <typename E, typename SE>
+void explode_typed(void* fine, const void* coarse, int half, float ratio, const E* e, int ne, const SE* sv, int ns,
+                   float* saved, int parity, cudaStream_t s) {
+  const unsigned g = blocks_for(ne > ns ? ne : ns, 256);
   if (half)
-    k_explode<__half><<<blocks_for(n, 256), 256, 0, s>>>((__half*)fine, (const __half*)coarse, e, ne, sv, ns, saved,
-                                                          parity, ratio);
+    k_explode<__half, E, SE><<<g, 256, 0, s>>>((__half*)fine, (const __half*)coarse, e, ne, sv, ns, saved, parity,
+                                                ratio);
   else
-    k_explode<float><<<blocks_for(n, 256), 256, 0, s>>>((float*)fine, (const float*)coarse, e, ne, sv, ns, saved,
-                                                         parity, ratio);
+    k_explode<float, E, SE><<<g, 256, 0, s>>>((float*)fine, (const float*)coarse, e, ne, sv, ns, saved, parity, ratio);
+}
+
+int launch_explode(void* fine, const void* coarse, int half, float ratio, const void* e, int narrow, int ne,
+                   const void* sv, int ns, float* saved, int parity, void* stream) {
+  if (ne == 0 && ns == 0) return LBM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (narrow)
+    explode_typed(fine, coarse, half, ratio, (const ExplodeEntryN*)e, ne, (const SaveEntryN*)sv, ns, saved, parity, s);
+  else
+    explode_typed(fine, coarse, half, ratio, (const ExplodeEntry*)e, ne, (const SaveEntry*)sv, ns, saved, parity, s);
   return check_launch("explode");
 }
 
-int launch_inflow(void* fine, const void* coarse, int half, float ratio, const InflowEntry* e, int n,
+template <typename E>
+void inflow_typed(void* fine, const void* coarse, int half, float ratio, const E* e, int n, const float* saved,
+                  int parity, cudaStream_t s) {
+  if (half)
+    k_inflow<__half, E><<<blocks_for(n, 256), 256, 0, s>>>((__half*)fine, (const __half*)coarse, e, n, saved, parity,
+                                                            ratio);
+  else
+    k_inflow<float, E><<<blocks_for(n, 256), 256, 0, s>>>((float*)fine, (const float*)coarse, e, n, saved, parity,
+                                                           ratio);
+}
+
+int launch_inflow(void* fine, const void* coarse, int half, float ratio, const void* e, int narrow, int n,
                   const float* saved, int parity, void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (half)
-    k_inflow<__half><<<blocks_for(n, 256), 256, 0, s>>>((__half*)fine, (const __half*)coarse, e, n, saved, parity,
-                                                         ratio);
-  else
-    k_inflow<float><<<blocks_for(n, 256), 256, 0, s>>>((float*)fine, (const float*)coarse, e, n, saved, parity, ratio);
+  if (narrow) inflow_typed(fine, coarse, half, ratio, (const InflowEntryN*)e, n, saved, parity, s);
+  else inflow_typed(fine, coarse, half, ratio, (const InflowEntry*)e, n, saved, parity, s);
   return check_launch("inflow");
 }
 
-int launch_coalesce(void* coarse, const void* fine, int half, float ratio, const CoalesceEntry* e, int n,
+template <typename E>
+void coalesce_typed(void* coarse, const void* fine, int half, float ratio, const E* e, int n, const float* saved,
+                    int parity, cudaStream_t s) {
+  if (half)
+    k_coalesce<__half, E><<<blocks_for(n, 256), 256, 0, s>>>((__half*)coarse, (const __half*)fine, e, n, saved,
+                                                              parity, ratio);
+  else
+    k_coalesce<float, E><<<blocks_for(n, 256), 256, 0, s>>>((float*)coarse, (const float*)fine, e, n, saved, parity,
+                                                             ratio);
+}
+
+int launch_coalesce(void* coarse, const void* fine, int half, float ratio, const void* e, int narrow, int n,
                     const float* saved, int parity, void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (half)
-    k_coalesce<__half><<<blocks_for(n, 256), 256, 0, s>>>((__half*)coarse, (const __half*)fine, e, n, saved, parity,
-                                                           ratio);
-  else
-    k_coalesce<float><<<blocks_for(n, 256), 256, 0, s>>>((float*)coarse, (const float*)fine, e, n, saved, parity,
-                                                          ratio);
+  if (narrow) coalesce_typed(coarse, fine, half, ratio, (const CoalesceEntryN*)e, n, saved, parity, s);
+  else coalesce_typed(coarse, fine, half, ratio, (const CoalesceEntry*)e, n, saved, parity, s);
   return check_launch("coalesce");
 }
 

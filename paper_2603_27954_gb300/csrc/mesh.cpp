@@ -792,4 +792,56 @@ int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vecto
   return LBM_OK;
 }
 
+// 32-bit copies of the boundary and interface tables of every level whose
+// own array and (for the interface) finer array hold fewer than 2^31 elements
+template <class Wide, class Narrow, class F>
+void narrow_copy(const std::vector<Wide>& in, std::vector<Narrow>* out, F&& conv) {
+  out->resize(in.size());
+  const long long n = (long long)in.size(), chunk = 1 << 16;
+  parallel_for((n + chunk - 1) / chunk, [&](long long c) {
+    for (long long k = c * chunk; k < std::min(n, (c + 1) * chunk); ++k) (*out)[k] = conv(in[k]);
+  });
+}
+
+void narrow_tables(Mesh* m) {
+  const long long lim = (1LL << 31) - 1;
+  for (int l = 0; l < m->L; ++l) {
+    Level& v = m->lv[l];
+    v.narrow_ok = v.f_elems() <= lim && (l + 1 == m->L || m->lv[l + 1].f_elems() <= lim);
+    if (!v.narrow_ok) {
+      for (int p = 0; p < 2; ++p) {
+        v.wall_n[p].clear();
+        v.face_n[p].clear();
+      }
+      v.expl_n.clear();
+      v.save_n.clear();
+      v.infl_n.clear();
+      v.coal_n.clear();
+      continue;
+    }
+    for (int p = 0; p < 2; ++p) {
+      narrow_copy(v.wall[p], &v.wall_n[p], [](const WallEntry& w) {
+        return WallEntryN{(int)w.dst, (int)w.a, (int)w.b, (int)w.c, w.q, w.dir};
+      });
+      narrow_copy(v.face[p], &v.face_n[p],
+                  [](const FaceEntry& e) { return FaceEntryN{(int)e.dst, (int)e.src, e.dir}; });
+    }
+    narrow_copy(v.expl, &v.expl_n,
+                [](const ExplodeEntry& e) { return ExplodeEntryN{(int)e.dst, {(int)e.src[0], (int)e.src[1]}}; });
+    narrow_copy(v.save, &v.save_n, [](const SaveEntry& e) { return SaveEntryN{(int)e.src}; });
+    narrow_copy(v.infl, &v.infl_n, [](const InflowEntry& e) {
+      return InflowEntryN{(int)e.dst, {(int)e.csrc[0], (int)e.csrc[1]}, e.r};
+    });
+    narrow_copy(v.coal, &v.coal_n, [](const CoalesceEntry& e) {
+      CoalesceEntryN o;
+      o.dst[0] = (int)e.dst[0];
+      o.dst[1] = (int)e.dst[1];
+      for (int j = 0; j < 8; ++j) o.fsrc[j] = (int)e.fsrc[j];
+      o.nfine = (short)e.nfine;
+      o.ncoarse = (short)e.ncoarse;
+      return o;
+    });
+  }
+}
+
 }  // namespace lbm

@@ -256,8 +256,9 @@ def test_watchdog_reports_nan_from_host_injection(L, stream):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 def test_wide_offset_kernels_equal_narrow(L, stream, precision):
-    """The 64-bit-offset collide kernels (used by levels above 2^31 elements)
-    give bit-identical populations on the two-level case."""
+    """The 64-bit-offset collide kernels and boundary / interface tables (used
+    by levels above 2^31 elements) give bit-identical populations on the
+    two-level case; switching after binding re-uploads the tables."""
     c = W.CASES["amr2_small"]
     prec = L.LBM_FP32 if precision == "fp32" else L.LBM_FP16_DEV
     doms = []
