@@ -686,6 +686,85 @@ int build_interface(Mesh& m, int l) {
 
 }  // namespace
 
+// Order of [0, n) by ascending (key(i), i), keys non-negative: a parallel
+// sort of 64-bit words key << b | i when they fit (b = bits of n - 1), else of
+// key / index pairs.
+template <class K>
+std::vector<long long> sorted_order(long long n, K&& key) {
+  std::vector<long long> perm((size_t)n);
+  int b = 1;
+  while ((1LL << b) < n) ++b;
+  std::atomic<long long> kmax{0};
+  parallel_for((n + 65535) / 65536, [&](long long c) {
+    long long mx = 0;
+    for (long long i = c * 65536; i < std::min(n, (c + 1) * 65536); ++i) mx = std::max(mx, key(i));
+    long long cur = kmax.load();
+    while (mx > cur && !kmax.compare_exchange_weak(cur, mx)) {
+    }
+  });
+  if (b < 62 && kmax.load() < (1LL << (62 - b))) {
+    std::vector<unsigned long long> w((size_t)n);
+    parallel_for(n, [&](long long i) { w[(size_t)i] = ((unsigned long long)key(i) << b) | (unsigned long long)i; }, 4096);
+    parallel_sort(w);
+    const unsigned long long mask = (1ULL << b) - 1;
+    parallel_for(n, [&](long long i) { perm[(size_t)i] = (long long)(w[(size_t)i] & mask); }, 4096);
+    return perm;
+  }
+  std::vector<std::pair<long long, long long>> kv((size_t)n);
+  parallel_for(n, [&](long long i) { kv[(size_t)i] = {key(i), i}; }, 4096);
+  parallel_sort(kv);
+  parallel_for(n, [&](long long i) { perm[(size_t)i] = kv[(size_t)i].second; }, 4096);
+  return perm;
+}
+template <class T>
+void permute(std::vector<T>& v, const std::vector<long long>& perm, int stride = 1) {
+  std::vector<T> out(v.size());
+  parallel_for((long long)perm.size(), [&](long long i) {
+    for (int k = 0; k < stride; ++k) out[(size_t)i * stride + k] = v[(size_t)perm[i] * stride + k];
+  }, 4096);
+  v.swap(out);
+}
+
+// Table order for the device: entries sorted by destination address, so that
+// a warp's threads write neighbouring cells of one population plane instead
+// of the 27 planes of one cell (every entry has its own destination, so the
+// order changes no result).  Cut links stay grouped by branch (contiguous
+// per-branch ranges) and are sorted by destination inside each branch; the
+// two parity tables of the faces and of the links share one order with their
+// per-entry companions (face positions, links).
+static void order_tables(Mesh& m) {
+  for (int l = 0; l < m.L; ++l) {
+    Level& v = m.lv[l];
+    if (!v.links.empty()) {
+      // links come grouped by branch; sort inside each branch's range
+      std::vector<long long> perm(v.links.size());
+      for (size_t sg = 0; sg + 1 < v.seg_begin.size(); ++sg) {
+        const long long b0 = v.seg_begin[sg], n = v.seg_begin[sg + 1] - b0;
+        if (n <= 0) continue;
+        const auto local = sorted_order(n, [&](long long i) { return v.wall[0][(size_t)(b0 + i)].dst; });
+        for (long long i = 0; i < n; ++i) perm[(size_t)(b0 + i)] = b0 + local[(size_t)i];
+      }
+      permute(v.links, perm);
+      for (int p = 0; p < 2; ++p) permute(v.wall[p], perm);
+    }
+    if (!v.face[0].empty()) {
+      const auto perm = sorted_order((long long)v.face[0].size(),
+                                     [&](long long i) { return v.face[0][(size_t)i].dst; });
+      for (int p = 0; p < 2; ++p) permute(v.face[p], perm);
+      if (v.face_pos.size() == 4 * v.face[0].size()) permute(v.face_pos, perm, 4);
+    }
+    if (!v.expl.empty())
+      permute(v.expl, sorted_order((long long)v.expl.size(),
+                                   [&](long long i) { return v.expl[(size_t)i].dst; }));
+    if (!v.infl.empty())
+      permute(v.infl, sorted_order((long long)v.infl.size(),
+                                   [&](long long i) { return v.infl[(size_t)i].dst; }));
+    if (!v.coal.empty())
+      permute(v.coal, sorted_order((long long)v.coal.size(),
+                                   [&](long long i) { return v.coal[(size_t)i].dst[0]; }));
+  }
+}
+
 int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vector<Prim>& prims, Mesh* out) {
   Mesh& m = *out;
   m.L = d.levels;
@@ -789,6 +868,7 @@ int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vecto
     rc = build_interface(m, l);
     if (rc) return rc;
   }
+  order_tables(m);
   return LBM_OK;
 }
 
