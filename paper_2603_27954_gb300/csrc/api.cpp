@@ -81,7 +81,7 @@ struct lbm_domain {
   // device
   char* base = nullptr;
   size_t need = 0;
-  size_t off_partials = 0, off_accum = 0, off_mpart = 0;
+  size_t off_partials = 0, off_accum = 0, off_mpart = 0, off_wdone = 0;
   size_t off_linkf = 0, off_segb = 0, off_segacc = 0;  // per-branch forces (finest level)
   int n_seg = 0;
   bool branch_forces = false;
@@ -273,15 +273,15 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s) {
     Timed t(dm, KC_WALLS, (long long)v.wall[parity].size());
     int n = (int)v.wall[parity].size();
     const bool per_branch = dm->branch_forces && l == m.L - 1;
+    // the finest level's walls reduce the force of the step in the same launch
+    const bool finest = l == m.L - 1;
     if ((rc = launch_walls(f, half, 1.0f / v.scale, dm->ref27, dm->base + v.off_wall[parity], v.narrow, n,
                            dm->dev<double>(dm->off_partials), per_branch ? dm->dev<double>(dm->off_linkf) : nullptr,
-                           s)))
+                           dm->dev<unsigned>(dm->off_wdone), finest ? dm->dev<double>(dm->off_accum) : nullptr,
+                           v.wall_rest, s)))
       return rc;
     if (per_branch && (rc = launch_segments(dm->dev<double>(dm->off_linkf), dm->dev<int>(dm->off_segb), dm->n_seg,
                                             dm->dev<double>(dm->off_segacc), s)))
-      return rc;
-    if (l == m.L - 1 && (rc = launch_force_reduce(dm->dev<double>(dm->off_partials), walls_partial_count(n),
-                                                  dm->dev<double>(dm->off_accum), s)))
       return rc;
   }
   return LBM_OK;
@@ -362,7 +362,7 @@ int kernels_per_step(const Mesh& m, int l) {
   if (l == 0 && !v.face[0].empty()) k += 1;
   if (l == 0 && m.turbulent) k += 1;
   if (l == 0 && m.friction) k += 2;
-  if (!v.wall[0].empty()) k += (l == m.L - 1) ? 2 : 1;
+  if (!v.wall[0].empty()) k += 1;
   if (l + 1 < m.L) k += 2 * kernels_per_step(m, l + 1) + (v.expl.size() || v.save.size() ? 1 : 0) +
                         (v.infl.empty() ? 0 : 1) + (v.coal.empty() ? 0 : 1);
   return k;
@@ -401,6 +401,18 @@ int build(lbm_domain* d) {
     v.scale = d->d.precision == LBM_FP16_DEV ? 8192.0f : 1.0f;
   }
   narrow_tables(&d->mesh);
+  // exact total of c_i 2 w_i over each level's cut links (zero for a body
+  // whose links close a surface), the rest-weight part of the momentum
+  // exchange that the wall kernel leaves out of its FP32 link sums
+  for (Level& v : d->mesh.lv) {
+    for (int a = 0; a < 3; ++a) v.wall_rest[a] = 0.0;
+    for (const Link& k : v.links) {
+      const double w2 = 2.0 * rest_weight(k.dir);
+      v.wall_rest[0] += cx(k.dir) * w2;
+      v.wall_rest[1] += cy(k.dir) * w2;
+      v.wall_rest[2] += cz(k.dir) * w2;
+    }
+  }
   // device layout (table space for the 64-bit form, which the 32-bit one fits)
   size_t off = 0;
   auto put = [&](size_t bytes) {
@@ -451,6 +463,7 @@ int build(lbm_domain* d) {
     d->off_facepos = put(d->mesh.lv[0].face_pos.size() * sizeof(int));
   }
   d->off_mpart = put(max_blocks * 5 * sizeof(double));
+  d->off_wdone = put(sizeof(unsigned));
   d->need = off;
   double u[3] = {d->d.u_in, 0, 0};
   for (int i = 0; i < 27; ++i) d->feq_in[i] = (float)(equilibrium(i, 1.0, u) - rest_weight(i));
@@ -549,6 +562,7 @@ int upload(lbm_domain* d) {
 
 int reset_force(lbm_domain* d) {
   CK(cudaMemsetAsync(d->base + d->off_accum, 0, 8 * sizeof(double), d->stream));
+  CK(cudaMemsetAsync(d->base + d->off_wdone, 0, sizeof(unsigned), d->stream));
   CK(cudaMemsetAsync(d->base + d->off_fmean, 0, std::max<size_t>(1, d->prims.size()) * 4 * sizeof(double), d->stream));
   if (d->n_seg) CK(cudaMemsetAsync(d->base + d->off_segacc, 0, (size_t)d->n_seg * 4 * sizeof(double), d->stream));
   return LBM_OK;

@@ -172,6 +172,7 @@ struct Level {
   std::vector<SaveEntry> save;
   std::vector<InflowEntry> infl;
   std::vector<CoalesceEntry> coal;
+  double wall_rest[3] = {0, 0, 0};  // sum over the cut links of c_i 2 w_i
   // 32-bit forms (filled when narrow_ok) and the form on the device
   bool narrow_ok = false, narrow = false;
   std::vector<WallEntryN> wall_n[2];
@@ -262,11 +263,15 @@ int launch_tick(long long* tick, void* stream);
 // per-sample viscous traction times area, tangential part: out[3 k .. 3 k + 2]
 int launch_friction(const void* f, int half, float inv_scale, const Ref27& ref, int B, const int* nbr, int odd,
                     float omega1, const FrictionSample* e, int n, double* out, void* stream);
+// Bouzidi update and momentum exchange of one link table; with `accum` set,
+// the force of this step (gauge-form link sums plus rest[3], the exact sum of
+// c_i 2 w_i over the links) goes to accum[0..2] and is added to accum[3..6]
+// by the launch's last CTA (`done`: a zeroed counter it leaves zeroed).
 int launch_walls(void* f, int half, float inv_scale, const Ref27& ref, const void* e, int narrow, int n,
-                 double* partials, double* link_force, void* stream);
+                 double* partials, double* link_force, unsigned* done, double* accum, const double rest[3],
+                 void* stream);
 int launch_segments(const double* link_force, const int* seg_begin, int n_seg, double* seg_accum, void* stream);
 int walls_partial_count(int n);
-int launch_force_reduce(const double* partials, int nparts, double* accum, void* stream);
 int launch_explode(void* fine, const void* coarse, int half, float ratio, const void* e, int narrow, int ne,
                    const void* s, int ns, float* saved, int parity, void* stream);
 int launch_inflow(void* fine, const void* coarse, int half, float ratio, const void* e, int narrow, int n,

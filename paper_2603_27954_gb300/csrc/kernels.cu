@@ -4,9 +4,9 @@
 //              active block, one thread per (x, y) column walking z.
 //  k_faces     domain faces of level 0 (inflow, zero-gradient outflow, slip).
 //  k_walls     Bouzidi linear bounce-back on cut links fused with the
-//              momentum-exchange force; FP64 warp-shuffle + CTA reduction
-//              into per-CTA partials.
-//  k_force     fixed-order FP64 sum of the partials (deterministic).
+//              momentum-exchange force: float-float warp sums, FP64 CTA
+//              partials, and the fixed-order FP64 total by the last CTA
+//              (deterministic).
 //  k_explode / k_inflow / k_coalesce   refinement-interface transfer.
 //  k_fill      equilibrium initialisation; k_mass FP64 mass / momentum.
 //
@@ -193,12 +193,41 @@ __device__ void block_sum3(double& a, double& b, double& c) {
   }
 }
 
+// float-float value (hi + lo, |lo| <= ulp(hi) / 2) and its exact-error sum
+// (Knuth's TwoSum, then Dekker's fast renormalisation): ~2^-44 relative,
+// enough for FP64 bookkeeping of the momentum exchange without FP64 math in
+// every lane (GB300's FP64 rate is a small fraction of its FP32 rate)
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, t);
+  return FF{h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ FF ff_warp_sum(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = ff_add(v, FF{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)});
+  return v;
+}
+
+// One launch per cut-link table: Bouzidi update, the momentum exchange of
+// every link in gauge form g = c_i (f*_i + f_ibar - 2 w_i) (FP32 per link,
+// float-float warp sums, FP64 per CTA), and - with `accum` set - the last CTA
+// to finish sums the CTA partials in a fixed order into accum[0..6] (the
+// 2 w_i terms enter as their exact host-side total `rest`).  `done` counts
+// finished CTAs and is reset by the last one.
 template <typename S, typename E>
 __global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const E* __restrict__ e, int n,
                                                         float inv_scale, Ref27 ref, double* __restrict__ partials,
-                                                        double* __restrict__ link_force) {
+                                                        double* __restrict__ link_force, unsigned* __restrict__ done,
+                                                        double* __restrict__ accum, double3 rest) {
   const int t = blockIdx.x * kWallThreads + threadIdx.x;
-  double Fx = 0.0, Fy = 0.0, Fz = 0.0;
+  float gx = 0.0f, gy = 0.0f, gz = 0.0f;
   if (t < n) {
     const E w = e[t];
     const float fa = Store<S>::ld(f, w.a);  // f*_i(x_f), toward the wall (stored deviation)
@@ -221,28 +250,71 @@ __global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const
     const int i = w.dir;
     if (Store<S>::scaled) out += wi_ref * (ref.v[i] - ref.v[26 - i]) / inv_scale;
     Store<S>::st(f, w.dst, out);
-    // momentum exchange, resting wall: c_i (f*_i + f_ibar), full populations
-    const double wi = (dcx(i) ? 1.0 / 6.0 : 2.0 / 3.0) * (dcy(i) ? 1.0 / 6.0 : 2.0 / 3.0) *
-                      (dcz(i) ? 1.0 / 6.0 : 2.0 / 3.0);
-    double sum = (double)fa + (double)out;
-    if (Store<S>::scaled) sum = sum * (double)inv_scale + (double)ref.v[i] + (double)ref.v[26 - i];
-    const double s = 2.0 * wi + sum;
-    Fx = dcx(i) * s;
-    Fy = dcy(i) * s;
-    Fz = dcz(i) * s;
-    // per-link force in gauge form (rest state f = w subtracted): a branch's
-    // links do not close a surface, so the reference pressure must not enter
+    // gauge-form momentum exchange of the link, resting wall: full
+    // populations minus the rest weights, (f*_i - w_i) + (f_ibar - w_ibar)
+    float sum = fa + out;
+    if (Store<S>::scaled) sum = fmaf(sum, inv_scale, ref.v[i] + ref.v[26 - i]);
+    gx = dcx(i) ? (dcx(i) > 0 ? sum : -sum) : 0.0f;
+    gy = dcy(i) ? (dcy(i) > 0 ? sum : -sum) : 0.0f;
+    gz = dcz(i) ? (dcz(i) > 0 ? sum : -sum) : 0.0f;
+    // per-link force for the branch sums: a branch's links do not close a
+    // surface, so the reference pressure must not enter
     if (link_force) {
-      link_force[3 * (size_t)t] = dcx(i) * sum;
-      link_force[3 * (size_t)t + 1] = dcy(i) * sum;
-      link_force[3 * (size_t)t + 2] = dcz(i) * sum;
+      link_force[3 * (size_t)t] = gx;
+      link_force[3 * (size_t)t + 1] = gy;
+      link_force[3 * (size_t)t + 2] = gz;
     }
   }
-  block_sum3<kWallThreads>(Fx, Fy, Fz);
+  const FF sx = ff_warp_sum(FF{gx, 0.0f}), sy = ff_warp_sum(FF{gy, 0.0f}), sz = ff_warp_sum(FF{gz, 0.0f});
+  __shared__ double ws[3][kWallThreads / 32];
+  __shared__ bool last;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    ws[0][wid] = (double)sx.hi + (double)sx.lo;
+    ws[1][wid] = (double)sy.hi + (double)sy.lo;
+    ws[2][wid] = (double)sz.hi + (double)sz.lo;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    partials[3 * blockIdx.x + 0] = Fx;
-    partials[3 * blockIdx.x + 1] = Fy;
-    partials[3 * blockIdx.x + 2] = Fz;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = 0; k < kWallThreads / 32; ++k) {
+      a += ws[0][k];
+      b += ws[1][k];
+      c += ws[2][k];
+    }
+    partials[3 * blockIdx.x + 0] = a;
+    partials[3 * blockIdx.x + 1] = b;
+    partials[3 * blockIdx.x + 2] = c;
+    last = false;
+    if (accum) {
+      __threadfence();  // partials visible before the count
+      last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  // last CTA: fixed-order FP64 sum of all CTA partials (the same for any
+  // completion order)
+  __threadfence();
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += kWallThreads) {
+    a += __ldcg(&partials[3 * k]);
+    b += __ldcg(&partials[3 * k + 1]);
+    c += __ldcg(&partials[3 * k + 2]);
+  }
+  block_sum3<kWallThreads>(a, b, c);
+  if (threadIdx.x == 0) {
+    a += rest.x;
+    b += rest.y;
+    c += rest.z;
+    accum[0] = a;
+    accum[1] = b;
+    accum[2] = c;
+    accum[3] += a;
+    accum[4] += b;
+    accum[5] += c;
+    accum[6] += 1.0;
+    *done = 0u;
   }
 }
 
@@ -264,27 +336,6 @@ __global__ void __launch_bounds__(256) k_segments(const double* __restrict__ lin
     seg_accum[4 * k + 1] += b;
     seg_accum[4 * k + 2] += c;
     seg_accum[4 * k + 3] += 1.0;
-  }
-}
-
-// accum: [0..2] force of the last finest step, [3..5] running sum, [6] count
-__global__ void __launch_bounds__(256) k_force(const double* __restrict__ partials, int nparts,
-                                               double* __restrict__ accum) {
-  double a = 0, b = 0, c = 0;
-  for (int k = threadIdx.x; k < nparts; k += 256) {
-    a += partials[3 * k];
-    b += partials[3 * k + 1];
-    c += partials[3 * k + 2];
-  }
-  block_sum3<256>(a, b, c);
-  if (threadIdx.x == 0) {
-    accum[0] = a;
-    accum[1] = b;
-    accum[2] = c;
-    accum[3] += a;
-    accum[4] += b;
-    accum[5] += c;
-    accum[6] += 1.0;
   }
 }
 
@@ -592,18 +643,24 @@ int walls_partial_count(int n) { return (int)blocks_for(n, kWallThreads); }
 
 template <typename E>
 void walls_typed(void* f, int half, float inv_scale, const Ref27& ref, const E* e, int n, double* partials,
-                 double* link_force, cudaStream_t s) {
+                 double* link_force, unsigned* done, double* accum, double3 rest, cudaStream_t s) {
   const unsigned g = blocks_for(n, kWallThreads);
-  if (half) k_walls<__half, E><<<g, kWallThreads, 0, s>>>((__half*)f, e, n, inv_scale, ref, partials, link_force);
-  else k_walls<float, E><<<g, kWallThreads, 0, s>>>((float*)f, e, n, inv_scale, ref, partials, link_force);
+  if (half)
+    k_walls<__half, E><<<g, kWallThreads, 0, s>>>((__half*)f, e, n, inv_scale, ref, partials, link_force, done, accum,
+                                                  rest);
+  else
+    k_walls<float, E><<<g, kWallThreads, 0, s>>>((float*)f, e, n, inv_scale, ref, partials, link_force, done, accum,
+                                                 rest);
 }
 
 int launch_walls(void* f, int half, float inv_scale, const Ref27& ref, const void* e, int narrow, int n,
-                 double* partials, double* link_force, void* stream) {
+                 double* partials, double* link_force, unsigned* done, double* accum, const double rest[3],
+                 void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (narrow) walls_typed(f, half, inv_scale, ref, (const WallEntryN*)e, n, partials, link_force, s);
-  else walls_typed(f, half, inv_scale, ref, (const WallEntry*)e, n, partials, link_force, s);
+  const double3 r = make_double3(rest[0], rest[1], rest[2]);
+  if (narrow) walls_typed(f, half, inv_scale, ref, (const WallEntryN*)e, n, partials, link_force, done, accum, r, s);
+  else walls_typed(f, half, inv_scale, ref, (const WallEntry*)e, n, partials, link_force, done, accum, r, s);
   return check_launch("walls");
 }
 
@@ -613,10 +670,6 @@ int launch_segments(const double* link_force, const int* seg_begin, int n_seg, d
   return check_launch("segments");
 }
 
-int launch_force_reduce(const double* partials, int nparts, double* accum, void* stream) {
-  k_force<<<1, 256, 0, (cudaStream_t)stream>>>(partials, nparts, accum);
-  return check_launch("force");
-}
 
 template <typename E, typename SE>
 void explode_typed(void* fine, const void* coarse, int half, float ratio, const E* e, int ne, const SE* sv, int ns,
