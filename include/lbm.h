@@ -59,16 +59,19 @@ typedef enum {
    FP64.  lbm_get_populations returns f_i - w_i in either form. */
 typedef enum { LBM_FP32 = 1, LBM_FP16_DEV = 2 } lbm_precision;
 
-/* Collide-kernel variants (all compute the same result).  Odd AA step:
-   per-thread column pointers (default), TMA/cp.async staging through shared
-   memory (FP32 and 16^3 blocks only; others fall back to the default), or
-   direct neighbour addressing.  Even step: direct loads and stores, a
-   4-stage TMA bulk pipeline (FP32 and 16^3 blocks only), or two
-   x-neighbouring cells per thread moved with 4-byte pairs and collided as one
-   in packed FP32 (FP16 storage only; the FP16 direct even step runs the same
-   packed code in both lanes and equals it bit for bit).  Defaults: column
-   pointers; direct even step for FP32, pairs for FP16. */
-typedef enum { LBM_ODD_COLUMNS = 0, LBM_ODD_STAGED = 1, LBM_ODD_DIRECT = 2 } lbm_odd_variant;
+/* Collide-kernel variants (all compute the same result; within the FP16 form
+   the packed two-cell kernels and the one-cell ones differ in the last bit of
+   FP32 rounding).  Odd AA step: per-thread column pointers, TMA/cp.async
+   staging through shared memory (FP32 and 16^3 blocks only; others fall back
+   to column pointers), direct neighbour addressing, or two x-neighbouring
+   cells per thread collided as one in packed FP32 (FP16 storage only).  Even
+   step: direct loads and stores, a 4-stage TMA bulk pipeline (FP32 and 16^3
+   blocks only), or two x-neighbouring cells per thread moved with 4-byte
+   pairs and collided as one in packed FP32 (FP16 storage only; the FP16
+   direct even step runs the same packed code in both lanes and equals it bit
+   for bit).  Defaults: column pointers and the direct even step for FP32,
+   pairs in both steps for FP16. */
+typedef enum { LBM_ODD_COLUMNS = 0, LBM_ODD_STAGED = 1, LBM_ODD_DIRECT = 2, LBM_ODD_PAIRS = 3 } lbm_odd_variant;
 typedef enum { LBM_EVEN_DIRECT = 0, LBM_EVEN_TMA = 1, LBM_EVEN_PAIRS = 2 } lbm_even_variant;
 
 /* Problem statement (Sec. 2.2-2.3): domain, inflow, Re_H, refinement.
@@ -353,8 +356,9 @@ typedef struct {
   int z_split_even;  /* CTAs (or persistent-grid work units) per active block of the even step: */
   int z_split_odd;   /*   1, 2, 4 ... up to the block size, each walking block/z_split slabs
                         (results are identical for every split).  0 = automatic, per launch:
-                        8 for FP32 in 16^3 blocks; for FP16 in 16^3 blocks the fewest that give
-                        the launch at least 32 CTAs per SM (at most 8); 1 for 8^3 blocks.
+                        8 for FP32 and for the FP16 odd step in 16^3 blocks; for the FP16 even
+                        step the fewest that give the launch at least 32 CTAs per SM (at most
+                        8); 1 for 8^3 blocks.
                         Ignored by the staged and TMA variants. */
 } lbm_schedule;
 int lbm_set_schedule(lbm_domain* d, const lbm_schedule* s);

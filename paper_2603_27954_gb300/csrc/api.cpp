@@ -46,13 +46,13 @@ double equilibrium(int i, double rho, const double u[3]) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // automatic z split of a collide launch over `blocks` active blocks (log2 of
-// the CTAs per block), from GB300 sweeps with 16^3 blocks: FP32 steps run
-// fastest with 8 CTAs per block on every workload; FP16 steps gain from a
-// split only while the grid is short (the fewest CTAs per block that give at
-// least 32 CTAs per SM); 8^3 blocks are not split
-int auto_zshift(const lbm_domain_desc& s, long long blocks, int sms) {
+// the CTAs per block), from GB300 sweeps with 16^3 blocks: FP32 steps and the
+// FP16 odd step run fastest with 8 CTAs per block on every workload; the FP16
+// even step gains from a split only while the grid is short (the fewest CTAs
+// per block that give at least 32 CTAs per SM); 8^3 blocks are not split
+int auto_zshift(const lbm_domain_desc& s, long long blocks, int sms, int odd) {
   if (s.block != 16) return 0;
-  if (s.precision == LBM_FP32) return 3;
+  if (s.precision == LBM_FP32 || odd) return 3;
   int k = 0;
   while (k < 3 && (blocks << k) < 32LL * sms) ++k;
   return k;
@@ -234,7 +234,7 @@ int level_zshift(lbm_domain* dm, const Level& v, int odd) {
   const int req = odd ? dm->z_split_odd : dm->z_split_even;
   if (req) return zshift_req(req, dm->d.block);
   if (!dm->sms) dm->sms = device_sms();
-  return auto_zshift(dm->d, v.n_active, dm->sms);
+  return auto_zshift(dm->d, v.n_active, dm->sms, odd);
 }
 
 CollideArgs collide_args(lbm_domain* dm, int l) {
@@ -714,7 +714,10 @@ int lbm_create_domain(const lbm_domain_desc* desc, void* cuda_stream, lbm_domain
   if (!d) return fail(LBM_ENOMEM, "host allocation");
   d->d = s;
   d->stream = (cudaStream_t)cuda_stream;
-  if (s.precision == LBM_FP16_DEV) d->even_variant = LBM_EVEN_PAIRS;
+  if (s.precision == LBM_FP16_DEV) {
+    d->even_variant = LBM_EVEN_PAIRS;
+    d->odd_variant = LBM_ODD_PAIRS;
+  }
   *out = d;
   return LBM_OK;
 }
@@ -1325,7 +1328,8 @@ void lbm_destroy(lbm_domain* d) {
 namespace {
 
 bool variant_ok(const lbm_domain* d, int odd, int even) {
-  if (odd < LBM_ODD_COLUMNS || odd > LBM_ODD_DIRECT || even < LBM_EVEN_DIRECT || even > LBM_EVEN_PAIRS) return false;
+  if (odd < LBM_ODD_COLUMNS || odd > LBM_ODD_PAIRS || even < LBM_EVEN_DIRECT || even > LBM_EVEN_PAIRS) return false;
+  if (odd == LBM_ODD_PAIRS && d->d.precision != LBM_FP16_DEV) return false;
   const bool staged_ok = d->d.precision == LBM_FP32 && d->d.block == 16;
   if (odd == LBM_ODD_STAGED && !staged_ok) return false;
   if (even == LBM_EVEN_TMA && !staged_ok) return false;
@@ -1399,7 +1403,7 @@ int lbm_autotune(lbm_domain* d, int steps, lbm_schedule* best, double* ms_per_st
   // coordinate search: the kernel variants at the current z splits, then the
   // even step's split, then the odd step's
   const lbm_schedule start = b;
-  for (int odd = LBM_ODD_COLUMNS; odd <= LBM_ODD_DIRECT; ++odd)
+  for (int odd = LBM_ODD_COLUMNS; odd <= LBM_ODD_PAIRS; ++odd)
     for (int even = LBM_EVEN_DIRECT; even <= LBM_EVEN_PAIRS; ++even) {
       if (!variant_ok(d, odd, even)) continue;
       lbm_schedule c = start;
@@ -1486,7 +1490,7 @@ void build_descs(lbm_batch* b) {
 int batch_zshift(lbm_batch* b, int l, int parity) {
   const int req = parity ? b->sched.z_split_odd : b->sched.z_split_even;
   if (req) return zshift_req(req, b->B);
-  return auto_zshift(b->doms[0]->d, (long long)b->items[l].size(), b->sms);
+  return auto_zshift(b->doms[0]->d, (long long)b->items[l].size(), b->sms, parity);
 }
 
 int batch_advance(lbm_batch* b, int l, int parity) {

@@ -169,6 +169,119 @@ __global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_h2(Co
   }
 }
 
+// Odd step of the FP16 form with two x-neighbouring cells (x0, x0 + 1), x0
+// even, per thread, collided as one in packed FP32.  A thread keeps 9 column
+// pointers: for each of the rows y - 1, y, y + 1 the columns x0 - 1, x0 and
+// x0 + 2 (each in whichever block holds it).  The pull of a population with
+// c_x = 0 is one aligned 4-byte load of both cells' values, with c_x = +-1 two
+// 2-byte loads (x0 - 1 / x0, or x0 + 1 / x0 + 2); the push mirrors it.  Every
+// neighbour of an active block has storage, so both lanes always load; only
+// fluid cells store.  The z-face slabs take the general addressing per cell.
+#ifndef LBM_ODD_PAIR_MINB
+#define LBM_ODD_PAIR_MINB 6
+#endif
+template <int B, typename IDX>
+__global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_h2(CollideArgs a) {
+  constexpr int C3 = B * B * B, S2 = B * B, H = B / 2;
+  __shared__ IDX s_base[27];
+  const ZSeg zg = z_segment(blockIdx.x, a.zshift_odd, B);
+  const int blk = zg.blk, t = threadIdx.x;
+  if (t < 27) s_base[t] = (IDX)a.nbr[(size_t)blk * 27 + t] * (IDX)(27 * C3);
+  __syncthreads();
+  const int x0 = 2 * (t % H), ly = t / H;
+  __half* __restrict__ f = reinterpret_cast<__half*>(a.f);
+  // slab-lz column of cell (x, y), x and y within one block of the block's range
+  auto colp = [&](int x, int y, int lz) -> __half* {
+    const int xyd = block_digit<B>(x) + 3 * block_digit<B>(y);
+    return f + (s_base[xyd + 9] + (IDX)((lz * B + (y & (B - 1))) * B + (x & (B - 1))));
+  };
+  // general address of population slot `slot` at (x, y, lz) + (dx, dy, dz)
+  auto gaddr = [&](int x, int dx, int dy, int lz, int dz, int slot) {
+    const int nx = x + dx, ny = ly + dy, nz = lz + dz;
+    const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
+    const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
+    return s_base[bd] + (IDX)(slot * C3 + nc);
+  };
+  const int mo = a.maskoff[blk];
+  const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
+  const Rates rates{a.omega1, a.omega2, a.galilean};
+  for (int lz = zg.z0; lz < zg.z1; ++lz) {
+    const int cell = (lz * B + ly) * B + x0;
+    const bool m0 = !mask || mask[cell], m1 = !mask || mask[cell + 1];
+    if (!m0 && !m1) continue;
+    const bool face = lz == 0 || lz == B - 1;
+    F2 d[27];
+    if (!face) {
+      __half *cL[3], *cC[3], *cR[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        cL[k] = colp(x0 - 1, ly + k - 1, lz);
+        cC[k] = colp(x0, ly + k - 1, lz);
+        cR[k] = colp(x0 + 2, ly + k - 1, lz);
+      }
+#pragma unroll
+      for (int i = 0; i < 27; ++i) {  // pull f_i from (x - c_i, ibar) for both cells
+        const int k = 1 - dcy(i);
+        const int off = (26 - i) * C3 - dcz(i) * S2;
+        float lo, hi;
+        if (dcx(i) == 0) {
+          const __half2 h = *reinterpret_cast<const __half2*>(cC[k] + off);
+          lo = __low2float(h);
+          hi = __high2float(h);
+        } else if (dcx(i) > 0) {
+          lo = __half2float(cL[k][off]);
+          hi = __half2float(cC[k][off]);
+        } else {
+          lo = __half2float(cC[k][off + 1]);
+          hi = __half2float(cR[k][off]);
+        }
+        d[i] = F2::pack(lo, hi);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 27; ++i) {
+        const float lo = __half2float(f[gaddr(x0, -dcx(i), -dcy(i), lz, -dcz(i), 26 - i)]);
+        const float hi = __half2float(f[gaddr(x0 + 1, -dcx(i), -dcy(i), lz, -dcz(i), 26 - i)]);
+        d[i] = F2::pack(lo, hi);
+      }
+    }
+    cumulant_collide_h2(d, rates, a.inv_scale, a.scale, &a.ref);
+    asm volatile("" ::: "memory");  // keep the pointer rebuild after the collision
+    if (!face) {
+      __half *cL[3], *cC[3], *cR[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        cL[k] = colp(x0 - 1, ly + k - 1, lz);
+        cC[k] = colp(x0, ly + k - 1, lz);
+        cR[k] = colp(x0 + 2, ly + k - 1, lz);
+      }
+#pragma unroll
+      for (int i = 0; i < 27; ++i) {  // push f*_i to (x + c_i, i) for both cells
+        const int k = 1 + dcy(i);
+        const int off = i * C3 + dcz(i) * S2;
+        const __half lo = __float2half_rn(d[i].lo()), hi = __float2half_rn(d[i].hi());
+        if (dcx(i) == 0) {
+          if (m0 && m1) *reinterpret_cast<__half2*>(cC[k] + off) = __halves2half2(lo, hi);
+          else if (m0) cC[k][off] = lo;
+          else cC[k][off + 1] = hi;
+        } else if (dcx(i) > 0) {
+          if (m0) cC[k][off + 1] = lo;
+          if (m1) cR[k][off] = hi;
+        } else {
+          if (m0) cL[k][off] = lo;
+          if (m1) cC[k][off] = hi;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 27; ++i) {
+        if (m0) f[gaddr(x0, dcx(i), dcy(i), lz, dcz(i), i)] = __float2half_rn(d[i].lo());
+        if (m1) f[gaddr(x0 + 1, dcx(i), dcy(i), lz, dcz(i), i)] = __float2half_rn(d[i].hi());
+      }
+    }
+  }
+}
+
 template <int B, bool ODD, typename IDX, typename S>
 __global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_collide(CollideArgs a) {
   __shared__ IDX s_base[27];

@@ -46,7 +46,7 @@ class Schedule(C.Structure):
                 "z_split_odd": self.z_split_odd}
 
 
-ODD_VARIANTS = {0: "columns", 1: "staged", 2: "direct"}
+ODD_VARIANTS = {0: "columns", 1: "staged", 2: "direct", 3: "pairs"}
 EVEN_VARIANTS = {0: "direct", 1: "tma", 2: "pairs"}
 
 

@@ -123,3 +123,38 @@ def test_fp16_paired_even_step_equals_direct(L, stream, case):
         d.close()
     for a, b in zip(*out):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("case", ["tiny", "amr2_small"])
+def test_fp16_odd_step_variants_agree(L, stream, case):
+    """The paired odd step (two x-neighbouring cells per thread, one packed
+    collision) against the one-cell column-pointer and direct odd steps,
+    over several z splits: the packed and the one-cell arithmetic round
+    differently in the last FP32 bit, so some stored binary16 values differ
+    by one unit (at most ~1.5e-5 in f at these magnitudes, most of them far
+    smaller: many stored values are near zero); the pair kernel
+    itself gives the same result for every z split, bit for bit."""
+    c = W.CASES[case]
+    B = c["block"]
+    runs = {}
+    for odd, zo in ((3, 1), (3, 2), (3, B // 2), (3, B), (0, 0), (2, 1)):
+        desc = L.domain_desc(*c["n0"], levels=c["levels"], block=B, bc=c["bc"], u_in=c["u_in"],
+                             re_h=c["re_h"], precision=L.LBM_FP16_DEV)
+        d = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=stream)
+        d.set_schedule(0, odd, 2, 0, zo)
+        d.step(5)
+        runs[(odd, zo)] = [d.get_populations(l) for l in range(c["levels"])], d.drag()[1]
+        d.close()
+    ref = runs[(3, 1)]
+    for key, got in runs.items():
+        for a, b in zip(ref[0], got[0]):
+            if key[0] == 3:
+                np.testing.assert_array_equal(a, b, err_msg=str(key))
+            else:
+                ok = ~np.isnan(a)
+                assert np.array_equal(ok, ~np.isnan(b))
+                diff = np.abs(a[ok] - b[ok])
+                # one binary16 unit of the stored values at most, on average far below it
+                assert diff.max() < 2e-5, (key, diff.max())
+                assert diff.mean() < 1e-7, (key, diff.mean())
+        np.testing.assert_allclose(ref[1], got[1], rtol=1e-4, atol=1e-5 * np.abs(ref[1]).max(), err_msg=str(key))

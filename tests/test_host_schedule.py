@@ -19,7 +19,7 @@ def domain(precision, block=16):
     (L.LBM_FP32, 16, 0, 2, False), (L.LBM_FP32, 8, 1, 0, False), (L.LBM_FP32, 8, 0, 1, False),
     (L.LBM_FP16_DEV, 16, 0, 2, True), (L.LBM_FP16_DEV, 8, 2, 2, True), (L.LBM_FP16_DEV, 16, 1, 0, False),
     (L.LBM_FP16_DEV, 16, 0, 1, False), (L.LBM_FP32, 16, 3, 0, False), (L.LBM_FP32, 16, 0, 3, False),
-    (L.LBM_FP16_DEV, 16, 3, 2, False),
+    (L.LBM_FP16_DEV, 16, 3, 2, True), (L.LBM_FP16_DEV, 8, 3, 0, True), (L.LBM_FP16_DEV, 16, 4, 2, False),
 ])
 def test_schedule_validation(precision, block, odd, even, ok):
     h = domain(precision, block)
@@ -35,7 +35,7 @@ def test_schedule_validation(precision, block, odd, even, ok):
 
 
 def test_default_schedules():
-    for precision, odd, even in ((L.LBM_FP32, 0, 0), (L.LBM_FP16_DEV, 0, 2)):
+    for precision, odd, even in ((L.LBM_FP32, 0, 0), (L.LBM_FP16_DEV, 3, 2)):
         h = domain(precision)
         s = L.lbm_get_schedule(h)
         assert (s.odd_variant, s.even_variant) == (odd, even)
