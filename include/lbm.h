@@ -64,13 +64,13 @@ typedef enum { LBM_FP32 = 1, LBM_FP16_DEV = 2 } lbm_precision;
    FP32 rounding).  Odd AA step: per-thread column pointers, TMA/cp.async
    staging through shared memory (FP32 and 16^3 blocks only; others fall back
    to column pointers), direct neighbour addressing, or two x-neighbouring
-   cells per thread collided as one in packed FP32 (FP16 storage only).  Even
-   step: direct loads and stores, a 4-stage TMA bulk pipeline (FP32 and 16^3
-   blocks only), or two x-neighbouring cells per thread moved with 4-byte
-   pairs and collided as one in packed FP32 (FP16 storage only; the FP16
-   direct even step runs the same packed code in both lanes and equals it bit
-   for bit).  Defaults: column pointers and the direct even step for FP32,
-   pairs in both steps for FP16. */
+   cells per thread collided as one in packed FP32.  Even step: direct loads
+   and stores, a 4-stage TMA bulk pipeline (FP32 and 16^3 blocks only), or two
+   x-neighbouring cells per thread moved with pair loads and stores (4 bytes
+   in FP16, 8 in FP32) and collided as one in packed FP32 (the FP16 direct
+   even step runs the same packed code in both lanes and equals it bit for
+   bit).  Defaults: column pointers and the direct even step for FP32, pairs
+   in both steps for FP16; lbm_autotune measures all of them. */
 typedef enum { LBM_ODD_COLUMNS = 0, LBM_ODD_STAGED = 1, LBM_ODD_DIRECT = 2, LBM_ODD_PAIRS = 3 } lbm_odd_variant;
 typedef enum { LBM_EVEN_DIRECT = 0, LBM_EVEN_TMA = 1, LBM_EVEN_PAIRS = 2 } lbm_even_variant;
 

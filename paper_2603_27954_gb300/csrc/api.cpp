@@ -1329,11 +1329,9 @@ namespace {
 
 bool variant_ok(const lbm_domain* d, int odd, int even) {
   if (odd < LBM_ODD_COLUMNS || odd > LBM_ODD_PAIRS || even < LBM_EVEN_DIRECT || even > LBM_EVEN_PAIRS) return false;
-  if (odd == LBM_ODD_PAIRS && d->d.precision != LBM_FP16_DEV) return false;
   const bool staged_ok = d->d.precision == LBM_FP32 && d->d.block == 16;
   if (odd == LBM_ODD_STAGED && !staged_ok) return false;
   if (even == LBM_EVEN_TMA && !staged_ok) return false;
-  if (even == LBM_EVEN_PAIRS && d->d.precision != LBM_FP16_DEV) return false;
   return true;
 }
 

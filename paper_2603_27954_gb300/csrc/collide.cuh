@@ -123,17 +123,44 @@ __device__ __forceinline__ void collide_block(const CollideArgs& a, const int bl
   }
 }
 
-// Even step of the FP16 form with two x-neighbouring cells per thread: one
-// 4-byte load or store moves a population of both cells, halving the
-// load/store instructions of the one-cell-per-thread kernel (whose FP16 form
-// is bound by instruction issue, not bytes), and the two collisions run as
-// one in packed FP32 (two lanes per instruction); a pair with one non-fluid
-// cell writes only the other.
+// Two x-neighbouring stored values (an even element index, so the pair is
+// 4-byte aligned in FP16 and 8-byte aligned in FP32) as the two lanes of a
+// packed FP32 register, and back.
+template <typename S>
+struct PairIO;
+template <>
+struct PairIO<float> {
+  static __device__ __forceinline__ F2 ld(const float* p) {
+    return F2{*reinterpret_cast<const unsigned long long*>(p)};
+  }
+  static __device__ __forceinline__ void st(float* p, F2 v) { *reinterpret_cast<unsigned long long*>(p) = v.v; }
+};
+template <>
+struct PairIO<__half> {
+  static __device__ __forceinline__ F2 ld(const __half* p) {
+    const __half2 h = *reinterpret_cast<const __half2*>(p);
+    return F2::pack(__low2float(h), __high2float(h));
+  }
+  static __device__ __forceinline__ void st(__half* p, F2 v) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v.lo(), v.hi());
+  }
+};
+// the collision of a pair in either storage form
+template <typename S>
+__device__ __forceinline__ void collide_pair(F2* d, const CollideArgs& a, const Rates& r) {
+  collide_cell<F2, Store<S>::scaled>(d, r, a.inv_scale, a.scale, &a.ref);
+}
+
+// Even step with two x-neighbouring cells per thread: one 4-byte (FP16) or
+// 8-byte (FP32) load or store moves a population of both cells, halving the
+// load/store instructions of the one-cell-per-thread kernel, and the two
+// collisions run as one in packed FP32 (two lanes per instruction); a pair
+// with one non-fluid cell writes only the other.
 #ifndef LBM_PAIR_MINB
 #define LBM_PAIR_MINB 6
 #endif
-template <int B, typename IDX>
-__global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_h2(CollideArgs a) {
+template <int B, typename IDX, typename S>
+__global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_p2(CollideArgs a) {
   constexpr int C3 = B * B * B;
   const ZSeg zg = z_segment(blockIdx.x, a.zshift_even, B);
   const int blk = zg.blk;
@@ -142,46 +169,42 @@ __global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_h2(Co
   const int mo = a.maskoff[blk];
   const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
   const Rates rates{a.omega1, a.omega2, a.galilean};
-  __half* __restrict__ f = reinterpret_cast<__half*>(a.f);
+  S* __restrict__ f = reinterpret_cast<S*>(a.f);
   for (int lz = zg.z0; lz < zg.z1; ++lz) {
     const int cell = (lz * B + ly) * B + lx;
     const bool m0 = !mask || mask[cell], m1 = !mask || mask[cell + 1];
     if (!m0 && !m1) continue;
-    const __half2* p = reinterpret_cast<const __half2*>(f + own + cell);
+    S* p = f + own + cell;
     F2 d[27];
 #pragma unroll
-    for (int i = 0; i < 27; ++i) {
-      const __half2 h = p[i * (C3 / 2)];
-      d[i] = F2::pack(__low2float(h), __high2float(h));
-    }
-    cumulant_collide_h2(d, rates, a.inv_scale, a.scale, &a.ref);
+    for (int i = 0; i < 27; ++i) d[i] = PairIO<S>::ld(p + i * C3);
+    collide_pair<S>(d, a, rates);
     if (m0 && m1) {
-      __half2* q = reinterpret_cast<__half2*>(f + own + cell);
 #pragma unroll
-      for (int i = 0; i < 27; ++i) q[(26 - i) * (C3 / 2)] = __floats2half2_rn(d[i].lo(), d[i].hi());
+      for (int i = 0; i < 27; ++i) PairIO<S>::st(p + (26 - i) * C3, d[i]);
     } else if (m0) {
 #pragma unroll
-      for (int i = 0; i < 27; ++i) f[own + (IDX)((26 - i) * C3 + cell)] = __float2half_rn(d[i].lo());
+      for (int i = 0; i < 27; ++i) Store<S>::st(p, (26 - i) * C3, d[i].lo());
     } else {
 #pragma unroll
-      for (int i = 0; i < 27; ++i) f[own + (IDX)((26 - i) * C3 + cell + 1)] = __float2half_rn(d[i].hi());
+      for (int i = 0; i < 27; ++i) Store<S>::st(p, (26 - i) * C3 + 1, d[i].hi());
     }
   }
 }
 
-// Odd step of the FP16 form with two x-neighbouring cells (x0, x0 + 1), x0
-// even, per thread, collided as one in packed FP32.  A thread keeps 9 column
-// pointers: for each of the rows y - 1, y, y + 1 the columns x0 - 1, x0 and
-// x0 + 2 (each in whichever block holds it).  The pull of a population with
-// c_x = 0 is one aligned 4-byte load of both cells' values, with c_x = +-1 two
-// 2-byte loads (x0 - 1 / x0, or x0 + 1 / x0 + 2); the push mirrors it.  Every
+// Odd step with two x-neighbouring cells (x0, x0 + 1), x0 even, per thread,
+// collided as one in packed FP32.  A thread keeps 9 column pointers: for each
+// of the rows y - 1, y, y + 1 the columns x0 - 1, x0 and x0 + 2 (each in
+// whichever block holds it).  The pull of a population with c_x = 0 is one
+// aligned pair load of both cells' values, with c_x = +-1 two single loads
+// (x0 - 1 / x0, or x0 + 1 / x0 + 2); the push mirrors it.  Every
 // neighbour of an active block has storage, so both lanes always load; only
 // fluid cells store.  The z-face slabs take the general addressing per cell.
 #ifndef LBM_ODD_PAIR_MINB
 #define LBM_ODD_PAIR_MINB 6
 #endif
-template <int B, typename IDX>
-__global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_h2(CollideArgs a) {
+template <int B, typename IDX, typename S>
+__global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_p2(CollideArgs a) {
   constexpr int C3 = B * B * B, S2 = B * B, H = B / 2;
   __shared__ IDX s_base[27];
   const ZSeg zg = z_segment(blockIdx.x, a.zshift_odd, B);
@@ -189,9 +212,9 @@ __global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_h2
   if (t < 27) s_base[t] = (IDX)a.nbr[(size_t)blk * 27 + t] * (IDX)(27 * C3);
   __syncthreads();
   const int x0 = 2 * (t % H), ly = t / H;
-  __half* __restrict__ f = reinterpret_cast<__half*>(a.f);
+  S* __restrict__ f = reinterpret_cast<S*>(a.f);
   // slab-lz column of cell (x, y), x and y within one block of the block's range
-  auto colp = [&](int x, int y, int lz) -> __half* {
+  auto colp = [&](int x, int y, int lz) -> S* {
     const int xyd = block_digit<B>(x) + 3 * block_digit<B>(y);
     return f + (s_base[xyd + 9] + (IDX)((lz * B + (y & (B - 1))) * B + (x & (B - 1))));
   };
@@ -212,7 +235,7 @@ __global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_h2
     const bool face = lz == 0 || lz == B - 1;
     F2 d[27];
     if (!face) {
-      __half *cL[3], *cC[3], *cR[3];
+      S *cL[3], *cC[3], *cR[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         cL[k] = colp(x0 - 1, ly + k - 1, lz);
@@ -223,32 +246,20 @@ __global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_h2
       for (int i = 0; i < 27; ++i) {  // pull f_i from (x - c_i, ibar) for both cells
         const int k = 1 - dcy(i);
         const int off = (26 - i) * C3 - dcz(i) * S2;
-        float lo, hi;
-        if (dcx(i) == 0) {
-          const __half2 h = *reinterpret_cast<const __half2*>(cC[k] + off);
-          lo = __low2float(h);
-          hi = __high2float(h);
-        } else if (dcx(i) > 0) {
-          lo = __half2float(cL[k][off]);
-          hi = __half2float(cC[k][off]);
-        } else {
-          lo = __half2float(cC[k][off + 1]);
-          hi = __half2float(cR[k][off]);
-        }
-        d[i] = F2::pack(lo, hi);
+        if (dcx(i) == 0) d[i] = PairIO<S>::ld(cC[k] + off);
+        else if (dcx(i) > 0) d[i] = F2::pack(Store<S>::ld(cL[k], off), Store<S>::ld(cC[k], off));
+        else d[i] = F2::pack(Store<S>::ld(cC[k], off + 1), Store<S>::ld(cR[k], off));
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < 27; ++i) {
-        const float lo = __half2float(f[gaddr(x0, -dcx(i), -dcy(i), lz, -dcz(i), 26 - i)]);
-        const float hi = __half2float(f[gaddr(x0 + 1, -dcx(i), -dcy(i), lz, -dcz(i), 26 - i)]);
-        d[i] = F2::pack(lo, hi);
-      }
+      for (int i = 0; i < 27; ++i)
+        d[i] = F2::pack(Store<S>::ld(f, gaddr(x0, -dcx(i), -dcy(i), lz, -dcz(i), 26 - i)),
+                        Store<S>::ld(f, gaddr(x0 + 1, -dcx(i), -dcy(i), lz, -dcz(i), 26 - i)));
     }
-    cumulant_collide_h2(d, rates, a.inv_scale, a.scale, &a.ref);
+    collide_pair<S>(d, a, rates);
     asm volatile("" ::: "memory");  // keep the pointer rebuild after the collision
     if (!face) {
-      __half *cL[3], *cC[3], *cR[3];
+      S *cL[3], *cC[3], *cR[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         cL[k] = colp(x0 - 1, ly + k - 1, lz);
@@ -259,24 +270,23 @@ __global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_h2
       for (int i = 0; i < 27; ++i) {  // push f*_i to (x + c_i, i) for both cells
         const int k = 1 + dcy(i);
         const int off = i * C3 + dcz(i) * S2;
-        const __half lo = __float2half_rn(d[i].lo()), hi = __float2half_rn(d[i].hi());
         if (dcx(i) == 0) {
-          if (m0 && m1) *reinterpret_cast<__half2*>(cC[k] + off) = __halves2half2(lo, hi);
-          else if (m0) cC[k][off] = lo;
-          else cC[k][off + 1] = hi;
+          if (m0 && m1) PairIO<S>::st(cC[k] + off, d[i]);
+          else if (m0) Store<S>::st(cC[k], off, d[i].lo());
+          else Store<S>::st(cC[k], off + 1, d[i].hi());
         } else if (dcx(i) > 0) {
-          if (m0) cC[k][off + 1] = lo;
-          if (m1) cR[k][off] = hi;
+          if (m0) Store<S>::st(cC[k], off + 1, d[i].lo());
+          if (m1) Store<S>::st(cR[k], off, d[i].hi());
         } else {
-          if (m0) cL[k][off] = lo;
-          if (m1) cC[k][off] = hi;
+          if (m0) Store<S>::st(cL[k], off, d[i].lo());
+          if (m1) Store<S>::st(cC[k], off, d[i].hi());
         }
       }
     } else {
 #pragma unroll
       for (int i = 0; i < 27; ++i) {
-        if (m0) f[gaddr(x0, dcx(i), dcy(i), lz, dcz(i), i)] = __float2half_rn(d[i].lo());
-        if (m1) f[gaddr(x0 + 1, dcx(i), dcy(i), lz, dcz(i), i)] = __float2half_rn(d[i].hi());
+        if (m0) Store<S>::st(f, gaddr(x0, dcx(i), dcy(i), lz, dcz(i), i), d[i].lo());
+        if (m1) Store<S>::st(f, gaddr(x0 + 1, dcx(i), dcy(i), lz, dcz(i), i), d[i].hi());
       }
     }
   }

@@ -510,15 +510,15 @@ void collide_on(const CollideArgs& a, int odd, cudaStream_t s) {
   if (odd) {
     if (f32 && a.odd_variant == LBM_ODD_STAGED && B == 16)
       k_collide_odd_staged<IDX><<<a.n_active, 256, kStageBytes, s>>>(a);
-    else if (!f32 && a.odd_variant == LBM_ODD_PAIRS)
-      k_collide_odd_h2<B, IDX><<<a.n_active << a.zshift_odd, B * B / 2, 0, s>>>(a);
+    else if (a.odd_variant == LBM_ODD_PAIRS)
+      k_collide_odd_p2<B, IDX, S><<<a.n_active << a.zshift_odd, B * B / 2, 0, s>>>(a);
     else if (a.odd_variant == LBM_ODD_DIRECT) k_collide<B, true, IDX, S><<<a.n_active << a.zshift_odd, B * B, 0, s>>>(a);
     else k_collide_odd_cols<B, IDX, S><<<a.n_active << a.zshift_odd, B * B, 0, s>>>(a);
   } else {
     if (f32 && a.even_variant == LBM_EVEN_TMA && B == 16)
       k_collide_even_tma<IDX><<<a.n_active, 256, kEvenBytes, s>>>(a);
-    else if (!f32 && a.even_variant == LBM_EVEN_PAIRS)
-      k_collide_even_h2<B, IDX><<<a.n_active << a.zshift_even, B * B / 2, 0, s>>>(a);
+    else if (a.even_variant == LBM_EVEN_PAIRS)
+      k_collide_even_p2<B, IDX, S><<<a.n_active << a.zshift_even, B * B / 2, 0, s>>>(a);
     else k_collide<B, false, IDX, S><<<a.n_active << a.zshift_even, B * B, 0, s>>>(a);
   }
 }

@@ -16,9 +16,10 @@ def domain(precision, block=16):
 
 @pytest.mark.parametrize("precision,block,odd,even,ok", [
     (L.LBM_FP32, 16, 0, 0, True), (L.LBM_FP32, 16, 1, 1, True), (L.LBM_FP32, 16, 2, 0, True),
-    (L.LBM_FP32, 16, 0, 2, False), (L.LBM_FP32, 8, 1, 0, False), (L.LBM_FP32, 8, 0, 1, False),
+    (L.LBM_FP32, 16, 0, 2, True), (L.LBM_FP32, 8, 1, 0, False), (L.LBM_FP32, 8, 0, 1, False),
     (L.LBM_FP16_DEV, 16, 0, 2, True), (L.LBM_FP16_DEV, 8, 2, 2, True), (L.LBM_FP16_DEV, 16, 1, 0, False),
-    (L.LBM_FP16_DEV, 16, 0, 1, False), (L.LBM_FP32, 16, 3, 0, False), (L.LBM_FP32, 16, 0, 3, False),
+    (L.LBM_FP16_DEV, 16, 0, 1, False), (L.LBM_FP32, 16, 3, 0, True), (L.LBM_FP32, 16, 0, 3, False),
+    (L.LBM_FP32, 8, 3, 2, True), (L.LBM_FP32, 16, 4, 0, False),
     (L.LBM_FP16_DEV, 16, 3, 2, True), (L.LBM_FP16_DEV, 8, 3, 0, True), (L.LBM_FP16_DEV, 16, 4, 2, False),
 ])
 def test_schedule_validation(precision, block, odd, even, ok):
