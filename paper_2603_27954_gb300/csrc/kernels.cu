@@ -378,12 +378,24 @@ __global__ void k_coalesce(S* __restrict__ coarse, const S* __restrict__ fine, c
   Store<S>::st(coarse, dst, v * 0.125f);
 }
 
+// one CTA per (storage block, population plane): the plane's C3 values are
+// all equal, written as 16-byte words
 template <typename S>
-__global__ void k_fill(S* __restrict__ f, long long n, int c3, Feq27 dev) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const int i = (int)((t / c3) % 27);
-  Store<S>::st(f, t, dev.v[i]);
+__global__ void __launch_bounds__(256) k_fill(S* __restrict__ f, int c3, Feq27 dev) {
+  const long long chunk = blockIdx.x;
+  const float v = dev.v[(int)(chunk % 27)];
+  uint4 w;
+  if (std::is_same<S, float>::value) {
+    const unsigned b = __float_as_uint(v);
+    w = make_uint4(b, b, b, b);
+  } else {
+    const unsigned short h = __half_as_ushort(__float2half_rn(v));
+    const unsigned b = (unsigned)h | ((unsigned)h << 16);
+    w = make_uint4(b, b, b, b);
+  }
+  uint4* p = reinterpret_cast<uint4*>(f + chunk * c3);
+  const int nw = c3 * (int)sizeof(S) / 16;
+  for (int k = threadIdx.x; k < nw; k += blockDim.x) p[k] = w;
 }
 
 // FP64 mass and momentum of the incoming populations of one level; per CTA
@@ -739,11 +751,12 @@ int launch_fill(void* f, int half, long long n_blocks, int B, const float dev[27
   Feq27 v;
   for (int i = 0; i < 27; ++i) v.v[i] = dev[i];
   const int c3 = B * B * B;
-  long long n = n_blocks * 27LL * c3;
-  if (n == 0) return LBM_OK;
+  const long long chunks = n_blocks * 27LL;
+  if (chunks == 0) return LBM_OK;
+  if (chunks > 0x7fffffffLL) return LBM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (half) k_fill<__half><<<blocks_for(n, 256), 256, 0, s>>>((__half*)f, n, c3, v);
-  else k_fill<float><<<blocks_for(n, 256), 256, 0, s>>>((float*)f, n, c3, v);
+  if (half) k_fill<__half><<<(unsigned)chunks, 256, 0, s>>>((__half*)f, c3, v);
+  else k_fill<float><<<(unsigned)chunks, 256, 0, s>>>((float*)f, c3, v);
   return check_launch("fill");
 }
 
