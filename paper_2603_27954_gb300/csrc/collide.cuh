@@ -199,7 +199,9 @@ __global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_p2(Co
 // aligned pair load of both cells' values, with c_x = +-1 two single loads
 // (x0 - 1 / x0, or x0 + 1 / x0 + 2); the push mirrors it.  Every
 // neighbour of an active block has storage, so both lanes always load; only
-// fluid cells store.  The z-face slabs take the general addressing per cell.
+// fluid cells store.  On the two z-face slabs the pointers are built per c_z
+// group, for the slab (of this block or of its z neighbour) that the group
+// reaches.
 #ifndef LBM_ODD_PAIR_MINB
 #define LBM_ODD_PAIR_MINB 6
 #endif
@@ -218,12 +220,10 @@ __global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_p2
     const int xyd = block_digit<B>(x) + 3 * block_digit<B>(y);
     return f + (s_base[xyd + 9] + (IDX)((lz * B + (y & (B - 1))) * B + (x & (B - 1))));
   };
-  // general address of population slot `slot` at (x, y, lz) + (dx, dy, dz)
-  auto gaddr = [&](int x, int dx, int dy, int lz, int dz, int slot) {
-    const int nx = x + dx, ny = ly + dy, nz = lz + dz;
-    const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
-    const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
-    return s_base[bd] + (IDX)(slot * C3 + nc);
+  // slab-zs column of cell (x, y), zs in [-1, B] (this block or a z neighbour)
+  auto colpz = [&](int x, int y, int zs) -> S* {
+    const int bd = block_digit<B>(x) + 3 * block_digit<B>(y) + 9 * block_digit<B>(zs);
+    return f + (s_base[bd] + (IDX)(((zs & (B - 1)) * B + (y & (B - 1))) * B + (x & (B - 1))));
   };
   const int mo = a.maskoff[blk];
   const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
@@ -252,9 +252,24 @@ __global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_p2
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < 27; ++i)
-        d[i] = F2::pack(Store<S>::ld(f, gaddr(x0, -dcx(i), -dcy(i), lz, -dcz(i), 26 - i)),
-                        Store<S>::ld(f, gaddr(x0 + 1, -dcx(i), -dcy(i), lz, -dcz(i), 26 - i)));
+      for (int g = -1; g <= 1; ++g) {  // directions pulling from slab lz + g (c_z = -g)
+        S *cL[3], *cC[3], *cR[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          cL[k] = colpz(x0 - 1, ly + k - 1, lz + g);
+          cC[k] = colpz(x0, ly + k - 1, lz + g);
+          cR[k] = colpz(x0 + 2, ly + k - 1, lz + g);
+        }
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+          if (-dcz(i) != g) continue;
+          const int k = 1 - dcy(i);
+          const int off = (26 - i) * C3;
+          if (dcx(i) == 0) d[i] = PairIO<S>::ld(cC[k] + off);
+          else if (dcx(i) > 0) d[i] = F2::pack(Store<S>::ld(cL[k], off), Store<S>::ld(cC[k], off));
+          else d[i] = F2::pack(Store<S>::ld(cC[k], off + 1), Store<S>::ld(cR[k], off));
+        }
+      }
     }
     collide_pair<S>(d, a, rates);
     asm volatile("" ::: "memory");  // keep the pointer rebuild after the collision
@@ -284,9 +299,31 @@ __global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_p2
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < 27; ++i) {
-        if (m0) Store<S>::st(f, gaddr(x0, dcx(i), dcy(i), lz, dcz(i), i), d[i].lo());
-        if (m1) Store<S>::st(f, gaddr(x0 + 1, dcx(i), dcy(i), lz, dcz(i), i), d[i].hi());
+      for (int g = -1; g <= 1; ++g) {  // directions pushing into slab lz + g (c_z = g)
+        S *cL[3], *cC[3], *cR[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          cL[k] = colpz(x0 - 1, ly + k - 1, lz + g);
+          cC[k] = colpz(x0, ly + k - 1, lz + g);
+          cR[k] = colpz(x0 + 2, ly + k - 1, lz + g);
+        }
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+          if (dcz(i) != g) continue;
+          const int k = 1 + dcy(i);
+          const int off = i * C3;
+          if (dcx(i) == 0) {
+            if (m0 && m1) PairIO<S>::st(cC[k] + off, d[i]);
+            else if (m0) Store<S>::st(cC[k], off, d[i].lo());
+            else Store<S>::st(cC[k], off + 1, d[i].hi());
+          } else if (dcx(i) > 0) {
+            if (m0) Store<S>::st(cC[k], off + 1, d[i].lo());
+            if (m1) Store<S>::st(cR[k], off, d[i].hi());
+          } else {
+            if (m0) Store<S>::st(cL[k], off, d[i].lo());
+            if (m1) Store<S>::st(cC[k], off, d[i].hi());
+          }
+        }
       }
     }
   }
@@ -607,9 +644,10 @@ __global__ void __launch_bounds__(256, 2) k_collide_even_tma(CollideArgs a) {
 // x - c) lies in one of 9 columns (dx, dy) of this block or of its x/y
 // neighbours, at slab z + cz; with a pointer to each of those 9 columns,
 // advanced by one slab per iteration, every pull and push is a single
-// memory instruction with a constant offset (plane and dz).  The two z-face
-// slabs, where 9 directions reach into the z neighbours, take the general
-// address path (the branch is uniform across the CTA).
+// memory instruction with a constant offset (plane and dz).  On the two
+// z-face slabs, where 9 directions reach into the z neighbours, the pointers
+// are built per c_z group for the slab that group reaches (the branch is
+// uniform across the CTA).
 template <int B, typename IDX, typename S>
 __device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int blk, IDX* s_base, IDX* s_col,
                                                int z0 = 0, int z1 = B) {
@@ -647,6 +685,16 @@ __device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int b
       }
     }
   };
+  // the 9 column pointers at slab zs in [-1, B]: of this block's (x, y)
+  // neighbourhood or of its z neighbour's (the z-face slabs, per c_z group)
+  auto zcols = [&](S** col, int zs) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int nx = lx + (k % 3 - 1), ny = ly + (k / 3 - 1);
+      const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(zs);
+      col[k] = f + s_base[bd] + (IDX)(((zs & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1)));
+    }
+  };
   const int mo = a.maskoff[blk];
   const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
   const Rates rates{a.omega1, a.omega2, a.galilean};
@@ -663,11 +711,12 @@ __device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int b
           d[i] = Store<S>::ld(col[(1 - dcx(i)) + 3 * (1 - dcy(i))], (26 - i) * C3 - dcz(i) * S2);
       } else {
 #pragma unroll
-        for (int i = 0; i < 27; ++i) {
-          const int nx = lx - dcx(i), ny = ly - dcy(i), nz = lz - dcz(i);
-          const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
-          const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
-          d[i] = Store<S>::ld(f, s_base[bd] + (IDX)((26 - i) * C3 + nc));
+        for (int g = -1; g <= 1; ++g) {  // directions pulling from slab lz + g (c_z = -g)
+          S* col[9];
+          zcols(col, lz + g);
+#pragma unroll
+          for (int i = 0; i < 27; ++i)
+            if (-dcz(i) == g) d[i] = Store<S>::ld(col[(1 - dcx(i)) + 3 * (1 - dcy(i))], (26 - i) * C3);
         }
       }
       cumulant_collide_s<Store<S>::scaled>(d, rates, a.inv_scale, a.scale, &a.ref);
@@ -680,11 +729,12 @@ __device__ __forceinline__ void odd_cols_block(const CollideArgs& a, const int b
           Store<S>::st(col[(1 + dcx(i)) + 3 * (1 + dcy(i))], i * C3 + dcz(i) * S2, d[i]);
       } else {
 #pragma unroll
-        for (int i = 0; i < 27; ++i) {
-          const int nx = lx + dcx(i), ny = ly + dcy(i), nz = lz + dcz(i);
-          const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
-          const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
-          Store<S>::st(f, s_base[bd] + (IDX)(i * C3 + nc), d[i]);
+        for (int g = -1; g <= 1; ++g) {  // directions pushing into slab lz + g (c_z = g)
+          S* col[9];
+          zcols(col, lz + g);
+#pragma unroll
+          for (int i = 0; i < 27; ++i)
+            if (dcz(i) == g) Store<S>::st(col[(1 + dcx(i)) + 3 * (1 + dcy(i))], i * C3, d[i]);
         }
       }
     }
