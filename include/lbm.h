@@ -392,6 +392,14 @@ void lbm_batch_destroy(lbm_batch* b);
    code; results are identical.  Toggling recaptures the graphs. */
 int lbm_set_wide_offsets(lbm_domain* d, int on);
 
+/* Run the level-0 face kernel and the wall kernels as parallel branches of
+   the step (side streams; parallel graph branches) wherever a host check at
+   lbm_set_geometry found that no slot they write is read or written by the
+   kernels they run beside, and no slot they read is written by them
+   (default on).  Results are identical either way.  Toggling recaptures the
+   graphs. */
+int lbm_set_overlap(lbm_domain* d, int on);
+
 /* Every `every` coarse steps lbm_step checks for NaN/Inf and densities
    outside [0.5, 2] (synchronising); 0 disables (default). */
 int lbm_set_watchdog(lbm_domain* d, int every);

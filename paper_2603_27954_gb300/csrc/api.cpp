@@ -82,6 +82,11 @@ struct lbm_domain {
   char* base = nullptr;
   size_t need = 0;
   size_t off_partials = 0, off_accum = 0, off_mpart = 0, off_wdone = 0;
+  // parallel branches of the step: [0] the level-0 faces, [1] the walls
+  bool overlap = true;
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
+  bool pend[2] = {false, false};
   size_t off_linkf = 0, off_segb = 0, off_segacc = 0;  // per-branch forces (finest level)
   int n_seg = 0;
   bool branch_forces = false;
@@ -246,15 +251,66 @@ CollideArgs collide_args(lbm_domain* dm, int l) {
                      level_zshift(dm, v, 0), level_zshift(dm, v, 1), ref_shift(dm, v)};
 }
 
+// Branches of the step on side streams: fork from the domain's stream, run,
+// and join back before the next collide (walls) or at the end of the coarse
+// step (faces, walls).  Inside a graph capture they become parallel branches.
+int side_streams(lbm_domain* d) {
+  if (d->side[0]) return LBM_OK;
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaStreamCreateWithFlags(&d->side[k], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&d->ev_fork[k], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&d->ev_join[k], cudaEventDisableTiming));
+  }
+  return LBM_OK;
+}
+int join_branch(lbm_domain* d, int k) {
+  if (!d->pend[k]) return LBM_OK;
+  d->pend[k] = false;
+  CK(cudaStreamWaitEvent(d->stream, d->ev_join[k], 0));
+  return LBM_OK;
+}
+// the stream branch k's kernels go to (forked from the domain's stream)
+int fork_branch(lbm_domain* d, int k, cudaStream_t* s) {
+  int rc = side_streams(d);
+  if (!rc) rc = join_branch(d, k);
+  if (rc) return rc;
+  CK(cudaEventRecord(d->ev_fork[k], d->stream));
+  CK(cudaStreamWaitEvent(d->side[k], d->ev_fork[k], 0));
+  *s = d->side[k];
+  return LBM_OK;
+}
+int close_branch(lbm_domain* d, int k) {
+  CK(cudaEventRecord(d->ev_join[k], d->side[k]));
+  d->pend[k] = true;
+  return LBM_OK;
+}
+void destroy_side_streams(lbm_domain* d) {
+  for (int k = 0; k < 2; ++k) {
+    if (d->side[k]) {
+      cudaStreamSynchronize(d->side[k]);
+      cudaStreamDestroy(d->side[k]);
+    }
+    if (d->ev_fork[k]) cudaEventDestroy(d->ev_fork[k]);
+    if (d->ev_join[k]) cudaEventDestroy(d->ev_join[k]);
+    d->side[k] = nullptr;
+    d->ev_fork[k] = d->ev_join[k] = nullptr;
+  }
+}
+
 // level l after its collide-stream sweep: faces (level 0), bounce-back and
-// momentum exchange, per-branch and total force reductions (finest level)
-int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s) {
+// momentum exchange, per-branch and total force reductions (finest level).
+// With `branches` the faces and the walls run on side streams where the host
+// check found them independent of what follows (results are identical).
+int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s, bool branches) {
   Mesh& m = dm->mesh;
   Level& v = m.lv[l];
   void* f = dm->base + v.off_f;
   const int half = v.esize == 2;
   int rc;
+  branches = branches && dm->overlap && !dm->timing && s == dm->stream;
   if (l == 0 && !v.face[parity].empty()) {
+    cudaStream_t fs = s;
+    if (branches && m.ovl_faces && (rc = fork_branch(dm, 0, &fs))) return rc;
     Timed t(dm, KC_FACES, (long long)v.face[parity].size());
     float feq[27];
     for (int i = 0; i < 27; ++i) feq[i] = (float)((dm->feq_in[i] - dm->ref[i]) * v.scale);
@@ -266,11 +322,14 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s) {
       tb.tick = dm->dev<long long>(dm->off_tick);
     }
     if ((rc = launch_faces(f, half, dm->base + v.off_face[parity], v.narrow, (int)v.face[parity].size(), feq, tb,
-                           s)))
+                           fs)))
       return rc;
+    if (fs != s && (rc = close_branch(dm, 0))) return rc;
   }
   if (!v.wall[parity].empty()) {
     Timed t(dm, KC_WALLS, (long long)v.wall[parity].size());
+    const cudaStream_t s_main = s;
+    if (branches && v.ovl_walls && (rc = fork_branch(dm, 1, &s))) return rc;
     int n = (int)v.wall[parity].size();
     const bool per_branch = dm->branch_forces && l == m.L - 1;
     // the finest level's walls reduce the force of the step in the same launch
@@ -283,6 +342,7 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s) {
     if (per_branch && (rc = launch_segments(dm->dev<double>(dm->off_linkf), dm->dev<int>(dm->off_segb), dm->n_seg,
                                             dm->dev<double>(dm->off_segacc), s)))
       return rc;
+    if (s != s_main && (rc = close_branch(dm, 1))) return rc;
   }
   return LBM_OK;
 }
@@ -327,6 +387,7 @@ int friction_into(lbm_domain* dm, int odd, double* acc, cudaStream_t s) {
 // after the last kernel of a coarse step of parity p
 int end_coarse_step(lbm_domain* dm, int parity, cudaStream_t s) {
   int rc;
+  if ((rc = join_branch(dm, 0)) || (rc = join_branch(dm, 1))) return rc;
   if (dm->d.i_u > 0 && (rc = launch_tick(dm->dev<long long>(dm->off_tick), s))) return rc;
   if (dm->friction_mean) {
     // the finest level's incoming values: parity 0 on refined domains, else the next level-0 parity
@@ -341,11 +402,12 @@ int advance(lbm_domain* dm, int l, int parity) {
   Mesh& m = dm->mesh;
   Level& v = m.lv[l];
   int rc;
+  if ((rc = join_branch(dm, 1))) return rc;  // walls before the next collide of any level
   {
     Timed t(dm, parity ? KC_COLLIDE_ODD : KC_COLLIDE, v.n_fluid);
     if ((rc = launch_collide(collide_args(dm, l), v.B, parity, dm->stream))) return rc;
   }
-  if ((rc = post_collide(dm, l, parity, dm->stream))) return rc;
+  if ((rc = post_collide(dm, l, parity, dm->stream, true))) return rc;
   if (l + 1 < m.L) {
     if ((rc = advance(dm, l + 1, 0))) return rc;
     if ((rc = iface_explode(dm, l, parity, dm->stream))) return rc;
@@ -1182,6 +1244,13 @@ int lbm_friction_samples(const lbm_domain* d, double* rows, int n, int* count) {
   return LBM_OK;
 }
 
+int lbm_set_overlap(lbm_domain* d, int on) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (d->overlap != (on != 0)) free_graphs(d);
+  d->overlap = on != 0;
+  return LBM_OK;
+}
+
 int lbm_set_wide_offsets(lbm_domain* d, int on) {
   if (!d) return fail(LBM_EINVAL, "null argument");
   const bool change = d->wide_offsets != (on != 0);
@@ -1317,6 +1386,7 @@ int lbm_load(lbm_domain* d, const char* path) {
 void lbm_destroy(lbm_domain* d) {
   if (!d) return;
   free_graphs(d);
+  destroy_side_streams(d);
   unpin_tables(d);
   for (auto e : d->pool) cudaEventDestroy(e);
   delete d;
@@ -1499,7 +1569,7 @@ int batch_advance(lbm_batch* b, int l, int parity) {
                                 batch_zshift(b, l, parity), b->stream);
   if (rc) return fail(rc, cuda_error_string());
   if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) {
-         return l < d->mesh.L ? post_collide(d, l, parity, s) : LBM_OK;
+         return l < d->mesh.L ? post_collide(d, l, parity, s, false) : LBM_OK;
        })))
     return rc;
   if (l + 1 < b->L) {

@@ -173,6 +173,9 @@ struct Level {
   std::vector<InflowEntry> infl;
   std::vector<CoalesceEntry> coal;
   double wall_rest[3] = {0, 0, 0};  // sum over the cut links of c_i 2 w_i
+  // the walls may run beside the next interface transfer of the coarser level
+  // (no slot one writes is read or written by the other; checked on the host)
+  bool ovl_walls = false;
   // 32-bit forms (filled when narrow_ok) and the form on the device
   bool narrow_ok = false, narrow = false;
   std::vector<WallEntryN> wall_n[2];
@@ -198,6 +201,9 @@ struct Level {
 };
 
 struct Mesh {
+  // the level-0 faces may run beside everything up to the end of the coarse
+  // step (no slot they touch is touched by the level-0 walls or interface)
+  bool ovl_faces = false;
   bool turbulent = false;  // level-0 inflow from random Fourier modes (one tick launch per coarse step)
   bool friction = false;   // wall-shear sums at the end of every coarse step (two launches)
   int L = 1, B = 16;

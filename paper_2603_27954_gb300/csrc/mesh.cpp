@@ -765,6 +765,87 @@ static void order_tables(Mesh& m) {
   }
 }
 
+// Which boundary kernels may run beside others (as parallel branches of the
+// step): a kernel may overlap a sequence of others when no slot it writes is
+// read or written by them and no slot it reads is written by them.  Slots are
+// keyed (element offset, level); the sets are sorted and probed in parallel.
+namespace {
+using KeySet = std::vector<long long>;
+long long slot_key(int l, long long off) { return off * 8 + l; }
+void finish(KeySet& k) {
+  parallel_sort(k);
+  k.erase(std::unique(k.begin(), k.end()), k.end());
+}
+bool disjoint(const KeySet& a, const KeySet& b) {
+  const KeySet& small = a.size() < b.size() ? a : b;
+  const KeySet& large = a.size() < b.size() ? b : a;
+  if (small.empty()) return true;
+  std::atomic<bool> hit{false};
+  const long long n = (long long)small.size(), chunk = 1 << 15;
+  parallel_for((n + chunk - 1) / chunk, [&](long long c) {
+    for (long long i = c * chunk; i < std::min(n, (c + 1) * chunk) && !hit.load(std::memory_order_relaxed); ++i)
+      if (std::binary_search(large.begin(), large.end(), small[(size_t)i])) hit.store(true);
+  });
+  return !hit.load();
+}
+}  // namespace
+
+static void overlap_checks(Mesh& m) {
+  const int L = m.L;
+  std::vector<KeySet> iw(L), ir(L), ww(L), wr(L);
+  for (int l = 0; l < L; ++l) {
+    const Level& v = m.lv[l];
+    for (int p = 0; p < 2; ++p)
+      for (const WallEntry& w : v.wall[p]) {
+        ww[l].push_back(slot_key(l, w.dst));
+        wr[l].push_back(slot_key(l, w.a));
+        if (w.b >= 0) wr[l].push_back(slot_key(l, w.b));
+        wr[l].push_back(slot_key(l, w.c));
+      }
+    finish(ww[l]);
+    finish(wr[l]);
+    if (l + 1 == L) continue;
+    const int fl = l + 1;  // interface of coarse level l with fine level l + 1
+    for (const ExplodeEntry& e : v.expl) {
+      iw[l].push_back(slot_key(fl, e.dst));
+      ir[l].push_back(slot_key(l, e.src[0]));
+      ir[l].push_back(slot_key(l, e.src[1]));
+    }
+    for (const SaveEntry& e : v.save) ir[l].push_back(slot_key(fl, e.src));
+    for (const InflowEntry& e : v.infl) {
+      iw[l].push_back(slot_key(fl, e.dst));
+      if (e.r < 0) {
+        ir[l].push_back(slot_key(l, e.csrc[0]));
+        ir[l].push_back(slot_key(l, e.csrc[1]));
+      }
+    }
+    for (const CoalesceEntry& e : v.coal) {
+      iw[l].push_back(slot_key(l, e.dst[0]));
+      iw[l].push_back(slot_key(l, e.dst[1]));
+      for (int k = 0; k < e.nfine; ++k)
+        if (e.fsrc[k] >= 0) ir[l].push_back(slot_key(fl, e.fsrc[k]));
+    }
+    finish(iw[l]);
+    finish(ir[l]);
+  }
+  for (int l = 0; l < L; ++l) {
+    Level& v = m.lv[l];
+    v.ovl_walls = l >= 1 && !ww[l].empty() && disjoint(ww[l], iw[l - 1]) && disjoint(ww[l], ir[l - 1]) &&
+                  disjoint(wr[l], iw[l - 1]);
+  }
+  const Level& v0 = m.lv[0];
+  KeySet fw, fr;
+  for (int p = 0; p < 2; ++p)
+    for (const FaceEntry& e : v0.face[p]) {
+      fw.push_back(slot_key(0, e.dst));
+      if (e.src >= 0) fr.push_back(slot_key(0, e.src));
+    }
+  finish(fw);
+  finish(fr);
+  m.ovl_faces = !fw.empty() && disjoint(fw, iw[0]) && disjoint(fw, ir[0]) && disjoint(fw, ww[0]) &&
+                disjoint(fw, wr[0]) && disjoint(fr, iw[0]) && disjoint(fr, ww[0]);
+}
+
 int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vector<Prim>& prims, Mesh* out) {
   Mesh& m = *out;
   m.L = d.levels;
@@ -869,6 +950,7 @@ int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vecto
     if (rc) return rc;
   }
   order_tables(m);
+  overlap_checks(m);
   return LBM_OK;
 }
 

@@ -90,6 +90,7 @@ def _load():
         "lbm_branch_drag_estimate": ([dp, i, dp, C.c_double, dp, dp], i),
         "lbm_set_branch_forces": ([vp, i], i),
         "lbm_set_wide_offsets": ([vp, i], i),
+        "lbm_set_overlap": ([vp, i], i),
         "lbm_set_inflow_turbulence": ([vp, i, C.c_double], i),
         "lbm_friction": ([vp, dp, dp, i, dp], i),
         "lbm_set_friction_mean": ([vp, i], i),
@@ -356,6 +357,10 @@ def lbm_autotune(h, steps=3):
 
 def lbm_set_wide_offsets(h, on):
     return _ck(_lib.lbm_set_wide_offsets(h, int(bool(on))), "lbm_set_wide_offsets")
+
+
+def lbm_set_overlap(h, on):
+    return _ck(_lib.lbm_set_overlap(h, int(bool(on))), "lbm_set_overlap")
 
 
 def lbm_get_branch_forces(h, n_branches):

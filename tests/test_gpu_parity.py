@@ -298,3 +298,23 @@ def test_fp32_pair_kernels_match_oracle(L, stream, case, odd, even):
         compare_pops(runs[0][0][lv], sim.f(lv), 2e-6)
         np.testing.assert_array_equal(runs[0][0][lv], runs[1][0][lv])
     np.testing.assert_allclose(runs[0][1], sim.force()[0], rtol=1e-4, atol=1e-7)
+
+
+@pytest.mark.parametrize("case", ["tiny", "amr2_small", "amr3_small"])
+def test_parallel_branches_equal_serial_step(L, stream, case):
+    """Faces and walls as parallel branches of the step (where the host check
+    allows) give the serial step's populations and forces bit for bit, with
+    and without graphs."""
+    levels = W.CASES[case]["levels"]
+    runs = []
+    for overlap, graphs in ((False, True), (True, True), (True, False)):
+        dom = gpu_case(L, stream, case)
+        dom.set_overlap(overlap)
+        dom.use_graphs(graphs)
+        dom.step(5)
+        runs.append(([dom.get_populations(lv) for lv in range(levels)], dom.drag()[1]))
+        dom.close()
+    for got in runs[1:]:
+        for a, b in zip(runs[0][0], got[0]):
+            np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(runs[0][1], got[1])
