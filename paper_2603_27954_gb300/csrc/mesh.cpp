@@ -790,60 +790,152 @@ bool disjoint(const KeySet& a, const KeySet& b) {
 }
 }  // namespace
 
-static void overlap_checks(Mesh& m) {
+// fill `out` with f(entry k, slot j) for the n entries of `tab`, `per` slots
+// each (negative values skipped), in parallel, then sort and deduplicate
+template <class T, class F>
+void key_set(const std::vector<T>& tab, int per, F&& f, KeySet* out) {
+  const size_t base = out->size();
+  out->resize(base + tab.size() * (size_t)per, -1);
+  parallel_for((long long)tab.size(), [&](long long k) {
+    for (int j = 0; j < per; ++j) (*out)[base + (size_t)k * per + j] = f(tab[(size_t)k], j);
+  }, 4096);
+}
+void finish_keys(KeySet& k) {
+  k.erase(std::remove(k.begin(), k.end(), -1LL), k.end());
+  finish(k);
+}
+
+// the exact test at slot level, for the pairs whose block sets met
+static void slot_checks(Mesh& m, std::vector<char>* walls_ok, bool* faces_ok) {
   const int L = m.L;
   std::vector<KeySet> iw(L), ir(L), ww(L), wr(L);
   for (int l = 0; l < L; ++l) {
     const Level& v = m.lv[l];
+    for (int p = 0; p < 2; ++p) {
+      key_set(v.wall[p], 1, [&](const WallEntry& w, int) { return slot_key(l, w.dst); }, &ww[l]);
+      key_set(v.wall[p], 3, [&](const WallEntry& w, int j) {
+        const long long o = j == 0 ? w.a : (j == 1 ? w.b : w.c);
+        return o >= 0 ? slot_key(l, o) : -1LL;
+      }, &wr[l]);
+    }
+    finish_keys(ww[l]);
+    finish_keys(wr[l]);
+  }
+  const Level& v0 = m.lv[0];
+  const bool faces = !v0.face[0].empty();
+  for (int l = 0; l + 1 < L; ++l) {
+    if (!((l == 0 && faces) || !ww[l + 1].empty())) continue;
+    const Level& v = m.lv[l];
+    const int fl = l + 1;
+    key_set(v.expl, 1, [&](const ExplodeEntry& e, int) { return slot_key(fl, e.dst); }, &iw[l]);
+    key_set(v.infl, 1, [&](const InflowEntry& e, int) { return slot_key(fl, e.dst); }, &iw[l]);
+    key_set(v.coal, 2, [&](const CoalesceEntry& e, int j) { return slot_key(l, e.dst[j]); }, &iw[l]);
+    key_set(v.expl, 2, [&](const ExplodeEntry& e, int j) { return slot_key(l, e.src[j]); }, &ir[l]);
+    key_set(v.save, 1, [&](const SaveEntry& e, int) { return slot_key(fl, e.src); }, &ir[l]);
+    key_set(v.infl, 2, [&](const InflowEntry& e, int j) { return e.r < 0 ? slot_key(l, e.csrc[j]) : -1LL; },
+            &ir[l]);
+    key_set(v.coal, 8, [&](const CoalesceEntry& e, int j) {
+      return j < e.nfine && e.fsrc[j] >= 0 ? slot_key(fl, e.fsrc[j]) : -1LL;
+    }, &ir[l]);
+    finish_keys(iw[l]);
+    finish_keys(ir[l]);
+  }
+  for (int l = 1; l < L; ++l)
+    if (!(*walls_ok)[l])
+      (*walls_ok)[l] = !ww[l].empty() && disjoint(ww[l], iw[l - 1]) && disjoint(ww[l], ir[l - 1]) &&
+                       disjoint(wr[l], iw[l - 1]);
+  if (faces && !*faces_ok) {
+    KeySet fw, fr;
+    for (int p = 0; p < 2; ++p) {
+      key_set(v0.face[p], 1, [&](const FaceEntry& e, int) { return slot_key(0, e.dst); }, &fw);
+      key_set(v0.face[p], 1, [&](const FaceEntry& e, int) { return e.src >= 0 ? slot_key(0, e.src) : -1LL; },
+              &fr);
+    }
+    finish_keys(fw);
+    finish_keys(fr);
+    *faces_ok = disjoint(fw, iw[0]) && disjoint(fw, ir[0]) && disjoint(fw, ww[0]) && disjoint(fw, wr[0]) &&
+                disjoint(fr, iw[0]) && disjoint(fr, ww[0]);
+  }
+}
+
+// Storage blocks a set of slots touches, per level (a slot's block is its
+// element offset over 27 B^3): disjoint block sets prove disjoint slot sets
+// cheaply, the usual case (tree links deep inside the finest level, faces at
+// the domain boundary, interface tables at the refinement boxes).
+struct BlockMarks {
+  std::vector<std::vector<char>> on;
+  explicit BlockMarks(const Mesh& m) : on(m.L) {
+    for (int l = 0; l < m.L; ++l) on[l].assign((size_t)std::max(1, m.lv[l].n_storage), 0);
+  }
+  void mark(const Mesh& m, int l, long long off) {
+    if (off >= 0) on[l][(size_t)(off / (27LL * m.lv[l].cells_per_block()))] = 1;
+  }
+};
+bool blocks_disjoint(const BlockMarks& a, const BlockMarks& b) {
+  for (size_t l = 0; l < a.on.size(); ++l)
+    for (size_t k = 0; k < a.on[l].size(); ++k)
+      if (a.on[l][k] && b.on[l][k]) return false;
+  return true;
+}
+
+static void overlap_checks(Mesh& m) {
+  const int L = m.L;
+  // block-level pass
+  std::vector<BlockMarks> ww(L, BlockMarks(m)), wr(L, BlockMarks(m)), iwr(L, BlockMarks(m)), iw(L, BlockMarks(m));
+  for (int l = 0; l < L; ++l) {
+    const Level& v = m.lv[l];
     for (int p = 0; p < 2; ++p)
       for (const WallEntry& w : v.wall[p]) {
-        ww[l].push_back(slot_key(l, w.dst));
-        wr[l].push_back(slot_key(l, w.a));
-        if (w.b >= 0) wr[l].push_back(slot_key(l, w.b));
-        wr[l].push_back(slot_key(l, w.c));
+        ww[l].mark(m, l, w.dst);
+        wr[l].mark(m, l, w.a);
+        wr[l].mark(m, l, w.b);
+        wr[l].mark(m, l, w.c);
       }
-    finish(ww[l]);
-    finish(wr[l]);
     if (l + 1 == L) continue;
-    const int fl = l + 1;  // interface of coarse level l with fine level l + 1
+    const int fl = l + 1;
+    // iw: slots the interface writes; iwr: slots it reads or writes
     for (const ExplodeEntry& e : v.expl) {
-      iw[l].push_back(slot_key(fl, e.dst));
-      ir[l].push_back(slot_key(l, e.src[0]));
-      ir[l].push_back(slot_key(l, e.src[1]));
+      iw[l].mark(m, fl, e.dst);
+      iwr[l].mark(m, fl, e.dst);
+      iwr[l].mark(m, l, e.src[0]);
+      iwr[l].mark(m, l, e.src[1]);
     }
-    for (const SaveEntry& e : v.save) ir[l].push_back(slot_key(fl, e.src));
+    for (const SaveEntry& e : v.save) iwr[l].mark(m, fl, e.src);
     for (const InflowEntry& e : v.infl) {
-      iw[l].push_back(slot_key(fl, e.dst));
+      iw[l].mark(m, fl, e.dst);
+      iwr[l].mark(m, fl, e.dst);
       if (e.r < 0) {
-        ir[l].push_back(slot_key(l, e.csrc[0]));
-        ir[l].push_back(slot_key(l, e.csrc[1]));
+        iwr[l].mark(m, l, e.csrc[0]);
+        iwr[l].mark(m, l, e.csrc[1]);
       }
     }
     for (const CoalesceEntry& e : v.coal) {
-      iw[l].push_back(slot_key(l, e.dst[0]));
-      iw[l].push_back(slot_key(l, e.dst[1]));
-      for (int k = 0; k < e.nfine; ++k)
-        if (e.fsrc[k] >= 0) ir[l].push_back(slot_key(fl, e.fsrc[k]));
+      for (int j = 0; j < 2; ++j) {
+        iw[l].mark(m, l, e.dst[j]);
+        iwr[l].mark(m, l, e.dst[j]);
+      }
+      for (int k = 0; k < e.nfine; ++k) iwr[l].mark(m, fl, e.fsrc[k]);
     }
-    finish(iw[l]);
-    finish(ir[l]);
-  }
-  for (int l = 0; l < L; ++l) {
-    Level& v = m.lv[l];
-    v.ovl_walls = l >= 1 && !ww[l].empty() && disjoint(ww[l], iw[l - 1]) && disjoint(ww[l], ir[l - 1]) &&
-                  disjoint(wr[l], iw[l - 1]);
   }
   const Level& v0 = m.lv[0];
-  KeySet fw, fr;
+  BlockMarks fw(m), fr(m);
   for (int p = 0; p < 2; ++p)
     for (const FaceEntry& e : v0.face[p]) {
-      fw.push_back(slot_key(0, e.dst));
-      if (e.src >= 0) fr.push_back(slot_key(0, e.src));
+      fw.mark(m, 0, e.dst);
+      fr.mark(m, 0, e.src);
     }
-  finish(fw);
-  finish(fr);
-  m.ovl_faces = !fw.empty() && disjoint(fw, iw[0]) && disjoint(fw, ir[0]) && disjoint(fw, ww[0]) &&
-                disjoint(fw, wr[0]) && disjoint(fr, iw[0]) && disjoint(fr, ww[0]);
+  std::vector<char> walls_ok(L, 0);
+  for (int l = 1; l < L; ++l)
+    walls_ok[l] = !m.lv[l].wall[0].empty() && blocks_disjoint(ww[l], iwr[l - 1]) && blocks_disjoint(wr[l], iw[l - 1]);
+  const bool faces = !v0.face[0].empty();
+  bool faces_ok = faces && blocks_disjoint(fw, iwr[0]) && blocks_disjoint(fw, ww[0]) && blocks_disjoint(fw, wr[0]) &&
+                  blocks_disjoint(fr, iw[0]) && blocks_disjoint(fr, ww[0]);
+  bool exact = false;
+  for (int l = 1; l < L; ++l) exact |= !walls_ok[l] && !m.lv[l].wall[0].empty();
+  exact |= faces && !faces_ok;
+  if (exact) slot_checks(m, &walls_ok, &faces_ok);
+  for (int l = 0; l < L; ++l) m.lv[l].ovl_walls = walls_ok[l] != 0;
+  m.ovl_faces = faces_ok;
 }
 
 int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vector<Prim>& prims, Mesh* out) {
