@@ -399,6 +399,10 @@ int lbm_set_wide_offsets(lbm_domain* d, int on);
    (default on).  Results are identical either way.  Toggling recaptures the
    graphs. */
 int lbm_set_overlap(lbm_domain* d, int on);
+/* What that check found: *faces = 1 if the level-0 faces may run as a
+   branch; bit l of *walls set if the walls of level l may.  Either pointer
+   may be NULL.  Needs lbm_set_geometry; no device work. */
+int lbm_get_overlap(const lbm_domain* d, int* faces, int* walls);
 
 /* Every `every` coarse steps lbm_step checks for NaN/Inf and densities
    outside [0.5, 2] (synchronising); 0 disables (default). */

@@ -1251,6 +1251,18 @@ int lbm_set_overlap(lbm_domain* d, int on) {
   return LBM_OK;
 }
 
+int lbm_get_overlap(const lbm_domain* d, int* faces, int* walls) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
+  if (faces) *faces = d->mesh.ovl_faces ? 1 : 0;
+  if (walls) {
+    *walls = 0;
+    for (int l = 0; l < d->mesh.L; ++l)
+      if (d->mesh.lv[l].ovl_walls) *walls |= 1 << l;
+  }
+  return LBM_OK;
+}
+
 int lbm_set_wide_offsets(lbm_domain* d, int on) {
   if (!d) return fail(LBM_EINVAL, "null argument");
   const bool change = d->wide_offsets != (on != 0);

@@ -91,6 +91,7 @@ def _load():
         "lbm_set_branch_forces": ([vp, i], i),
         "lbm_set_wide_offsets": ([vp, i], i),
         "lbm_set_overlap": ([vp, i], i),
+        "lbm_get_overlap": ([vp, ip, ip], i),
         "lbm_set_inflow_turbulence": ([vp, i, C.c_double], i),
         "lbm_friction": ([vp, dp, dp, i, dp], i),
         "lbm_set_friction_mean": ([vp, i], i),
@@ -361,6 +362,13 @@ def lbm_set_wide_offsets(h, on):
 
 def lbm_set_overlap(h, on):
     return _ck(_lib.lbm_set_overlap(h, int(bool(on))), "lbm_set_overlap")
+
+
+def lbm_get_overlap(h):
+    """(faces may branch, bit mask of levels whose walls may branch)"""
+    f, w = C.c_int(), C.c_int()
+    _ck(_lib.lbm_get_overlap(h, C.byref(f), C.byref(w)), "lbm_get_overlap")
+    return bool(f.value), w.value
 
 
 def lbm_get_branch_forces(h, n_branches):

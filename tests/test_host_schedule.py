@@ -77,3 +77,29 @@ def test_z_split_defaults_to_automatic():
             s = L.lbm_get_schedule(h)
             assert (s.z_split_even, s.z_split_odd) == (0, 0)
             L.lbm_destroy(h)
+
+
+def test_overlap_check_finds_independent_and_conflicting_kernels():
+    """The host check behind the parallel branches: a cylinder clear of the
+    domain faces leaves the faces free to overlap the walls; one that crosses
+    the slip walls puts cut links next to face entries and keeps them serial;
+    refined trees let the finest walls overlap the interface transfer."""
+    from paper_2603_27954_gb300 import workloads as W
+
+    def single(seg):
+        h = L.lbm_create_domain(L.domain_desc(32, 32, 32, block=16, bc=("inout", "slip", "slip"), u_in=0.05,
+                                              nu_finest=0.02))
+        L.lbm_set_geometry_prims(h, [0], np.array([seg]))
+        r = L.lbm_get_overlap(h)
+        L.lbm_destroy(h)
+        return r
+
+    assert single([16.0, 16.0, 6.0, 16.0, 16.0, 26.0, 6.0, 0.0]) == (True, 0)
+    assert single([16.0, -2.0, 16.0, 16.0, 34.0, 16.0, 6.0, 0.0]) == (False, 0)
+    for case, bits in (("amr2_small", 2), ("amr3_small", 4)):
+        c = W.CASES[case]
+        h = L.lbm_create_domain(L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"],
+                                              u_in=c["u_in"], re_h=c["re_h"]))
+        L.lbm_set_geometry(h, L.tree_desc(**c["tree"]))
+        assert L.lbm_get_overlap(h) == (True, bits)
+        L.lbm_destroy(h)
