@@ -87,6 +87,10 @@ struct lbm_domain {
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
   bool pend[2] = {false, false};
+  // per level with a finer level: its collide and boundary kernels run beside
+  // the finer level's first sub-step (they touch different arrays)
+  std::vector<cudaStream_t> lside;
+  std::vector<cudaEvent_t> lfork, ljoin;
   size_t off_linkf = 0, off_segb = 0, off_segacc = 0;  // per-branch forces (finest level)
   int n_seg = 0;
   bool branch_forces = false;
@@ -284,7 +288,43 @@ int close_branch(lbm_domain* d, int k) {
   d->pend[k] = true;
   return LBM_OK;
 }
+// level l's own work on its side stream, beside the finer levels' first
+// sub-step; joined before the interface transfer that needs both
+int fork_level(lbm_domain* d, int l, cudaStream_t* s) {
+  if ((int)d->lside.size() < d->mesh.L) {
+    const size_t n0 = d->lside.size();
+    d->lside.resize(d->mesh.L, nullptr);
+    d->lfork.resize(d->mesh.L, nullptr);
+    d->ljoin.resize(d->mesh.L, nullptr);
+    for (size_t k = n0; k < d->lside.size(); ++k) {
+      CK(cudaStreamCreateWithFlags(&d->lside[k], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&d->lfork[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&d->ljoin[k], cudaEventDisableTiming));
+    }
+  }
+  CK(cudaEventRecord(d->lfork[l], d->stream));
+  CK(cudaStreamWaitEvent(d->lside[l], d->lfork[l], 0));
+  *s = d->lside[l];
+  return LBM_OK;
+}
+int join_level(lbm_domain* d, int l) {
+  CK(cudaEventRecord(d->ljoin[l], d->lside[l]));
+  CK(cudaStreamWaitEvent(d->stream, d->ljoin[l], 0));
+  return LBM_OK;
+}
+
 void destroy_side_streams(lbm_domain* d) {
+  for (size_t k = 0; k < d->lside.size(); ++k) {
+    if (d->lside[k]) {
+      cudaStreamSynchronize(d->lside[k]);
+      cudaStreamDestroy(d->lside[k]);
+    }
+    if (d->lfork[k]) cudaEventDestroy(d->lfork[k]);
+    if (d->ljoin[k]) cudaEventDestroy(d->ljoin[k]);
+  }
+  d->lside.clear();
+  d->lfork.clear();
+  d->ljoin.clear();
   for (int k = 0; k < 2; ++k) {
     if (d->side[k]) {
       cudaStreamSynchronize(d->side[k]);
@@ -403,13 +443,21 @@ int advance(lbm_domain* dm, int l, int parity) {
   Level& v = m.lv[l];
   int rc;
   if ((rc = join_branch(dm, 1))) return rc;  // walls before the next collide of any level
+  // a level with a finer level runs its collide and boundary kernels beside
+  // the finer levels' first sub-step (disjoint arrays), joined before explode;
+  // not when it has cut links (the wall kernels of all levels share their
+  // force partials)
+  const bool split = l + 1 < m.L && dm->overlap && !dm->timing && v.wall[0].empty();
+  cudaStream_t cs = dm->stream;
+  if (split && (rc = fork_level(dm, l, &cs))) return rc;
   {
     Timed t(dm, parity ? KC_COLLIDE_ODD : KC_COLLIDE, v.n_fluid);
-    if ((rc = launch_collide(collide_args(dm, l), v.B, parity, dm->stream))) return rc;
+    if ((rc = launch_collide(collide_args(dm, l), v.B, parity, cs))) return rc;
   }
-  if ((rc = post_collide(dm, l, parity, dm->stream, true))) return rc;
+  if ((rc = post_collide(dm, l, parity, cs, true))) return rc;
   if (l + 1 < m.L) {
     if ((rc = advance(dm, l + 1, 0))) return rc;
+    if (split && (rc = join_level(dm, l))) return rc;
     if ((rc = iface_explode(dm, l, parity, dm->stream))) return rc;
     if ((rc = advance(dm, l + 1, 1))) return rc;
     if ((rc = iface_inflow(dm, l, parity, dm->stream))) return rc;
