@@ -296,11 +296,6 @@ LBM_DI void cumulant_collide_h_as_pair(float* d, const Rates& r, float inv_s_in,
 #pragma unroll
   for (int i = 0; i < 27; ++i) d[i] = p[i].lo();
 }
-// FP16 storage, two cells (lanes lo and hi of each register)
-LBM_DI void cumulant_collide_h2(F2* d, const Rates& r, float inv_s_in, float s_out, const RefShift* ref) {
-  collide_cell<F2, true>(d, r, inv_s_in, s_out, ref);
-}
-
 // one cell, storage form chosen at compile time
 template <bool SCALED>
 LBM_DI void cumulant_collide_s(float* d, const Rates& r, float inv_s_in, float s_out, const RefShift* ref = nullptr) {
