@@ -17,6 +17,7 @@
 // below is a list of (destination slot, source slots) pairs per parity.
 #include <algorithm>
 #include <atomic>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -867,8 +868,11 @@ struct BlockMarks {
   explicit BlockMarks(const Mesh& m) : on(m.L) {
     for (int l = 0; l < m.L; ++l) on[l].assign((size_t)std::max(1, m.lv[l].n_storage), 0);
   }
+  // block of an element offset: offset / (27 B^3), by a constant divisor
   void mark(const Mesh& m, int l, long long off) {
-    if (off >= 0) on[l][(size_t)(off / (27LL * m.lv[l].cells_per_block()))] = 1;
+    if (off < 0) return;
+    const long long b = m.B == 16 ? off / (27LL * 4096) : (m.B == 8 ? off / (27LL * 512) : off / (27LL * m.B * m.B * m.B));
+    on[l][(size_t)b] = 1;
   }
 };
 bool blocks_disjoint(const BlockMarks& a, const BlockMarks& b) {
@@ -880,50 +884,63 @@ bool blocks_disjoint(const BlockMarks& a, const BlockMarks& b) {
 
 static void overlap_checks(Mesh& m) {
   const int L = m.L;
-  // block-level pass
+  // block-level pass: one task per mark set (each writes only its own)
   std::vector<BlockMarks> ww(L, BlockMarks(m)), wr(L, BlockMarks(m)), iwr(L, BlockMarks(m)), iw(L, BlockMarks(m));
+  const Level& v0 = m.lv[0];
+  BlockMarks fw(m), fr(m);
+  std::vector<std::function<void()>> tasks;
   for (int l = 0; l < L; ++l) {
     const Level& v = m.lv[l];
-    for (int p = 0; p < 2; ++p)
-      for (const WallEntry& w : v.wall[p]) {
-        ww[l].mark(m, l, w.dst);
-        wr[l].mark(m, l, w.a);
-        wr[l].mark(m, l, w.b);
-        wr[l].mark(m, l, w.c);
-      }
+    tasks.push_back([&, l] {
+      for (int p = 0; p < 2; ++p)
+        for (const WallEntry& w : v.wall[p]) ww[l].mark(m, l, w.dst);
+    });
+    tasks.push_back([&, l] {
+      for (int p = 0; p < 2; ++p)
+        for (const WallEntry& w : v.wall[p]) {
+          wr[l].mark(m, l, w.a);
+          wr[l].mark(m, l, w.b);
+          wr[l].mark(m, l, w.c);
+        }
+    });
     if (l + 1 == L) continue;
     const int fl = l + 1;
     // iw: slots the interface writes; iwr: slots it reads or writes
-    for (const ExplodeEntry& e : v.expl) {
-      iw[l].mark(m, fl, e.dst);
-      iwr[l].mark(m, fl, e.dst);
-      iwr[l].mark(m, l, e.src[0]);
-      iwr[l].mark(m, l, e.src[1]);
-    }
-    for (const SaveEntry& e : v.save) iwr[l].mark(m, fl, e.src);
-    for (const InflowEntry& e : v.infl) {
-      iw[l].mark(m, fl, e.dst);
-      iwr[l].mark(m, fl, e.dst);
-      if (e.r < 0) {
-        iwr[l].mark(m, l, e.csrc[0]);
-        iwr[l].mark(m, l, e.csrc[1]);
+    tasks.push_back([&, l, fl] {
+      for (const ExplodeEntry& e : v.expl) iw[l].mark(m, fl, e.dst);
+      for (const InflowEntry& e : v.infl) iw[l].mark(m, fl, e.dst);
+      for (const CoalesceEntry& e : v.coal)
+        for (int j = 0; j < 2; ++j) iw[l].mark(m, l, e.dst[j]);
+    });
+    tasks.push_back([&, l, fl] {
+      for (const ExplodeEntry& e : v.expl) {
+        iwr[l].mark(m, fl, e.dst);
+        iwr[l].mark(m, l, e.src[0]);
+        iwr[l].mark(m, l, e.src[1]);
       }
-    }
-    for (const CoalesceEntry& e : v.coal) {
-      for (int j = 0; j < 2; ++j) {
-        iw[l].mark(m, l, e.dst[j]);
-        iwr[l].mark(m, l, e.dst[j]);
+      for (const SaveEntry& e : v.save) iwr[l].mark(m, fl, e.src);
+      for (const InflowEntry& e : v.infl) {
+        iwr[l].mark(m, fl, e.dst);
+        if (e.r < 0) {
+          iwr[l].mark(m, l, e.csrc[0]);
+          iwr[l].mark(m, l, e.csrc[1]);
+        }
       }
-      for (int k = 0; k < e.nfine; ++k) iwr[l].mark(m, fl, e.fsrc[k]);
-    }
+      for (const CoalesceEntry& e : v.coal) {
+        for (int j = 0; j < 2; ++j) iwr[l].mark(m, l, e.dst[j]);
+        for (int k = 0; k < e.nfine; ++k) iwr[l].mark(m, fl, e.fsrc[k]);
+      }
+    });
   }
-  const Level& v0 = m.lv[0];
-  BlockMarks fw(m), fr(m);
-  for (int p = 0; p < 2; ++p)
-    for (const FaceEntry& e : v0.face[p]) {
-      fw.mark(m, 0, e.dst);
-      fr.mark(m, 0, e.src);
-    }
+  tasks.push_back([&] {
+    for (int p = 0; p < 2; ++p)
+      for (const FaceEntry& e : v0.face[p]) fw.mark(m, 0, e.dst);
+  });
+  tasks.push_back([&] {
+    for (int p = 0; p < 2; ++p)
+      for (const FaceEntry& e : v0.face[p]) fr.mark(m, 0, e.src);
+  });
+  parallel_for((long long)tasks.size(), [&](long long k) { tasks[(size_t)k](); });
   std::vector<char> walls_ok(L, 0);
   for (int l = 1; l < L; ++l)
     walls_ok[l] = !m.lv[l].wall[0].empty() && blocks_disjoint(ww[l], iwr[l - 1]) && blocks_disjoint(wr[l], iw[l - 1]);
