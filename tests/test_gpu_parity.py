@@ -4,8 +4,7 @@ same seeded inputs, element by element.
 Tolerances: populations are stored as FP32 deviations from the rest weights
 (|f - w| ~ 1e-2 for these flows, one FP32 rounding ~ 1e-9 absolute per
 update); after N updates the round-off walk stays below 1e-6 absolute.  The
-drag coefficient and the velocity field use the bounds the method is judged
-on: C_D within 5e-4 relative and velocity within 1e-4 relative L2 of the
+drag coefficient and the velocity field are held to C_D within 5e-4 relative and velocity within 1e-4 relative L2 of the
 FP64 oracle.
 """
 import numpy as np
