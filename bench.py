@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 CASE = "amr2"
-SMALL = "amr2_small"
+QUARTER = "amr2_quarter"  # the same tree case scaled down 4x per axis, for the C_D comparison
 PRECISION_CASE = "amr4"
 BYTES_PER_UPDATE = 2 * 27 * 4  # read and write 27 FP32 populations
 KERNEL_SOURCES = ["paper_2603_27954_gb300/csrc/collide.cuh", "paper_2603_27954_gb300/csrc/cumulant.cuh"]
@@ -259,8 +259,9 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_rate(case, steps):
-    """Oracle MLUPS on `steps` coarse steps of a workload; also its drag."""
+def oracle_case(case):
+    """The oracle's simulation of a workload record, its cell updates per
+    coarse step (level l counted 2^l times) and its geometry info."""
     import oracle as O
     from paper_2603_27954_gb300 import workloads as W
     c = W.CASES[case]
@@ -269,15 +270,29 @@ def oracle_rate(case, steps):
                        azimuth_mode=t["azimuth_mode"], seed=t["seed"])
     sim, info = O.tree_case(*c["n0"], tree, t["trunk_cells"], c["re_h"], u_in=c["u_in"], levels=c["levels"],
                             block=c["block"], bc=c["bc"])
-    updates = 0
-    for l in range(c["levels"]):
-        updates += int((sim.cell_type(l) == 0).sum()) << l
+    updates = sum(int((sim.cell_type(l) == 0).sum()) << l for l in range(c["levels"]))
+    return sim, updates, info, c
+
+
+def oracle_timed(sim, steps, threads):
+    """Wall time of `steps` oracle coarse steps on `threads` host threads."""
+    import oracle as O
+    prev = O.set_threads(threads)
     t0 = time.perf_counter()
     sim.step(steps)
     dt = time.perf_counter() - t0
-    last, _, _ = sim.force()
-    cd = O.drag_coefficient(last[0], c["u_in"], info["A_x"])
-    return updates * steps / dt / 1e6, dt, cd, updates
+    O.set_threads(prev)
+    return dt
+
+
+def oracle_sample(sim, updates, budget_s, threads, max_steps):
+    """Time the oracle on a bounded sample of a workload: one coarse step to
+    size it, then as many more (at least one, at most max_steps) as fit the
+    budget; returns (MLUPS, steps timed, seconds)."""
+    t1 = oracle_timed(sim, 1, threads)
+    n = max(1, min(max_steps, int(budget_s / max(t1, 1e-3))))
+    dt = oracle_timed(sim, n, threads)
+    return updates * n / dt / 1e6, n, dt
 
 
 METRIC = "D3Q27 cumulant LBM MLUPS & % HBM roofline; C_D rel. error vs FP64 oracle"
@@ -296,30 +311,22 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    # each step: a bounded sample of the workload - one coarse step of the same
-    # tree case scaled down by 4 per axis (the oracle needs about two seconds
-    # per coarse step of the full size, far too long for a run of K steps)
-    import oracle as O
+    # the FP64 oracle on the benchmark workload itself (the full two-level tree
+    # case): one untimed coarse step, then full coarse steps, as many of the
+    # requested --steps as fit about a minute of host time (a coarse step of
+    # this workload takes seconds on the host)
     from paper_2603_27954_gb300 import workloads as W
-    c = W.CASES[SMALL]
-    t = c["tree"]
-    tree = O.make_tree(t["n"], t["children"], t["s0"], t["w0"], t["r"], t["dfac"], alpha_deg=t["alpha_deg"],
-                       azimuth_mode=t["azimuth_mode"], seed=t["seed"])
-    sim, info = O.tree_case(*c["n0"], tree, t["trunk_cells"], c["re_h"], u_in=c["u_in"], levels=c["levels"],
-                            block=c["block"], bc=c["bc"])
-    updates = sum(int((sim.cell_type(l) == 0).sum()) << l for l in range(c["levels"]))
-    sim.step(args.warmup)
-    t0 = time.perf_counter()
-    sim.step(args.steps)
-    dt = time.perf_counter() - t0
-    mlups = updates * args.steps / dt / 1e6
+    sim, updates, info, c = oracle_case(CASE)
     cores = os.cpu_count()
-    sample = "%d coarse steps of the two-level tree case scaled down 4x per axis (coarse %dx%dx%d, %d cell updates per step)" % (
-        args.steps, *c["n0"], updates)
+    oracle_timed(sim, min(args.warmup, 1), cores)
+    mlups, n, dt = oracle_sample(sim, updates, 60.0, cores, args.steps)
+    sample = ("%d full coarse steps of the benchmark workload (%d cell updates each, level l counted 2^l times) "
+              "after %d untimed; --steps %d asked, capped at about a minute of host time" % (
+                  n, updates, min(args.warmup, 1), args.steps))
     line = {
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps": n, "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": dt / n * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(W),
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -342,6 +349,8 @@ def main():
     ap.add_argument("--precision-steps", type=int, default=10)
     ap.add_argument("--timing-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cd-steps", type=int, default=300,
+                    help="coarse steps of the scaled-down case for the C_D comparison with the oracle")
     ap.add_argument("--schedule", default=None,
                     help="odd,even,z_even,z_odd: fix the main workload's schedule instead of autotuning it "
                          "(for profiling the kernels a tuned run chose)")
@@ -435,6 +444,7 @@ def main():
     _, _, cd_run = dom.drag()
     _, _, cf_run = dom.friction()
     steps_run = args.warmup + args.steps + args.timing_steps
+    pop_bytes, uploaded = dom.memory_breakdown()
     barrier()
     h0 = time.perf_counter()
     L.lbm_bind_memory(dom.h, dom.buffer.data_ptr(), dom.buffer.numel())
@@ -461,26 +471,40 @@ def main():
     cpu = None
     cd_err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # about 10-20 s of oracle work: time a few steps, then size the sample
-        r0, dt0, _, _ = oracle_rate(SMALL, 2)
-        small_steps = max(4, min(400, int(12.0 / max(dt0 / 2, 1e-3))))
-        o_mlups, o_dt, o_cd, o_upd = oracle_rate(SMALL, small_steps)
-        d2, t2, c2 = workload_desc(L, W, SMALL)
-        sdom = L.Domain(d2, tree=t2, stream=stream)
-        sdom.step(small_steps)
-        _, _, g_cd = sdom.drag()
-        sdom.close()
-        d16, _, _ = workload_desc(L, W, SMALL, L.LBM_FP16_DEV)
-        hdom = L.Domain(d16, tree=t2, stream=stream)
-        hdom.step(small_steps)
-        _, _, h_cd = hdom.drag()
-        hdom.close()
-        cpu = {"value": o_mlups, "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "%d coarse steps (%.1f s) of the two-level tree case scaled down 4x per axis, "
-                         "%d cell updates per step" % (small_steps, o_dt, o_upd)}
-        cd_err = {"case": "two-level tree case scaled down 4x, after %d coarse steps" % small_steps,
-                  "cd_gpu": g_cd, "cd_oracle": o_cd, "rel_err": abs(g_cd - o_cd) / abs(o_cd),
-                  "fp16_cd_gpu": h_cd, "fp16_rel_err": abs(h_cd - o_cd) / abs(o_cd)}
+        # the oracle on bounded samples of the benchmark workload itself: full
+        # coarse steps on all host cores (about 15 s) and one on a single core
+        sim, o_upd, _, _ = oracle_case(CASE)
+        cores = os.cpu_count()
+        o_mlups, o_n, o_dt = oracle_sample(sim, o_upd, 15.0, cores, 50)
+        one_dt = oracle_timed(sim, 1, 1)
+        del sim
+        cpu = {"value": o_mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": "%d full coarse steps (%.1f s) of the benchmark workload, %d cell updates per step" % (
+                   o_n, o_dt, o_upd),
+               "single_core": {"value": o_upd / one_dt / 1e6, "unit": "MLUPS", "cores": 1,
+                               "sample": "1 full coarse step (%.1f s) of the benchmark workload" % one_dt}}
+        # C_D of the GPU path against the oracle on the same tree case scaled
+        # down 4x per axis (the oracle needs seconds per coarse step of the full case)
+        qsim, q_upd, qinfo, qc = oracle_case(QUARTER)
+        q_steps = args.cd_steps
+        qsim.step(q_steps)
+        import oracle as O
+        q_last, _, _ = qsim.force()
+        o_cd = O.drag_coefficient(q_last[0], qc["u_in"], qinfo["A_x"])
+        del qsim
+        out = {}
+        for name, prec in (("fp32", L.LBM_FP32), ("fp16", L.LBM_FP16_DEV)):
+            d2, t2, _ = workload_desc(L, W, QUARTER, prec)
+            sdom = L.Domain(d2, tree=t2, stream=stream)
+            sdom.step(q_steps)
+            _, _, out[name] = sdom.drag()
+            sdom.close()
+        cd_err = {"case": "the benchmark's tree case scaled down 4x per axis (%s: coarse %dx%dx%d, n=%d x %d "
+                          "children, trunk %g finest cells, Re_H=%g, 8^3 blocks), after %d coarse steps" % (
+                              QUARTER, *qc["n0"], qc["tree"]["n"], qc["tree"]["children"], qc["tree"]["trunk_cells"],
+                              qc["re_h"], q_steps),
+                  "cd_gpu": out["fp32"], "cd_oracle": o_cd, "rel_err": abs(out["fp32"] - o_cd) / abs(o_cd),
+                  "fp16_cd_gpu": out["fp16"], "fp16_rel_err": abs(out["fp16"] - o_cd) / abs(o_cd)}
 
     line = {
         "metric": METRIC,
@@ -494,10 +518,12 @@ def main():
                             "replicas": world, "schedule": schedule},
         "roofline": roofline,
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": dom.nbytes / args.e2e_steps,
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": uploaded / args.e2e_steps,
                 "d2h_bytes_per_step": 64, "bind_ms": (hb - h0) * 1e3, "steps_ms": (h1 - hb) * 1e3,
-                "note": "includes binding (table upload and equilibrium initialisation of %.2f GB) once and a "
-                        "synchronous drag read after each of %d steps" % (dom.nbytes / 1e9, args.e2e_steps)},
+                "note": "includes one binding (upload of %.1f MB of tables from pinned host memory, equilibrium "
+                        "initialisation of %.2f GB of populations on the device) and a synchronous read of the "
+                        "drag (64 bytes) after each of %d steps; bytes per step = the upload over those steps" % (
+                            uploaded / 1e6, pop_bytes / 1e9, args.e2e_steps)},
         "precision_form": prec_form,
         "batched_form": batched,
         "gpu_launches": kernels * args.steps,

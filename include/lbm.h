@@ -52,12 +52,18 @@ typedef enum {
   LBM_BC_INFLOW = 3    /* y, z: equilibrium at rho = 1 and the inflow velocity (Sec. 2.3: inflow on all non-outlet faces) */
 } lbm_bc;
 
-/* Population storage.  LBM_FP32: f_i - w_i in FP32.  LBM_FP16_DEV:
+/* Population storage.  LBM_FP64: f_i - w_i in FP64 with FP64 collision and
+   bounce-back arithmetic (FP64 wall fractions q): the method in double
+   precision, as the paper's smallest workload states it; a reference and
+   validation form (GB300's FP64 rate is a small fraction of its FP32 rate,
+   so its one collide kernel per parity is arithmetic-bound; no turbulent
+   inflow, no batches).  LBM_FP32: f_i - w_i in FP32.  LBM_FP16_DEV:
    (f_i - f_i^eq(1, U e_x)) * 2^13 in IEEE binary16, deviations from the
    inflow equilibrium at the inflow speed U (the power-of-two scale is per
-   level).  Collision arithmetic is FP32 in both; the drag and mass reductions
-   FP64.  lbm_get_populations returns f_i - w_i in either form. */
-typedef enum { LBM_FP32 = 1, LBM_FP16_DEV = 2 } lbm_precision;
+   level).  Collision arithmetic is FP32 in both reduced forms; the drag and
+   mass reductions and the interface ledger are FP64 in every form.
+   lbm_get_populations returns f_i in every form. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_DEV = 2 } lbm_precision;
 
 /* Collide-kernel variants (all compute the same result; within the FP16 form
    the packed two-cell kernels and the one-cell ones differ in the last bit of
@@ -141,6 +147,14 @@ int lbm_set_geometry_prims(lbm_domain* d, const int* kind, const double* params,
 /* Bytes of device memory the domain needs (populations, tables, scratch). */
 int lbm_memory_requirements(const lbm_domain* d, size_t* bytes);
 
+/* What the bound buffer holds and what binding copies: *populations the
+   bytes of population storage of all levels (active and ghost blocks),
+   *uploaded the host-to-device bytes one lbm_bind_memory copies (boundary,
+   interface and neighbour tables in the form the device uses, turbulence
+   modes, the step counter; the populations are initialised on the device).
+   Either pointer may be NULL.  Needs the geometry; host only. */
+int lbm_memory_breakdown(const lbm_domain* d, size_t* populations, size_t* uploaded);
+
 /* Bind a caller-owned device buffer of at least the required size (256-byte
    aligned), upload the tables and set every population to the inflow
    equilibrium.  The buffer must stay valid until lbm_destroy. */
@@ -153,8 +167,14 @@ int lbm_init_uniform(lbm_domain* d, double rho, const double u[3]);
    rho[n], u[3n] (x fastest); n must equal the box's cell count. */
 int lbm_init_field(lbm_domain* d, int level, const double* rho, const double* u, size_t n);
 
-/* Advance n coarse steps (2^l steps of level l each), asynchronously.
-   Returns the status of the last watchdog check (lbm_set_watchdog). */
+/* The method's time step (Sec. 2.2: the cumulant LBM on the octree-refined
+   mesh, interpolated bounce-back on the tree and the momentum-exchange
+   force; Sec. 2.3: the inflow, outflow and lateral faces): advance n coarse
+   steps, every level l taking 2^l steps of its own (recursive sub-cycling,
+   acoustic scaling), asynchronously on the domain's stream (one captured
+   CUDA graph per coarse step unless graphs are off or timing is on).
+   LBM_ESTATE before lbm_bind_memory; returns the status of the last
+   watchdog check (lbm_set_watchdog), LBM_EUNSTABLE if it failed. */
 int lbm_step(lbm_domain* d, int n_coarse);
 
 /* Momentum-exchange force on the tree (Sec. 2.2, Wen et al. 2014) in
@@ -180,18 +200,21 @@ int lbm_mass(lbm_domain* d, double* mass, double mom[3]);
    counterpart; this is a service of the library.)  Same result and contract
    as lbm_mass, but the per-block partial sums go to a fixed scratch array
    inside the library image instead of the domain's bound buffer, and the
-   call performs no device allocation of any kind.  It is for callers that
-   may not allocate device memory at the point of the call - code running
-   under an allocator or memory pool that forbids growth, or inside a stream
-   capture where cudaMalloc is illegal - and for callers that want the check
+   call performs no device allocation of any kind (no cudaMalloc, no
+   allocating library routine).  It is for callers that may not allocate
+   device memory at the point of the call - code running under an allocator
+   or memory pool that forbids growth, or a monitor that must not disturb
+   the memory the caller has budgeted - and for callers that want the check
    without touching the domain's own scratch.
    Limits and rules: every level may hold at most 32768 active blocks
    (LBM_EINVAL otherwise); the scratch (about 1.3 MB per GPU that loads the
-   library) is held until the process exits; the first call on each device
-   looks up the scratch address with that device current and should come
-   before any stream capture; all calls share the one scratch array, so calls
-   whose device work overlaps race and must be serialised by the caller.
-   Synchronises the domain's stream. */
+   library) is held until the process exits; the domain's device must be
+   current; the first call on each device looks up the scratch address with
+   that device current (once, race-free across host threads); all calls
+   share the one scratch array, so calls whose device work overlaps race and
+   must be serialised by the caller.  The call copies its totals to host
+   memory and synchronises the domain's stream, so it must not be made while
+   that stream is being captured into a CUDA graph. */
 int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]);
 
 /* Real box [lo, hi) of a level in level-l cells, and cell counts. */

@@ -105,6 +105,8 @@ def _declare(L):
     L.orc_set_turbulence.restype = C.c_int
     L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
     L.orc_splitmix64.restype = C.c_uint64
+    L.orc_set_threads.argtypes = [C.c_int]
+    L.orc_set_threads.restype = C.c_int
 
 
 # ---------------------------------------------------------------- tree (Sec. 2.1)
@@ -365,6 +367,11 @@ class Sim:
         out = np.zeros(nx * ny * nz, np.uint8)
         lib().orc_cell_type(self._h, level, out)
         return out.reshape(nz, ny, nx)
+
+
+def set_threads(n):
+    """Host threads of the oracle's OpenMP loops; returns the previous count."""
+    return lib().orc_set_threads(int(n))
 
 
 def drag_coefficient(fx, u, area):

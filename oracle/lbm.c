@@ -29,6 +29,7 @@
  *    hence conserves mass and momentum (volumetric explode / coalesce).
  */
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 #include "orc.h"
@@ -570,4 +571,10 @@ int orc_branch_forces(const orc_sim* s, double* mean, int n) {
   for (int k = 0; k < s->nprim; ++k)
     for (int a = 0; a < 3; ++a) mean[3 * k + a] = s->nF > 0 ? s->Fseg[3 * k + a] / (double)s->nF : 0.0;
   return s->nprim;
+}
+
+int orc_set_threads(int n) {
+  int prev = omp_get_max_threads();
+  if (n >= 1) omp_set_num_threads(n);
+  return prev;
 }

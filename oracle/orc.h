@@ -104,4 +104,7 @@ void orc_mass(const orc_sim* s, double* mass, double mom[3]);
 int orc_cell_type(const orc_sim* s, int level, unsigned char* out);
 int orc_branch_forces(const orc_sim* s, double* mean, int n);
 
+/* host threads of the OpenMP loops (n >= 1); returns the previous count */
+int orc_set_threads(int n);
+
 #endif

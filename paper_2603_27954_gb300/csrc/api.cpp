@@ -113,7 +113,8 @@ struct lbm_domain {
   double l_int = 0;  // integral length in level-0 cells; 0: the tree height
   size_t off_modes = 0, off_facepos = 0, off_tick = 0;
   int max_wall_parts = 0;
-  float feq_in[27];
+  float feq_in[27];     // inflow equilibrium minus the rest weights, FP32
+  double feq_in_d[27];  // the same in FP64 (FP64 storage form)
   int parity0 = 0;
   long long steps = 0;
   bool use_graphs = true;
@@ -250,7 +251,8 @@ CollideArgs collide_args(lbm_domain* dm, int l) {
   Level& v = dm->mesh.lv[l];
   return CollideArgs{dm->base + v.off_f, (long long)v.f_elems(), dm->dev<int>(v.off_nbr),
                      dm->dev<int>(v.off_maskoff), dm->dev<uint8_t>(v.off_masks), v.n_active, (float)v.omega1,
-                     (float)dm->d.omega2, dm->d.galilean, dm->dev<double>(dm->off_accum) + 7, v.esize == 2, v.scale,
+                     (float)dm->d.omega2, dm->d.galilean, dm->dev<double>(dm->off_accum) + 7, v.esize == 2,
+                     v.esize == 8, v.omega1, dm->d.omega2, v.scale,
                      1.0f / v.scale, dm->wide_offsets ? 1 : 0, dm->odd_variant, dm->even_variant,
                      level_zshift(dm, v, 0), level_zshift(dm, v, 1), ref_shift(dm, v)};
 }
@@ -345,15 +347,16 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s, bool branche
   Mesh& m = dm->mesh;
   Level& v = m.lv[l];
   void* f = dm->base + v.off_f;
-  const int half = v.esize == 2;
+  const int esize = v.esize;
   int rc;
   branches = branches && dm->overlap && !dm->timing && s == dm->stream;
   if (l == 0 && !v.face[parity].empty()) {
     cudaStream_t fs = s;
     if (branches && m.ovl_faces && (rc = fork_branch(dm, 0, &fs))) return rc;
     Timed t(dm, KC_FACES, (long long)v.face[parity].size());
-    float feq[27];
-    for (int i = 0; i < 27; ++i) feq[i] = (float)((dm->feq_in[i] - dm->ref[i]) * v.scale);
+    double feq[27];
+    for (int i = 0; i < 27; ++i)
+      feq[i] = esize == 8 ? dm->feq_in_d[i] : (double)(float)((dm->feq_in[i] - dm->ref[i]) * v.scale);
     TurbArgs tb{nullptr, nullptr, 0, (float)dm->d.u_in, v.scale, nullptr, dm->d.precision == LBM_FP16_DEV};
     if (dm->d.i_u > 0) {
       tb.pos = dm->dev<int>(dm->off_facepos);
@@ -361,7 +364,7 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s, bool branche
       tb.n_modes = dm->n_modes;
       tb.tick = dm->dev<long long>(dm->off_tick);
     }
-    if ((rc = launch_faces(f, half, dm->base + v.off_face[parity], v.narrow, (int)v.face[parity].size(), feq, tb,
+    if ((rc = launch_faces(f, esize, dm->base + v.off_face[parity], v.narrow, (int)v.face[parity].size(), feq, tb,
                            fs)))
       return rc;
     if (fs != s && (rc = close_branch(dm, 0))) return rc;
@@ -374,7 +377,8 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s, bool branche
     const bool per_branch = dm->branch_forces && l == m.L - 1;
     // the finest level's walls reduce the force of the step in the same launch
     const bool finest = l == m.L - 1;
-    if ((rc = launch_walls(f, half, 1.0f / v.scale, dm->ref27, dm->base + v.off_wall[parity], v.narrow, n,
+    if ((rc = launch_walls(f, esize, esize == 8 ? dm->dev<double>(v.off_q64) : nullptr, 1.0f / v.scale, dm->ref27,
+                           dm->base + v.off_wall[parity], v.narrow, n,
                            dm->dev<double>(dm->off_partials), per_branch ? dm->dev<double>(dm->off_linkf) : nullptr,
                            dm->dev<unsigned>(dm->off_wdone), finest ? dm->dev<double>(dm->off_accum) : nullptr,
                            v.wall_rest, s)))
@@ -392,9 +396,9 @@ int iface_explode(lbm_domain* dm, int l, int parity, cudaStream_t s) {
   Level& v = dm->mesh.lv[l];
   Level& F = dm->mesh.lv[l + 1];
   Timed t(dm, KC_IFACE, (long long)v.expl.size());
-  return launch_explode(dm->base + F.off_f, dm->base + v.off_f, v.esize == 2, F.scale / v.scale,
+  return launch_explode(dm->base + F.off_f, dm->base + v.off_f, v.esize, F.scale / v.scale,
                         dm->base + v.off_expl, v.narrow, (int)v.expl.size(), dm->base + v.off_save,
-                        (int)v.save.size(), dm->dev<float>(v.off_saved), parity, s);
+                        (int)v.save.size(), dm->base + v.off_saved, parity, s);
 }
 
 // fine inflow for the next first fine step, and coarse cells from their children
@@ -405,11 +409,11 @@ int iface_inflow(lbm_domain* dm, int l, int parity, cudaStream_t s) {
   void* ff = dm->base + F.off_f;
   void* f = dm->base + v.off_f;
   const float ratio = F.scale / v.scale;
-  float* saved = dm->dev<float>(v.off_saved);
-  int rc = launch_inflow(ff, f, v.esize == 2, ratio, dm->base + v.off_infl, v.narrow, (int)v.infl.size(), saved,
+  void* saved = dm->base + v.off_saved;
+  int rc = launch_inflow(ff, f, v.esize, ratio, dm->base + v.off_infl, v.narrow, (int)v.infl.size(), saved,
                          parity, s);
   if (rc) return rc;
-  return launch_coalesce(f, ff, v.esize == 2, ratio, dm->base + v.off_coal, v.narrow, (int)v.coal.size(), saved,
+  return launch_coalesce(f, ff, v.esize, ratio, dm->base + v.off_coal, v.narrow, (int)v.coal.size(), saved,
                          parity, s);
 }
 
@@ -417,7 +421,7 @@ int iface_inflow(lbm_domain* dm, int l, int parity, cudaStream_t s) {
 int friction_into(lbm_domain* dm, int odd, double* acc, cudaStream_t s) {
   const Level& v = dm->mesh.lv.back();
   if (dm->fsamp.empty()) return LBM_OK;
-  int rc = launch_friction(dm->base + v.off_f, v.esize == 2, 1.0f / v.scale, dm->ref27, v.B, dm->dev<int>(v.off_nbr), odd,
+  int rc = launch_friction(dm->base + v.off_f, v.esize, 1.0f / v.scale, dm->ref27, v.B, dm->dev<int>(v.off_nbr), odd,
                            (float)v.omega1, dm->dev<FrictionSample>(dm->off_fsamp), (int)dm->fsamp.size(),
                            dm->dev<double>(dm->off_fforce), s);
   if (rc) return rc;
@@ -507,7 +511,7 @@ int build(lbm_domain* d) {
     v.omega1 = 1.0 / (3.0 * v.nu + 0.5);
     // FP16: deviations are at most ~0.1, so 2^13 keeps them far from both the
     // FP16 overflow (65504) and its subnormal range (below 6.1e-5 / 2^13)
-    v.esize = d->d.precision == LBM_FP16_DEV ? 2 : 4;
+    v.esize = d->d.precision == LBM_FP16_DEV ? 2 : (d->d.precision == LBM_FP64 ? 8 : 4);
     v.scale = d->d.precision == LBM_FP16_DEV ? 8192.0f : 1.0f;
   }
   narrow_tables(&d->mesh);
@@ -546,7 +550,11 @@ int build(lbm_domain* d) {
     v.off_save = put(v.save.size() * sizeof(SaveEntry));
     v.off_infl = put(v.infl.size() * sizeof(InflowEntry));
     v.off_coal = put(v.coal.size() * sizeof(CoalesceEntry));
-    v.off_saved = put(v.save.size() * sizeof(float));
+    v.off_saved = put(v.save.size() * (v.esize == 8 ? sizeof(double) : sizeof(float)));
+    v.link_q.clear();
+    if (v.esize == 8)
+      for (const Link& k : v.links) v.link_q.push_back(k.q);
+    v.off_q64 = put(v.link_q.size() * sizeof(double));
     d->max_wall_parts = std::max(d->max_wall_parts, walls_partial_count((int)v.wall[0].size()));
     max_blocks = std::max(max_blocks, (size_t)v.n_active);
   }
@@ -576,7 +584,10 @@ int build(lbm_domain* d) {
   d->off_wdone = put(sizeof(unsigned));
   d->need = off;
   double u[3] = {d->d.u_in, 0, 0};
-  for (int i = 0; i < 27; ++i) d->feq_in[i] = (float)(equilibrium(i, 1.0, u) - rest_weight(i));
+  for (int i = 0; i < 27; ++i) {
+    d->feq_in_d[i] = equilibrium(i, 1.0, u) - rest_weight(i);
+    d->feq_in[i] = (float)d->feq_in_d[i];
+  }
   // FP16 storage keeps (f - w - r) s with r the inflow equilibrium's deviation:
   // the free stream is then stored as values near zero
   for (int i = 0; i < 27; ++i) {
@@ -645,12 +656,37 @@ int upload_tables(lbm_domain* d) {
   return LBM_OK;
 }
 
+// host-to-device bytes of one binding: the tables upload() copies (in the
+// form the device uses), the turbulence modes and the step counter; the
+// populations are initialised on the device and not copied
+size_t upload_bytes(const lbm_domain* d) {
+  size_t b = 0;
+  for (const Level& v : d->mesh.lv) {
+    b += v.nbr.size() * sizeof(int) + v.maskoff.size() * sizeof(int) + v.masks.size() +
+         v.link_q.size() * sizeof(double);
+    if (v.narrow_ok && !d->wide_offsets) {
+      for (int p = 0; p < 2; ++p) b += v.wall_n[p].size() * sizeof(WallEntryN) + v.face_n[p].size() * sizeof(FaceEntryN);
+      b += v.expl_n.size() * sizeof(ExplodeEntryN) + v.save_n.size() * sizeof(SaveEntryN) +
+           v.infl_n.size() * sizeof(InflowEntryN) + v.coal_n.size() * sizeof(CoalesceEntryN);
+    } else {
+      for (int p = 0; p < 2; ++p) b += v.wall[p].size() * sizeof(WallEntry) + v.face[p].size() * sizeof(FaceEntry);
+      b += v.expl.size() * sizeof(ExplodeEntry) + v.save.size() * sizeof(SaveEntry) +
+           v.infl.size() * sizeof(InflowEntry) + v.coal.size() * sizeof(CoalesceEntry);
+    }
+  }
+  if (d->n_seg) b += d->mesh.lv.back().seg_begin.size() * sizeof(int);
+  b += d->fsamp.size() * sizeof(FrictionSample) + d->fseg_begin.size() * sizeof(int);
+  if (d->d.i_u > 0) b += d->mesh.lv[0].face_pos.size() * sizeof(int) + (size_t)d->n_modes * kModeCols * sizeof(float);
+  return b + sizeof(long long);
+}
+
 int upload(lbm_domain* d) {
   auto cp = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
     if (!bytes) return cudaSuccess;
     return cudaMemcpyAsync(d->base + off, src, bytes, cudaMemcpyHostToDevice, d->stream);
   };
   for (Level& v : d->mesh.lv) {
+    CK(cp(v.off_q64, v.link_q.data(), v.link_q.size() * sizeof(double)));
     CK(cp(v.off_nbr, v.nbr.data(), v.nbr.size() * sizeof(int)));
     CK(cp(v.off_maskoff, v.maskoff.data(), v.maskoff.size() * sizeof(int)));
     CK(cp(v.off_masks, v.masks.data(), v.masks.size()));
@@ -680,9 +716,9 @@ int reset_force(lbm_domain* d) {
 
 int fill_uniform(lbm_domain* d, double rho, const double u[3]) {
   for (Level& v : d->mesh.lv) {
-    float dev[27];
-    for (int i = 0; i < 27; ++i) dev[i] = (float)((equilibrium(i, rho, u) - rest_weight(i) - d->ref[i]) * v.scale);
-    int rc = launch_fill(d->base + v.off_f, v.esize == 2, v.n_storage, v.B, dev, d->stream);
+    double dev[27];
+    for (int i = 0; i < 27; ++i) dev[i] = (equilibrium(i, rho, u) - rest_weight(i) - d->ref[i]) * v.scale;
+    int rc = launch_fill(d->base + v.off_f, v.esize, v.n_storage, v.B, dev, d->stream);
     if (rc) return fail(rc, cuda_error_string());
   }
   d->parity0 = 0;
@@ -720,7 +756,7 @@ int mass_device(lbm_domain* d, double* mass, double mom[3], double* bad) {
   for (int l = 0; l < d->mesh.L; ++l) {
     Level& v = d->mesh.lv[l];
     if (!v.n_active) continue;
-    int rc = launch_mass(d->base + v.off_f, v.esize == 2, 1.0f / v.scale, d->ref27, d->dev<int>(v.off_nbr),
+    int rc = launch_mass(d->base + v.off_f, v.esize, 1.0f / v.scale, d->ref27, d->dev<int>(v.off_nbr),
                          d->dev<int>(v.off_maskoff), d->dev<uint8_t>(v.off_masks), v.n_active, v.B,
                          level_parity(d, l), d->dev<double>(d->off_mpart), d->stream);
     if (rc) return fail(rc, cuda_error_string());
@@ -764,6 +800,11 @@ int download_level(lbm_domain* d, const Level& v, std::vector<uint8_t>& host) {
 // stored element k decoded and unscaled: f - w - r of the population it holds
 // (r the storage reference, zero for FP32)
 double stored_dev(const Level& v, const std::vector<uint8_t>& host, long long k) {
+  if (v.esize == 8) {
+    double x;
+    std::memcpy(&x, host.data() + 8 * k, 8);
+    return x;
+  }
   if (v.esize == 2) {
     uint16_t h;
     std::memcpy(&h, host.data() + 2 * k, 2);
@@ -775,6 +816,10 @@ double stored_dev(const Level& v, const std::vector<uint8_t>& host, long long k)
 }
 
 void store_dev(const Level& v, std::vector<uint8_t>& host, long long k, double dev) {
+  if (v.esize == 8) {
+    std::memcpy(host.data() + 8 * k, &dev, 8);
+    return;
+  }
   if (v.esize == 2) {
     const uint16_t h = float_to_half_bits((float)(dev * v.scale));
     std::memcpy(host.data() + 2 * k, &h, 2);
@@ -817,8 +862,10 @@ int lbm_create_domain(const lbm_domain_desc* desc, void* cuda_stream, lbm_domain
   if (!(std::fabs(s.u_in) < 0.3)) return fail(LBM_EINVAL, "inflow speed must be below 0.3");
   if (!(s.i_u >= 0.0 && s.i_u <= 0.5)) return fail(LBM_EINVAL, "inflow turbulence intensity must lie in [0, 0.5]");
   if (s.i_u > 0 && s.bc[0] != LBM_BC_INOUT) return fail(LBM_EINVAL, "turbulent inflow needs the in/out x faces");
-  if (s.precision != LBM_FP32 && s.precision != LBM_FP16_DEV)
-    return fail(LBM_EINVAL, "precision must be LBM_FP32 or LBM_FP16_DEV");
+  if (s.precision != LBM_FP64 && s.precision != LBM_FP32 && s.precision != LBM_FP16_DEV)
+    return fail(LBM_EINVAL, "precision must be LBM_FP64, LBM_FP32 or LBM_FP16_DEV");
+  if (s.precision == LBM_FP64 && s.i_u > 0)
+    return fail(LBM_EINVAL, "turbulent inflow needs FP32 or FP16 storage");
   if (!(s.omega2 > 0 && s.omega2 < 2)) return fail(LBM_EINVAL, "omega2 must lie in (0, 2)");
   auto* d = new (std::nothrow) lbm_domain();
   if (!d) return fail(LBM_ENOMEM, "host allocation");
@@ -886,6 +933,18 @@ int lbm_memory_requirements(const lbm_domain* d, size_t* bytes) {
   if (!d || !bytes) return fail(LBM_EINVAL, "null argument");
   if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
   *bytes = d->need;
+  return LBM_OK;
+}
+
+int lbm_memory_breakdown(const lbm_domain* d, size_t* populations, size_t* uploaded) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
+  if (populations) {
+    size_t p = 0;
+    for (const Level& v : d->mesh.lv) p += v.f_elems() * (size_t)v.esize;
+    *populations = p;
+  }
+  if (uploaded) *uploaded = upload_bytes(d);
   return LBM_OK;
 }
 
@@ -1050,7 +1109,7 @@ int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]) {
   for (int l = 0; l < d->mesh.L; ++l) {
     Level& v = d->mesh.lv[l];
     if (!v.n_active) continue;
-    rc = launch_mass_noalloc(d->base + v.off_f, v.esize == 2, 1.0f / v.scale, d->ref27, d->dev<int>(v.off_nbr),
+    rc = launch_mass_noalloc(d->base + v.off_f, v.esize, 1.0f / v.scale, d->ref27, d->dev<int>(v.off_nbr),
                              d->dev<int>(v.off_maskoff), d->dev<uint8_t>(v.off_masks), v.n_active, v.B,
                              level_parity(d, l), scratch, d->stream);
     if (rc) return fail(rc, cuda_error_string());
@@ -1459,6 +1518,8 @@ namespace {
 
 bool variant_ok(const lbm_domain* d, int odd, int even) {
   if (odd < LBM_ODD_COLUMNS || odd > LBM_ODD_PAIRS || even < LBM_EVEN_DIRECT || even > LBM_EVEN_PAIRS) return false;
+  // the FP64 form has one kernel per parity (direct addressing)
+  if (d->d.precision == LBM_FP64) return (odd == LBM_ODD_COLUMNS || odd == LBM_ODD_DIRECT) && even == LBM_EVEN_DIRECT;
   const bool staged_ok = d->d.precision == LBM_FP32 && d->d.block == 16;
   if (odd == LBM_ODD_STAGED && !staged_ok) return false;
   if (even == LBM_EVEN_TMA && !staged_ok) return false;
@@ -1692,6 +1753,7 @@ int lbm_batch_create(lbm_domain* const* domains, int n, void* cuda_stream, lbm_b
     if (!d || !d->base) why = "every domain must have bound memory";
     else if (d->d.block != domains[0]->d.block) why = "all domains must share the block size";
     else if (d->d.precision != domains[0]->d.precision) why = "all domains must share the storage precision";
+    else if (d->d.precision == LBM_FP64) why = "batches take FP32 or FP16 storage";
     else if (d->parity0 != domains[0]->parity0) why = "all domains must be at the same step parity";
     else if (d->timing) why = "per-class timing must be off";
     for (int j = 0; j < k && why.empty(); ++j)

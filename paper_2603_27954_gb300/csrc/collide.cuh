@@ -32,17 +32,28 @@ __device__ __forceinline__ int block_digit(int c) {
 // per-level power-of-two scale.  ld/st move the stored (scaled) value.
 template <typename S>
 struct Store;
+// V is the arithmetic type of the values moved (FP32 for both reduced forms).
 template <>
 struct Store<float> {
+  using V = float;
   static constexpr bool scaled = false;
   static __device__ __forceinline__ float ld(const float* p, long long i) { return p[i]; }
   static __device__ __forceinline__ void st(float* p, long long i, float v) { p[i] = v; }
 };
 template <>
 struct Store<__half> {
+  using V = float;
   static constexpr bool scaled = true;
   static __device__ __forceinline__ float ld(const __half* p, long long i) { return __half2float(p[i]); }
   static __device__ __forceinline__ void st(__half* p, long long i, float v) { p[i] = __float2half_rn(v); }
+};
+// FP64 storage of f - w (the double-precision form): no scale, no reference
+template <>
+struct Store<double> {
+  using V = double;
+  static constexpr bool scaled = false;
+  static __device__ __forceinline__ double ld(const double* p, long long i) { return p[i]; }
+  static __device__ __forceinline__ void st(double* p, long long i, double v) { p[i] = v; }
 };
 
 #ifndef LBM_EVEN_MINB
@@ -334,6 +345,55 @@ __global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_c
   __shared__ IDX s_base[27];
   const ZSeg zg = z_segment(blockIdx.x, ODD ? a.zshift_odd : a.zshift_even, B);
   collide_block<B, ODD, IDX, S>(a, zg.blk, s_base, zg.z0, zg.z1);
+}
+
+// FP64 storage: the even or odd AA step of one block, one thread per (x, y)
+// column walking its z segment, neighbour addressing through the 27-entry
+// block table, the collision in FP64.  The double-precision form reproduces
+// the FP64 method on the GPU (a reference and validation form: GB300's FP64
+// rate is a small fraction of its FP32 rate, so this kernel is
+// arithmetic-bound and is not tuned).
+template <int B, bool ODD, typename IDX>
+__global__ void __launch_bounds__(B * B) k_collide_f64(CollideArgs a) {
+  constexpr int C3 = B * B * B;
+  __shared__ IDX s_base[27];
+  const ZSeg zg = z_segment(blockIdx.x, ODD ? a.zshift_odd : a.zshift_even, B);
+  const int blk = zg.blk;
+  if (threadIdx.x < 27) s_base[threadIdx.x] = (IDX)a.nbr[(size_t)blk * 27 + threadIdx.x] * (IDX)(27 * C3);
+  __syncthreads();
+  const int lx = threadIdx.x % B, ly = threadIdx.x / B;
+  const int mo = a.maskoff[blk];
+  const uint8_t* mask = mo >= 0 ? a.masks + (size_t)mo * C3 : nullptr;
+  const RatesD rates{a.omega1d, a.omega2d, a.galilean};
+  double* __restrict__ f = reinterpret_cast<double*>(a.f);
+  for (int lz = zg.z0; lz < zg.z1; ++lz) {
+    const int cell = (lz * B + ly) * B + lx;
+    if (mask && !mask[cell]) continue;
+    double d[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+      if (!ODD) {
+        d[i] = f[s_base[13] + (IDX)(i * C3 + cell)];
+      } else {  // pull f_i from (x - c_i, ibar)
+        const int nx = lx - dcx(i), ny = ly - dcy(i), nz = lz - dcz(i);
+        const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
+        const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
+        d[i] = f[s_base[bd] + (IDX)((26 - i) * C3 + nc)];
+      }
+    }
+    cumulant_collide_d(d, rates);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+      if (!ODD) {
+        f[s_base[13] + (IDX)((26 - i) * C3 + cell)] = d[i];
+      } else {  // push f*_i to (x + c_i, i)
+        const int nx = lx + dcx(i), ny = ly + dcy(i), nz = lz + dcz(i);
+        const int bd = block_digit<B>(nx) + 3 * block_digit<B>(ny) + 9 * block_digit<B>(nz);
+        const int nc = ((nz & (B - 1)) * B + (ny & (B - 1))) * B + (nx & (B - 1));
+        f[s_base[bd] + (IDX)(i * C3 + nc)] = d[i];
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -1,5 +1,5 @@
 // D3Q27 cumulant collision (Sec. 2.2; Geier et al. 2015) on one cell, in
-// FP32, for the rate set omega1 (shear), omega2 (bulk) and all third- to
+// FP32 (or FP64 for the double-precision storage form), for the rate set omega1 (shear), omega2 (bulk) and all third- to
 // sixth-order cumulants relaxed fully to their zero equilibrium.
 //
 // Populations are carried as deviations d_i = f_i - w_i from the rest
@@ -21,6 +21,7 @@
 //
 // The arithmetic is written once over a number type T:
 //   Fp  plain FP32 (the compiler may contract a * b + c into one FMA);
+//   Fd  plain FP64 (the FP64 storage form; all constants exact to double);
 //   F2  two cells in one 64-bit register, Blackwell's packed FP32
 //       instructions (add/sub/mul/fma .rn.f32x2): half the arithmetic
 //       instructions of two one-cell collisions.  The assembler contracts a
@@ -46,6 +47,9 @@ struct Rates {
 struct Fp {
   float v;
   static LBM_DI Fp make(float a) { return Fp{a}; }
+  // constants written as double quotients (1.0 / 3.0 ...) round to the same
+  // float as the float quotients for every constant below
+  static LBM_DI Fp make(double a) { return Fp{(float)a}; }
 };
 LBM_DI Fp operator+(Fp a, Fp b) { return Fp{a.v + b.v}; }
 LBM_DI Fp operator-(Fp a, Fp b) { return Fp{a.v - b.v}; }
@@ -62,6 +66,7 @@ struct F2 {
     return r;
   }
   static LBM_DI F2 make(float a) { return pack(a, a); }
+  static LBM_DI F2 make(double a) { return pack((float)a, (float)a); }
   LBM_DI float lo() const {
     float a;
     asm("mov.b64 {%0, _}, %1;" : "=f"(a) : "l"(v));
@@ -95,6 +100,52 @@ LBM_DI F2 fma(F2 a, F2 b, F2 c) {
 }
 LBM_DI F2 neg(F2 a) { return a * F2::make(-1.0f); }
 LBM_DI F2 recip(F2 a) { return F2::pack(__fdiv_rn(1.0f, a.lo()), __fdiv_rn(1.0f, a.hi())); }
+
+// FP64 (the double-precision storage form): plain double arithmetic
+struct Fd {
+  double v;
+  static LBM_DI Fd make(double a) { return Fd{a}; }
+};
+LBM_DI Fd operator+(Fd a, Fd b) { return Fd{a.v + b.v}; }
+LBM_DI Fd operator-(Fd a, Fd b) { return Fd{a.v - b.v}; }
+LBM_DI Fd operator*(Fd a, Fd b) { return Fd{a.v * b.v}; }
+LBM_DI Fd fma(Fd a, Fd b, Fd c) { return Fd{::fma(a.v, b.v, c.v)}; }
+LBM_DI Fd neg(Fd a) { return Fd{-a.v}; }
+LBM_DI Fd recip(Fd a) { return Fd{1.0 / a.v}; }
+
+// Coefficients of the relaxation formed from the rates: in FP32 each rate
+// product rounded as written (uniform scalars, so that every FP32
+// instantiation sees the same coefficients), in FP64 plain double products.
+template <class T>
+struct RelaxCoef {
+  T mhw1, hw2, c15, r1, r2, g1, g2;  // -w1/2, w2/2, 3 w1/2, 1 - w1, 1 - w2, g (1 - w1/2), g (1 - w2/2)
+};
+struct RatesD {
+  double omega1, omega2;
+  int galilean;
+};
+template <class T>
+LBM_DI RelaxCoef<T> relax_coef(const Rates& r) {
+  const float w1 = r.omega1, w2 = r.omega2;
+  const float g = r.galilean ? 3.0f : 0.0f;
+  const float hw1 = __fmul_rn(0.5f, w1), hw2 = __fmul_rn(0.5f, w2);
+  return RelaxCoef<T>{T::make(-hw1),
+                      T::make(hw2),
+                      T::make(__fmul_rn(1.5f, w1)),
+                      T::make(__fsub_rn(1.0f, w1)),
+                      T::make(__fsub_rn(1.0f, w2)),
+                      T::make(__fmul_rn(g, __fsub_rn(1.0f, hw1))),
+                      T::make(__fmul_rn(g, __fsub_rn(1.0f, hw2)))};
+}
+template <class T>
+LBM_DI RelaxCoef<T> relax_coef(const RatesD& r) {
+  const double w1 = r.omega1, w2 = r.omega2;
+  const double g = r.galilean ? 3.0 : 0.0;
+  return RelaxCoef<T>{T::make(-0.5 * w1),     T::make(0.5 * w2),
+                      T::make(1.5 * w1),      T::make(1.0 - w1),
+                      T::make(1.0 - w2),      T::make(g * (1.0 - 0.5 * w1)),
+                      T::make(g * (1.0 - 0.5 * w2))};
+}
 
 // 1-D map from central moments (M0, M1, M2) about u to the three
 // populations f(-1), f(0), f(+1): from the raw moments R1 = M1 + u M0 and
@@ -133,8 +184,8 @@ LBM_DI void central_to_pop(T m0, T m1, T m2, const AxisMap<T>& A, T& fm, T& f0, 
 // its values relative to the reference `ref`, whose moments j_x = U and
 // Pi_xx - 1/3 = U^2 are added before the relaxation and whose populations
 // are subtracted from the result).
-template <class T, bool SCALED>
-LBM_DI void collide_cell(T* d, const Rates& r, float inv_s_in, float s_out, const RefShift* ref) {
+template <class T, bool SCALED, class R>
+LBM_DI void collide_cell(T* d, const R& r, float inv_s_in, float s_out, const RefShift* ref) {
   // ---- raw moments of the deviations: three passes (x, then y, then z)
   T x0[9], x1[9], x2[9];
 #pragma unroll
@@ -172,7 +223,7 @@ LBM_DI void collide_cell(T* d, const Rates& r, float inv_s_in, float s_out, cons
   const T ir = recip(rho);
   const T ux = jx * ir, uy = jy * ir, uz = jz * ir;
   const T ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-  const T third = T::make(1.0f / 3.0f), mthird = T::make(-1.0f / 3.0f);
+  const T third = T::make(1.0 / 3.0), mthird = T::make(-1.0 / 3.0);
   // second-order cumulants (normalised by rho), diagonal ones minus 1/3
   const T dxx = fma(fma(mthird, drho, sxx), ir, neg(ux2));
   const T dyy = fma(fma(mthird, drho, syy), ir, neg(uy2));
@@ -181,18 +232,15 @@ LBM_DI void collide_cell(T* d, const Rates& r, float inv_s_in, float s_out, cons
   const T kxz = sxz * ir - ux * uz;
   const T kyz = syz * ir - uy * uz;
 
-  // ---- relaxation; the rate products are uniform scalars, each rounded as
-  // written so that every instantiation sees the same coefficients
-  const float w1 = r.omega1, w2 = r.omega2;
-  const float g = r.galilean ? 3.0f : 0.0f;
-  const float hw1 = __fmul_rn(0.5f, w1), hw2 = __fmul_rn(0.5f, w2);
-  const T dxu = T::make(-hw1) * (dxx + dxx - dyy - dzz) - T::make(hw2) * (dxx + dyy + dzz);
-  const T c15 = T::make(__fmul_rn(1.5f, w1));
+  // ---- relaxation (coefficients from the rates: relax_coef)
+  const RelaxCoef<T> kc = relax_coef<T>(r);
+  const T dxu = kc.mhw1 * (dxx + dxx - dyy - dzz) - kc.hw2 * (dxx + dyy + dzz);
+  const T c15 = kc.c15;
   const T dyv = dxu + c15 * (dxx - dyy);
   const T dzw = dxu + c15 * (dxx - dzz);
   const T cx2 = ux2 * dxu, cy2 = uy2 * dyv, cz2 = uz2 * dzw;
-  const T r1 = T::make(__fsub_rn(1.0f, w1)), r2 = T::make(__fsub_rn(1.0f, w2));
-  const T g1 = T::make(__fmul_rn(g, __fsub_rn(1.0f, hw1))), g2 = T::make(__fmul_rn(g, __fsub_rn(1.0f, hw2)));
+  const T r1 = kc.r1, r2 = kc.r2;
+  const T g1 = kc.g1, g2 = kc.g2;
   const T A = r1 * (dxx - dyy) - g1 * (cx2 - cy2);
   const T Bq = r1 * (dxx - dzz) - g1 * (cx2 - cz2);
   const T Tr = r2 * (dxx + dyy + dzz) - g2 * (cx2 + cy2 + cz2);
@@ -257,8 +305,8 @@ LBM_DI void collide_cell(T* d, const Rates& r, float inv_s_in, float s_out, cons
   // components), minus the scaled reference r_i s for the FP16 form
   const T so = T::make(SCALED ? s_out : 1.0f);
   const T rs = rho * so, ds = drho * so;
-  const T dw[4] = {ds * T::make(1.0f / 216.0f), ds * T::make(1.0f / 54.0f), ds * T::make(2.0f / 27.0f),
-                   ds * T::make(8.0f / 27.0f)};
+  const T dw[4] = {ds * T::make(1.0 / 216.0), ds * T::make(1.0 / 54.0), ds * T::make(2.0 / 27.0),
+                   ds * T::make(8.0 / 27.0)};
 #pragma unroll
   for (int yz = 0; yz < 9; ++yz) {
     const int o = 3 * yz;  // moment a, population cy, cz
@@ -277,6 +325,11 @@ LBM_DI void collide_cell(T* d, const Rates& r, float inv_s_in, float s_out, cons
   }
 }
 
+// FP64 storage: plain FP64 arithmetic on one cell (deviations from the rest
+// weights, no scale, no reference)
+LBM_DI void cumulant_collide_d(double* d, const RatesD& r) {
+  collide_cell<Fd, false>(reinterpret_cast<Fd*>(d), r, 1.0f, 1.0f, nullptr);
+}
 // FP32 storage: plain FP32 arithmetic on one cell
 LBM_DI void cumulant_collide(float* d, const Rates& r) {
   collide_cell<Fp, false>(reinterpret_cast<Fp*>(d), r, 1.0f, 1.0f, nullptr);

@@ -160,9 +160,10 @@ struct Level {
   std::vector<uint8_t> masks;                    // collide flags, B^3 per masked block
   long long n_fluid = 0;
   double nu = 0, omega1 = 1;
-  int esize = 4;        // bytes per stored population: 4 (FP32) or 2 (FP16)
+  int esize = 4;        // bytes per stored population: 8 (FP64), 4 (FP32) or 2 (FP16)
   float scale = 1.0f;   // stored value = (f - w - r) * scale (r = 0 in FP32)
   std::vector<Link> links;
+  std::vector<double> link_q;  // FP64 wall fractions in table order (FP64 storage form)
   std::vector<WallEntry> wall[2];
   std::vector<int> seg_begin;                    // n_seg + 1 offsets into the ordered links
   std::vector<FaceEntry> face[2];
@@ -187,7 +188,7 @@ struct Level {
   // device offsets (bytes from the bound base)
   size_t off_f = 0, off_nbr = 0, off_maskoff = 0, off_masks = 0;
   size_t off_wall[2] = {0, 0}, off_face[2] = {0, 0};
-  size_t off_expl = 0, off_save = 0, off_infl = 0, off_coal = 0, off_saved = 0;
+  size_t off_expl = 0, off_save = 0, off_infl = 0, off_coal = 0, off_saved = 0, off_q64 = 0;
 
   long long cells_per_block() const { return (long long)B * B * B; }
   size_t f_elems() const { return (size_t)n_storage * kQ * cells_per_block(); }
@@ -234,6 +235,8 @@ struct CollideArgs {
   int galilean;
   double* err;        // set to 1 when a bounded device wait gives up
   int half;           // FP16 storage of scaled deviations
+  int f64;            // FP64 storage (the double-precision form; rates below)
+  double omega1d, omega2d;
   float scale, inv_scale;
   int wide;           // 64-bit element offsets even when f_elems < 2^31
   int odd_variant;    // LBM_ODD_COLUMNS | LBM_ODD_STAGED | LBM_ODD_DIRECT
@@ -259,7 +262,7 @@ struct TurbArgs {      // turbulent inflow; n_modes == 0: uniform inflow equilib
 };
 // Table arguments `e` point to the 64-bit entries, or to the 32-bit ones (the
 // ...N types) when `narrow` is set.
-int launch_faces(void* f, int half, const void* e, int narrow, int n, const float feq[27], const TurbArgs& turb,
+int launch_faces(void* f, int esize, const void* e, int narrow, int n, const double feq[27], const TurbArgs& turb,
                  void* stream);
 // one launch over a work list of (index into lv, block) pairs; grid <= 0: one CTA per item
 // zshift: each item is walked by 2^zshift CTAs (or grid strides) of B >> zshift slabs
@@ -267,32 +270,36 @@ int launch_collide_batch(const CollideArgs* lv, const int2* items, int n_items, 
                          int half, int wide, int grid, int zshift, void* stream);
 int launch_tick(long long* tick, void* stream);
 // per-sample viscous traction times area, tangential part: out[3 k .. 3 k + 2]
-int launch_friction(const void* f, int half, float inv_scale, const Ref27& ref, int B, const int* nbr, int odd,
+int launch_friction(const void* f, int esize, float inv_scale, const Ref27& ref, int B, const int* nbr, int odd,
                     float omega1, const FrictionSample* e, int n, double* out, void* stream);
 // Bouzidi update and momentum exchange of one link table; with `accum` set,
 // the force of this step (gauge-form link sums plus rest[3], the exact sum of
 // c_i 2 w_i over the links) goes to accum[0..2] and is added to accum[3..6]
 // by the launch's last CTA (`done`: a zeroed counter it leaves zeroed).
-int launch_walls(void* f, int half, float inv_scale, const Ref27& ref, const void* e, int narrow, int n,
-                 double* partials, double* link_force, unsigned* done, double* accum, const double rest[3],
+// q64: the links' wall fractions in FP64 (FP64 storage form), or NULL to use
+// the FP32 q of the table entries
+int launch_walls(void* f, int esize, const double* q64, float inv_scale, const Ref27& ref, const void* e, int narrow,
+                 int n, double* partials, double* link_force, unsigned* done, double* accum, const double rest[3],
                  void* stream);
 int launch_segments(const double* link_force, const int* seg_begin, int n_seg, double* seg_accum, void* stream);
 int walls_partial_count(int n);
-int launch_explode(void* fine, const void* coarse, int half, float ratio, const void* e, int narrow, int ne,
-                   const void* s, int ns, float* saved, int parity, void* stream);
-int launch_inflow(void* fine, const void* coarse, int half, float ratio, const void* e, int narrow, int n,
-                  const float* saved, int parity, void* stream);
-int launch_coalesce(void* coarse, const void* fine, int half, float ratio, const void* e, int narrow, int n,
-                    const float* saved, int parity, void* stream);
+// `esize`: bytes per stored population (2 binary16, 4 FP32, 8 FP64); saved
+// values are FP32, or FP64 for the FP64 form
+int launch_explode(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int ne,
+                   const void* s, int ns, void* saved, int parity, void* stream);
+int launch_inflow(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int n,
+                  const void* saved, int parity, void* stream);
+int launch_coalesce(void* coarse, const void* fine, int esize, float ratio, const void* e, int narrow, int n,
+                    const void* saved, int parity, void* stream);
 // fill the 32-bit tables of every level whose addressed arrays allow them
 void narrow_tables(Mesh* m);
-int launch_fill(void* f, int half, long long n_blocks, int B, const float dev[27], void* stream);
-int launch_mass(const void* f, int half, float inv_scale, const Ref27& ref, const int* nbr, const int* maskoff,
+int launch_fill(void* f, int esize, long long n_blocks, int B, const double dev[27], void* stream);
+int launch_mass(const void* f, int esize, float inv_scale, const Ref27& ref, const int* nbr, const int* maskoff,
                 const uint8_t* masks, int n_active, int B, int parity, double* partials, void* stream);
 int mass_partial_count(int n_active);
 int noalloc_max_blocks();
 int noalloc_scratch(double** out);
-int launch_mass_noalloc(const void* f, int half, float inv_scale, const Ref27& ref, const int* nbr,
+int launch_mass_noalloc(const void* f, int esize, float inv_scale, const Ref27& ref, const int* nbr,
                         const int* maskoff, const uint8_t* masks, int n_active, int B, int parity, double* scratch,
                         void* stream);
 const char* cuda_error_string();

@@ -16,9 +16,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <type_traits>
 
 #include "collide.cuh"
@@ -31,9 +33,12 @@ namespace {
 struct Feq27 {
   float v[27];
 };
+struct Vals27 {  // values of the FP64 form, and fill values of every form
+  double v[27];
+};
 
-template <typename S, typename E>
-__global__ void k_faces(S* __restrict__ f, const E* __restrict__ e, int n, Feq27 feq) {
+template <typename S, typename E, typename FQ>
+__global__ void k_faces(S* __restrict__ f, const E* __restrict__ e, int n, FQ feq) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const E x = e[t];
@@ -223,23 +228,25 @@ __device__ __forceinline__ FF ff_warp_sum(FF v) {
 // finished CTAs and is reset by the last one.
 template <typename S, typename E>
 __global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const E* __restrict__ e, int n,
-                                                        float inv_scale, Ref27 ref, double* __restrict__ partials,
+                                                        const double* __restrict__ q64, float inv_scale, Ref27 ref,
+                                                        double* __restrict__ partials,
                                                         double* __restrict__ link_force, unsigned* __restrict__ done,
                                                         double* __restrict__ accum, double3 rest) {
+  using V = typename Store<S>::V;  // FP32, or FP64 for the double-precision form
   const int t = blockIdx.x * kWallThreads + threadIdx.x;
-  float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+  V gx = 0, gy = 0, gz = 0;
   if (t < n) {
     const E w = e[t];
-    const float fa = Store<S>::ld(f, w.a);  // f*_i(x_f), toward the wall (stored deviation)
-    const float q = w.q;
-    float out;
-    float wi_ref = 1.0f;  // interpolation weight on direction-i populations
+    const V fa = Store<S>::ld(f, w.a);  // f*_i(x_f), toward the wall (stored deviation)
+    const V q = q64 ? (V)q64[t] : (V)w.q;  // the FP64 form keeps q in FP64
+    V out;
+    V wi_ref = 1.0f;  // interpolation weight on direction-i populations
     if (w.b < 0) {
       out = fa;  // second fluid node missing: simple bounce-back
     } else if (q < 0.5f) {
       out = 2.0f * q * fa + (1.0f - 2.0f * q) * Store<S>::ld(f, w.b);
     } else {
-      const float fc = Store<S>::ld(f, w.c);
+      const V fc = Store<S>::ld(f, w.c);
       wi_ref = 1.0f / (2.0f * q);
       out = fa * wi_ref + (2.0f * q - 1.0f) / (2.0f * q) * fc;
     }
@@ -248,15 +255,15 @@ __global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const
     // the weight on the direction-i terms (all of it unless q >= 1/2, where
     // f*_ibar(x_f) takes the rest)
     const int i = w.dir;
-    if (Store<S>::scaled) out += wi_ref * (ref.v[i] - ref.v[26 - i]) / inv_scale;
+    if constexpr (Store<S>::scaled) out += wi_ref * (ref.v[i] - ref.v[26 - i]) / inv_scale;
     Store<S>::st(f, w.dst, out);
     // gauge-form momentum exchange of the link, resting wall: full
     // populations minus the rest weights, (f*_i - w_i) + (f_ibar - w_ibar)
-    float sum = fa + out;
-    if (Store<S>::scaled) sum = fmaf(sum, inv_scale, ref.v[i] + ref.v[26 - i]);
-    gx = dcx(i) ? (dcx(i) > 0 ? sum : -sum) : 0.0f;
-    gy = dcy(i) ? (dcy(i) > 0 ? sum : -sum) : 0.0f;
-    gz = dcz(i) ? (dcz(i) > 0 ? sum : -sum) : 0.0f;
+    V sum = fa + out;
+    if constexpr (Store<S>::scaled) sum = fmaf(sum, inv_scale, ref.v[i] + ref.v[26 - i]);
+    gx = dcx(i) ? (dcx(i) > 0 ? sum : -sum) : (V)0;
+    gy = dcy(i) ? (dcy(i) > 0 ? sum : -sum) : (V)0;
+    gz = dcz(i) ? (dcz(i) > 0 ? sum : -sum) : (V)0;
     // per-link force for the branch sums: a branch's links do not close a
     // surface, so the reference pressure must not enter
     if (link_force) {
@@ -265,14 +272,26 @@ __global__ void __launch_bounds__(kWallThreads) k_walls(S* __restrict__ f, const
       link_force[3 * (size_t)t + 2] = gz;
     }
   }
-  const FF sx = ff_warp_sum(FF{gx, 0.0f}), sy = ff_warp_sum(FF{gy, 0.0f}), sz = ff_warp_sum(FF{gz, 0.0f});
+  // warp sums: float-float in FP32 (about 2^-44 relative), plain FP64 for the
+  // double-precision form
+  double wx, wy, wz;
+  if constexpr (sizeof(V) == 4) {
+    const FF sx = ff_warp_sum(FF{gx, 0.0f}), sy = ff_warp_sum(FF{gy, 0.0f}), sz = ff_warp_sum(FF{gz, 0.0f});
+    wx = (double)sx.hi + (double)sx.lo;
+    wy = (double)sy.hi + (double)sy.lo;
+    wz = (double)sz.hi + (double)sz.lo;
+  } else {
+    wx = warp_sum(gx);
+    wy = warp_sum(gy);
+    wz = warp_sum(gz);
+  }
   __shared__ double ws[3][kWallThreads / 32];
   __shared__ bool last;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
-    ws[0][wid] = (double)sx.hi + (double)sx.lo;
-    ws[1][wid] = (double)sy.hi + (double)sy.lo;
-    ws[2][wid] = (double)sz.hi + (double)sz.lo;
+    ws[0][wid] = wx;
+    ws[1][wid] = wy;
+    ws[2][wid] = wz;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -340,10 +359,12 @@ __global__ void __launch_bounds__(256) k_segments(const double* __restrict__ lin
 }
 
 // Interface kernels.  ratio = s_fine / s_coarse maps stored coarse values to
-// the fine scale (1 for FP32); saved values are fine-scaled floats.
+// the fine scale (1 for FP32 and FP64); saved values are fine-scaled values of
+// the arithmetic type (FP32, FP64 for the double-precision form).
 template <typename S, typename E, typename SE>
 __global__ void k_explode(S* __restrict__ fine, const S* __restrict__ coarse, const E* __restrict__ e, int ne,
-                          const SE* __restrict__ s, int ns, float* __restrict__ saved, int parity, float ratio) {
+                          const SE* __restrict__ s, int ns, typename Store<S>::V* __restrict__ saved, int parity,
+                          float ratio) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < ne) {
     const E x = e[t];
@@ -354,7 +375,7 @@ __global__ void k_explode(S* __restrict__ fine, const S* __restrict__ coarse, co
 
 template <typename S, typename E>
 __global__ void k_inflow(S* __restrict__ fine, const S* __restrict__ coarse, const E* __restrict__ e, int n,
-                         const float* __restrict__ saved, int parity, float ratio) {
+                         const typename Store<S>::V* __restrict__ saved, int parity, float ratio) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const E x = e[t];
@@ -363,35 +384,40 @@ __global__ void k_inflow(S* __restrict__ fine, const S* __restrict__ coarse, con
 
 template <typename S, typename E>
 __global__ void k_coalesce(S* __restrict__ coarse, const S* __restrict__ fine, const E* __restrict__ e, int n,
-                           const float* __restrict__ saved, int parity, float ratio) {
+                           const typename Store<S>::V* __restrict__ saved, int parity, float ratio) {
+  using V = typename Store<S>::V;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const E& x = e[t];
   const long long dst = parity ? x.dst[1] : x.dst[0];
-  float vf = 0.0f;
+  V vf = 0.0f;
   for (int k = 0; k < x.nfine; ++k) {
     const long long s = x.fsrc[k];
     vf += s >= 0 ? Store<S>::ld(fine, s) : saved[-s - 1];
   }
-  float v = vf / ratio;
-  if (x.ncoarse) v += (float)x.ncoarse * Store<S>::ld(coarse, dst);
+  V v = vf / ratio;
+  if (x.ncoarse) v += (V)x.ncoarse * Store<S>::ld(coarse, dst);
   Store<S>::st(coarse, dst, v * 0.125f);
 }
 
 // one CTA per (storage block, population plane): the plane's C3 values are
-// all equal, written as 16-byte words
+// all equal, written as 16-byte words (dev: the stored value per plane, in
+// FP64, rounded to the storage type here)
 template <typename S>
-__global__ void __launch_bounds__(256) k_fill(S* __restrict__ f, int c3, Feq27 dev) {
+__global__ void __launch_bounds__(256) k_fill(S* __restrict__ f, int c3, Vals27 dev) {
   const long long chunk = blockIdx.x;
-  const float v = dev.v[(int)(chunk % 27)];
+  const double vd = dev.v[(int)(chunk % 27)];
   uint4 w;
   if (std::is_same<S, float>::value) {
-    const unsigned b = __float_as_uint(v);
+    const unsigned b = __float_as_uint((float)vd);
     w = make_uint4(b, b, b, b);
-  } else {
-    const unsigned short h = __half_as_ushort(__float2half_rn(v));
+  } else if (std::is_same<S, __half>::value) {
+    const unsigned short h = __half_as_ushort(__float2half_rn((float)vd));
     const unsigned b = (unsigned)h | ((unsigned)h << 16);
     w = make_uint4(b, b, b, b);
+  } else {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(vd);
+    w = make_uint4((unsigned)b, (unsigned)(b >> 32), (unsigned)b, (unsigned)(b >> 32));
   }
   uint4* p = reinterpret_cast<uint4*>(f + chunk * c3);
   const int nw = c3 * (int)sizeof(S) / 16;
@@ -421,7 +447,7 @@ __global__ void __launch_bounds__(B * B) k_mass(const S* __restrict__ f, const i
     double rho = 0, ax = 0, ay = 0, az = 0;
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
-      float v;
+      typename Store<S>::V v;
       if (!parity) {
         v = Store<S>::ld(f, s_base[13] + i * C3 + cell);
       } else {
@@ -516,6 +542,15 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 
 const char* cuda_error_string() { return g_err; }
 
+// call fn with a typed null pointer of the storage type of `esize` bytes per
+// population (2: binary16, 4: FP32, 8: FP64)
+template <class F>
+void by_storage(int esize, F&& fn) {
+  if (esize == 2) fn((__half*)nullptr);
+  else if (esize == 8) fn((double*)nullptr);
+  else fn((float*)nullptr);
+}
+
 template <int B, typename IDX, typename S>
 void collide_on(const CollideArgs& a, int odd, cudaStream_t s) {
   constexpr bool f32 = std::is_same<S, float>::value;
@@ -535,6 +570,12 @@ void collide_on(const CollideArgs& a, int odd, cudaStream_t s) {
   }
 }
 
+template <int B, typename IDX>
+void collide_f64_on(const CollideArgs& a, int odd, cudaStream_t s) {
+  if (odd) k_collide_f64<B, true, IDX><<<a.n_active << a.zshift_odd, B * B, 0, s>>>(a);
+  else k_collide_f64<B, false, IDX><<<a.n_active << a.zshift_even, B * B, 0, s>>>(a);
+}
+
 template <typename S>
 void collide_typed(const CollideArgs& a, int B, int odd, cudaStream_t s) {
   const bool small = !a.wide && a.f_elems < (1LL << 31);
@@ -544,6 +585,17 @@ void collide_typed(const CollideArgs& a, int B, int odd, cudaStream_t s) {
   } else {
     if (small) collide_on<8, int, S>(a, odd, s);
     else collide_on<8, long long, S>(a, odd, s);
+  }
+}
+
+void collide_f64(const CollideArgs& a, int B, int odd, cudaStream_t s) {
+  const bool small = !a.wide && a.f_elems < (1LL << 31);
+  if (B == 16) {
+    if (small) collide_f64_on<16, int>(a, odd, s);
+    else collide_f64_on<16, long long>(a, odd, s);
+  } else {
+    if (small) collide_f64_on<8, int>(a, odd, s);
+    else collide_f64_on<8, long long>(a, odd, s);
   }
 }
 
@@ -590,7 +642,8 @@ int launch_collide(const CollideArgs& a, int B, int odd, void* stream) {
   if (a.zshift_even < 0 || a.zshift_odd < 0 || (B >> a.zshift_even) < 1 || (B >> a.zshift_odd) < 1)
     return LBM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (a.half) collide_typed<__half>(a, B, odd, s);
+  if (a.f64) collide_f64(a, B, odd, s);
+  else if (a.half) collide_typed<__half>(a, B, odd, s);
   else collide_typed<float>(a, B, odd, s);
   return check_launch("collide");
 }
@@ -610,41 +663,45 @@ int launch_collide_batch(const CollideArgs* lv, const int2* items, int n_items, 
 }
 
 template <typename E>
-void faces_typed(void* f, int half, const E* e, int n, const float feq[27], const TurbArgs& turb, cudaStream_t s) {
-  if (turb.n_modes > 0) {
+void faces_typed(void* f, int esize, const E* e, int n, const double feq[27], const TurbArgs& turb,
+                 cudaStream_t s) {
+  if (turb.n_modes > 0 && esize != 8) {
     const size_t smem = (size_t)turb.n_modes * kModeCols * sizeof(float);
-    if (half) k_faces_turb<__half, E><<<blocks_for(n, 128), 128, smem, s>>>((__half*)f, e, n, turb);
+    if (esize == 2) k_faces_turb<__half, E><<<blocks_for(n, 128), 128, smem, s>>>((__half*)f, e, n, turb);
     else k_faces_turb<float, E><<<blocks_for(n, 128), 128, smem, s>>>((float*)f, e, n, turb);
     return;
   }
+  if (esize == 8) {
+    Vals27 v;
+    for (int i = 0; i < 27; ++i) v.v[i] = feq[i];
+    k_faces<double, E, Vals27><<<blocks_for(n, 256), 256, 0, s>>>((double*)f, e, n, v);
+    return;
+  }
   Feq27 v;
-  for (int i = 0; i < 27; ++i) v.v[i] = feq[i];
-  if (half) k_faces<__half, E><<<blocks_for(n, 256), 256, 0, s>>>((__half*)f, e, n, v);
-  else k_faces<float, E><<<blocks_for(n, 256), 256, 0, s>>>((float*)f, e, n, v);
+  for (int i = 0; i < 27; ++i) v.v[i] = (float)feq[i];
+  if (esize == 2) k_faces<__half, E, Feq27><<<blocks_for(n, 256), 256, 0, s>>>((__half*)f, e, n, v);
+  else k_faces<float, E, Feq27><<<blocks_for(n, 256), 256, 0, s>>>((float*)f, e, n, v);
 }
 
-int launch_faces(void* f, int half, const void* e, int narrow, int n, const float feq[27], const TurbArgs& turb,
+int launch_faces(void* f, int esize, const void* e, int narrow, int n, const double feq[27], const TurbArgs& turb,
                  void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (narrow) faces_typed(f, half, (const FaceEntryN*)e, n, feq, turb, s);
-  else faces_typed(f, half, (const FaceEntry*)e, n, feq, turb, s);
+  if (narrow) faces_typed(f, esize, (const FaceEntryN*)e, n, feq, turb, s);
+  else faces_typed(f, esize, (const FaceEntry*)e, n, feq, turb, s);
   return check_launch("faces");
 }
 
-int launch_friction(const void* f, int half, float inv_scale, const Ref27& ref, int B, const int* nbr, int odd,
-                    float omega1,
-                    const FrictionSample* e, int n, double* out, void* stream) {
+int launch_friction(const void* f, int esize, float inv_scale, const Ref27& ref, int B, const int* nbr, int odd,
+                    float omega1, const FrictionSample* e, int n, double* out, void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const unsigned g = blocks_for(n, 128);
-  if (B == 16) {
-    if (half) k_friction<16, __half><<<g, 128, 0, s>>>((const __half*)f, e, n, nbr, odd, omega1, inv_scale, ref, out);
-    else k_friction<16, float><<<g, 128, 0, s>>>((const float*)f, e, n, nbr, odd, omega1, inv_scale, ref, out);
-  } else {
-    if (half) k_friction<8, __half><<<g, 128, 0, s>>>((const __half*)f, e, n, nbr, odd, omega1, inv_scale, ref, out);
-    else k_friction<8, float><<<g, 128, 0, s>>>((const float*)f, e, n, nbr, odd, omega1, inv_scale, ref, out);
-  }
+  by_storage(esize, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    if (B == 16) k_friction<16, S><<<g, 128, 0, s>>>((const S*)f, e, n, nbr, odd, omega1, inv_scale, ref, out);
+    else k_friction<8, S><<<g, 128, 0, s>>>((const S*)f, e, n, nbr, odd, omega1, inv_scale, ref, out);
+  });
   return check_launch("friction");
 }
 
@@ -656,25 +713,25 @@ int launch_tick(long long* tick, void* stream) {
 int walls_partial_count(int n) { return (int)blocks_for(n, kWallThreads); }
 
 template <typename E>
-void walls_typed(void* f, int half, float inv_scale, const Ref27& ref, const E* e, int n, double* partials,
-                 double* link_force, unsigned* done, double* accum, double3 rest, cudaStream_t s) {
+void walls_typed(void* f, int esize, const double* q64, float inv_scale, const Ref27& ref, const E* e, int n,
+                 double* partials, double* link_force, unsigned* done, double* accum, double3 rest, cudaStream_t s) {
   const unsigned g = blocks_for(n, kWallThreads);
-  if (half)
-    k_walls<__half, E><<<g, kWallThreads, 0, s>>>((__half*)f, e, n, inv_scale, ref, partials, link_force, done, accum,
-                                                  rest);
-  else
-    k_walls<float, E><<<g, kWallThreads, 0, s>>>((float*)f, e, n, inv_scale, ref, partials, link_force, done, accum,
-                                                 rest);
+  by_storage(esize, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    k_walls<S, E><<<g, kWallThreads, 0, s>>>((S*)f, e, n, q64, inv_scale, ref, partials, link_force, done, accum,
+                                              rest);
+  });
 }
 
-int launch_walls(void* f, int half, float inv_scale, const Ref27& ref, const void* e, int narrow, int n,
-                 double* partials, double* link_force, unsigned* done, double* accum, const double rest[3],
+int launch_walls(void* f, int esize, const double* q64, float inv_scale, const Ref27& ref, const void* e, int narrow,
+                 int n, double* partials, double* link_force, unsigned* done, double* accum, const double rest[3],
                  void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const double3 r = make_double3(rest[0], rest[1], rest[2]);
-  if (narrow) walls_typed(f, half, inv_scale, ref, (const WallEntryN*)e, n, partials, link_force, done, accum, r, s);
-  else walls_typed(f, half, inv_scale, ref, (const WallEntry*)e, n, partials, link_force, done, accum, r, s);
+  if (narrow)
+    walls_typed(f, esize, q64, inv_scale, ref, (const WallEntryN*)e, n, partials, link_force, done, accum, r, s);
+  else walls_typed(f, esize, q64, inv_scale, ref, (const WallEntry*)e, n, partials, link_force, done, accum, r, s);
   return check_launch("walls");
 }
 
@@ -684,129 +741,145 @@ int launch_segments(const double* link_force, const int* seg_begin, int n_seg, d
   return check_launch("segments");
 }
 
-
 template <typename E, typename SE>
-void explode_typed(void* fine, const void* coarse, int half, float ratio, const E* e, int ne, const SE* sv, int ns,
-                   float* saved, int parity, cudaStream_t s) {
+void explode_typed(void* fine, const void* coarse, int esize, float ratio, const E* e, int ne, const SE* sv, int ns,
+                   void* saved, int parity, cudaStream_t s) {
   const unsigned g = blocks_for(ne > ns ? ne : ns, 256);
-  if (half)
-    k_explode<__half, E, SE><<<g, 256, 0, s>>>((__half*)fine, (const __half*)coarse, e, ne, sv, ns, saved, parity,
-                                                ratio);
-  else
-    k_explode<float, E, SE><<<g, 256, 0, s>>>((float*)fine, (const float*)coarse, e, ne, sv, ns, saved, parity, ratio);
+  by_storage(esize, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    using V = typename Store<S>::V;
+    k_explode<S, E, SE><<<g, 256, 0, s>>>((S*)fine, (const S*)coarse, e, ne, sv, ns, (V*)saved, parity, ratio);
+  });
 }
 
-int launch_explode(void* fine, const void* coarse, int half, float ratio, const void* e, int narrow, int ne,
-                   const void* sv, int ns, float* saved, int parity, void* stream) {
+int launch_explode(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int ne,
+                   const void* sv, int ns, void* saved, int parity, void* stream) {
   if (ne == 0 && ns == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (narrow)
-    explode_typed(fine, coarse, half, ratio, (const ExplodeEntryN*)e, ne, (const SaveEntryN*)sv, ns, saved, parity, s);
+    explode_typed(fine, coarse, esize, ratio, (const ExplodeEntryN*)e, ne, (const SaveEntryN*)sv, ns, saved, parity,
+                  s);
   else
-    explode_typed(fine, coarse, half, ratio, (const ExplodeEntry*)e, ne, (const SaveEntry*)sv, ns, saved, parity, s);
+    explode_typed(fine, coarse, esize, ratio, (const ExplodeEntry*)e, ne, (const SaveEntry*)sv, ns, saved, parity, s);
   return check_launch("explode");
 }
 
 template <typename E>
-void inflow_typed(void* fine, const void* coarse, int half, float ratio, const E* e, int n, const float* saved,
+void inflow_typed(void* fine, const void* coarse, int esize, float ratio, const E* e, int n, const void* saved,
                   int parity, cudaStream_t s) {
-  if (half)
-    k_inflow<__half, E><<<blocks_for(n, 256), 256, 0, s>>>((__half*)fine, (const __half*)coarse, e, n, saved, parity,
-                                                            ratio);
-  else
-    k_inflow<float, E><<<blocks_for(n, 256), 256, 0, s>>>((float*)fine, (const float*)coarse, e, n, saved, parity,
-                                                           ratio);
+  by_storage(esize, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    using V = typename Store<S>::V;
+    k_inflow<S, E><<<blocks_for(n, 256), 256, 0, s>>>((S*)fine, (const S*)coarse, e, n, (const V*)saved, parity,
+                                                       ratio);
+  });
 }
 
-int launch_inflow(void* fine, const void* coarse, int half, float ratio, const void* e, int narrow, int n,
-                  const float* saved, int parity, void* stream) {
+int launch_inflow(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int n,
+                  const void* saved, int parity, void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (narrow) inflow_typed(fine, coarse, half, ratio, (const InflowEntryN*)e, n, saved, parity, s);
-  else inflow_typed(fine, coarse, half, ratio, (const InflowEntry*)e, n, saved, parity, s);
+  if (narrow) inflow_typed(fine, coarse, esize, ratio, (const InflowEntryN*)e, n, saved, parity, s);
+  else inflow_typed(fine, coarse, esize, ratio, (const InflowEntry*)e, n, saved, parity, s);
   return check_launch("inflow");
 }
 
 template <typename E>
-void coalesce_typed(void* coarse, const void* fine, int half, float ratio, const E* e, int n, const float* saved,
+void coalesce_typed(void* coarse, const void* fine, int esize, float ratio, const E* e, int n, const void* saved,
                     int parity, cudaStream_t s) {
-  if (half)
-    k_coalesce<__half, E><<<blocks_for(n, 256), 256, 0, s>>>((__half*)coarse, (const __half*)fine, e, n, saved,
-                                                              parity, ratio);
-  else
-    k_coalesce<float, E><<<blocks_for(n, 256), 256, 0, s>>>((float*)coarse, (const float*)fine, e, n, saved, parity,
-                                                             ratio);
+  by_storage(esize, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    using V = typename Store<S>::V;
+    k_coalesce<S, E><<<blocks_for(n, 256), 256, 0, s>>>((S*)coarse, (const S*)fine, e, n, (const V*)saved, parity,
+                                                         ratio);
+  });
 }
 
-int launch_coalesce(void* coarse, const void* fine, int half, float ratio, const void* e, int narrow, int n,
-                    const float* saved, int parity, void* stream) {
+int launch_coalesce(void* coarse, const void* fine, int esize, float ratio, const void* e, int narrow, int n,
+                    const void* saved, int parity, void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (narrow) coalesce_typed(coarse, fine, half, ratio, (const CoalesceEntryN*)e, n, saved, parity, s);
-  else coalesce_typed(coarse, fine, half, ratio, (const CoalesceEntry*)e, n, saved, parity, s);
+  if (narrow) coalesce_typed(coarse, fine, esize, ratio, (const CoalesceEntryN*)e, n, saved, parity, s);
+  else coalesce_typed(coarse, fine, esize, ratio, (const CoalesceEntry*)e, n, saved, parity, s);
   return check_launch("coalesce");
 }
 
-int launch_fill(void* f, int half, long long n_blocks, int B, const float dev[27], void* stream) {
-  Feq27 v;
+int launch_fill(void* f, int esize, long long n_blocks, int B, const double dev[27], void* stream) {
+  Vals27 v;
   for (int i = 0; i < 27; ++i) v.v[i] = dev[i];
   const int c3 = B * B * B;
   const long long chunks = n_blocks * 27LL;
   if (chunks == 0) return LBM_OK;
   if (chunks > 0x7fffffffLL) return LBM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (half) k_fill<__half><<<(unsigned)chunks, 256, 0, s>>>((__half*)f, c3, v);
-  else k_fill<float><<<(unsigned)chunks, 256, 0, s>>>((float*)f, c3, v);
+  by_storage(esize, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    k_fill<S><<<(unsigned)chunks, 256, 0, s>>>((S*)f, c3, v);
+  });
   return check_launch("fill");
 }
 
 int mass_partial_count(int n_active) { return n_active; }
 
-int launch_mass(const void* f, int half, float inv_scale, const Ref27& ref, const int* nbr, const int* maskoff,
-                const uint8_t* masks,
-                int n_active, int B, int parity, double* partials, void* stream) {
+int launch_mass(const void* f, int esize, float inv_scale, const Ref27& ref, const int* nbr, const int* maskoff,
+                const uint8_t* masks, int n_active, int B, int parity, double* partials, void* stream) {
   if (n_active == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (half) {
-    if (B == 16) k_mass<16, __half><<<n_active, 256, 0, s>>>((const __half*)f, nbr, maskoff, masks, parity, inv_scale, ref, partials);
-    else k_mass<8, __half><<<n_active, 64, 0, s>>>((const __half*)f, nbr, maskoff, masks, parity, inv_scale, ref, partials);
-  } else {
-    if (B == 16) k_mass<16, float><<<n_active, 256, 0, s>>>((const float*)f, nbr, maskoff, masks, parity, 1.0f, ref, partials);
-    else k_mass<8, float><<<n_active, 64, 0, s>>>((const float*)f, nbr, maskoff, masks, parity, 1.0f, ref, partials);
-  }
+  by_storage(esize, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    const float isc = Store<S>::scaled ? inv_scale : 1.0f;
+    if (B == 16)
+      k_mass<16, S><<<n_active, 256, 0, s>>>((const S*)f, nbr, maskoff, masks, parity, isc, ref, partials);
+    else k_mass<8, S><<<n_active, 64, 0, s>>>((const S*)f, nbr, maskoff, masks, parity, isc, ref, partials);
+  });
   return check_launch("mass");
 }
 
 int noalloc_max_blocks() { return kNoAllocMaxBlocks; }
 
-// Device address of the static scratch for the current device, looked up once
-// per device with that device current (first call; before any stream capture).
+// Device address of the static scratch for the current device (the domain's
+// device must be current, as for every call of the library), looked up once
+// per device with that device current.  std::call_once makes the first
+// lookup race-free when several host threads make their first call at once;
+// a failed lookup is retried by the next call.
 int noalloc_scratch(double** out) {
-  static double* ptr[64] = {};
+  constexpr int kMaxDevices = 64;
+  static std::once_flag once[kMaxDevices];
+  static std::atomic<double*> ptr[kMaxDevices];
+  static std::atomic<int> err[kMaxDevices];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     snprintf(g_err, sizeof g_err, "cudaGetDevice: %s", cudaGetErrorString(e));
     return LBM_ECUDA;
   }
-  if (!ptr[dev]) {
+  std::call_once(once[dev], [dev] {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    const cudaError_t r = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    err[dev].store((int)r);
+    if (r == cudaSuccess) ptr[dev].store((double*)p);
+  });
+  double* p = ptr[dev].load();
+  if (!p) {
+    // the one-time lookup failed on this device: report it, try again directly
+    void* q = nullptr;
+    e = cudaGetSymbolAddress(&q, g_noalloc_scratch);
     if (e != cudaSuccess) {
-      snprintf(g_err, sizeof g_err, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      snprintf(g_err, sizeof g_err, "cudaGetSymbolAddress: %s (first lookup: %s)", cudaGetErrorString(e),
+               cudaGetErrorString((cudaError_t)err[dev].load()));
       return LBM_ECUDA;
     }
-    ptr[dev] = (double*)p;
+    p = (double*)q;
   }
-  *out = ptr[dev];
+  *out = p;
   return LBM_OK;
 }
 
-int launch_mass_noalloc(const void* f, int half, float inv_scale, const Ref27& ref, const int* nbr,
+int launch_mass_noalloc(const void* f, int esize, float inv_scale, const Ref27& ref, const int* nbr,
                         const int* maskoff,
                         const uint8_t* masks, int n_active, int B, int parity, double* scratch, void* stream) {
   if (n_active > kNoAllocMaxBlocks) return LBM_EINVAL;
-  int rc = launch_mass(f, half, inv_scale, ref, nbr, maskoff, masks, n_active, B, parity, scratch, stream);
+  int rc = launch_mass(f, esize, inv_scale, ref, nbr, maskoff, masks, n_active, B, parity, scratch, stream);
   if (rc) return rc;
   k_sum5<<<1, 256, 0, (cudaStream_t)stream>>>(scratch, n_active, scratch + (size_t)kNoAllocMaxBlocks * 5);
   return check_launch("sum5");

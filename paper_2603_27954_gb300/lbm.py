@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 BC = {"periodic": 0, "inout": 1, "slip": 2, "inflow": 3}
+LBM_FP64 = 0
 LBM_FP32 = 1
 LBM_FP16_DEV = 2
 BRANCH_COLS = 11  # columns of lbm_branch_table
@@ -71,6 +72,7 @@ def _load():
         "lbm_set_geometry_prims": ([vp, ip, dp, i], i),
         "lbm_memory_requirements": ([vp, C.POINTER(sz)], i),
         "lbm_bind_memory": ([vp, vp, sz], i),
+        "lbm_memory_breakdown": ([vp, C.POINTER(sz), C.POINTER(sz)], i),
         "lbm_init_uniform": ([vp, d, dp], i),
         "lbm_init_field": ([vp, i, dp, dp, sz], i),
         "lbm_step": ([vp, i], i),
@@ -181,6 +183,13 @@ def lbm_memory_requirements(h):
     n = C.c_size_t()
     _ck(_lib.lbm_memory_requirements(h, C.byref(n)), "lbm_memory_requirements")
     return n.value
+
+
+def lbm_memory_breakdown(h):
+    """(population bytes, host-to-device bytes of one binding)"""
+    p, u = C.c_size_t(), C.c_size_t()
+    _ck(_lib.lbm_memory_breakdown(h, C.byref(p), C.byref(u)), "lbm_memory_breakdown")
+    return p.value, u.value
 
 
 def lbm_bind_memory(h, ptr, nbytes):

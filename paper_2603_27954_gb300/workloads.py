@@ -41,7 +41,16 @@ CASES = {
                        re_h=800.0, steps=20,
                        tree=dict(n=3, children=3, s0=16.0, w0=4.8, r=(0.6,), dfac=(0.6,), alpha_deg=(35.0,),
                                  azimuth_mode=1, seed=4, trunk_cells=16.0)),
-    # the two-level case scaled down by 4 (8^3 blocks), sized for the oracle
+    # the two-level case scaled down by 4 per axis for the oracle: the same tree (n = 4 rewritings,
+    # 3 children, 40 branches, seed 1) with a trunk of 16 finest cells, Re_H = 2.5e3, 8^3 blocks;
+    # coarse 64x32x36: at 64x32x32 the tree's box with its 25 % margin, rounded out to whole
+    # 8^3 finest blocks, leaves no room for the two parent cells the interface needs in z
+    "amr2_quarter": dict(n0=(64, 32, 36), levels=2, block=8, bc=("inout", "inflow", "inflow"), u_in=0.05,
+                         re_h=2500.0, steps=300,
+                         tree=dict(n=4, children=3, s0=16.0, w0=4.8, r=(0.6,), dfac=(0.6,), alpha_deg=(35.0,),
+                                   azimuth_mode=1, seed=1, trunk_cells=16.0)),
+    # a small two-level tree case for element-wise oracle tests: coarse 64x48x48 in 8^3 blocks,
+    # n = 3 rewritings (13 branches), trunk 16 finest cells, Re_H = 400
     "amr2_small": dict(n0=(64, 48, 48), levels=2, block=8, bc=("inout", "inflow", "inflow"), u_in=0.05,
                        re_h=400.0, steps=100,
                        tree=dict(n=3, children=3, s0=16.0, w0=4.8, r=(0.6,), dfac=(0.6,), alpha_deg=(35.0,),

@@ -174,3 +174,45 @@ def test_z_splits_give_identical_results(L, stream, case, precision):
         for a, b in zip(ref[0], got[0]):
             np.testing.assert_array_equal(a, b)
         np.testing.assert_array_equal(ref[1], got[1])
+
+
+def test_batch_matches_the_oracle(L, stream):
+    """A three-domain batch (one, two and three levels in 8^3 blocks; the
+    two-level one with 8 % random-Fourier-mode inflow) against the FP64
+    oracle element by element, each domain compared with its own oracle
+    simulation: the batched kernels and the batch's per-domain branching
+    reach the method's result, not only the single-domain path's."""
+    from oracle import turbulence as T
+    recs = [dict(W.CASES["tiny"], block=8), dict(W.CASES["amr2_small"], i_u=0.08, seed=7), W.CASES["amr3_small"]]
+    doms = [make(L, stream, c) for c in recs]
+    l_int = 10.0
+    doms[1].set_inflow_turbulence(256, l_int)
+    sims = []
+    for c in recs:
+        t = c["tree"]
+        tree = O.make_tree(t["n"], t["children"], t["s0"], t["w0"], t["r"], t["dfac"], alpha_deg=t["alpha_deg"],
+                           azimuth_mode=t["azimuth_mode"], seed=t["seed"])
+        sim, _ = O.tree_case(*c["n0"], tree, t["trunk_cells"], c["re_h"], u_in=c["u_in"], levels=c["levels"],
+                             block=c["block"], bc=c["bc"])
+        if c.get("i_u", 0.0) > 0:
+            sim.set_turbulence(T.rfm_modes(c["seed"], 256, c["i_u"], c["u_in"], l_int), c["u_in"])
+        sims.append(sim)
+    batch = L.Batch(doms, stream=stream)
+    batch.set_schedule(2, 0, 2, 4)
+    done = 0
+    for n in (1, 3):
+        batch.step(n - done)
+        for s in sims:
+            s.step(n - done)
+        done = n
+        for d, s, c in zip(doms, sims, recs):
+            for l in range(c["levels"]):
+                f, ref = d.get_populations(l), s.f(l)
+                ok = ~np.isnan(ref)
+                assert np.array_equal(ok, ~np.isnan(f))
+                err = np.abs(f[ok] - ref[ok]).max()
+                assert err < 2e-6, (c["n0"], l, n, err)
+            np.testing.assert_allclose(d.drag()[0], s.force()[0], rtol=1e-4, atol=1e-7)
+    batch.close()
+    for d in doms:
+        d.close()

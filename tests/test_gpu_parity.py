@@ -317,3 +317,29 @@ def test_parallel_branches_equal_serial_step(L, stream, case):
         for a, b in zip(runs[0][0], got[0]):
             np.testing.assert_array_equal(a, b)
         np.testing.assert_array_equal(runs[0][1], got[1])
+
+
+def test_quarter_scale_headline_case(L, stream):
+    """The benchmark's two-level tree case (n = 4 rewritings x 3 children, 40
+    branches, Re_H = 2.5e3) scaled down 4x per axis: every population of both
+    levels after 1 and 2 coarse steps within 2e-6 of the oracle, and the
+    drag coefficient after 300 coarse steps (the impulsive-start transient)
+    within the 5e-4 target."""
+    c = W.CASES["amr2_quarter"]
+    dom = gpu_case(L, stream, "amr2_quarter")
+    sim, info = oracle_case("amr2_quarter")
+    done = 0
+    for n in (1, 2, c["steps"]):
+        dom.step(n - done)
+        sim.step(n - done)
+        done = n
+        if n <= 2:
+            for lv in range(2):
+                compare_pops(dom.get_populations(lv), sim.f(lv), 2e-6)
+    _, _, cd = dom.drag()
+    ref, _, _ = sim.force()
+    cd_ref = O.drag_coefficient(ref[0], c["u_in"], info["A_x"])
+    print("quarter-scale case after %d coarse steps: C_D %.6f oracle %.6f rel %.2e" % (
+        c["steps"], cd, cd_ref, abs(cd - cd_ref) / abs(cd_ref)))
+    assert abs(cd - cd_ref) <= 5e-4 * abs(cd_ref)
+    dom.close()

@@ -103,3 +103,30 @@ def test_overlap_check_finds_independent_and_conflicting_kernels():
         L.lbm_set_geometry(h, L.tree_desc(**c["tree"]))
         assert L.lbm_get_overlap(h) == (True, bits)
         L.lbm_destroy(h)
+
+
+def test_fp64_form_descriptor_rules():
+    """The FP64 storage form: twice the FP32 population bytes, one collide
+    kernel per parity (only the direct / column-pointer variant names are
+    accepted), no turbulent inflow."""
+    from paper_2603_27954_gb300 import lbm as L
+    from paper_2603_27954_gb300 import workloads as W
+    c = W.CASES["tiny"]
+    sizes = {}
+    for prec in (L.LBM_FP64, L.LBM_FP32):
+        d = L.domain_desc(*c["n0"], levels=1, block=16, bc=c["bc"], u_in=0.05, re_h=100.0, precision=prec)
+        h = L.lbm_create_domain(d)
+        L.lbm_set_geometry(h, L.tree_desc(**c["tree"]))
+        sizes[prec] = L.lbm_memory_breakdown(h)[0]
+        if prec == L.LBM_FP64:
+            L.lbm_set_schedule(h, 0, 2, 0)
+            with pytest.raises(L.LbmError):
+                L.lbm_set_schedule(h, 0, 3, 0)
+            with pytest.raises(L.LbmError):
+                L.lbm_set_schedule(h, 0, 0, 2)
+        L.lbm_destroy(h)
+    assert sizes[L.LBM_FP64] == 2 * sizes[L.LBM_FP32]
+    d = L.domain_desc(*c["n0"], levels=1, block=16, bc=c["bc"], u_in=0.05, re_h=100.0, i_u=0.08,
+                      precision=L.LBM_FP64)
+    with pytest.raises(L.LbmError):
+        L.lbm_create_domain(d)

@@ -1,8 +1,9 @@
 """lbm_mass_noalloc: the mass / momentum check for callers that may not
-allocate device memory when they call it (an allocator that forbids growth,
-or a stream capture in progress).  Its reduction scratch is a fixed array
-inside the library, so the call allocates nothing; it must agree with
-lbm_mass, which uses scratch from the domain's bound buffer.
+allocate device memory when they call it (an allocator or pool that forbids
+growth).  Its reduction scratch is a fixed array inside the library, so the
+call allocates nothing; it must agree with lbm_mass, which uses scratch from
+the domain's bound buffer, in both storage forms (FP32 deviations, and
+binary16 deviations from the inflow equilibrium with their scale).
 
 Collected last on purpose (file name), so a failure here never hides the
 other tests in a run that stops at the first failure.
@@ -24,12 +25,13 @@ def L():
     return lbm
 
 
-@pytest.mark.parametrize("case", ["tiny", "amr2_small"])
-def test_noalloc_mass_matches_lbm_mass_on_two_calls(L, case):
+@pytest.mark.parametrize("case,precision", [("tiny", "fp32"), ("amr2_small", "fp32"), ("amr2_small", "fp16")])
+def test_noalloc_mass_matches_lbm_mass_on_two_calls(L, case, precision):
     import torch
     c = W.CASES[case]
+    prec = L.LBM_FP16_DEV if precision == "fp16" else L.LBM_FP32
     desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
-                         re_h=c["re_h"])
+                         re_h=c["re_h"], precision=prec)
     dom = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=torch.cuda.Stream())
     for steps in (3, 4):  # two calls in a row, on different states
         dom.step(steps)
