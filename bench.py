@@ -413,6 +413,28 @@ def main():
 
     value, ms_max = job_rate(updates, args.steps, ms, world, reduce_max)
 
+    # cost of the FP64 interface ledger (on in the timed run): the same
+    # schedule with the ledger off, timed the same way
+    def time_steps(n):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dom.step(n)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    n_l = max(50, args.steps // 4)
+    dom.set_interface_ledger(False)
+    dom.step(3)
+    ms_off = time_steps(n_l)
+    dom.set_interface_ledger(True)
+    dom.step(3)
+    ms_on = time_steps(n_l)
+    ledger = {"ms_per_step_on": ms_on, "ms_per_step_off": ms_off, "cost_frac": ms_on / ms_off - 1.0,
+              "steps": n_l, "note": "FP64 interface ledger on (default, as in the timed run) against off, "
+                                    "same tuned schedule"}
+
     # per-kernel timing with CUDA events on the domain's stream (direct launches)
     dom.set_timing(True)
     dom.step(args.timing_steps)
@@ -524,6 +546,7 @@ def main():
                         "initialisation of %.2f GB of populations on the device) and a synchronous read of the "
                         "drag (64 bytes) after each of %d steps; bytes per step = the upload over those steps" % (
                             uploaded / 1e6, pop_bytes / 1e9, args.e2e_steps)},
+        "interface_ledger": ledger,
         "precision_form": prec_form,
         "batched_form": batched,
         "gpu_launches": kernels * args.steps,

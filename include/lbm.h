@@ -181,7 +181,8 @@ int lbm_step(lbm_domain* d, int n_coarse);
    finest-level lattice units: force_last of the last finest step and
    force_mean averaged over the finest steps since the last init or
    lbm_reset_force; c_d = force_last[0] / (1/2 U^2 A_x) (Eq. 7, rho = 1,
-   A_x in finest cells^2).  Any pointer may be NULL.  Synchronises. */
+   A_x in finest cells^2).  Any pointer may be NULL.  Synchronises.
+   lbm_reset_force also clears the interface ledger (lbm_interface_ledger). */
 int lbm_drag(lbm_domain* d, double force_last[3], double force_mean[3], double* c_d);
 int lbm_reset_force(lbm_domain* d);
 
@@ -216,6 +217,42 @@ int lbm_mass(lbm_domain* d, double* mass, double mom[3]);
    memory and synchronises the domain's stream, so it must not be made while
    that stream is being captured into a CUDA graph. */
 int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]);
+
+/* Mass and momentum of one level (as lbm_mass: FP64 on device, level-l
+   cells weigh 8^-l).  Synchronises. */
+int lbm_level_mass(lbm_domain* d, int level, double* mass, double mom[3]);
+
+/* FP64 ledger of the refinement interface between `level` and level + 1
+   (Sec. 2.2's octree refinement; the volumetric transfer between the
+   levels).  Every coarse step the interface kernels record, as exact 64-bit
+   fixed-point sums reported in FP64, twelve values - mass and momentum
+   (x, y, z) of three flows, in level-0 cell volumes (a level-l cell weighs
+   8^-l), full populations f_i:
+     [0..3]  In:    coarse post-collision values handed to the fine level
+                    (the explode and inflow transfers)
+     [4..7]  OutF:  fine values the coalesce transfer takes from the fine
+                    level
+     [8..11] RecvC: what the coarse cells next to the fine region receive
+                    (8 x the stored coalesce result minus the part it keeps
+                    from the coarse cell itself)
+   so that over any stretch of steps, up to the rounding of the collisions,
+   the fine level's mass and momentum change by In - OutF and the coarse
+   level's by RecvC - In (plus the flows of its own coarser interface, and
+   nothing else in a closed box); RecvC - OutF is the interface's rounding
+   defect.
+   The interface kernels run once per step of the coarser level, so `last`
+   holds the flows of the last step of `level` (one coarse step for level 0,
+   half of one for level 1, ...) and *steps counts those steps; total: the
+   sum since binding, lbm_init_uniform or lbm_reset_force (which clear the
+   ledger).  Resolution: every recorded population deviation is rounded to
+   a multiple of 2^-40 (exact for binary16 storage; at most 2^-41 per entry
+   in FP32 and FP64), and the sums themselves are exact and independent of
+   the order of the threads.
+   The ledger is on by default; lbm_set_interface_ledger(d, 0) drops its
+   sums from the interface kernels (toggling recaptures the graphs and clears
+   the ledger).  LBM_EINVAL for the finest level.  Synchronises. */
+int lbm_set_interface_ledger(lbm_domain* d, int on);
+int lbm_interface_ledger(lbm_domain* d, int level, double last[12], double total[12], long long* steps);
 
 /* Real box [lo, hi) of a level in level-l cells, and cell counts. */
 int lbm_level_info(const lbm_domain* d, int level, int lo[3], int hi[3], long long* n_fluid,

@@ -94,6 +94,7 @@ struct lbm_domain {
   size_t off_linkf = 0, off_segb = 0, off_segacc = 0;  // per-branch forces (finest level)
   int n_seg = 0;
   bool branch_forces = false;
+  bool ledger = true;         // FP64 interface ledger (lbm_set_interface_ledger)
   bool wide_offsets = false;  // force the 64-bit-offset collide kernels
   int odd_variant = LBM_ODD_COLUMNS, even_variant = LBM_EVEN_DIRECT;
   int z_split_even = 0, z_split_odd = 0;  // collide CTAs per active block; 0: automatic
@@ -392,13 +393,19 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s, bool branche
 }
 
 // coarse post-collision values into the fine ghosts before the second fine step
+int c3_log2(int B) { return B == 16 ? 12 : 9; }
+LedgerDev* ledger_of(lbm_domain* dm, const Level& v) {
+  return dm->ledger ? dm->dev<LedgerDev>(v.off_ledger) : nullptr;
+}
+
 int iface_explode(lbm_domain* dm, int l, int parity, cudaStream_t s) {
   Level& v = dm->mesh.lv[l];
   Level& F = dm->mesh.lv[l + 1];
   Timed t(dm, KC_IFACE, (long long)v.expl.size());
   return launch_explode(dm->base + F.off_f, dm->base + v.off_f, v.esize, F.scale / v.scale,
                         dm->base + v.off_expl, v.narrow, (int)v.expl.size(), dm->base + v.off_save,
-                        (int)v.save.size(), dm->base + v.off_saved, parity, s);
+                        (int)v.save.size(), dm->base + v.off_saved, parity, ledger_of(dm, v), c3_log2(v.B),
+                        1.0f / F.scale, s);
 }
 
 // fine inflow for the next first fine step, and coarse cells from their children
@@ -411,10 +418,10 @@ int iface_inflow(lbm_domain* dm, int l, int parity, cudaStream_t s) {
   const float ratio = F.scale / v.scale;
   void* saved = dm->base + v.off_saved;
   int rc = launch_inflow(ff, f, v.esize, ratio, dm->base + v.off_infl, v.narrow, (int)v.infl.size(), saved,
-                         parity, s);
+                         parity, ledger_of(dm, v), c3_log2(v.B), 1.0f / F.scale, s);
   if (rc) return rc;
   return launch_coalesce(f, ff, v.esize, ratio, dm->base + v.off_coal, v.narrow, (int)v.coal.size(), saved,
-                         parity, s);
+                         parity, ledger_of(dm, v), v.ledger_const, c3_log2(v.B), 1.0f / v.scale, 1.0f / F.scale, s);
 }
 
 // friction of the finest level at the current step boundary, added to acc
@@ -555,6 +562,7 @@ int build(lbm_domain* d) {
     if (v.esize == 8)
       for (const Link& k : v.links) v.link_q.push_back(k.q);
     v.off_q64 = put(v.link_q.size() * sizeof(double));
+    v.off_ledger = put(l + 1 < L ? sizeof(LedgerDev) : 0);
     d->max_wall_parts = std::max(d->max_wall_parts, walls_partial_count((int)v.wall[0].size()));
     max_blocks = std::max(max_blocks, (size_t)v.n_active);
   }
@@ -593,6 +601,30 @@ int build(lbm_domain* d) {
   for (int i = 0; i < 27; ++i) {
     d->ref[i] = d->d.precision == LBM_FP16_DEV ? equilibrium(i, 1.0, u) - rest_weight(i) : 0.0;
     d->ref27.v[i] = (float)d->ref[i];
+  }
+  // the constant part (w_i + r_i) of the full populations the interface
+  // flows carry, per flow, and the fine cell volume (level-0 cell = 1)
+  for (int l = 0; l + 1 < L; ++l) {
+    Level& v = d->mesh.lv[l];
+    LedgerConst& lc = v.ledger_const;
+    lc = LedgerConst{};
+    lc.vol = std::ldexp(1.0, -3 * (l + 1));
+    const long long c3 = v.cells_per_block();
+    auto add = [&](int flow, int dir, double weight) {
+      const double wr = (rest_weight(dir) + d->ref[dir]) * weight;
+      lc.c[4 * flow] += wr;
+      lc.c[4 * flow + 1] += cx(dir) * wr;
+      lc.c[4 * flow + 2] += cy(dir) * wr;
+      lc.c[4 * flow + 3] += cz(dir) * wr;
+    };
+    for (const ExplodeEntry& e : v.expl) add(0, 26 - (int)((e.dst / c3) % 27), 1.0);
+    for (const InflowEntry& e : v.infl)
+      if (e.r < 0) add(0, (int)((e.dst / c3) % 27), 1.0);
+    for (const CoalesceEntry& e : v.coal) {
+      const int dir = 26 - (int)((e.dst[0] / c3) % 27);
+      add(1, dir, e.nfine);
+      add(2, dir, e.nfine);
+    }
   }
   d->built = true;
   return LBM_OK;
@@ -711,6 +743,8 @@ int reset_force(lbm_domain* d) {
   CK(cudaMemsetAsync(d->base + d->off_wdone, 0, sizeof(unsigned), d->stream));
   CK(cudaMemsetAsync(d->base + d->off_fmean, 0, std::max<size_t>(1, d->prims.size()) * 4 * sizeof(double), d->stream));
   if (d->n_seg) CK(cudaMemsetAsync(d->base + d->off_segacc, 0, (size_t)d->n_seg * 4 * sizeof(double), d->stream));
+  for (int l = 0; l + 1 < d->mesh.L; ++l)
+    CK(cudaMemsetAsync(d->base + d->mesh.lv[l].off_ledger, 0, sizeof(LedgerDev), d->stream));
   return LBM_OK;
 }
 
@@ -750,10 +784,11 @@ int capture_graphs(lbm_domain* d) {
   return LBM_OK;
 }
 
-int mass_device(lbm_domain* d, double* mass, double mom[3], double* bad) {
+int mass_device(lbm_domain* d, double* mass, double mom[3], double* bad, int only = -1) {
   double m = 0, p[3] = {0, 0, 0}, b = 0;
   std::vector<double> part;
   for (int l = 0; l < d->mesh.L; ++l) {
+    if (only >= 0 && l != only) continue;
     Level& v = d->mesh.lv[l];
     if (!v.n_active) continue;
     int rc = launch_mass(d->base + v.off_f, v.esize, 1.0f / v.scale, d->ref27, d->dev<int>(v.off_nbr),
@@ -1124,6 +1159,40 @@ int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]) {
   if (mass) *mass = m;
   if (mom)
     for (int a = 0; a < 3; ++a) mom[a] = p[a];
+  return LBM_OK;
+}
+
+int lbm_level_mass(lbm_domain* d, int level, double* mass, double mom[3]) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
+  return mass_device(d, mass, mom, nullptr, level);
+}
+
+int lbm_set_interface_ledger(lbm_domain* d, int on) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (d->ledger != (on != 0)) {
+    free_graphs(d);
+    d->ledger = on != 0;
+    if (d->base)
+      for (int l = 0; l + 1 < d->mesh.L; ++l)
+        CK(cudaMemsetAsync(d->base + d->mesh.lv[l].off_ledger, 0, sizeof(LedgerDev), d->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_interface_ledger(lbm_domain* d, int level, double last[12], double total[12], long long* steps) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  if (!valid_level(d, level) || level + 1 >= d->mesh.L) return fail(LBM_EINVAL, "no interface below this level");
+  LedgerDev h;
+  CK(cudaMemcpyAsync(&h, d->base + d->mesh.lv[level].off_ledger, sizeof h, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  for (int k = 0; k < kLedgerVals; ++k) {
+    if (last) last[k] = h.last[k];
+    if (total) total[k] = h.total[k];
+  }
+  if (steps) *steps = (long long)h.steps;
   return LBM_OK;
 }
 

@@ -135,6 +135,31 @@ struct CoalesceEntryN {
   short nfine, ncoarse;
 };
 
+// FP64 ledger of one refinement interface (coarse level l, fine level l + 1).
+// Per coarse step three flows are summed, each as mass and momentum (x, y,
+// z), in volume units of a fine cell: In, the coarse values the explode and
+// inflow transfers hand to the fine level; OutF, the fine values the coalesce
+// transfer takes from it; RecvC, what the coarse slots receive (8 x the
+// stored coalesce result minus its n_coarse x old-value part).  Device sums
+// are exact 64-bit fixed point (quantum 2^-40 of a population deviation), in
+// kLedgerCopies copies to spread atomic traffic; the coalesce launch's last
+// CTA folds them into FP64 `last` and `total` and clears them.
+constexpr int kLedgerCopies = 32;
+constexpr int kLedgerVals = 12;  // In (m, jx, jy, jz), OutF (...), RecvC (...)
+struct LedgerDev {
+  long long acc[kLedgerCopies][kLedgerVals];
+  unsigned done, pad;
+  double last[kLedgerVals];
+  double total[kLedgerVals];
+  double steps;
+};
+// host-computed parts of the fold: the constant part (w_i + r_i) of every
+// entry's full population, per flow, and the fine cell's volume
+struct LedgerConst {
+  double c[kLedgerVals];
+  double vol;
+};
+
 // ---------------------------------------------------------------- mesh
 enum CellType : uint8_t { FLUID = 0, SOLID = 1, COVERED = 2, OUTSIDE = 3 };
 enum BlockState : int8_t { ABSENT = 0, ACTIVE = 1, GHOST = 2 };
@@ -189,6 +214,8 @@ struct Level {
   size_t off_f = 0, off_nbr = 0, off_maskoff = 0, off_masks = 0;
   size_t off_wall[2] = {0, 0}, off_face[2] = {0, 0};
   size_t off_expl = 0, off_save = 0, off_infl = 0, off_coal = 0, off_saved = 0, off_q64 = 0;
+  size_t off_ledger = 0;  // LedgerDev of the interface with the next finer level
+  LedgerConst ledger_const{};
 
   long long cells_per_block() const { return (long long)B * B * B; }
   size_t f_elems() const { return (size_t)n_storage * kQ * cells_per_block(); }
@@ -284,13 +311,18 @@ int launch_walls(void* f, int esize, const double* q64, float inv_scale, const R
 int launch_segments(const double* link_force, const int* seg_begin, int n_seg, double* seg_accum, void* stream);
 int walls_partial_count(int n);
 // `esize`: bytes per stored population (2 binary16, 4 FP32, 8 FP64); saved
-// values are FP32, or FP64 for the FP64 form
+// values are FP32, or FP64 for the FP64 form.  `ledger` (or NULL) is the
+// interface's ledger; c3_log2 = log2 of the cells per block (the direction of
+// an entry is the population plane of its destination slot); inv_sc / inv_sf
+// undo the storage scale of the coarse / fine level.
 int launch_explode(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int ne,
-                   const void* s, int ns, void* saved, int parity, void* stream);
+                   const void* s, int ns, void* saved, int parity, LedgerDev* ledger, int c3_log2, float inv_sf,
+                   void* stream);
 int launch_inflow(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int n,
-                  const void* saved, int parity, void* stream);
+                  const void* saved, int parity, LedgerDev* ledger, int c3_log2, float inv_sf, void* stream);
 int launch_coalesce(void* coarse, const void* fine, int esize, float ratio, const void* e, int narrow, int n,
-                    const void* saved, int parity, void* stream);
+                    const void* saved, int parity, LedgerDev* ledger, const LedgerConst& lc, int c3_log2,
+                    float inv_sc, float inv_sf, void* stream);
 // fill the 32-bit tables of every level whose addressed arrays allow them
 void narrow_tables(Mesh* m);
 int launch_fill(void* f, int esize, long long n_blocks, int B, const double dev[27], void* stream);

@@ -358,46 +358,271 @@ __global__ void __launch_bounds__(256) k_segments(const double* __restrict__ lin
   }
 }
 
+// ---------------------------------------------------------------- interface ledger
+
+// a population deviation in the ledger's fixed point (quantum 2^-40): exact for
+// binary16 values (11 significant bits times 2^-13), rounded at 2^-41 for
+// FP32 values below 2^-17 and for FP64 values
+__device__ __forceinline__ long long fx40(float v) { return __float2ll_rn(v * 0x1p40f); }
+__device__ __forceinline__ long long fx40(double v) { return __double2ll_rn(v * 0x1p40); }
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Adds NF flows of every thread's entry (q[f]: fixed-point population values
+// of direction dir, dir < 0 for a thread without an entry) to the ledger's
+// values [4 first, 4 first + 4 NF): mass and the three momentum components.
+// Warps whose entries share one direction (the tables are ordered by
+// destination slot, so most do) sum one value per flow, the others four;
+// lanes 0..4 NF - 1 then add the warp's sums to one of the kLedgerCopies
+// copies (chosen by warp), so no CTA-wide barrier is needed.  Every lane of
+// the warp must call it.
+template <int NF>
+__device__ __forceinline__ void ledger_add(LedgerDev* __restrict__ L, int first, const long long (&q)[NF], int dir) {
+  const int lane = threadIdx.x & 31;
+  const int d0 = __reduce_max_sync(0xffffffffu, dir);
+  const bool uni = __all_sync(0xffffffffu, dir < 0 || dir == d0);
+  long long mine = 0;  // lane 4 f + c holds component c of flow f
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    if (uni) {
+      const long long m = warp_sum_ll(q[f]);  // valid in lane 0
+      const long long mb = __shfl_sync(0xffffffffu, m, 0);
+      const int c = lane - 4 * f;
+      if (c >= 0 && c < 4 && d0 >= 0) mine = c == 0 ? mb : (c == 1 ? dcx(d0) : (c == 2 ? dcy(d0) : dcz(d0))) * mb;
+    } else {
+      const int cxx = dir < 0 ? 0 : dcx(dir), cyy = dir < 0 ? 0 : dcy(dir), czz = dir < 0 ? 0 : dcz(dir);
+      const long long v[4] = {q[f], cxx * q[f], cyy * q[f], czz * q[f]};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const long long sum = __shfl_sync(0xffffffffu, warp_sum_ll(v[c]), 0);
+        if (lane == 4 * f + c) mine = sum;
+      }
+    }
+  }
+  if (lane < 4 * NF && mine) {
+    const int copy = (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kLedgerCopies);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&L->acc[copy][first + lane]), (unsigned long long)mine);
+  }
+}
+
+// A warp's running ledger sum over consecutive rounds of entries that share
+// one direction: entries add to it while the warp's direction stays the
+// same, and it is reduced and added to the ledger only when the direction
+// changes and at the end (one reduction per run instead of one per round).
+struct LedgerRun {
+  long long acc = 0;
+  int dir = -1;  // the run's direction, the same in every lane
+};
+__device__ __forceinline__ void ledger_flush(LedgerRun& r, LedgerDev* __restrict__ L, int first) {
+  if (r.dir >= 0) {
+    const long long q[1] = {r.acc};
+    ledger_add<1>(L, first, q, r.dir);
+  }
+  r.acc = 0;
+  r.dir = -1;
+}
+__device__ __forceinline__ void ledger_run_add(LedgerRun& r, LedgerDev* __restrict__ L, int first, long long q,
+                                               int dir) {
+  const int d0 = __reduce_max_sync(0xffffffffu, dir);
+  const bool uni = __all_sync(0xffffffffu, dir < 0 || dir == d0);
+  if (uni && (d0 < 0 || r.dir < 0 || d0 == r.dir)) {
+    r.acc += q;
+    if (d0 >= 0) r.dir = d0;
+    return;
+  }
+  ledger_flush(r, L, first);
+  if (uni) {
+    r.acc = q;
+    r.dir = d0;
+  } else {
+    const long long qq[1] = {q};
+    ledger_add<1>(L, first, qq, dir);
+  }
+}
+
+// entries per thread of the explode and inflow transfers: a warp walks
+// kIfaceRounds consecutive rounds of 32 entries.  One: more entries per
+// thread cut the ledger's reductions but slowed the transfers' dependent
+// gathers more (GB300, two-level tree workload: 4 rounds, interface kernels
+// 78.5 -> 85.7 us per coarse step without the ledger).
+constexpr int kIfaceRounds = 1;
+
+// population plane of an element offset (log2 of the cells per block given)
+__device__ __forceinline__ int plane_of(long long off, int c3_log2) { return (int)((off >> c3_log2) % 27); }
+
+// a 64-bit integer as float with round-to-odd (truncated, last bit set when
+// inexact): rounding that to binary16 gives the correctly rounded binary16 of
+// the integer (float keeps more than two bits beyond binary16's eleven)
+__device__ __forceinline__ float ll_to_float_odd(long long q) {
+  const float z = __ll2float_rz(q);
+  if (__float2ll_rz(z) == q) return z;
+  return __uint_as_float(__float_as_uint(z) | 1u);
+}
+
 // Interface kernels.  ratio = s_fine / s_coarse maps stored coarse values to
 // the fine scale (1 for FP32 and FP64); saved values are fine-scaled values of
 // the arithmetic type (FP32, FP64 for the double-precision form).
 template <typename S, typename E, typename SE>
-__global__ void k_explode(S* __restrict__ fine, const S* __restrict__ coarse, const E* __restrict__ e, int ne,
-                          const SE* __restrict__ s, int ns, typename Store<S>::V* __restrict__ saved, int parity,
-                          float ratio) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < ne) {
-    const E x = e[t];
-    Store<S>::st(fine, x.dst, Store<S>::ld(coarse, parity ? x.src[1] : x.src[0]) * ratio);
+__global__ void __launch_bounds__(256) k_explode(S* __restrict__ fine, const S* __restrict__ coarse,
+                                                 const E* __restrict__ e, int ne, const SE* __restrict__ s, int ns,
+                                                 typename Store<S>::V* __restrict__ saved, int parity, float ratio,
+                                                 LedgerDev* __restrict__ ledger, int c3_log2, float inv_sf) {
+  using V = typename Store<S>::V;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * kIfaceRounds);
+  LedgerRun run;
+#pragma unroll
+  for (int k = 0; k < kIfaceRounds; ++k) {
+    const long long t = w0 + 32 * k + lane;
+    long long q = 0;
+    int dir = -1;
+    if (t < ne) {
+      const E x = e[t];
+      const V v = Store<S>::ld(coarse, parity ? x.src[1] : x.src[0]) * ratio;
+      Store<S>::st(fine, x.dst, v);
+      if (ledger) {
+        q = fx40(v * (V)inv_sf);
+        dir = 26 - plane_of(x.dst, c3_log2);
+      }
+    }
+    if (t < ns) saved[t] = Store<S>::ld(fine, s[t].src);
+    if (ledger) ledger_run_add(run, ledger, 0, q, dir);
   }
-  if (t < ns) saved[t] = Store<S>::ld(fine, s[t].src);
+  if (ledger) ledger_flush(run, ledger, 0);
 }
 
 template <typename S, typename E>
-__global__ void k_inflow(S* __restrict__ fine, const S* __restrict__ coarse, const E* __restrict__ e, int n,
-                         const typename Store<S>::V* __restrict__ saved, int parity, float ratio) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const E x = e[t];
-  Store<S>::st(fine, x.dst, x.r >= 0 ? saved[x.r] : Store<S>::ld(coarse, parity ? x.csrc[1] : x.csrc[0]) * ratio);
+__global__ void __launch_bounds__(256) k_inflow(S* __restrict__ fine, const S* __restrict__ coarse,
+                                                const E* __restrict__ e, int n,
+                                                const typename Store<S>::V* __restrict__ saved, int parity,
+                                                float ratio, LedgerDev* __restrict__ ledger, int c3_log2,
+                                                float inv_sf) {
+  using V = typename Store<S>::V;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * kIfaceRounds);
+  LedgerRun run;
+#pragma unroll
+  for (int k = 0; k < kIfaceRounds; ++k) {
+    const long long t = w0 + 32 * k + lane;
+    long long q = 0;
+    int dir = -1;
+    if (t < n) {
+      const E x = e[t];
+      if (x.r >= 0) {
+        Store<S>::st(fine, x.dst, saved[x.r]);  // a fine value back into the fine level: no flow
+      } else {
+        const V v = Store<S>::ld(coarse, parity ? x.csrc[1] : x.csrc[0]) * ratio;
+        Store<S>::st(fine, x.dst, v);
+        if (ledger) {
+          q = fx40(v * (V)inv_sf);
+          dir = plane_of(x.dst, c3_log2);
+        }
+      }
+    }
+    if (ledger) ledger_run_add(run, ledger, 0, q, dir);
+  }
+  if (ledger) ledger_flush(run, ledger, 0);
 }
 
+// Coarse cell next to the fine region, one direction: the mean of its 8
+// children's values (fine values, or n_coarse times its own coarse value),
+// summed exactly and rounded to storage once.  In the reduced forms the sum
+// is taken in 64-bit fixed point (deviations x 2^40: exact for binary16
+// values, within 2^-41 per value in FP32, far below one FP32 unit of any
+// deviation above 1e-5), then rounded once (FP32: the integer to nearest
+// float; binary16: via round-to-odd float); the FP64 form sums in FP64.
+// With a ledger: the fine values taken (OutF) and what the coarse slot
+// receives, 8 x stored - n_coarse x old (RecvC); the launch's last CTA folds
+// the coarse step's sums into the FP64 records.
 template <typename S, typename E>
 __global__ void k_coalesce(S* __restrict__ coarse, const S* __restrict__ fine, const E* __restrict__ e, int n,
-                           const typename Store<S>::V* __restrict__ saved, int parity, float ratio) {
+                           const typename Store<S>::V* __restrict__ saved, int parity, float ratio,
+                           LedgerDev* __restrict__ ledger, LedgerConst lc, int c3_log2, float inv_sc, float inv_sf) {
   using V = typename Store<S>::V;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const E& x = e[t];
-  const long long dst = parity ? x.dst[1] : x.dst[0];
-  V vf = 0.0f;
-  for (int k = 0; k < x.nfine; ++k) {
-    const long long s = x.fsrc[k];
-    vf += s >= 0 ? Store<S>::ld(fine, s) : saved[-s - 1];
+  long long q[2] = {0, 0};
+  int dir = -1;
+  if (t < n) {
+    const E& x = e[t];
+    const long long dst = parity ? x.dst[1] : x.dst[0];
+    const V vc = x.ncoarse ? Store<S>::ld(coarse, dst) : (V)0;
+    if constexpr (sizeof(V) == 4) {
+      long long qf = 0;  // the fine values' deviations, fixed point
+      for (int k = 0; k < x.nfine; ++k) {
+        const long long s = x.fsrc[k];
+        qf += fx40((s >= 0 ? Store<S>::ld(fine, s) : saved[-s - 1]) * inv_sf);
+      }
+      const long long qc = x.ncoarse ? fx40(vc * inv_sc) : 0;
+      const long long qt = qf + x.ncoarse * qc;  // 8 x the new deviation, fixed point
+      // the new stored value: qt x 2^-43 deviations x the coarse scale, one rounding
+      float stored;
+      if constexpr (std::is_same<S, __half>::value) {
+        const __half h = __float2half_rn(ll_to_float_odd(qt) * (0x1p-43f / inv_sc));
+        coarse[dst] = h;
+        stored = __half2float(h);
+      } else {
+        stored = __ll2float_rn(qt) * 0x1p-43f;
+        Store<S>::st(coarse, dst, stored);
+      }
+      if (ledger) {
+        q[0] = qf;
+        // 8 x the stored deviation x 2^40 is an integer in both forms (the
+        // rounded qt in FP32, a binary16 value x 2^30): exact
+        q[1] = __float2ll_rn(stored * (0x1p43f * inv_sc)) - x.ncoarse * qc;
+      }
+    } else {
+      V acc = 0;
+      long long qf = 0;
+      for (int k = 0; k < x.nfine; ++k) {
+        const long long s = x.fsrc[k];
+        const V v = s >= 0 ? Store<S>::ld(fine, s) : saved[-s - 1];
+        acc += v;
+        if (ledger) qf += fx40(v);
+      }
+      const V stored = (acc / (V)ratio + (V)x.ncoarse * vc) * 0.125;
+      Store<S>::st(coarse, dst, stored);
+      if (ledger) {
+        q[0] = qf;
+        q[1] = 8 * fx40(stored) - (long long)x.ncoarse * fx40(vc);
+      }
+    }
+    if (ledger) {
+      const int pl = plane_of(dst, c3_log2);
+      dir = parity ? pl : 26 - pl;
+    }
   }
-  V v = vf / ratio;
-  if (x.ncoarse) v += (V)x.ncoarse * Store<S>::ld(coarse, dst);
-  Store<S>::st(coarse, dst, v * 0.125f);
+  if (!ledger) return;
+  ledger_add<2>(ledger, 4, q, dir);
+  // the last CTA of the launch folds the step's sums (explode, inflow and this
+  // launch) into the FP64 records and clears them for the next coarse step
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&ledger->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < kLedgerVals) {
+    const int k = threadIdx.x;
+    long long sum = 0;
+    for (int c = 0; c < kLedgerCopies; ++c) {
+      sum += (long long)__ldcg(reinterpret_cast<const unsigned long long*>(&ledger->acc[c][k]));
+      ledger->acc[c][k] = 0;
+    }
+    const double v = lc.vol * ((double)sum * 0x1p-40 + lc.c[k]);
+    ledger->last[k] = v;
+    ledger->total[k] += v;
+  }
+  if (threadIdx.x == 0) {
+    ledger->steps += 1.0;
+    ledger->done = 0u;
+  }
 }
 
 // one CTA per (storage block, population plane): the plane's C3 values are
@@ -743,64 +968,74 @@ int launch_segments(const double* link_force, const int* seg_begin, int n_seg, d
 
 template <typename E, typename SE>
 void explode_typed(void* fine, const void* coarse, int esize, float ratio, const E* e, int ne, const SE* sv, int ns,
-                   void* saved, int parity, cudaStream_t s) {
-  const unsigned g = blocks_for(ne > ns ? ne : ns, 256);
+                   void* saved, int parity, LedgerDev* ledger, int c3_log2, float inv_sf, cudaStream_t s) {
+  const unsigned g = blocks_for(ne > ns ? ne : ns, 256 * kIfaceRounds);
   by_storage(esize, [&](auto* tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     using V = typename Store<S>::V;
-    k_explode<S, E, SE><<<g, 256, 0, s>>>((S*)fine, (const S*)coarse, e, ne, sv, ns, (V*)saved, parity, ratio);
+    k_explode<S, E, SE><<<g, 256, 0, s>>>((S*)fine, (const S*)coarse, e, ne, sv, ns, (V*)saved, parity, ratio, ledger,
+                                           c3_log2, inv_sf);
   });
 }
 
 int launch_explode(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int ne,
-                   const void* sv, int ns, void* saved, int parity, void* stream) {
+                   const void* sv, int ns, void* saved, int parity, LedgerDev* ledger, int c3_log2, float inv_sf,
+                   void* stream) {
   if (ne == 0 && ns == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (narrow)
     explode_typed(fine, coarse, esize, ratio, (const ExplodeEntryN*)e, ne, (const SaveEntryN*)sv, ns, saved, parity,
-                  s);
+                  ledger, c3_log2, inv_sf, s);
   else
-    explode_typed(fine, coarse, esize, ratio, (const ExplodeEntry*)e, ne, (const SaveEntry*)sv, ns, saved, parity, s);
+    explode_typed(fine, coarse, esize, ratio, (const ExplodeEntry*)e, ne, (const SaveEntry*)sv, ns, saved, parity,
+                  ledger, c3_log2, inv_sf, s);
   return check_launch("explode");
 }
 
 template <typename E>
 void inflow_typed(void* fine, const void* coarse, int esize, float ratio, const E* e, int n, const void* saved,
-                  int parity, cudaStream_t s) {
+                  int parity, LedgerDev* ledger, int c3_log2, float inv_sf, cudaStream_t s) {
   by_storage(esize, [&](auto* tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     using V = typename Store<S>::V;
-    k_inflow<S, E><<<blocks_for(n, 256), 256, 0, s>>>((S*)fine, (const S*)coarse, e, n, (const V*)saved, parity,
-                                                       ratio);
+    k_inflow<S, E><<<blocks_for(n, 256 * kIfaceRounds), 256, 0, s>>>((S*)fine, (const S*)coarse, e, n, (const V*)saved, parity,
+                                                       ratio, ledger, c3_log2, inv_sf);
   });
 }
 
 int launch_inflow(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int n,
-                  const void* saved, int parity, void* stream) {
+                  const void* saved, int parity, LedgerDev* ledger, int c3_log2, float inv_sf, void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (narrow) inflow_typed(fine, coarse, esize, ratio, (const InflowEntryN*)e, n, saved, parity, s);
-  else inflow_typed(fine, coarse, esize, ratio, (const InflowEntry*)e, n, saved, parity, s);
+  if (narrow)
+    inflow_typed(fine, coarse, esize, ratio, (const InflowEntryN*)e, n, saved, parity, ledger, c3_log2, inv_sf, s);
+  else inflow_typed(fine, coarse, esize, ratio, (const InflowEntry*)e, n, saved, parity, ledger, c3_log2, inv_sf, s);
   return check_launch("inflow");
 }
 
 template <typename E>
 void coalesce_typed(void* coarse, const void* fine, int esize, float ratio, const E* e, int n, const void* saved,
-                    int parity, cudaStream_t s) {
+                    int parity, LedgerDev* ledger, const LedgerConst& lc, int c3_log2, float inv_sc, float inv_sf,
+                    cudaStream_t s) {
   by_storage(esize, [&](auto* tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     using V = typename Store<S>::V;
     k_coalesce<S, E><<<blocks_for(n, 256), 256, 0, s>>>((S*)coarse, (const S*)fine, e, n, (const V*)saved, parity,
-                                                         ratio);
+                                                         ratio, ledger, lc, c3_log2, inv_sc, inv_sf);
   });
 }
 
 int launch_coalesce(void* coarse, const void* fine, int esize, float ratio, const void* e, int narrow, int n,
-                    const void* saved, int parity, void* stream) {
+                    const void* saved, int parity, LedgerDev* ledger, const LedgerConst& lc, int c3_log2,
+                    float inv_sc, float inv_sf, void* stream) {
   if (n == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (narrow) coalesce_typed(coarse, fine, esize, ratio, (const CoalesceEntryN*)e, n, saved, parity, s);
-  else coalesce_typed(coarse, fine, esize, ratio, (const CoalesceEntry*)e, n, saved, parity, s);
+  if (narrow)
+    coalesce_typed(coarse, fine, esize, ratio, (const CoalesceEntryN*)e, n, saved, parity, ledger, lc, c3_log2,
+                   inv_sc, inv_sf, s);
+  else
+    coalesce_typed(coarse, fine, esize, ratio, (const CoalesceEntry*)e, n, saved, parity, ledger, lc, c3_log2, inv_sc,
+                   inv_sf, s);
   return check_launch("coalesce");
 }
 

@@ -82,6 +82,9 @@ def _load():
         "lbm_get_velocity": ([vp, i, dp, dp, sz], i),
         "lbm_mass": ([vp, dp, dp], i),
         "lbm_mass_noalloc": ([vp, dp, dp], i),
+        "lbm_level_mass": ([vp, i, dp, dp], i),
+        "lbm_set_interface_ledger": ([vp, i], i),
+        "lbm_interface_ledger": ([vp, i, dp, dp, llp], i),
         "lbm_level_info": ([vp, i, ip, ip, llp, llp, llp], i),
         "lbm_geometry_info": ([vp, dp, dp, ip, dp], i),
         "lbm_get_cell_types": ([vp, i, ubp, sz], i),
@@ -257,6 +260,23 @@ def lbm_mass_noalloc(h):
     m, p = C.c_double(), np.zeros(3)
     _ck(_lib.lbm_mass_noalloc(h, C.byref(m), _dp(p)), "lbm_mass_noalloc")
     return m.value, p
+
+
+def lbm_level_mass(h, level):
+    m, p = C.c_double(), np.zeros(3)
+    _ck(_lib.lbm_level_mass(h, level, C.byref(m), _dp(p)), "lbm_level_mass")
+    return m.value, p
+
+
+def lbm_set_interface_ledger(h, on):
+    return _ck(_lib.lbm_set_interface_ledger(h, int(bool(on))), "lbm_set_interface_ledger")
+
+
+def lbm_interface_ledger(h, level):
+    """(last coarse step's 12 values, totals, steps): In, OutF, RecvC x (mass, jx, jy, jz)."""
+    last, total, n = np.zeros(12), np.zeros(12), C.c_longlong()
+    _ck(_lib.lbm_interface_ledger(h, level, _dp(last), _dp(total), C.byref(n)), "lbm_interface_ledger")
+    return last, total, n.value
 
 
 def lbm_geometry_info(h):
