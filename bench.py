@@ -159,55 +159,66 @@ def precision_form(L, W, torch, stream, steps, warmup, peak):
     return out
 
 
-def batched_form(L, W, torch, stream, steps, peak):
+def batched_form(L, W, torch, stream, steps, peak, blocks=(16, 8)):
     """The 16-case batched form: the cases stepped one after another (each by
     its own CUDA graph) against the batch (one persistent collide launch per
-    level depth and sub-step, one graph per coarse step), schedule from the
-    autotuner."""
-    doms, updates = [], 0
-    for c in W.batch_cases():
-        desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
-                             re_h=c["re_h"], i_u=c["i_u"], seed=c["seed"])
-        d = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=stream)
-        updates += d.work_per_step()[0]
-        doms.append(d)
-    blocks = [L.lbm_level_info(d.h, 0)["n_active_blocks"] for d in doms]
+    level depth and sub-step, one graph per coarse step).  The tuner picks the
+    block size (the cases built in 16^3 and in 8^3 blocks) and, per block
+    size, the batch schedule (lbm_batch_autotune)."""
+    per_block = {}
+    for bsz in blocks:
+        doms, updates = [], 0
+        for c in W.batch_cases():
+            desc = L.domain_desc(*c["n0"], levels=c["levels"], block=bsz, bc=c["bc"], u_in=c["u_in"],
+                                 re_h=c["re_h"], i_u=c["i_u"], seed=c["seed"])
+            d = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=stream)
+            updates += d.work_per_step()[0]
+            doms.append(d)
+        nblocks = [L.lbm_level_info(d.h, 0)["n_active_blocks"] for d in doms]
 
-    def timed(fn):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
+        def timed(fn):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
 
-    def sequential(n):
-        for _ in range(n):
-            for d in doms:
-                d.step(1)
+        def sequential(n):
+            for _ in range(n):
+                for d in doms:
+                    d.step(1)
 
-    sequential(3)
-    ms_seq = timed(lambda: sequential(steps))
-    batch = L.Batch(doms, stream=stream)
-    best, tune_ms = batch.autotune(steps=3)
-    batch.step(3)
-    ms_batch = timed(lambda: batch.step(steps))
-    batch.close()
-    gb = sum(d.nbytes for d in doms) / 1e9
-    for d in doms:
-        d.close()
-    torch.cuda.empty_cache()
-    seq = updates * steps / (ms_seq / 1e3) / 1e6
-    bat = updates * steps / (ms_batch / 1e3) / 1e6
+        sequential(3)
+        ms_seq = timed(lambda: sequential(steps))
+        batch = L.Batch(doms, stream=stream)
+        best, tune_ms = batch.autotune(steps=3)
+        batch.step(3)
+        ms_batch = timed(lambda: batch.step(steps))
+        batch.close()
+        gb = sum(d.nbytes for d in doms) / 1e9
+        for d in doms:
+            d.close()
+        torch.cuda.empty_cache()
+        per_block[bsz] = {"value": updates * steps / (ms_batch / 1e3) / 1e6,
+                          "sequential_value": updates * steps / (ms_seq / 1e3) / 1e6,
+                          "ms_per_step": ms_batch / steps, "sequential_ms_per_step": ms_seq / steps,
+                          "updates_per_step": updates, "device_gb": gb, "schedule": best.as_dict(),
+                          "autotune_ms_per_step": tune_ms, "coarse_blocks": [min(nblocks), max(nblocks)]}
+    bsz = max(per_block, key=lambda k: per_block[k]["value"])
+    r = per_block[bsz]
     return {"workload": "16 cases: trees of 1-4 child generations x Re_H {2.5e3, 1e4, 4e4, 1.2e5}, 2-3 levels, "
-                        "16^3 blocks (%d-%d coarse blocks per case), I_u = 8 %% random-Fourier-mode inflow in half "
-                        "of them" % (min(blocks), max(blocks)),
-            "unit": "MLUPS", "steps": steps, "updates_per_step": updates, "device_gb": gb,
-            "value": bat, "sequential_value": seq, "speedup_vs_sequential": bat / seq,
-            "ms_per_step": ms_batch / steps, "sequential_ms_per_step": ms_seq / steps,
-            "schedule": best.as_dict(), "autotune_ms_per_step": tune_ms,
-            "path_frac": updates * BYTES_PER_UPDATE * steps / (ms_batch / 1e3) / 1e9 / peak}
+                        "I_u = 8 %% random-Fourier-mode inflow in half of them; block size picked by the tuner "
+                        "(%d^3: %d-%d coarse blocks per case)" % (bsz, *r["coarse_blocks"]),
+            "unit": "MLUPS", "steps": steps, "block": bsz, "updates_per_step": r["updates_per_step"],
+            "device_gb": r["device_gb"], "value": r["value"], "sequential_value": r["sequential_value"],
+            "speedup_vs_sequential": r["value"] / r["sequential_value"], "ms_per_step": r["ms_per_step"],
+            "sequential_ms_per_step": r["sequential_ms_per_step"], "schedule": r["schedule"],
+            "autotune_ms_per_step": r["autotune_ms_per_step"],
+            "path_frac": r["value"] * 1e6 * BYTES_PER_UPDATE / 1e9 / peak,
+            "per_block_size": {str(k): {kk: v[kk] for kk in ("value", "sequential_value", "schedule")}
+                               for k, v in per_block.items()}}
 
 
 class Clocks:
@@ -349,6 +360,9 @@ def main():
     ap.add_argument("--precision-steps", type=int, default=10)
     ap.add_argument("--timing-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--learned-form", type=float, default=0.0,
+                    help="also run the learned form at this fraction of its full data set (1: ~1.9e5 branch samples, "
+                         "about 16 GPU-minutes) and add its report")
     ap.add_argument("--cd-steps", type=int, default=300,
                     help="coarse steps of the scaled-down case for the C_D comparison with the oracle")
     ap.add_argument("--schedule", default=None,
@@ -490,6 +504,16 @@ def main():
     if not args.no_batched_form:
         batched = batched_form(L, W, torch, stream, args.batched_steps, peak)
 
+    learned = None
+    if args.learned_form > 0:
+        from paper_2603_27954_gb300 import surrogate as SG
+        counts = {k: max(1, int(round(v * args.learned_form))) for k, v in W.LEARNED_COUNTS.items()}
+        learned, ens = SG.learned_form(stream=stream, counts=counts)
+        for members in ens.values():
+            for m in members:
+                m.close()
+        learned["scale"] = args.learned_form
+
     cpu = None
     cd_err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -547,6 +571,7 @@ def main():
                         "drag (64 bytes) after each of %d steps; bytes per step = the upload over those steps" % (
                             uploaded / 1e6, pop_bytes / 1e9, args.e2e_steps)},
         "interface_ledger": ledger,
+        "learned_form": learned,
         "precision_form": prec_form,
         "batched_form": batched,
         "gpu_launches": kernels * args.steps,

@@ -77,7 +77,14 @@ typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_DEV = 2 } lbm_precision;
    even step runs the same packed code in both lanes and equals it bit for
    bit).  Defaults: column pointers and the direct even step for FP32, pairs
    in both steps for FP16; lbm_autotune measures all of them. */
-typedef enum { LBM_ODD_COLUMNS = 0, LBM_ODD_STAGED = 1, LBM_ODD_DIRECT = 2, LBM_ODD_PAIRS = 3 } lbm_odd_variant;
+typedef enum {
+  LBM_ODD_COLUMNS = 0,
+  LBM_ODD_STAGED = 1,
+  LBM_ODD_DIRECT = 2,
+  LBM_ODD_PAIRS = 3,   /* registers budgeted for 6 resident CTAs per SM */
+  LBM_ODD_PAIRS_7 = 4, /* the same kernel budgeted for 7 (72 registers, a few spills; 16^3 blocks) */
+  LBM_ODD_PAIRS_8 = 5  /* ... for 8 (64 registers, more spills; 16^3 blocks) */
+} lbm_odd_variant;
 typedef enum { LBM_EVEN_DIRECT = 0, LBM_EVEN_TMA = 1, LBM_EVEN_PAIRS = 2 } lbm_even_variant;
 
 /* Problem statement (Sec. 2.2-2.3): domain, inflow, Re_H, refinement.
@@ -322,6 +329,16 @@ int lbm_branch_table(const lbm_domain* d, double* rows, int n, int* count);
 int lbm_branch_drag_estimate(const double* rows, int n, const double* c_sect, double area, double* cd_est,
                              double* c_out);
 
+/* The measured sectional coefficients of Eq. 3 (Sec. 2.4), rho = 1:
+   c_drag[k] = mean F_x,k / (U^2 L_k D_k / 2) from the per-branch forces
+   averaged since the last lbm_reset_force (lbm_set_branch_forces must be on),
+   c_fric[k] the same from the per-branch friction means
+   (lbm_set_friction_mean; zeros while it is off); *cd = mean F_x /
+   (U^2 A_x / 2) over the same window (Eq. 7), *cf the friction's (NaN while
+   the friction mean is off).  Any pointer may be NULL; n is the capacity
+   in branches.  Host arithmetic after reading the device sums; synchronises. */
+int lbm_branch_coefficients(lbm_domain* d, double* c_drag, double* c_fric, int n, double* cd, double* cf);
+
 /* ---- Friction and pressure drag (Sec. 3: C_F from the wall shear stress
    integrated over the tree surface, C_P = C_D - C_F) ----
    The surface of every primitive is covered by quadrature points (spacing
@@ -374,6 +391,11 @@ int lbm_mlp_get_params(lbm_mlp* m, float* host, long long n);
 int lbm_mlp_set_normalization(lbm_mlp* m, const float* mu_x, const float* sd_x, float mu_y, float sd_y);
 /* y[b] = prediction (de-standardised) for x[b]; asynchronous */
 int lbm_mlp_forward(lbm_mlp* m, const float* x, int batch, float* y);
+/* y[b] = the mean prediction of n networks (an ensemble trained from
+   different seeds) for x[b]: every member's forward pass and the running
+   mean on the device, asynchronously.  Members must share n_in and the
+   stream and have capacity for the batch. */
+int lbm_mlp_ensemble_forward(lbm_mlp* const* nets, int n, const float* x, int batch, float* y);
 /* loss and the gradient of the loss with respect to the parameters (host
    array of lbm_mlp_param_count floats, may be NULL); synchronises */
 int lbm_mlp_gradients(lbm_mlp* m, const float* x, const float* y, const int* idx, int batch, float* grad_host,
@@ -432,9 +454,12 @@ int lbm_autotune(lbm_domain* d, int steps, lbm_schedule* best, double* ms_per_st
    interface kernels follow on the batch's stream, and each coarse step of
    the whole batch is one CUDA graph launch.  Results are identical to
    stepping each domain alone.  The batch binds its own small device buffer
-   (descriptors and work lists).  Batches take the column-pointer or direct
-   odd step and the direct even step.  The domains must outlive the batch
-   and must not be stepped on their own while they are in it. */
+   (descriptors and work lists).  Batches take the column-pointer, direct or
+   paired (two cells per thread, 6 CTAs per SM) odd step and the direct or
+   paired even step; lbm_batch_autotune times every combination at one CTA
+   per work unit, then persistent grids for the best, then the z splits.
+   FP32 or FP16 storage.  The domains must outlive the batch and must not
+   be stepped on their own while they are in it. */
 typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_domain* const* domains, int n, void* cuda_stream, lbm_batch** out);
 int lbm_batch_memory_requirements(const lbm_batch* b, size_t* bytes);

@@ -1293,6 +1293,38 @@ int lbm_branch_table(const lbm_domain* d, double* rows, int n, int* count) {
   return LBM_OK;
 }
 
+int lbm_branch_coefficients(lbm_domain* d, double* c_drag, double* c_fric, int n, double* cd, double* cf) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  if (!d->have_tree) return fail(LBM_ESTATE, "no tree: set the geometry from a tree or segments");
+  const int nb = d->tree.count();
+  if ((c_drag || c_fric) && n < nb) return fail(LBM_EINVAL, "capacity below the number of branches");
+  const double u = d->d.u_in, q = 0.5 * u * u;
+  if (!(q > 0)) return fail(LBM_ESTATE, "no inflow speed to normalise by");
+  std::vector<double> fb((size_t)std::max(1, nb) * 3), fr((size_t)std::max(1, nb) * 3);
+  long long steps = 0;
+  int rc = lbm_get_branch_forces(d, fb.data(), nb, &steps);
+  if (rc) return rc;
+  double fmean[3] = {0, 0, 0};
+  long long fsteps = 0;
+  if (d->friction_mean && (rc = lbm_get_friction_mean(d, fmean, fr.data(), nb, &fsteps))) return rc;
+  double mean[3];
+  if ((rc = lbm_drag(d, nullptr, mean, nullptr))) return rc;
+  // Eq. (3): F_d,k = c_k (rho U^2 / 2) L_k D_k, rho = 1; segment rows hold L and D
+  for (int k = 0; k < nb; ++k) {
+    const double* sg = &d->tree.seg[8 * (size_t)k];
+    const double len = std::sqrt((sg[3] - sg[0]) * (sg[3] - sg[0]) + (sg[4] - sg[1]) * (sg[4] - sg[1]) +
+                                 (sg[5] - sg[2]) * (sg[5] - sg[2]));
+    const double ld = q * len * sg[6];
+    if (c_drag) c_drag[k] = steps > 0 ? fb[3 * (size_t)k] / ld : 0.0;
+    if (c_fric) c_fric[k] = fsteps > 0 ? fr[3 * (size_t)k] / ld : 0.0;
+  }
+  // Eq. (7) over the same window: C_D = F_x / (rho U^2 A_x / 2), and C_F likewise
+  if (cd) *cd = d->A_x > 0 ? mean[0] / (q * d->A_x) : std::numeric_limits<double>::quiet_NaN();
+  if (cf) *cf = d->A_x > 0 && fsteps > 0 ? fmean[0] / (q * d->A_x) : std::numeric_limits<double>::quiet_NaN();
+  return LBM_OK;
+}
+
 int lbm_branch_drag_estimate(const double* rows, int n, const double* c_sect, double area, double* cd_est,
                              double* c_out) {
   if (!rows || !cd_est || n < 0 || !(area > 0)) return fail(LBM_EINVAL, "bad argument");
@@ -1586,7 +1618,8 @@ void lbm_destroy(lbm_domain* d) {
 namespace {
 
 bool variant_ok(const lbm_domain* d, int odd, int even) {
-  if (odd < LBM_ODD_COLUMNS || odd > LBM_ODD_PAIRS || even < LBM_EVEN_DIRECT || even > LBM_EVEN_PAIRS) return false;
+  if (odd < LBM_ODD_COLUMNS || odd > LBM_ODD_PAIRS_8 || even < LBM_EVEN_DIRECT || even > LBM_EVEN_PAIRS) return false;
+  if ((odd == LBM_ODD_PAIRS_7 || odd == LBM_ODD_PAIRS_8) && d->d.block != 16) return false;
   // the FP64 form has one kernel per parity (direct addressing)
   if (d->d.precision == LBM_FP64) return (odd == LBM_ODD_COLUMNS || odd == LBM_ODD_DIRECT) && even == LBM_EVEN_DIRECT;
   const bool staged_ok = d->d.precision == LBM_FP32 && d->d.block == 16;
@@ -1661,7 +1694,7 @@ int lbm_autotune(lbm_domain* d, int steps, lbm_schedule* best, double* ms_per_st
   // coordinate search: the kernel variants at the current z splits, then the
   // even step's split, then the odd step's
   const lbm_schedule start = b;
-  for (int odd = LBM_ODD_COLUMNS; odd <= LBM_ODD_PAIRS; ++odd)
+  for (int odd = LBM_ODD_COLUMNS; odd <= LBM_ODD_PAIRS_8; ++odd)
     for (int even = LBM_EVEN_DIRECT; even <= LBM_EVEN_PAIRS; ++even) {
       if (!variant_ok(d, odd, even)) continue;
       lbm_schedule c = start;
@@ -1755,7 +1788,7 @@ int batch_advance(lbm_batch* b, int l, int parity) {
   const int grid = b->sched.ctas_per_sm > 0 ? b->sched.ctas_per_sm * b->sms : 0;
   int rc = launch_collide_batch(reinterpret_cast<const CollideArgs*>(b->base + b->off_descs),
                                 reinterpret_cast<const int2*>(b->base + b->off_items[l]), (int)b->items[l].size(), b->B,
-                                parity, b->sched.odd_variant, b->half, b->wide, grid,
+                                parity, b->sched.odd_variant, b->sched.even_variant, b->half, b->wide, grid,
                                 batch_zshift(b, l, parity), b->stream);
   if (rc) return fail(rc, cuda_error_string());
   if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) {
@@ -1893,12 +1926,15 @@ int lbm_batch_bind_memory(lbm_batch* b, void* ptr, size_t bytes) {
 
 int lbm_batch_set_schedule(lbm_batch* b, const lbm_schedule* s) {
   if (!b || !s) return fail(LBM_EINVAL, "null argument");
-  if (s->ctas_per_sm < 0 || s->ctas_per_sm > 64 || (s->odd_variant != LBM_ODD_COLUMNS && s->odd_variant != LBM_ODD_DIRECT))
-    return fail(LBM_EINVAL, "batches take column-pointer or direct odd steps and 0..64 CTAs per SM");
+  if (s->ctas_per_sm < 0 || s->ctas_per_sm > 64 ||
+      (s->odd_variant != LBM_ODD_COLUMNS && s->odd_variant != LBM_ODD_DIRECT && s->odd_variant != LBM_ODD_PAIRS) ||
+      (s->even_variant != LBM_EVEN_DIRECT && s->even_variant != LBM_EVEN_PAIRS))
+    return fail(LBM_EINVAL,
+                "batches take column-pointer, direct or paired odd steps, direct or paired even steps and 0..64 CTAs "
+                "per SM");
   if (zshift_req(s->z_split_even, b->B) == -1 || zshift_req(s->z_split_odd, b->B) == -1)
     return fail(LBM_EINVAL, "z splits must be 0 or a power of two up to the block size");
   b->sched = *s;
-  b->sched.even_variant = LBM_EVEN_DIRECT;
   free_batch_graphs(b);
   for (lbm_domain* d : b->doms) free_graphs(d);
   if (b->base) return upload_descs(b);
@@ -1970,13 +2006,23 @@ int lbm_batch_autotune(lbm_batch* b, int steps, lbm_schedule* best, double* ms_p
   // coordinate search: odd variant and persistent grid at the current z
   // splits, then the even step's split, then the odd step's
   const lbm_schedule start = b->sched;
-  for (int odd : {(int)LBM_ODD_COLUMNS, (int)LBM_ODD_DIRECT})
-    for (int c : kCtas) {
+  // the collide variants at one CTA per work unit, then the persistent grid
+  // for the best of them, then the z splits
+  for (int odd : {(int)LBM_ODD_COLUMNS, (int)LBM_ODD_DIRECT, (int)LBM_ODD_PAIRS})
+    for (int even : {(int)LBM_EVEN_DIRECT, (int)LBM_EVEN_PAIRS}) {
       lbm_schedule s = start;
-      s.ctas_per_sm = c;
+      s.ctas_per_sm = 0;
       s.odd_variant = odd;
+      s.even_variant = even;
       if (!rc) rc = try_one(s);
     }
+  const lbm_schedule variants = bs;
+  for (int c : kCtas) {
+    if (c == 0) continue;
+    lbm_schedule s = variants;
+    s.ctas_per_sm = c;
+    if (!rc) rc = try_one(s);
+  }
   for (int z = 0; z <= b->B && !rc; z = z ? 2 * z : 1) {
     lbm_schedule s = bs;
     s.z_split_even = z;

@@ -171,10 +171,8 @@ __device__ __forceinline__ void collide_pair(F2* d, const CollideArgs& a, const 
 #define LBM_PAIR_MINB 6
 #endif
 template <int B, typename IDX, typename S>
-__global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_p2(CollideArgs a) {
+__device__ __forceinline__ void even_pair_block(const CollideArgs& a, const int blk, const ZSeg zg) {
   constexpr int C3 = B * B * B;
-  const ZSeg zg = z_segment(blockIdx.x, a.zshift_even, B);
-  const int blk = zg.blk;
   const IDX own = (IDX)a.nbr[(size_t)blk * 27 + 13] * (IDX)(27 * C3);
   const int lx = 2 * (threadIdx.x % (B / 2)), ly = threadIdx.x / (B / 2);
   const int mo = a.maskoff[blk];
@@ -202,6 +200,11 @@ __global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_p2(Co
     }
   }
 }
+template <int B, typename IDX, typename S>
+__global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_p2(CollideArgs a) {
+  const ZSeg zg = z_segment(blockIdx.x, a.zshift_even, B);
+  even_pair_block<B, IDX, S>(a, zg.blk, zg);
+}
 
 // Odd step with two x-neighbouring cells (x0, x0 + 1), x0 even, per thread,
 // collided as one in packed FP32.  A thread keeps 9 column pointers: for each
@@ -213,15 +216,14 @@ __global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_p2(Co
 // fluid cells store.  On the two z-face slabs the pointers are built per c_z
 // group, for the slab (of this block or of its z neighbour) that the group
 // reaches.
-#ifndef LBM_ODD_PAIR_MINB
-#define LBM_ODD_PAIR_MINB 6
-#endif
+// MINB: resident CTAs per SM the registers are budgeted for (6: 80
+// registers, no spills; 7: 72 registers, 24 bytes spilled; 8: 64 registers,
+// ~170 bytes spilled) - more warps in flight against spill traffic, chosen
+// by the autotuner (lbm_odd_variant LBM_ODD_PAIRS, _PAIRS_7, _PAIRS_8)
 template <int B, typename IDX, typename S>
-__global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_p2(CollideArgs a) {
+__device__ __forceinline__ void odd_pair_block(const CollideArgs& a, const int blk, IDX* s_base, const ZSeg zg) {
   constexpr int C3 = B * B * B, S2 = B * B, H = B / 2;
-  __shared__ IDX s_base[27];
-  const ZSeg zg = z_segment(blockIdx.x, a.zshift_odd, B);
-  const int blk = zg.blk, t = threadIdx.x;
+  const int t = threadIdx.x;
   if (t < 27) s_base[t] = (IDX)a.nbr[(size_t)blk * 27 + t] * (IDX)(27 * C3);
   __syncthreads();
   const int x0 = 2 * (t % H), ly = t / H;
@@ -338,6 +340,13 @@ __global__ void __launch_bounds__(B * B / 2, LBM_ODD_PAIR_MINB) k_collide_odd_p2
       }
     }
   }
+}
+
+template <int B, typename IDX, typename S, int MINB>
+__global__ void __launch_bounds__(B * B / 2, MINB) k_collide_odd_p2(CollideArgs a) {
+  __shared__ IDX s_base[27];
+  const ZSeg zg = z_segment(blockIdx.x, a.zshift_odd, B);
+  odd_pair_block<B, IDX, S>(a, zg.blk, s_base, zg);
 }
 
 template <int B, bool ODD, typename IDX, typename S>
@@ -811,9 +820,15 @@ __global__ void __launch_bounds__(B * B, odd_minb<S>()) k_collide_odd_cols(Colli
 
 // Batched, persistent form: the CTAs walk a work list of (level descriptor,
 // block) pairs that spans several domains and levels, `gridDim.x` apart.
-// KIND 0: even step; 1: odd step, direct addressing; 2: odd step, column pointers.
+// KIND 0: even step; 1: odd step, direct addressing; 2: odd step, column
+// pointers; 3: even step, two cells per thread; 4: odd step, two cells per
+// thread (KIND 3 and 4 run B * B / 2 threads).
+template <int KIND>
+constexpr int batch_minb() {
+  return KIND == 0 ? LBM_EVEN_MINB : (KIND >= 3 ? LBM_PAIR_MINB : LBM_ODD_MINB);
+}
 template <int B, int KIND, typename IDX, typename S>
-__global__ void __launch_bounds__(B * B, KIND ? LBM_ODD_MINB : LBM_EVEN_MINB)
+__global__ void __launch_bounds__(KIND >= 3 ? B * B / 2 : B * B, batch_minb<KIND>())
     k_collide_batch(const CollideArgs* __restrict__ lv, const int2* __restrict__ items, int n, int zshift) {
   __shared__ IDX s_base[27];
   __shared__ IDX s_col[KIND == 2 && std::is_same<S, __half>::value ? 9 * B * B : 1];
@@ -823,6 +838,8 @@ __global__ void __launch_bounds__(B * B, KIND ? LBM_ODD_MINB : LBM_EVEN_MINB)
     const CollideArgs a = lv[w.x];
     __syncthreads();  // the previous item's readers of s_base are done
     if (KIND == 2) odd_cols_block<B, IDX, S>(a, w.y, s_base, s_col, zg.z0, zg.z1);
+    else if (KIND == 3) even_pair_block<B, IDX, S>(a, w.y, zg);
+    else if (KIND == 4) odd_pair_block<B, IDX, S>(a, w.y, s_base, zg);
     else collide_block<B, KIND == 1, IDX, S>(a, w.y, s_base, zg.z0, zg.z1);
   }
 }

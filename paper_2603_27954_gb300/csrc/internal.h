@@ -294,7 +294,7 @@ int launch_faces(void* f, int esize, const void* e, int narrow, int n, const dou
 // one launch over a work list of (index into lv, block) pairs; grid <= 0: one CTA per item
 // zshift: each item is walked by 2^zshift CTAs (or grid strides) of B >> zshift slabs
 int launch_collide_batch(const CollideArgs* lv, const int2* items, int n_items, int B, int odd, int odd_variant,
-                         int half, int wide, int grid, int zshift, void* stream);
+                         int even_variant, int half, int wide, int grid, int zshift, void* stream);
 int launch_tick(long long* tick, void* stream);
 // per-sample viscous traction times area, tangential part: out[3 k .. 3 k + 2]
 int launch_friction(const void* f, int esize, float inv_scale, const Ref27& ref, int B, const int* nbr, int odd,

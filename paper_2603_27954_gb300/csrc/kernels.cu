@@ -782,8 +782,12 @@ void collide_on(const CollideArgs& a, int odd, cudaStream_t s) {
   if (odd) {
     if (f32 && a.odd_variant == LBM_ODD_STAGED && B == 16)
       k_collide_odd_staged<IDX><<<a.n_active, 256, kStageBytes, s>>>(a);
-    else if (a.odd_variant == LBM_ODD_PAIRS)
-      k_collide_odd_p2<B, IDX, S><<<a.n_active << a.zshift_odd, B * B / 2, 0, s>>>(a);
+    else if (a.odd_variant == LBM_ODD_PAIRS_7 && B == 16)
+      k_collide_odd_p2<B, IDX, S, 7><<<a.n_active << a.zshift_odd, B * B / 2, 0, s>>>(a);
+    else if (a.odd_variant == LBM_ODD_PAIRS_8 && B == 16)
+      k_collide_odd_p2<B, IDX, S, 8><<<a.n_active << a.zshift_odd, B * B / 2, 0, s>>>(a);
+    else if (a.odd_variant == LBM_ODD_PAIRS || a.odd_variant == LBM_ODD_PAIRS_7 || a.odd_variant == LBM_ODD_PAIRS_8)
+      k_collide_odd_p2<B, IDX, S, 6><<<a.n_active << a.zshift_odd, B * B / 2, 0, s>>>(a);
     else if (a.odd_variant == LBM_ODD_DIRECT) k_collide<B, true, IDX, S><<<a.n_active << a.zshift_odd, B * B, 0, s>>>(a);
     else k_collide_odd_cols<B, IDX, S><<<a.n_active << a.zshift_odd, B * B, 0, s>>>(a);
   } else {
@@ -828,7 +832,9 @@ template <int B, typename IDX, typename S>
 void batch_on(const CollideArgs* lv, const int2* items, int n, int kind, int grid, int zshift, cudaStream_t s) {
   if (kind == 0) k_collide_batch<B, 0, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n, zshift);
   else if (kind == 1) k_collide_batch<B, 1, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n, zshift);
-  else k_collide_batch<B, 2, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n, zshift);
+  else if (kind == 2) k_collide_batch<B, 2, IDX, S><<<grid, B * B, 0, s>>>(lv, items, n, zshift);
+  else if (kind == 3) k_collide_batch<B, 3, IDX, S><<<grid, B * B / 2, 0, s>>>(lv, items, n, zshift);
+  else k_collide_batch<B, 4, IDX, S><<<grid, B * B / 2, 0, s>>>(lv, items, n, zshift);
 }
 
 template <typename S>
@@ -874,11 +880,13 @@ int launch_collide(const CollideArgs& a, int B, int odd, void* stream) {
 }
 
 int launch_collide_batch(const CollideArgs* lv, const int2* items, int n_items, int B, int odd, int odd_variant,
-                         int half, int wide, int grid, int zshift, void* stream) {
+                         int even_variant, int half, int wide, int grid, int zshift, void* stream) {
   if (n_items == 0) return LBM_OK;
   if (B != 16 && B != 8) return LBM_EINVAL;
   if (zshift < 0 || (B >> zshift) < 1) return LBM_EINVAL;
-  const int kind = !odd ? 0 : (odd_variant == LBM_ODD_DIRECT ? 1 : 2);
+  const bool odd_pairs = odd_variant == LBM_ODD_PAIRS || odd_variant == LBM_ODD_PAIRS_7 || odd_variant == LBM_ODD_PAIRS_8;
+  const int kind = !odd ? (even_variant == LBM_EVEN_PAIRS ? 3 : 0)
+                        : (odd_pairs ? 4 : (odd_variant == LBM_ODD_DIRECT ? 1 : 2));
   const int units = n_items << zshift;
   const int g = grid > 0 ? std::min(grid, units) : units;
   cudaStream_t s = (cudaStream_t)stream;

@@ -154,6 +154,13 @@ __global__ void k_denorm(const float* __restrict__ Yh, int batch, float mu, floa
   if (t < batch) Y[t] = Yh[t] * sd + mu;
 }
 
+// ensemble mean: Y = (first ? 0 : Y) + w (y_hat sd + mu), member by member
+__global__ void k_ens_acc(const float* __restrict__ Yh, int batch, float mu, float sd, float w, int first,
+                          float* __restrict__ Y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < batch) Y[t] = (first ? 0.0f : Y[t]) + w * (Yh[t] * sd + mu);
+}
+
 // Adam (Kingma & Ba 2015) on the FP32 master weights, then their BF16 copy
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1, float c2,
@@ -237,6 +244,11 @@ int mlp_colsum(const float* dZ, int batch, int N, float* db, void* stream) {
 int mlp_denorm(const float* Yh, int batch, float mu, float sd, float* Y, void* stream) {
   k_denorm<<<nb(batch, 256), 256, 0, (cudaStream_t)stream>>>(Yh, batch, mu, sd, Y);
   return mlp_check("denorm");
+}
+
+int mlp_ens_acc(const float* Yh, int batch, float mu, float sd, float w, int first, float* Y, void* stream) {
+  k_ens_acc<<<nb(batch, 256), 256, 0, (cudaStream_t)stream>>>(Yh, batch, mu, sd, w, first, Y);
+  return mlp_check("ens_acc");
 }
 
 int mlp_adam(float* w, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
@@ -490,6 +502,23 @@ int lbm_mlp_forward(lbm_mlp* m, const float* x, int batch, float* y) {
   int rc = mlp_forward_dev(m, x, nullptr, batch);
   if (rc) return rc;
   MRC(lbm::mlp_denorm(m->dev<float>(m->o_yh), batch, m->mu_y, m->sd_y, y, m->stream));
+  return LBM_OK;
+}
+
+int lbm_mlp_ensemble_forward(lbm_mlp* const* nets, int n, const float* x, int batch, float* y) {
+  if (!nets || n < 1 || !x || !y || batch < 1) return mfail(LBM_EINVAL, "bad argument");
+  for (int k = 0; k < n; ++k) {
+    const lbm_mlp* m = nets[k];
+    if (!ready(m) || batch > m->max_batch) return mfail(LBM_EINVAL, "bad member or batch above its capacity");
+    if (m->n_in != nets[0]->n_in || m->stream != nets[0]->stream)
+      return mfail(LBM_EINVAL, "ensemble members must share their input count and stream");
+  }
+  for (int k = 0; k < n; ++k) {
+    lbm_mlp* m = nets[k];
+    int rc = mlp_forward_dev(m, x, nullptr, batch);
+    if (rc) return rc;
+    MRC(lbm::mlp_ens_acc(m->dev<float>(m->o_yh), batch, m->mu_y, m->sd_y, 1.0f / (float)n, k == 0, y, m->stream));
+  }
   return LBM_OK;
 }
 

@@ -47,7 +47,7 @@ class Schedule(C.Structure):
                 "z_split_odd": self.z_split_odd}
 
 
-ODD_VARIANTS = {0: "columns", 1: "staged", 2: "direct", 3: "pairs"}
+ODD_VARIANTS = {0: "columns", 1: "staged", 2: "direct", 3: "pairs", 4: "pairs_7", 5: "pairs_8"}
 EVEN_VARIANTS = {0: "direct", 1: "tma", 2: "pairs"}
 
 
@@ -93,6 +93,8 @@ def _load():
         "lbm_set_watchdog": ([vp, i], i),
         "lbm_branch_table": ([vp, dp, i, ip], i),
         "lbm_branch_drag_estimate": ([dp, i, dp, C.c_double, dp, dp], i),
+        "lbm_branch_coefficients": ([vp, dp, dp, i, dp, dp], i),
+        "lbm_mlp_ensemble_forward": ([C.POINTER(vp), i, vp, i, vp], i),
         "lbm_set_branch_forces": ([vp, i], i),
         "lbm_set_wide_offsets": ([vp, i], i),
         "lbm_set_overlap": ([vp, i], i),
@@ -419,6 +421,15 @@ def lbm_branch_drag_estimate(rows, area, c_sect=None):
     return cd.value, c_out[:n]
 
 
+def lbm_branch_coefficients(h, n_branches):
+    """Eq. 3's measured sectional coefficients: (c_drag, c_fric, C_D, C_F) over the averaging window."""
+    cd_, cf_ = np.zeros(max(1, n_branches)), np.zeros(max(1, n_branches))
+    cd, cf = C.c_double(), C.c_double()
+    _ck(_lib.lbm_branch_coefficients(h, _dp(cd_), _dp(cf_), n_branches, C.byref(cd), C.byref(cf)),
+        "lbm_branch_coefficients")
+    return cd_[:n_branches], cf_[:n_branches], cd.value, cf.value
+
+
 def lbm_branch_table(h):
     n = C.c_int()
     _ck(_lib.lbm_branch_table(h, None, 0, C.byref(n)), "lbm_branch_table")
@@ -590,6 +601,17 @@ class Mlp:
         _mck(_lib.lbm_mlp_param_count(h, C.byref(p)), "lbm_mlp_param_count")
         self.n_params, self.max_batch, self.n_in = p.value, max_batch, n_in
 
+    # stream ordering: the network's kernels run on its own stream; tensors
+    # the caller made on its current stream are ready before they start
+    # (_enter), and the caller's stream waits for their results (_leave)
+    def _enter(self):
+        if self.stream is not None:
+            self.stream.wait_stream(self._torch.cuda.current_stream())
+
+    def _leave(self):
+        if self.stream is not None:
+            self._torch.cuda.current_stream().wait_stream(self.stream)
+
     def set_params(self, w):
         w = np.ascontiguousarray(w, dtype=np.float32)
         _mck(_lib.lbm_mlp_set_params(self.h, _fp(w), len(w)), "lbm_mlp_set_params")
@@ -608,14 +630,17 @@ class Mlp:
     def forward(self, x):
         """x: device float32 tensor (batch, n_in) -> device tensor (batch,)."""
         y = self._torch.empty(x.shape[0], dtype=self._torch.float32, device=x.device)
+        self._enter()
         _mck(_lib.lbm_mlp_forward(self.h, C.c_void_p(x.data_ptr()), x.shape[0], C.c_void_p(y.data_ptr())),
              "lbm_mlp_forward")
+        self._leave()
         return y
 
     def gradients(self, x, y, idx=None):
         g = np.zeros(self.n_params, np.float32)
         loss = C.c_double()
         n = idx.shape[0] if idx is not None else x.shape[0]
+        self._enter()
         _mck(_lib.lbm_mlp_gradients(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                     C.c_void_p(idx.data_ptr() if idx is not None else 0), n, _fp(g),
                                     C.byref(loss)), "lbm_mlp_gradients")
@@ -624,9 +649,11 @@ class Mlp:
     def train_step(self, x, y, idx=None, lr=1e-3, want_loss=False):
         loss = C.c_double()
         n = idx.shape[0] if idx is not None else x.shape[0]
+        self._enter()
         _mck(_lib.lbm_mlp_train_step(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                      C.c_void_p(idx.data_ptr() if idx is not None else 0), n, float(lr),
                                      C.byref(loss) if want_loss else None), "lbm_mlp_train_step")
+        self._leave()
         return loss.value if want_loss else None
 
     def close(self):
@@ -641,6 +668,18 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def mlp_ensemble_forward(nets, x):
+    """Mean prediction of several Mlp objects (device tensor x) -> device tensor."""
+    import torch
+    y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    arr = (C.c_void_p * len(nets))(*[m.h for m in nets])
+    nets[0]._enter()
+    _mck(_lib.lbm_mlp_ensemble_forward(arr, len(nets), C.c_void_p(x.data_ptr()), x.shape[0], C.c_void_p(y.data_ptr())),
+         "lbm_mlp_ensemble_forward")
+    nets[0]._leave()
+    return y
 
 
 class Batch:
@@ -663,8 +702,8 @@ class Batch:
     def step(self, n=1):
         return _ck(_lib.lbm_batch_step(self.h, int(n)), "lbm_batch_step")
 
-    def set_schedule(self, ctas_per_sm=0, odd_variant=0, z_split_even=0, z_split_odd=0):
-        s = Schedule(ctas_per_sm, odd_variant, 0, z_split_even, z_split_odd)
+    def set_schedule(self, ctas_per_sm=0, odd_variant=0, z_split_even=0, z_split_odd=0, even_variant=0):
+        s = Schedule(ctas_per_sm, odd_variant, even_variant, z_split_even, z_split_odd)
         return _ck(_lib.lbm_batch_set_schedule(self.h, C.byref(s)), "lbm_batch_set_schedule")
 
     def get_schedule(self):

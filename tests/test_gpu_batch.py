@@ -47,15 +47,19 @@ def state(dom, levels):
         dom.geometry_info()["n_segments"])[0]
 
 
-@pytest.mark.parametrize("ctas,odd,ze,zo", [(0, 0, 1, 1), (2, 0, 0, 0), (3, 2, 2, 8), (1, 2, 4, 1), (0, 2, 8, 4)])
-def test_batch_equals_domains_stepped_alone(L, stream, ctas, odd, ze, zo):
+@pytest.mark.parametrize("ctas,odd,ze,zo,even", [(0, 0, 1, 1, 0), (2, 0, 0, 0, 0), (3, 2, 2, 8, 0), (1, 2, 4, 1, 0),
+                                                 (0, 2, 8, 4, 0), (0, 3, 1, 1, 2), (2, 3, 2, 4, 2), (0, 3, 0, 0, 0)])
+def test_batch_equals_domains_stepped_alone(L, stream, ctas, odd, ze, zo, even):
+    """Every schedule, including the paired (two cells per thread) kernels in
+    the batch, equals the domains stepped alone with the same kernels."""
     recs = records()
     alone = [make(L, stream, c) for c in recs]
     for d in alone:
+        d.set_schedule(0, odd, even)
         d.step(5)
     doms = [make(L, stream, c) for c in recs]
     batch = L.Batch(doms, stream=stream)
-    batch.set_schedule(ctas, odd, ze, zo)
+    batch.set_schedule(ctas, odd, ze, zo, even)
     batch.step(5)
     for a, b, c in zip(alone, doms, recs):
         sa, sb = state(a, c["levels"]), state(b, c["levels"])
@@ -74,11 +78,11 @@ def test_batch_autotune_picks_a_candidate_and_graphs_match_direct(L, stream):
     d2 = [make(L, stream, c) for c in recs]
     b1, b2 = L.Batch(d1, stream=stream), L.Batch(d2, stream=stream)
     best, ms = b1.autotune(steps=2)
-    assert best.ctas_per_sm in (0, 1, 2, 3, 4, 6, 8) and best.odd_variant in (0, 2) and ms > 0
+    assert best.ctas_per_sm in (0, 1, 2, 3, 4, 6, 8) and best.odd_variant in (0, 2, 3) and ms > 0
     # both batches continue from the same state: re-initialise, then step with and without graphs
     for d in d1 + d2:
         d.init_uniform(1.0, np.array([0.05, 0.0, 0.0]))
-    b2.set_schedule(best.ctas_per_sm, best.odd_variant)
+    b2.set_schedule(best.ctas_per_sm, best.odd_variant, even_variant=best.even_variant)
     b2.use_graphs(False)
     b1.step(4)
     b2.step(4)

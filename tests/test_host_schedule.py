@@ -1,6 +1,7 @@
 """Schedule validation on the host (no GPU): every collide-variant pair a
 domain accepts, and the ones it must refuse (staged and TMA kernels only
-for FP32 in 16^3 blocks, paired even steps only for FP16 storage)."""
+for FP32 in 16^3 blocks, the 7- and 8-CTA budgets of the paired odd step
+only in 16^3 blocks)."""
 import numpy as np
 import pytest
 
@@ -19,8 +20,11 @@ def domain(precision, block=16):
     (L.LBM_FP32, 16, 0, 2, True), (L.LBM_FP32, 8, 1, 0, False), (L.LBM_FP32, 8, 0, 1, False),
     (L.LBM_FP16_DEV, 16, 0, 2, True), (L.LBM_FP16_DEV, 8, 2, 2, True), (L.LBM_FP16_DEV, 16, 1, 0, False),
     (L.LBM_FP16_DEV, 16, 0, 1, False), (L.LBM_FP32, 16, 3, 0, True), (L.LBM_FP32, 16, 0, 3, False),
-    (L.LBM_FP32, 8, 3, 2, True), (L.LBM_FP32, 16, 4, 0, False),
-    (L.LBM_FP16_DEV, 16, 3, 2, True), (L.LBM_FP16_DEV, 8, 3, 0, True), (L.LBM_FP16_DEV, 16, 4, 2, False),
+    (L.LBM_FP32, 8, 3, 2, True), (L.LBM_FP32, 16, 6, 0, False),
+    (L.LBM_FP16_DEV, 16, 3, 2, True), (L.LBM_FP16_DEV, 8, 3, 0, True), (L.LBM_FP16_DEV, 16, 6, 2, False),
+    # the pair kernel budgeted for 7 or 8 resident CTAs: 16^3 blocks only
+    (L.LBM_FP32, 16, 4, 0, True), (L.LBM_FP16_DEV, 16, 5, 2, True), (L.LBM_FP32, 8, 4, 0, False),
+    (L.LBM_FP16_DEV, 8, 5, 2, False),
 ])
 def test_schedule_validation(precision, block, odd, even, ok):
     h = domain(precision, block)
