@@ -91,7 +91,7 @@ def tune(L, dom, u_in, steps):
     return best.as_dict()
 
 
-def measure_form(L, W, torch, stream, case, precision, steps, warmup, timing_steps=20, tune_steps=3):
+def measure_form(L, W, torch, stream, case, precision, steps, warmup, timing_steps=20, tune_steps=3, schedule=None):
     """Whole-path MLUPS of one workload in one storage form (CUDA events on
     the domain's stream) under its autotuned schedule, the collide kernels'
     algorithmic GB/s from the library's per-class timing, and the C_D after
@@ -99,7 +99,12 @@ def measure_form(L, W, torch, stream, case, precision, steps, warmup, timing_ste
     desc, tree, c = workload_desc(L, W, case, precision)
     dom = L.Domain(desc, tree=tree, stream=stream)
     updates, _ = dom.work_per_step()
-    schedule = tune(L, dom, c["u_in"], tune_steps)
+    if schedule:
+        odd, even, ze, zo = (int(v) for v in schedule.split(","))
+        dom.set_schedule(0, odd, even, ze, zo)
+        schedule = dom.get_schedule().as_dict()
+    else:
+        schedule = tune(L, dom, c["u_in"], tune_steps)
     dom.step(warmup)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -125,10 +130,10 @@ def measure_form(L, W, torch, stream, case, precision, steps, warmup, timing_ste
             "schedule": schedule}
 
 
-def fp16_form(L, W, torch, stream, steps, warmup, fp32_value, peak):
+def fp16_form(L, W, torch, stream, steps, warmup, fp32_value, peak, schedule=None):
     """The FP16-deviation storage form on the same workload: MLUPS, its
     collide roofline at 108 B per update, and the speed-up over FP32."""
-    r = measure_form(L, W, torch, stream, CASE, L.LBM_FP16_DEV, steps, warmup)
+    r = measure_form(L, W, torch, stream, CASE, L.LBM_FP16_DEV, steps, warmup, schedule=schedule)
     return {"value": r["value"], "unit": "MLUPS", "speedup_vs_fp32": r["value"] / fp32_value,
             "ms_per_step": r["ms_per_step"],
             "dtype": "f16 storage of (f - f^eq(1, U e_x)) * 2^13, f32 collision, f64 reductions",
@@ -368,6 +373,8 @@ def main():
     ap.add_argument("--schedule", default=None,
                     help="odd,even,z_even,z_odd: fix the main workload's schedule instead of autotuning it "
                          "(for profiling the kernels a tuned run chose)")
+    ap.add_argument("--fp16-schedule", default=None,
+                    help="odd,even,z_even,z_odd: fix the FP16 form's schedule instead of autotuning it")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
@@ -496,7 +503,7 @@ def main():
 
     fp16 = None
     if not args.no_fp16:
-        fp16 = fp16_form(L, W, torch, stream, args.steps, args.warmup, value, peak)
+        fp16 = fp16_form(L, W, torch, stream, args.steps, args.warmup, value, peak, args.fp16_schedule)
     prec_form = None
     if not args.no_precision_form:
         prec_form = precision_form(L, W, torch, stream, args.precision_steps, 3, peak)

@@ -112,14 +112,22 @@ struct lbm_domain {
   // turbulent inflow (random Fourier modes), on when d.i_u > 0
   int n_modes = 256;
   double l_int = 0;  // integral length in level-0 cells; 0: the tree height
-  size_t off_modes = 0, off_facepos = 0, off_tick = 0;
+  size_t off_modes = 0, off_turbidx = 0, off_turbcells = 0, off_turbvel = 0, off_tick = 0;
   int max_wall_parts = 0;
   float feq_in[27];     // inflow equilibrium minus the rest weights, FP32
   double feq_in_d[27];  // the same in FP64 (FP64 storage form)
   int parity0 = 0;
   long long steps = 0;
   bool use_graphs = true;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // graph[v][p]: one coarse step of parity p; v = 0 starts from a complete
+  // state, v = 1 first runs the coalesce transfers the previous step left
+  // pending (their parities in coal_in[p]); either leaves coal_out[p]
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  std::vector<int> coal_in[2], coal_out[2];
+  // per level: parity of the level's last step whose coalesce transfer is
+  // still to run (-1: none); lbm_step runs them before it returns
+  std::vector<int> pend_coal;
+  int wall_branch_level = -1;  // level whose walls branch 1 carries
   int watchdog = 0;
   int last_status = LBM_OK;
   // timing
@@ -183,11 +191,12 @@ void pin_tables(lbm_domain* d) {
 }
 
 void free_graphs(lbm_domain* d) {
-  for (auto& g : d->graph)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  for (auto& gv : d->graph)
+    for (auto& g : gv)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
 }
 
 cudaEvent_t take_event(lbm_domain* d) {
@@ -358,9 +367,13 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s, bool branche
     double feq[27];
     for (int i = 0; i < 27; ++i)
       feq[i] = esize == 8 ? dm->feq_in_d[i] : (double)(float)((dm->feq_in[i] - dm->ref[i]) * v.scale);
-    TurbArgs tb{nullptr, nullptr, 0, (float)dm->d.u_in, v.scale, nullptr, dm->d.precision == LBM_FP16_DEV};
+    TurbArgs tb{nullptr, nullptr, nullptr, 0, nullptr, 0, (float)dm->d.u_in, v.scale, nullptr,
+                dm->d.precision == LBM_FP16_DEV};
     if (dm->d.i_u > 0) {
-      tb.pos = dm->dev<int>(dm->off_facepos);
+      tb.idx = dm->dev<int>(dm->off_turbidx);
+      tb.cells = dm->dev<int>(dm->off_turbcells);
+      tb.vel = dm->dev<float>(dm->off_turbvel);
+      tb.n_cells = (int)(v.turb_cells.size() / 4);
       tb.modes = dm->dev<float>(dm->off_modes);
       tb.n_modes = dm->n_modes;
       tb.tick = dm->dev<long long>(dm->off_tick);
@@ -373,7 +386,10 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s, bool branche
   if (!v.wall[parity].empty()) {
     Timed t(dm, KC_WALLS, (long long)v.wall[parity].size());
     const cudaStream_t s_main = s;
-    if (branches && v.ovl_walls && (rc = fork_branch(dm, 1, &s))) return rc;
+    if (branches && v.ovl_walls) {
+      if ((rc = fork_branch(dm, 1, &s))) return rc;
+      dm->wall_branch_level = l;
+    }
     int n = (int)v.wall[parity].size();
     const bool per_branch = dm->branch_forces && l == m.L - 1;
     // the finest level's walls reduce the force of the step in the same launch
@@ -392,36 +408,42 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s, bool branche
   return LBM_OK;
 }
 
-// coarse post-collision values into the fine ghosts before the second fine step
 int c3_log2(int B) { return B == 16 ? 12 : 9; }
 LedgerDev* ledger_of(lbm_domain* dm, const Level& v) {
   return dm->ledger ? dm->dev<LedgerDev>(v.off_ledger) : nullptr;
 }
 
-int iface_explode(lbm_domain* dm, int l, int parity, cudaStream_t s) {
+// The transfers from the coarse level to the finer one, in up to two
+// launches per coarse step: `explode` (coarse post-collision values into the
+// fine ghost slots the finer level's second sub-step pulls from: they only
+// need the coarse collide, and the fine level's first sub-step touches its
+// active cells' own slots only, so they may run beside it) and
+// `save_inflow` (the fine values of the first sub-step that leave the box,
+// for the coalesce transfer, and the fine inflow for the next first
+// sub-step: both touch slots the second sub-step neither reads nor writes,
+// so they may run beside it; they must finish before the coalesce
+// transfer, which reads the saved values and overwrites coarse slots the
+// inflow reads).
+int iface_transfer(lbm_domain* dm, int l, int parity, cudaStream_t s, bool explode, bool save_inflow) {
   Level& v = dm->mesh.lv[l];
   Level& F = dm->mesh.lv[l + 1];
-  Timed t(dm, KC_IFACE, (long long)v.expl.size());
+  const int ne = explode ? (int)v.expl.size() : 0;
+  const int ns = save_inflow ? (int)v.save.size() : 0, ni = save_inflow ? (int)v.infl.size() : 0;
+  Timed t(dm, KC_IFACE, (long long)ne + ni);
   return launch_explode(dm->base + F.off_f, dm->base + v.off_f, v.esize, F.scale / v.scale,
-                        dm->base + v.off_expl, v.narrow, (int)v.expl.size(), dm->base + v.off_save,
-                        (int)v.save.size(), dm->base + v.off_saved, parity, ledger_of(dm, v), c3_log2(v.B),
-                        1.0f / F.scale, s);
+                        dm->base + v.off_expl, v.narrow, ne, dm->base + v.off_save, ns, dm->base + v.off_infl, ni,
+                        dm->base + v.off_saved, parity, ledger_of(dm, v), c3_log2(v.B), 1.0f / F.scale, s);
 }
 
-// fine inflow for the next first fine step, and coarse cells from their children
-int iface_inflow(lbm_domain* dm, int l, int parity, cudaStream_t s) {
+// after the fine level's second sub-step: coarse cells next to the fine
+// region from their children
+int iface_coalesce(lbm_domain* dm, int l, int parity, cudaStream_t s) {
   Level& v = dm->mesh.lv[l];
   Level& F = dm->mesh.lv[l + 1];
-  Timed t(dm, KC_IFACE, (long long)v.infl.size() + (long long)v.coal.size());
-  void* ff = dm->base + F.off_f;
-  void* f = dm->base + v.off_f;
-  const float ratio = F.scale / v.scale;
-  void* saved = dm->base + v.off_saved;
-  int rc = launch_inflow(ff, f, v.esize, ratio, dm->base + v.off_infl, v.narrow, (int)v.infl.size(), saved,
-                         parity, ledger_of(dm, v), c3_log2(v.B), 1.0f / F.scale, s);
-  if (rc) return rc;
-  return launch_coalesce(f, ff, v.esize, ratio, dm->base + v.off_coal, v.narrow, (int)v.coal.size(), saved,
-                         parity, ledger_of(dm, v), v.ledger_const, c3_log2(v.B), 1.0f / v.scale, 1.0f / F.scale, s);
+  Timed t(dm, KC_IFACE, (long long)v.coal.size());
+  return launch_coalesce(dm->base + v.off_f, dm->base + F.off_f, v.esize, F.scale / v.scale, dm->base + v.off_coal,
+                         v.narrow, (int)v.coal.size(), dm->base + v.off_saved, parity, ledger_of(dm, v),
+                         v.ledger_const, c3_log2(v.B), 1.0f / v.scale, 1.0f / F.scale, s);
 }
 
 // friction of the finest level at the current step boundary, added to acc
@@ -449,11 +471,21 @@ int end_coarse_step(lbm_domain* dm, int parity, cudaStream_t s) {
 }
 
 // one step of level l (recursively the two steps of every finer level)
+// whether level l's collide of this parity runs in two launches around the
+// join of the walls its previous step left running on branch 1: first the
+// blocks those walls do not touch, then the rest
+bool wall_split(const lbm_domain* dm, const Level& v, int l, int parity) {
+  return dm->overlap && !dm->timing && dm->pend[1] && dm->wall_branch_level == l && v.n_windep[parity] > 0 &&
+         v.n_windep[parity] < v.n_active && dm->odd_variant != LBM_ODD_STAGED;
+}
+
 int advance(lbm_domain* dm, int l, int parity) {
   Mesh& m = dm->mesh;
   Level& v = m.lv[l];
   int rc;
-  if ((rc = join_branch(dm, 1))) return rc;  // walls before the next collide of any level
+  const bool wsplit = wall_split(dm, v, l, parity);
+  // walls before the next collide of any level (of the blocks they touch)
+  if (!wsplit && (rc = join_branch(dm, 1))) return rc;
   // a level with a finer level runs its collide and boundary kernels beside
   // the finer levels' first sub-step (disjoint arrays), joined before explode;
   // not when it has cut links (the wall kernels of all levels share their
@@ -461,31 +493,100 @@ int advance(lbm_domain* dm, int l, int parity) {
   const bool split = l + 1 < m.L && dm->overlap && !dm->timing && v.wall[0].empty();
   cudaStream_t cs = dm->stream;
   if (split && (rc = fork_level(dm, l, &cs))) return rc;
-  {
+  if ((int)dm->pend_coal.size() != m.L) dm->pend_coal.assign(m.L, -1);
+  if (dm->pend_coal[l] >= 0) {
+    // the coalesce transfer of this level's previous step: it reads the finer
+    // level's ghost and saved values, which nothing touches before the
+    // explode below, and writes this level's slots, which the collide reads
+    if ((rc = iface_coalesce(dm, l, dm->pend_coal[l], cs))) return rc;
+    dm->pend_coal[l] = -1;
+  }
+  if (wsplit) {
+    // (a level with walls is never split off: cs is the domain's stream)
+    CollideArgs a = collide_args(dm, l);
+    a.blocks = dm->dev<int>(v.off_wblocks[parity]);
+    a.n_active = v.n_windep[parity];
+    if ((rc = launch_collide(a, v.B, parity, cs))) return rc;
+    if ((rc = join_branch(dm, 1))) return rc;
+    a.blocks += v.n_windep[parity];
+    a.n_active = v.n_active - v.n_windep[parity];
+    if ((rc = launch_collide(a, v.B, parity, cs))) return rc;
+  } else {
     Timed t(dm, parity ? KC_COLLIDE_ODD : KC_COLLIDE, v.n_fluid);
     if ((rc = launch_collide(collide_args(dm, l), v.B, parity, cs))) return rc;
   }
   if ((rc = post_collide(dm, l, parity, cs, true))) return rc;
   if (l + 1 < m.L) {
+    // the transfers with the finer level run beside its sub-steps when the
+    // finer level's walls touch none of their slots (host check); else in
+    // the serial order
+    const Level& F = m.lv[l + 1];
+    const bool beside = dm->overlap && !dm->timing && (F.wall[0].empty() || F.ovl_walls);
+    // explode right after this level's collide, on its side stream beside
+    // the finer level's first sub-step when the level is split off
+    const bool expl_side = split && beside;
+    if (expl_side && (rc = iface_transfer(dm, l, parity, cs, true, false))) return rc;
     if ((rc = advance(dm, l + 1, 0))) return rc;
     if (split && (rc = join_level(dm, l))) return rc;
-    if ((rc = iface_explode(dm, l, parity, dm->stream))) return rc;
+    // save and inflow entries on the level's side stream beside the finer
+    // level's second sub-step, joined before the coalesce transfer
+    const bool branch = beside && (v.save.size() || v.infl.size());
+    if (!expl_side || !branch) {
+      if ((rc = iface_transfer(dm, l, parity, dm->stream, !expl_side, !branch))) return rc;
+    }
+    if (branch) {
+      cudaStream_t is;
+      if ((rc = fork_level(dm, l, &is)) || (rc = iface_transfer(dm, l, parity, is, false, true))) return rc;
+    }
     if ((rc = advance(dm, l + 1, 1))) return rc;
-    if ((rc = iface_inflow(dm, l, parity, dm->stream))) return rc;
+    if (branch && (rc = join_level(dm, l))) return rc;
+    // the coalesce transfer waits for the head of this level's next step,
+    // beside the finer level's first sub-step (which touches neither the
+    // fine ghost and saved values it reads nor this level)
+    if (beside) dm->pend_coal[l] = parity;
+    else if ((rc = iface_coalesce(dm, l, parity, dm->stream))) return rc;
   }
   if (l == 0) return end_coarse_step(dm, parity, dm->stream);
   return LBM_OK;
 }
 
-int kernels_per_step(const Mesh& m, int l) {
+// the pending coalesce transfers, finest first (each reads only its finer
+// level's ghost and saved values, which no other pending transfer writes)
+int flush_coalesce(lbm_domain* dm) {
+  for (int l = (int)dm->pend_coal.size() - 1; l >= 0; --l) {
+    if (dm->pend_coal[l] < 0) continue;
+    int rc = iface_coalesce(dm, l, dm->pend_coal[l], dm->stream);
+    if (rc) return rc;
+    dm->pend_coal[l] = -1;
+  }
+  return LBM_OK;
+}
+bool any_pending(const lbm_domain* dm) {
+  for (int p : dm->pend_coal)
+    if (p >= 0) return true;
+  return false;
+}
+
+int kernels_per_step(const lbm_domain* d, int l) {
+  const Mesh& m = d->mesh;
   const Level& v = m.lv[l];
   int k = 1;
+  // the finest level's second sub-step in two launches around the join of
+  // the first sub-step's walls
+  if (l + 2 == m.L) {
+    const Level& F = m.lv[l + 1];
+    if (d->overlap && F.ovl_walls && F.n_windep[1] > 0 && F.n_windep[1] < F.n_active &&
+        d->odd_variant != LBM_ODD_STAGED)
+      k += 1;
+  }
   if (l == 0 && !v.face[0].empty()) k += 1;
-  if (l == 0 && m.turbulent) k += 1;
+  if (l == 0 && m.turbulent) k += 2;
   if (l == 0 && m.friction) k += 2;
   if (!v.wall[0].empty()) k += 1;
-  if (l + 1 < m.L) k += 2 * kernels_per_step(m, l + 1) + (v.expl.size() || v.save.size() ? 1 : 0) +
-                        (v.infl.empty() ? 0 : 1) + (v.coal.empty() ? 0 : 1);
+  // explode, save + inflow (launches of their own beside the finer level's
+  // two sub-steps while overlap is on), coalesce
+  if (l + 1 < m.L) k += 2 * kernels_per_step(d, l + 1) + (v.expl.empty() ? 0 : 1) +
+                        (v.save.size() || v.infl.size() ? 1 : 0) + (v.coal.empty() ? 0 : 1);
   return k;
 }
 
@@ -549,6 +650,7 @@ int build(lbm_domain* d) {
     v.off_nbr = put(v.nbr.size() * sizeof(int));
     v.off_maskoff = put(v.maskoff.size() * sizeof(int));
     v.off_masks = put(v.masks.size());
+    for (int p = 0; p < 2; ++p) v.off_wblocks[p] = put(v.wblocks[p].size() * sizeof(int));
     for (int p = 0; p < 2; ++p) {
       v.off_wall[p] = put(v.wall[p].size() * sizeof(WallEntry));
       v.off_face[p] = put(v.face[p].size() * sizeof(FaceEntry));
@@ -586,7 +688,10 @@ int build(lbm_domain* d) {
   d->mesh.friction = d->friction_mean;
   if (d->d.i_u > 0) {
     d->off_modes = put((size_t)kMaxModes * kModeCols * sizeof(float));
-    d->off_facepos = put(d->mesh.lv[0].face_pos.size() * sizeof(int));
+    const Level& l0 = d->mesh.lv[0];
+    d->off_turbidx = put(l0.turb_idx.size() * sizeof(int));
+    d->off_turbcells = put(l0.turb_cells.size() * sizeof(int));
+    d->off_turbvel = put(l0.turb_cells.size() * sizeof(float));
   }
   d->off_mpart = put(max_blocks * 5 * sizeof(double));
   d->off_wdone = put(sizeof(unsigned));
@@ -695,7 +800,7 @@ size_t upload_bytes(const lbm_domain* d) {
   size_t b = 0;
   for (const Level& v : d->mesh.lv) {
     b += v.nbr.size() * sizeof(int) + v.maskoff.size() * sizeof(int) + v.masks.size() +
-         v.link_q.size() * sizeof(double);
+         v.link_q.size() * sizeof(double) + (v.wblocks[0].size() + v.wblocks[1].size()) * sizeof(int);
     if (v.narrow_ok && !d->wide_offsets) {
       for (int p = 0; p < 2; ++p) b += v.wall_n[p].size() * sizeof(WallEntryN) + v.face_n[p].size() * sizeof(FaceEntryN);
       b += v.expl_n.size() * sizeof(ExplodeEntryN) + v.save_n.size() * sizeof(SaveEntryN) +
@@ -708,7 +813,9 @@ size_t upload_bytes(const lbm_domain* d) {
   }
   if (d->n_seg) b += d->mesh.lv.back().seg_begin.size() * sizeof(int);
   b += d->fsamp.size() * sizeof(FrictionSample) + d->fseg_begin.size() * sizeof(int);
-  if (d->d.i_u > 0) b += d->mesh.lv[0].face_pos.size() * sizeof(int) + (size_t)d->n_modes * kModeCols * sizeof(float);
+  if (d->d.i_u > 0)
+    b += (d->mesh.lv[0].turb_idx.size() + d->mesh.lv[0].turb_cells.size()) * sizeof(int) +
+         (size_t)d->n_modes * kModeCols * sizeof(float);
   return b + sizeof(long long);
 }
 
@@ -722,6 +829,7 @@ int upload(lbm_domain* d) {
     CK(cp(v.off_nbr, v.nbr.data(), v.nbr.size() * sizeof(int)));
     CK(cp(v.off_maskoff, v.maskoff.data(), v.maskoff.size() * sizeof(int)));
     CK(cp(v.off_masks, v.masks.data(), v.masks.size()));
+    for (int p = 0; p < 2; ++p) CK(cp(v.off_wblocks[p], v.wblocks[p].data(), v.wblocks[p].size() * sizeof(int)));
   }
   int rc = upload_tables(d);
   if (rc) return rc;
@@ -731,7 +839,8 @@ int upload(lbm_domain* d) {
   CK(cp(d->off_fsegb, d->fseg_begin.data(), d->fseg_begin.size() * sizeof(int)));
   if (d->d.i_u > 0) {
     const Level& l0 = d->mesh.lv[0];
-    CK(cp(d->off_facepos, l0.face_pos.data(), l0.face_pos.size() * sizeof(int)));
+    CK(cp(d->off_turbidx, l0.turb_idx.data(), l0.turb_idx.size() * sizeof(int)));
+    CK(cp(d->off_turbcells, l0.turb_cells.data(), l0.turb_cells.size() * sizeof(int)));
     int rc = upload_modes(d);
     if (rc) return rc;
   }
@@ -767,19 +876,37 @@ long long incoming_slot(const Level& v, int parity, int x, int y, int z, int i) 
   return v.addr(x - cx(i), y - cy(i), z - cz(i), opposite(i));
 }
 
+// capture one coarse step of parity p starting from the pending transfers
+// `pre`; the host-side pending state is restored afterwards
+int capture_one(lbm_domain* d, int p, const std::vector<int>& pre, cudaGraphExec_t* out, std::vector<int>* post) {
+  const std::vector<int> keep = d->pend_coal;
+  d->pend_coal = pre;
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = advance(d, 0, p);
+  cudaError_t e = cudaStreamEndCapture(d->stream, &g);
+  *post = d->pend_coal;
+  d->pend_coal = keep;
+  if (rc) return fail(rc, cuda_error_string());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return LBM_OK;
+}
+
 int capture_graphs(lbm_domain* d) {
   if (!d->use_graphs || d->stream == nullptr || d->timing) return LBM_OK;
+  const std::vector<int> none(d->mesh.L, -1);
+  int rc;
+  for (int p = 0; p < 2; ++p)
+    if (!d->graph[0][p] && (rc = capture_one(d, p, none, &d->graph[0][p], &d->coal_out[p]))) return rc;
+  // the chained form of parity p follows a step of parity 1 - p
   for (int p = 0; p < 2; ++p) {
-    if (d->graph[p]) continue;
-    cudaGraph_t g;
-    CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = advance(d, 0, p);
-    cudaError_t e = cudaStreamEndCapture(d->stream, &g);
-    if (rc) return fail(rc, cuda_error_string());
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&d->graph[p], g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    d->coal_in[p] = d->coal_out[1 - p];
+    if (d->coal_in[p] == none || d->graph[1][p]) continue;
+    std::vector<int> post;
+    if ((rc = capture_one(d, p, d->coal_in[p], &d->graph[1][p], &post))) return rc;
   }
   return LBM_OK;
 }
@@ -1040,20 +1167,29 @@ int lbm_step(lbm_domain* d, int n) {
   int rc = capture_graphs(d);
   if (rc) return rc;
   for (int k = 0; k < n; ++k) {
-    if (d->graph[d->parity0] && !d->timing) {
-      CK(cudaGraphLaunch(d->graph[d->parity0], d->stream));
+    const int p = d->parity0;
+    if (d->graph[0][p] && !d->timing) {
+      // a step that follows one in this call starts with the transfers that
+      // one left pending (the chained graph), else from a complete state
+      const bool chain = any_pending(d);
+      if (chain && (d->pend_coal != d->coal_in[p] || !d->graph[1][p]) && (rc = flush_coalesce(d)))
+        return fail(rc, cuda_error_string());
+      CK(cudaGraphLaunch(d->graph[any_pending(d) ? 1 : 0][p], d->stream));
+      d->pend_coal = d->coal_out[p];
     } else {
-      if ((rc = advance(d, 0, d->parity0))) return fail(rc, cuda_error_string());
+      if ((rc = advance(d, 0, p))) return fail(rc, cuda_error_string());
     }
     d->parity0 ^= 1;
     d->steps++;
     if (d->watchdog > 0 && d->steps % d->watchdog == 0) {
       double bad = 0;
+      if ((rc = flush_coalesce(d))) return fail(rc, cuda_error_string());
       if ((rc = mass_device(d, nullptr, nullptr, &bad))) return rc;
       d->last_status = bad > 0 ? LBM_EUNSTABLE : LBM_OK;
       if (bad > 0) return fail(LBM_EUNSTABLE, "watchdog: non-finite or out-of-range density");
     }
   }
+  if ((rc = flush_coalesce(d))) return fail(rc, cuda_error_string());
   return d->last_status;
 }
 
@@ -1528,7 +1664,7 @@ int lbm_work_per_step(const lbm_domain* d, long long* cell_updates, int* kernels
   long long cu = 0;
   for (int l = 0; l < d->mesh.L; ++l) cu += d->mesh.lv[l].n_fluid << l;
   if (cell_updates) *cell_updates = cu;
-  if (kernels) *kernels = kernels_per_step(d->mesh, 0);
+  if (kernels) *kernels = kernels_per_step(d, 0);
   return LBM_OK;
 }
 
@@ -1798,12 +1934,12 @@ int batch_advance(lbm_batch* b, int l, int parity) {
   if (l + 1 < b->L) {
     if ((rc = batch_advance(b, l + 1, 0))) return rc;
     if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) {
-           return l + 1 < d->mesh.L ? iface_explode(d, l, parity, s) : LBM_OK;
+           return l + 1 < d->mesh.L ? iface_transfer(d, l, parity, s, true, true) : LBM_OK;
          })))
       return rc;
     if ((rc = batch_advance(b, l + 1, 1))) return rc;
     if ((rc = fan_out(b, [&](lbm_domain* d, cudaStream_t s) {
-           int r = l + 1 < d->mesh.L ? iface_inflow(d, l, parity, s) : LBM_OK;
+           int r = l + 1 < d->mesh.L ? iface_coalesce(d, l, parity, s) : LBM_OK;
            if (!r && l == 0) r = end_coarse_step(d, parity, s);
            return r;
          })))

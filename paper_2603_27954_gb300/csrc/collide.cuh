@@ -79,6 +79,13 @@ __device__ __forceinline__ ZSeg z_segment(int unit, int zshift, int B) {
   const int nz = B >> zshift, z0 = (unit & ((1 << zshift) - 1)) * nz;
   return ZSeg{unit >> zshift, z0, z0 + nz};
 }
+// the active block of launched block index b (a launch over a block subset)
+__device__ __forceinline__ int block_of(const CollideArgs& a, int b) { return a.blocks ? a.blocks[b] : b; }
+__device__ __forceinline__ ZSeg z_segment(const CollideArgs& a, int unit, int zshift, int B) {
+  ZSeg z = z_segment(unit, zshift, B);
+  z.blk = block_of(a, z.blk);
+  return z;
+}
 
 // IDX: element-offset type, 32-bit when the level's array has < 2^31 elements
 // One active block `blk` of a level: even step (own slots) or odd step with
@@ -202,7 +209,7 @@ __device__ __forceinline__ void even_pair_block(const CollideArgs& a, const int 
 }
 template <int B, typename IDX, typename S>
 __global__ void __launch_bounds__(B * B / 2, LBM_PAIR_MINB) k_collide_even_p2(CollideArgs a) {
-  const ZSeg zg = z_segment(blockIdx.x, a.zshift_even, B);
+  const ZSeg zg = z_segment(a, blockIdx.x, a.zshift_even, B);
   even_pair_block<B, IDX, S>(a, zg.blk, zg);
 }
 
@@ -345,14 +352,14 @@ __device__ __forceinline__ void odd_pair_block(const CollideArgs& a, const int b
 template <int B, typename IDX, typename S, int MINB>
 __global__ void __launch_bounds__(B * B / 2, MINB) k_collide_odd_p2(CollideArgs a) {
   __shared__ IDX s_base[27];
-  const ZSeg zg = z_segment(blockIdx.x, a.zshift_odd, B);
+  const ZSeg zg = z_segment(a, blockIdx.x, a.zshift_odd, B);
   odd_pair_block<B, IDX, S>(a, zg.blk, s_base, zg);
 }
 
 template <int B, bool ODD, typename IDX, typename S>
 __global__ void __launch_bounds__(B * B, ODD ? LBM_ODD_MINB : LBM_EVEN_MINB) k_collide(CollideArgs a) {
   __shared__ IDX s_base[27];
-  const ZSeg zg = z_segment(blockIdx.x, ODD ? a.zshift_odd : a.zshift_even, B);
+  const ZSeg zg = z_segment(a, blockIdx.x, ODD ? a.zshift_odd : a.zshift_even, B);
   collide_block<B, ODD, IDX, S>(a, zg.blk, s_base, zg.z0, zg.z1);
 }
 
@@ -366,7 +373,7 @@ template <int B, bool ODD, typename IDX>
 __global__ void __launch_bounds__(B * B) k_collide_f64(CollideArgs a) {
   constexpr int C3 = B * B * B;
   __shared__ IDX s_base[27];
-  const ZSeg zg = z_segment(blockIdx.x, ODD ? a.zshift_odd : a.zshift_even, B);
+  const ZSeg zg = z_segment(a, blockIdx.x, ODD ? a.zshift_odd : a.zshift_even, B);
   const int blk = zg.blk;
   if (threadIdx.x < 27) s_base[threadIdx.x] = (IDX)a.nbr[(size_t)blk * 27 + threadIdx.x] * (IDX)(27 * C3);
   __syncthreads();
@@ -539,7 +546,7 @@ __global__ void __launch_bounds__(256, LBM_STAGED_MINB) k_collide_odd_staged(Col
   Stage16* st = reinterpret_cast<Stage16*>(smem);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NS * sizeof(Stage16));
   IDX* s_base = reinterpret_cast<IDX*>(smem + NS * sizeof(Stage16) + 128);
-  const int blk = blockIdx.x;
+  const int blk = block_of(a, blockIdx.x);
   const int t = threadIdx.x;
   if (t < 27) s_base[t] = (IDX)a.nbr[(size_t)blk * 27 + t] * (IDX)(27 * C3);
   if (t == 0) {
@@ -643,7 +650,7 @@ __global__ void __launch_bounds__(256, 2) k_collide_even_tma(CollideArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   float(*st)[27][256] = reinterpret_cast<float(*)[27][256]>(smem);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NS * 27 * 1024);
-  const int blk = blockIdx.x;
+  const int blk = block_of(a, blockIdx.x);
   const int t = threadIdx.x;
   const IDX own = (IDX)a.nbr[(size_t)blk * 27 + 13] * (IDX)(27 * C3);
   float* __restrict__ fb = reinterpret_cast<float*>(a.f) + own;
@@ -814,7 +821,7 @@ template <int B, typename IDX, typename S>
 __global__ void __launch_bounds__(B * B, odd_minb<S>()) k_collide_odd_cols(CollideArgs a) {
   __shared__ IDX s_base[27];
   __shared__ IDX s_col[std::is_same<S, __half>::value ? 9 * B * B : 1];
-  const ZSeg zg = z_segment(blockIdx.x, a.zshift_odd, B);
+  const ZSeg zg = z_segment(a, blockIdx.x, a.zshift_odd, B);
   odd_cols_block<B, IDX, S>(a, zg.blk, s_base, s_col, zg.z0, zg.z1);
 }
 

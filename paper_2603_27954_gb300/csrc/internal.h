@@ -193,6 +193,10 @@ struct Level {
   std::vector<int> seg_begin;                    // n_seg + 1 offsets into the ordered links
   std::vector<FaceEntry> face[2];
   std::vector<int> face_pos;  // per face entry: pulled-from cell (x, y, z, 0), periodic axes wrapped
+  // turbulent inflow: the distinct cells face entries pull the inflow
+  // equilibrium from (x, y, z, 0 each), and per face entry the index of its
+  // cell (-1 for an entry that copies a fluid value)
+  std::vector<int> turb_cells, turb_idx;
   // interface with the next finer level (this level = coarse)
   std::vector<ExplodeEntry> expl;
   std::vector<SaveEntry> save;
@@ -202,6 +206,12 @@ struct Level {
   // the walls may run beside the next interface transfer of the coarser level
   // (no slot one writes is read or written by the other; checked on the host)
   bool ovl_walls = false;
+  // per parity p of a collide: the active blocks it may update while the
+  // walls of the step before still run (no slot they touch is touched by
+  // those walls), n_windep[p] of them, followed by the others
+  std::vector<int> wblocks[2];
+  int n_windep[2] = {0, 0};
+  size_t off_wblocks[2] = {0, 0};
   // 32-bit forms (filled when narrow_ok) and the form on the device
   bool narrow_ok = false, narrow = false;
   std::vector<WallEntryN> wall_n[2];
@@ -271,6 +281,7 @@ struct CollideArgs {
   int zshift_even;    // log2 of the CTAs per active block (each walks B >> zshift slabs)
   int zshift_odd;     //   of the even and of the odd step (one-CTA-per-block kernels)
   RefShift ref;       // FP16 storage reference (unused for FP32)
+  const int* blocks;  // launch over these active blocks (n_active of them); nullptr: all, in order
 };
 int prepare_kernels();
 int launch_collide(const CollideArgs& a, int B, int odd, void* stream);
@@ -279,7 +290,10 @@ struct Ref27 {
   float v[27];
 };
 struct TurbArgs {      // turbulent inflow; n_modes == 0: uniform inflow equilibrium
-  const int* pos;       // per face entry: level-0 cell (x, y, z, 0) the value is pulled from
+  const int* idx;       // per face entry: index of the cell it pulls from, -1: the entry copies a value
+  const int* cells;     // per pulled-from cell: level-0 (x, y, z, 0)
+  float* vel;           // per pulled-from cell: the step's inflow velocity (ux, uy, uz, 0)
+  int n_cells;
   const float* modes;   // n_modes x kModeCols
   int n_modes;
   float u;              // mean inflow speed along x
@@ -315,11 +329,10 @@ int walls_partial_count(int n);
 // interface's ledger; c3_log2 = log2 of the cells per block (the direction of
 // an entry is the population plane of its destination slot); inv_sc / inv_sf
 // undo the storage scale of the coarse / fine level.
+// the explode, save and inflow entries of an interface in one launch
 int launch_explode(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int ne,
-                   const void* s, int ns, void* saved, int parity, LedgerDev* ledger, int c3_log2, float inv_sf,
-                   void* stream);
-int launch_inflow(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int n,
-                  const void* saved, int parity, LedgerDev* ledger, int c3_log2, float inv_sf, void* stream);
+                   const void* s, int ns, const void* ie, int ni, void* saved, int parity, LedgerDev* ledger,
+                   int c3_log2, float inv_sf, void* stream);
 int launch_coalesce(void* coarse, const void* fine, int esize, float ratio, const void* e, int narrow, int n,
                     const void* saved, int parity, LedgerDev* ledger, const LedgerConst& lc, int c3_log2,
                     float inv_sc, float inv_sf, void* stream);

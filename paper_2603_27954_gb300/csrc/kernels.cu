@@ -7,7 +7,7 @@
 //              momentum-exchange force: float-float warp sums, FP64 CTA
 //              partials, and the fixed-order FP64 total by the last CTA
 //              (deterministic).
-//  k_explode / k_inflow / k_coalesce   refinement-interface transfer.
+//  k_explode (with the inflow entries) / k_coalesce   refinement-interface transfer.
 //  k_fill      equilibrium initialisation; k_mass FP64 mass / momentum.
 //
 // The step is a bandwidth-bound stencil: every population is read once and
@@ -57,24 +57,17 @@ __device__ __forceinline__ float eq_dev(int i, float ux, float uy, float uz) {
   return eq_axis(a, ux) * eq_axis(b, uy) * eq_axis(c, uz) - w;
 }
 
-// faces with a turbulent inflow: entries that pull the inflow equilibrium get
-// it at the velocity U e_x + sum_n a_n cos(k_n . (p - U t e_x) + psi_n) of their
-// pulled-from cell centre p, t = coarse steps done (frozen field carried at U)
-template <typename S, typename E>
-__global__ void __launch_bounds__(128) k_faces_turb(S* __restrict__ f, const E* __restrict__ e, int n,
-                                                     TurbArgs tb) {
+// turbulent inflow velocity U e_x + sum_n a_n cos(k_n . (p - U t e_x) + psi_n)
+// at the centre p of every cell the faces pull the inflow equilibrium from,
+// t = coarse steps done (frozen field carried at U); once per cell and step
+__global__ void __launch_bounds__(128) k_turb_velocity(TurbArgs tb) {
   extern __shared__ float sm[];  // the mode table
   for (int k = threadIdx.x; k < tb.n_modes * kModeCols; k += blockDim.x) sm[k] = tb.modes[k];
   __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const E x = e[t];
-  if (x.src >= 0) {
-    f[x.dst] = f[x.src];
-    return;
-  }
-  const float px = tb.pos[4 * t] + 0.5f - tb.u * (float)(*tb.tick);
-  const float py = tb.pos[4 * t + 1] + 0.5f, pz = tb.pos[4 * t + 2] + 0.5f;
+  if (t >= tb.n_cells) return;
+  const float px = tb.cells[4 * t] + 0.5f - tb.u * (float)(*tb.tick);
+  const float py = tb.cells[4 * t + 1] + 0.5f, pz = tb.cells[4 * t + 2] + 0.5f;
   float ux = tb.u, uy = 0.0f, uz = 0.0f;
   for (int m = 0; m < tb.n_modes; ++m) {
     const float* r = sm + m * kModeCols;
@@ -83,8 +76,24 @@ __global__ void __launch_bounds__(128) k_faces_turb(S* __restrict__ f, const E* 
     uy = fmaf(r[4], c, uy);
     uz = fmaf(r[5], c, uz);
   }
+  reinterpret_cast<float4*>(tb.vel)[t] = make_float4(ux, uy, uz, 0.0f);
+}
+
+// faces with a turbulent inflow: entries that pull the inflow equilibrium get
+// it at their pulled-from cell's velocity of the step (k_turb_velocity)
+template <typename S, typename E>
+__global__ void __launch_bounds__(256) k_faces_turb(S* __restrict__ f, const E* __restrict__ e, int n,
+                                                     TurbArgs tb) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const E x = e[t];
+  if (x.src >= 0) {
+    f[x.dst] = f[x.src];
+    return;
+  }
+  const float4 v = reinterpret_cast<const float4*>(tb.vel)[tb.idx[t]];
   const float r = tb.shift ? eq_dev(x.dir, tb.u, 0.0f, 0.0f) : 0.0f;
-  Store<S>::st(f, x.dst, (eq_dev(x.dir, ux, uy, uz) - r) * tb.scale);
+  Store<S>::st(f, x.dst, (eq_dev(x.dir, v.x, v.y, v.z) - r) * tb.scale);
 }
 
 __global__ void k_tick(long long* tick) { *tick += 1; }
@@ -409,10 +418,13 @@ __device__ __forceinline__ void ledger_add(LedgerDev* __restrict__ L, int first,
   }
 }
 
-// A warp's running ledger sum over consecutive rounds of entries that share
-// one direction: entries add to it while the warp's direction stays the
-// same, and it is reduced and added to the ledger only when the direction
-// changes and at the end (one reduction per run instead of one per round).
+// A warp's running ledger sum over consecutive entries of a thread (the
+// explode and the inflow entry of the same index) that share one direction:
+// entries add to it while the warp's direction stays the same, and it is
+// reduced and added to the ledger only when the direction changes and at the
+// end.  (Four entries per thread cut the reductions further but slowed the
+// transfers' dependent gathers more: interface kernels 78.5 -> 85.7 us per
+// coarse step on GB300.)
 struct LedgerRun {
   long long acc = 0;
   int dir = -1;  // the run's direction, the same in every lane
@@ -444,13 +456,6 @@ __device__ __forceinline__ void ledger_run_add(LedgerRun& r, LedgerDev* __restri
   }
 }
 
-// entries per thread of the explode and inflow transfers: a warp walks
-// kIfaceRounds consecutive rounds of 32 entries.  One: more entries per
-// thread cut the ledger's reductions but slowed the transfers' dependent
-// gathers more (GB300, two-level tree workload: 4 rounds, interface kernels
-// 78.5 -> 85.7 us per coarse step without the ledger).
-constexpr int kIfaceRounds = 1;
-
 // population plane of an element offset (log2 of the cells per block given)
 __device__ __forceinline__ int plane_of(long long off, int c3_log2) { return (int)((off >> c3_log2) % 27); }
 
@@ -466,66 +471,60 @@ __device__ __forceinline__ float ll_to_float_odd(long long q) {
 // Interface kernels.  ratio = s_fine / s_coarse maps stored coarse values to
 // the fine scale (1 for FP32 and FP64); saved values are fine-scaled values of
 // the arithmetic type (FP32, FP64 for the double-precision form).
-template <typename S, typename E, typename SE>
+//
+// One kernel moves what the coarse step hands to the fine level, from three
+// entry tables: the explode entries (coarse post-collision values into the
+// fine ghost slots the second sub-step pulls from), the save entries (fine
+// values of the first sub-step that leave the box, for the coalesce
+// transfer) and the inflow entries (the values the fine cells at the box
+// edge pull at the next first sub-step).  Ghost slots live in ghost blocks,
+// which the first sub-step (an even step: own slots of active blocks only)
+// never touches, so the explode entries may run beside it.  The save sources,
+// slots (x, ibar) of active cells with x + c_i outside the box, and the
+// inflow destinations, slots (x, i) with x - c_i outside, are neither read
+// nor written by the second sub-step (either would need an active cell at
+// that outside point), so the save and inflow entries may run beside it.  An
+// inflow entry that takes a fine value (x - 2 c_i inside the box) reads it
+// from the slot the save entry copies, which nothing writes meanwhile.
+template <typename S, typename E, typename SE, typename IE>
 __global__ void __launch_bounds__(256) k_explode(S* __restrict__ fine, const S* __restrict__ coarse,
                                                  const E* __restrict__ e, int ne, const SE* __restrict__ s, int ns,
+                                                 const IE* __restrict__ ie, int ni,
                                                  typename Store<S>::V* __restrict__ saved, int parity, float ratio,
                                                  LedgerDev* __restrict__ ledger, int c3_log2, float inv_sf) {
   using V = typename Store<S>::V;
-  const int lane = threadIdx.x & 31;
-  const long long w0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * kIfaceRounds);
-  LedgerRun run;
-#pragma unroll
-  for (int k = 0; k < kIfaceRounds; ++k) {
-    const long long t = w0 + 32 * k + lane;
-    long long q = 0;
-    int dir = -1;
-    if (t < ne) {
-      const E x = e[t];
-      const V v = Store<S>::ld(coarse, parity ? x.src[1] : x.src[0]) * ratio;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long q = 0, qi = 0;
+  int dir = -1, diri = -1;
+  if (t < ne) {
+    const E x = e[t];
+    const V v = Store<S>::ld(coarse, parity ? x.src[1] : x.src[0]) * ratio;
+    Store<S>::st(fine, x.dst, v);
+    if (ledger) {
+      q = fx40(v * (V)inv_sf);
+      dir = 26 - plane_of(x.dst, c3_log2);
+    }
+  }
+  if (t < ns) saved[t] = Store<S>::ld(fine, s[t].src);
+  if (t < ni) {
+    const IE x = ie[t];
+    if (x.r >= 0) {
+      Store<S>::st(fine, x.dst, Store<S>::ld(fine, s[x.r].src));  // a fine value back into the fine level: no flow
+    } else {
+      const V v = Store<S>::ld(coarse, parity ? x.csrc[1] : x.csrc[0]) * ratio;
       Store<S>::st(fine, x.dst, v);
       if (ledger) {
-        q = fx40(v * (V)inv_sf);
-        dir = 26 - plane_of(x.dst, c3_log2);
+        qi = fx40(v * (V)inv_sf);
+        diri = plane_of(x.dst, c3_log2);
       }
     }
-    if (t < ns) saved[t] = Store<S>::ld(fine, s[t].src);
-    if (ledger) ledger_run_add(run, ledger, 0, q, dir);
   }
-  if (ledger) ledger_flush(run, ledger, 0);
-}
-
-template <typename S, typename E>
-__global__ void __launch_bounds__(256) k_inflow(S* __restrict__ fine, const S* __restrict__ coarse,
-                                                const E* __restrict__ e, int n,
-                                                const typename Store<S>::V* __restrict__ saved, int parity,
-                                                float ratio, LedgerDev* __restrict__ ledger, int c3_log2,
-                                                float inv_sf) {
-  using V = typename Store<S>::V;
-  const int lane = threadIdx.x & 31;
-  const long long w0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * kIfaceRounds);
-  LedgerRun run;
-#pragma unroll
-  for (int k = 0; k < kIfaceRounds; ++k) {
-    const long long t = w0 + 32 * k + lane;
-    long long q = 0;
-    int dir = -1;
-    if (t < n) {
-      const E x = e[t];
-      if (x.r >= 0) {
-        Store<S>::st(fine, x.dst, saved[x.r]);  // a fine value back into the fine level: no flow
-      } else {
-        const V v = Store<S>::ld(coarse, parity ? x.csrc[1] : x.csrc[0]) * ratio;
-        Store<S>::st(fine, x.dst, v);
-        if (ledger) {
-          q = fx40(v * (V)inv_sf);
-          dir = plane_of(x.dst, c3_log2);
-        }
-      }
-    }
-    if (ledger) ledger_run_add(run, ledger, 0, q, dir);
+  if (ledger) {
+    LedgerRun run;
+    ledger_run_add(run, ledger, 0, q, dir);
+    ledger_run_add(run, ledger, 0, qi, diri);
+    ledger_flush(run, ledger, 0);
   }
-  if (ledger) ledger_flush(run, ledger, 0);
 }
 
 // Coarse cell next to the fine region, one direction: the mean of its 8
@@ -899,9 +898,12 @@ template <typename E>
 void faces_typed(void* f, int esize, const E* e, int n, const double feq[27], const TurbArgs& turb,
                  cudaStream_t s) {
   if (turb.n_modes > 0 && esize != 8) {
-    const size_t smem = (size_t)turb.n_modes * kModeCols * sizeof(float);
-    if (esize == 2) k_faces_turb<__half, E><<<blocks_for(n, 128), 128, smem, s>>>((__half*)f, e, n, turb);
-    else k_faces_turb<float, E><<<blocks_for(n, 128), 128, smem, s>>>((float*)f, e, n, turb);
+    if (turb.n_cells > 0) {
+      const size_t smem = (size_t)turb.n_modes * kModeCols * sizeof(float);
+      k_turb_velocity<<<blocks_for(turb.n_cells, 128), 128, smem, s>>>(turb);
+    }
+    if (esize == 2) k_faces_turb<__half, E><<<blocks_for(n, 256), 256, 0, s>>>((__half*)f, e, n, turb);
+    else k_faces_turb<float, E><<<blocks_for(n, 256), 256, 0, s>>>((float*)f, e, n, turb);
     return;
   }
   if (esize == 8) {
@@ -974,51 +976,31 @@ int launch_segments(const double* link_force, const int* seg_begin, int n_seg, d
   return check_launch("segments");
 }
 
-template <typename E, typename SE>
+template <typename E, typename SE, typename IE>
 void explode_typed(void* fine, const void* coarse, int esize, float ratio, const E* e, int ne, const SE* sv, int ns,
-                   void* saved, int parity, LedgerDev* ledger, int c3_log2, float inv_sf, cudaStream_t s) {
-  const unsigned g = blocks_for(ne > ns ? ne : ns, 256 * kIfaceRounds);
+                   const IE* ie, int ni, void* saved, int parity, LedgerDev* ledger, int c3_log2, float inv_sf,
+                   cudaStream_t s) {
+  const unsigned g = blocks_for(std::max(ne, std::max(ns, ni)), 256);
   by_storage(esize, [&](auto* tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     using V = typename Store<S>::V;
-    k_explode<S, E, SE><<<g, 256, 0, s>>>((S*)fine, (const S*)coarse, e, ne, sv, ns, (V*)saved, parity, ratio, ledger,
-                                           c3_log2, inv_sf);
+    k_explode<S, E, SE, IE><<<g, 256, 0, s>>>((S*)fine, (const S*)coarse, e, ne, sv, ns, ie, ni, (V*)saved, parity,
+                                               ratio, ledger, c3_log2, inv_sf);
   });
 }
 
 int launch_explode(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int ne,
-                   const void* sv, int ns, void* saved, int parity, LedgerDev* ledger, int c3_log2, float inv_sf,
-                   void* stream) {
-  if (ne == 0 && ns == 0) return LBM_OK;
+                   const void* sv, int ns, const void* ie, int ni, void* saved, int parity, LedgerDev* ledger,
+                   int c3_log2, float inv_sf, void* stream) {
+  if (ne == 0 && ns == 0 && ni == 0) return LBM_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (narrow)
-    explode_typed(fine, coarse, esize, ratio, (const ExplodeEntryN*)e, ne, (const SaveEntryN*)sv, ns, saved, parity,
-                  ledger, c3_log2, inv_sf, s);
+    explode_typed(fine, coarse, esize, ratio, (const ExplodeEntryN*)e, ne, (const SaveEntryN*)sv, ns,
+                  (const InflowEntryN*)ie, ni, saved, parity, ledger, c3_log2, inv_sf, s);
   else
-    explode_typed(fine, coarse, esize, ratio, (const ExplodeEntry*)e, ne, (const SaveEntry*)sv, ns, saved, parity,
-                  ledger, c3_log2, inv_sf, s);
+    explode_typed(fine, coarse, esize, ratio, (const ExplodeEntry*)e, ne, (const SaveEntry*)sv, ns,
+                  (const InflowEntry*)ie, ni, saved, parity, ledger, c3_log2, inv_sf, s);
   return check_launch("explode");
-}
-
-template <typename E>
-void inflow_typed(void* fine, const void* coarse, int esize, float ratio, const E* e, int n, const void* saved,
-                  int parity, LedgerDev* ledger, int c3_log2, float inv_sf, cudaStream_t s) {
-  by_storage(esize, [&](auto* tag) {
-    using S = std::remove_pointer_t<decltype(tag)>;
-    using V = typename Store<S>::V;
-    k_inflow<S, E><<<blocks_for(n, 256 * kIfaceRounds), 256, 0, s>>>((S*)fine, (const S*)coarse, e, n, (const V*)saved, parity,
-                                                       ratio, ledger, c3_log2, inv_sf);
-  });
-}
-
-int launch_inflow(void* fine, const void* coarse, int esize, float ratio, const void* e, int narrow, int n,
-                  const void* saved, int parity, LedgerDev* ledger, int c3_log2, float inv_sf, void* stream) {
-  if (n == 0) return LBM_OK;
-  cudaStream_t s = (cudaStream_t)stream;
-  if (narrow)
-    inflow_typed(fine, coarse, esize, ratio, (const InflowEntryN*)e, n, saved, parity, ledger, c3_log2, inv_sf, s);
-  else inflow_typed(fine, coarse, esize, ratio, (const InflowEntry*)e, n, saved, parity, ledger, c3_log2, inv_sf, s);
-  return check_launch("inflow");
 }
 
 template <typename E>

@@ -733,6 +733,27 @@ void permute(std::vector<T>& v, const std::vector<long long>& perm, int stride =
 // per-branch ranges) and are sorted by destination inside each branch; the
 // two parity tables of the faces and of the links share one order with their
 // per-entry companions (face positions, links).
+// The distinct outside cells the level-0 face entries pull the inflow
+// equilibrium from: several entries pull the same cell (along different
+// directions), so a turbulent inflow velocity is evaluated once per cell.
+static void turbulence_cells(Mesh& m) {
+  Level& v = m.lv[0];
+  v.turb_cells.clear();
+  v.turb_idx.assign(v.face[0].size(), -1);
+  if (v.face_pos.size() != 4 * v.face[0].size()) return;
+  const long long sx = (long long)m.n0[0] + 2, sy = (long long)m.n0[1] + 2;
+  std::unordered_map<long long, int> at;
+  at.reserve(v.face[0].size() / 4 + 16);
+  for (size_t t = 0; t < v.face[0].size(); ++t) {
+    if (v.face[0][t].src >= 0) continue;
+    const int* p = &v.face_pos[4 * t];
+    const long long key = ((long long)(p[2] + 1) * sy + (p[1] + 1)) * sx + (p[0] + 1);
+    auto it = at.emplace(key, (int)(v.turb_cells.size() / 4));
+    if (it.second) v.turb_cells.insert(v.turb_cells.end(), {p[0], p[1], p[2], 0});
+    v.turb_idx[t] = it.first->second;
+  }
+}
+
 static void order_tables(Mesh& m) {
   for (int l = 0; l < m.L; ++l) {
     Level& v = m.lv[l];
@@ -955,6 +976,53 @@ static void overlap_checks(Mesh& m) {
   m.ovl_faces = faces_ok;
 }
 
+// Per collide parity p, the active blocks whose update touches no slot the
+// wall kernel of the step before (table wall[1 - p]) reads or writes, then
+// the others.  An even step touches the own slots of its cells; an odd step
+// touches slot (y, m) only from cell y - c_m (its pull of f_mbar and its push
+// of f_m), so each wall slot names exactly one updating cell.
+static void wall_blocks(Mesh& m) {
+  for (int l = 0; l < m.L; ++l) {
+    Level& v = m.lv[l];
+    for (int p = 0; p < 2; ++p) {
+      v.wblocks[p].clear();
+      v.n_windep[p] = 0;
+    }
+    if (v.wall[0].empty()) continue;
+    const long long C3 = v.cells_per_block();
+    const int B = v.B;
+    for (int p = 0; p < 2; ++p) {
+      std::vector<char> dep(v.n_active, 0);
+      auto touch = [&](long long off) {
+        if (off < 0) return;
+        const long long sb = off / (kQ * C3);
+        if (p == 0) {
+          if (sb < v.n_active) dep[(size_t)sb] = 1;
+          return;
+        }
+        const int dir = (int)((off / C3) % kQ), cell = (int)(off % C3);
+        int o[3];
+        block_origin(v, v.grid_of[(size_t)sb], o);
+        int local;
+        const int s = v.locate(o[0] + cell % B - cx(dir), o[1] + (cell / B) % B - cy(dir),
+                               o[2] + cell / (B * B) - cz(dir), &local);
+        if (s >= 0 && s < v.n_active) dep[(size_t)s] = 1;
+      };
+      for (const WallEntry& w : v.wall[1 - p]) {
+        touch(w.dst);
+        touch(w.a);
+        touch(w.b);
+        touch(w.c);
+      }
+      for (int s = 0; s < v.n_active; ++s)
+        if (!dep[(size_t)s]) v.wblocks[p].push_back(s);
+      v.n_windep[p] = (int)v.wblocks[p].size();
+      for (int s = 0; s < v.n_active; ++s)
+        if (dep[(size_t)s]) v.wblocks[p].push_back(s);
+    }
+  }
+}
+
 int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vector<Prim>& prims, Mesh* out) {
   Mesh& m = *out;
   m.L = d.levels;
@@ -1059,7 +1127,9 @@ int build_mesh(const lbm_domain_desc& d, const int boxes[6][6], const std::vecto
     if (rc) return rc;
   }
   order_tables(m);
+  turbulence_cells(m);
   overlap_checks(m);
+  wall_blocks(m);
   return LBM_OK;
 }
 
