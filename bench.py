@@ -88,7 +88,17 @@ def tune(L, dom, u_in, steps):
     best, _ = dom.autotune(steps)
     L.lbm_init_uniform(dom.h, 1.0, np.array([u_in, 0.0, 0.0]))
     L.lbm_reset_force(dom.h)
-    return best.as_dict()
+    return dict(best.as_dict(), overlap_features=dom.get_overlap_features())
+
+
+def fixed_schedule(dom, spec):
+    """odd,even,z_even,z_odd[,overlap feature mask]: a fixed schedule (for
+    profiling the kernels a tuned run chose)."""
+    v = [int(x) for x in spec.split(",")]
+    dom.set_schedule(0, *v[:4])
+    if len(v) > 4:
+        dom.set_overlap_features(v[4])
+    return dict(dom.get_schedule().as_dict(), overlap_features=dom.get_overlap_features())
 
 
 def measure_form(L, W, torch, stream, case, precision, steps, warmup, timing_steps=20, tune_steps=3, schedule=None):
@@ -100,9 +110,7 @@ def measure_form(L, W, torch, stream, case, precision, steps, warmup, timing_ste
     dom = L.Domain(desc, tree=tree, stream=stream)
     updates, _ = dom.work_per_step()
     if schedule:
-        odd, even, ze, zo = (int(v) for v in schedule.split(","))
-        dom.set_schedule(0, odd, even, ze, zo)
-        schedule = dom.get_schedule().as_dict()
+        schedule = fixed_schedule(dom, schedule)
     else:
         schedule = tune(L, dom, c["u_in"], tune_steps)
     dom.step(warmup)
@@ -371,10 +379,10 @@ def main():
     ap.add_argument("--cd-steps", type=int, default=300,
                     help="coarse steps of the scaled-down case for the C_D comparison with the oracle")
     ap.add_argument("--schedule", default=None,
-                    help="odd,even,z_even,z_odd: fix the main workload's schedule instead of autotuning it "
-                         "(for profiling the kernels a tuned run chose)")
+                    help="odd,even,z_even,z_odd[,overlap mask]: fix the main workload's schedule instead of "
+                         "autotuning it (for profiling the kernels a tuned run chose)")
     ap.add_argument("--fp16-schedule", default=None,
-                    help="odd,even,z_even,z_odd: fix the FP16 form's schedule instead of autotuning it")
+                    help="odd,even,z_even,z_odd[,overlap mask]: fix the FP16 form's schedule instead of autotuning it")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
@@ -401,13 +409,12 @@ def main():
     desc, tree, c = workload_desc(L, W, CASE)
     stream = torch.cuda.Stream()
     dom = L.Domain(desc, tree=tree, stream=stream)
-    updates, kernels = dom.work_per_step()
     if args.schedule:
-        odd, even, ze, zo = (int(v) for v in args.schedule.split(","))
-        dom.set_schedule(0, odd, even, ze, zo)
-        schedule = dom.get_schedule().as_dict()
+        schedule = fixed_schedule(dom, args.schedule)
     else:
         schedule = tune(L, dom, c["u_in"], 3)
+    # launches per coarse step under the schedule and reorderings chosen
+    updates, kernels = dom.work_per_step()
     dom.step(args.warmup)
     torch.cuda.synchronize()
 

@@ -430,7 +430,10 @@ int lbm_inflow_modes(const lbm_domain* d, double* modes, int n, int* count);
    lbm_autotune and lbm_batch_autotune time every available candidate for
    `steps` coarse steps (after one untimed step each) with CUDA events and
    keep the fastest; they advance the simulation by the steps they time, so
-   re-initialise (lbm_init_uniform) before a production run. */
+   re-initialise (lbm_init_uniform) before a production run.  lbm_autotune
+   then times a few masks of lbm_set_overlap_features under the chosen
+   schedule (overlap and graphs on; at least 16 steps each, twice) and leaves
+   the fastest set (lbm_get_overlap_features reports it). */
 typedef struct {
   int ctas_per_sm;   /* batches only; ignored by single domains */
   int odd_variant;   /* lbm_odd_variant */
@@ -484,6 +487,37 @@ int lbm_set_wide_offsets(lbm_domain* d, int on);
    (default on).  Results are identical either way.  Toggling recaptures the
    graphs. */
 int lbm_set_overlap(lbm_domain* d, int on);
+
+/* The reorderings lbm_set_overlap switches on, each separately (all by
+   default).  Every one reorders the same launches over the domain's stream
+   and side streams where the host check, or the slot rules of the AA
+   update, show that the kernels it places side by side touch disjoint
+   slots; results are identical under every mask.
+   LBM_OVL_BRANCHES: level-0 faces and wall kernels as parallel branches.
+   LBM_OVL_LEVELS: a level without cut links runs its collide, faces and
+     (with LBM_OVL_TRANSFERS) explode transfer beside the finer level's
+     first sub-step.
+   LBM_OVL_TRANSFERS: the save and inflow transfers beside the finer
+     level's second sub-step (when the finer level's walls touch none of
+     their slots).
+   LBM_OVL_DEFER: a level's coalesce transfer at the head of its next step
+     (lbm_step runs the pending ones before it returns).
+   LBM_OVL_WALL_SPLIT: the finest level's second sub-step updates the
+     blocks its first sub-step's walls do not touch before those walls
+     finish (two launches).
+   Default: LBM_OVL_BRANCHES | LBM_OVL_LEVELS | LBM_OVL_TRANSFERS;
+   lbm_autotune also tries masks with the other two and keeps the fastest.
+   Unknown bits give LBM_EINVAL.  Changing the mask recaptures the graphs. */
+enum {
+  LBM_OVL_BRANCHES = 1,
+  LBM_OVL_LEVELS = 2,
+  LBM_OVL_TRANSFERS = 4,
+  LBM_OVL_DEFER = 8,
+  LBM_OVL_WALL_SPLIT = 16,
+  LBM_OVL_ALL = 31
+};
+int lbm_set_overlap_features(lbm_domain* d, int mask);
+int lbm_get_overlap_features(const lbm_domain* d, int* mask);
 /* What that check found: *faces = 1 if the level-0 faces may run as a
    branch; bit l of *walls set if the walls of level l may.  Either pointer
    may be NULL.  Needs lbm_set_geometry; no device work. */

@@ -128,6 +128,10 @@ struct lbm_domain {
   // still to run (-1: none); lbm_step runs them before it returns
   std::vector<int> pend_coal;
   int wall_branch_level = -1;  // level whose walls branch 1 carries
+  // reorderings on while overlap is on (deferred coalesce and the collide
+  // split around the walls join measured slower on the tree workloads;
+  // lbm_autotune tries them)
+  int ovl_feat = LBM_OVL_BRANCHES | LBM_OVL_LEVELS | LBM_OVL_TRANSFERS;
   int watchdog = 0;
   int last_status = LBM_OK;
   // timing
@@ -183,7 +187,7 @@ void pin_tables(lbm_domain* d) {
       pin(v.face[p].data(), v.face[p].size() * sizeof(FaceEntry));
     }
     pin(v.expl.data(), v.expl.size() * sizeof(ExplodeEntry));
-    pin(v.save.data(), v.save.size() * sizeof(SaveEntry));
+    pin(v.save_dev.data(), v.save_dev.size() * sizeof(SaveEntry));
     pin(v.infl.data(), v.infl.size() * sizeof(InflowEntry));
     pin(v.coal.data(), v.coal.size() * sizeof(CoalesceEntry));
   }
@@ -349,6 +353,9 @@ void destroy_side_streams(lbm_domain* d) {
   }
 }
 
+// whether a reordering of the step is on
+bool ovl(const lbm_domain* d, int feature) { return d->overlap && !d->timing && (d->ovl_feat & feature); }
+
 // level l after its collide-stream sweep: faces (level 0), bounce-back and
 // momentum exchange, per-branch and total force reductions (finest level).
 // With `branches` the faces and the walls run on side streams where the host
@@ -359,7 +366,7 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s, bool branche
   void* f = dm->base + v.off_f;
   const int esize = v.esize;
   int rc;
-  branches = branches && dm->overlap && !dm->timing && s == dm->stream;
+  branches = branches && ovl(dm, LBM_OVL_BRANCHES) && s == dm->stream;
   if (l == 0 && !v.face[parity].empty()) {
     cudaStream_t fs = s;
     if (branches && m.ovl_faces && (rc = fork_branch(dm, 0, &fs))) return rc;
@@ -475,7 +482,7 @@ int end_coarse_step(lbm_domain* dm, int parity, cudaStream_t s) {
 // join of the walls its previous step left running on branch 1: first the
 // blocks those walls do not touch, then the rest
 bool wall_split(const lbm_domain* dm, const Level& v, int l, int parity) {
-  return dm->overlap && !dm->timing && dm->pend[1] && dm->wall_branch_level == l && v.n_windep[parity] > 0 &&
+  return ovl(dm, LBM_OVL_WALL_SPLIT) && dm->pend[1] && dm->wall_branch_level == l && v.n_windep[parity] > 0 &&
          v.n_windep[parity] < v.n_active && dm->odd_variant != LBM_ODD_STAGED;
 }
 
@@ -490,7 +497,7 @@ int advance(lbm_domain* dm, int l, int parity) {
   // the finer levels' first sub-step (disjoint arrays), joined before explode;
   // not when it has cut links (the wall kernels of all levels share their
   // force partials)
-  const bool split = l + 1 < m.L && dm->overlap && !dm->timing && v.wall[0].empty();
+  const bool split = l + 1 < m.L && ovl(dm, LBM_OVL_LEVELS) && v.wall[0].empty();
   cudaStream_t cs = dm->stream;
   if (split && (rc = fork_level(dm, l, &cs))) return rc;
   if ((int)dm->pend_coal.size() != m.L) dm->pend_coal.assign(m.L, -1);
@@ -502,15 +509,21 @@ int advance(lbm_domain* dm, int l, int parity) {
     dm->pend_coal[l] = -1;
   }
   if (wsplit) {
-    // (a level with walls is never split off: cs is the domain's stream)
+    // the blocks the walls do not touch on this stream (a level with walls
+    // is never split off: cs is the domain's stream); the others on the
+    // walls' branch after the walls and after everything this stream did so
+    // far (the coarser level's explode among it).  The next fork or the end
+    // of the coarse step joins the branch.
+    CK(cudaEventRecord(dm->ev_fork[1], dm->stream));
+    CK(cudaStreamWaitEvent(dm->side[1], dm->ev_fork[1], 0));
     CollideArgs a = collide_args(dm, l);
     a.blocks = dm->dev<int>(v.off_wblocks[parity]);
     a.n_active = v.n_windep[parity];
     if ((rc = launch_collide(a, v.B, parity, cs))) return rc;
-    if ((rc = join_branch(dm, 1))) return rc;
     a.blocks += v.n_windep[parity];
     a.n_active = v.n_active - v.n_windep[parity];
-    if ((rc = launch_collide(a, v.B, parity, cs))) return rc;
+    if ((rc = launch_collide(a, v.B, parity, dm->side[1]))) return rc;
+    if ((rc = close_branch(dm, 1))) return rc;
   } else {
     Timed t(dm, parity ? KC_COLLIDE_ODD : KC_COLLIDE, v.n_fluid);
     if ((rc = launch_collide(collide_args(dm, l), v.B, parity, cs))) return rc;
@@ -521,7 +534,8 @@ int advance(lbm_domain* dm, int l, int parity) {
     // finer level's walls touch none of their slots (host check); else in
     // the serial order
     const Level& F = m.lv[l + 1];
-    const bool beside = dm->overlap && !dm->timing && (F.wall[0].empty() || F.ovl_walls);
+    const bool walls_clear = F.wall[0].empty() || F.ovl_walls;
+    const bool beside = ovl(dm, LBM_OVL_TRANSFERS) && walls_clear;
     // explode right after this level's collide, on its side stream beside
     // the finer level's first sub-step when the level is split off
     const bool expl_side = split && beside;
@@ -543,7 +557,7 @@ int advance(lbm_domain* dm, int l, int parity) {
     // the coalesce transfer waits for the head of this level's next step,
     // beside the finer level's first sub-step (which touches neither the
     // fine ghost and saved values it reads nor this level)
-    if (beside) dm->pend_coal[l] = parity;
+    if (ovl(dm, LBM_OVL_DEFER) && walls_clear) dm->pend_coal[l] = parity;
     else if ((rc = iface_coalesce(dm, l, parity, dm->stream))) return rc;
   }
   if (l == 0) return end_coarse_step(dm, parity, dm->stream);
@@ -573,20 +587,26 @@ int kernels_per_step(const lbm_domain* d, int l) {
   int k = 1;
   // the finest level's second sub-step in two launches around the join of
   // the first sub-step's walls
+  const bool on = d->overlap;
   if (l + 2 == m.L) {
     const Level& F = m.lv[l + 1];
-    if (d->overlap && F.ovl_walls && F.n_windep[1] > 0 && F.n_windep[1] < F.n_active &&
-        d->odd_variant != LBM_ODD_STAGED)
+    if (on && (d->ovl_feat & LBM_OVL_WALL_SPLIT) && (d->ovl_feat & LBM_OVL_BRANCHES) && F.ovl_walls &&
+        F.n_windep[1] > 0 && F.n_windep[1] < F.n_active && d->odd_variant != LBM_ODD_STAGED)
       k += 1;
   }
   if (l == 0 && !v.face[0].empty()) k += 1;
   if (l == 0 && m.turbulent) k += 2;
   if (l == 0 && m.friction) k += 2;
   if (!v.wall[0].empty()) k += 1;
-  // explode, save + inflow (launches of their own beside the finer level's
-  // two sub-steps while overlap is on), coalesce
-  if (l + 1 < m.L) k += 2 * kernels_per_step(d, l + 1) + (v.expl.empty() ? 0 : 1) +
-                        (v.save.size() || v.infl.size() ? 1 : 0) + (v.coal.empty() ? 0 : 1);
+  // explode, save + inflow (launches of their own when the transfers run
+  // beside the finer level's sub-steps, else one), coalesce
+  if (l + 1 < m.L) {
+    const Level& F = m.lv[l + 1];
+    const bool beside = on && (d->ovl_feat & LBM_OVL_TRANSFERS) && (F.wall[0].empty() || F.ovl_walls);
+    const bool any = v.expl.size() || v.save.size() || v.infl.size();
+    k += 2 * kernels_per_step(d, l + 1) + (v.coal.empty() ? 0 : 1) +
+         (beside ? (v.expl.empty() ? 0 : 1) + (v.save.size() || v.infl.size() ? 1 : 0) : (any ? 1 : 0));
+  }
   return k;
 }
 
@@ -723,8 +743,7 @@ int build(lbm_domain* d) {
       lc.c[4 * flow + 3] += cz(dir) * wr;
     };
     for (const ExplodeEntry& e : v.expl) add(0, 26 - (int)((e.dst / c3) % 27), 1.0);
-    for (const InflowEntry& e : v.infl)
-      if (e.r < 0) add(0, (int)((e.dst / c3) % 27), 1.0);
+    for (const InflowEntry& e : v.infl) add(0, (int)((e.dst / c3) % 27), 1.0);
     for (const CoalesceEntry& e : v.coal) {
       const int dir = 26 - (int)((e.dst[0] / c3) % 27);
       add(1, dir, e.nfine);
@@ -786,7 +805,7 @@ int upload_tables(lbm_domain* d) {
       CK(cp(v.off_face[p], v.face[p].data(), v.face[p].size() * sizeof(FaceEntry)));
     }
     CK(cp(v.off_expl, v.expl.data(), v.expl.size() * sizeof(ExplodeEntry)));
-    CK(cp(v.off_save, v.save.data(), v.save.size() * sizeof(SaveEntry)));
+    CK(cp(v.off_save, v.save_dev.data(), v.save_dev.size() * sizeof(SaveEntry)));
     CK(cp(v.off_infl, v.infl.data(), v.infl.size() * sizeof(InflowEntry)));
     CK(cp(v.off_coal, v.coal.data(), v.coal.size() * sizeof(CoalesceEntry)));
   }
@@ -1595,6 +1614,19 @@ int lbm_set_overlap(lbm_domain* d, int on) {
   return LBM_OK;
 }
 
+int lbm_set_overlap_features(lbm_domain* d, int mask) {
+  if (!d || (mask & ~LBM_OVL_ALL)) return fail(LBM_EINVAL, "bad argument");
+  if (d->ovl_feat != mask) free_graphs(d);
+  d->ovl_feat = mask;
+  return LBM_OK;
+}
+
+int lbm_get_overlap_features(const lbm_domain* d, int* mask) {
+  if (!d || !mask) return fail(LBM_EINVAL, "null argument");
+  *mask = d->ovl_feat;
+  return LBM_OK;
+}
+
 int lbm_get_overlap(const lbm_domain* d, int* faces, int* walls) {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
@@ -1850,6 +1882,29 @@ int lbm_autotune(lbm_domain* d, int steps, lbm_schedule* best, double* ms_per_st
   }
   rc = lbm_set_schedule(d, &b);
   if (rc) return rc;
+  // then the reorderings of the step under that schedule: a few candidate
+  // masks, each timed twice over at least 16 steps (their differences are a
+  // few per cent)
+  if (d->overlap && d->use_graphs) {
+    const int kMasks[] = {LBM_OVL_BRANCHES | LBM_OVL_LEVELS | LBM_OVL_TRANSFERS, LBM_OVL_BRANCHES | LBM_OVL_LEVELS,
+                          LBM_OVL_ALL & ~LBM_OVL_WALL_SPLIT, LBM_OVL_ALL & ~LBM_OVL_DEFER, LBM_OVL_ALL,
+                          LBM_OVL_BRANCHES};
+    const int n = std::max(steps, 16);
+    double mbest = std::numeric_limits<double>::infinity();
+    int mask = d->ovl_feat;
+    for (int rep = 0; rep < 2; ++rep)
+      for (int k = 0; k < 6; ++k) {
+        const int m = kMasks[rep ? 5 - k : k];
+        double ms;
+        if ((rc = lbm_set_overlap_features(d, m)) || (rc = time_steps(d, n, &ms))) return rc;
+        if (ms < mbest) {
+          mbest = ms;
+          mask = m;
+        }
+      }
+    if ((rc = lbm_set_overlap_features(d, mask))) return rc;
+    bms = std::min(bms, mbest);
+  }
   if (best) *best = b;
   if (ms_per_step) *ms_per_step = bms;
   return LBM_OK;

@@ -95,8 +95,8 @@ struct SaveEntry {       // fine post-collision value of the first fine step kep
 };
 struct InflowEntry {     // fine inflow for the next first fine step
   long long dst;         // fine own slot
-  long long csrc[2];     // coarse post-collision slot per coarse parity (used when r < 0)
-  int r;                 // index into the saved values, or -1
+  long long csrc[2];     // coarse post-collision slot per coarse parity
+  int sv;                // saved value the destination holds before this write (its save index), or -1
   int pad;
 };
 struct CoalesceEntry {   // coarse cell next to the fine region, one direction
@@ -127,7 +127,7 @@ struct SaveEntryN {
 struct InflowEntryN {
   int dst;
   int csrc[2];
-  int r;
+  int sv;
 };
 struct CoalesceEntryN {
   int dst[2];
@@ -200,6 +200,9 @@ struct Level {
   // interface with the next finer level (this level = coarse)
   std::vector<ExplodeEntry> expl;
   std::vector<SaveEntry> save;
+  // the save table as the device gets it: entries whose slot an inflow entry
+  // saves itself (before overwriting it) carry src = -1
+  std::vector<SaveEntry> save_dev;
   std::vector<InflowEntry> infl;
   std::vector<CoalesceEntry> coal;
   double wall_rest[3] = {0, 0, 0};  // sum over the cut links of c_i 2 w_i

@@ -483,9 +483,12 @@ __device__ __forceinline__ float ll_to_float_odd(long long q) {
 // slots (x, ibar) of active cells with x + c_i outside the box, and the
 // inflow destinations, slots (x, i) with x - c_i outside, are neither read
 // nor written by the second sub-step (either would need an active cell at
-// that outside point), so the save and inflow entries may run beside it.  An
-// inflow entry that takes a fine value (x - 2 c_i inside the box) reads it
-// from the slot the save entry copies, which nothing writes meanwhile.
+// that outside point), so the save and inflow entries may run beside it.
+// Every save source is also an inflow destination (slot (b, ibar) with
+// b + c_i outside the box is where b pulls f_ibar at the next first
+// sub-step): the inflow entry's thread saves it before writing, and the save
+// entry itself is skipped (src = -1), so no thread reads a slot another
+// thread of the launch writes.
 template <typename S, typename E, typename SE, typename IE>
 __global__ void __launch_bounds__(256) k_explode(S* __restrict__ fine, const S* __restrict__ coarse,
                                                  const E* __restrict__ e, int ne, const SE* __restrict__ s, int ns,
@@ -505,18 +508,20 @@ __global__ void __launch_bounds__(256) k_explode(S* __restrict__ fine, const S* 
       dir = 26 - plane_of(x.dst, c3_log2);
     }
   }
-  if (t < ns) saved[t] = Store<S>::ld(fine, s[t].src);
+  if (t < ns) {
+    const auto src = s[t].src;
+    if (src >= 0) saved[t] = Store<S>::ld(fine, src);
+  }
   if (t < ni) {
     const IE x = ie[t];
-    if (x.r >= 0) {
-      Store<S>::st(fine, x.dst, Store<S>::ld(fine, s[x.r].src));  // a fine value back into the fine level: no flow
-    } else {
-      const V v = Store<S>::ld(coarse, parity ? x.csrc[1] : x.csrc[0]) * ratio;
-      Store<S>::st(fine, x.dst, v);
-      if (ledger) {
-        qi = fx40(v * (V)inv_sf);
-        diri = plane_of(x.dst, c3_log2);
-      }
+    // a destination that also holds a value leaving the box is saved by
+    // this thread before it is overwritten
+    if (x.sv >= 0) saved[x.sv] = Store<S>::ld(fine, x.dst);
+    const V v = Store<S>::ld(coarse, parity ? x.csrc[1] : x.csrc[0]) * ratio;
+    Store<S>::st(fine, x.dst, v);
+    if (ledger) {
+      qi = fx40(v * (V)inv_sf);
+      diri = plane_of(x.dst, c3_log2);
     }
   }
   if (ledger) {

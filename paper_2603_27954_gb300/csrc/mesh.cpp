@@ -481,9 +481,8 @@ int build_faces(Mesh& m) {
 // region (see the oracle's description of the same scheme); it reduces to:
 //  * before the second fine step, a fine cell x whose neighbour x - c_i lies
 //    outside receives the coarse post-collision f*_i of parent(x - c_i);
-//  * before the next first fine step it receives f*_i of x - 2c_i: the fine
-//    post-collision value of the first fine step when x - 2c_i is inside,
-//    else the coarse value of parent(x - 2c_i);
+//  * before the next first fine step it receives f*_i of x - 2c_i, which
+//    for a box region lies outside too: the coarse value of parent(x - 2c_i);
 //  * a coarse cell W next to the fine region receives, per direction, the
 //    mean over its 8 children p of: fine f*_i(p - c_i) of the second fine
 //    step, or fine f*_i(p - 2c_i) of the first, or coarse f*_i(W - c_i).
@@ -498,7 +497,8 @@ int build_interface(Mesh& m, int l) {
   static const char* const kErr[] = {"", "refinement interface crosses a solid",
                                      "refinement box too close to the coarser level's edge",
                                      "interface slot without storage",
-                                     "refinement box too close to a solid or an edge"};
+                                     "refinement box too close to a solid or an edge",
+                                   "refinement region is not a box"};
   // one part per z plane, concatenated in z order: the tables come out in
   // the order of a sequential z, y, x sweep.  Saved slots are requested by
   // key (per-part request numbers) and numbered at the end, distinct keys in
@@ -520,10 +520,6 @@ int build_interface(Mesh& m, int l) {
   parallel_for(hi[2] - lo[2], [&](long long zi) {
     Part& P = fine[(size_t)zi];
     const int z = lo[2] + (int)zi;
-    auto save_index = [&](int x, int y, int zz, int i) -> int {
-      P.want.push_back(F.addr(x, y, zz, opposite(i)));
-      return (int)P.want.size() - 1;
-    };
     for (int y = lo[1]; y < hi[1]; ++y) {
       // cells of the box's outer shell only: all of x on the y/z faces, else the two x ends
       const bool face = y == lo[1] || y == hi[1] - 1 || z == lo[2] || z == hi[2] - 1;
@@ -544,28 +540,26 @@ int build_interface(Mesh& m, int l) {
           e.dst = F.addr(ax, ay, az, opposite(i));
           e.src[0] = coarse_post(px, py, pz, i, 0);
           e.src[1] = coarse_post(px, py, pz, i, 1);
+          // the value x pulls at the next first sub-step left x - 2 c_i
+          // two fine steps before: outside a box (x - c_i is outside, and
+          // so is every point further along -c_i), hence the coarse value
+          // of its parent
           InflowEntry f{};
           f.dst = F.addr(x, y, z, i);
+          f.sv = -1;
           int bx = x - 2 * cx(i), by = y - 2 * cy(i), bz = z - 2 * cz(i);
           if (in_box(lo, hi, bx, by, bz)) {
-            if (F.cell_type(bx, by, bz) != FLUID) {
-              P.err = 1;
-              return;
-            }
-            f.r = save_index(bx, by, bz, i);
-            f.csrc[0] = f.csrc[1] = -1;
-          } else {
-            int qx = floordiv(bx, 2), qy = floordiv(by, 2), qz = floordiv(bz, 2);
-            if (C.cell_type(qx, qy, qz) != FLUID) {
-              P.err = 2;
-              return;
-            }
-            f.r = -1;
-            f.csrc[0] = coarse_post(qx, qy, qz, i, 0);
-            f.csrc[1] = coarse_post(qx, qy, qz, i, 1);
+            P.err = 5;
+            return;
           }
-          if (e.dst < 0 || e.src[0] < 0 || e.src[1] < 0 || f.dst < 0 ||
-              (f.r < 0 && (f.csrc[0] < 0 || f.csrc[1] < 0))) {
+          int qx = floordiv(bx, 2), qy = floordiv(by, 2), qz = floordiv(bz, 2);
+          if (C.cell_type(qx, qy, qz) != FLUID) {
+            P.err = 2;
+            return;
+          }
+          f.csrc[0] = coarse_post(qx, qy, qz, i, 0);
+          f.csrc[1] = coarse_post(qx, qy, qz, i, 1);
+          if (e.dst < 0 || e.src[0] < 0 || e.src[1] < 0 || f.dst < 0 || f.csrc[0] < 0 || f.csrc[1] < 0) {
             P.err = 3;
             return;
           }
@@ -648,8 +642,6 @@ int build_interface(Mesh& m, int l) {
   parallel_for((long long)(fine.size() + coarse.size()), [&](long long k) {
     if (k < (long long)fine.size()) {
       Part& P = fine[k];
-      for (InflowEntry& f : P.infl)
-        if (f.r >= 0) f.r += (int)wo[k];
       std::copy(P.expl.begin(), P.expl.end(), C.expl.begin() + eo[k]);
       std::copy(P.infl.begin(), P.infl.end(), C.infl.begin() + eo[k]);
       std::copy(P.want.begin(), P.want.end(), want.begin() + wo[k]);
@@ -673,9 +665,17 @@ int build_interface(Mesh& m, int l) {
   auto resolve = [&](long long req) {
     return (long long)(std::lower_bound(keys.begin(), keys.end(), want[req]) - keys.begin());
   };
+  // a saved slot that an inflow entry overwrites (every slot (b, ibar) with
+  // b + c_i outside the box is an inflow destination) is saved by that
+  // entry's thread just before its write; the save entry itself is skipped
+  C.save_dev = C.save;
   parallel_for((long long)C.infl.size(), [&](long long n) {
     InflowEntry& f = C.infl[n];
-    if (f.r >= 0) f.r = (int)resolve(f.r);
+    auto it = std::lower_bound(keys.begin(), keys.end(), f.dst);
+    if (it != keys.end() && *it == f.dst) {
+      f.sv = (int)(it - keys.begin());
+      C.save_dev[(size_t)f.sv].src = -1;
+    }
   }, 4096);
   parallel_for((long long)C.coal.size(), [&](long long n) {
     CoalesceEntry& e = C.coal[n];
@@ -854,7 +854,7 @@ static void slot_checks(Mesh& m, std::vector<char>* walls_ok, bool* faces_ok) {
     key_set(v.coal, 2, [&](const CoalesceEntry& e, int j) { return slot_key(l, e.dst[j]); }, &iw[l]);
     key_set(v.expl, 2, [&](const ExplodeEntry& e, int j) { return slot_key(l, e.src[j]); }, &ir[l]);
     key_set(v.save, 1, [&](const SaveEntry& e, int) { return slot_key(fl, e.src); }, &ir[l]);
-    key_set(v.infl, 2, [&](const InflowEntry& e, int j) { return e.r < 0 ? slot_key(l, e.csrc[j]) : -1LL; },
+    key_set(v.infl, 2, [&](const InflowEntry& e, int j) { return slot_key(l, e.csrc[j]); },
             &ir[l]);
     key_set(v.coal, 8, [&](const CoalesceEntry& e, int j) {
       return j < e.nfine && e.fsrc[j] >= 0 ? slot_key(fl, e.fsrc[j]) : -1LL;
@@ -942,10 +942,8 @@ static void overlap_checks(Mesh& m) {
       for (const SaveEntry& e : v.save) iwr[l].mark(m, fl, e.src);
       for (const InflowEntry& e : v.infl) {
         iwr[l].mark(m, fl, e.dst);
-        if (e.r < 0) {
-          iwr[l].mark(m, l, e.csrc[0]);
-          iwr[l].mark(m, l, e.csrc[1]);
-        }
+        iwr[l].mark(m, l, e.csrc[0]);
+        iwr[l].mark(m, l, e.csrc[1]);
       }
       for (const CoalesceEntry& e : v.coal) {
         for (int j = 0; j < 2; ++j) iwr[l].mark(m, l, e.dst[j]);
@@ -1169,9 +1167,9 @@ void narrow_tables(Mesh* m) {
     }
     narrow_copy(v.expl, &v.expl_n,
                 [](const ExplodeEntry& e) { return ExplodeEntryN{(int)e.dst, {(int)e.src[0], (int)e.src[1]}}; });
-    narrow_copy(v.save, &v.save_n, [](const SaveEntry& e) { return SaveEntryN{(int)e.src}; });
+    narrow_copy(v.save_dev, &v.save_n, [](const SaveEntry& e) { return SaveEntryN{(int)e.src}; });
     narrow_copy(v.infl, &v.infl_n, [](const InflowEntry& e) {
-      return InflowEntryN{(int)e.dst, {(int)e.csrc[0], (int)e.csrc[1]}, e.r};
+      return InflowEntryN{(int)e.dst, {(int)e.csrc[0], (int)e.csrc[1]}, e.sv};
     });
     narrow_copy(v.coal, &v.coal_n, [](const CoalesceEntry& e) {
       CoalesceEntryN o;

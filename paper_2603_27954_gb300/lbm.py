@@ -99,6 +99,8 @@ def _load():
         "lbm_set_wide_offsets": ([vp, i], i),
         "lbm_set_overlap": ([vp, i], i),
         "lbm_get_overlap": ([vp, ip, ip], i),
+        "lbm_set_overlap_features": ([vp, i], i),
+        "lbm_get_overlap_features": ([vp, ip], i),
         "lbm_set_inflow_turbulence": ([vp, i, C.c_double], i),
         "lbm_friction": ([vp, dp, dp, i, dp], i),
         "lbm_set_friction_mean": ([vp, i], i),
@@ -393,6 +395,20 @@ def lbm_set_wide_offsets(h, on):
 
 def lbm_set_overlap(h, on):
     return _ck(_lib.lbm_set_overlap(h, int(bool(on))), "lbm_set_overlap")
+
+
+LBM_OVL_BRANCHES, LBM_OVL_LEVELS, LBM_OVL_TRANSFERS, LBM_OVL_DEFER, LBM_OVL_WALL_SPLIT = 1, 2, 4, 8, 16
+LBM_OVL_ALL = 31
+
+
+def lbm_set_overlap_features(h, mask):
+    return _ck(_lib.lbm_set_overlap_features(h, int(mask)), "lbm_set_overlap_features")
+
+
+def lbm_get_overlap_features(h):
+    m = C.c_int()
+    _ck(_lib.lbm_get_overlap_features(h, C.byref(m)), "lbm_get_overlap_features")
+    return m.value
 
 
 def lbm_get_overlap(h):

@@ -301,22 +301,31 @@ def test_fp32_pair_kernels_match_oracle(L, stream, case, odd, even):
 
 @pytest.mark.parametrize("case", ["tiny", "amr2_small", "amr3_small"])
 def test_parallel_branches_equal_serial_step(L, stream, case):
-    """Faces and walls as parallel branches of the step (where the host check
-    allows) give the serial step's populations and forces bit for bit, with
-    and without graphs."""
+    """Every reordering of the step (faces and walls as parallel branches,
+    levels and transfers beside the finer sub-steps, deferred coalesce, the
+    collide split around the walls join; each alone and all together) gives
+    the serial step's populations and forces bit for bit, with and without
+    graphs, in one call of five steps and in five calls of one."""
     levels = W.CASES[case]["levels"]
     runs = []
-    for overlap, graphs in ((False, True), (True, True), (True, False)):
+    masks = (L.LBM_OVL_BRANCHES, L.LBM_OVL_LEVELS, L.LBM_OVL_TRANSFERS, L.LBM_OVL_DEFER,
+             L.LBM_OVL_BRANCHES | L.LBM_OVL_WALL_SPLIT, L.LBM_OVL_ALL)
+    variants = [(False, True, L.LBM_OVL_ALL, 1)] + [(True, True, m, 1) for m in masks] + \
+        [(True, False, L.LBM_OVL_ALL, 1), (True, True, L.LBM_OVL_ALL, 5)]
+    for overlap, graphs, mask, calls in variants:
         dom = gpu_case(L, stream, case)
         dom.set_overlap(overlap)
+        dom.set_overlap_features(mask)
+        assert dom.get_overlap_features() == mask
         dom.use_graphs(graphs)
-        dom.step(5)
+        for _ in range(calls):
+            dom.step(5 // calls)
         runs.append(([dom.get_populations(lv) for lv in range(levels)], dom.drag()[1]))
         dom.close()
-    for got in runs[1:]:
+    for v, got in zip(variants[1:], runs[1:]):
         for a, b in zip(runs[0][0], got[0]):
-            np.testing.assert_array_equal(a, b)
-        np.testing.assert_array_equal(runs[0][1], got[1])
+            np.testing.assert_array_equal(a, b, err_msg=str(v))
+        np.testing.assert_array_equal(runs[0][1], got[1], err_msg=str(v))
 
 
 def test_quarter_scale_headline_case(L, stream):

@@ -134,3 +134,18 @@ def test_fp64_form_descriptor_rules():
                       precision=L.LBM_FP64)
     with pytest.raises(L.LbmError):
         L.lbm_create_domain(d)
+
+
+def test_overlap_features_mask():
+    """The reorderings switch on and off one by one (default: branches,
+    levels and transfers); unknown bits are refused."""
+    h = domain(L.LBM_FP32)
+    assert L.lbm_get_overlap_features(h) == L.LBM_OVL_BRANCHES | L.LBM_OVL_LEVELS | L.LBM_OVL_TRANSFERS
+    for m in (0, L.LBM_OVL_BRANCHES, L.LBM_OVL_DEFER | L.LBM_OVL_LEVELS, L.LBM_OVL_ALL):
+        L.lbm_set_overlap_features(h, m)
+        assert L.lbm_get_overlap_features(h) == m
+    for bad in (32, -1, 64 | 1):
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_set_overlap_features(h, bad)
+        assert e.value.code == L.LBM_EINVAL
+    L.lbm_destroy(h)
