@@ -124,10 +124,9 @@ def test_fp64_form_descriptor_rules():
         sizes[prec] = L.lbm_memory_breakdown(h)[0]
         if prec == L.LBM_FP64:
             L.lbm_set_schedule(h, 0, 2, 0)
-            with pytest.raises(L.LbmError):
-                L.lbm_set_schedule(h, 0, 3, 0)
-            with pytest.raises(L.LbmError):
-                L.lbm_set_schedule(h, 0, 0, 2)
+            for odd, even in ((3, 0), (0, 2), (6, 0)):
+                with pytest.raises(L.LbmError):
+                    L.lbm_set_schedule(h, 0, odd, even)
         L.lbm_destroy(h)
     assert sizes[L.LBM_FP64] == 2 * sizes[L.LBM_FP32]
     d = L.domain_desc(*c["n0"], levels=1, block=16, bc=c["bc"], u_in=0.05, re_h=100.0, i_u=0.08,
