@@ -289,12 +289,13 @@ int join_branch(lbm_domain* d, int k) {
   CK(cudaStreamWaitEvent(d->stream, d->ev_join[k], 0));
   return LBM_OK;
 }
-// the stream branch k's kernels go to (forked from the domain's stream)
-int fork_branch(lbm_domain* d, int k, cudaStream_t* s) {
+// the stream branch k's kernels go to (forked from `parent`, by default the
+// domain's stream)
+int fork_branch(lbm_domain* d, int k, cudaStream_t* s, cudaStream_t parent = nullptr) {
   int rc = side_streams(d);
   if (!rc) rc = join_branch(d, k);
   if (rc) return rc;
-  CK(cudaEventRecord(d->ev_fork[k], d->stream));
+  CK(cudaEventRecord(d->ev_fork[k], parent ? parent : d->stream));
   CK(cudaStreamWaitEvent(d->side[k], d->ev_fork[k], 0));
   *s = d->side[k];
   return LBM_OK;
@@ -366,10 +367,14 @@ int post_collide(lbm_domain* dm, int l, int parity, cudaStream_t s, bool branche
   void* f = dm->base + v.off_f;
   const int esize = v.esize;
   int rc;
+  // the faces may branch off the level's side stream too (the host check
+  // covers everything up to the end of the coarse step); the walls only off
+  // the domain's stream
+  const bool face_branch = branches && ovl(dm, LBM_OVL_BRANCHES) && m.ovl_faces;
   branches = branches && ovl(dm, LBM_OVL_BRANCHES) && s == dm->stream;
   if (l == 0 && !v.face[parity].empty()) {
     cudaStream_t fs = s;
-    if (branches && m.ovl_faces && (rc = fork_branch(dm, 0, &fs))) return rc;
+    if (face_branch && (rc = fork_branch(dm, 0, &fs, s))) return rc;
     Timed t(dm, KC_FACES, (long long)v.face[parity].size());
     double feq[27];
     for (int i = 0; i < 27; ++i)
