@@ -191,6 +191,16 @@ int lbm_step(lbm_domain* d, int n_coarse);
    A_x in finest cells^2).  Any pointer may be NULL.  Synchronises.
    lbm_reset_force also clears the interface ledger (lbm_interface_ledger). */
 int lbm_drag(lbm_domain* d, double force_last[3], double force_mean[3], double* c_d);
+/* The same without synchronising: enqueues on the domain's stream a copy of
+   the 8 force accumulators (force of the last finest step [3], their sum over
+   the finest steps [3], the number of those steps, and a status word that
+   is nonzero when a bounded device wait gave up) to host_acc, which the
+   caller owns (page-locked for the copy to overlap later work) and may read
+   once the stream has passed this point; lbm_drag_decode turns them into
+   lbm_drag's outputs (LBM_ETIMEOUT for a nonzero status). */
+int lbm_drag_enqueue(lbm_domain* d, double host_acc[8]);
+int lbm_drag_decode(const lbm_domain* d, const double acc[8], double force_last[3], double force_mean[3],
+                    double* c_d);
 int lbm_reset_force(lbm_domain* d);
 
 /* Populations f_i(x) of one level's real box (27 per cell, NaN for cells

@@ -1217,12 +1217,15 @@ int lbm_step(lbm_domain* d, int n) {
   return d->last_status;
 }
 
-int lbm_drag(lbm_domain* d, double last[3], double mean[3], double* c_d) {
-  if (!d) return fail(LBM_EINVAL, "null argument");
+int lbm_drag_enqueue(lbm_domain* d, double host_acc[8]) {
+  if (!d || !host_acc) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
-  double acc[8];
-  CK(cudaMemcpyAsync(acc, d->base + d->off_accum, sizeof acc, cudaMemcpyDeviceToHost, d->stream));
-  CK(cudaStreamSynchronize(d->stream));
+  CK(cudaMemcpyAsync(host_acc, d->base + d->off_accum, 8 * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+  return LBM_OK;
+}
+
+int lbm_drag_decode(const lbm_domain* d, const double acc[8], double last[3], double mean[3], double* c_d) {
+  if (!d || !acc) return fail(LBM_EINVAL, "null argument");
   if (acc[7] != 0.0) return fail(LBM_ETIMEOUT, "a bounded device wait gave up (collide staging)");
   if (last)
     for (int a = 0; a < 3; ++a) last[a] = acc[a];
@@ -1233,6 +1236,15 @@ int lbm_drag(lbm_domain* d, double last[3], double mean[3], double* c_d) {
     *c_d = (d->A_x > 0 && u != 0) ? acc[0] / (0.5 * u * u * d->A_x) : std::numeric_limits<double>::quiet_NaN();
   }
   return LBM_OK;
+}
+
+int lbm_drag(lbm_domain* d, double last[3], double mean[3], double* c_d) {
+  if (!d) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  double acc[8];
+  CK(cudaMemcpyAsync(acc, d->base + d->off_accum, sizeof acc, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return lbm_drag_decode(d, acc, last, mean, c_d);
 }
 
 int lbm_reset_force(lbm_domain* d) {

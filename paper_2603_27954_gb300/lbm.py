@@ -77,6 +77,8 @@ def _load():
         "lbm_init_field": ([vp, i, dp, dp, sz], i),
         "lbm_step": ([vp, i], i),
         "lbm_drag": ([vp, dp, dp, dp], i),
+        "lbm_drag_enqueue": ([vp, vp], i),
+        "lbm_drag_decode": ([vp, dp, dp, dp, dp], i),
         "lbm_reset_force": ([vp], i),
         "lbm_get_populations": ([vp, i, dp, sz], i),
         "lbm_get_velocity": ([vp, i, dp, dp, sz], i),
@@ -221,6 +223,20 @@ def lbm_step(h, n):
 def lbm_drag(h):
     last, mean, cd = np.zeros(3), np.zeros(3), C.c_double()
     _ck(_lib.lbm_drag(h, _dp(last), _dp(mean), C.byref(cd)), "lbm_drag")
+    return last, mean, cd.value
+
+
+def lbm_drag_enqueue(h, host_ptr):
+    """Enqueue the copy of the 8 force accumulators to host memory at
+    host_ptr (an address, page-locked for the copy to be asynchronous)."""
+    return _ck(_lib.lbm_drag_enqueue(h, C.c_void_p(host_ptr)), "lbm_drag_enqueue")
+
+
+def lbm_drag_decode(h, acc):
+    """lbm_drag's (force_last, force_mean, c_d) from 8 accumulators."""
+    a = np.ascontiguousarray(acc, dtype=np.float64)
+    last, mean, cd = np.zeros(3), np.zeros(3), C.c_double()
+    _ck(_lib.lbm_drag_decode(h, _dp(a), _dp(last), _dp(mean), C.byref(cd)), "lbm_drag_decode")
     return last, mean, cd.value
 
 

@@ -352,3 +352,21 @@ def test_quarter_scale_headline_case(L, stream):
         c["steps"], cd, cd_ref, abs(cd - cd_ref) / abs(cd_ref)))
     assert abs(cd - cd_ref) <= 5e-4 * abs(cd_ref)
     dom.close()
+
+
+def test_drag_enqueue_matches_drag(L, stream):
+    """The asynchronous force read (copy to page-locked memory on the
+    domain's stream, decoded on the host) gives lbm_drag's values."""
+    import torch
+    dom = gpu_case(L, stream, "amr2_small")
+    slot = torch.zeros(8, dtype=torch.float64, pin_memory=True)
+    for _ in range(3):
+        dom.step(2)
+        L.lbm_drag_enqueue(dom.h, slot.data_ptr())
+        stream.synchronize()
+        got = L.lbm_drag_decode(dom.h, slot.numpy())
+        want = dom.drag()
+        for a, b in zip(got[:2], want[:2]):
+            np.testing.assert_array_equal(a, b)
+        assert got[2] == want[2]
+    dom.close()
