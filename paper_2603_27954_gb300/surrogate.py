@@ -8,7 +8,7 @@ c_k = F_x,k / (rho U^2 L_k D_k / 2) (lbm_branch_coefficients, from the
 time-averaged per-branch momentum-exchange forces).  A network trained by the
 library's BF16/FP32 kernels predicts c_k, an ensemble of such networks is
 averaged on the device (lbm_mlp_ensemble_forward), and Eq. 5 turns the
-predictions into C_D-est (lbm_branch_drag_estimate).  The LBM stays the judge:
+predictions into C_D-est (lbm_branch_drag_estimate).  The LBM stays the reference:
 held-out (geometry, Re_H) points are simulated and their C_D compared with
 the estimate.
 

@@ -142,10 +142,10 @@ def learned_cases(family, count, seed):
     return out
 
 
-# the judge: 8 held-out (geometry, Re_H) points across the range, tree seeds
+# the evaluation: 8 held-out (geometry, Re_H) points across the range, tree seeds
 # outside the training draws' range, uniform inflow (with 8 % turbulent inflow
 # the C_D of one averaging window scatters by 7-13 % from window to window -
-# eddies as large as the tree - so such a point cannot judge an estimate at
+# eddies as large as the tree - so such a point cannot test an estimate at
 # the per-cent level; turbulent held-out trees are reported apart)
 LEARNED_JUDGES = [
     dict(family=1, tree_seed=(1 << 30) + 1, re_h=3.0e3, i_u=0.0, inflow_seed=11),

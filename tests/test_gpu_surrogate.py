@@ -215,7 +215,7 @@ def test_branch_coefficients_partition_the_drag(L, stream):
 
 
 # the reduced learned form below: a regression test of the pipeline, not its
-# target (the full data set and its judge are run by `bench.py --learned-form`)
+# target (the full data set and its held-out evaluation are run by `bench.py --learned-form`)
 REDUCED = {1: 64, 2: 96, 3: 16}
 
 
@@ -223,7 +223,7 @@ def test_learned_form_pipeline_beats_the_cylinder_law(L, stream):
     """The learned form end to end on a reduced data set (LBM samples of the
     three tree families across Re_H 2.5e3-1.2e5, named-input and
     chosen-input ensembles trained by the library's kernels, the 8 held-out
-    judge points): the learned estimate beats the cylinder law and the
+    evaluation points): the learned estimate beats the cylinder law and the
     chosen inputs beat the named ones."""
     from paper_2603_27954_gb300 import surrogate as SG
     rep, nets = SG.learned_form(stream=stream, counts=REDUCED, members=2, train_steps=4000, curve_points=3)
