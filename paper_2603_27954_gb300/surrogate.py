@@ -93,6 +93,14 @@ def simulate(cases, stream=None, group=8, protocol=None):
     return out
 
 
+def sample_weights(samples):
+    """Per branch, its share of Eq. 5's sum: L_k D_k over its tree's frontal
+    area, normalised over all branches (training by these weights fits c_k
+    where it moves C_D-est, rather than where branches are numerous)."""
+    w = np.concatenate([s.rows[:, 6] * s.rows[:, 7] / s.area for s in samples]).astype(np.float64)
+    return w / w.sum()
+
+
 def dataset(samples, features=FEATURES):
     """Stack the branch rows of several samples: inputs (float32, n x k) and
     the sectional drag coefficients (float32, n)."""
@@ -108,8 +116,11 @@ def standardisation(x, y):
     return x.mean(axis=0), sd, float(y.mean()), float(y.std()) or 1.0
 
 
-def train(x, y, width=128, hidden=3, steps=2000, batch=256, lr=3e-4, seed=0, stream=None):
-    """Fit one network to (x, y) with mini-batch Adam; returns the Mlp."""
+def train(x, y, width=128, hidden=3, steps=2000, batch=256, lr=3e-4, seed=0, stream=None, weights=None):
+    """Fit one network to (x, y) with mini-batch Adam; returns the Mlp.  With
+    `weights` every epoch draws its n samples with probability proportional
+    to them (with replacement): the squared error is then weighted by them in
+    expectation."""
     import torch
     n = len(y)
     rng = np.random.default_rng(seed)
@@ -127,7 +138,8 @@ def train(x, y, width=128, hidden=3, steps=2000, batch=256, lr=3e-4, seed=0, str
     per_epoch = max(1, n // b)
     done = 0
     while done < steps:
-        perm = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
+        order = rng.permutation(n) if weights is None else rng.choice(n, size=n, p=weights)
+        perm = torch.from_numpy(order.astype(np.int32)).cuda()
         for k in range(per_epoch):
             if done == steps:
                 break
@@ -166,42 +178,60 @@ def branch_table_at(case, re_h):
 
 
 def learned_form(stream=None, counts=None, members=4, train_steps=20000, group=8, seed=2026, curve_points=15,
-                 log=None):
+                 log=None, weighting="none", data=None):
     """The learned form end to end: LBM data from trees of the three families,
     named-input and chosen-input ensembles trained by the library's kernels,
     and their Eq. 5 estimates judged against the LBM at the held-out points;
     also C_D-est of one held-out tree from Re_H = 2.5e3 to 1e9.  Returns a
-    report (dict) and the trained ensembles."""
+    report (dict) and the trained ensembles.  weighting "area" trains with
+    each branch weighted by its share of Eq. 5 (sample_weights).  `data`: a
+    file the simulated samples are written to, or read from when it exists
+    (the same counts and seed)."""
+    import os
+    import pickle
     counts = counts or W.LEARNED_COUNTS
-    report = {"families": {}, "protocol": dict(W.LEARNED_PROTOCOL)}
+    report = {"families": {}, "protocol": dict(W.LEARNED_PROTOCOL), "weighting": weighting}
     t0 = time.time()
     train_samples = []
-    for fam, n in sorted(counts.items()):
-        if n <= 0:
-            continue
-        t = time.time()
-        s = simulate(W.learned_cases(fam, n, seed), stream=stream, group=group)
-        train_samples += s
-        report["families"][fam] = {"cases": n, "kept": len(s), "branches": int(sum(len(x.c) for x in s)),
-                                   "seconds": time.time() - t}
-        if log:
-            log("family %d: %d cases, %d kept, %.1f s" % (fam, n, len(s), time.time() - t))
+    judges = None
+    if data and os.path.exists(data):
+        with open(data, "rb") as fh:
+            saved = pickle.load(fh)
+        train_samples, judges, report["families"] = saved["train"], saved["judges"], saved["families"]
+        report["data_file"] = data
+    else:
+        for fam, n in sorted(counts.items()):
+            if n <= 0:
+                continue
+            t = time.time()
+            s = simulate(W.learned_cases(fam, n, seed), stream=stream, group=group)
+            train_samples += s
+            report["families"][fam] = {"cases": n, "kept": len(s), "branches": int(sum(len(x.c) for x in s)),
+                                       "seconds": time.time() - t}
+            if log:
+                log("family %d: %d cases, %d kept, %.1f s" % (fam, n, len(s), time.time() - t))
     # one case in ten stays out of training (cases alternate between uniform
     # and turbulent inflow, so positions 0 and 5 of every 20 take both kinds):
     # its estimate is reported by inflow kind, the turbulent ones against one
     # noisy averaging window
-    held = [s for k, s in enumerate(train_samples) if k % 20 in (0, 5)]
-    train_samples = [s for k, s in enumerate(train_samples) if k % 20 not in (0, 5)]
+    generated = train_samples
+    held = [s for k, s in enumerate(generated) if k % 20 in (0, 5)]
+    train_samples = [s for k, s in enumerate(generated) if k % 20 not in (0, 5)]
     report["samples"] = int(sum(len(x.c) for x in train_samples))
+    if judges is None:
+        judges = []
+        for c in W.LEARNED_JUDGES:  # the held-out points, one run each
+            judges += simulate([c], stream=stream, group=1)
+        if data:
+            with open(data, "wb") as fh:
+                pickle.dump({"train": generated, "judges": judges, "families": report["families"]}, fh)
     report["data_seconds"] = time.time() - t0
-    judges = []
-    for c in W.LEARNED_JUDGES:  # the held-out points, one run each
-        judges += simulate([c], stream=stream, group=1)
+    weights = sample_weights(train_samples) if weighting == "area" else None
     nets = {}
     for name, feats in (("chosen", FEATURES), ("named", FEATURES_NAMED)):
         t = time.time()
         x, y = dataset(train_samples, feats)
-        nets[name] = train_ensemble(x, y, members=members, steps=train_steps, stream=stream)
+        nets[name] = train_ensemble(x, y, members=members, steps=train_steps, stream=stream, weights=weights)
         report["train_seconds_" + name] = time.time() - t
     rows = []
     for j in judges:
@@ -248,11 +278,14 @@ if __name__ == "__main__":
     ap.add_argument("--members", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=20000)
     ap.add_argument("--out", default=None, help="also write the report to this file")
+    ap.add_argument("--weighting", default="none", choices=["none", "area"],
+                    help="area: train with each branch weighted by its share of Eq. 5")
+    ap.add_argument("--data", default=None, help="write the simulated samples here, or read them if it exists")
     args = ap.parse_args()
     import torch
     counts = {k: max(1, int(round(v * args.scale))) for k, v in W.LEARNED_COUNTS.items()}
     rep, ens = learned_form(stream=torch.cuda.Stream(), counts=counts, members=args.members,
-                            train_steps=args.train_steps)
+                            train_steps=args.train_steps, weighting=args.weighting, data=args.data)
     for members in ens.values():
         for m in members:
             m.close()
