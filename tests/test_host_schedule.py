@@ -148,3 +148,17 @@ def test_overlap_features_mask():
             L.lbm_set_overlap_features(h, bad)
         assert e.value.code == L.LBM_EINVAL
     L.lbm_destroy(h)
+
+
+def test_learned_form_branch_weights():
+    """Each branch's training weight is its share of Eq. 5's sum, L_k D_k /
+    A_x of its own tree, normalised over all branches."""
+    from paper_2603_27954_gb300 import surrogate as SG
+    rows = np.zeros((3, 12))
+    rows[:, 6] = [10.0, 5.0, 2.0]
+    rows[:, 7] = [3.0, 2.0, 1.0]
+    a = SG.Sample(rows, np.ones(3), 100.0, 1.0, {})
+    b = SG.Sample(rows[:2], np.ones(2), 50.0, 1.0, {})
+    w = SG.sample_weights([a, b])
+    raw = np.array([30 / 100, 10 / 100, 2 / 100, 30 / 50, 10 / 50])
+    np.testing.assert_allclose(w, raw / raw.sum(), rtol=1e-15)
