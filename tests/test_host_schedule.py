@@ -162,3 +162,25 @@ def test_learned_form_branch_weights():
     w = SG.sample_weights([a, b])
     raw = np.array([30 / 100, 10 / 100, 2 / 100, 30 / 50, 10 / 50])
     np.testing.assert_allclose(w, raw / raw.sum(), rtol=1e-15)
+
+
+def test_drag_decode_on_the_host():
+    """lbm_drag_decode turns the 8 force accumulators into lbm_drag's
+    outputs: the last force, the mean over the counted steps, C_D by Eq. 7
+    with the tree's frontal area; a nonzero status word is LBM_ETIMEOUT."""
+    from paper_2603_27954_gb300 import workloads as W
+    c = W.CASES["tiny"]
+    h = L.lbm_create_domain(L.domain_desc(*c["n0"], levels=1, block=16, bc=c["bc"], u_in=c["u_in"],
+                                          re_h=c["re_h"]))
+    L.lbm_set_geometry(h, L.tree_desc(**c["tree"]))
+    area = L.lbm_geometry_info(h)["A_x"]
+    acc = np.array([0.5, -0.1, 0.2, 3.0, 0.6, -0.9, 3.0, 0.0])
+    last, mean, cd = L.lbm_drag_decode(h, acc)
+    np.testing.assert_array_equal(last, acc[:3])
+    np.testing.assert_allclose(mean, acc[3:6] / 3.0, rtol=1e-15)
+    assert cd == pytest.approx(0.5 / (0.5 * c["u_in"] ** 2 * area), rel=1e-15)
+    acc[7] = 1.0
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_drag_decode(h, acc)
+    assert e.value.code == L.LBM_ETIMEOUT
+    L.lbm_destroy(h)
