@@ -123,9 +123,10 @@ struct lbm_domain {
   // state, v = 1 first runs the coalesce transfers the previous step left
   // pending (their parities in coal_in[p]); either leaves coal_out[p]
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  // two coarse steps (parity p, then 1 - p) in one graph, where no transfer
-  // is left pending between steps: half the graph launches and boundaries
-  cudaGraphExec_t graph2[2] = {nullptr, nullptr};
+  // runs of kRun[r] coarse steps (parity p first) in one graph, where no
+  // transfer is left pending between steps: fewer graph launches and
+  // boundaries between them
+  cudaGraphExec_t graphr[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   std::vector<int> coal_in[2], coal_out[2];
   // per level: parity of the level's last step whose coalesce transfer is
   // still to run (-1: none); lbm_step runs them before it returns
@@ -204,11 +205,12 @@ void free_graphs(lbm_domain* d) {
         cudaGraphExecDestroy(g);
         g = nullptr;
       }
-  for (auto& g : d->graph2)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  for (auto& gv : d->graphr)
+    for (auto& g : gv)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
 }
 
 cudaEvent_t take_event(lbm_domain* d) {
@@ -927,14 +929,18 @@ int capture_one(lbm_domain* d, int p, const std::vector<int>& pre, cudaGraphExec
   return LBM_OK;
 }
 
-// two coarse steps from a complete state, leaving none pending
-int capture_two(lbm_domain* d, int p, cudaGraphExec_t* out) {
+// coarse steps per run graph (even counts: a run ends at the parity it
+// started with)
+constexpr int kRun[2] = {8, 2};
+
+// `steps` coarse steps from a complete state, leaving none pending
+int capture_run(lbm_domain* d, int p, int steps, cudaGraphExec_t* out) {
   const std::vector<int> keep = d->pend_coal;
   d->pend_coal.assign(d->mesh.L, -1);
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
-  int rc = advance(d, 0, p);
-  if (!rc) rc = advance(d, 0, 1 - p);
+  int rc = LBM_OK;
+  for (int k = 0; k < steps && !rc; ++k) rc = advance(d, 0, (p + k) & 1);
   cudaError_t e = cudaStreamEndCapture(d->stream, &g);
   d->pend_coal = keep;
   if (rc) return fail(rc, cuda_error_string());
@@ -952,8 +958,9 @@ int capture_graphs(lbm_domain* d) {
   for (int p = 0; p < 2; ++p)
     if (!d->graph[0][p] && (rc = capture_one(d, p, none, &d->graph[0][p], &d->coal_out[p]))) return rc;
   if (d->coal_out[0] == none && d->coal_out[1] == none)
-    for (int p = 0; p < 2; ++p)
-      if (!d->graph2[p] && (rc = capture_two(d, p, &d->graph2[p]))) return rc;
+    for (int r = 0; r < 2; ++r)
+      for (int p = 0; p < 2; ++p)
+        if (!d->graphr[r][p] && (rc = capture_run(d, p, kRun[r], &d->graphr[r][p]))) return rc;
   // the chained form of parity p follows a step of parity 1 - p
   for (int p = 0; p < 2; ++p) {
     d->coal_in[p] = d->coal_out[1 - p];
@@ -1221,12 +1228,15 @@ int lbm_step(lbm_domain* d, int n) {
   if (rc) return rc;
   for (int k = 0; k < n; ++k) {
     const int p = d->parity0;
-    if (d->graph2[p] && !d->timing && k + 1 < n && d->watchdog <= 0 && !any_pending(d)) {
-      CK(cudaGraphLaunch(d->graph2[p], d->stream));
-      d->steps += 2;
-      ++k;  // two coarse steps: the parity is back to p
-      continue;
-    }
+    bool ran = false;
+    for (int r = 0; r < 2 && !ran; ++r)
+      if (d->graphr[r][p] && !d->timing && k + kRun[r] <= n && d->watchdog <= 0 && !any_pending(d)) {
+        CK(cudaGraphLaunch(d->graphr[r][p], d->stream));
+        d->steps += kRun[r];
+        k += kRun[r] - 1;  // an even run: the parity is back to p
+        ran = true;
+      }
+    if (ran) continue;
     if (d->graph[0][p] && !d->timing) {
       // a step that follows one in this call starts with the transfers that
       // one left pending (the chained graph), else from a complete state

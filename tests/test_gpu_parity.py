@@ -207,15 +207,20 @@ def test_uniform_flow_crosses_refinement_on_gpu(L, stream):
     dom.close()
 
 
-def test_graph_replay_equals_direct_launches(L, stream):
+@pytest.mark.parametrize("calls", [(3,), (19,), (1, 8, 2, 9)])
+def test_graph_replay_equals_direct_launches(L, stream, calls):
+    """Graph replay (single coarse steps, runs of two and of eight in one
+    graph, as the call lengths allow) equals direct launches bit for bit."""
     a = gpu_case(L, stream, "amr2_small")
     b = gpu_case(L, stream, "amr2_small")
     b.use_graphs(False)
-    a.step(3)
-    b.step(3)
+    for n in calls:
+        a.step(n)
+        b.step(n)
     for lv in (0, 1):
         np.testing.assert_array_equal(a.get_populations(lv), b.get_populations(lv))
     np.testing.assert_array_equal(a.drag()[0], b.drag()[0])
+    np.testing.assert_array_equal(a.drag()[1], b.drag()[1])
     a.close()
     b.close()
 
