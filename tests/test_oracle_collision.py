@@ -153,3 +153,50 @@ def test_body_force_adds_momentum():
     out = O.collide(f, O.rates(1.7), force=F)
     np.testing.assert_allclose(out @ C27 - f @ C27, F, atol=1e-16)
     assert out.sum() == pytest.approx(f.sum(), abs=1e-15)
+
+
+def test_each_cumulant_group_relaxes_by_its_own_rate():
+    """Geier et al. (2015), the relaxation the paper's cumulant LBM uses
+    (Sec. 2.2): with ten distinct rates and no Galilean correction, each
+    group of cumulants moves toward its equilibrium by (1 - omega) of its own
+    rate - omega1 the off-diagonal and deviatoric second order, omega2 the
+    trace (equilibrium 1 = 3 c_s^2), omega3 / omega4 the sums / differences
+    of the third-order pairs, omega5 k111, omega6 the two fourth-order
+    differences, omega7 their sum, omega8 k211 and its permutations, omega9
+    fifth order, omega10 sixth order.  Both sides are cumulants from the
+    brute-force rational expansion, so this pins the general-rate branches
+    of the oracle's relaxation independently of its own transform."""
+    f = _perturbed(11, 0.1)
+    w1, w2 = 1.37, 0.61
+    hi = (0.23, 1.71, 0.48, 1.29, 0.87, 1.53, 0.35, 1.91)  # omega3 .. omega10
+    out = O.collide(f, O.rates(w1, w2, hi, galilean=False))
+    kb = brute_force_cumulants([Fraction(x) for x in f])
+    ka = brute_force_cumulants([Fraction(x) for x in out])
+
+    def K(k, a, b, c):
+        return k[a + 3 * b + 9 * c]
+
+    def check(expr, omega, eq=0.0):
+        before, after = expr(kb), expr(ka)
+        assert after - eq == pytest.approx((1 - omega) * (before - eq), rel=1e-9, abs=1e-15)
+
+    for (a, b, c) in ((1, 1, 0), (1, 0, 1), (0, 1, 1)):
+        check(lambda k: K(k, a, b, c), w1)
+    check(lambda k: K(k, 2, 0, 0) - K(k, 0, 2, 0), w1)
+    check(lambda k: K(k, 2, 0, 0) - K(k, 0, 0, 2), w1)
+    check(lambda k: K(k, 2, 0, 0) + K(k, 0, 2, 0) + K(k, 0, 0, 2), w2, eq=1.0)
+    for (p, q) in (((1, 2, 0), (1, 0, 2)), ((2, 1, 0), (0, 1, 2)), ((2, 0, 1), (0, 2, 1))):
+        check(lambda k: K(k, *p) + K(k, *q), hi[0])
+        check(lambda k: K(k, *p) - K(k, *q), hi[1])
+    check(lambda k: K(k, 1, 1, 1), hi[2])
+    check(lambda k: K(k, 2, 2, 0) - 2 * K(k, 2, 0, 2) + K(k, 0, 2, 2), hi[3])
+    check(lambda k: K(k, 2, 2, 0) + K(k, 2, 0, 2) - 2 * K(k, 0, 2, 2), hi[3])
+    check(lambda k: K(k, 2, 2, 0) + K(k, 2, 0, 2) + K(k, 0, 2, 2), hi[4])
+    for idx in ((2, 1, 1), (1, 2, 1), (1, 1, 2)):
+        check(lambda k: K(k, *idx), hi[5])
+    for idx in ((2, 2, 1), (2, 1, 2), (1, 2, 2)):
+        check(lambda k: K(k, *idx), hi[6])
+    check(lambda k: K(k, 2, 2, 2), hi[7])
+    # mass and momentum (first-order cumulants are the velocity) unchanged
+    assert ka[0] == pytest.approx(kb[0], rel=1e-14)
+    np.testing.assert_allclose([ka[1], ka[3], ka[9]], [kb[1], kb[3], kb[9]], rtol=1e-12, atol=1e-16)
