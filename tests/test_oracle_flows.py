@@ -341,3 +341,45 @@ def test_slip_walls_equal_the_mirrored_periodic_domain(axis):
     # the field is not trivial: the walls' neighbourhood carries a normal flow
     _, ua = a.macro(0)
     assert np.abs(np.take(ua, [0], axis=ax_np)[..., axis]).max() > 1e-3
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_refinement_with_zero_rates_is_an_exact_coarse_shift(levels):
+    """With every relaxation rate zero the collision is the identity and the
+    lattice only streams.  A composite field that is constant over each coarse
+    cell (the finer levels hold their coarse parent's populations) is then
+    carried by exactly one coarse cell along c_i per coarse step on every
+    level: the finer levels stream 2^l times per coarse step (recursive
+    sub-cycling), the explode hands a coarse cell's populations to its
+    virtual children and the coalesce averages the 8 children that arrived
+    (volumetric transfer, Sec. 2.2's octree refinement).  A wrong child
+    index, parent index, averaging weight or sub-step count shows up as a
+    population from the wrong coarse cell."""
+    N = 8
+    boxes = [None, [4, 4, 4, 12, 12, 12], [12, 12, 12, 20, 20, 20]][:levels]
+    s = O.Sim(N, N, N, levels=levels, boxes=boxes, bc=("periodic",) * 3, nu0=1e30, omega2=0.0,
+              omega_hi=(0.0,) * 8, galilean=False, u_in=0.0)
+    rng = np.random.default_rng(21 + levels)
+    rho0 = 1.0 + 0.02 * rng.standard_normal((N, N, N))
+    u0 = 0.05 * rng.standard_normal((N, N, N, 3))
+
+    def parent_slice(l, arr):
+        lo, hi = s.box(l)
+        idx = [np.arange(lo[a], hi[a]) >> l for a in (2, 1, 0)]
+        return arr[np.ix_(*idx)]
+
+    for l in range(levels):
+        s.init_field(l, parent_slice(l, rho0), parent_slice(l, u0))
+    F0 = np.stack([O.equilibrium(r, v) for r, v in zip(rho0.ravel(), u0.reshape(-1, 3))]).reshape(N, N, N, 27)
+    done = 0
+    for k in (1, 2, 5):
+        s.step(k - done)
+        done = k
+        want = np.empty_like(F0)
+        for i in range(27):
+            cx_, cy_, cz_ = C27[i]
+            want[..., i] = np.roll(F0[..., i], (k * cz_, k * cy_, k * cx_), axis=(0, 1, 2))
+        for l in range(levels):
+            ok = s.cell_type(l) == 0
+            got = s.f(l)[ok]
+            np.testing.assert_allclose(got, parent_slice(l, want)[ok], rtol=0, atol=1e-14)
