@@ -383,3 +383,35 @@ def test_refinement_with_zero_rates_is_an_exact_coarse_shift(levels):
             ok = s.cell_type(l) == 0
             got = s.f(l)[ok]
             np.testing.assert_allclose(got, parent_slice(l, want)[ok], rtol=0, atol=1e-14)
+
+
+def test_links_without_a_second_fluid_node_bounce_back_simply():
+    """A fluid layer one cell thick between two plates: every cut link's
+    second node x_f - c_i is solid, so the interpolated bounce-back has no
+    second value and the link bounces back simply, f_ibar = f*_i(x_f),
+    whatever its wall fraction q.  Two plate placements with different q on
+    both walls give the same populations bit for bit, and mass is conserved
+    exactly (a q-dependent formula would break both)."""
+    runs = []
+    for qa, qb in ((0.3, 0.8), (0.45, 0.15)):
+        s = O.Sim(6, 4, 5, bc=("periodic",) * 3, nu0=0.04, u_in=0.0, force=(3e-5, 0.0, 1e-5))
+        # cells y = 1 (centre 1.5) are fluid; the plates' surfaces sit qa below and qb above it
+        s.set_prims(O.prims([(2, (-1, -1, -1, 7, 1.5 - qa, 6)), (2, (-1, 1.5 + qb, -1, 7, 5, 6))]))
+        t = s.cell_type(0)
+        assert (t[:, 1, :] == 0).all() and (t[:, [0, 2, 3], :] == 1).all()
+        cell, d, q = s.links(0)
+        cy = C27[d][:, 1]
+        # a link's direction points from the fluid cell into the wall
+        np.testing.assert_allclose(q[cy == -1], qa, rtol=1e-12)
+        np.testing.assert_allclose(q[cy == 1], qb, rtol=1e-12)
+        assert len(q) == 18 * 6 * 5
+        rng = np.random.default_rng(3)
+        rho = 1.0 + 0.01 * rng.standard_normal((5, 4, 6))
+        u = 0.02 * rng.standard_normal((5, 4, 6, 3))
+        s.init_field(0, rho, u)
+        m0, _ = s.mass()
+        s.step(25)
+        m1, _ = s.mass()
+        assert abs(m1 - m0) / m0 < 1e-14
+        runs.append(s.f(0)[:, 1, :])
+    np.testing.assert_array_equal(runs[0], runs[1])
