@@ -415,3 +415,32 @@ def test_links_without_a_second_fluid_node_bounce_back_simply():
         assert abs(m1 - m0) / m0 < 1e-14
         runs.append(s.f(0)[:, 1, :])
     np.testing.assert_array_equal(runs[0], runs[1])
+
+
+def _oracle_tree(t):
+    return O.make_tree(t["n"], t["children"], t["s0"], t["w0"], t["r"], t["dfac"], alpha_deg=t["alpha_deg"],
+                       azimuth_mode=t["azimuth_mode"], seed=t["seed"])
+
+
+def test_sampled_one_cell_recursion_reproduces_the_oracle_step():
+    """The sampled check used on runs too large for the oracle (each level-l
+    interior cell advanced by 2^l one-cell collide-stream updates per coarse
+    step) reproduces the oracle's own two-level step on the quarter-scale
+    tree case from a non-uniform state, to round-off: the recursion, its
+    direction convention and its interior criterion are those of the
+    stepping itself."""
+    from sampled_cells import check_level
+    from paper_2603_27954_gb300 import workloads as W
+    c = W.CASES["amr2_quarter"]
+    sim, info = O.tree_case(*c["n0"], _oracle_tree(c["tree"]), c["tree"]["trunk_cells"], c["re_h"],
+                            u_in=c["u_in"], levels=c["levels"], block=c["block"], bc=c["bc"])
+    for l in range(2):
+        lo, hi = sim.box(l)
+        rho, u = W.tgv_fields(lo, hi, 2 ** l, 16, 0.02, (c["u_in"], 0.0, 0.01))
+        sim.init_field(l, rho, u)
+    sim.step(2)
+    S0 = [sim.f(l) for l in range(2)]
+    sim.step(1)
+    for l in range(2):
+        n, err, moved = check_level(S0[l], sim.f(l), sim.cell_type(l), l, info["nu0"] * 2 ** l, 40, l, 1e-13)
+        assert n == 40 and moved > 1e-4
