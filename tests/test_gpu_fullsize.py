@@ -2,12 +2,13 @@
 
 Two levels, coarse 256 x 128 x 128 in 16^3 blocks, the n = 4 x 3-children
 tree with a trunk of 64 finest cells, Re_H = 2.5e3 (1.27e7 cell updates per
-coarse step), FP32, in the launch configuration the benchmark times: the
-schedule the library's autotuner picks and graph replay.  From a non-uniform
-state, one coarse step of the GPU is compared on sampled interior cells of
-both levels with the FP64 oracle's one-cell collision applied 2^l times
-(`sampled_cells`), within the element-wise tolerance of the smaller parity
-cases (2e-6 absolute on the populations).
+coarse step), in FP32 and in the FP16 deviation form, in the launch
+configuration the benchmark times: the schedule the library's autotuner
+picks and graph replay.  From a non-uniform state, one coarse step of the
+GPU is compared on sampled interior cells of both levels with the FP64
+oracle's one-cell collision applied 2^l times (`sampled_cells`), within the
+element-wise tolerances of the smaller parity cases (2e-6 absolute on the
+populations in FP32, 2e-4 in binary16 storage).
 """
 import numpy as np
 import pytest
@@ -27,12 +28,14 @@ def L():
     return lbm
 
 
-def test_benchmark_workload_sampled_cells_match_the_oracle(L):
+@pytest.mark.parametrize("precision,atol", [("fp32", 2e-6), ("fp16", 2e-4)])
+def test_benchmark_workload_sampled_cells_match_the_oracle(L, precision, atol):
     import torch
     stream = torch.cuda.Stream()
     c = W.CASES["amr2"]
+    prec = L.LBM_FP16_DEV if precision == "fp16" else L.LBM_FP32
     desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
-                         re_h=c["re_h"])
+                         re_h=c["re_h"], precision=prec)
     dom = L.Domain(desc, tree=L.tree_desc(**c["tree"]), stream=stream)
     schedule, _ = dom.autotune(8)
     for lv in range(2):
@@ -47,9 +50,9 @@ def test_benchmark_workload_sampled_cells_match_the_oracle(L):
     for lv in range(2):
         after = dom.get_populations(lv)
         n, err, moved = check_level(before[lv], after, dom.get_cell_types(lv), lv, nu_finest / 2 ** (1 - lv),
-                                    150, 10 + lv, 2e-6)
-        print("level %d: %d sampled cells, max |f - f_oracle| = %.3g (populations moved up to %.3g); schedule %s"
-              % (lv, n, err, moved, schedule.as_dict()))
+                                    150, 10 + lv, atol)
+        print("%s level %d: %d sampled cells, max |f - f_oracle| = %.3g (populations moved up to %.3g); schedule %s"
+              % (precision, lv, n, err, moved, schedule.as_dict()))
         assert n == 150 and moved > 1e-5  # the state changes by far more than the error
     assert np.isfinite(dom.drag()[2])
     dom.close()
