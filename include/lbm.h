@@ -207,6 +207,16 @@ int lbm_reset_force(lbm_domain* d);
    that are not fluid), at the current coarse-step boundary.  Synchronises. */
 int lbm_get_populations(lbm_domain* d, int level, double* f, size_t n_cells);
 
+/* lbm_get_populations for the window [lo, hi) of a level's real box (cell
+   coordinates counted from the box's first cell, x fastest in f), reading
+   only the stored elements that window's fluid cells hold, so a small window
+   of a level too large to copy whole costs little; f holds 27 values per
+   cell (NaN for cells that are not fluid).  n_cells must equal the window's
+   cell count; an empty window or one reaching outside the box gives
+   LBM_EINVAL.  Synchronises. */
+int lbm_get_populations_window(lbm_domain* d, int level, const int lo[3], const int hi[3], double* f,
+                               size_t n_cells);
+
 /* Density and velocity per cell of one level's real box (NaN: not fluid). */
 int lbm_get_velocity(lbm_domain* d, int level, double* rho, double* u, size_t n_cells);
 

@@ -2,6 +2,7 @@
 // the recursively sub-cycled step driver, drag and diagnostics.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1317,6 +1318,61 @@ int lbm_get_populations(lbm_domain* d, int level, double* f, size_t n) {
           f[27 * k + i] = fl ? rest_weight(i) + d->ref[i] + stored_dev(v, host, incoming_slot(v, par, x, y, z, i))
                              : std::numeric_limits<double>::quiet_NaN();
       }
+  return LBM_OK;
+}
+
+int lbm_get_populations_window(lbm_domain* d, int level, const int lo[3], const int hi[3], double* f,
+                               size_t n) {
+  if (!d || !f || !lo || !hi) return fail(LBM_EINVAL, "null argument");
+  if (!d->base) return fail(LBM_ESTATE, "bind memory first");
+  if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
+  const Level& v = d->mesh.lv[level];
+  long long cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (lo[a] < 0 || lo[a] >= hi[a] || hi[a] > v.rhi[a] - v.rlo[a])
+      return fail(LBM_EINVAL, "window empty or outside the level's box");
+    cells *= hi[a] - lo[a];
+  }
+  if ((long long)n != cells) return fail(LBM_EINVAL, "cell count does not match the window");
+  const int par = level_parity(d, level);
+  // the stored element each (cell, direction) reads, -1 for cells that are not fluid
+  std::vector<long long> slot((size_t)cells * kQ, -1), uniq;
+  uniq.reserve(slot.size());
+  size_t k = 0;
+  for (int z = lo[2]; z < hi[2]; ++z)
+    for (int y = lo[1]; y < hi[1]; ++y)
+      for (int x = lo[0]; x < hi[0]; ++x, ++k) {
+        const int gx = v.rlo[0] + x, gy = v.rlo[1] + y, gz = v.rlo[2] + z;
+        if (v.cell_type(gx, gy, gz) != FLUID) continue;
+        for (int i = 0; i < kQ; ++i) {
+          const long long e = incoming_slot(v, par, gx, gy, gz, i);
+          if (e < 0 || e >= (long long)v.f_elems()) return fail(LBM_ESTATE, "fluid cell without storage");
+          slot[kQ * k + i] = e;
+          uniq.push_back(e);
+        }
+      }
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+  // one copy per run of consecutive elements
+  std::vector<uint8_t> host(uniq.size() * (size_t)v.esize);
+  for (size_t a = 0; a < uniq.size();) {
+    size_t b = a + 1;
+    while (b < uniq.size() && uniq[b] == uniq[b - 1] + 1) ++b;
+    CK(cudaMemcpyAsync(host.data() + a * v.esize, d->base + v.off_f + (size_t)uniq[a] * v.esize,
+                       (b - a) * (size_t)v.esize, cudaMemcpyDeviceToHost, d->stream));
+    a = b;
+  }
+  CK(cudaStreamSynchronize(d->stream));
+  for (size_t c = 0; c < (size_t)cells; ++c)
+    for (int i = 0; i < kQ; ++i) {
+      const long long e = slot[kQ * c + i];
+      if (e < 0) {
+        f[kQ * c + i] = std::numeric_limits<double>::quiet_NaN();
+        continue;
+      }
+      const long long pos = std::lower_bound(uniq.begin(), uniq.end(), e) - uniq.begin();
+      f[kQ * c + i] = rest_weight(i) + d->ref[i] + stored_dev(v, host, pos);
+    }
   return LBM_OK;
 }
 

@@ -81,6 +81,7 @@ def _load():
         "lbm_drag_decode": ([vp, dp, dp, dp, dp], i),
         "lbm_reset_force": ([vp], i),
         "lbm_get_populations": ([vp, i, dp, sz], i),
+        "lbm_get_populations_window": ([vp, i, ip, ip, dp, sz], i),
         "lbm_get_velocity": ([vp, i, dp, dp, sz], i),
         "lbm_mass": ([vp, dp, dp], i),
         "lbm_mass_noalloc": ([vp, dp, dp], i),
@@ -260,6 +261,17 @@ def lbm_get_populations(h, level):
     nx, ny, nz = _box_shape(h, level)
     out = np.zeros(nx * ny * nz * 27)
     _ck(_lib.lbm_get_populations(h, level, _dp(out), nx * ny * nz), "lbm_get_populations")
+    return out.reshape(nz, ny, nx, 27)
+
+
+def lbm_get_populations_window(h, level, lo, hi):
+    """Populations of the cells [lo, hi) (x, y, z; counted from the level's
+    box) as an array (z, y, x, 27)."""
+    lo_c, hi_c = (C.c_int * 3)(*[int(v) for v in lo]), (C.c_int * 3)(*[int(v) for v in hi])
+    nx, ny, nz = (int(hi[a]) - int(lo[a]) for a in range(3))
+    out = np.zeros(max(nx * ny * nz, 0) * 27)
+    _ck(_lib.lbm_get_populations_window(h, level, lo_c, hi_c, _dp(out), max(nx * ny * nz, 0)),
+        "lbm_get_populations_window")
     return out.reshape(nz, ny, nx, 27)
 
 

@@ -33,25 +33,42 @@ def pick(mask, n, seed):
 
 class Recursion:
     """f(cell) after `updates` collide-stream updates of the state S
-    (z, y, x, 27), memoised per (cell, updates)."""
+    (z, y, x, 27), each cell's collision computed once (memoised)."""
 
     def __init__(self, S, nu):
-        self.S, self.r, self.memo = S, O.rates(1.0 / (3.0 * nu + 0.5)), {}
+        self.S, self.r, self.memo, self.post_memo = S, O.rates(1.0 / (3.0 * nu + 0.5)), {}, {}
+
+    def post(self, cell, updates):
+        """The collision of cell's populations after `updates` updates."""
+        key = (cell, updates)
+        if key not in self.post_memo:
+            self.post_memo[key] = O.collide(self.after(cell, updates), self.r)
+        return self.post_memo[key]
 
     def after(self, cell, updates):
-        key = (tuple(int(v) for v in cell), updates)
+        cell = tuple(int(v) for v in cell)
+        key = (cell, updates)
         if key in self.memo:
             return self.memo[key]
         if updates == 0:
-            out = self.S[key[0]]
+            out = self.S[cell]
         else:
             out = np.empty(27)
             for i in range(27):
                 cx, cy, cz = C27[i]
-                src = (key[0][0] - cz, key[0][1] - cy, key[0][2] - cx)
-                out[i] = O.collide(self.after(src, updates - 1), self.r)[i]
+                out[i] = self.post((cell[0] - cz, cell[1] - cy, cell[2] - cx), updates - 1)[i]
         self.memo[key] = out
         return out
+
+
+def window_all_fluid(types, cell, radius):
+    """True when the (2 radius + 1)^3 window around cell (z, y, x) lies in the
+    level's box and holds only fluid cells."""
+    lo = [int(c) - radius for c in cell]
+    if min(lo) < 0 or any(int(c) + radius >= types.shape[a] for a, c in enumerate(cell)):
+        return False
+    return bool((types[lo[0]:lo[0] + 2 * radius + 1, lo[1]:lo[1] + 2 * radius + 1,
+                       lo[2]:lo[2] + 2 * radius + 1] == 0).all())
 
 
 def check_level(S0, S1, types, level, nu_level, n, seed, atol):
