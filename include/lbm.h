@@ -8,7 +8,9 @@
  *
  * Conventions common to every call
  *  - Every call returns an lbm_status (0 on success, a negative code on
- *    failure); no call aborts or throws across this boundary.
+ *    failure); no call aborts or throws across this boundary: a host
+ *    allocation that fails inside the library returns LBM_ENOMEM, any other
+ *    internal C++ exception LBM_ESTATE, each with its message.
  *  - Lattice units throughout: lengths in cells of the level named, the
  *    inflow speed in cells per time step, density 1 at rest.  "Finest
  *    cells" are cells of the finest refinement level.

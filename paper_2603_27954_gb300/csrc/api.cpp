@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -25,6 +27,21 @@ int fail(int code, const std::string& msg) {
 int cuda_fail(cudaError_t e, const char* what) {
   g_error = std::string(what) + ": " + cudaGetErrorString(e);
   return LBM_ECUDA;
+}
+// No C++ exception leaves the C-ABI: the one in flight (called from a catch
+// handler) becomes a status and a message.
+int exception_status() {
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    return fail(LBM_ENOMEM, "host memory allocation failed");
+  } catch (const std::length_error&) {
+    return fail(LBM_ENOMEM, "host allocation too large");
+  } catch (const std::exception& e) {
+    return fail(LBM_ESTATE, std::string("internal error: ") + e.what());
+  } catch (...) {
+    return fail(LBM_ESTATE, "internal error");
+  }
 }
 #define CK(call)                                   \
   do {                                             \
@@ -1071,7 +1088,7 @@ const char* lbm_status_string(int s) {
   }
 }
 
-int lbm_create_domain(const lbm_domain_desc* desc, void* cuda_stream, lbm_domain** out) {
+int lbm_create_domain(const lbm_domain_desc* desc, void* cuda_stream, lbm_domain** out) try {
   if (!desc || !out) return fail(LBM_EINVAL, "null argument");
   *out = nullptr;
   const lbm_domain_desc& s = *desc;
@@ -1100,9 +1117,11 @@ int lbm_create_domain(const lbm_domain_desc* desc, void* cuda_stream, lbm_domain
   }
   *out = d;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_geometry_prims(lbm_domain* d, const int* kind, const double* params, int n) {
+int lbm_set_geometry_prims(lbm_domain* d, const int* kind, const double* params, int n) try {
   if (!d || n < 0 || (n > 0 && (!kind || !params))) return fail(LBM_EINVAL, "bad primitives");
   if (d->base) return fail(LBM_ESTATE, "geometry is fixed once memory is bound");
   d->prims.clear();
@@ -1114,9 +1133,11 @@ int lbm_set_geometry_prims(lbm_domain* d, const int* kind, const double* params,
   }
   if (!d->have_tree) d->H = 0;
   return build(d);
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_geometry_segments(lbm_domain* d, const double* seg, int n) {
+int lbm_set_geometry_segments(lbm_domain* d, const double* seg, int n) try {
   if (!d || n < 0 || (n > 0 && !seg)) return fail(LBM_EINVAL, "bad segments");
   if (d->base) return fail(LBM_ESTATE, "geometry is fixed once memory is bound");
   d->tree.seg.assign(seg, seg + 8 * (size_t)n);
@@ -1131,9 +1152,11 @@ int lbm_set_geometry_segments(lbm_domain* d, const double* seg, int n) {
   d->H = n ? tree_height(d->tree) : 0.0;
   d->A_x = n ? frontal_area(d->tree, 0.125) : 0.0;
   return build(d);
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_geometry(lbm_domain* d, const lbm_tree_desc* t) {
+int lbm_set_geometry(lbm_domain* d, const lbm_tree_desc* t) try {
   if (!d || !t) return fail(LBM_EINVAL, "null argument");
   if (!(t->trunk_cells > 0)) return fail(LBM_EINVAL, "trunk_cells must be positive");
   Tree tr;
@@ -1150,16 +1173,20 @@ int lbm_set_geometry(lbm_domain* d, const lbm_tree_desc* t) {
     tree_affine(&tr, 1.0, sh);
   }
   return lbm_set_geometry_segments(d, tr.seg.data(), tr.count());
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_memory_requirements(const lbm_domain* d, size_t* bytes) {
+int lbm_memory_requirements(const lbm_domain* d, size_t* bytes) try {
   if (!d || !bytes) return fail(LBM_EINVAL, "null argument");
   if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
   *bytes = d->need;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_memory_breakdown(const lbm_domain* d, size_t* populations, size_t* uploaded) {
+int lbm_memory_breakdown(const lbm_domain* d, size_t* populations, size_t* uploaded) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
   if (populations) {
@@ -1169,9 +1196,11 @@ int lbm_memory_breakdown(const lbm_domain* d, size_t* populations, size_t* uploa
   }
   if (uploaded) *uploaded = upload_bytes(d);
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_bind_memory(lbm_domain* d, void* ptr, size_t bytes) {
+int lbm_bind_memory(lbm_domain* d, void* ptr, size_t bytes) try {
   if (!d || !ptr) return fail(LBM_EINVAL, "null argument");
   if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
   if (bytes < d->need) return fail(LBM_ENOMEM, "bound buffer smaller than lbm_memory_requirements");
@@ -1187,18 +1216,22 @@ int lbm_bind_memory(lbm_domain* d, void* ptr, size_t bytes) {
   if ((rc = fill_uniform(d, 1.0, u))) return rc;
   d->steps = 0;
   return set_tick(d);
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_init_uniform(lbm_domain* d, double rho, const double u[3]) {
+int lbm_init_uniform(lbm_domain* d, double rho, const double u[3]) try {
   if (!d || !u) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   int rc = fill_uniform(d, rho, u);
   if (rc) return rc;
   d->steps = 0;
   return set_tick(d);
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_init_field(lbm_domain* d, int level, const double* rho, const double* u, size_t n) {
+int lbm_init_field(lbm_domain* d, int level, const double* rho, const double* u, size_t n) try {
   if (!d || !rho || !u) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
@@ -1220,9 +1253,11 @@ int lbm_init_field(lbm_domain* d, int level, const double* rho, const double* u,
   CK(cudaMemcpyAsync(d->base + v.off_f, host.data(), host.size(), cudaMemcpyHostToDevice, d->stream));
   CK(cudaStreamSynchronize(d->stream));
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_step(lbm_domain* d, int n) {
+int lbm_step(lbm_domain* d, int n) try {
   if (!d || n < 0) return fail(LBM_EINVAL, "bad argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   int rc = capture_graphs(d);
@@ -1261,16 +1296,20 @@ int lbm_step(lbm_domain* d, int n) {
   }
   if ((rc = flush_coalesce(d))) return fail(rc, cuda_error_string());
   return d->last_status;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_drag_enqueue(lbm_domain* d, double host_acc[8]) {
+int lbm_drag_enqueue(lbm_domain* d, double host_acc[8]) try {
   if (!d || !host_acc) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   CK(cudaMemcpyAsync(host_acc, d->base + d->off_accum, 8 * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_drag_decode(const lbm_domain* d, const double acc[8], double last[3], double mean[3], double* c_d) {
+int lbm_drag_decode(const lbm_domain* d, const double acc[8], double last[3], double mean[3], double* c_d) try {
   if (!d || !acc) return fail(LBM_EINVAL, "null argument");
   if (acc[7] != 0.0) return fail(LBM_ETIMEOUT, "a bounded device wait gave up (collide staging)");
   if (last)
@@ -1282,24 +1321,30 @@ int lbm_drag_decode(const lbm_domain* d, const double acc[8], double last[3], do
     *c_d = (d->A_x > 0 && u != 0) ? acc[0] / (0.5 * u * u * d->A_x) : std::numeric_limits<double>::quiet_NaN();
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_drag(lbm_domain* d, double last[3], double mean[3], double* c_d) {
+int lbm_drag(lbm_domain* d, double last[3], double mean[3], double* c_d) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   double acc[8];
   CK(cudaMemcpyAsync(acc, d->base + d->off_accum, sizeof acc, cudaMemcpyDeviceToHost, d->stream));
   CK(cudaStreamSynchronize(d->stream));
   return lbm_drag_decode(d, acc, last, mean, c_d);
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_reset_force(lbm_domain* d) {
+int lbm_reset_force(lbm_domain* d) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   return reset_force(d);
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_get_populations(lbm_domain* d, int level, double* f, size_t n) {
+int lbm_get_populations(lbm_domain* d, int level, double* f, size_t n) try {
   if (!d || !f) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
@@ -1319,10 +1364,12 @@ int lbm_get_populations(lbm_domain* d, int level, double* f, size_t n) {
                              : std::numeric_limits<double>::quiet_NaN();
       }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
 int lbm_get_populations_window(lbm_domain* d, int level, const int lo[3], const int hi[3], double* f,
-                               size_t n) {
+                               size_t n) try {
   if (!d || !f || !lo || !hi) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
@@ -1374,9 +1421,11 @@ int lbm_get_populations_window(lbm_domain* d, int level, const int lo[3], const 
       f[kQ * c + i] = rest_weight(i) + d->ref[i] + stored_dev(v, host, pos);
     }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_get_velocity(lbm_domain* d, int level, double* rho, double* u, size_t n) {
+int lbm_get_velocity(lbm_domain* d, int level, double* rho, double* u, size_t n) try {
   if (!d || !rho || !u) return fail(LBM_EINVAL, "null argument");
   if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
   std::vector<double> f(n * 27);
@@ -1395,15 +1444,19 @@ int lbm_get_velocity(lbm_domain* d, int level, double* rho, double* u, size_t n)
     for (int a = 0; a < 3; ++a) u[3 * k + a] = j[a] / r;
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_mass(lbm_domain* d, double* mass, double mom[3]) {
+int lbm_mass(lbm_domain* d, double* mass, double mom[3]) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   return mass_device(d, mass, mom, nullptr);
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]) {
+int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   for (const Level& v : d->mesh.lv)
@@ -1433,16 +1486,20 @@ int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]) {
   if (mom)
     for (int a = 0; a < 3; ++a) mom[a] = p[a];
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_level_mass(lbm_domain* d, int level, double* mass, double mom[3]) {
+int lbm_level_mass(lbm_domain* d, int level, double* mass, double mom[3]) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level");
   return mass_device(d, mass, mom, nullptr, level);
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_interface_ledger(lbm_domain* d, int on) {
+int lbm_set_interface_ledger(lbm_domain* d, int on) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (d->ledger != (on != 0)) {
     free_graphs(d);
@@ -1452,9 +1509,11 @@ int lbm_set_interface_ledger(lbm_domain* d, int on) {
         CK(cudaMemsetAsync(d->base + d->mesh.lv[l].off_ledger, 0, sizeof(LedgerDev), d->stream));
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_interface_ledger(lbm_domain* d, int level, double last[12], double total[12], long long* steps) {
+int lbm_interface_ledger(lbm_domain* d, int level, double last[12], double total[12], long long* steps) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   if (!valid_level(d, level) || level + 1 >= d->mesh.L) return fail(LBM_EINVAL, "no interface below this level");
@@ -1467,10 +1526,12 @@ int lbm_interface_ledger(lbm_domain* d, int level, double last[12], double total
   }
   if (steps) *steps = (long long)h.steps;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
 int lbm_level_info(const lbm_domain* d, int level, int lo[3], int hi[3], long long* n_fluid, long long* n_links,
-                   long long* n_active_blocks) {
+                   long long* n_active_blocks) try {
   if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level or geometry not set");
   const Level& v = d->mesh.lv[level];
   for (int a = 0; a < 3; ++a) {
@@ -1481,18 +1542,22 @@ int lbm_level_info(const lbm_domain* d, int level, int lo[3], int hi[3], long lo
   if (n_links) *n_links = (long long)v.links.size();
   if (n_active_blocks) *n_active_blocks = v.n_active;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_geometry_info(const lbm_domain* d, double* height, double* area, int* nseg, double* nu_f) {
+int lbm_geometry_info(const lbm_domain* d, double* height, double* area, int* nseg, double* nu_f) try {
   if (!d || !d->built) return fail(LBM_ESTATE, "geometry not set");
   if (height) *height = d->H;
   if (area) *area = d->A_x;
   if (nseg) *nseg = d->have_tree ? d->tree.count() : 0;
   if (nu_f) *nu_f = d->nu_f;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_get_cell_types(const lbm_domain* d, int level, unsigned char* out, size_t n) {
+int lbm_get_cell_types(const lbm_domain* d, int level, unsigned char* out, size_t n) try {
   if (!out || !valid_level(d, level)) return fail(LBM_EINVAL, "bad argument");
   const Level& v = d->mesh.lv[level];
   if ((long long)n != box_cells(v)) return fail(LBM_EINVAL, "cell count does not match the level's box");
@@ -1501,10 +1566,12 @@ int lbm_get_cell_types(const lbm_domain* d, int level, unsigned char* out, size_
     for (int y = v.rlo[1]; y < v.rhi[1]; ++y)
       for (int x = v.rlo[0]; x < v.rhi[0]; ++x, ++k) out[k] = (unsigned char)v.cell_type(x, y, z);
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
 int lbm_get_links(const lbm_domain* d, int level, long long* cell, int* dir, double* q, size_t n,
-                  long long* count) {
+                  long long* count) try {
   if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level or geometry not set");
   const Level& v = d->mesh.lv[level];
   if (count) *count = (long long)v.links.size();
@@ -1517,25 +1584,31 @@ int lbm_get_links(const lbm_domain* d, int level, long long* cell, int* dir, dou
     q[k] = L.q;
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_get_segments(const lbm_domain* d, double* seg, int n, int* count) {
+int lbm_get_segments(const lbm_domain* d, double* seg, int n, int* count) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   int c = d->have_tree ? d->tree.count() : 0;
   if (count) *count = c;
   if (seg)
     for (int k = 0; k < c && k < n; ++k) std::memcpy(seg + 8 * k, &d->tree.seg[8 * k], 8 * sizeof(double));
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_branch_forces(lbm_domain* d, int on) {
+int lbm_set_branch_forces(lbm_domain* d, int on) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (d->branch_forces != (on != 0)) free_graphs(d);
   d->branch_forces = on != 0;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_get_branch_forces(lbm_domain* d, double* mean, int n, long long* steps) {
+int lbm_get_branch_forces(lbm_domain* d, double* mean, int n, long long* steps) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   if (n < d->n_seg) return fail(LBM_EINVAL, "capacity below the number of branches");
@@ -1550,9 +1623,11 @@ int lbm_get_branch_forces(lbm_domain* d, double* mean, int n, long long* steps) 
     for (int a = 0; a < 3; ++a) mean[3 * k + a] = acc[4 * k + 3] > 0 ? acc[4 * k + a] / acc[4 * k + 3] : 0.0;
   if (steps) *steps = cnt;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_branch_table(const lbm_domain* d, double* rows, int n, int* count) {
+int lbm_branch_table(const lbm_domain* d, double* rows, int n, int* count) try {
   if (!d || !d->built) return fail(LBM_ESTATE, "geometry not set");
   if (!d->have_tree) return fail(LBM_ESTATE, "no tree: set the geometry from a tree or segments");
   std::vector<double> tab;
@@ -1564,9 +1639,11 @@ int lbm_branch_table(const lbm_domain* d, double* rows, int n, int* count) {
     std::memcpy(rows, tab.data(), tab.size() * sizeof(double));
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_branch_coefficients(lbm_domain* d, double* c_drag, double* c_fric, int n, double* cd, double* cf) {
+int lbm_branch_coefficients(lbm_domain* d, double* c_drag, double* c_fric, int n, double* cd, double* cf) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   if (!d->have_tree) return fail(LBM_ESTATE, "no tree: set the geometry from a tree or segments");
@@ -1596,10 +1673,12 @@ int lbm_branch_coefficients(lbm_domain* d, double* c_drag, double* c_fric, int n
   if (cd) *cd = d->A_x > 0 ? mean[0] / (q * d->A_x) : std::numeric_limits<double>::quiet_NaN();
   if (cf) *cf = d->A_x > 0 && fsteps > 0 ? fmean[0] / (q * d->A_x) : std::numeric_limits<double>::quiet_NaN();
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
 int lbm_branch_drag_estimate(const double* rows, int n, const double* c_sect, double area, double* cd_est,
-                             double* c_out) {
+                             double* c_out) try {
   if (!rows || !cd_est || n < 0 || !(area > 0)) return fail(LBM_EINVAL, "bad argument");
   double sum = 0;
   for (int k = 0; k < n; ++k) {
@@ -1610,9 +1689,11 @@ int lbm_branch_drag_estimate(const double* rows, int n, const double* c_sect, do
   }
   *cd_est = sum / area;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_inflow_turbulence(lbm_domain* d, int n_modes, double integral_length) {
+int lbm_set_inflow_turbulence(lbm_domain* d, int n_modes, double integral_length) try {
   if (!d || n_modes < 1 || n_modes > kMaxModes || integral_length < 0) return fail(LBM_EINVAL, "bad argument");
   if (!(d->d.i_u > 0)) return fail(LBM_ESTATE, "the domain has uniform inflow (i_u = 0)");
   d->n_modes = n_modes;
@@ -1622,9 +1703,11 @@ int lbm_set_inflow_turbulence(lbm_domain* d, int n_modes, double integral_length
     return upload_modes(d);
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_inflow_modes(const lbm_domain* d, double* modes, int n, int* count) {
+int lbm_inflow_modes(const lbm_domain* d, double* modes, int n, int* count) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
   const int c = d->d.i_u > 0 ? d->n_modes : 0;
@@ -1637,6 +1720,8 @@ int lbm_inflow_modes(const lbm_domain* d, double* modes, int n, int* count) {
       for (int j = 0; j < 7; ++j) modes[7 * k + j] = m[(size_t)k * kModeCols + j];
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
 // sums the per-branch accumulators into total and (optionally) per-branch rows
@@ -1656,7 +1741,7 @@ void friction_rows(const lbm_domain* d, const std::vector<double>& acc, double t
   if (steps) *steps = cnt;
 }
 
-int lbm_friction(lbm_domain* d, double force[3], double* per_branch, int n, double* c_f) {
+int lbm_friction(lbm_domain* d, double force[3], double* per_branch, int n, double* c_f) try {
   if (!d || !force) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   if (per_branch && n < (int)d->prims.size()) return fail(LBM_EINVAL, "capacity below the number of branches");
@@ -1673,17 +1758,21 @@ int lbm_friction(lbm_domain* d, double force[3], double* per_branch, int n, doub
     *c_f = (d->A_x > 0 && u != 0) ? force[0] / (0.5 * u * u * d->A_x) : std::numeric_limits<double>::quiet_NaN();
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_friction_mean(lbm_domain* d, int on) {
+int lbm_set_friction_mean(lbm_domain* d, int on) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (d->friction_mean != (on != 0)) free_graphs(d);
   d->friction_mean = on != 0;
   d->mesh.friction = d->friction_mean;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_get_friction_mean(lbm_domain* d, double mean[3], double* per_branch, int n, long long* steps) {
+int lbm_get_friction_mean(lbm_domain* d, double mean[3], double* per_branch, int n, long long* steps) try {
   if (!d || !mean) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   if (per_branch && n < (int)d->prims.size()) return fail(LBM_EINVAL, "capacity below the number of branches");
@@ -1693,9 +1782,11 @@ int lbm_get_friction_mean(lbm_domain* d, double mean[3], double* per_branch, int
   CK(cudaStreamSynchronize(d->stream));
   friction_rows(d, acc, mean, per_branch, true, steps);
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_friction_samples(const lbm_domain* d, double* rows, int n, int* count) {
+int lbm_friction_samples(const lbm_domain* d, double* rows, int n, int* count) try {
   if (!d || !d->built) return fail(LBM_ESTATE, "set the geometry first");
   const int c = (int)d->fsamp.size();
   if (count) *count = c;
@@ -1723,29 +1814,37 @@ int lbm_friction_samples(const lbm_domain* d, double* rows, int n, int* count) {
     }
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_overlap(lbm_domain* d, int on) {
+int lbm_set_overlap(lbm_domain* d, int on) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (d->overlap != (on != 0)) free_graphs(d);
   d->overlap = on != 0;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_overlap_features(lbm_domain* d, int mask) {
+int lbm_set_overlap_features(lbm_domain* d, int mask) try {
   if (!d || (mask & ~LBM_OVL_ALL)) return fail(LBM_EINVAL, "bad argument");
   if (d->ovl_feat != mask) free_graphs(d);
   d->ovl_feat = mask;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_get_overlap_features(const lbm_domain* d, int* mask) {
+int lbm_get_overlap_features(const lbm_domain* d, int* mask) try {
   if (!d || !mask) return fail(LBM_EINVAL, "null argument");
   *mask = d->ovl_feat;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_get_overlap(const lbm_domain* d, int* faces, int* walls) {
+int lbm_get_overlap(const lbm_domain* d, int* faces, int* walls) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (!d->built) return fail(LBM_ESTATE, "set the geometry first");
   if (faces) *faces = d->mesh.ovl_faces ? 1 : 0;
@@ -1755,9 +1854,11 @@ int lbm_get_overlap(const lbm_domain* d, int* faces, int* walls) {
       if (d->mesh.lv[l].ovl_walls) *walls |= 1 << l;
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_wide_offsets(lbm_domain* d, int on) {
+int lbm_set_wide_offsets(lbm_domain* d, int on) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   const bool change = d->wide_offsets != (on != 0);
   if (change) free_graphs(d);
@@ -1765,28 +1866,36 @@ int lbm_set_wide_offsets(lbm_domain* d, int on) {
   // the tables follow (their device space holds the 64-bit form either way)
   if (change && d->base) return upload_tables(d);
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_watchdog(lbm_domain* d, int every) {
+int lbm_set_watchdog(lbm_domain* d, int every) try {
   if (!d || every < 0) return fail(LBM_EINVAL, "bad argument");
   d->watchdog = every;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_use_graphs(lbm_domain* d, int on) {
+int lbm_use_graphs(lbm_domain* d, int on) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   d->use_graphs = on != 0;
   if (!on) free_graphs(d);
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_set_timing(lbm_domain* d, int on) {
+int lbm_set_timing(lbm_domain* d, int on) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   d->timing = on != 0;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_get_timing(lbm_domain* d, double ms[6], long long launches[6], long long units[6]) {
+int lbm_get_timing(lbm_domain* d, double ms[6], long long launches[6], long long units[6]) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   if (d->base) CK(cudaStreamSynchronize(d->stream));
   for (auto& r : d->recs) {
@@ -1807,18 +1916,22 @@ int lbm_get_timing(lbm_domain* d, double ms[6], long long launches[6], long long
     d->units[k] = 0;
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_work_per_step(const lbm_domain* d, long long* cell_updates, int* kernels) {
+int lbm_work_per_step(const lbm_domain* d, long long* cell_updates, int* kernels) try {
   if (!d || !d->built) return fail(LBM_ESTATE, "geometry not set");
   long long cu = 0;
   for (int l = 0; l < d->mesh.L; ++l) cu += d->mesh.lv[l].n_fluid << l;
   if (cell_updates) *cell_updates = cu;
   if (kernels) *kernels = kernels_per_step(d, 0);
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_save(lbm_domain* d, const char* path) {
+int lbm_save(lbm_domain* d, const char* path) try {
   if (!d || !path) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   FILE* fp = std::fopen(path, "wb");
@@ -1846,9 +1959,11 @@ int lbm_save(lbm_domain* d, const char* path) {
   std::fwrite(acc, sizeof acc, 1, fp);
   bool ok = std::fclose(fp) == 0;
   return ok ? LBM_OK : fail(LBM_EINVAL, "write failed");
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_load(lbm_domain* d, const char* path) {
+int lbm_load(lbm_domain* d, const char* path) try {
   if (!d || !path) return fail(LBM_EINVAL, "null argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   FILE* fp = std::fopen(path, "rb");
@@ -1887,15 +2002,19 @@ int lbm_load(lbm_domain* d, const char* path) {
   d->parity0 = (int)hdr[1];
   d->steps = hdr[2];
   return set_tick(d);
+} catch (...) {
+  return exception_status();
 }
 
-void lbm_destroy(lbm_domain* d) {
+void lbm_destroy(lbm_domain* d) try {
   if (!d) return;
   free_graphs(d);
   destroy_side_streams(d);
   unpin_tables(d);
   for (auto e : d->pool) cudaEventDestroy(e);
   delete d;
+} catch (...) {
+  exception_status();
 }
 
 
@@ -1935,7 +2054,7 @@ int time_steps(lbm_domain* d, int steps, double* ms) {
 
 }  // namespace
 
-int lbm_set_schedule(lbm_domain* d, const lbm_schedule* s) {
+int lbm_set_schedule(lbm_domain* d, const lbm_schedule* s) try {
   if (!d || !s) return fail(LBM_EINVAL, "null argument");
   if (!variant_ok(d, s->odd_variant, s->even_variant)) return fail(LBM_EINVAL, "variant not available here");
   if (zshift_req(s->z_split_even, d->d.block) == -1 || zshift_req(s->z_split_odd, d->d.block) == -1)
@@ -1948,9 +2067,11 @@ int lbm_set_schedule(lbm_domain* d, const lbm_schedule* s) {
   d->z_split_even = s->z_split_even;
   d->z_split_odd = s->z_split_odd;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_get_schedule(const lbm_domain* d, lbm_schedule* s) {
+int lbm_get_schedule(const lbm_domain* d, lbm_schedule* s) try {
   if (!d || !s) return fail(LBM_EINVAL, "null argument");
   s->ctas_per_sm = 0;
   s->odd_variant = d->odd_variant;
@@ -1958,9 +2079,11 @@ int lbm_get_schedule(const lbm_domain* d, lbm_schedule* s) {
   s->z_split_even = d->z_split_even;
   s->z_split_odd = d->z_split_odd;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_autotune(lbm_domain* d, int steps, lbm_schedule* best, double* ms_per_step) {
+int lbm_autotune(lbm_domain* d, int steps, lbm_schedule* best, double* ms_per_step) try {
   if (!d || steps < 1) return fail(LBM_EINVAL, "bad argument");
   if (!d->base) return fail(LBM_ESTATE, "bind memory first");
   lbm_schedule b;
@@ -2026,6 +2149,8 @@ int lbm_autotune(lbm_domain* d, int steps, lbm_schedule* best, double* ms_per_st
   if (best) *best = b;
   if (ms_per_step) *ms_per_step = bms;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
 }  // extern "C"
@@ -2152,7 +2277,7 @@ int capture_batch(lbm_batch* b) {
 
 extern "C" {
 
-int lbm_batch_create(lbm_domain* const* domains, int n, void* cuda_stream, lbm_batch** out) {
+int lbm_batch_create(lbm_domain* const* domains, int n, void* cuda_stream, lbm_batch** out) try {
   if (!domains || n < 1 || !out) return fail(LBM_EINVAL, "bad argument");
   *out = nullptr;
   auto* b = new (std::nothrow) lbm_batch();
@@ -2212,15 +2337,19 @@ int lbm_batch_create(lbm_domain* const* domains, int n, void* cuda_stream, lbm_b
   b->need = off;
   *out = b;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_batch_memory_requirements(const lbm_batch* b, size_t* bytes) {
+int lbm_batch_memory_requirements(const lbm_batch* b, size_t* bytes) try {
   if (!b || !bytes) return fail(LBM_EINVAL, "null argument");
   *bytes = b->need;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_batch_bind_memory(lbm_batch* b, void* ptr, size_t bytes) {
+int lbm_batch_bind_memory(lbm_batch* b, void* ptr, size_t bytes) try {
   if (!b || !ptr) return fail(LBM_EINVAL, "null argument");
   if (bytes < b->need) return fail(LBM_ENOMEM, "bound buffer smaller than lbm_batch_memory_requirements");
   if ((uintptr_t)ptr & 255) return fail(LBM_EINVAL, "bound buffer must be 256-byte aligned");
@@ -2231,9 +2360,11 @@ int lbm_batch_bind_memory(lbm_batch* b, void* ptr, size_t bytes) {
       CK(cudaMemcpyAsync(b->base + b->off_items[l], b->items[l].data(), b->items[l].size() * sizeof(int2),
                          cudaMemcpyHostToDevice, b->stream));
   return upload_descs(b);
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_batch_set_schedule(lbm_batch* b, const lbm_schedule* s) {
+int lbm_batch_set_schedule(lbm_batch* b, const lbm_schedule* s) try {
   if (!b || !s) return fail(LBM_EINVAL, "null argument");
   if (s->ctas_per_sm < 0 || s->ctas_per_sm > 64 ||
       (s->odd_variant != LBM_ODD_COLUMNS && s->odd_variant != LBM_ODD_DIRECT && s->odd_variant != LBM_ODD_PAIRS) ||
@@ -2248,15 +2379,19 @@ int lbm_batch_set_schedule(lbm_batch* b, const lbm_schedule* s) {
   for (lbm_domain* d : b->doms) free_graphs(d);
   if (b->base) return upload_descs(b);
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_batch_get_schedule(const lbm_batch* b, lbm_schedule* s) {
+int lbm_batch_get_schedule(const lbm_batch* b, lbm_schedule* s) try {
   if (!b || !s) return fail(LBM_EINVAL, "null argument");
   *s = b->sched;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_batch_step(lbm_batch* b, int n) {
+int lbm_batch_step(lbm_batch* b, int n) try {
   if (!b || n < 0) return fail(LBM_EINVAL, "bad argument");
   if (!b->base) return fail(LBM_ESTATE, "bind memory first");
   const int p0 = b->doms[0]->parity0;
@@ -2277,16 +2412,20 @@ int lbm_batch_step(lbm_batch* b, int n) {
     }
   }
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_batch_use_graphs(lbm_batch* b, int on) {
+int lbm_batch_use_graphs(lbm_batch* b, int on) try {
   if (!b) return fail(LBM_EINVAL, "null argument");
   b->use_graphs = on != 0;
   if (!on) free_batch_graphs(b);
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-int lbm_batch_autotune(lbm_batch* b, int steps, lbm_schedule* best, double* ms_per_step) {
+int lbm_batch_autotune(lbm_batch* b, int steps, lbm_schedule* best, double* ms_per_step) try {
   if (!b || steps < 1) return fail(LBM_EINVAL, "bad argument");
   if (!b->base) return fail(LBM_ESTATE, "bind memory first");
   static const int kCtas[] = {0, 1, 2, 3, 4, 6, 8};
@@ -2349,9 +2488,11 @@ int lbm_batch_autotune(lbm_batch* b, int steps, lbm_schedule* best, double* ms_p
   if (best) *best = bs;
   if (ms_per_step) *ms_per_step = bms;
   return LBM_OK;
+} catch (...) {
+  return exception_status();
 }
 
-void lbm_batch_destroy(lbm_batch* b) {
+void lbm_batch_destroy(lbm_batch* b) try {
   if (!b) return;
   free_batch_graphs(b);
   if (b->stream) cudaStreamSynchronize(b->stream);
@@ -2362,6 +2503,8 @@ void lbm_batch_destroy(lbm_batch* b) {
   for (cudaEvent_t ev : b->done) cudaEventDestroy(ev);
   if (b->fork) cudaEventDestroy(b->fork);
   delete b;
+} catch (...) {
+  exception_status();
 }
 
 }  // extern "C"

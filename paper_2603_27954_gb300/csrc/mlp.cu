@@ -9,6 +9,8 @@
 
 #include <cmath>
 #include <cstdio>
+#include <new>
+#include <stdexcept>
 
 #include "internal.h"
 
@@ -293,6 +295,21 @@ int mfail(int code, const std::string& m) {
   g_mlp_api_err = m;
   return code;
 }
+// No C++ exception leaves the C-ABI: the one in flight (called from a catch
+// handler) becomes a status and a message.
+int mexception_status() {
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    return mfail(LBM_ENOMEM, "host memory allocation failed");
+  } catch (const std::length_error&) {
+    return mfail(LBM_ENOMEM, "host allocation too large");
+  } catch (const std::exception& e) {
+    return mfail(LBM_ESTATE, std::string("internal error: ") + e.what());
+  } catch (...) {
+    return mfail(LBM_ESTATE, "internal error");
+  }
+}
 #define MCK(call)                                                             \
   do {                                                                        \
     cudaError_t e_ = (call);                                                  \
@@ -404,7 +421,7 @@ bool ready(const lbm_mlp* m) { return m && m->base; }
 
 extern "C" {
 
-int lbm_mlp_create(int n_in, int width, int hidden_layers, void* stream, lbm_mlp** out) {
+int lbm_mlp_create(int n_in, int width, int hidden_layers, void* stream, lbm_mlp** out) try {
   if (!out || n_in < 1 || n_in > 64 || width < 1 || width > 1024 || hidden_layers < 1 || hidden_layers > 8)
     return mfail(LBM_EINVAL, "n_in 1..64, width 1..1024, hidden layers 1..8");
   auto* m = new (std::nothrow) lbm_mlp();
@@ -429,17 +446,21 @@ int lbm_mlp_create(int n_in, int width, int hidden_layers, void* stream, lbm_mlp
   m->PW = pw;
   *out = m;
   return LBM_OK;
+} catch (...) {
+  return mexception_status();
 }
 
-int lbm_mlp_memory_requirements(const lbm_mlp* m, int max_batch, size_t* bytes) {
+int lbm_mlp_memory_requirements(const lbm_mlp* m, int max_batch, size_t* bytes) try {
   if (!m || !bytes || max_batch < 1) return mfail(LBM_EINVAL, "bad argument");
   lbm_mlp tmp = *m;
   mlp_layout(&tmp, max_batch);
   *bytes = tmp.need;
   return LBM_OK;
+} catch (...) {
+  return mexception_status();
 }
 
-int lbm_mlp_bind_memory(lbm_mlp* m, void* dev, size_t bytes, int max_batch) {
+int lbm_mlp_bind_memory(lbm_mlp* m, void* dev, size_t bytes, int max_batch) try {
   if (!m || !dev || max_batch < 1) return mfail(LBM_EINVAL, "bad argument");
   if ((uintptr_t)dev & 255) return mfail(LBM_EINVAL, "buffer must be 256-byte aligned");
   mlp_layout(m, max_batch);
@@ -455,15 +476,19 @@ int lbm_mlp_bind_memory(lbm_mlp* m, void* dev, size_t bytes, int max_batch) {
   for (size_t o : {m->o_w, m->o_g, m->o_m, m->o_v}) MCK(cudaMemsetAsync(m->base + o, 0, m->P * 4, m->stream));
   MCK(cudaStreamSynchronize(m->stream));
   return LBM_OK;
+} catch (...) {
+  return mexception_status();
 }
 
-int lbm_mlp_param_count(const lbm_mlp* m, long long* n) {
+int lbm_mlp_param_count(const lbm_mlp* m, long long* n) try {
   if (!m || !n) return mfail(LBM_EINVAL, "null argument");
   *n = m->P;
   return LBM_OK;
+} catch (...) {
+  return mexception_status();
 }
 
-int lbm_mlp_set_params(lbm_mlp* m, const float* host, long long n) {
+int lbm_mlp_set_params(lbm_mlp* m, const float* host, long long n) try {
   if (!ready(m) || !host || n != m->P) return mfail(LBM_EINVAL, "bind memory first; n must equal the parameter count");
   MCK(cudaMemcpyAsync(m->base + m->o_w, host, n * 4, cudaMemcpyHostToDevice, m->stream));
   MCK(cudaMemsetAsync(m->base + m->o_m, 0, n * 4, m->stream));
@@ -473,16 +498,20 @@ int lbm_mlp_set_params(lbm_mlp* m, const float* host, long long n) {
   MCK(cudaStreamSynchronize(m->stream));
   m->t = 0;
   return LBM_OK;
+} catch (...) {
+  return mexception_status();
 }
 
-int lbm_mlp_get_params(lbm_mlp* m, float* host, long long n) {
+int lbm_mlp_get_params(lbm_mlp* m, float* host, long long n) try {
   if (!ready(m) || !host || n != m->P) return mfail(LBM_EINVAL, "bind memory first; n must equal the parameter count");
   MCK(cudaMemcpyAsync(host, m->base + m->o_w, n * 4, cudaMemcpyDeviceToHost, m->stream));
   MCK(cudaStreamSynchronize(m->stream));
   return LBM_OK;
+} catch (...) {
+  return mexception_status();
 }
 
-int lbm_mlp_set_normalization(lbm_mlp* m, const float* mu_x, const float* sd_x, float mu_y, float sd_y) {
+int lbm_mlp_set_normalization(lbm_mlp* m, const float* mu_x, const float* sd_x, float mu_y, float sd_y) try {
   if (!ready(m) || !mu_x || !sd_x || !(sd_y > 0)) return mfail(LBM_EINVAL, "bad argument");
   std::vector<float> norm(2 * m->n_in);
   for (int i = 0; i < m->n_in; ++i) {
@@ -495,17 +524,21 @@ int lbm_mlp_set_normalization(lbm_mlp* m, const float* mu_x, const float* sd_x, 
   m->mu_y = mu_y;
   m->sd_y = sd_y;
   return LBM_OK;
+} catch (...) {
+  return mexception_status();
 }
 
-int lbm_mlp_forward(lbm_mlp* m, const float* x, int batch, float* y) {
+int lbm_mlp_forward(lbm_mlp* m, const float* x, int batch, float* y) try {
   if (!ready(m) || !x || !y || batch < 1 || batch > m->max_batch) return mfail(LBM_EINVAL, "bad argument");
   int rc = mlp_forward_dev(m, x, nullptr, batch);
   if (rc) return rc;
   MRC(lbm::mlp_denorm(m->dev<float>(m->o_yh), batch, m->mu_y, m->sd_y, y, m->stream));
   return LBM_OK;
+} catch (...) {
+  return mexception_status();
 }
 
-int lbm_mlp_ensemble_forward(lbm_mlp* const* nets, int n, const float* x, int batch, float* y) {
+int lbm_mlp_ensemble_forward(lbm_mlp* const* nets, int n, const float* x, int batch, float* y) try {
   if (!nets || n < 1 || !x || !y || batch < 1) return mfail(LBM_EINVAL, "bad argument");
   for (int k = 0; k < n; ++k) {
     const lbm_mlp* m = nets[k];
@@ -520,10 +553,12 @@ int lbm_mlp_ensemble_forward(lbm_mlp* const* nets, int n, const float* x, int ba
     MRC(lbm::mlp_ens_acc(m->dev<float>(m->o_yh), batch, m->mu_y, m->sd_y, 1.0f / (float)n, k == 0, y, m->stream));
   }
   return LBM_OK;
+} catch (...) {
+  return mexception_status();
 }
 
 int lbm_mlp_gradients(lbm_mlp* m, const float* x, const float* y, const int* idx, int batch, float* grad_host,
-                      double* loss) {
+                      double* loss) try {
   if (!ready(m) || !x || !y || batch < 1 || batch > m->max_batch) return mfail(LBM_EINVAL, "bad argument");
   int rc = mlp_loss_grad(m, x, y, idx, batch, loss);
   if (rc) return rc;
@@ -532,10 +567,12 @@ int lbm_mlp_gradients(lbm_mlp* m, const float* x, const float* y, const int* idx
     MCK(cudaStreamSynchronize(m->stream));
   }
   return LBM_OK;
+} catch (...) {
+  return mexception_status();
 }
 
 int lbm_mlp_train_step(lbm_mlp* m, const float* x, const float* y, const int* idx, int batch, float lr,
-                       double* loss) {
+                       double* loss) try {
   if (!ready(m) || !x || !y || batch < 1 || batch > m->max_batch || !(lr > 0)) return mfail(LBM_EINVAL, "bad argument");
   int rc = mlp_loss_grad(m, x, y, idx, batch, loss);
   if (rc) return rc;
@@ -546,6 +583,8 @@ int lbm_mlp_train_step(lbm_mlp* m, const float* x, const float* y, const int* id
                     m->P, lr, b1, b2, 1e-8f, c1, c2, m->dev<__nv_bfloat16>(m->o_wb), m->dev<int>(m->o_map),
                     m->stream));
   return LBM_OK;
+} catch (...) {
+  return mexception_status();
 }
 
 const char* lbm_mlp_last_error(void) { return g_mlp_api_err.c_str(); }

@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdlib>
+#include <exception>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -24,7 +26,11 @@ inline int host_threads() {
   return n;
 }
 
-// f(i) for i in [0, n); chunks of `grain` indices are claimed dynamically
+// f(i) for i in [0, n); chunks of `grain` indices are claimed dynamically.
+// An exception thrown by f on any thread stops the loop and is rethrown on
+// the calling thread once every thread has finished (none escapes a worker,
+// which would end the process); if a thread cannot be started, the threads
+// already running finish the loop.
 template <class F>
 void parallel_for(long long n, F&& f, long long grain = 1) {
   const int nt = (int)std::min<long long>(host_threads(), (n + grain - 1) / std::max(1LL, grain));
@@ -33,19 +39,32 @@ void parallel_for(long long n, F&& f, long long grain = 1) {
     return;
   }
   std::atomic<long long> next{0};
+  std::exception_ptr err;
+  std::mutex err_mu;
   auto work = [&] {
-    for (;;) {
-      const long long b = next.fetch_add(grain);
-      if (b >= n) break;
-      const long long e = std::min(n, b + grain);
-      for (long long i = b; i < e; ++i) f(i);
+    try {
+      for (;;) {
+        const long long b = next.fetch_add(grain);
+        if (b >= n) break;
+        const long long e = std::min(n, b + grain);
+        for (long long i = b; i < e; ++i) f(i);
+      }
+    } catch (...) {
+      std::lock_guard<std::mutex> lock(err_mu);
+      if (!err) err = std::current_exception();
+      next.store(n);
     }
   };
   std::vector<std::thread> pool;
   pool.reserve(nt - 1);
-  for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  try {
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  } catch (...) {
+    // fewer threads: the ones started and this one finish the loop
+  }
   work();
   for (auto& th : pool) th.join();
+  if (err) std::rethrow_exception(err);
 }
 
 // ascending sort: chunks sorted in parallel, then merged pairwise

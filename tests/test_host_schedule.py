@@ -184,3 +184,36 @@ def test_drag_decode_on_the_host():
         L.lbm_drag_decode(h, acc)
     assert e.value.code == L.LBM_ETIMEOUT
     L.lbm_destroy(h)
+
+
+def test_host_allocation_failure_returns_a_status():
+    """A host allocation that fails inside the library - here the mesh build
+    of a 2048^3 domain in a process whose address space is capped at 8 GB -
+    comes back as LBM_ENOMEM with a message, and the caller carries on: no
+    C++ exception crosses the C-ABI (one would end the calling process with
+    std::terminate)."""
+    import os
+    import subprocess
+    import sys
+    import textwrap
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = textwrap.dedent("""
+        import resource, sys
+        resource.setrlimit(resource.RLIMIT_AS, (8 << 30, 8 << 30))
+        sys.path.insert(0, %r)
+        import numpy as np
+        from paper_2603_27954_gb300 import lbm as L
+        h = L.lbm_create_domain(L.domain_desc(2048, 2048, 2048, bc=("inout", "slip", "slip"), nu_finest=0.01))
+        try:
+            L.lbm_set_geometry_prims(h, [], np.zeros((0, 8)))
+        except L.LbmError as e:
+            print("status", e.code)
+        L.lbm_destroy(h)
+        h = L.lbm_create_domain(L.domain_desc(32, 32, 32, bc=("inout", "slip", "slip"), nu_finest=0.01))
+        L.lbm_set_geometry_prims(h, [], np.zeros((0, 8)))
+        L.lbm_destroy(h)
+        print("alive")
+    """ % root)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "status %d" % L.LBM_ENOMEM in r.stdout and "alive" in r.stdout, r.stdout
