@@ -567,7 +567,10 @@ int lbm_get_timing(lbm_domain* d, double ms[6], long long launches[6], long long
 int lbm_work_per_step(const lbm_domain* d, long long* cell_updates, int* kernels);
 
 /* Write / read the full state (populations, parities, step and force
-   history) to / from a file; the domain must be built identically. */
+   history) to / from a file; the domain must be built identically.
+   lbm_load checks the file's header and size before it copies anything: a
+   file that does not match the domain gives LBM_EINVAL and leaves the
+   domain's state unchanged. */
 int lbm_save(lbm_domain* d, const char* path);
 int lbm_load(lbm_domain* d, const char* path);
 

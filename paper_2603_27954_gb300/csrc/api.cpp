@@ -1971,10 +1971,20 @@ int lbm_load(lbm_domain* d, const char* path) try {
   char magic[8];
   long long hdr[4];
   bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "LBMSTAT1", 8) == 0 &&
-            std::fread(hdr, sizeof hdr, 1, fp) == 1 && hdr[0] == (long long)d->need && hdr[3] == d->mesh.L;
+            std::fread(hdr, sizeof hdr, 1, fp) == 1 && hdr[0] == (long long)d->need && hdr[3] == d->mesh.L &&
+            (hdr[1] == 0 || hdr[1] == 1) && hdr[2] >= 0;
   if (!ok) {
     std::fclose(fp);
     return fail(LBM_EINVAL, "state file does not match this domain");
+  }
+  // the whole file is checked for the size lbm_save writes before anything
+  // is copied, so that a truncated file leaves the domain's state unchanged
+  long long want = 8 + (long long)sizeof hdr + 8 * (long long)sizeof(double);
+  for (const Level& v : d->mesh.lv) want += (long long)(v.f_elems() * (size_t)v.esize);
+  const long long here = (long long)ftello(fp);
+  if (fseeko(fp, 0, SEEK_END) != 0 || (long long)ftello(fp) != want || fseeko(fp, (off_t)here, SEEK_SET) != 0) {
+    std::fclose(fp);
+    return fail(LBM_EINVAL, "state file has the wrong size for this domain");
   }
   std::vector<uint8_t> host;
   for (const Level& v : d->mesh.lv) {
