@@ -95,6 +95,8 @@ def _declare(L):
     L.orc_get_macro.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
     L.orc_level_links.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
     L.orc_level_links.restype = C.c_int
+    L.orc_level_link_segs.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
+    L.orc_level_link_segs.restype = C.c_int
     L.orc_force.argtypes = [C.c_void_p, _dp, _dp, C.POINTER(C.c_long)]
     L.orc_mass.argtypes = [C.c_void_p, C.POINTER(C.c_double), _dp]
     L.orc_cell_type.argtypes = [C.c_void_p, C.c_int, _bp]
@@ -339,6 +341,13 @@ class Sim:
         q = np.zeros(n)
         lib().orc_level_links(self._h, level, cell.ctypes.data, d.ctypes.data, q.ctypes.data, n)
         return cell, d, q
+
+    def link_segments(self, level):
+        """The primitive (branch) each cut link of the level belongs to, in the order of links()."""
+        n = lib().orc_level_links(self._h, level, None, None, None, 0)
+        seg = np.zeros(n, np.int32)
+        lib().orc_level_link_segs(self._h, level, seg.ctypes.data, n)
+        return seg
 
     def force(self):
         last, tot = np.zeros(3), np.zeros(3)

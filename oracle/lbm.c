@@ -531,6 +531,15 @@ int orc_level_links(const orc_sim* s, int level, long* cell, int* dir, double* q
   return n;
 }
 
+/* the primitive (branch) each cut link of a level is attributed to, in the
+   order of orc_level_links */
+int orc_level_link_segs(const orc_sim* s, int level, int* seg, int max) {
+  const lev* v = &s->lv[level];
+  int n = 0;
+  for (long k = 0; k < v->nlink && n < max; ++k, ++n) seg[n] = v->lseg[k];
+  return n;
+}
+
 void orc_force(const orc_sim* s, double last[3], double sum[3], long* nsum) {
   const lev* v = &s->lv[s->L - 1];
   for (int a = 0; a < 3; ++a) { last[a] = v->F[a]; sum[a] = s->Fsum[a]; }

@@ -99,6 +99,7 @@ void orc_level_box(const orc_sim* s, int level, int lo[3], int hi[3]);
 void orc_get_f(const orc_sim* s, int level, double* out);
 void orc_get_macro(const orc_sim* s, int level, double* rho, double* u);
 int orc_level_links(const orc_sim* s, int level, long* cell, int* dir, double* q, int max);
+int orc_level_link_segs(const orc_sim* s, int level, int* seg, int max);
 void orc_force(const orc_sim* s, double last[3], double sum[3], long* nsum);
 void orc_mass(const orc_sim* s, double* mass, double mom[3]);
 int orc_cell_type(const orc_sim* s, int level, unsigned char* out);
