@@ -300,6 +300,12 @@ int lbm_get_cell_types(const lbm_domain* d, int level, unsigned char* out, size_
 int lbm_get_links(const lbm_domain* d, int level, long long* cell, int* dir, double* q, size_t n,
                   long long* count);
 
+/* The branch (primitive index) each cut link of a level belongs to - the
+   cylinder its ray from the fluid cell enters first - in the order of
+   lbm_get_links; n is the capacity, *count the number of links.  This is
+   the attribution behind the per-branch forces (Sec. 2.4). */
+int lbm_get_link_branches(const lbm_domain* d, int level, int* branch, size_t n, long long* count);
+
 /* Placed segments (rows of 8 doubles) of the tree; n capacity. */
 int lbm_get_segments(const lbm_domain* d, double* seg, int n, int* count);
 

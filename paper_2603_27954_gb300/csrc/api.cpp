@@ -1588,6 +1588,17 @@ int lbm_get_links(const lbm_domain* d, int level, long long* cell, int* dir, dou
   return exception_status();
 }
 
+int lbm_get_link_branches(const lbm_domain* d, int level, int* branch, size_t n, long long* count) try {
+  if (!valid_level(d, level)) return fail(LBM_EINVAL, "bad level or geometry not set");
+  const Level& v = d->mesh.lv[level];
+  if (count) *count = (long long)v.links.size();
+  if (branch)
+    for (size_t k = 0; k < v.links.size() && k < n; ++k) branch[k] = v.links[k].seg;
+  return LBM_OK;
+} catch (...) {
+  return exception_status();
+}
+
 int lbm_get_segments(const lbm_domain* d, double* seg, int n, int* count) try {
   if (!d) return fail(LBM_EINVAL, "null argument");
   int c = d->have_tree ? d->tree.count() : 0;

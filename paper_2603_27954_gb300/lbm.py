@@ -92,6 +92,7 @@ def _load():
         "lbm_geometry_info": ([vp, dp, dp, ip, dp], i),
         "lbm_get_cell_types": ([vp, i, ubp, sz], i),
         "lbm_get_links": ([vp, i, llp, ip, dp, sz, llp], i),
+        "lbm_get_link_branches": ([vp, i, ip, sz, llp], i),
         "lbm_get_segments": ([vp, dp, i, ip], i),
         "lbm_set_watchdog": ([vp, i], i),
         "lbm_branch_table": ([vp, dp, i, ip], i),
@@ -335,6 +336,16 @@ def lbm_get_links(h, level):
     _ck(_lib.lbm_get_links(h, level, cell.ctypes.data_as(C.POINTER(C.c_longlong)),
                            d.ctypes.data_as(C.POINTER(C.c_int)), _dp(q), n.value, C.byref(n)), "lbm_get_links")
     return cell, d, q
+
+
+def lbm_get_link_branches(h, level):
+    """The branch of each cut link of a level, in the order of lbm_get_links."""
+    n = C.c_longlong()
+    _ck(_lib.lbm_get_link_branches(h, level, None, 0, C.byref(n)), "lbm_get_link_branches")
+    out = np.zeros(n.value, np.int32)
+    _ck(_lib.lbm_get_link_branches(h, level, out.ctypes.data_as(C.POINTER(C.c_int)), n.value, C.byref(n)),
+        "lbm_get_link_branches")
+    return out
 
 
 def lbm_get_segments(h):

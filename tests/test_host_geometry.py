@@ -85,6 +85,26 @@ def test_cell_types_and_links_match_oracle(case):
     L.lbm_destroy(h)
 
 
+@pytest.mark.parametrize("case", ["tiny", "amr2_small", "amr2_quarter"])
+def test_link_branches_match_oracle(case):
+    """The branch each finest-level cut link is attributed to (the cylinder
+    its ray enters first; per-branch forces, Sec. 2.4) is the oracle's,
+    link for link: integer data, compared exactly."""
+    h = lib_domain(case)
+    sim, _ = oracle_case(case)
+    fin = W.CASES[case]["levels"] - 1
+    c1, d1, _ = L.lbm_get_links(h, fin)
+    b1 = L.lbm_get_link_branches(h, fin)
+    c2, d2, _ = sim.links(fin)
+    b2 = sim.link_segments(fin)
+    k1, k2 = np.lexsort((d1, c1)), np.lexsort((d2, c2))
+    np.testing.assert_array_equal(c1[k1], c2[k2])
+    np.testing.assert_array_equal(d1[k1], d2[k2])
+    np.testing.assert_array_equal(b1[k1], b2[k2])
+    assert len(np.unique(b1)) == L.lbm_geometry_info(h)["n_segments"]
+    L.lbm_destroy(h)
+
+
 def test_planar_walls_links_match_oracle():
     """General primitives (two half-spaces) classify and link identically."""
     kinds = [1, 1]
