@@ -34,6 +34,7 @@ CASE = "amr2"
 QUARTER = "amr2_quarter"  # the same tree case scaled down 4x per axis, for the C_D comparison
 PRECISION_CASE = "amr4"
 BYTES_PER_UPDATE = 2 * 27 * 4  # read and write 27 FP32 populations
+NOMINAL_HBM_GBS = 7900.0  # GB300's nominal HBM3e bandwidth (the measured copy peak is the roofline)
 KERNEL_SOURCES = ["paper_2603_27954_gb300/csrc/collide.cuh", "paper_2603_27954_gb300/csrc/cumulant.cuh"]
 
 
@@ -487,6 +488,7 @@ def main():
     roofline = {"bound": "hbm", "kernel": "k_collide (fused collide-stream)",
                 "achieved": coll_gbs, "peak": peak, "peak_kind": peak_kind + " copy bandwidth", "unit": "GB/s",
                 "frac": coll_gbs / peak,
+                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": coll_gbs / NOMINAL_HBM_GBS,
                 "traffic": tr["bytes_per_launch"] if tr else None,
                 "traffic_note": tr["note"] if tr else "no ncu capture of the current kernel sources",
                 "algorithmic_bytes_per_launch": coll_units * BYTES_PER_UPDATE / max(1, coll_launch),
