@@ -538,7 +538,9 @@ def main():
     if not args.no_batched_form:
         batched = batched_form(L, W, torch, stream, args.batched_steps, peak)
 
-    learned = None
+    learned = {"ran": False, "how": "bench.py --learned-form 1 (about 20 min: 1.9e5 LBM branch samples, "
+                                     "two 4-member ensembles, eight held-out LBM judging runs)",
+               "last_full_run": "profiles/learned_form_sectional_drag.md"}
     if args.learned_form > 0:
         from paper_2603_27954_gb300 import surrogate as SG
         counts = {k: max(1, int(round(v * args.learned_form))) for k, v in W.LEARNED_COUNTS.items()}
