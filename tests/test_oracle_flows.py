@@ -444,3 +444,33 @@ def test_sampled_one_cell_recursion_reproduces_the_oracle_step():
     for l in range(2):
         n, err, moved = check_level(S0[l], sim.f(l), sim.cell_type(l), l, info["nu0"] * 2 ** l, 40, l, 1e-13)
         assert n == 40 and moved > 1e-4
+
+
+def test_lateral_inflow_faces_pull_the_inflow_equilibrium_and_interior_streams():
+    """Sec. 2.3's inflow on the faces other than the outlet: from a random
+    non-uniform state, after one step every population a cell pulls from
+    outside y or z (x - c_i beyond a lateral face) is the inflow equilibrium
+    f^eq(1, U e_x) exactly, whatever the interior holds, and every population
+    pulled from inside is the post-collision value at x - c_i (plain
+    streaming, one-cell collision pinned separately)."""
+    nx, ny, nz, nu, U = 4, 5, 6, 0.03, 0.05
+    s = O.Sim(nx, ny, nz, bc=("periodic", "inflow", "inflow"), nu0=nu, u_in=U)
+    rng = np.random.default_rng(17)
+    s.init_field(0, 1.0 + 0.01 * rng.standard_normal((nz, ny, nx)), 0.03 * rng.standard_normal((nz, ny, nx, 3)))
+    A = _post_collision(s, nu)
+    s.step(1)
+    B = s.f(0)
+    feq_in = O.equilibrium(1.0, [U, 0.0, 0.0])
+    outside = 0
+    for i in range(27):
+        cx, cy, cz = C27[i]
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    sy, sz, sx = y - cy, z - cz, (x - cx) % nx
+                    if 0 <= sy < ny and 0 <= sz < nz:
+                        assert B[z, y, x, i] == A[sz, sy, sx, i]
+                    else:
+                        assert B[z, y, x, i] == feq_in[i]
+                        outside += 1
+    assert outside > 0
