@@ -86,3 +86,28 @@ def test_oracle_turbulent_inflow_reaches_the_interior():
     dev = u[:, :, 0, :] - np.array([U, 0, 0])
     rms = np.sqrt((dev ** 2).mean())
     assert 0.1 * I_U * U < rms < 3 * I_U * U
+
+
+def test_inflow_face_pulls_the_equilibrium_of_the_frozen_field(modes):
+    """Taylor's hypothesis at the inflow face: at coarse step t every
+    population a first-plane cell pulls across x = 0, from the outside cell
+    g = (-1, y - c_y, z - c_z), is f^eq(1, U e_x + u'(g + 1/2 - U t e_x)) with
+    u' the mode sum, to round-off - the outside cell's centre, not the
+    pulling cell's, and the field carried by U t, not U (t + 1)."""
+    C27 = np.array([[i % 3 - 1, (i // 3) % 3 - 1, i // 9 - 1] for i in range(27)])
+    nx, ny, nz = 6, 7, 5
+    sim = O.Sim(nx, ny, nz, bc=("inout", "periodic", "periodic"), nu0=0.02, u_in=U)
+    sim.set_turbulence(modes, U)
+    for t in range(3):
+        sim.step(1)
+        f = sim.f(0)
+        checked = 0
+        for i in np.flatnonzero(C27[:, 0] == 1):
+            cx, cy, cz = C27[i]
+            for z in range(nz):
+                for y in range(ny):
+                    g = np.array([-1.0, (y - cy) % ny, (z - cz) % nz]) + 0.5
+                    u = np.array([U, 0.0, 0.0]) + T.fluctuation(modes, g - np.array([U * t, 0.0, 0.0]))
+                    assert f[z, y, 0, i] == pytest.approx(O.equilibrium(1.0, u)[i], rel=0, abs=1e-15)
+                    checked += 1
+        assert checked == 9 * ny * nz
