@@ -180,8 +180,10 @@ int lbm_init_field(lbm_domain* d, int level, const double* rho, const double* u,
    mesh, interpolated bounce-back on the tree and the momentum-exchange
    force; Sec. 2.3: the inflow, outflow and lateral faces): advance n coarse
    steps, every level l taking 2^l steps of its own (recursive sub-cycling,
-   acoustic scaling), asynchronously on the domain's stream (one captured
-   CUDA graph per coarse step unless graphs are off or timing is on).
+   acoustic scaling), asynchronously on the domain's stream (captured CUDA
+   graphs - runs of eight and of two coarse steps while that many remain and
+   no transfer is pending, else one per coarse step - unless graphs are off
+   or timing is on; the results are the same either way).
    LBM_ESTATE before lbm_bind_memory; returns the status of the last
    watchdog check (lbm_set_watchdog), LBM_EUNSTABLE if it failed. */
 int lbm_step(lbm_domain* d, int n_coarse);
