@@ -43,7 +43,8 @@ typedef enum {
   LBM_ENOMEM = -2,    /* host allocation failed or the bound buffer is too small */
   LBM_ECUDA = -3,     /* a CUDA runtime call failed (message: lbm_last_error) */
   LBM_EUNSTABLE = -4, /* the watchdog found NaN/Inf or a density outside [0.5, 2] */
-  LBM_ESTATE = -5,    /* call out of order (e.g. stepping before binding memory) */
+  LBM_ESTATE = -5,    /* call out of order (e.g. stepping before binding memory), or an
+                         internal error (lbm_last_error says which) */
   LBM_ETIMEOUT = -6   /* reserved: a bounded device wait gave up */
 } lbm_status;
 
