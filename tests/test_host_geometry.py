@@ -129,6 +129,35 @@ def test_planar_walls_links_match_oracle():
     L.lbm_destroy(h)
 
 
+def test_degenerate_wall_fractions_clamp_alike():
+    """Walls that graze the cell centres: a plane 1e-9 below a row of fluid
+    centres gives q = 1e-9, clamped to 1e-6, and a plane through a row of
+    centres makes that row solid (inclusive test) and gives q = 1 from the
+    next row.  Library and oracle classify, link and clamp identically."""
+    kinds = [1, 1]
+    params = np.zeros((2, 8))
+    params[0, :4] = (0, 1, 0, 10.5 - 1e-9)   # n.x <= d: rows y <= 9 solid, row 10 fluid at 1e-9
+    params[1, :4] = (0, -1, 0, -20.5)        # -y <= -20.5: rows y >= 20 solid (centre 20.5 on the plane)
+    h = L.lbm_create_domain(L.domain_desc(16, 32, 16, block=16, bc=("periodic",) * 3, nu_finest=0.1))
+    L.lbm_set_geometry_prims(h, kinds, params)
+    s = O.Sim(16, 32, 16, bc=("periodic",) * 3, nu0=0.1, u_in=0.0)
+    s.set_prims(O.prims([(1, params[0, :4]), (1, params[1, :4])]))
+    t = L.lbm_get_cell_types(h, 0)
+    np.testing.assert_array_equal(t, s.cell_type(0))
+    assert (t[:, 10, :] == 0).all() and (t[:, 9, :] == 1).all() and (t[:, 20, :] == 1).all()
+    c1, d1, q1 = L.lbm_get_links(h, 0)
+    c2, d2, q2 = s.links(0)
+    k1, k2 = np.lexsort((d1, c1)), np.lexsort((d2, c2))
+    np.testing.assert_array_equal(c1[k1], c2[k2])
+    np.testing.assert_array_equal(d1[k1], d2[k2])
+    np.testing.assert_allclose(q1[k1], q2[k2], rtol=0, atol=1e-15)
+    y = (c1 // 16) % 32
+    cy = (d1 // 3) % 3 - 1
+    assert np.all(q1[(y == 10) & (cy == -1)] == 1e-6)
+    assert np.all(q1[(y == 19) & (cy == 1)] == 1.0)
+    L.lbm_destroy(h)
+
+
 def test_invalid_descriptors_are_rejected():
     bad = [
         dict(levels=0), dict(levels=7), dict(block=12), dict(u_in=0.5),
