@@ -31,3 +31,54 @@ def test_status_strings():
     from paper_2603_27954_gb300 import lbm as L
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert L.lbm_status_string(code) != "unknown status"
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include "lbm.h"
+int main(void) {
+  lbm_domain_desc dd = {256, 128, 128, 2, 16, {LBM_BC_INOUT, LBM_BC_INFLOW, LBM_BC_INFLOW},
+                        0.05, 2500.0, 0.0, 0.0, 0, 0.25, LBM_FP32, 1, 1.0, {{0}}};
+  lbm_tree_desc td = {4, 3, 64.0, 19.2, 0.02, {0.6, 0.6, 0.6}, {0.6, 0.6, 0.6}, {35.0, 35.0, 35.0}, {0.0},
+                      1, 1, 64.0};
+  lbm_domain* d;
+  if (lbm_create_domain(&dd, NULL, &d) || lbm_set_geometry(d, &td)) {
+    printf("error %s\n", lbm_last_error());
+    return 1;
+  }
+  size_t bytes;
+  double H, A, nu;
+  int ns;
+  lbm_memory_requirements(d, &bytes);
+  lbm_geometry_info(d, &H, &A, &ns, &nu);
+  printf("%zu %.17g %.17g %d %.17g\n", bytes, H, A, ns, nu);
+  lbm_destroy(d);
+  return 0;
+}
+"""
+
+
+def test_header_compiles_as_c_and_a_c_caller_matches_the_binding(tmp_path):
+    """include/lbm.h is plain C (C11, warnings as errors), and a C caller that
+    fills the descriptors by position builds the two-level benchmark tree's
+    geometry exactly as the Python binding's ctypes structures do: the
+    struct layouts on both sides of the boundary agree."""
+    import subprocess
+    from paper_2603_27954_gb300 import lbm as L
+    from paper_2603_27954_gb300 import workloads as W
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(L.LIB_PATH)
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-L", libdir, "-llbm", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    c = W.CASES["amr2"]
+    h = L.lbm_create_domain(L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"],
+                                          u_in=c["u_in"], re_h=c["re_h"]))
+    L.lbm_set_geometry(h, L.tree_desc(**c["tree"]))
+    g = L.lbm_geometry_info(h)
+    assert int(out[0]) == L.lbm_memory_requirements(h)
+    assert float(out[1]) == g["H"] and float(out[2]) == g["A_x"] and float(out[4]) == g["nu_finest"]
+    assert int(out[3]) == g["n_segments"] == 40
+    L.lbm_destroy(h)
