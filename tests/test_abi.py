@@ -82,3 +82,53 @@ def test_header_compiles_as_c_and_a_c_caller_matches_the_binding(tmp_path):
     assert float(out[1]) == g["H"] and float(out[2]) == g["A_x"] and float(out[4]) == g["nu_finest"]
     assert int(out[3]) == g["n_segments"] == 40
     L.lbm_destroy(h)
+
+
+LAYOUT_PROBE = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "lbm.h"
+#define F(T, m) printf(#T " " #m " %zu\n", offsetof(T, m))
+int main(void) {
+  printf("lbm_domain_desc size %zu\n", sizeof(lbm_domain_desc));
+  F(lbm_domain_desc, nx); F(lbm_domain_desc, ny); F(lbm_domain_desc, nz); F(lbm_domain_desc, levels);
+  F(lbm_domain_desc, block); F(lbm_domain_desc, bc); F(lbm_domain_desc, u_in); F(lbm_domain_desc, re_h);
+  F(lbm_domain_desc, nu_finest); F(lbm_domain_desc, i_u); F(lbm_domain_desc, seed);
+  F(lbm_domain_desc, refine_margin); F(lbm_domain_desc, precision); F(lbm_domain_desc, galilean);
+  F(lbm_domain_desc, omega2); F(lbm_domain_desc, boxes);
+  printf("lbm_tree_desc size %zu\n", sizeof(lbm_tree_desc));
+  F(lbm_tree_desc, n); F(lbm_tree_desc, children); F(lbm_tree_desc, s0); F(lbm_tree_desc, w0);
+  F(lbm_tree_desc, min_len); F(lbm_tree_desc, r); F(lbm_tree_desc, dfac); F(lbm_tree_desc, alpha_deg);
+  F(lbm_tree_desc, phi_deg); F(lbm_tree_desc, azimuth_mode); F(lbm_tree_desc, seed);
+  F(lbm_tree_desc, trunk_cells);
+  printf("lbm_schedule size %zu\n", sizeof(lbm_schedule));
+  F(lbm_schedule, ctas_per_sm); F(lbm_schedule, odd_variant); F(lbm_schedule, even_variant);
+  F(lbm_schedule, z_split_even); F(lbm_schedule, z_split_odd);
+  return 0;
+}
+"""
+
+
+def test_descriptor_layouts_match_the_binding(tmp_path):
+    """Every field offset and the size of the three descriptor structs, as a
+    C compiler lays them out from include/lbm.h, equal those of the Python
+    binding's ctypes structures."""
+    import subprocess
+    from paper_2603_27954_gb300 import lbm as L
+    src = tmp_path / "layout.c"
+    src.write_text(LAYOUT_PROBE)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    types = {"lbm_domain_desc": L.DomainDesc, "lbm_tree_desc": L.TreeDesc, "lbm_schedule": L.Schedule}
+    seen = 0
+    for line in lines:
+        name, field, value = line.split()
+        py = types[name]
+        if field == "size":
+            assert C.sizeof(py) == int(value), name
+        else:
+            assert getattr(py, field).offset == int(value), (name, field)
+        seen += 1
+    assert seen == 3 + 16 + 12 + 5
