@@ -132,3 +132,39 @@ def test_descriptor_layouts_match_the_binding(tmp_path):
             assert getattr(py, field).offset == int(value), (name, field)
         seen += 1
     assert seen == 3 + 16 + 12 + 5
+
+
+def _prototypes():
+    """name -> list of parameter declarations, from include/*.h (comments stripped)."""
+    out = {}
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(lbm_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src):
+            params = [p.strip() for p in m.group(2).split(",")]
+            out[m.group(1)] = [] if params == ["void"] or params == [""] else params
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """For every function the Python binding declares, its ctypes argument
+    list has the header's arity, and each argument is a pointer exactly where
+    the header's parameter is a pointer or an array."""
+    from paper_2603_27954_gb300 import lbm as L
+    lib = L._lib
+    protos = _prototypes()
+    pointerish = (C.c_void_p, C.c_char_p)
+    checked = 0
+    for name, params in protos.items():
+        fn = getattr(lib, name, None)
+        if fn is None or fn.argtypes is None:
+            continue
+        assert len(fn.argtypes) == len(params), (name, params, fn.argtypes)
+        for p, t in zip(params, fn.argtypes):
+            is_ptr = "*" in p or "[" in p
+            py_ptr = t in pointerish or issubclass(t, C._Pointer)
+            assert is_ptr == py_ptr, (name, p, t)
+        checked += 1
+    assert checked >= 60
