@@ -106,6 +106,10 @@ static void central_moments(const double* f, double rho, const double u[3], doub
   }
 }
 
+/* cumulants from central moments by the set-partition formula of joint
+   cumulants (the definition behind Geier et al. 2015's cumulants): k_t is
+   the sum over partitions of the multiset of t into blocks of size >= 2 of
+   (-1)^(b-1) (b-1)! times the product of the blocks' central moments */
 static void cum_from_mom(const double* m, double* k) {
   for (int t = 0; t < 27; ++t) {
     double s = 0;
@@ -119,6 +123,8 @@ static void cum_from_mom(const double* m, double* k) {
   }
 }
 
+/* the inverse: central moments as the sum over the same partitions of the
+   product of the blocks' cumulants */
 static void mom_from_cum(const double* k, double* m) {
   for (int t = 0; t < 27; ++t) {
     double s = 0;
@@ -132,6 +138,9 @@ static void mom_from_cum(const double* k, double* m) {
   }
 }
 
+/* cumulants of one cell's populations (Sec. 2.2 names the cumulant LBM of
+   Geier et al. 2015): rho, the mean velocity, then the cumulants of orders
+   2 to 6 from the central moments */
 void orc_cumulants(const double* f, double* k) {
   orc_init();
   double rho = 0, j[3] = {0, 0, 0};

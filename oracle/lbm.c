@@ -90,6 +90,10 @@ static int in_real(const lev* v, int x, int y, int z) {
 }
 static int wrapi(int a, int n) { a %= n; return a < 0 ? a + n : a; }
 
+/* cell types of every level of the refinement hierarchy (Sec. 2.2's octree
+   refinement, boxes per reading 12): fluid, covered by the next finer level,
+   or virtual (the margin around a finer level's box), and the ring of coarse
+   cells next to a finer box that receive its coalesced populations */
 static void classify_levels(orc_sim* s) {
   for (int l = 0; l < s->L; ++l) {
     lev* v = &s->lv[l];
@@ -227,6 +231,11 @@ static long level0_cell(const orc_sim* s, int x, int y, int z) {
   return lidx(v, g[0], g[1], g[2]);
 }
 
+/* solid cells (cell centre inside a primitive, inclusive) and the cut links
+   of Sec. 2.2's interpolated bounce-back: for every fluid cell and direction
+   c_i reaching a solid cell, the wall fraction q (first entry of the ray,
+   clamped to [1e-6, 1]), the second fluid node x_f - c_i and the branch the
+   link belongs to (reading 17) */
 int orc_set_prims(orc_sim* s, const orc_prim* pr, int np) {
   int L = s->L;
   classify_levels(s); /* fresh cell types and ring flags */
@@ -324,6 +333,9 @@ static double inflow_value(const orc_sim* s, const int g[3], int i) {
   return feq[i];
 }
 
+/* Sec. 2.3's domain faces: the value a level-0 cell pulls from position g,
+   inside or outside the domain (inflow face, lateral inflow or slip faces,
+   zero-gradient outflow; periodic axes wrap) */
 static double pull0(const orc_sim* s, const double* A, int gx, int gy, int gz, int i) {
   const lev* v = &s->lv[0];
   int g[3] = {gx, gy, gz};
@@ -344,6 +356,8 @@ static double pull0(const orc_sim* s, const double* A, int gx, int gy, int gz, i
   return A[27 * lidx(v, g[0], g[1], g[2]) + j];
 }
 
+/* the cumulant collision (Sec. 2.2, Geier et al. 2015) of every fluid cell
+   of level l, in place, at the level's rates (omega1 from nu_l) */
 static void collide_level(orc_sim* s, int l) {
   lev* v = &s->lv[l];
   const double* F = (l == 0 && s->L == 1) ? s->d.force : NULL;
@@ -356,6 +370,11 @@ static void collide_level(orc_sim* s, int l) {
   }
 }
 
+/* streaming f_i(x, t+1) = f*_i(x - c_i, t) of level l into the second array
+   (Sec. 2.2), the faces of Sec. 2.3 on level 0, then the interpolated
+   bounce-back of every cut link (Bouzidi et al. 2001) with its
+   momentum-exchange force (Wen et al. 2014), and the coalesce transfer from
+   the next finer level into the ring cells */
 static void stream_level(orc_sim* s, int l) {
   lev* v = &s->lv[l];
   const double* A = v->A;
@@ -433,6 +452,9 @@ static void stream_level(orc_sim* s, int l) {
   v->B = (double*)A;
 }
 
+/* one step of level l with recursive sub-cycling (acoustic scaling): collide
+   level l, explode its post-collision populations into the next finer
+   level's virtual cells, advance that level twice, then stream level l */
 static void step_level(orc_sim* s, int l) {
   collide_level(s, l);
   if (l + 1 < s->L) {
