@@ -168,3 +168,41 @@ def test_binding_signatures_match_the_header():
             assert is_ptr == py_ptr, (name, p, t)
         checked += 1
     assert checked >= 60
+
+
+NULL_PROBE = r"""
+import ctypes as C
+import re
+import sys
+sys.path.insert(0, %r)
+from paper_2603_27954_gb300 import lbm as L
+src = re.sub(r"/\*.*?\*/", "", open(%r).read(), flags=re.S)
+void_fns = {"lbm_destroy", "lbm_batch_destroy", "lbm_mlp_destroy"}
+text_fns = {"lbm_status_string", "lbm_last_error", "lbm_mlp_last_error"}
+for name in sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src))):
+    if name in text_fns:
+        continue
+    fn = getattr(L._lib, name)
+    args = [None if (t in (C.c_void_p, C.c_char_p) or issubclass(t, C._Pointer)) else
+            (0.0 if t in (C.c_double, C.c_float) else 0) for t in fn.argtypes]
+    rc = fn(*args)
+    print(name, "void" if name in void_fns else rc)
+"""
+
+
+def test_every_entry_point_rejects_null_arguments(tmp_path):
+    """The error path of the boundary without a GPU: every declared function
+    called with null pointers and zero sizes returns a negative status
+    (LBM_EINVAL, or LBM_ESTATE where the call is out of order) and the
+    destroy functions accept a null handle; nothing crashes (run in a child
+    process, so that a crash is a test failure, not the end of the run)."""
+    import subprocess
+    import sys
+    code = NULL_PROBE % (ROOT, os.path.join(ROOT, "include", "lbm.h"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    seen = dict(line.split() for line in r.stdout.splitlines())
+    assert len(seen) >= 75
+    for name, rc in seen.items():
+        if rc != "void":
+            assert int(rc) in (-1, -5), (name, rc)
