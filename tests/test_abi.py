@@ -1,8 +1,12 @@
-"""The C-ABI library loads and exports every function include/lbm.h declares
-(no device calls)."""
+"""The C-ABI boundary without a GPU: the library loads and exports every
+function include/lbm.h declares, the header is plain C whose struct layouts
+and prototypes the Python binding mirrors, and the error paths (null
+arguments, calls out of order) return statuses instead of crashing."""
 import ctypes as C
 import os
 import re
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -206,3 +210,46 @@ def test_every_entry_point_rejects_null_arguments(tmp_path):
     for name, rc in seen.items():
         if rc != "void":
             assert int(rc) in (-1, -5), (name, rc)
+
+
+def test_device_calls_before_binding_are_out_of_order(tmp_path):
+    """With the geometry set but no device buffer bound, every call that needs
+    the device state returns LBM_ESTATE (no device work is attempted), and the
+    host-only queries succeed."""
+    import numpy as np
+    from paper_2603_27954_gb300 import lbm as L
+    from paper_2603_27954_gb300 import workloads as W
+    c = W.CASES["amr2_small"]
+    h = L.lbm_create_domain(L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"],
+                                          u_in=c["u_in"], re_h=c["re_h"]))
+    L.lbm_set_geometry(h, L.tree_desc(**c["tree"]))
+    nx, ny, nz = (L.lbm_level_info(h, 0)["hi"][a] - L.lbm_level_info(h, 0)["lo"][a] for a in range(3))
+    n = nx * ny * nz
+    acc = np.zeros(8)
+    calls = {
+        "lbm_step": lambda: L.lbm_step(h, 1),
+        "lbm_drag": lambda: L.lbm_drag(h),
+        "lbm_drag_enqueue": lambda: L._ck(L._lib.lbm_drag_enqueue(h, acc.ctypes.data), "lbm_drag_enqueue"),
+        "lbm_reset_force": lambda: L.lbm_reset_force(h),
+        "lbm_get_populations": lambda: L.lbm_get_populations(h, 0),
+        "lbm_get_populations_window": lambda: L.lbm_get_populations_window(h, 0, (0, 0, 0), (2, 2, 2)),
+        "lbm_mass": lambda: L.lbm_mass(h),
+        "lbm_mass_noalloc": lambda: L.lbm_mass_noalloc(h),
+        "lbm_level_mass": lambda: L.lbm_level_mass(h, 0),
+        "lbm_interface_ledger": lambda: L.lbm_interface_ledger(h, 0),
+        "lbm_init_uniform": lambda: L.lbm_init_uniform(h, 1.0, (0.05, 0.0, 0.0)),
+        "lbm_init_field": lambda: L.lbm_init_field(h, 0, np.ones(n), np.zeros((n, 3))),
+        "lbm_get_branch_forces": lambda: L.lbm_get_branch_forces(h, 64),
+        "lbm_friction": lambda: L.lbm_friction(h),
+        "lbm_save": lambda: L.lbm_save(h, str(tmp_path / "state.bin")),
+        "lbm_load": lambda: L.lbm_load(h, str(tmp_path / "state.bin")),
+        "lbm_autotune": lambda: L.lbm_autotune(h, 1),
+    }
+    for name, call in calls.items():
+        with pytest.raises(L.LbmError) as e:
+            call()
+        assert e.value.code == L.LBM_ESTATE, (name, str(e.value))
+    assert L.lbm_memory_requirements(h) > 0
+    assert L.lbm_geometry_info(h)["n_segments"] == 13
+    assert L.lbm_work_per_step(h)[0] > 0
+    L.lbm_destroy(h)
