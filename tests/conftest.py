@@ -2,8 +2,10 @@ import os
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-if ROOT not in sys.path:
-    sys.path.insert(0, ROOT)
+HERE = os.path.dirname(os.path.abspath(__file__))
+for p in (ROOT, HERE):  # the package and oracle; the tests' own helper modules
+    if p not in sys.path:
+        sys.path.insert(0, p)
 
 
 def pytest_configure(config):
