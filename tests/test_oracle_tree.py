@@ -219,3 +219,23 @@ def test_cut_links_belong_to_the_branch_their_ray_enters_first(case):
         tied = np.flatnonzero(ent <= tmin + 1e-9)
         assert segs[k] in tied, (k, segs[k], ent)
         assert q[k] == pytest.approx(max(tmin, 1e-6), abs=1e-9)
+
+
+@pytest.mark.parametrize("theta_deg", [90.0, 60.0, 35.0])
+def test_frontal_area_counts_overlapping_branches_once(theta_deg):
+    """A_x is the area of the union of the projected cylinders (Eq. 7's
+    frontal area; overlaps counted once): two long cross-flow cylinders in
+    the y-z plane crossing at angle theta project to two strips of width D
+    whose overlap is a rhombus of area D^2 / sin(theta), so
+    A_x = 2 L D - D^2 / sin(theta) (the flat caps project to nothing)."""
+    th = math.radians(theta_deg)
+    L, D = 40.0, 3.0
+    c = np.array([20.0, 50.0, 50.0])
+    a1 = np.array([0.0, 0.0, 1.0])
+    a2 = np.array([0.0, math.sin(th), math.cos(th)])
+    seg = np.array([list(c - 0.5 * L * a1) + list(c + 0.5 * L * a1) + [D, 0.0],
+                    list(c - 0.5 * L * a2) + list(c + 0.5 * L * a2) + [D, 1.0]])
+    exact = 2 * L * D - D * D / math.sin(th)
+    assert O.frontal_area(seg, 1.0 / 32) == pytest.approx(exact, rel=2e-3)
+    # each alone is L x D; the union is less than their sum by the rhombus
+    assert O.frontal_area(seg[:1], 1.0 / 32) == pytest.approx(L * D, rel=1e-3)
