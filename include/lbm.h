@@ -328,7 +328,7 @@ int lbm_set_branch_forces(lbm_domain* d, int on);
 int lbm_get_branch_forces(lbm_domain* d, double* mean_xyz, int n, long long* steps);
 
 /* Branch-wise description of the tree for the analytical model (Sec. 2.4,
-   Eq. 3: F_d = C_d (1/2 rho U^2) L D sin^3(alpha)) and its learned sectional
+   Eq. 2: F_d = C_d (1/2 rho U^2) L D sin^3(alpha)) and its learned sectional
    drag: one row of LBM_BRANCH_COLS doubles per branch, in lbm_get_segments
    order:
      0 log10 Re_d (U D / nu, finest level)   1 generation   2 D/H
@@ -347,7 +347,7 @@ int lbm_get_branch_forces(lbm_domain* d, double* mean_xyz, int n, long long* ste
 #define LBM_BRANCH_COLS 11
 int lbm_branch_table(const lbm_domain* d, double* rows, int n, int* count);
 
-/* Branch-wise drag estimate (Sec. 2.4, Eq. 3 summed as in Eq. 5): with
+/* Branch-wise drag estimate (Sec. 2.4, Eq. 2 summed as in Eq. 4): with
    c_k = F_d,k / (rho U^2 L_k D_k / 2) the sectional drag coefficient of
    branch k, C_D-est = sum_k c_k L_k D_k / A_x.  rows: n rows of
    lbm_branch_table (host, LBM_BRANCH_COLS doubles each); c_sect: host array of n c_k, or
@@ -360,12 +360,12 @@ int lbm_branch_table(const lbm_domain* d, double* rows, int n, int* count);
 int lbm_branch_drag_estimate(const double* rows, int n, const double* c_sect, double area, double* cd_est,
                              double* c_out);
 
-/* The measured sectional coefficients of Eq. 3 (Sec. 2.4), rho = 1:
+/* The measured sectional coefficients of Eqs. 2 and 3 (Sec. 2.4), rho = 1:
    c_drag[k] = mean F_x,k / (U^2 L_k D_k / 2) from the per-branch forces
    averaged since the last lbm_reset_force (lbm_set_branch_forces must be on),
    c_fric[k] the same from the per-branch friction means
    (lbm_set_friction_mean; zeros while it is off); *cd = mean F_x /
-   (U^2 A_x / 2) over the same window (Eq. 7), *cf the friction's (NaN while
+   (U^2 A_x / 2) over the same window (Eq. 7), *cf the friction's (Eq. 8; NaN while
    the friction mean is off).  Any pointer may be NULL; n is the capacity
    in branches.  Host arithmetic after reading the device sums; synchronises. */
 int lbm_branch_coefficients(lbm_domain* d, double* c_drag, double* c_fric, int n, double* cd, double* cf);
@@ -397,7 +397,7 @@ int lbm_set_friction_mean(lbm_domain* d, int on);
 int lbm_get_friction_mean(lbm_domain* d, double mean[3], double* per_branch, int n, long long* steps);
 int lbm_friction_samples(const lbm_domain* d, double* rows, int n, int* count);
 
-/* ---- Sectional-drag surrogate (a learned C_d for Eq. 3, Sec. 2.4) ----
+/* ---- Sectional-drag surrogate (a learned C_d for Eq. 2, Sec. 2.4) ----
    A fully connected network: n_in inputs, `hidden` layers of `width` GELU
    units, one output; BF16 weights with FP32 accumulation in its forward and
    backward kernels, FP32 master weights and Adam (beta 0.9 / 0.999, eps 1e-8)
@@ -437,7 +437,7 @@ int lbm_mlp_train_step(lbm_mlp* m, const float* x, const float* y, const int* id
 const char* lbm_mlp_last_error(void);
 void lbm_mlp_destroy(lbm_mlp* m);
 
-/* Turbulent inflow (domains with i_u > 0; Sec. 4.3 defines I_u = u'_rms / U).
+/* Turbulent inflow (domains with i_u > 0; Sec. 4.2 defines I_u = u'_rms / U).
    Every inflow-equilibrium value pulled from outside level 0 is the
    equilibrium at rho = 1 and u = U e_x + u'(p - U t e_x) at the centre p of
    the cell it is pulled from, t the coarse steps done: a frozen synthetic

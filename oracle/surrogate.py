@@ -5,8 +5,8 @@ baseline of the benchmark, never by the product path.
 
 Branch-wise model (Sec. 2.4): every branch is a cylinder of length L and
 diameter D whose axis makes the angle alpha with the free stream; its drag is
-F_d = C_d (rho U^2 / 2) L D sin^3(alpha) (Eq. 3) and the tree estimate is
-C_D-est = sum_k F_d,k / (rho U^2 A_x / 2) (Eq. 5), A_x the frontal area.  The
+F_d = C_d (rho U^2 / 2) L D sin^3(alpha) (Eq. 2) and the tree estimate is
+C_D-est = sum_k F_d,k / (rho U^2 A_x / 2) (Eq. 4), A_x the frontal area.  The
 local Reynolds number of a branch is U D / nu.  The paper fits C_d(Re) to
 cylinder measurements that are not available here; `cylinder_cd_white` is
 the textbook fit C_d = 1 + 10 Re^(-2/3) (F. M. White, Fluid Mechanics, the
@@ -50,14 +50,14 @@ def branch_geometry(seg):
 
 
 def branch_forces_model(seg, u, nu, cd_of_re, rho=1.0):
-    """Eq. 3 for every branch: F_d,k = C_d(Re_k) (rho u^2 / 2) L_k D_k sin^3 alpha_k."""
+    """Eq. 2 for every branch: F_d,k = C_d(Re_k) (rho u^2 / 2) L_k D_k sin^3 alpha_k."""
     L, D, cosa = branch_geometry(seg)
     sin3 = np.sqrt(np.maximum(0.0, 1.0 - cosa * cosa)) ** 3
     return cd_of_re(u * D / nu) * 0.5 * rho * u * u * L * D * sin3
 
 
 def tree_cd_estimate(forces, u, area, rho=1.0):
-    """Eq. 5: C_D-est = sum_k F_d,k / (rho u^2 A_x / 2)."""
+    """Eq. 4: C_D-est = sum_k F_d,k / (rho u^2 A_x / 2)."""
     return float(np.sum(forces)) / (0.5 * rho * u * u * area)
 
 

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY: imported by tests, the smoke check and the CPU
 baseline of the benchmark, never by the product path.
 
-Sec. 4.3 defines the inflow turbulence intensity I_u = u'_rms / U; the paper
+Sec. 4.2 defines the inflow turbulence intensity I_u = u'_rms / U; the paper
 uses it only in its analytical model.  The LBM inflow here is a random-
 Fourier-mode field (Kraichnan 1970; Smirnov, Shi & Celik 2001):
 

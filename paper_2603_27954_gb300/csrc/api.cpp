@@ -1671,7 +1671,7 @@ int lbm_branch_coefficients(lbm_domain* d, double* c_drag, double* c_fric, int n
   if (d->friction_mean && (rc = lbm_get_friction_mean(d, fmean, fr.data(), nb, &fsteps))) return rc;
   double mean[3];
   if ((rc = lbm_drag(d, nullptr, mean, nullptr))) return rc;
-  // Eq. (3): F_d,k = c_k (rho U^2 / 2) L_k D_k, rho = 1; segment rows hold L and D
+  // Eq. (2): F_d,k = c_k (rho U^2 / 2) L_k D_k, rho = 1; segment rows hold L and D
   for (int k = 0; k < nb; ++k) {
     const double* sg = &d->tree.seg[8 * (size_t)k];
     const double len = std::sqrt((sg[3] - sg[0]) * (sg[3] - sg[0]) + (sg[4] - sg[1]) * (sg[4] - sg[1]) +
@@ -1680,7 +1680,7 @@ int lbm_branch_coefficients(lbm_domain* d, double* c_drag, double* c_fric, int n
     if (c_drag) c_drag[k] = steps > 0 ? fb[3 * (size_t)k] / ld : 0.0;
     if (c_fric) c_fric[k] = fsteps > 0 ? fr[3 * (size_t)k] / ld : 0.0;
   }
-  // Eq. (7) over the same window: C_D = F_x / (rho U^2 A_x / 2), and C_F likewise
+  // Eqs. (7), (8) over the same window: C_D = F_x / (rho U^2 A_x / 2), and C_F likewise
   if (cd) *cd = d->A_x > 0 ? mean[0] / (q * d->A_x) : std::numeric_limits<double>::quiet_NaN();
   if (cf) *cf = d->A_x > 0 && fsteps > 0 ? fmean[0] / (q * d->A_x) : std::numeric_limits<double>::quiet_NaN();
   return LBM_OK;

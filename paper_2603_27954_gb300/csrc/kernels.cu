@@ -1,13 +1,18 @@
 // GB300 (sm_103a) kernels of the cumulant LBM step.
 //
 //  k_collide   fused collision + streaming, in-place AA pattern, one CTA per
-//              active block, one thread per (x, y) column walking z.
-//  k_faces     domain faces of level 0 (inflow, zero-gradient outflow, slip).
+//              active block, one thread per (x, y) column walking z (Sec. 2.2:
+//              the cumulant LBM of Geier et al. 2015).
+//  k_faces     domain faces of level 0 (Sec. 2.3: inflow, zero-gradient
+//              outflow; slip or inflow lateral faces).
 //  k_walls     Bouzidi linear bounce-back on cut links fused with the
-//              momentum-exchange force: float-float warp sums, FP64 CTA
-//              partials, and the fixed-order FP64 total by the last CTA
+//              momentum-exchange force (Sec. 2.2: interpolated bounce-back,
+//              Wen et al. 2014; C_D by Eq. 7): float-float warp sums, FP64
+//              CTA partials, and the fixed-order FP64 total by the last CTA
 //              (deterministic).
-//  k_explode (with the inflow entries) / k_coalesce   refinement-interface transfer.
+//  k_explode (with the inflow entries) / k_coalesce   refinement-interface
+//              transfer of Sec. 2.2's octree refinement (volumetric explode and
+//              coalesce, with the FP64 interface ledger).
 //  k_fill      equilibrium initialisation; k_mass FP64 mass / momentum.
 //
 // The step is a bandwidth-bound stencil: every population is read once and

@@ -1,6 +1,7 @@
 // Sectional-drag surrogate: a small MLP (inputs of the branch-wise model,
-// hidden layers of GELU units, one output) trained and evaluated by these
-// kernels.  Weights are used in BF16 with FP32 accumulation; FP32 master
+// hidden layers of GELU units, one output: the sectional drag coefficient
+// C_d of Eq. 2, summed over the branches by Eq. 4, Sec. 2.4) trained and
+// evaluated by these kernels.  Weights are used in BF16 with FP32 accumulation; FP32 master
 // weights and Adam moments are kept beside them.  Every reduction (weight
 // gradients, bias gradients, loss) runs in a fixed order, so training is
 // deterministic.

@@ -1,8 +1,8 @@
 // Synthetic turbulent inflow: a random-Fourier-mode velocity field (Kraichnan
 // 1970; Smirnov, Shi & Celik 2001) with a von Karman energy spectrum, frozen
 // and carried through the inflow plane at the mean speed (Taylor's
-// hypothesis).  The paper uses the inflow turbulence intensity I_u only in
-// its analytical model; this field lets the LBM see the same intensity.
+// hypothesis).  The paper uses the inflow turbulence intensity I_u (Sec. 4.2)
+// only in its analytical model; this field lets the LBM see the same intensity.
 //
 //   u'(x) = sum_n a_n cos(k_n . x + psi_n),  a_n = 2 u_n sigma_n,  sigma_n . k_n = 0
 //

@@ -465,7 +465,7 @@ def lbm_get_branch_forces(h, n_branches):
 
 
 def lbm_branch_drag_estimate(rows, area, c_sect=None):
-    """Eq. 5 over the branches of a branch table; returns (C_D-est, c_k)."""
+    """Eq. 4 over the branches of a branch table; returns (C_D-est, c_k)."""
     rows = np.ascontiguousarray(rows, dtype=np.float64)
     n = rows.shape[0]
     c_out = np.zeros(max(1, n))
@@ -477,7 +477,7 @@ def lbm_branch_drag_estimate(rows, area, c_sect=None):
 
 
 def lbm_branch_coefficients(h, n_branches):
-    """Eq. 3's measured sectional coefficients: (c_drag, c_fric, C_D, C_F) over the averaging window."""
+    """Eq. 2's measured sectional coefficients: (c_drag, c_fric, C_D, C_F) over the averaging window."""
     cd_, cf_ = np.zeros(max(1, n_branches)), np.zeros(max(1, n_branches))
     cd, cf = C.c_double(), C.c_double()
     _ck(_lib.lbm_branch_coefficients(h, _dp(cd_), _dp(cf_), n_branches, C.byref(cd), C.byref(cf)),

@@ -1,19 +1,19 @@
 """Learned sectional drag for the branch-wise model (Sec. 2.4).
 
-The paper estimates a tree's drag by summing Eq. 3 over its branches with a
-cylinder law C_d(Re) fitted to measurements (Eq. 5).  Here the per-branch
+The paper estimates a tree's drag by summing Eq. 2 over its branches with a
+cylinder law C_d(Re) fitted to measurements (Eq. 4).  Here the per-branch
 law is learned from the LBM itself: every simulated tree yields, per branch,
 the features of lbm_branch_table and the measured sectional coefficient
 c_k = F_x,k / (rho U^2 L_k D_k / 2) (lbm_branch_coefficients, from the
 time-averaged per-branch momentum-exchange forces).  A network trained by the
 library's BF16/FP32 kernels predicts c_k, an ensemble of such networks is
-averaged on the device (lbm_mlp_ensemble_forward), and Eq. 5 turns the
+averaged on the device (lbm_mlp_ensemble_forward), and Eq. 4 turns the
 predictions into C_D-est (lbm_branch_drag_estimate).  The LBM stays the reference:
 held-out (geometry, Re_H) points are simulated and their C_D compared with
 the estimate.
 
 Everything numeric runs in liblbm (simulation, feature table, coefficients,
-network kernels, Eq. 5); this module only sequences the calls and stacks
+network kernels, Eq. 4); this module only sequences the calls and stacks
 arrays.
 """
 import time
@@ -94,7 +94,7 @@ def simulate(cases, stream=None, group=8, protocol=None):
 
 
 def sample_weights(samples):
-    """Per branch, its share of Eq. 5's sum: L_k D_k over its tree's frontal
+    """Per branch, its share of Eq. 4's sum: L_k D_k over its tree's frontal
     area, normalised over all branches (training by these weights fits c_k
     where it moves C_D-est, rather than where branches are numerous)."""
     w = np.concatenate([s.rows[:, 6] * s.rows[:, 7] / s.area for s in samples]).astype(np.float64)
@@ -163,7 +163,7 @@ def predict(nets, rows, features=FEATURES):
 
 
 def estimate(rows, area, c=None):
-    """Eq. 5: C_D-est from sectional coefficients c (None: the cylinder law)."""
+    """Eq. 4: C_D-est from sectional coefficients c (None: the cylinder law)."""
     return L.lbm_branch_drag_estimate(rows, area, c)[0]
 
 
@@ -181,10 +181,10 @@ def learned_form(stream=None, counts=None, members=4, train_steps=20000, group=8
                  log=None, weighting="none", data=None):
     """The learned form end to end: LBM data from trees of the three families,
     named-input and chosen-input ensembles trained by the library's kernels,
-    and their Eq. 5 estimates judged against the LBM at the held-out points;
+    and their Eq. 4 estimates judged against the LBM at the held-out points;
     also C_D-est of one held-out tree from Re_H = 2.5e3 to 1e9.  Returns a
     report (dict) and the trained ensembles.  weighting "area" trains with
-    each branch weighted by its share of Eq. 5 (sample_weights).  `data`: a
+    each branch weighted by its share of Eq. 4 (sample_weights).  `data`: a
     file the simulated samples are written to, or read from when it exists
     (the same counts and seed)."""
     import os
@@ -279,7 +279,7 @@ if __name__ == "__main__":
     ap.add_argument("--train-steps", type=int, default=20000)
     ap.add_argument("--out", default=None, help="also write the report to this file")
     ap.add_argument("--weighting", default="none", choices=["none", "area"],
-                    help="area: train with each branch weighted by its share of Eq. 5")
+                    help="area: train with each branch weighted by its share of Eq. 4")
     ap.add_argument("--data", default=None, help="write the simulated samples here, or read them if it exists")
     args = ap.parse_args()
     import torch

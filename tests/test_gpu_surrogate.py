@@ -190,8 +190,8 @@ def test_mlp_ensemble_forward_is_the_members_mean(L):
 
 
 def test_branch_coefficients_partition_the_drag(L, stream):
-    """Eq. 3's measured coefficients: c_k (U^2 / 2) L_k D_k are the mean branch
-    forces, and their Eq. 5 sum over the frontal area is the C_D of the same
+    """Eq. 2's measured coefficients: c_k (U^2 / 2) L_k D_k are the mean branch
+    forces, and their Eq. 4 sum over the frontal area is the C_D of the same
     window (the branch forces partition the total)."""
     c = W.CASES["amr2_small"]
     desc = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],

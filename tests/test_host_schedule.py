@@ -151,7 +151,7 @@ def test_overlap_features_mask():
 
 
 def test_learned_form_branch_weights():
-    """Each branch's training weight is its share of Eq. 5's sum, L_k D_k /
+    """Each branch's training weight is its share of Eq. 4's sum, L_k D_k /
     A_x of its own tree, normalised over all branches."""
     from paper_2603_27954_gb300 import surrogate as SG
     rows = np.zeros((3, 12))

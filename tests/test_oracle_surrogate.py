@@ -1,5 +1,5 @@
 """Pins for the branch-wise model and network oracle (no GPU): closed forms of
-Eq. 3 and Eq. 5 for single cylinders, the cylinder-law value at Re = 1000,
+Eq. 2 and Eq. 4 for single cylinders, the cylinder-law value at Re = 1000,
 bfloat16 rounding against torch's conversion and hand-worked ties, GELU
 identities, backpropagation against central finite differences, Adam's
 closed form for a constant gradient, and the library's branch feature table
@@ -195,7 +195,7 @@ def test_oracle_branch_forces_partition_the_total_force():
 
 @pytest.mark.parametrize("case", ["tiny", "amr2"])
 def test_library_branch_estimate_matches_oracle(case):
-    """Eq. 5 with the cylinder law, and with given sectional coefficients."""
+    """Eq. 4 with the cylinder law, and with given sectional coefficients."""
     c = W.CASES[case]
     d = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
                       re_h=c["re_h"])
