@@ -2,9 +2,13 @@
 
 Closed forms: Taylor-Green decay exp(-2 nu k^2 t), the Poiseuille parabola
 (with second-order convergence of the interpolated bounce-back for several
-wall fractions q).  Invariants: the momentum-exchange balance per step, mass
-and momentum conservation across a refinement interface, uniform flow left
-unchanged by the face conditions and by the interface.
+wall fractions q), Lamb's low-Re cylinder drag.  Invariants: the
+momentum-exchange balance per step, mass and momentum conservation across a
+refinement interface, uniform flow left unchanged by the face conditions and
+by the interface.  Exact special cases: the outflow and inflow faces cell by
+cell, slip walls as mirror planes, the refined levels as an exact shift when
+every rate is zero, simple bounce-back where a link has no second fluid node,
+and one coarse step as 2^l one-cell updates per level.
 """
 import numpy as np
 import pytest
