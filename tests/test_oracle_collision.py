@@ -6,7 +6,9 @@
 * the equilibrium against its defining moments;
 * textbook special cases of the collision: all rates one gives the
   factorised equilibrium, all rates zero gives the identity, the rest state
-  is a fixed point, mass and momentum are conserved.
+  is a fixed point, mass and momentum are conserved;
+* with ten distinct rates, every cumulant group (measured by the brute-force
+  expansion) relaxes by its own rate.
 """
 from fractions import Fraction
 from itertools import product

@@ -1,8 +1,9 @@
 """Pins of the oracle's tree and geometry (Sec. 2.1 Eq. 1, Tables 1-2; Sec. 2.3).
 
 Each test checks the oracle against something other than itself: values the
-paper prints, closed-form areas and ray intersections, or a published test
-vector.
+paper prints, closed-form areas (single, tilted and crossing cylinders) and
+ray intersections, a published test vector, or a brute-force entry search
+along each cut link's ray (the branch it belongs to and its wall fraction).
 """
 import ctypes as C
 import math

@@ -1,8 +1,9 @@
 """Pins for the synthetic turbulent inflow (no GPU): every mode is
 divergence-free, the amplitudes carry exactly (3/2) (I_u U)^2, the sampled
 field has zero mean, the stream-wise variance its modes predict and zero
-numerical divergence, the von Karman shape peaks at sqrt(12/5) kappa_e, and
-the library's mode table (host code) equals the oracle's restatement."""
+numerical divergence, the von Karman shape peaks at sqrt(12/5) kappa_e, the
+library's mode table (host code) equals the oracle's restatement, and the
+inflow face pulls the equilibrium of the frozen field exactly."""
 import math
 
 import numpy as np
