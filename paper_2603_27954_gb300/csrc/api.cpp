@@ -1561,10 +1561,24 @@ int lbm_get_cell_types(const lbm_domain* d, int level, unsigned char* out, size_
   if (!out || !valid_level(d, level)) return fail(LBM_EINVAL, "bad argument");
   const Level& v = d->mesh.lv[level];
   if ((long long)n != box_cells(v)) return fail(LBM_EINVAL, "cell count does not match the level's box");
+  // blocks without storage hold no fluid cell: inside the next finer level's
+  // box they are covered by it, elsewhere (the finest level) solid
+  const Level* fine = level + 1 < d->mesh.L ? &d->mesh.lv[level + 1] : nullptr;
+  auto under_fine = [&](int x, int y, int z) {
+    if (!fine) return false;
+    const int c[3] = {x, y, z};
+    for (int a = 0; a < 3; ++a)
+      if (2 * c[a] < fine->rlo[a] || 2 * c[a] + 1 >= fine->rhi[a]) return false;
+    return true;
+  };
   size_t k = 0;
   for (int z = v.rlo[2]; z < v.rhi[2]; ++z)
     for (int y = v.rlo[1]; y < v.rhi[1]; ++y)
-      for (int x = v.rlo[0]; x < v.rhi[0]; ++x, ++k) out[k] = (unsigned char)v.cell_type(x, y, z);
+      for (int x = v.rlo[0]; x < v.rhi[0]; ++x, ++k) {
+        CellType t = v.cell_type(x, y, z);
+        if (t == OUTSIDE) t = under_fine(x, y, z) ? COVERED : SOLID;
+        out[k] = (unsigned char)t;
+      }
   return LBM_OK;
 } catch (...) {
   return exception_status();

@@ -61,7 +61,7 @@ def test_geometry_scalars_match_oracle(case):
     L.lbm_destroy(h)
 
 
-@pytest.mark.parametrize("case", ["tiny", "amr2_small"])
+@pytest.mark.parametrize("case", ["tiny", "amr2_small", "amr3_small", "amr4_quarter"])
 def test_cell_types_and_links_match_oracle(case):
     h = lib_domain(case)
     sim, info = oracle_case(case)
@@ -77,7 +77,9 @@ def test_cell_types_and_links_match_oracle(case):
         k2 = np.lexsort((d2, c2))
         np.testing.assert_array_equal(c1[k1], c2[k2])
         np.testing.assert_array_equal(d1[k1], d2[k2])
-        np.testing.assert_allclose(q1[k1], q2[k2], rtol=0, atol=1e-12)
+        # two independent FP64 ray-cylinder computations: they agree to a few
+        # 1e-12 at finest coordinates of several hundred cells
+        np.testing.assert_allclose(q1[k1], q2[k2], rtol=0, atol=1e-11)
         total_links += len(q1)
         if len(q1):
             assert (q1 > 0).all() and (q1 <= 1).all()
