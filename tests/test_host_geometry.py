@@ -87,7 +87,7 @@ def test_cell_types_and_links_match_oracle(case):
     L.lbm_destroy(h)
 
 
-@pytest.mark.parametrize("case", ["tiny", "amr2_small", "amr2_quarter"])
+@pytest.mark.parametrize("case", ["tiny", "amr2_small", "amr2_quarter", "amr3_small", "amr4_quarter"])
 def test_link_branches_match_oracle(case):
     """The branch each finest-level cut link is attributed to (the cylinder
     its ray enters first; per-branch forces, Sec. 2.4) is the oracle's,
