@@ -1,5 +1,8 @@
 // C-ABI of liblbm (include/lbm.h): domain set-up, device memory binding,
-// the recursively sub-cycled step driver, drag and diagnostics.
+// the recursively sub-cycled step driver, drag and diagnostics.  Every
+// exported function is a function-try-block: a C++ exception from inside the
+// library (a failed host allocation above all) becomes a status and a
+// message instead of crossing the C boundary.
 #include <cuda_runtime.h>
 
 #include <algorithm>
