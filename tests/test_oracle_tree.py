@@ -240,3 +240,36 @@ def test_frontal_area_counts_overlapping_branches_once(theta_deg):
     assert O.frontal_area(seg, 1.0 / 32) == pytest.approx(exact, rel=2e-3)
     # each alone is L x D; the union is less than their sum by the rhombus
     assert O.frontal_area(seg[:1], 1.0 / 32) == pytest.approx(L * D, rel=1e-3)
+
+
+def test_refinement_boxes_of_a_hand_worked_case():
+    """Reading 12's box rule worked by hand for one vertical cylinder, finest
+    cells from (128, 128, 100) to (128, 128, 160), D = 8, three levels,
+    coarse 64^3 in 8^3 blocks:
+    bounding box x, y [124, 132], z [100, 160]; grown by 25 % of the extent
+    per side: x, y [122, 134], z [85, 175]; outward to whole finest blocks:
+    x, y [120, 136], z [80, 176].  Level 1: that box's footprint [60, 68] x
+    [60, 68] x [40, 88], outward to blocks [56, 72] x [56, 72] x [40, 88],
+    plus one block per side: [48, 80] x [48, 80] x [32, 96].  The library
+    builds the same boxes; a tree whose level-1 box would leave the domain is
+    rejected."""
+    from paper_2603_27954_gb300 import lbm as L
+    seg = np.array([[128.0, 128.0, 100.0, 128.0, 128.0, 160.0, 8.0, 0.0]])
+    want = [None, [48, 48, 32, 80, 80, 96], [120, 120, 80, 136, 136, 176]]
+    assert O.refine_boxes(seg, 3, (64, 64, 64), 8) == want
+    h = L.lbm_create_domain(L.domain_desc(64, 64, 64, levels=3, block=8, bc=("inout", "slip", "slip"),
+                                          nu_finest=0.01))
+    L.lbm_set_geometry_segments(h, seg)
+    for lv in (1, 2):
+        info = L.lbm_level_info(h, lv)
+        assert list(info["lo"]) + list(info["hi"]) == want[lv]
+    L.lbm_destroy(h)
+    # near the floor: the level-1 box would start at z = -8
+    low = np.array([[40.0, 32.0, 20.0, 40.0, 32.0, 40.0, 4.0, 0.0]])
+    assert O.refine_boxes(low, 3, (32, 16, 16), 8)[1][2] < 0
+    h = L.lbm_create_domain(L.domain_desc(32, 16, 16, levels=3, block=8, bc=("inout", "slip", "slip"),
+                                          nu_finest=0.01))
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_set_geometry_segments(h, low)
+    assert e.value.code == L.LBM_EINVAL
+    L.lbm_destroy(h)
