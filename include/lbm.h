@@ -246,8 +246,7 @@ int lbm_mass(lbm_domain* d, double* mass, double mom[3]);
    that device current (once, race-free across host threads); all calls
    share the one scratch array, so calls whose device work overlaps race and
    must be serialised by the caller.  The call copies its totals to host
-   memory and synchronises the domain's stream, so it must not be made while
-   that stream is being captured into a CUDA graph. */
+   memory and synchronises the domain's stream before it returns. */
 int lbm_mass_noalloc(lbm_domain* d, double* mass, double mom[3]);
 
 /* Mass and momentum of one level (as lbm_mass: FP64 on device, level-l
