@@ -2,6 +2,8 @@
 placement, tree height, frontal area, refinement boxes, cell classification
 per level and the cut links with their wall fractions.  Cell types and link
 sets are integer data and must agree exactly."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -23,7 +25,18 @@ def lib_domain(case):
     return h
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _release_oracle_cases():
+    """The cached oracle geometries (several GB for the four-level case) live
+    only as long as this module's tests."""
+    yield
+    oracle_case.cache_clear()
+
+
+@functools.lru_cache(maxsize=None)
 def oracle_case(case):
+    """The oracle's geometry of a workload case (built once per case; the
+    tests here only read it)."""
     c = W.CASES[case]
     return O.tree_case(*c["n0"], oracle_tree(c["tree"]), c["tree"]["trunk_cells"], c["re_h"], u_in=c["u_in"],
                        levels=c["levels"], block=c["block"], bc=c["bc"])
@@ -41,7 +54,7 @@ def test_lsystem_matches_oracle_paper_form(n):
     L.lbm_destroy(h)
 
 
-@pytest.mark.parametrize("case", ["tiny", "amr2_small", "amr2"])
+@pytest.mark.parametrize("case", ["tiny", "amr2_small", "amr2", "amr3_small", "amr4_quarter"])
 def test_geometry_scalars_match_oracle(case):
     h = lib_domain(case)
     g = L.lbm_geometry_info(h)
@@ -58,6 +71,16 @@ def test_geometry_scalars_match_oracle(case):
     for l in range(1, len(info["boxes"])):
         li = L.lbm_level_info(h, l)
         assert list(li["lo"]) + list(li["hi"]) == list(info["boxes"][l])
+    if case in ("amr3_small", "amr4_quarter"):
+        # fluid cells and cut links per level, and the cell updates of a coarse step (sum n_l 2^l)
+        sim, _ = oracle_case(case)
+        work = 0
+        for l in range(len(info["boxes"])):
+            li = L.lbm_level_info(h, l)
+            nf = int((sim.cell_type(l) == 0).sum())
+            assert li["n_fluid"] == nf and li["n_links"] == len(sim.links(l)[0])
+            work += nf << l
+        assert L.lbm_work_per_step(h)[0] == work
     L.lbm_destroy(h)
 
 
