@@ -72,7 +72,7 @@ def test_shielding_depth_tandem_and_side_by_side():
     assert S.shielding_depth(half, 1) == 0.5
 
 
-@pytest.mark.parametrize("case", ["tiny", "amr2_small"])
+@pytest.mark.parametrize("case", ["tiny", "amr2_small", "amr2", "amr4_quarter"])
 def test_library_branch_table_matches_oracle(case):
     c = W.CASES[case]
     d = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
