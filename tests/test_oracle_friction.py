@@ -93,7 +93,7 @@ def test_channel_wall_friction_balances_the_body_force(o):
     np.testing.assert_allclose(F, [g * (yb - ya), 0, 0], rtol=2e-3, atol=1e-12)
 
 
-@pytest.mark.parametrize("case", ["tiny", "amr2_small"])
+@pytest.mark.parametrize("case", ["tiny", "amr2_small", "amr2_quarter"])
 def test_library_quadrature_matches_oracle(case):
     c = W.CASES[case]
     d = L.domain_desc(*c["n0"], levels=c["levels"], block=c["block"], bc=c["bc"], u_in=c["u_in"],
