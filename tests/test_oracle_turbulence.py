@@ -55,14 +55,19 @@ def test_sampled_field_statistics(modes):
     assert np.abs(div).max() < 1e-6 * grad
 
 
-def test_library_mode_table_matches_oracle():
-    desc = L.domain_desc(64, 32, 32, bc=("inout", "slip", "slip"), u_in=U, nu_finest=0.02, i_u=I_U, seed=SEED)
+@pytest.mark.parametrize("seed,n,i_u,u,lint", [(SEED, 256, I_U, U, LINT), (0, 64, 0.15, 0.08, 6.0),
+                                                (2 ** 40 + 3, 128, 0.02, 0.03, 180.0)])
+def test_library_mode_table_matches_oracle(seed, n, i_u, u, lint):
+    """The library's mode table (host code) is the oracle's, for several seeds,
+    mode counts, intensities, speeds and integral lengths (down to the
+    wavenumber cap pi / 4 for short integral lengths)."""
+    desc = L.domain_desc(64, 32, 32, bc=("inout", "slip", "slip"), u_in=u, nu_finest=0.02, i_u=i_u, seed=seed)
     h = L.lbm_create_domain(desc)
     L.lbm_set_geometry_prims(h, [], np.zeros((0, 8)))
-    L.lbm_set_inflow_turbulence(h, 256, LINT)
+    L.lbm_set_inflow_turbulence(h, n, lint)
     lib_modes = L.lbm_inflow_modes(h)
     L.lbm_destroy(h)
-    np.testing.assert_allclose(lib_modes, T.rfm_modes(SEED, 256, I_U, U, LINT), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(lib_modes, T.rfm_modes(seed, n, i_u, u, lint), rtol=1e-12, atol=1e-15)
 
 
 def test_uniform_inflow_domain_has_no_modes():
