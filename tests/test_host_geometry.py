@@ -214,3 +214,20 @@ def test_ragged_domain_keeps_every_cell():
     assert info["n_active_blocks"] == 3 * 2 * 2
     assert (L.lbm_get_cell_types(h, 0) == 0).all()
     L.lbm_destroy(h)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_lsystem_with_four_distinct_children_matches_oracle(mode):
+    """Rule p1 with the most children the boundary allows (4), each with its
+    own length and diameter factor, branching angle and turn, in both child
+    orientation forms: the library's string rewriting and turtle give the
+    oracle's recursive turtle's segments."""
+    kw = dict(children=4, s0=40.0, w0=8.0, r=(0.7, 0.6, 0.5, 0.65), dfac=(0.7, 0.6, 0.55, 0.5),
+              alpha_deg=(25.0, -40.0, 55.0, -15.0), phi_deg=(0.0, 90.0, 200.0, 300.0), azimuth_mode=mode, seed=9)
+    h = L.lbm_create_domain(L.domain_desc(64, 64, 64, bc=("periodic",) * 3, nu_finest=0.01))
+    L.lbm_set_geometry(h, L.tree_desc(4, trunk_cells=20.0, **kw))
+    seg = L.lbm_get_segments(h)
+    L.lbm_destroy(h)
+    ref = O.place_tree(O.make_tree(4, **kw), 20.0, (64, 64, 64))
+    assert len(seg) == 1 + 4 + 16 + 64
+    np.testing.assert_allclose(seg, ref, rtol=0, atol=1e-9)
